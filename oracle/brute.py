@@ -1,0 +1,245 @@
+"""Dense brute-force evaluation of the DG weak form on tiny affine meshes.
+
+Test infrastructure only; its sole job is to pin ``residual``.  It shares the
+pointwise physics (``physics``: fluxes, LLF, wall states, which the tests pin
+separately against closed forms) but none of the discretisation code: it
+builds its own Lagrange polynomials (numpy.polynomial, nodes from numpy's
+Gauss-Legendre routine), fits each element's affine map from its node
+coordinates, integrates every term of the weak form (Sec. 3.3: volume term
+(F^nu - F^c) : grad V, surface numerical flux, BR1 lifting, mass matrix) with
+an independent higher-order Gauss rule, finds the neighbour's value at each
+face point by locating that physical point inside the neighbour (ignoring the
+nbr_face / orient tables), and solves with the dense mass matrix.
+
+On affine elements every integrand is a polynomial the higher-order rule
+integrates exactly, and the collocated scheme's Gauss-node quadrature is exact
+for the same integrands, so the two must agree to rounding.
+"""
+import itertools
+
+import numpy as np
+import torch
+from numpy.polynomial import Polynomial
+
+from . import physics as ph
+
+
+class _Lagrange:
+    def __init__(self, n):
+        self.x, _ = np.polynomial.legendre.leggauss(n)
+        self.l = []
+        for j in range(n):
+            others = [self.x[k] for k in range(n) if k != j]
+            poly = Polynomial.fromroots(others)
+            self.l.append(poly / poly(self.x[j]))
+        self.dl = [lj.deriv() for lj in self.l]
+
+    def val(self, t):
+        return np.array([lj(t) for lj in self.l])
+
+    def der(self, t):
+        return np.array([lj(t) for lj in self.dl])
+
+
+def _t(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float64))
+
+
+class BruteDG:
+    def __init__(self, mesh, gas, period=None):
+        self.mesh, self.gas = mesh, gas
+        self.d = d = mesh.dim
+        self.n = n = mesh.p + 1
+        self.N = n ** d
+        self.nf = d + 2
+        self.L = _Lagrange(n)
+        self.xq, self.wq = np.polynomial.legendre.leggauss(n + 3)
+        self.multi = [tuple((q // n ** a) % n for a in range(d)) for q in range(self.N)]
+        self.period = period
+        # affine maps x = x0 + A xi fitted from the node coordinates
+        self.x0, self.A = [], []
+        xi = self.L.x
+        design = np.array([[1.0] + [xi[m[a]] for a in range(d)] for m in self.multi])
+        for e in range(mesh.n_elem):
+            coef, *_ = np.linalg.lstsq(design, mesh.xyz[e].T, rcond=None)
+            self.x0.append(coef[0])
+            self.A.append(coef[1:].T)          # A[c][a] = dx_c / dxi_a
+
+    # ---- polynomial evaluation of nodal data of element e at a reference point
+    def basis_at(self, xi):
+        vals = [self.L.val(xi[a]) for a in range(self.d)]
+        ders = [self.L.der(xi[a]) for a in range(self.d)]
+        phi = np.array([np.prod([vals[a][m[a]] for a in range(self.d)]) for m in self.multi])
+        grad = np.array([[np.prod([(ders if b == a else vals)[b][m[b]] for b in range(self.d)])
+                          for a in range(self.d)] for m in self.multi])      # [N][a] d/dxi_a
+        return phi, grad
+
+    def locate(self, e, x):
+        """Reference coordinates of physical point x in element e (with periodic images)."""
+        Ainv = np.linalg.inv(self.A[e])
+        shifts = [np.zeros(self.d)]
+        if self.period is not None:
+            shifts = [np.array(s) * np.array(self.period)
+                      for s in itertools.product([-1, 0, 1], repeat=self.d)]
+        best = None
+        for s in shifts:
+            xi = Ainv @ (x + s - self.x0[e])
+            err = np.max(np.abs(xi)) - 1.0
+            if best is None or err < best[0]:
+                best = (err, xi)
+        assert best[0] < 1e-9, "face point not found in neighbour"
+        return best[1]
+
+    def face_points(self, a, side):
+        rest = [b for b in range(self.d) if b != a]
+        pts = []
+        for idx in itertools.product(range(self.n), repeat=self.d - 1):
+            xi = np.zeros(self.d)
+            xi[a] = -1.0 if side == 0 else 1.0
+            for k, b in enumerate(rest):
+                xi[b] = self.L.x[idx[k]]
+            pts.append((xi, idx))
+        return pts, rest
+
+    def normal(self, e, a, side):
+        J = np.linalg.det(self.A[e])
+        Ainv = np.linalg.inv(self.A[e])
+        v = J * Ainv[a, :]                    # J grad xi_a
+        return v if side == 1 else -v
+
+    # ---- the operator
+    def residual(self, U):
+        d, n, N, nf = self.d, self.n, self.N, self.nf
+        mesh, gas = self.mesh, self.gas
+        E = mesh.n_elem
+        U = np.asarray(U, dtype=np.float64)
+        quad = list(itertools.product(range(len(self.xq)), repeat=d))
+        qpts = [(np.array([self.xq[i[a]] for a in range(d)]), np.prod([self.wq[i[a]] for a in range(d)]))
+                for i in quad]
+        # mass matrices (dense, exact) and basis tables at quadrature points
+        tab = [self.basis_at(x) for x, _ in qpts]
+        mass, Ainvs, Js = [], [], []
+        for e in range(E):
+            J = abs(np.linalg.det(self.A[e]))
+            Ainv = np.linalg.inv(self.A[e])
+            M = sum(w * np.outer(phi, phi) for (x, w), (phi, _) in zip(qpts, tab)) * J
+            mass.append(M)
+            Ainvs.append(Ainv)
+            Js.append(J)
+
+        def eval_at(e, V, xi):                  # V[c][N] nodal data of element e
+            phi, _ = self.basis_at(xi)
+            return V @ phi
+
+        def face_rhs(e, a, side, values):       # sum over face points of values * l_q * face weight
+            pts, rest = self.face_points(a, side)
+            # integrate the face interpolant of ``values`` against l_q with the high rule
+            out = np.zeros((values.shape[1], N))
+            for iq in itertools.product(range(len(self.xq)), repeat=d - 1):
+                xi = np.zeros(d)
+                xi[a] = -1.0 if side == 0 else 1.0
+                wt = 1.0
+                face_phi = np.ones(len(pts))
+                for k, b in enumerate(rest):
+                    xi[b] = self.xq[iq[k]]
+                    wt *= self.wq[iq[k]]
+                for m, (_, idx) in enumerate(pts):
+                    face_phi[m] = np.prod([self.L.val(xi[b])[idx[k]] for k, b in enumerate(rest)])
+                phi, _ = self.basis_at(xi)
+                val = values.T @ face_phi         # [c]
+                out += wt * np.outer(val, phi)
+            return out
+
+        def neighbour_value(e, a, side, xi, V):
+            f = 2 * a + side
+            nb = mesh.neighbor[e, f]
+            x = self.x0[e] + self.A[e] @ xi
+            xin = self.locate(nb, x)
+            return nb, xin, eval_at(nb, V[nb], xin)
+
+        def wall(e, f):
+            return mesh.neighbor[e, f] < 0
+
+        # BR1 gradient, by projection
+        Q = np.zeros((E, d, nf, N))
+        if gas.viscous:
+            for e in range(E):
+                rhs = np.zeros((d, nf, N))
+                for (x, w), (phi, gref) in zip(qpts, tab):
+                    gx = gref @ self.Ainv_T(Ainvs[e])       # [N][c] d l_r / d x_c
+                    gradU = U[e] @ gx                       # [nf][c]
+                    for c in range(d):
+                        rhs[c] += w * Js[e] * np.outer(gradU[:, c], phi)
+                for a in range(d):
+                    for side in (0, 1):
+                        pts, _ = self.face_points(a, side)
+                        Sn = self.normal(e, a, side)
+                        jump = np.zeros((len(pts), nf))
+                        for m, (xi, _) in enumerate(pts):
+                            Um = eval_at(e, U[e], xi)
+                            if wall(e, 2 * a + side):
+                                Uhat = ph.wall_state(_t(Um[None]), d).numpy()[0]
+                            else:
+                                _, _, Up = neighbour_value(e, a, side, xi, U)
+                                Uhat = 0.5 * (Um + Up)
+                            jump[m] = Uhat - Um
+                        for c in range(d):
+                            rhs[c] += face_rhs(e, a, side, jump * Sn[c])
+                for c in range(d):
+                    Q[e, c] = np.linalg.solve(mass[e], rhs[c].T).T
+
+        def visc_G(e, xi, Sn, at_wall):
+            Uf = eval_at(e, U[e], xi)
+            Qf = np.stack([eval_at(e, Q[e, c], xi) for c in range(d)])
+            if at_wall:
+                return ph.adiabatic_wall_viscous_flux(_t(Uf[None]), _t(Qf[None]), _t(Sn[None]), gas, d).numpy()[0]
+            return ph.normal_viscous_flux(_t(Uf[None]), _t(Qf[None]), _t(Sn[None]), gas, d).numpy()[0]
+
+        f_out = np.zeros((E, nf, N))
+        for e in range(E):
+            B = np.zeros((nf, N))
+            # volume: - int (F^c - F^nu) : grad l_q
+            for (x, w), (phi, gref) in zip(qpts, tab):
+                gx = gref @ self.Ainv_T(Ainvs[e])           # [N][c]
+                Un = U[e] @ phi                               # interpolated nodal flux below
+                # interpolant of the nodal flux (collocation), evaluated at x
+                Fn = ph.convective_flux(_t(U[e].T), gas, d).numpy()       # [N][i][nf]
+                if gas.viscous:
+                    Fn = Fn - ph.viscous_flux(_t(U[e].T), _t(Q[e].transpose(2, 0, 1)), gas, d).numpy()
+                Fx = np.einsum("r,rif->if", phi, Fn)
+                B -= w * Js[e] * np.einsum("if,qi->fq", Fx, gx)
+            # surface
+            for a in range(d):
+                for side in (0, 1):
+                    f_id = 2 * a + side
+                    pts, _ = self.face_points(a, side)
+                    Sn = self.normal(e, a, side)
+                    vals = np.zeros((len(pts), nf))
+                    for m, (xi, _) in enumerate(pts):
+                        Um = eval_at(e, U[e], xi)
+                        if wall(e, f_id):
+                            Up = ph.mirror_state(_t(Um[None]), _t(Sn[None]), d).numpy()[0]
+                        else:
+                            nb, xin, Up = neighbour_value(e, a, side, xi, U)
+                        Fc = ph.llf_flux(_t(Um[None]), _t(Up[None]), _t(Sn[None]), gas, d).numpy()[0]
+                        Fv = 0.0
+                        if gas.viscous:
+                            if wall(e, f_id):
+                                Fv = visc_G(e, xi, Sn, True)
+                            else:
+                                # neighbour's own outward normal at the shared face
+                                an = int(np.argmax(np.abs(xin)))
+                                sn = 1 if xin[an] > 0 else 0
+                                Snb = self.normal(nb, an, sn)
+                                Gm = visc_G(e, xi, Sn, False)
+                                Gp = visc_G(nb, xin, Snb, False)
+                                Fv = 0.5 * (Gm - Gp)
+                        vals[m] = Fc - Fv
+                    B += face_rhs(e, a, side, vals)
+            f_out[e] = -np.linalg.solve(mass[e], B.T).T
+        return f_out
+
+    @staticmethod
+    def Ainv_T(Ainv):
+        # d l / d x_c = sum_a d l / d xi_a * d xi_a / d x_c = gref @ Ainv
+        return Ainv
