@@ -1,0 +1,151 @@
+/*
+ * dgx -- explicit discontinuous-Galerkin right-hand side for the compressible
+ * Euler / Navier-Stokes equations on one NVIDIA B300 (sm_103a).
+ *
+ * The library evaluates the explicit-region operator of a geometry-split IMEX
+ * scheme (the paper's Sec. 3.3 DG weak form with the mass matrix of the
+ * semi-discrete system in Sec. 4.2) and advances it with the explicit ARK
+ * stage and solution updates of Sec. 4.2 / Algorithm 1.  Readings used where
+ * the paper differs or is silent:
+ *   - convective numerical flux: local Lax-Friedrichs (Rusanov), wave speed
+ *     max over both sides of |u.n| + c (the paper uses the Vijayasundaram flux);
+ *   - viscous terms: BR1 (Bassi-Rebay 1) lifted gradient of the conservative
+ *     variables and the central viscous flux 1/2 (G^- - G^+), each side's
+ *     F^nu(U, Q) dotted with its own outward area normal (the paper uses SIPG);
+ *   - collocated nodal basis on (p+1)^d Gauss-Legendre points, diagonal mass;
+ *   - adiabatic no-slip walls: LLF against the mirror state, BR1 face value
+ *     U_w = (rho, 0, .., rho e_i) (App. B no-slip state) and the wall viscous
+ *     flux F^nu(U_w, Q^-).n with zero normal heat flux;
+ *   - sign: f(U) = dU/dt = -M^{-1} B(U), B the weak form of Sec. 3.3, so the
+ *     ERK update reads y_i = U_n + dt sum_j a_ij f(y_j).
+ *
+ * Data layout (all device buffers are caller-owned):
+ *   state U[E][nf][N], nf = d + 2 fields (rho, rho u, rho v, [rho w], rho E),
+ *   N = (p+1)^d nodes, node q = q0 + n q1 (+ n^2 q2), x index fastest;
+ *   FP64 handles take double buffers, FP32 handles float buffers (the ARK master
+ *   state is always double).
+ * Mesh tables (host arrays, copied): neighbor[E][2d] = element across local face
+ *   f (faces 2a: xi_a = -1, 2a+1: xi_a = +1) or -(1+tag) on a boundary
+ *   (tag 0 = adiabatic no-slip wall); nbr_face[E][2d] = the neighbour's local
+ *   face; orient[E][2d] maps the own face point (s, t) -- the two remaining
+ *   local indices in increasing axis order, index s + n t -- to the
+ *   neighbour's (u, v): bit 2 swaps s and t first, bit 0 reverses u, bit 1
+ *   reverses v (2D: only bit 0).
+ *
+ * Errors: every entry point returns a dgx_status; host-side validation fails
+ * synchronously with DGX_EINVAL and leaves the handle unchanged.  Device-side
+ * conditions (a non-finite residual) raise a flag that dgx_check() reports.
+ * No entry point exits, throws or prints.  All compute calls are asynchronous
+ * on the given stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream) and allocate nothing: scratch memory is the caller's workspace.
+ */
+#ifndef DGX_H
+#define DGX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DGX_OK = 0,
+  DGX_EINVAL = 1,       /* bad argument, inconsistent mesh table, size mismatch     */
+  DGX_ENOMEM = 2,       /* host or device allocation failed (set-up calls only)     */
+  DGX_ECUDA = 3,        /* a CUDA runtime call failed                               */
+  DGX_ENONFINITE = 4,   /* a kernel produced NaN/Inf (reported by dgx_check)        */
+  DGX_ETIMEOUT = 5,     /* a bounded device wait gave up (reported by dgx_check)    */
+  DGX_EUNSUPPORTED = 6, /* valid request this build does not implement              */
+  DGX_ESTATE = 7        /* call out of order (e.g. compute before a mesh is set)    */
+} dgx_status;
+
+typedef enum { DGX_FP64 = 0, DGX_FP32 = 1 } dgx_precision;
+
+/* Workspace kinds for dgx_workspace_bytes. */
+typedef enum { DGX_OP_RHS = 0, DGX_OP_VJP = 1, DGX_OP_ARK = 2, DGX_OP_ARK_ADJOINT = 3 } dgx_op;
+
+/* Problem statement (Sec. 2): dimension, polynomial degree k = p, element
+ * count, viscous (Navier-Stokes, 1) or inviscid (Euler, 0), arithmetic
+ * precision and the nondimensional parameters.  With rho_ref = |u_ref| =
+ * L_ref = 1 and theta_inf = 1: R = 1/(gamma Ma^2), mu = 1/Re (constant),
+ * kappa = c_p mu / Pr, lambda = -2 mu / 3 (Stokes).  Re, Pr are ignored when
+ * viscous = 0; Ma only fixes R, which the operator does not depend on. */
+typedef struct {
+  int32_t dim;        /* 2 or 3                                  */
+  int32_t p;          /* 1 .. 5                                  */
+  int32_t n_elem;     /* E >= 1                                  */
+  int32_t viscous;    /* 0 Euler, 1 Navier-Stokes (BR1)          */
+  int32_t precision;  /* dgx_precision                           */
+  double gamma, Re, Pr, Ma;
+} dgx_problem_desc;
+
+typedef struct dgx_handle dgx_handle;
+
+/* Create a handle (host + device set-up; allocates the handle's own small
+ * tables).  *out is NULL on failure. */
+dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out);
+dgx_status dgx_destroy(dgx_handle* h);
+
+/* Mesh of axis-aligned boxes (Sec. 3.1 mesh T_h): lower corner lo[E][d] and
+ * edge lengths size[E][d] > 0 (host, double).  Geometry is exact:
+ * J = prod(h_a/2), J dxi_a/dx_b = delta_ab prod_{c != a} h_c/2, so thin
+ * wall layers never go through coordinate differences.  Connectivity as in
+ * the header comment.  Replaces any previous mesh. */
+dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* size,
+                              const int32_t* neighbor, const int8_t* nbr_face, const int8_t* orient);
+
+/* Curvilinear mesh: node coordinates xyz[E][d][N] at the Gauss nodes (host,
+ * double); the element map is their degree-p tensor interpolant.  Metric terms
+ * are computed in FP64 on the host: 2D J dxi/dx = [[y_eta, -x_eta], [-y_xi, x_xi]],
+ * 3D the conservative curl form (discrete metric identities hold exactly).
+ * Interior faces use the averaged area normal (Sn^- - Sn^+)/2 in the
+ * convective flux, so the flux is exactly antisymmetric across a face. */
+dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz,
+                              const int32_t* neighbor, const int8_t* nbr_face, const int8_t* orient);
+
+/* Explicit Butcher tableau of an (s)-stage ERK (Sec. 4.2, padded ERK half of
+ * the ARK pair): A[s][s] row-major, strictly lower triangular, b[s], c[s]
+ * (host, double, copied).  s <= 8.  Default: none (dgx_ark_step -> DGX_ESTATE). */
+dgx_status dgx_set_tableau(dgx_handle* h, int32_t stages, const double* A, const double* b, const double* c);
+
+/* Bytes of caller-allocated device workspace for an operation (0 on error).
+ * The workspace must be 256-byte aligned; its contents need not be
+ * initialised and are not preserved between calls. */
+size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op);
+
+/* f = dU/dt = -M^{-1} B(U) (Sec. 3.3 weak form, Sec. 4.2 semi-discrete system):
+ * U, dUdt device [E][nf][N] in the handle's precision (distinct buffers).
+ * Covers face traces, BR1 gradient, LLF + BR1 face fluxes, volume fluxes,
+ * lifting and the inverse (diagonal) mass matrix. */
+dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, void* stream);
+
+/* Vector-Jacobian product gU = (df/dU)^T lambda of the operator above
+ * (hand-written adjoint: transposed contractions, transposed lifts and traces,
+ * pointwise flux Jacobians^T).  At exact ties of the LLF wave speed the
+ * interior side is differentiated; d|x|/dx at 0 is taken as 0. */
+dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace,
+                       void* stream);
+
+/* One explicit ARK step (Sec. 4.2 stage update y_i = U_n + dt sum_{j<i} a_ij f(y_j)
+ * and solution update U_{n+1} = U_n + dt sum_i b_i f(y_i); Algorithm 1 without
+ * the FSAL shortcut).  U64 (device, double [E][nf][N]) is updated in place;
+ * the stage residual and update are fused, the stage accumulation is in FP64
+ * (FP32 handles evaluate f in FP32 on a rounded copy of the stage state). */
+dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, void* stream);
+
+/* Synchronise with the device and report (then clear) device-side flags:
+ * DGX_ENONFINITE if any residual value was NaN/Inf since the last check. */
+dgx_status dgx_check(dgx_handle* h);
+
+const char* dgx_status_string(dgx_status s);
+
+/* Sizes the binding needs: element count, nodes per element, fields, face
+ * points per face, the chosen element-tile size. */
+dgx_status dgx_query(const dgx_handle* h, int32_t* n_elem, int32_t* nodes, int32_t* fields,
+                     int32_t* face_points, int32_t* tile);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

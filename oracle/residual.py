@@ -21,7 +21,9 @@ Dhat[i][m] = w_m D[m][i] / w_i this is, per node,
 
 where Fhat = s_J Fstar_n is the area-weighted outward numerical flux:
 
-  Fhat = LLF(U^-, U^+; Sn) - Fhat^nu,
+  Fhat = LLF(U^-, U^+; Sn_bar) - Fhat^nu,  Sn_bar = (Sn^- - Sn^+)/2 inside
+         (the two sides' outward area normals averaged; equal to Sn^- on
+         watertight faces), Sn^- on walls,
   Fhat^nu = 1/2 (G^- - G^+) on interior faces, G = F^nu(U_f, Q_f) . Sn_own
             (each side's viscous flux with its own outward normal),
   Fhat^nu = F^{nu,w}(U_w, Q^-) . Sn on adiabatic walls (q.n = 0).
@@ -168,7 +170,13 @@ class DGOperator:
 
     def convective_face_flux(self, TU_S, TUn_S, S):
         d, k = self.d, len(S)
-        Sn = self.geo.Sn[S].to(TU_S.dtype)
+        # interior faces: averaged area normal (Sn^- - Sn^+)/2, so the flux is
+        # exactly antisymmetric across the face (equal to Sn^- on watertight
+        # faces up to rounding); walls: own normal
+        Sn_own = self.geo.Sn[S]
+        Sn_nb = self.gather_neighbor(self.geo.Sn, S)
+        wall_f = (self.nb[S] < 0)[:, :, None, None]
+        Sn = torch.where(wall_f, Sn_own, 0.5 * (Sn_own - Sn_nb)).to(TU_S.dtype)
         UL = self._faces_flat(TU_S)
         Snf = Sn.permute(0, 1, 3, 2).reshape(-1, d)
         UR_int = self._faces_flat(TUn_S)
@@ -229,6 +237,41 @@ class DGOperator:
             parts.update(TU=TU[S0], Fface=Fface)
             return f, parts
         return f
+
+
+def term_scale(op, U, elems=None):
+    """Per-node magnitude of the terms the residual sums (test infrastructure).
+
+    The same weak form as ``residual`` with every flux and every matrix entry
+    replaced by its absolute value: (1/J) sum_a sum_m |Dhat| (|F^c~| + |F^nu~|)
+    + sum_faces |l/w| (|Fhat^c| + |Fhat^nu|) / J.  Two FP64 evaluations of f that
+    differ only in rounding order agree to a small multiple of eps times this
+    scale, however much the terms cancel (low-Mach or near-uniform states).
+    """
+    d, nf = op.d, op.nf
+    S0 = torch.arange(op.E) if elems is None else torch.as_tensor(elems, dtype=torch.long)
+    f, parts = op.residual(U, elems, return_parts=True)
+    Un = op.nodes(U)[S0]
+    flatU = Un.permute(0, *range(2, 2 + d), 1).reshape(-1, nf)
+    F = ph.convective_flux(flatU, op.gas, d).abs()
+    if op.gas.viscous:
+        Qflat = parts["Q"].permute(0, *range(3, 3 + d), 1, 2).reshape(-1, d, nf)
+        F = F + ph.viscous_flux(flatU, Qflat, op.gas, d).abs()
+    k0 = len(S0)
+    F = F.reshape((k0,) + (op.n,) * d + (d, nf)).permute(0, 1 + d, 2 + d, *range(1, 1 + d))
+    J = op.geo.J[S0]
+    Ja = op.geo.Ja[S0].abs()
+    vol = 0
+    for a in range(d):
+        Ft = sum(Ja[:, a, c].unsqueeze(1) * F[:, c] for c in range(d))
+        vol = vol + along(Ft, a, d, op.Dhat.abs())
+    saved = op.lift_vec
+    op.lift_vec = [v.abs() for v in saved]
+    try:
+        surf = op.lift(parts["Fface"].abs(), J)
+    finally:
+        op.lift_vec = saved
+    return (vol / J.unsqueeze(1) + surf).reshape(k0, nf, -1)
 
 
 def residual(mesh, gas, U, elems=None):

@@ -1,0 +1,143 @@
+"""Build libdgx.so: nvcc for sm_103a, one translation unit per (dim, precision,
+degree) so the kernel templates compile in parallel, linked into one shared
+library next to this file.  Run ``python -m paper_2607_16044_b300.build``.
+"""
+import concurrent.futures
+import hashlib
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(os.path.dirname(HERE), "_build")
+LIB = os.path.join(HERE, "libdgx.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "--expt-relaxed-constexpr", "-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")]
+DEGREES = (1, 2, 3, 4, 5)
+
+UNIT = """// generated by build.py: instantiation of the (D={D}, S={S}, P={P}) launch table
+#include "dispatch.h"
+namespace dgx {{
+namespace {{
+using Sc = {S};
+struct R {{
+  static cudaError_t rhs(const void* M, bool v, bool c, const void* U, void* out, const Work& w, cudaStream_t st) {{
+    return Ops<{D}, {P}, Sc>::rhs(*(const Mesh<Sc>*)M, v, c, (const Sc*)U, (Sc*)out, w, st);
+  }}
+  static cudaError_t tr64(const void* M, const double* U, void* TU, void* sh, cudaStream_t st) {{
+    return Ops<{D}, {P}, Sc>::template trace<double>(*(const Mesh<Sc>*)M, U, (Sc*)TU, (Sc*)sh, st);
+  }}
+  static cudaError_t stage(const void* M, bool v, bool c, const void* U, const Work& w, const void* sa, cudaStream_t st) {{
+    return Ops<{D}, {P}, Sc>::stage(*(const Mesh<Sc>*)M, v, c, (const Sc*)U, w, *(const Stage<Sc>*)sa, st);
+  }}
+{VJP_FN}
+}};
+}}  // namespace
+const Table* table_d{D}_{T}_p{P}() {{
+  static const Table t = {{&R::rhs, &R::tr64, &R::stage, {VJP_PTR}}};
+  return &t;
+}}
+}}  // namespace dgx
+"""
+
+DISPATCH = """// generated by build.py: degree dispatch
+#include "dispatch.h"
+namespace dgx {{
+{DECLS}
+{FUNCS}
+}}  // namespace dgx
+"""
+
+
+def _vjp_available():
+    return os.path.exists(os.path.join(CSRC, "vjp.cuh"))
+
+
+def _write_sources():
+    os.makedirs(BUILD, exist_ok=True)
+    units = []
+    decls, funcs = [], []
+    vjp = _vjp_available()
+    for D in (2, 3):
+        for S, T in (("double", "f64"), ("float", "f32")):
+            cases = []
+            for P in DEGREES:
+                name = f"table_d{D}_{T}_p{P}"
+                decls.append(f"const Table* {name}();")
+                cases.append(f"    case {P}: return {name}();")
+                vjp_fn = ""
+                vjp_ptr = "nullptr"
+                if vjp:
+                    vjp_fn = ("  static cudaError_t vjp(const void* M, bool v, bool c, const void* U, const void* lam,"
+                              " void* g, const void* vw, cudaStream_t st) {\n"
+                              f"    return Ops<{D}, {P}, Sc>::vjp(*(const Mesh<Sc>*)M, v, c, (const Sc*)U,"
+                              " (const Sc*)lam, (Sc*)g, *(const VjpWork*)vw, st);\n  }")
+                    vjp_ptr = "&R::vjp"
+                src = UNIT.format(D=D, S=S, P=P, T=T, VJP_FN=vjp_fn, VJP_PTR=vjp_ptr)
+                path = os.path.join(BUILD, f"unit_d{D}_{T}_p{P}.cu")
+                _write_if_changed(path, src)
+                units.append(path)
+            funcs.append(f"const Table* table_d{D}_{T}(int P) {{\n  switch (P) {{\n" + "\n".join(cases)
+                         + "\n    default: return nullptr;\n  }\n}")
+    path = os.path.join(BUILD, "dispatch_gen.cu")
+    _write_if_changed(path, DISPATCH.format(DECLS="\n".join(decls), FUNCS="\n".join(funcs)))
+    units.append(path)
+    units.append(os.path.join(CSRC, "host.cu"))
+    return units
+
+
+def _write_if_changed(path, text):
+    if os.path.exists(path) and open(path).read() == text:
+        return
+    with open(path, "w") as f:
+        f.write(text)
+
+
+def _deps_hash():
+    h = hashlib.sha256()
+    for root in (CSRC, os.path.join(os.path.dirname(HERE), "include")):
+        for name in sorted(os.listdir(root)):
+            if name.endswith((".cu", ".cuh", ".h")):
+                h.update(name.encode())
+                h.update(open(os.path.join(root, name), "rb").read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def _compile(src, deps):
+    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    stamp = obj + ".stamp"
+    key = deps + open(src).read()
+    key = hashlib.sha256(key.encode()).hexdigest()
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == key:
+        return obj
+    cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    with open(stamp, "w") as f:
+        f.write(key)
+    return obj
+
+
+def build(verbose=True, jobs=None):
+    units = _write_sources()
+    deps = _deps_hash()
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    with concurrent.futures.ThreadPoolExecutor(jobs) as ex:
+        objs = list(ex.map(lambda s: _compile(s, deps), units))
+    cmd = [NVCC, *ARCH, "-shared", "-o", LIB, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    if verbose:
+        print(f"built {LIB}")
+    return LIB
+
+
+if __name__ == "__main__":
+    build()
+    sys.exit(0)

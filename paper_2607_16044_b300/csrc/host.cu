@@ -1,0 +1,593 @@
+// Host runtime of the dgx library: handle, 1D basis, geometry (FP64), mesh
+// validation, unique-face list, workspace layout and the C ABI of dgx.h.
+//
+// Everything that depends only on the mesh is computed once here in FP64 and
+// uploaded in the handle's precision; the compute entry points only enqueue
+// kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dgx.h"
+#include "dispatch.h"
+
+using dgx::Tab;
+
+struct dgx_handle {
+  dgx_problem_desc desc;
+  int d, p, n, N, nf, nfp, NF, E, T;
+  bool viscous, fp64;
+  size_t s;  // bytes per scalar
+  const dgx::Table* tab;
+  void* d_tabs = nullptr;      // Tab<S>[6]
+  unsigned* d_flags = nullptr;
+  // mesh
+  bool has_mesh = false, curv = false;
+  int nFaces = 0;
+  int* d_nb = nullptr;
+  int8_t* d_nbf = nullptr;
+  int8_t* d_ori = nullptr;
+  int4* d_faces = nullptr;
+  void* d_rh = nullptr;
+  void* d_Ja = nullptr;
+  void* d_iJ = nullptr;
+  void* d_SnE = nullptr;
+  void* d_SnF = nullptr;
+  // tableau
+  int stages = 0;
+  double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
+};
+
+namespace {
+
+// ---------------------------------------------------------------- 1D basis
+// Gauss-Legendre nodes by Newton's method on P_n (three-term recurrence),
+// weights 2/((1-x^2) P_n'(x)^2); Lagrange derivative matrix from barycentric
+// weights, diagonal = -(sum of the row's off-diagonal entries).
+struct Basis {
+  int n;
+  std::vector<double> x, w, D, lm, lp;
+};
+
+void legendre(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    p = 1.0;
+    dp = 0.0;
+    return;
+  }
+  for (int k = 1; k < n; ++k) {
+    const double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (p0 - x * p1) / (1.0 - x * x);
+}
+
+Basis make_basis(int p) {
+  Basis B;
+  const int n = p + 1;
+  B.n = n;
+  B.x.resize(n);
+  B.w.resize(n);
+  for (int j = 0; j < n; ++j) {
+    double x = -std::cos(M_PI * (j + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double P, dP;
+      legendre(n, x, P, dP);
+      const double dx = P / dP;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    double P, dP;
+    legendre(n, x, P, dP);
+    B.x[j] = x;
+    B.w[j] = 2.0 / ((1.0 - x * x) * dP * dP);
+  }
+  std::vector<double> bw(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) bw[j] /= (B.x[j] - B.x[k]);
+  B.D.assign(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (i != j) {
+        B.D[i * n + j] = (bw[j] / bw[i]) / (B.x[i] - B.x[j]);
+        diag -= B.D[i * n + j];
+      }
+    B.D[i * n + i] = diag;
+  }
+  B.lm.assign(n, 1.0);
+  B.lp.assign(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) {
+        B.lm[j] *= (-1.0 - B.x[k]) / (B.x[j] - B.x[k]);
+        B.lp[j] *= (1.0 - B.x[k]) / (B.x[j] - B.x[k]);
+      }
+  return B;
+}
+
+template <typename S>
+void fill_tab(const Basis& B, Tab<S>& t) {
+  std::memset(&t, 0, sizeof(t));
+  const int n = B.n;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      t.D[i * 6 + j] = (S)B.D[i * n + j];
+      t.Dh[i * 6 + j] = (S)(B.w[j] * B.D[j * n + i] / B.w[i]);
+    }
+  for (int j = 0; j < n; ++j) {
+    t.lm[j] = (S)B.lm[j];
+    t.lp[j] = (S)B.lp[j];
+    t.Lm[j] = (S)(B.lm[j] / B.w[j]);
+    t.Lp[j] = (S)(B.lp[j] / B.w[j]);
+  }
+}
+
+int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+int omap(int code, int fp, int n, int d) {
+  if (d == 2) return (code & 1) ? n - 1 - fp : fp;
+  int s = fp % n, t = fp / n;
+  if (code & 4) std::swap(s, t);
+  const int u = (code & 1) ? n - 1 - s : s;
+  const int v = (code & 2) ? n - 1 - t : t;
+  return u + n * v;
+}
+
+int pw(int n, int a) { return a == 0 ? 1 : (a == 1 ? n : (a == 2 ? n * n : n * n * n)); }
+int node_of(int n, int m, int fp, int a) { return fp % pw(n, a) + m * pw(n, a) + (fp / pw(n, a)) * pw(n, a + 1); }
+int fpoint_of(int n, int q, int a) { return q % pw(n, a) + (q / pw(n, a + 1)) * pw(n, a); }
+
+template <typename T>
+dgx_status upload(const std::vector<T>& v, void** dst) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (v.empty()) return DGX_OK;
+  if (cudaMalloc(dst, v.size() * sizeof(T)) != cudaSuccess) return DGX_ENOMEM;
+  if (cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return DGX_ECUDA;
+  return DGX_OK;
+}
+
+dgx_status upload_real(dgx_handle* h, const std::vector<double>& v, void** dst) {
+  if (h->fp64) return upload(v, dst);
+  std::vector<float> f(v.size());
+  for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+  return upload(f, dst);
+}
+
+void free_mesh(dgx_handle* h) {
+  void* ptrs[] = {h->d_nb, h->d_nbf, h->d_ori, h->d_faces, h->d_rh, h->d_Ja, h->d_iJ, h->d_SnE, h->d_SnF};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  h->d_nb = nullptr;
+  h->d_nbf = nullptr;
+  h->d_ori = nullptr;
+  h->d_faces = nullptr;
+  h->d_rh = h->d_Ja = h->d_iJ = h->d_SnE = h->d_SnF = nullptr;
+  h->has_mesh = false;
+}
+
+// Connectivity checks shared by both mesh kinds; builds the unique-face list.
+dgx_status check_connectivity(dgx_handle* h, const int32_t* nb, const int8_t* nbf, const int8_t* ori,
+                              std::vector<int4>& faces) {
+  const int E = h->E, NF = h->NF, n = h->n, d = h->d, nfp = h->nfp;
+  const int maxcode = d == 2 ? 2 : 8;
+  faces.clear();
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < NF; ++f) {
+      const int k = e * NF + f;
+      const int o = nb[k];
+      if (o < 0) {
+        if (o != -1) return DGX_EUNSUPPORTED;  // only tag 0 (adiabatic wall) is implemented
+        faces.push_back(make_int4(e, o, f, 0));
+        continue;
+      }
+      if (o >= E) return DGX_EINVAL;
+      const int of = nbf[k];
+      if (of < 0 || of >= NF || ori[k] < 0 || ori[k] >= maxcode) return DGX_EINVAL;
+      const int k2 = o * NF + of;
+      if (nb[k2] != e || nbf[k2] != f) return DGX_EINVAL;  // not reciprocal
+      for (int fp = 0; fp < nfp; ++fp)
+        if (omap(ori[k2], omap(ori[k], fp, n, d), n, d) != fp) return DGX_EINVAL;
+      if (e < o || (e == o && f < of)) faces.push_back(make_int4(e, o, f | (of << 8) | (ori[k] << 16), 0));
+    }
+  return DGX_OK;
+}
+
+dgx_status upload_connectivity(dgx_handle* h, const int32_t* nb, const int8_t* nbf, const int8_t* ori,
+                               const std::vector<int4>& faces) {
+  const size_t m = (size_t)h->E * h->NF;
+  std::vector<int> vnb(nb, nb + m);
+  std::vector<int8_t> vnbf(nbf, nbf + m), vori(ori, ori + m);
+  dgx_status s;
+  if ((s = upload(vnb, (void**)&h->d_nb)) != DGX_OK) return s;
+  if ((s = upload(vnbf, (void**)&h->d_nbf)) != DGX_OK) return s;
+  if ((s = upload(vori, (void**)&h->d_ori)) != DGX_OK) return s;
+  if ((s = upload(faces, (void**)&h->d_faces)) != DGX_OK) return s;
+  h->nFaces = (int)faces.size();
+  return DGX_OK;
+}
+
+template <typename S>
+dgx::Mesh<S> mesh_view(const dgx_handle* h) {
+  dgx::Mesh<S> M;
+  M.E = h->E;
+  M.nFaces = h->nFaces;
+  M.nb = h->d_nb;
+  M.nbf = h->d_nbf;
+  M.ori = h->d_ori;
+  M.faces = h->d_faces;
+  M.geo.rh = (const S*)h->d_rh;
+  M.geo.Ja = (const S*)h->d_Ja;
+  M.geo.iJ = (const S*)h->d_iJ;
+  M.geo.SnE = (const S*)h->d_SnE;
+  M.geo.SnF = (const S*)h->d_SnF;
+  M.tabs = (const Tab<S>*)h->d_tabs;
+  const double g = h->desc.gamma;
+  const double mu = h->viscous ? 1.0 / h->desc.Re : 0.0;
+  M.gas.gamma = (S)g;
+  M.gas.gm1 = (S)(g - 1.0);
+  M.gas.mu = (S)mu;
+  M.gas.lam = (S)(-2.0 * mu / 3.0);
+  M.gas.kcv = (S)(h->viscous ? g * mu / h->desc.Pr : 0.0);
+  M.flags = h->d_flags;
+  return M;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t TU, FF, G, Q, Y, K, SH, total;
+};
+
+Layout layout(const dgx_handle* h, int op) {
+  Layout L{};
+  const size_t face = (size_t)h->E * h->NF * h->nf * h->nfp * h->s;
+  const size_t state = (size_t)h->E * h->nf * h->N * h->s;
+  size_t off = 0;
+  L.TU = off;
+  off += align256(face);
+  L.FF = off;
+  off += align256(face);
+  if (h->viscous) {
+    L.G = off;
+    off += align256(face);
+    L.Q = off;
+    off += align256(state * h->d);
+  }
+  if (op == DGX_OP_ARK) {
+    L.Y = off;
+    off += align256(state);
+    L.K = off;
+    off += align256(state) * (h->stages > 1 ? h->stages - 1 : 0);
+    if (!h->fp64) {
+      L.SH = off;
+      off += align256(state);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+dgx::Work work_at(const dgx_handle* h, void* ws, const Layout& L) {
+  char* b = (char*)ws;
+  dgx::Work w;
+  w.TU = b + L.TU;
+  w.FF = b + L.FF;
+  w.G = h->viscous ? b + L.G : nullptr;
+  w.Q = h->viscous ? b + L.Q : nullptr;
+  return w;
+}
+
+dgx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DGX_OK : DGX_ECUDA; }
+
+template <typename S>
+dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cudaStream_t st) {
+  const Layout L = layout(h, DGX_OP_ARK);
+  const dgx::Work w = work_at(h, workspace, L);
+  char* base = (char*)workspace;
+  S* Y = (S*)(base + L.Y);
+  const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
+  S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
+  const dgx::Mesh<S> M = mesh_view<S>(h);
+  cudaError_t err = h->tab->trace_from64(&M, U64, w.TU, shadow, st);
+  if (err != cudaSuccess) return DGX_ECUDA;
+  const S* y0 = h->fp64 ? (const S*)U64 : shadow;
+  const int s = h->stages;
+  for (int i = 0; i < s; ++i) {
+    dgx::Stage<S> sa{};
+    for (int j = 0; j < i; ++j) sa.k[j] = (const S*)(base + L.K + state * j);
+    sa.i = i;
+    sa.last = (i == s - 1);
+    if (!sa.last)
+      for (int j = 0; j <= i; ++j) sa.ca[j] = (S)(dt * h->A[(i + 1) * dgx::MAXSTAGES + j]);
+    for (int j = 0; j < s; ++j) sa.cb[j] = dt * h->b[j];
+    sa.base = y0;
+    sa.Un = U64;
+    sa.Y = Y;
+    sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
+    sa.shadow = shadow;
+    sa.TU = (S*)w.TU;
+    const S* Uin = (i == 0) ? y0 : Y;
+    err = h->tab->stage(&M, h->viscous, h->curv, Uin, w, &sa, st);
+    if (err != cudaSuccess) return DGX_ECUDA;
+  }
+  return DGX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dgx_status_string(dgx_status s) {
+  switch (s) {
+    case DGX_OK: return "ok";
+    case DGX_EINVAL: return "invalid argument";
+    case DGX_ENOMEM: return "out of memory";
+    case DGX_ECUDA: return "CUDA error";
+    case DGX_ENONFINITE: return "non-finite residual";
+    case DGX_ETIMEOUT: return "device wait timed out";
+    case DGX_EUNSUPPORTED: return "unsupported";
+    case DGX_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
+  if (!out) return DGX_EINVAL;
+  *out = nullptr;
+  if (!desc) return DGX_EINVAL;
+  if (desc->dim != 2 && desc->dim != 3) return DGX_EINVAL;
+  if (desc->p < 1 || desc->p > 5 || desc->n_elem < 1) return DGX_EINVAL;
+  if (desc->precision != DGX_FP64 && desc->precision != DGX_FP32) return DGX_EINVAL;
+  if (!(desc->gamma > 1.0)) return DGX_EINVAL;
+  if (desc->viscous && (!(desc->Re > 0.0) || !(desc->Pr > 0.0))) return DGX_EINVAL;
+  dgx_handle* h = new (std::nothrow) dgx_handle();
+  if (!h) return DGX_ENOMEM;
+  h->desc = *desc;
+  h->d = desc->dim;
+  h->p = desc->p;
+  h->n = desc->p + 1;
+  h->N = ipow(h->n, h->d);
+  h->nf = h->d + 2;
+  h->nfp = ipow(h->n, h->d - 1);
+  h->NF = 2 * h->d;
+  h->E = desc->n_elem;
+  h->T = (256 / h->N) > 0 ? 256 / h->N : 1;
+  h->viscous = desc->viscous != 0;
+  h->fp64 = desc->precision == DGX_FP64;
+  h->s = h->fp64 ? 8 : 4;
+  if (h->d == 2) h->tab = h->fp64 ? dgx::table_d2_f64(h->p) : dgx::table_d2_f32(h->p);
+  else h->tab = h->fp64 ? dgx::table_d3_f64(h->p) : dgx::table_d3_f32(h->p);
+  if (!h->tab) {
+    delete h;
+    return DGX_EUNSUPPORTED;
+  }
+  dgx_status st = DGX_OK;
+  if (h->fp64) {
+    std::vector<Tab<double>> t(6);
+    for (int p = 1; p <= 5; ++p) fill_tab(make_basis(p), t[p]);
+    st = upload(t, &h->d_tabs);
+  } else {
+    std::vector<Tab<float>> t(6);
+    for (int p = 1; p <= 5; ++p) fill_tab(make_basis(p), t[p]);
+    st = upload(t, &h->d_tabs);
+  }
+  if (st == DGX_OK && cudaMalloc((void**)&h->d_flags, sizeof(unsigned)) != cudaSuccess) st = DGX_ENOMEM;
+  if (st == DGX_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) st = DGX_ECUDA;
+  if (st != DGX_OK) {
+    dgx_destroy(h);
+    return st;
+  }
+  *out = h;
+  return DGX_OK;
+}
+
+dgx_status dgx_destroy(dgx_handle* h) {
+  if (!h) return DGX_EINVAL;
+  free_mesh(h);
+  if (h->d_tabs) cudaFree(h->d_tabs);
+  if (h->d_flags) cudaFree(h->d_flags);
+  delete h;
+  return DGX_OK;
+}
+
+dgx_status dgx_query(const dgx_handle* h, int32_t* n_elem, int32_t* nodes, int32_t* fields, int32_t* face_points,
+                     int32_t* tile) {
+  if (!h) return DGX_EINVAL;
+  if (n_elem) *n_elem = h->E;
+  if (nodes) *nodes = h->N;
+  if (fields) *fields = h->nf;
+  if (face_points) *face_points = h->nfp;
+  if (tile) *tile = h->T;
+  return DGX_OK;
+}
+
+dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* size, const int32_t* neighbor,
+                              const int8_t* nbr_face, const int8_t* orient) {
+  if (!h || !lo || !size || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
+  const int E = h->E, d = h->d;
+  for (size_t i = 0; i < (size_t)E * d; ++i)
+    if (!(size[i] > 0.0) || !std::isfinite(size[i]) || !std::isfinite(lo[i])) return DGX_EINVAL;
+  std::vector<int4> faces;
+  dgx_status st = check_connectivity(h, neighbor, nbr_face, orient, faces);
+  if (st != DGX_OK) return st;
+  free_mesh(h);
+  std::vector<double> rh((size_t)E * d);
+  for (size_t i = 0; i < rh.size(); ++i) rh[i] = 2.0 / size[i];
+  if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
+  if ((st = upload_real(h, rh, &h->d_rh)) != DGX_OK) return st;
+  h->curv = false;
+  h->has_mesh = true;
+  return DGX_OK;
+}
+
+dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
+                              const int8_t* orient) {
+  if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
+  const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
+  for (size_t i = 0; i < (size_t)E * d * N; ++i)
+    if (!std::isfinite(xyz[i])) return DGX_EINVAL;
+  std::vector<int4> faces;
+  dgx_status st = check_connectivity(h, neighbor, nbr_face, orient, faces);
+  if (st != DGX_OK) return st;
+  const Basis B = make_basis(h->p);
+  // derivative of nodal data along direction a
+  auto along = [&](const double* v, int a, double* out) {
+    for (int q = 0; q < N; ++q) {
+      const int fp = fpoint_of(n, q, a), qa = (q / pw(n, a)) % n;
+      double s = 0.0;
+      for (int m = 0; m < n; ++m) s += B.D[qa * n + m] * v[node_of(n, m, fp, a)];
+      out[q] = s;
+    }
+  };
+  std::vector<double> Ja((size_t)E * d * d * N), iJ((size_t)E * N), SnE((size_t)E * NF * d * nfp);
+  std::vector<double> dX(d * d * N), G(N), tmp(N), tmp2(N);
+  for (int e = 0; e < E; ++e) {
+    const double* X = xyz + (size_t)e * d * N;
+    for (int c = 0; c < d; ++c)
+      for (int b = 0; b < d; ++b) along(X + c * N, b, &dX[(c * d + b) * N]);  // dX[c][b] = dx_c/dxi_b
+    double* JaE = &Ja[(size_t)e * d * d * N];
+    for (int q = 0; q < N; ++q) {
+      double J;
+      auto m = [&](int c, int b) { return dX[(c * d + b) * N + q]; };
+      if (d == 2) {
+        J = m(0, 0) * m(1, 1) - m(0, 1) * m(1, 0);
+        JaE[(0 * d + 0) * N + q] = m(1, 1);
+        JaE[(0 * d + 1) * N + q] = -m(0, 1);
+        JaE[(1 * d + 0) * N + q] = -m(1, 0);
+        JaE[(1 * d + 1) * N + q] = m(0, 0);
+      } else {
+        J = m(0, 0) * (m(1, 1) * m(2, 2) - m(1, 2) * m(2, 1)) - m(0, 1) * (m(1, 0) * m(2, 2) - m(1, 2) * m(2, 0)) +
+            m(0, 2) * (m(1, 0) * m(2, 1) - m(1, 1) * m(2, 0));
+      }
+      if (!(J > 0.0)) return DGX_EINVAL;  // inverted or degenerate element
+      iJ[(size_t)e * N + q] = 1.0 / J;
+    }
+    if (d == 3) {
+      // conservative curl form: Ja[i][c] = -(D_j (X_l d_k X_m) - D_k (X_l d_j X_m)),
+      // (c, m, l) cyclic, (i, j, k) cyclic
+      for (int c = 0; c < 3; ++c) {
+        const int mm = (c + 1) % 3, ll = (c + 2) % 3;
+        for (int i = 0; i < 3; ++i) {
+          const int j = (i + 1) % 3, k = (i + 2) % 3;
+          for (int q = 0; q < N; ++q) G[q] = X[ll * N + q] * dX[(mm * 3 + k) * N + q];
+          along(G.data(), j, tmp.data());
+          for (int q = 0; q < N; ++q) G[q] = X[ll * N + q] * dX[(mm * 3 + j) * N + q];
+          along(G.data(), k, tmp2.data());
+          for (int q = 0; q < N; ++q) JaE[(i * 3 + c) * N + q] = -(tmp[q] - tmp2[q]);
+        }
+      }
+    }
+    // own outward area normals: +-Ja_a traced to xi_a = +-1
+    for (int face = 0; face < NF; ++face) {
+      const int a = face >> 1;
+      const std::vector<double>& l = (face & 1) ? B.lp : B.lm;
+      const double sgn = (face & 1) ? 1.0 : -1.0;
+      for (int c = 0; c < d; ++c)
+        for (int fp = 0; fp < nfp; ++fp) {
+          double s = 0.0;
+          for (int m = 0; m < n; ++m) s += l[m] * JaE[(a * d + c) * N + node_of(n, m, fp, a)];
+          SnE[(((size_t)e * NF + face) * d + c) * nfp + fp] = sgn * s;
+        }
+    }
+  }
+  // averaged normals of the unique faces, in the owner's face-point order
+  std::vector<double> SnF(faces.size() * d * nfp);
+  for (size_t F = 0; F < faces.size(); ++F) {
+    const int4 r = faces[F];
+    const int em = r.x, ep = r.y, fm = r.z & 0xff, fo = (r.z >> 8) & 0xff, code = (r.z >> 16) & 0xff;
+    for (int c = 0; c < d; ++c)
+      for (int fp = 0; fp < nfp; ++fp) {
+        const double own = SnE[(((size_t)em * NF + fm) * d + c) * nfp + fp];
+        double v = own;
+        if (ep >= 0) v = 0.5 * (own - SnE[(((size_t)ep * NF + fo) * d + c) * nfp + omap(code, fp, n, d)]);
+        SnF[(F * d + c) * nfp + fp] = v;
+      }
+  }
+  free_mesh(h);
+  if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
+  if ((st = upload_real(h, Ja, &h->d_Ja)) != DGX_OK) return st;
+  if ((st = upload_real(h, iJ, &h->d_iJ)) != DGX_OK) return st;
+  if ((st = upload_real(h, SnE, &h->d_SnE)) != DGX_OK) return st;
+  if ((st = upload_real(h, SnF, &h->d_SnF)) != DGX_OK) return st;
+  h->curv = true;
+  h->has_mesh = true;
+  return DGX_OK;
+}
+
+dgx_status dgx_set_tableau(dgx_handle* h, int32_t stages, const double* A, const double* b, const double* c) {
+  if (!h || !A || !b || !c || stages < 1 || stages > dgx::MAXSTAGES) return DGX_EINVAL;
+  for (int i = 0; i < stages; ++i)
+    for (int j = i; j < stages; ++j)
+      if (A[i * stages + j] != 0.0) return DGX_EINVAL;  // explicit only
+  h->stages = stages;
+  for (int i = 0; i < stages; ++i) {
+    for (int j = 0; j < stages; ++j) h->A[i * dgx::MAXSTAGES + j] = A[i * stages + j];
+    h->b[i] = b[i];
+    h->c[i] = c[i];
+  }
+  return DGX_OK;
+}
+
+size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
+  if (!h) return 0;
+  if (op == DGX_OP_ARK && h->stages == 0) return 0;
+  if (op < DGX_OP_RHS || op > DGX_OP_ARK) return 0;
+  return layout(h, op).total;
+}
+
+dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, void* stream) {
+  if (!h || !U || !dUdt || !workspace || U == dUdt) return DGX_EINVAL;
+  if (!h->has_mesh) return DGX_ESTATE;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  const Layout L = layout(h, DGX_OP_RHS);
+  const dgx::Work w = work_at(h, workspace, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->fp64) {
+    const dgx::Mesh<double> M = mesh_view<double>(h);
+    return cuda_status(h->tab->rhs(&M, h->viscous, h->curv, U, dUdt, w, st));
+  }
+  const dgx::Mesh<float> M = mesh_view<float>(h);
+  return cuda_status(h->tab->rhs(&M, h->viscous, h->curv, U, dUdt, w, st));
+}
+
+dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace, void* stream) {
+  if (!h || !U || !lambda || !gU || !workspace) return DGX_EINVAL;
+  if (!h->has_mesh) return DGX_ESTATE;
+  (void)stream;
+  return DGX_EUNSUPPORTED;
+}
+
+dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, void* stream) {
+  if (!h || !U64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->fp64) return ark_impl<double>(h, U64, dt, workspace, (cudaStream_t)stream);
+  return ark_impl<float>(h, U64, dt, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_check(dgx_handle* h) {
+  if (!h) return DGX_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DGX_ECUDA;
+  unsigned flags = 0;
+  if (cudaMemcpy(&flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return DGX_ECUDA;
+  if (cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) return DGX_ECUDA;
+  if (flags & 1u) return DGX_ENONFINITE;
+  if (flags & 2u) return DGX_ETIMEOUT;
+  return DGX_OK;
+}
+
+}  // extern "C"

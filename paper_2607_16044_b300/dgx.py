@@ -1,0 +1,196 @@
+"""Python binding of libdgx.so (the C ABI in include/dgx.h).
+
+Argument marshalling only: torch supplies device memory and the current CUDA
+stream, every step of the computation runs in the library's kernels.  There
+is no CPU fallback -- importing works anywhere, but constructing a ``Solver``
+raises if the shared library is missing or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgx.so")
+
+FP64, FP32 = 0, 1
+OP_RHS, OP_VJP, OP_ARK, OP_ARK_ADJOINT = 0, 1, 2, 3
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite residual",
+          5: "device wait timed out", 6: "unsupported", 7: "call out of order"}
+
+
+class DGXError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("p", ctypes.c_int32), ("n_elem", ctypes.c_int32),
+                ("viscous", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("Re", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("Ma", ctypes.c_double)]
+
+
+_lib = None
+
+EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_nodes", "dgx_set_tableau",
+           "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
+           "dgx_status_string", "dgx_query"]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdgx.so and declare its signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.dgx_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+    lib.dgx_destroy.argtypes = [vp]
+    lib.dgx_set_mesh_boxes.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.dgx_set_mesh_nodes.argtypes = [vp, vp, vp, vp, vp]
+    lib.dgx_set_tableau.argtypes = [vp, i32, vp, vp, vp]
+    lib.dgx_workspace_bytes.argtypes = [vp, i32]
+    lib.dgx_workspace_bytes.restype = ctypes.c_size_t
+    lib.dgx_rhs.argtypes = [vp, vp, vp, vp, vp]
+    lib.dgx_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.dgx_ark_step.argtypes = [vp, vp, dbl, vp, vp]
+    lib.dgx_check.argtypes = [vp]
+    lib.dgx_status_string.argtypes = [i32]
+    lib.dgx_status_string.restype = ctypes.c_char_p
+    lib.dgx_query.argtypes = [vp] + [ctypes.POINTER(i32)] * 5
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    lib.dgx_workspace_bytes.restype = ctypes.c_size_t
+    lib.dgx_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise DGXError(code, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """Explicit DG right-hand side on one mesh (see include/dgx.h).
+
+    ``mesh`` is a :class:`paper_2607_16044_b300.inputs.Mesh`; ``phys`` an
+    :class:`inputs.Physics`.  ``precision`` is "fp64" or "fp32".
+    """
+
+    def __init__(self, mesh, phys, precision: str = "fp64", device: Optional[torch.device] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("dgx needs a CUDA device; there is no CPU fallback")
+        self.lib = load_library()
+        self.mesh = mesh
+        self.phys = phys
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        desc = _Desc(mesh.dim, mesh.p, mesh.n_elem, int(phys.viscous), FP64 if precision == "fp64" else FP32,
+                     phys.gamma, phys.Re if phys.viscous else 0.0, phys.Pr, phys.Ma)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.dgx_create(ctypes.byref(desc), ctypes.byref(h)), "dgx_create")
+        self.h = h
+        self.shape = (mesh.n_elem, mesh.dim + 2, mesh.N)
+        nb = np.ascontiguousarray(mesh.neighbor, dtype=np.int32)
+        nbf = np.ascontiguousarray(mesh.nbr_face, dtype=np.int8)
+        ori = np.ascontiguousarray(mesh.orient, dtype=np.int8)
+        if mesh.kind == "boxes":
+            lo = np.ascontiguousarray(mesh.lo, dtype=np.float64)
+            sz = np.ascontiguousarray(mesh.size, dtype=np.float64)
+            _check(self.lib.dgx_set_mesh_boxes(h, _ptr(lo), _ptr(sz), _ptr(nb), _ptr(nbf), _ptr(ori)),
+                   "dgx_set_mesh_boxes")
+        else:
+            xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+            _check(self.lib.dgx_set_mesh_nodes(h, _ptr(xyz), _ptr(nb), _ptr(nbf), _ptr(ori)), "dgx_set_mesh_nodes")
+        self._ws = {}
+        self.stages = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dgx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def workspace(self, op: int) -> torch.Tensor:
+        nbytes = int(self.lib.dgx_workspace_bytes(self.h, op))
+        if nbytes == 0:
+            raise DGXError(7, "dgx_workspace_bytes")
+        ws = self._ws.get(op)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            self._ws[op] = ws
+        return ws
+
+    @staticmethod
+    def _aligned(ws: torch.Tensor):
+        p = ws.data_ptr()
+        return ctypes.c_void_p((p + 255) & ~255)
+
+    def _state(self, U, name="U", dtype=None):
+        dtype = dtype or self.dtype
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == dtype and U.is_contiguous()
+                and tuple(U.shape) == self.shape):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {self.shape}")
+        return ctypes.c_void_p(U.data_ptr())
+
+    def empty_state(self, dtype=None):
+        return torch.empty(self.shape, dtype=dtype or self.dtype, device=self.device)
+
+    def set_tableau(self, A, b, c):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        _check(self.lib.dgx_set_tableau(self.h, len(b), _ptr(A), _ptr(b), _ptr(c)), "dgx_set_tableau")
+        self.stages = len(b)
+        self._ws.pop(OP_ARK, None)
+
+    # ------------------------------------------------------------------ compute
+    def rhs(self, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        out = self.empty_state() if out is None else out
+        ws = self.workspace(OP_RHS)
+        _check(self.lib.dgx_rhs(self.h, self._state(U), self._state(out, "out"), self._aligned(ws),
+                                _stream_ptr(stream)), "dgx_rhs")
+        return out
+
+    def rhs_vjp(self, U: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+        out = self.empty_state() if out is None else out
+        ws = self.workspace(OP_VJP)
+        _check(self.lib.dgx_rhs_vjp(self.h, self._state(U), self._state(lam, "lambda"), self._state(out, "out"),
+                                    self._aligned(ws), _stream_ptr(stream)), "dgx_rhs_vjp")
+        return out
+
+    def ark_step(self, U64: torch.Tensor, dt: float, stream=None) -> torch.Tensor:
+        ws = self.workspace(OP_ARK)
+        _check(self.lib.dgx_ark_step(self.h, self._state(U64, "U64", torch.float64), float(dt), self._aligned(ws),
+                                     _stream_ptr(stream)), "dgx_ark_step")
+        return U64
+
+    def check(self):
+        _check(self.lib.dgx_check(self.h), "dgx_check")
