@@ -1,0 +1,381 @@
+"""Benchmark: DG residual DOF-evaluations per second on one B300.
+
+Workload: the 2D compressible Navier-Stokes channel -- x in [0, 5) periodic
+with 256 columns, y in [-1, 1] with 2 x 64 rows grown from each wall by ratio
+1.15 (aspect ratios up to ~1e3), adiabatic walls, p = 4 (25 Gauss nodes per
+element, 3,276,800 DOFs), Re = 1000, Ma = 0.3, Pr = 0.72, BR1 viscous flux,
+Poiseuille state with a seeded 1e-3 perturbation (synthetic, seeded).
+
+One step = one explicit ARS(3,4,3) step (4 fused residual + stage-update
+evaluations) followed by its discrete adjoint (reverse stage recurrence: 4
+vector-Jacobian products of the residual), i.e. 8 DOF-residual evaluations
+per DOF.  The headline runs the FP32 path (FP64 stage accumulation); the FP64
+path is measured the same way and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgx|reference]
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DG residual DOF-evals/s (fwd+VJP), % HBM roofline, FP32 vs FP64 at stated L2 err"
+UNIT = "DOF-evals/s"
+WORKLOAD = "2D NS channel 256x128 quads, wall stretching 1.15 (AR~1e3), p=4, Re=1000, Ma=0.3, Pr=0.72, BR1+LLF"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2032.0)}
+    return {"hbm_gbs": 6400.0, "source": "fallback", "sm_max_mhz": 2032.0}
+
+
+# ALU peaks derived from unit counts and the maximum SM clock (2032 MHz):
+# FP32: 148 SMs x 128 lanes x 2 flop/FMA; FP64: the nominal 1.25 TFLOP/s of B300.
+def alu_peak_tflops(prec, sm_mhz=2032.0):
+    if prec == "fp32":
+        return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return 1.25
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work per kernel launch (per element; s = bytes per scalar).
+# Bytes: each input read once and each output written once, as the kernel is
+# designed.  Flops: counted per node / face point from the operation list of
+# each kernel (FMA = 2 flops; a division or square root = 1).
+# ---------------------------------------------------------------------------
+def kernel_model(d, p, viscous, prec, stage_i=1, stages=4):
+    n = p + 1
+    N = n ** d
+    nf = d + 2
+    nfp = n ** (d - 1)
+    NF = 2 * d
+    s = 8 if prec == "fp64" else 4
+    state, face = nf * N, NF * nf * nfp
+    # pointwise flop counts
+    conv = 1 + 3 * d + 4 + d * (3 * d + 3)             # 1/rho, u, p, fluxes
+    visc = 1 + d + 2 + d * (6 + 4 * d) + d * d * 6 + d * (2 * d + 3)   # grads, tau, F^nu
+    llf = 2 * (1 + 4 * d + 6 + (3 * d + 4) + 3) + 2 + 3 * nf + (3 if d else 0)
+    m = {}
+    m["trace"] = {"bytes": state * 8 + state * s + face * s, "flops": face * 2 * n}
+    m["br1"] = {"bytes": state * s + 2 * face * s + d * state * s + face * s,
+                "flops": N * d * nf * 2 * n + N * d * nf * 6 + NF * nfp * nf * 3
+                + NF * nfp * (d * nf * 2 * n + visc)}
+    m["face"] = {"bytes": face * s * (2 + (1 if viscous else 0)),
+                 "flops": NF * nfp / 2 * (llf + (3 * nf if viscous else 0))}
+    stage_io = (2 + stage_i) * state * s + face * s
+    m["elem_stage"] = {"bytes": state * s + (d * state * s if viscous else 0) + face * s + stage_io,
+                       "flops": N * (conv + (visc + d * nf if viscous else 0) + d * nf * (2 * n + 6) + nf * 2 * (stage_i + 1))
+                       + face * 2 * n}
+    m["elem"] = {"bytes": state * s + (d * state * s if viscous else 0) + face * s + state * s,
+                 "flops": N * (conv + (visc + d * nf if viscous else 0) + d * nf * (2 * n + 6))}
+    # adjoint kernels (about 2-3x the forward pointwise work, same data movement pattern)
+    m["vjp_elem"] = {"bytes": 3 * state * s + (d * state * s if viscous else 0) + face * s,
+                     "flops": 2.5 * m["elem"]["flops"]}
+    m["vjp_face"] = {"bytes": 4 * face * s, "flops": 2.5 * m["face"]["flops"]}
+    m["vjp_br1"] = {"bytes": (3 + d) * state * s + 4 * face * s, "flops": 2.5 * m["br1"]["flops"]}
+    m["vjp_gather"] = {"bytes": 2 * state * s + 2 * face * s, "flops": face * 2 * n}
+    return m
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms (read only)."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, name in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_solver(prec):
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh, phys, U0 = I.channel2d_workload()
+    s = Solver(mesh, phys, prec)
+    A, b, c = ars343_explicit()
+    s.set_tableau(A, b, c)
+    return s, mesh, phys, U0
+
+
+def time_gpu(prec, steps, warmup, dt=1e-9):
+    import torch
+    s, mesh, phys, U0 = make_solver(prec)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    U = torch.as_tensor(U0, device=dev).contiguous()
+    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape), device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
+    stream = torch.cuda.current_stream()
+    has_vjp = s.supports_adjoint()
+
+    def step():
+        s.ark_step(U, dt)
+        if has_vjp:
+            s.ark_adjoint_step(U, lam, dt)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    s.check()
+    s.profile(True)
+    s.profile_reset()
+    times = []
+    with ClockSampler(dev.index or 0) as clocks:
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    prof = s.profile_read()
+    s.profile(False)
+    s.check()
+    # end-to-end through the public API with pinned host buffers
+    host_in = torch.as_tensor(U0).pin_memory()
+    host_lam = lam.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    host_lam_out = torch.empty_like(host_lam).pin_memory()
+    e2e = []
+    for k in range(max(3, steps // 2) + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U.copy_(host_in, non_blocking=True)
+        if has_vjp:
+            lam.copy_(host_lam, non_blocking=True)
+        step()
+        host_out.copy_(U, non_blocking=True)
+        if has_vjp:
+            host_lam_out.copy_(lam, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            e2e.append(e0.elapsed_time(e1))
+    s.check()
+    nbytes_state = U.numel() * 8
+    h2d = nbytes_state * (2 if has_vjp else 1)
+    d2h = nbytes_state * (2 if has_vjp else 1)
+    dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
+    evals_per_step = 4 * (2 if has_vjp else 1)
+    ms = float(np.mean(times))
+    return {"ms": ms, "ms_all": times, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
+            "evals_per_step": evals_per_step, "e2e_ms": float(np.mean(e2e)), "h2d": h2d, "d2h": d2h,
+            "mesh": mesh, "phys": phys, "has_vjp": has_vjp}
+
+
+def roofline(res, prec, pk):
+    mesh = res["mesh"]
+    model = kernel_model(mesh.dim, mesh.p, True, prec)
+    E = mesh.n_elem
+    best = None
+    for name, (launches, ms) in res["prof"].items():
+        if best is None or ms > best[2]:
+            best = (name, launches, ms)
+    name, launches, ms = best
+    per_launch_s = ms / launches / 1e3
+    mdl = model[name]
+    bytes_l = mdl["bytes"] * E
+    flops_l = mdl["flops"] * E
+    t_mem = bytes_l / (pk["hbm_gbs"] * 1e9)
+    t_alu = flops_l / (alu_peak_tflops(prec) * 1e12)
+    shares = {k: round(v[1] / sum(x[1] for x in res["prof"].values()), 4) for k, v in res["prof"].items()}
+    if t_mem >= t_alu:
+        ach = bytes_l / per_launch_s / 1e9
+        out = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": pk["source"]}
+    else:
+        ach = flops_l / per_launch_s / 1e12
+        peak = alu_peak_tflops(prec)
+        out = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+               "frac": round(ach / peak, 4), "peak_source": "derived (unit counts x 2032 MHz)" if prec == "fp32"
+               else "nominal B300 FP64"}
+    out.update({"kernel": name, "launches": launches, "avg_launch_us": round(per_launch_s * 1e6, 2),
+                "algorithmic_bytes": int(bytes_l), "algorithmic_flops": int(flops_l),
+                "traffic": None, "kernel_shares": shares})
+    return out
+
+
+def cpu_baseline(steps_hint=1):
+    """The FP64 oracle as it stands, on this host's cores: one residual of the
+    full workload (bounded sample), scaled to DOF-evals/s."""
+    import torch
+    from oracle.physics import Gas
+    from oracle.residual import DGOperator
+    from oracle.vjp import vjp
+    from paper_2607_16044_b300 import inputs as I
+    mesh, phys, U0 = I.channel2d_workload()
+    op = DGOperator(mesh, Gas(phys.gamma, Re=phys.Re, Pr=phys.Pr, viscous=phys.viscous))
+    U = torch.as_tensor(U0)
+    t0 = time.perf_counter()
+    op.residual(U)
+    t1 = time.perf_counter()
+    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape))
+    vjp(op, U, lam)
+    t2 = time.perf_counter()
+    dofs = U.numel()
+    return {"value": round(2 * dofs / (t2 - t0), 1), "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"one residual ({t1 - t0:.1f} s) + one VJP ({t2 - t1:.1f} s) of the full 256x128 p=4 "
+                      f"channel, FP64 torch CPU oracle"}
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle timed on the host cores, each step a
+    bounded sample of the workload (a fixed 1/32 element subset: 4 residuals
+    + 4 VJPs of the subset, as in one ARK step and its adjoint)."""
+    import torch
+    from oracle.physics import Gas
+    from oracle.residual import DGOperator
+    from oracle.vjp import vjp_rows
+    from paper_2607_16044_b300 import inputs as I
+    mesh, phys, U0 = I.channel2d_workload()
+    op = DGOperator(mesh, Gas(phys.gamma, Re=phys.Re, Pr=phys.Pr, viscous=phys.viscous))
+    U = torch.as_tensor(U0)
+    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape))
+    elems = np.arange(0, mesh.n_elem, 32)
+    per_elem_dofs = (mesh.dim + 2) * mesh.N
+
+    def step():
+        for _ in range(4):
+            op.residual(U, elems)
+        for _ in range(4):
+            vjp_rows(op, U, lam, elems)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 8 * len(elems) * per_elem_dofs / dt
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
+            "config": {"workload": WORKLOAD, "sample": f"{len(elems)} of {mesh.n_elem} elements per step"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"4 residuals + 4 VJPs on {len(elems)} elements (every 32nd) per step"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            reference_arm(args)
+        return
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    args.warmup = max(args.warmup, 3)
+    pk = peaks()
+    if world > 1:
+        torch.distributed.barrier()
+    r32 = time_gpu("fp32", args.steps, args.warmup)
+    r64 = time_gpu("fp64", max(3, args.steps // 4), 3)
+    ms = r32["ms"]
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    evals = r32["dofs"] * r32["evals_per_step"]
+    value = evals * world / (ms / 1e3)
+    e2e_value = evals / (r32["e2e_ms"] / 1e3) * world
+    roof = roofline(r32, "fp32", pk)
+    roof64 = roofline(r64, "fp64", pk)
+    launches = sum(v[0] for v in r32["prof"].values()) // max(1, args.steps)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
+            "config": {"workload": WORKLOAD, "elements": r32["mesh"].n_elem, "dofs": r32["dofs"],
+                       "step": ("1 ARS(3,4,3) step + its adjoint" if r32["has_vjp"] else "1 ARS(3,4,3) step"),
+                       "dof_evals_per_step": evals, "l2": "flushed (256 MB write) between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "gpu_launches": int(launches),
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": r32["h2d"],
+                    "d2h_bytes_per_step": r32["d2h"]},
+            "clocks": r32["clocks"],
+            "fp64": {"value": round(r64["dofs"] * r64["evals_per_step"] / (r64["ms"] / 1e3), 1), "unit": UNIT,
+                     "ms_per_step": round(r64["ms"], 4), "roofline": roof64, "clocks": r64["clocks"]}}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -140,6 +140,32 @@ dgx_status dgx_check(dgx_handle* h);
 
 const char* dgx_status_string(dgx_status s);
 
+/* Kernel kinds reported by the profiler. */
+typedef enum {
+  DGX_K_TRACE = 0,       /* face traces of a state                              */
+  DGX_K_BR1 = 1,         /* BR1 lifted gradient + own-face viscous fluxes       */
+  DGX_K_FACE = 2,        /* numerical flux at every unique face point           */
+  DGX_K_ELEM = 3,        /* volume + lift + inverse mass                        */
+  DGX_K_ELEM_STAGE = 4,  /* the same fused with the ARK stage update and traces */
+  DGX_K_VJP_ELEM = 5,    /* adjoint of the element kernel                       */
+  DGX_K_VJP_FACE = 6,    /* adjoint of the face fluxes                          */
+  DGX_K_VJP_BR1 = 7,     /* adjoint of the BR1 gradient and viscous face fluxes */
+  DGX_K_VJP_GATHER = 8,  /* adjoint of the traces (gather into the element)     */
+  DGX_KERNEL_KINDS = 9
+} dgx_kernel_kind;
+
+/* Per-kernel device timing (tracing).  While enabled, every kernel the
+ * library enqueues is bracketed by two CUDA events on its stream (enabling
+ * creates a pool of 8192 events; launches beyond 4096 between two reads are
+ * not recorded).  Not meant for use inside a stream capture.
+ * dgx_profile_read synchronises on the recorded events and returns, for one
+ * kernel kind, the launch count and summed device milliseconds accumulated
+ * since the last reset. */
+dgx_status dgx_profile_enable(dgx_handle* h, int32_t enable);
+dgx_status dgx_profile_read(dgx_handle* h, int32_t kind, int64_t* launches, double* ms);
+dgx_status dgx_profile_reset(dgx_handle* h);
+const char* dgx_kernel_name(int32_t kind);
+
 /* Sizes the binding needs: element count, nodes per element, fields, face
  * points per face, the chosen element-tile size. */
 dgx_status dgx_query(const dgx_handle* h, int32_t* n_elem, int32_t* nodes, int32_t* fields,

@@ -20,24 +20,37 @@ DEGREES = (1, 2, 3, 4, 5)
 
 UNIT = """// generated by build.py: instantiation of the (D={D}, S={S}, P={P}) launch table
 #include "dispatch.h"
+{VJP_INCLUDE}
 namespace dgx {{
 namespace {{
 using Sc = {S};
+using O = Ops<{D}, {P}, Sc>;
+inline const Mesh<Sc>& m(const void* M) {{ return *(const Mesh<Sc>*)M; }}
 struct R {{
-  static cudaError_t rhs(const void* M, bool v, bool c, const void* U, void* out, const Work& w, cudaStream_t st) {{
-    return Ops<{D}, {P}, Sc>::rhs(*(const Mesh<Sc>*)M, v, c, (const Sc*)U, (Sc*)out, w, st);
+  static cudaError_t trace(const void* M, const void* U, void* TU, cudaStream_t st) {{
+    return O::template trace<Sc>(m(M), (const Sc*)U, (Sc*)TU, nullptr, st);
   }}
   static cudaError_t tr64(const void* M, const double* U, void* TU, void* sh, cudaStream_t st) {{
-    return Ops<{D}, {P}, Sc>::template trace<double>(*(const Mesh<Sc>*)M, U, (Sc*)TU, (Sc*)sh, st);
+    return O::template trace<double>(m(M), U, (Sc*)TU, (Sc*)sh, st);
   }}
-  static cudaError_t stage(const void* M, bool v, bool c, const void* U, const Work& w, const void* sa, cudaStream_t st) {{
-    return Ops<{D}, {P}, Sc>::stage(*(const Mesh<Sc>*)M, v, c, (const Sc*)U, w, *(const Stage<Sc>*)sa, st);
+  static cudaError_t br1(const void* M, bool c, const void* U, const Work& w, cudaStream_t st) {{
+    return O::br1(m(M), c, (const Sc*)U, w, st);
   }}
-{VJP_FN}
+  static cudaError_t face(const void* M, bool v, bool c, const Work& w, cudaStream_t st) {{
+    return O::face(m(M), v, c, w, st);
+  }}
+  static cudaError_t elem(const void* M, bool v, bool c, const void* U, const Work& w, void* out, cudaStream_t st) {{
+    Stage<Sc> none{{}};
+    return O::template elem<0>(m(M), v, c, (const Sc*)U, w, (Sc*)out, none, st);
+  }}
+  static cudaError_t elem_stage(const void* M, bool v, bool c, const void* U, const Work& w, const void* sa,
+                                cudaStream_t st) {{
+    return O::template elem<1>(m(M), v, c, (const Sc*)U, w, nullptr, *(const Stage<Sc>*)sa, st);
+  }}
 }};
 }}  // namespace
 const Table* table_d{D}_{T}_p{P}() {{
-  static const Table t = {{&R::rhs, &R::tr64, &R::stage, {VJP_PTR}}};
+  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, {VJP_PTR}}};
   return &t;
 }}
 }}  // namespace dgx
@@ -68,15 +81,9 @@ def _write_sources():
                 name = f"table_d{D}_{T}_p{P}"
                 decls.append(f"const Table* {name}();")
                 cases.append(f"    case {P}: return {name}();")
-                vjp_fn = ""
-                vjp_ptr = "nullptr"
-                if vjp:
-                    vjp_fn = ("  static cudaError_t vjp(const void* M, bool v, bool c, const void* U, const void* lam,"
-                              " void* g, const void* vw, cudaStream_t st) {\n"
-                              f"    return Ops<{D}, {P}, Sc>::vjp(*(const Mesh<Sc>*)M, v, c, (const Sc*)U,"
-                              " (const Sc*)lam, (Sc*)g, *(const VjpWork*)vw, st);\n  }")
-                    vjp_ptr = "&R::vjp"
-                src = UNIT.format(D=D, S=S, P=P, T=T, VJP_FN=vjp_fn, VJP_PTR=vjp_ptr)
+                vjp_inc = '#include "vjp.cuh"' if vjp else ""
+                vjp_ptr = f"vjp_table<{D}, {P}, {S}>()" if vjp else "nullptr"
+                src = UNIT.format(D=D, S=S, P=P, T=T, VJP_INCLUDE=vjp_inc, VJP_PTR=vjp_ptr)
                 path = os.path.join(BUILD, f"unit_d{D}_{T}_p{P}.cu")
                 _write_if_changed(path, src)
                 units.append(path)

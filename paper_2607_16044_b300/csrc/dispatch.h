@@ -10,12 +10,15 @@
 namespace dgx {
 
 struct Table {
-  cudaError_t (*rhs)(const void* M, bool visc, bool curv, const void* U, void* out, const Work& w, cudaStream_t st);
+  // Individual kernel launches (the host composes residuals, stages and adjoints).
+  cudaError_t (*trace)(const void* M, const void* U, void* TU, cudaStream_t st);
   cudaError_t (*trace_from64)(const void* M, const double* U, void* TU, void* shadow, cudaStream_t st);
-  cudaError_t (*stage)(const void* M, bool visc, bool curv, const void* U, const Work& w, const void* stage,
-                       cudaStream_t st);
-  cudaError_t (*vjp)(const void* M, bool visc, bool curv, const void* U, const void* lam, void* g, const void* vw,
-                     cudaStream_t st);  // nullptr until the adjoint kernels are compiled in
+  cudaError_t (*br1)(const void* M, bool curv, const void* U, const Work& w, cudaStream_t st);
+  cudaError_t (*face)(const void* M, bool visc, bool curv, const Work& w, cudaStream_t st);
+  cudaError_t (*elem)(const void* M, bool visc, bool curv, const void* U, const Work& w, void* out, cudaStream_t st);
+  cudaError_t (*elem_stage)(const void* M, bool visc, bool curv, const void* U, const Work& w, const void* stage,
+                            cudaStream_t st);
+  const void* vjp;  // adjoint launch table (VjpTable) or nullptr
 };
 
 // Defined in the generated units: table for (D, P, S) or nullptr.

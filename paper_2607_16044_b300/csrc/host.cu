@@ -37,6 +37,15 @@ struct dgx_handle {
   void* d_iJ = nullptr;
   void* d_SnE = nullptr;
   void* d_SnF = nullptr;
+  dgx::Mesh<double> mesh64{};   // device views passed to the launch table
+  dgx::Mesh<float> mesh32{};
+  // per-kernel event profiler (tracing)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<int> ev_kind;
+  int64_t prof_launches[DGX_KERNEL_KINDS] = {};
+  double prof_ms[DGX_KERNEL_KINDS] = {};
   // tableau
   int stages = 0;
   double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
@@ -248,6 +257,32 @@ dgx::Mesh<S> mesh_view(const dgx_handle* h) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Enqueue one kernel; with profiling on, bracket it by two events on its stream.
+template <typename F>
+cudaError_t launch(dgx_handle* h, int kind, cudaStream_t st, F&& f) {
+  if (!h->prof || h->ev_used + 2 > h->ev_pool.size()) return f();
+  cudaEvent_t a = h->ev_pool[h->ev_used], b = h->ev_pool[h->ev_used + 1];
+  cudaEventRecord(a, st);
+  const cudaError_t err = f();
+  cudaEventRecord(b, st);
+  h->ev_used += 2;
+  h->ev_kind.push_back(kind);
+  return err;
+}
+
+void profile_collect(dgx_handle* h) {
+  for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+    float ms = 0.f;
+    cudaEventSynchronize(h->ev_pool[2 * i + 1]);
+    if (cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]) == cudaSuccess) {
+      h->prof_ms[h->ev_kind[i]] += ms;
+      h->prof_launches[h->ev_kind[i]] += 1;
+    }
+  }
+  h->ev_kind.clear();
+  h->ev_used = 0;
+}
+
 struct Layout {
   size_t TU, FF, G, Q, Y, K, SH, total;
 };
@@ -301,8 +336,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cuda
   S* Y = (S*)(base + L.Y);
   const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
   S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
-  const dgx::Mesh<S> M = mesh_view<S>(h);
-  cudaError_t err = h->tab->trace_from64(&M, U64, w.TU, shadow, st);
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  const dgx::Table* t = h->tab;
+  cudaError_t err =
+      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w.TU, shadow, st); });
   if (err != cudaSuccess) return DGX_ECUDA;
   const S* y0 = h->fp64 ? (const S*)U64 : shadow;
   const int s = h->stages;
@@ -321,7 +358,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cuda
     sa.shadow = shadow;
     sa.TU = (S*)w.TU;
     const S* Uin = (i == 0) ? y0 : Y;
-    err = h->tab->stage(&M, h->viscous, h->curv, Uin, w, &sa, st);
+    if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, Uin, w, st); });
+    if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
+    if (err == cudaSuccess)
+      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->viscous, h->curv, Uin, w, &sa, st); });
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -330,6 +370,42 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cuda
 }  // namespace
 
 extern "C" {
+
+const char* dgx_kernel_name(int32_t kind) {
+  static const char* names[DGX_KERNEL_KINDS] = {"trace", "br1", "face", "elem", "elem_stage",
+                                                "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"};
+  return (kind >= 0 && kind < DGX_KERNEL_KINDS) ? names[kind] : "unknown";
+}
+
+dgx_status dgx_profile_enable(dgx_handle* h, int32_t enable) {
+  if (!h) return DGX_EINVAL;
+  if (enable && h->ev_pool.empty()) {
+    h->ev_pool.resize(8192);
+    for (auto& e : h->ev_pool)
+      if (cudaEventCreate(&e) != cudaSuccess) return DGX_ECUDA;
+  }
+  if (!enable && h->prof) profile_collect(h);
+  h->prof = enable != 0;
+  return DGX_OK;
+}
+
+dgx_status dgx_profile_read(dgx_handle* h, int32_t kind, int64_t* launches, double* ms) {
+  if (!h || kind < 0 || kind >= DGX_KERNEL_KINDS) return DGX_EINVAL;
+  profile_collect(h);
+  if (launches) *launches = h->prof_launches[kind];
+  if (ms) *ms = h->prof_ms[kind];
+  return DGX_OK;
+}
+
+dgx_status dgx_profile_reset(dgx_handle* h) {
+  if (!h) return DGX_EINVAL;
+  profile_collect(h);
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+    h->prof_launches[k] = 0;
+    h->prof_ms[k] = 0.0;
+  }
+  return DGX_OK;
+}
 
 const char* dgx_status_string(dgx_status s) {
   switch (s) {
@@ -397,6 +473,7 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
 
 dgx_status dgx_destroy(dgx_handle* h) {
   if (!h) return DGX_EINVAL;
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_mesh(h);
   if (h->d_tabs) cudaFree(h->d_tabs);
   if (h->d_flags) cudaFree(h->d_flags);
@@ -431,6 +508,8 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   if ((st = upload_real(h, rh, &h->d_rh)) != DGX_OK) return st;
   h->curv = false;
   h->has_mesh = true;
+  h->mesh64 = mesh_view<double>(h);
+  h->mesh32 = mesh_view<float>(h);
   return DGX_OK;
 }
 
@@ -525,6 +604,8 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
   if ((st = upload_real(h, SnF, &h->d_SnF)) != DGX_OK) return st;
   h->curv = true;
   h->has_mesh = true;
+  h->mesh64 = mesh_view<double>(h);
+  h->mesh32 = mesh_view<float>(h);
   return DGX_OK;
 }
 
@@ -546,6 +627,7 @@ size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (!h) return 0;
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
   if (op < DGX_OP_RHS || op > DGX_OP_ARK) return 0;
+  if (op == DGX_OP_VJP && !h->tab->vjp) return 0;
   return layout(h, op).total;
 }
 
@@ -556,12 +638,15 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
   const Layout L = layout(h, DGX_OP_RHS);
   const dgx::Work w = work_at(h, workspace, L);
   cudaStream_t st = (cudaStream_t)stream;
-  if (h->fp64) {
-    const dgx::Mesh<double> M = mesh_view<double>(h);
-    return cuda_status(h->tab->rhs(&M, h->viscous, h->curv, U, dUdt, w, st));
-  }
-  const dgx::Mesh<float> M = mesh_view<float>(h);
-  return cuda_status(h->tab->rhs(&M, h->viscous, h->curv, U, dUdt, w, st));
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  const dgx::Table* t = h->tab;
+  cudaError_t err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
+  if (err == cudaSuccess && h->viscous)
+    err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+  if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_ELEM, st, [&] { return t->elem(M, h->viscous, h->curv, U, w, dUdt, st); });
+  return cuda_status(err);
 }
 
 dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace, void* stream) {

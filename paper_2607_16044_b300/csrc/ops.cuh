@@ -1,7 +1,8 @@
 // Launch layer: one Ops<D, P, S> per (dimension, degree, precision), explicitly
 // instantiated in generated translation units so the templates compile in
-// parallel.  Each entry enqueues kernels on a stream and returns the launch
-// status; nothing here allocates or synchronises.
+// parallel.  Each entry enqueues one kernel on a stream and returns the launch
+// status; nothing here allocates or synchronises.  The host runtime composes
+// residuals, ARK stages and adjoints from these launches.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -90,26 +91,6 @@ struct Ops {
     return cudaGetLastError();
   }
 
-  // f = dU/dt
-  static cudaError_t rhs(const Mesh<S>& M, bool visc, bool curv, const S* U, S* out, const Work& w,
-                         cudaStream_t st) {
-    cudaError_t err = trace<S>(M, U, (S*)w.TU, nullptr, st);
-    if (err != cudaSuccess) return err;
-    if (visc && (err = br1(M, curv, U, w, st)) != cudaSuccess) return err;
-    if ((err = face(M, visc, curv, w, st)) != cudaSuccess) return err;
-    Stage<S> none{};
-    return elem<0>(M, visc, curv, U, w, out, none, st);
-  }
-
-  // One ERK stage with the fused update; TU must hold the traces of U on entry
-  // and holds the traces of the next stage state on exit.
-  static cudaError_t stage(const Mesh<S>& M, bool visc, bool curv, const S* U, const Work& w, const Stage<S>& sa,
-                           cudaStream_t st) {
-    cudaError_t err = cudaSuccess;
-    if (visc && (err = br1(M, curv, U, w, st)) != cudaSuccess) return err;
-    if ((err = face(M, visc, curv, w, st)) != cudaSuccess) return err;
-    return elem<1>(M, visc, curv, U, w, nullptr, sa, st);
-  }
 };
 
 }  // namespace dgx

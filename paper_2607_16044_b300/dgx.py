@@ -40,7 +40,9 @@ _lib = None
 
 EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_nodes", "dgx_set_tableau",
            "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
-           "dgx_status_string", "dgx_query"]
+           "dgx_status_string", "dgx_query", "dgx_profile_enable", "dgx_profile_read", "dgx_profile_reset",
+           "dgx_kernel_name"]
+KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -66,10 +68,16 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_status_string.argtypes = [i32]
     lib.dgx_status_string.restype = ctypes.c_char_p
     lib.dgx_query.argtypes = [vp] + [ctypes.POINTER(i32)] * 5
+    lib.dgx_profile_enable.argtypes = [vp, i32]
+    lib.dgx_profile_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(dbl)]
+    lib.dgx_profile_reset.argtypes = [vp]
+    lib.dgx_kernel_name.argtypes = [i32]
+    lib.dgx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
     lib.dgx_status_string.restype = ctypes.c_char_p
+    lib.dgx_kernel_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -194,3 +202,23 @@ class Solver:
 
     def check(self):
         _check(self.lib.dgx_check(self.h), "dgx_check")
+
+    def supports_adjoint(self) -> bool:
+        return int(self.lib.dgx_workspace_bytes(self.h, OP_VJP)) > 0
+
+    # ------------------------------------------------------------------ tracing
+    def profile(self, enable: bool = True):
+        _check(self.lib.dgx_profile_enable(self.h, int(enable)), "dgx_profile_enable")
+
+    def profile_reset(self):
+        _check(self.lib.dgx_profile_reset(self.h), "dgx_profile_reset")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (launches, total device ms)} since the last reset."""
+        out = {}
+        for k, name in enumerate(KERNELS):
+            n, ms = ctypes.c_int64(), ctypes.c_double()
+            _check(self.lib.dgx_profile_read(self.h, k, ctypes.byref(n), ctypes.byref(ms)), "dgx_profile_read")
+            if n.value:
+                out[name] = (n.value, ms.value)
+        return out

@@ -106,3 +106,11 @@ def test_adjoint_recurrence_matches_autograd():
     out = ark.erk_step(op.residual, Ut, dt, A, b)
     (ref,) = torch.autograd.grad(out, Ut, lam)
     assert torch.allclose(lam_n, ref, rtol=1e-12, atol=1e-12 * ref.abs().max())
+
+
+def test_package_tableau_matches_oracle_tableau():
+    """The product's copy of the published coefficients equals the oracle's."""
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    A, b, c = ars343_explicit()
+    A2, b2, c2 = ark.ars343()
+    assert np.array_equal(A, A2) and np.array_equal(b, b2) and np.array_equal(c, c2)
