@@ -134,6 +134,22 @@ dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* g
  * (FP32 handles evaluate f in FP32 on a rounded copy of the stage state). */
 dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, void* stream);
 
+/* The same step, also storing the stage states y_1..y_s it evaluates (stage
+ * checkpointing for the adjoint): stages is a device buffer of s consecutive
+ * states [s][E][nf][N] in the handle's precision (y_1 = U_n, rounded to FP32
+ * on FP32 handles). */
+dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, void* stream);
+
+/* Discrete adjoint of one explicit ARK step (reverse of the Sec. 4.2 stage
+ * recurrence): with cotangent lam on U_{n+1},
+ *   mu_i = dt (b_i lam + sum_{j>i} a_ji nu_j),  nu_i = (df/dU)(y_i)^T mu_i,
+ *   lam_n = lam + sum_i nu_i,   i = s .. 1.
+ * stages = the y_i of the step (from dgx_ark_step_stages); lam64 (device,
+ * double [E][nf][N]) holds lambda_{n+1} on entry and lambda_n on exit; the
+ * accumulation into lam64 is in FP64. */
+dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                                void* stream);
+
 /* Synchronise with the device and report (then clear) device-side flags:
  * DGX_ENONFINITE if any residual value was NaN/Inf since the last check. */
 dgx_status dgx_check(dgx_handle* h);

@@ -14,6 +14,7 @@
 
 #include "../../include/dgx.h"
 #include "dispatch.h"
+#include "vjp.cuh"
 
 using dgx::Tab;
 
@@ -284,7 +285,7 @@ void profile_collect(dgx_handle* h) {
 }
 
 struct Layout {
-  size_t TU, FF, G, Q, Y, K, SH, total;
+  size_t TU, FF, G, Q, Y, K, SH, TUb, Gb, JB, Qb, NU, total;
 };
 
 Layout layout(const dgx_handle* h, int op) {
@@ -301,6 +302,22 @@ Layout layout(const dgx_handle* h, int op) {
     off += align256(face);
     L.Q = off;
     off += align256(state * h->d);
+  }
+  if (op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT) {
+    L.TUb = off;
+    off += align256(face);
+    if (h->viscous) {
+      L.Gb = off;
+      off += align256(face);
+      L.JB = off;
+      off += align256(face);
+      L.Qb = off;
+      off += align256(state * h->d);
+    }
+  }
+  if (op == DGX_OP_ARK_ADJOINT) {
+    L.NU = off;
+    off += align256(state) * (h->stages > 0 ? h->stages : 1);
   }
   if (op == DGX_OP_ARK) {
     L.Y = off;
@@ -326,22 +343,62 @@ dgx::Work work_at(const dgx_handle* h, void* ws, const Layout& L) {
   return w;
 }
 
+dgx::VjpWork vjp_work_at(const dgx_handle* h, void* ws, const Layout& L) {
+  char* b = (char*)ws;
+  dgx::VjpWork w{};
+  w.TU = b + L.TU;
+  w.FFb = b + L.FF;
+  w.G = h->viscous ? b + L.G : nullptr;
+  w.Q = h->viscous ? b + L.Q : nullptr;
+  w.TUb = b + L.TUb;
+  w.Gb = h->viscous ? b + L.Gb : nullptr;
+  w.JB = h->viscous ? b + L.JB : nullptr;
+  w.Qb = h->viscous ? b + L.Qb : nullptr;
+  return w;
+}
+
 dgx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DGX_OK : DGX_ECUDA; }
 
+// Forward recompute (traces, BR1) then the four adjoint kernels.  g receives
+// nu = (df/dU)(U)^T mu with mu described by cot (see dgx::Cot).
 template <typename S>
-dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cudaStream_t st) {
+cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, const dgx::Cot<S>& fin, void* g,
+                      const dgx::VjpWork& vw, cudaStream_t st) {
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  const dgx::Table* t = h->tab;
+  const dgx::VjpTable* v = (const dgx::VjpTable*)t->vjp;
+  dgx::Work w{vw.TU, vw.FFb, vw.G, vw.Q};
+  cudaError_t err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
+  if (err == cudaSuccess && h->viscous)
+    err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_VJP_ELEM, st, [&] { return v->elem(M, h->viscous, h->curv, U, vw, &cot, g, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_VJP_FACE, st, [&] { return v->face(M, h->viscous, h->curv, vw, st); });
+  if (err == cudaSuccess && h->viscous)
+    err = launch(h, DGX_K_VJP_BR1, st, [&] { return v->br1(M, h->curv, vw, g, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_VJP_GATHER, st, [&] { return v->gather(M, h->viscous, vw, g, &fin, st); });
+  return err;
+}
+
+template <typename S>
+dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st) {
   const Layout L = layout(h, DGX_OP_ARK);
   const dgx::Work w = work_at(h, workspace, L);
   char* base = (char*)workspace;
   S* Y = (S*)(base + L.Y);
   const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
   S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
+  const size_t state_b = (size_t)h->E * h->nf * h->N * h->s;
+  S* ys = (S*)stages;  // optional stage checkpoints y_1..y_s
+  S* first = ys ? ys : shadow;  // where the rounded (or copied) U_n goes
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   cudaError_t err =
-      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w.TU, shadow, st); });
+      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w.TU, first, st); });
   if (err != cudaSuccess) return DGX_ECUDA;
-  const S* y0 = h->fp64 ? (const S*)U64 : shadow;
+  const S* y0 = (h->fp64 && !ys) ? (const S*)U64 : first;
   const int s = h->stages;
   for (int i = 0; i < s; ++i) {
     dgx::Stage<S> sa{};
@@ -353,15 +410,48 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* workspace, cuda
     for (int j = 0; j < s; ++j) sa.cb[j] = dt * h->b[j];
     sa.base = y0;
     sa.Un = U64;
-    sa.Y = Y;
+    sa.Y = (ys && !sa.last) ? ys + (state_b / sizeof(S)) * (i + 1) : Y;
     sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
-    sa.shadow = shadow;
+    sa.shadow = shadow;  // FP32: rounded U_{n+1} (unused by the next step, which re-rounds U64)
     sa.TU = (S*)w.TU;
-    const S* Uin = (i == 0) ? y0 : Y;
+    const S* Uin = (i == 0) ? y0 : (ys ? ys + (state_b / sizeof(S)) * i : Y);
     if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, Uin, w, st); });
     if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
     if (err == cudaSuccess)
       err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->viscous, h->curv, Uin, w, &sa, st); });
+    if (err != cudaSuccess) return DGX_ECUDA;
+  }
+  return DGX_OK;
+}
+
+template <typename S>
+dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                            cudaStream_t st) {
+  const Layout L = layout(h, DGX_OP_ARK_ADJOINT);
+  const dgx::VjpWork vw = vjp_work_at(h, workspace, L);
+  const size_t state_b = (size_t)h->E * h->nf * h->N * h->s;
+  const size_t state_a = align256(state_b);
+  char* base = (char*)workspace;
+  auto NU = [&](int j) { return (S*)(base + L.NU + state_a * j); };
+  const int s = h->stages;
+  for (int i = s - 1; i >= 0; --i) {
+    const void* y = (const char*)stages + state_b * i;
+    dgx::Cot<S> cot{}, fin{};
+    cot.lam64 = lam64;
+    cot.c_lam = dt * h->b[i];
+    for (int j = i + 1; j < s; ++j) {
+      const double a = h->A[j * dgx::MAXSTAGES + i];
+      if (a != 0.0) {
+        cot.nu[cot.n_nu] = NU(j);
+        cot.c_nu[cot.n_nu] = dt * a;
+        ++cot.n_nu;
+      }
+    }
+    if (i == 0) {
+      fin.lam64_out = lam64;
+      for (int j = 1; j < s; ++j) fin.nu_all[fin.n_all++] = NU(j);
+    }
+    const cudaError_t err = vjp_chain<S>(h, y, cot, fin, NU(i), vw, st);
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -626,8 +716,9 @@ dgx_status dgx_set_tableau(dgx_handle* h, int32_t stages, const double* A, const
 size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (!h) return 0;
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
-  if (op < DGX_OP_RHS || op > DGX_OP_ARK) return 0;
-  if (op == DGX_OP_VJP && !h->tab->vjp) return 0;
+  if (op == DGX_OP_ARK_ADJOINT && h->stages == 0) return 0;
+  if (op < DGX_OP_RHS || op > DGX_OP_ARK_ADJOINT) return 0;
+  if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT) && !h->tab->vjp) return 0;
   return layout(h, op).total;
 }
 
@@ -650,18 +741,49 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
 }
 
 dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace, void* stream) {
-  if (!h || !U || !lambda || !gU || !workspace) return DGX_EINVAL;
+  if (!h || !U || !lambda || !gU || !workspace || gU == U || gU == lambda) return DGX_EINVAL;
   if (!h->has_mesh) return DGX_ESTATE;
-  (void)stream;
-  return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  const Layout L = layout(h, DGX_OP_VJP);
+  const dgx::VjpWork vw = vjp_work_at(h, workspace, L);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->fp64) {
+    dgx::Cot<double> cot{}, fin{};
+    cot.lam = (const double*)lambda;
+    cot.c_lam = 1.0;
+    return cuda_status(vjp_chain<double>(h, U, cot, fin, gU, vw, st));
+  }
+  dgx::Cot<float> cot{}, fin{};
+  cot.lam = (const float*)lambda;
+  cot.c_lam = 1.0;
+  return cuda_status(vjp_chain<float>(h, U, cot, fin, gU, vw, st));
 }
 
 dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, void* stream) {
   if (!h || !U64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
-  if (h->fp64) return ark_impl<double>(h, U64, dt, workspace, (cudaStream_t)stream);
-  return ark_impl<float>(h, U64, dt, workspace, (cudaStream_t)stream);
+  if (h->fp64) return ark_impl<double>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
+  return ark_impl<float>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, void* stream) {
+  if (!h || !U64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->fp64) return ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
+  return ark_impl<float>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                                void* stream) {
+  if (!h || !stages || !lam64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->fp64) return ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
+  return ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
 }
 
 dgx_status dgx_check(dgx_handle* h) {

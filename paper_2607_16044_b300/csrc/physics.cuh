@@ -193,3 +193,315 @@ __device__ __forceinline__ void llf_flux(const S (&UL)[D + 2], const S (&UR)[D +
 }
 
 }  // namespace dgx
+
+// ===========================================================================
+// Reverse-mode (vector-Jacobian) counterparts, derived by hand from the
+// forward formulas above.  Each *_vjp adds (d out / d in)^T * out_bar into the
+// input cotangents (callers zero them first).  Conventions: d|x|/dx = sign(x)
+// with sign(0) = 0; at a tie of the LLF wave speeds the interior side (L) is
+// differentiated.
+// ===========================================================================
+namespace dgx {
+
+template <typename S>
+__device__ __forceinline__ S sgn(S x) { return x > S(0) ? S(1) : (x < S(0) ? S(-1) : S(0)); }
+
+// Convective fluxes in all directions: Ub += (dF/dU)^T Fb.
+template <int D, typename S>
+__device__ __forceinline__ void conv_flux_all_vjp(const S (&U)[D + 2], const S (&Fb)[D][D + 2], const Gas<S>& g,
+                                                  S (&Ub)[D + 2]) {
+  const S ir = S(1) / U[0];
+  S u[D], mm = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = U[1 + i] * ir;
+    mm += U[1 + i] * u[i];
+  }
+  const S p = g.gm1 * (U[D + 1] - S(0.5) * mm);
+  const S h = U[D + 1] + p;
+  S mb[D], ub[D], pb = 0, hb = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    mb[i] = Fb[i][0];
+    ub[i] = S(0);
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      mb[j] += Fb[i][1 + j] * u[i];
+      ub[i] += Fb[i][1 + j] * U[1 + j];
+    }
+    pb += Fb[i][1 + i];
+    hb += Fb[i][D + 1] * u[i];
+    ub[i] += Fb[i][D + 1] * h;
+  }
+  S Eb = hb;
+  pb += hb;
+  Eb += g.gm1 * pb;
+  const S mmb = -S(0.5) * g.gm1 * pb;
+  S irb = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    mb[i] += mmb * u[i];
+    ub[i] += mmb * U[1 + i];
+    mb[i] += ub[i] * ir;
+    irb += ub[i] * U[1 + i];
+  }
+  Ub[0] += -irb * ir * ir;
+#pragma unroll
+  for (int i = 0; i < D; ++i) Ub[1 + i] += mb[i];
+  Ub[D + 1] += Eb;
+}
+
+// Viscous fluxes in all directions: Ub += (dF/dU)^T Fb, Qb += (dF/dQ)^T Fb.
+template <int D, typename S>
+__device__ __forceinline__ void visc_flux_all_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&Fb)[D][D + 2],
+                                                  const Gas<S>& g, S (&Ub)[D + 2], S (&Qb)[D][D + 2]) {
+  const S ir = S(1) / U[0];
+  S u[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = U[1 + i] * ir;
+  const S Et = U[D + 1] * ir;
+  S gu[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int i = 0; i < D; ++i) gu[a][i] = (Q[a][1 + i] - u[i] * Q[a][0]) * ir;
+  S div = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) div += gu[i][i];
+  // forward tau (needed for u_bar)
+  S tau[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) tau[i][j] = g.mu * (gu[i][j] + gu[j][i]) + (i == j ? g.lam * div : S(0));
+  // reverse
+  S ub[D], gub[D][D], geb[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ub[i] = S(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) gub[i][j] = S(0);
+  }
+  S divb = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const S we = Fb[i][D + 1];
+    geb[i] = g.kcv * we;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const S taub = Fb[i][1 + j] + we * u[j];
+      ub[j] += we * tau[i][j];
+      gub[i][j] += g.mu * taub;
+      gub[j][i] += g.mu * taub;
+      if (i == j) divb += g.lam * taub;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) gub[i][i] += divb;
+  S irb = 0, Etb = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    // ge[a] = (Q[a][E] - Et Q[a][0]) ir - sum_i u_i gu[a][i]
+    Qb[a][D + 1] += geb[a] * ir;
+    Qb[a][0] += -geb[a] * Et * ir;
+    Etb += -geb[a] * Q[a][0] * ir;
+    irb += geb[a] * (Q[a][D + 1] - Et * Q[a][0]);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      ub[i] += -geb[a] * gu[a][i];
+      gub[a][i] += -geb[a] * u[i];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      // gu[a][i] = (Q[a][1+i] - u_i Q[a][0]) ir
+      Qb[a][1 + i] += gub[a][i] * ir;
+      Qb[a][0] += -gub[a][i] * u[i] * ir;
+      ub[i] += -gub[a][i] * Q[a][0] * ir;
+      irb += gub[a][i] * (Q[a][1 + i] - u[i] * Q[a][0]);
+    }
+  Ub[D + 1] += Etb * ir;
+  irb += Etb * U[D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Ub[1 + i] += ub[i] * ir;
+    irb += ub[i] * U[1 + i];
+  }
+  Ub[0] += -irb * ir * ir;
+}
+
+// G = sum_i F^nu_i nv_i: cotangent Gb -> (Ub, Qb).
+template <int D, typename S>
+__device__ __forceinline__ void visc_flux_normal_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+                                                     const S (&Gb)[D + 2], const Gas<S>& g, S (&Ub)[D + 2],
+                                                     S (&Qb)[D][D + 2]) {
+  S Fb[D][D + 2];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) Fb[i][f] = Gb[f] * nv[i];
+  visc_flux_all_vjp<D, S>(U, Q, Fb, g, Ub, Qb);
+}
+
+// Adiabatic wall flux (0, tau(U_w, Q) nv, 0), d_a u_i = Q[a][1+i] / rho.
+template <int D, typename S>
+__device__ __forceinline__ void wall_visc_flux_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+                                                   const S (&Gb)[D + 2], const Gas<S>& g, S (&Ub)[D + 2],
+                                                   S (&Qb)[D][D + 2]) {
+  const S ir = S(1) / U[0];
+  S gub[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) gub[i][j] = S(0);
+  S divb = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const S taub = Gb[1 + j] * nv[i];
+      gub[i][j] += g.mu * taub;
+      gub[j][i] += g.mu * taub;
+      if (i == j) divb += g.lam * taub;
+    }
+#pragma unroll
+  for (int i = 0; i < D; ++i) gub[i][i] += divb;
+  S irb = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      Qb[a][1 + i] += gub[a][i] * ir;
+      irb += gub[a][i] * Q[a][1 + i];
+    }
+  Ub[0] += -irb * ir * ir;
+}
+
+// Mirror state R = (rho, m - 2 (m.n) n / |n|^2, rho E): linear and symmetric in m.
+template <int D, typename S>
+__device__ __forceinline__ void mirror_state_vjp(const S (&nv)[D], const S (&Rb)[D + 2], S (&Ub)[D + 2]) {
+  S n2 = 0, rn = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    n2 += nv[i] * nv[i];
+    rn += Rb[1 + i] * nv[i];
+  }
+  const S c = S(2) * rn / n2;
+  Ub[0] += Rb[0];
+#pragma unroll
+  for (int i = 0; i < D; ++i) Ub[1 + i] += Rb[1 + i] - c * nv[i];
+  Ub[D + 1] += Rb[D + 1];
+}
+
+// Wall state W = (rho, 0, rho E - |m|^2 / (2 rho)).
+template <int D, typename S>
+__device__ __forceinline__ void wall_state_vjp(const S (&U)[D + 2], const S (&Wb)[D + 2], S (&Ub)[D + 2]) {
+  const S ir = S(1) / U[0];
+  S mm = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) mm += U[1 + i] * U[1 + i];
+  Ub[0] += Wb[0] + Wb[D + 1] * S(0.5) * mm * ir * ir;
+#pragma unroll
+  for (int i = 0; i < D; ++i) Ub[1 + i] += -Wb[D + 1] * U[1 + i] * ir;
+  Ub[D + 1] += Wb[D + 1];
+}
+
+// LLF flux: cotangent Fb -> (ULb, URb).
+template <int D, typename S, bool UNIT>
+__device__ __forceinline__ void llf_flux_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
+                                             const S (&Fb)[D + 2], const Gas<S>& g, S (&ULb)[D + 2],
+                                             S (&URb)[D + 2]) {
+  S sJ = S(1);
+  if (!UNIT) {
+    S n2 = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
+    sJ = dsqrt(n2);
+  }
+  // forward quantities per side
+  S lamv[2], unv[2], cv[2], pv[2], irv[2];
+  S uv[2][D];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const S(&V)[D + 2] = side ? UR : UL;
+    const S ir = S(1) / V[0];
+    S un = 0, mm = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      uv[side][i] = V[1 + i] * ir;
+      un += uv[side][i] * nv[i];
+      mm += V[1 + i] * uv[side][i];
+    }
+    const S p = g.gm1 * (V[D + 1] - S(0.5) * mm);
+    cv[side] = dsqrt(g.gamma * p * ir);
+    lamv[side] = fabs(un) + cv[side] * sJ;
+    unv[side] = un;
+    pv[side] = p;
+    irv[side] = ir;
+  }
+  const bool left = lamv[0] >= lamv[1];
+  const S lam = left ? lamv[0] : lamv[1];
+  S lamb = 0;
+#pragma unroll
+  for (int f = 0; f < D + 2; ++f) {
+    lamb += -S(0.5) * Fb[f] * (UR[f] - UL[f]);
+    URb[f] += -S(0.5) * lam * Fb[f];
+    ULb[f] += S(0.5) * lam * Fb[f];
+  }
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const S(&V)[D + 2] = side ? UR : UL;
+    S(&Vb)[D + 2] = side ? URb : ULb;
+    const S ir = irv[side], un = unv[side], p = pv[side], c = cv[side];
+    const S sideLam = (left == (side == 0)) ? lamb : S(0);
+    // lam_side = |un| + c sJ
+    S unb = sideLam * sgn(un);
+    const S cb = sideLam * sJ;
+    // c = sqrt(gamma p ir)
+    S pb = 0, irb = 0;
+    if (c > S(0)) {
+      pb += cb * g.gamma * ir / (S(2) * c);
+      irb += cb * g.gamma * p / (S(2) * c);
+    }
+    // Fn = (m.n, m_j un + p n_j, (E + p) un) with cotangent Fb/2
+    S mb[D];
+    S Eb = S(0);
+    const S h = S(0.5);
+#pragma unroll
+    for (int i = 0; i < D; ++i) mb[i] = h * Fb[0] * nv[i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      mb[j] += h * Fb[1 + j] * un;
+      unb += h * Fb[1 + j] * V[1 + j];
+      pb += h * Fb[1 + j] * nv[j];
+    }
+    Eb += h * Fb[D + 1] * un;
+    pb += h * Fb[D + 1] * un;
+    unb += h * Fb[D + 1] * (V[D + 1] + p);
+    // un = u . n
+    S ub[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) ub[i] = unb * nv[i];
+    // p = gm1 (E - mm / 2), mm = m . u
+    Eb += g.gm1 * pb;
+    const S mmb = -S(0.5) * g.gm1 * pb;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      mb[i] += mmb * uv[side][i];
+      ub[i] += mmb * V[1 + i];
+      mb[i] += ub[i] * ir;
+      irb += ub[i] * V[1 + i];
+    }
+    Vb[0] += -irb * ir * ir;
+#pragma unroll
+    for (int i = 0; i < D; ++i) Vb[1 + i] += mb[i];
+    Vb[D + 1] += Eb;
+  }
+}
+
+}  // namespace dgx

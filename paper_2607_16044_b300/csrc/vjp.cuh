@@ -1,0 +1,596 @@
+// Adjoint (vector-Jacobian product) kernels of the explicit DG residual.
+//
+// g = (df/dU)^T lambda, obtained by running the forward pipeline of
+// kernels.cuh backwards (each step's transpose, derived by hand):
+//   k_vjp_elem    lambda -> Fhat_bar (transposed lift), U_bar (transposed
+//                 weak-divergence contraction and flux Jacobians^T), Q_bar
+//   k_vjp_face    per unique face point: LLF (and mirror-state) adjoint, written
+//                 to both sides' trace cotangents, and the viscous-flux cotangents
+//   k_vjp_br1     (NS) viscous face-flux adjoint, transposed Q traces, transposed
+//                 derivative contraction and BR1 lift adjoint; the neighbour's
+//                 share of each jump cotangent goes to a per-face buffer
+//   k_vjp_gather  transposed traces: g += sum_faces l(+-1) TU_bar (+ neighbours'
+//                 jump shares)
+// Every output location is written by exactly one thread (no atomics): face
+// quantities are per element and face, and the unique-face kernel writes both
+// sides of its face.
+//
+// For the ARK adjoint (reverse stage recurrence) the element kernel can form
+// its cotangent as  mu = c_lam * lam + sum_j c_j nu_j  on the fly, and the
+// gather kernel can finish lam_n = lam + sum_j nu_j in FP64.
+#pragma once
+#include "ops.cuh"
+
+namespace dgx {
+
+struct VjpWork {
+  void* TU;   // forward traces                  [E][2D][nf][nfp]
+  void* FFb;  // lift cotangent (Fhat_bar)        [E][2D][nf][nfp]
+  void* G;    // forward viscous face flux (unused by the adjoint, written by k_br1)
+  void* Q;    // forward BR1 gradient            [E][D][nf][N]
+  void* TUb;  // trace cotangents                 [E][2D][nf][nfp]
+  void* Gb;   // viscous face-flux cotangents     [E][2D][nf][nfp]
+  void* JB;   // BR1 jump cotangents              [E][2D][nf][nfp]
+  void* Qb;   // gradient cotangents              [E][D][nf][N]
+};
+
+// Cotangent source of the element kernel: mu = c_lam * lam + sum_j c_j nu_j.
+template <typename S>
+struct Cot {
+  const S* lam;        // plain VJP cotangent (S), or nullptr
+  const double* lam64; // ARK adjoint: lambda_{n+1} (double), or nullptr
+  double c_lam;
+  const S* nu[MAXSTAGES];
+  double c_nu[MAXSTAGES];
+  int n_nu;
+  // ARK adjoint finish (gather kernel of the last reverse stage):
+  // lam64_out = lam64 + g + sum_j nu_j
+  double* lam64_out;
+  const S* nu_all[MAXSTAGES];
+  int n_all;
+};
+
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC, bool CURV>
+__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_elem(Mesh<S> M, const S* __restrict__ U,
+                                                                const S* __restrict__ Q, Cot<S> cot,
+                                                                S* __restrict__ FFb, S* __restrict__ Ub,
+                                                                S* __restrict__ Qb) {
+  using H = Sh<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* mus = reinterpret_cast<S*>(smem_raw);  // [T][nf][N]
+  S* sDh = mus + T * H::STATE;
+  S* Lm = sDh + n * n;
+  S* Lp = Lm + n;
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  load_tab<S>(M.tabs, P, nullptr, sDh, nullptr, nullptr, Lm, Lp, n);
+  {
+    const size_t base = (size_t)e0 * H::STATE;
+    for (int i = threadIdx.x; i < nel * H::STATE; i += blockDim.x) {
+      double v = 0.0;
+      if (cot.lam) v += cot.c_lam * (double)cot.lam[base + i];
+      if (cot.lam64) v += cot.c_lam * cot.lam64[base + i];
+      for (int j = 0; j < cot.n_nu; ++j) v += cot.c_nu[j] * (double)cot.nu[j][base + i];
+      S s = (S)v;
+      if (CURV) {
+        const int t = i / H::STATE, q = i % N;
+        s *= M.geo.iJ[(size_t)(e0 + t) * N + q];
+      }
+      mus[i] = s;
+    }
+  }
+  __syncthreads();
+  // Fhat_bar[face][f][fp] = -rr_a sum_m L_side[m] mu[f](node(m, fp, a))   (output order)
+  {
+    S* dst = FFb + (size_t)e0 * H::FACE;
+    for (int i = threadIdx.x; i < nel * H::FACE; i += blockDim.x) {
+      const int fp = i % nfp;
+      int r = i / nfp;
+      const int f = r % nf;
+      r /= nf;
+      const int face = r % NF;
+      const int t = r / NF;
+      const int a = face >> 1;
+      const S* L = (face & 1) ? Lp : Lm;
+      const S* v = mus + (t * nf + f) * N;
+      S acc = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += L[m] * v[H::node(m, fp, a)];
+      const S rr = CURV ? S(1) : M.geo.rh[(e0 + t) * D + a];
+      dst[i] = -rr * acc;
+    }
+  }
+  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  if (t >= nel) return;
+  const int e = e0 + t;
+  // contravariant flux cotangent Ft_bar_a(q) = rr_a sum_m Dh[m][q_a] mu(node(m, fp_a(q), a))
+  S Fb[D][nf];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int fp = H::fpoint(q, a), qa = H::qa(q, a);
+    const S rr = CURV ? S(1) : M.geo.rh[e * D + a];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      const S* v = mus + (t * nf + f) * N;
+      S s = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) s += sDh[m * n + qa] * v[H::node(m, fp, a)];
+      Fb[a][f] = rr * s;
+    }
+  }
+  if (CURV) {  // physical flux cotangent F_bar_c = sum_a Ja[a][c] Ft_bar_a
+    S Fc[D][nf];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fc[c][f] = S(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        const S ja = M.geo.Ja[(((size_t)e * D + a) * D + c) * N + q];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) Fc[c][f] += ja * Fb[a][f];
+      }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fb[c][f] = Fc[c][f];
+  }
+  S Uq[nf], Ubq[nf];
+  const S* up = U + (size_t)e * H::STATE + q;
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    Uq[f] = up[f * N];
+    Ubq[f] = S(0);
+  }
+  conv_flux_all_vjp<D, S>(Uq, Fb, M.gas, Ubq);
+  if (VISC) {  // F = F^c - F^nu
+    S Qv[D][nf], Qbv[D][nf], Fm[D][nf];
+    const S* qp = Q + (size_t)e * D * H::STATE + q;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        Qv[c][f] = qp[(c * nf + f) * N];
+        Qbv[c][f] = S(0);
+        Fm[c][f] = -Fb[c][f];
+      }
+    visc_flux_all_vjp<D, S>(Uq, Qv, Fm, M.gas, Ubq, Qbv);
+    S* qb = Qb + (size_t)e * D * H::STATE + q;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) qb[(c * nf + f) * N] = Qbv[c][f];
+  }
+  S* ub = Ub + (size_t)e * H::STATE + q;
+#pragma unroll
+  for (int f = 0; f < nf; ++f) ub[f * N] = Ubq[f];
+}
+
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC, bool CURV>
+__global__ void __launch_bounds__(256) k_vjp_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ FFb,
+                                                  S* __restrict__ TUb, S* __restrict__ Gb) {
+  using H = Sh<D, P>;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= M.nFaces * nfp) return;
+  const int F = gid / nfp, fp = gid % nfp;
+  const int4 rec = M.faces[F];
+  const int em = rec.x, ep = rec.y;
+  const int fm = rec.z & 0xff, fo = (rec.z >> 8) & 0xff, code = (rec.z >> 16) & 0xff;
+  S nv[D];
+  if (CURV) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) nv[c] = M.geo.SnF[((size_t)F * D + c) * nfp + fp];
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) nv[c] = (c == (fm >> 1)) ? ((fm & 1) ? S(1) : S(-1)) : S(0);
+  }
+  const size_t oL = ((size_t)em * NF + fm) * nf * nfp + fp;
+  S UL[nf], UR[nf], sig[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    UL[f] = TU[oL + f * nfp];
+    sig[f] = FFb[oL + f * nfp];
+  }
+  int fpn = 0;
+  size_t oR = 0;
+  if (ep >= 0) {
+    fpn = orient_map<D, n>(code, fp);
+    oR = ((size_t)ep * NF + fo) * nf * nfp + fpn;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      UR[f] = TU[oR + f * nfp];
+      sig[f] -= FFb[oR + f * nfp];
+    }
+  } else {
+    mirror_state<D, S>(UL, nv, UR);
+  }
+  S ULb[nf], URb[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) ULb[f] = URb[f] = S(0);
+  llf_flux_vjp<D, S, !CURV>(UL, UR, nv, sig, M.gas, ULb, URb);
+  if (ep >= 0) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      TUb[oL + f * nfp] = ULb[f];
+      TUb[oR + f * nfp] = URb[f];
+    }
+    if (VISC) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        Gb[oL + f * nfp] = -S(0.5) * sig[f];
+        Gb[oR + f * nfp] = S(0.5) * sig[f];
+      }
+    }
+  } else {
+    mirror_state_vjp<D, S>(nv, URb, ULb);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) TUb[oL + f * nfp] = ULb[f];
+    if (VISC) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Gb[oL + f * nfp] = -sig[f];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool CURV>
+__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_br1(Mesh<S> M, const S* __restrict__ TU,
+                                                               const S* __restrict__ Q, const S* __restrict__ Gb,
+                                                               S* __restrict__ Qb, S* __restrict__ TUb,
+                                                               S* __restrict__ JB, S* __restrict__ Ub) {
+  using H = Sh<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* qs = reinterpret_cast<S*>(smem_raw);   // [T][D][nf][N]  forward Q, later dU_bar
+  S* qbs = qs + T * D * H::STATE;            // [T][D][nf][N]  Q_bar (total), later P
+  S* tqb = qbs + T * D * H::STATE;           // [T][NF][D][nf][nfp] TQ_bar
+  S* tub = tqb + T * NF * D * nf * nfp;      // [T][NF][nf][nfp] own TU_bar
+  S* sD = tub + T * H::FACE;
+  S* lm = sD + n * n;
+  S* lp = lm + n;
+  S* Lm = lp + n;
+  S* Lp = Lm + n;
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  load_tab<S>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
+  {
+    const S* qsrc = Q + (size_t)e0 * D * H::STATE;
+    const S* qbsrc = Qb + (size_t)e0 * D * H::STATE;
+    for (int i = threadIdx.x; i < nel * D * H::STATE; i += blockDim.x) {
+      qs[i] = qsrc[i];
+      qbs[i] = qbsrc[i];
+    }
+  }
+  __syncthreads();
+  // 1. viscous face-flux adjoint at every own face point
+  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+    const int fp = i % nfp;
+    const int face = (i / nfp) % NF;
+    const int t = i / (nfp * NF);
+    const int e = e0 + t;
+    const int a = face >> 1;
+    const S* l = (face & 1) ? lp : lm;
+    const size_t o = ((size_t)e * NF + face) * nf * nfp + fp;
+    S UL[nf], TQ[D][nf], nv[D], gb[nf], ubf[nf], tqbv[D][nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      UL[f] = TU[o + f * nfp];
+      gb[f] = Gb[o + f * nfp];
+      ubf[f] = TUb[o + f * nfp];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        const S* v = qs + ((t * D + c) * nf + f) * N;
+        S s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += l[m] * v[H::node(m, fp, a)];
+        TQ[c][f] = s;
+        tqbv[c][f] = S(0);
+      }
+    if (CURV) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) nv[c] = M.geo.SnE[(((size_t)e * NF + face) * D + c) * nfp + fp];
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c) nv[c] = (c == a) ? ((face & 1) ? S(1) : S(-1)) : S(0);
+    }
+    if (M.nb[e * NF + face] >= 0)
+      visc_flux_normal_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
+    else
+      wall_visc_flux_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) tub[((t * NF + face) * nf + f) * nfp + fp] = ubf[f];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) tqb[(((t * NF + face) * D + c) * nf + f) * nfp + fp] = tqbv[c][f];
+  }
+  __syncthreads();
+  // 2. Q_bar += transposed traces of TQ_bar; then P = (iJ) Q_bar in place
+  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  const bool active = t < nel;
+  const int e = e0 + t;
+  if (active) {
+    const S iJ = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S s = qbs[((t * D + c) * nf + f) * N + q];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int fp = H::fpoint(q, a), qa = H::qa(q, a);
+          s += lm[qa] * tqb[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + fp];
+          s += lp[qa] * tqb[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + fp];
+        }
+        qbs[((t * D + c) * nf + f) * N + q] = s * iJ;
+      }
+  }
+  __syncthreads();
+  // 3. dU_bar_b(q) = (box) r_b P_b  |  (curv) sum_c Ja[b][c] P_c   -> qs (forward Q no longer needed)
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S s;
+        if (CURV) {
+          s = 0;
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            s += M.geo.Ja[(((size_t)e * D + b) * D + c) * N + q] * qbs[((t * D + c) * nf + f) * N + q];
+        } else {
+          s = M.geo.rh[e * D + b] * qbs[((t * D + b) * nf + f) * N + q];
+        }
+        qs[((t * D + b) * nf + f) * N + q] = s;
+      }
+  }
+  __syncthreads();
+  // 4. U_bar += sum_b D_b^T dU_bar_b
+  if (active) {
+    S* ub = Ub + (size_t)e * H::STATE + q;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      S s = 0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        const int fp = H::fpoint(q, b), qb = H::qa(q, b);
+        const S* v = qs + ((t * D + b) * nf + f) * N;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += sD[m * n + qb] * v[H::node(m, fp, b)];
+      }
+      ub[f * N] += s;
+    }
+  }
+  // 5. jump cotangents J_bar[face][f][fp] and the own trace cotangent
+  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+    const int fp = i % nfp;
+    const int face = (i / nfp) % NF;
+    const int tt = i / (nfp * NF);
+    const int ee = e0 + tt;
+    const int a = face >> 1;
+    const S* L = (face & 1) ? Lp : Lm;
+    S jb[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      S s = 0;
+      if (CURV) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const S sn = M.geo.SnE[(((size_t)ee * NF + face) * D + c) * nfp + fp];
+          const S* v = qbs + ((tt * D + c) * nf + f) * N;
+          S sc = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) sc += L[m] * v[H::node(m, fp, a)];
+          s += sn * sc;
+        }
+      } else {
+        const S* v = qbs + ((tt * D + a) * nf + f) * N;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += L[m] * v[H::node(m, fp, a)];
+        s *= M.geo.rh[ee * D + a] * ((face & 1) ? S(1) : S(-1));
+      }
+      jb[f] = s;
+    }
+    const size_t o = ((size_t)ee * NF + face) * nf * nfp + fp;
+    S ubf[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) ubf[f] = tub[((tt * NF + face) * nf + f) * nfp + fp];
+    if (M.nb[ee * NF + face] >= 0) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        ubf[f] -= S(0.5) * jb[f];
+        JB[o + f * nfp] = jb[f];
+      }
+    } else {
+      S UL[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        UL[f] = TU[o + f * nfp];
+        ubf[f] -= jb[f];
+        JB[o + f * nfp] = S(0);
+      }
+      wall_state_vjp<D, S>(UL, jb, ubf);
+    }
+#pragma unroll
+    for (int f = 0; f < nf; ++f) TUb[o + f * nfp] = ubf[f];
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_gather(Mesh<S> M, const S* __restrict__ TUb,
+                                                                  const S* __restrict__ JB, S* g, Cot<S> cot) {
+  using H = Sh<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* tub = reinterpret_cast<S*>(smem_raw);  // [T][NF][nf][nfp]
+  S* lm = tub + T * H::FACE;
+  S* lp = lm + n;
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  load_tab<S>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);
+  {
+    const S* src = TUb + (size_t)e0 * H::FACE;
+    for (int i = threadIdx.x; i < nel * H::FACE; i += blockDim.x) {
+      S v = src[i];
+      if (VISC) {
+        const int fp = i % nfp;
+        const int f = (i / nfp) % nf;
+        const int face = (i / (nfp * nf)) % NF;
+        const int t = i / H::FACE;
+        const int e = e0 + t;
+        const int nbe = M.nb[e * NF + face];
+        if (nbe >= 0) {
+          const int fpn = orient_map<D, n>(M.ori[e * NF + face], fp);
+          v += S(0.5) * JB[(((size_t)nbe * NF + M.nbf[e * NF + face]) * nf + f) * nfp + fpn];
+        }
+      }
+      tub[i] = v;
+    }
+  }
+  __syncthreads();
+  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  if (t >= nel) return;
+  const int e = e0 + t;
+  const size_t off = (size_t)e * H::STATE + q;
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    S s = g[off + f * N];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int fp = H::fpoint(q, a), qa = H::qa(q, a);
+      s += lm[qa] * tub[((t * NF + 2 * a) * nf + f) * nfp + fp];
+      s += lp[qa] * tub[((t * NF + 2 * a + 1) * nf + f) * nfp + fp];
+    }
+    g[off + f * N] = s;
+    if (cot.lam64_out) {  // ARK adjoint: lambda_n = lambda_{n+1} + sum_j nu_j (FP64)
+      double acc = cot.lam64_out[off + f * N] + (double)s;
+      for (int j = 0; j < cot.n_all; ++j) acc += (double)cot.nu_all[j][off + f * N];
+      cot.lam64_out[off + f * N] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S>
+struct VjpOps {
+  using H = Sh<D, P>;
+  static size_t smem_elem() { return sizeof(S) * (H::T * H::STATE + H::n * H::n + 2 * H::n); }
+  static size_t smem_br1() {
+    return sizeof(S) * (2 * H::T * D * H::STATE + H::T * H::NF * D * H::nf * H::nfp + H::T * H::FACE +
+                        H::n * H::n + 4 * H::n);
+  }
+  static size_t smem_gather() { return sizeof(S) * (H::T * H::FACE + 2 * H::n); }
+  static int blocks(int E) { return (E + H::T - 1) / H::T; }
+  template <typename K>
+  static void allow(K k, size_t b) {
+    if (b > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+  }
+
+  static cudaError_t elem(const Mesh<S>& M, bool visc, bool curv, const S* U, const VjpWork& w, const Cot<S>& c,
+                          S* Ub, cudaStream_t st) {
+#define DGX_VE(V, C)                                                                                   \
+  {                                                                                                    \
+    auto k = k_vjp_elem<D, P, S, V, C>;                                                                \
+    allow(k, smem_elem());                                                                             \
+    k<<<blocks(M.E), H::THREADS, smem_elem(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb); \
+  }
+    if (visc) {
+      if (curv) DGX_VE(true, true) else DGX_VE(true, false)
+    } else {
+      if (curv) DGX_VE(false, true) else DGX_VE(false, false)
+    }
+#undef DGX_VE
+    return cudaGetLastError();
+  }
+
+  static cudaError_t face(const Mesh<S>& M, bool visc, bool curv, const VjpWork& w, cudaStream_t st) {
+    const int total = M.nFaces * H::nfp;
+    if (total == 0) return cudaSuccess;
+    const int nb = (total + 255) / 256;
+    const S* TU = (const S*)w.TU;
+    const S* FFb = (const S*)w.FFb;
+    S* TUb = (S*)w.TUb;
+    S* Gb = (S*)w.Gb;
+    if (visc) {
+      if (curv) k_vjp_face<D, P, S, true, true><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
+      else k_vjp_face<D, P, S, true, false><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
+    } else {
+      if (curv) k_vjp_face<D, P, S, false, true><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
+      else k_vjp_face<D, P, S, false, false><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t br1(const Mesh<S>& M, bool curv, const VjpWork& w, S* Ub, cudaStream_t st) {
+    const size_t sm = smem_br1();
+    if (curv) {
+      auto k = k_vjp_br1<D, P, S, true>;
+      allow(k, sm);
+      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb, (S*)w.Qb,
+                                             (S*)w.TUb, (S*)w.JB, Ub);
+    } else {
+      auto k = k_vjp_br1<D, P, S, false>;
+      allow(k, sm);
+      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb, (S*)w.Qb,
+                                             (S*)w.TUb, (S*)w.JB, Ub);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t gather(const Mesh<S>& M, bool visc, const VjpWork& w, S* g, const Cot<S>& c,
+                            cudaStream_t st) {
+    const size_t sm = smem_gather();
+    if (visc) {
+      auto k = k_vjp_gather<D, P, S, true>;
+      allow(k, sm);
+      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
+    } else {
+      auto k = k_vjp_gather<D, P, S, false>;
+      allow(k, sm);
+      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
+    }
+    return cudaGetLastError();
+  }
+};
+
+// Type-erased adjoint launch table (one per (D, P, S)).
+struct VjpTable {
+  cudaError_t (*elem)(const void* M, bool visc, bool curv, const void* U, const VjpWork& w, const void* cot,
+                      void* Ub, cudaStream_t st);
+  cudaError_t (*face)(const void* M, bool visc, bool curv, const VjpWork& w, cudaStream_t st);
+  cudaError_t (*br1)(const void* M, bool curv, const VjpWork& w, void* Ub, cudaStream_t st);
+  cudaError_t (*gather)(const void* M, bool visc, const VjpWork& w, void* g, const void* cot, cudaStream_t st);
+};
+
+template <int D, int P, typename S>
+const void* vjp_table() {
+  struct R {
+    static cudaError_t elem(const void* M, bool v, bool c, const void* U, const VjpWork& w, const void* cot, void* Ub,
+                            cudaStream_t st) {
+      return VjpOps<D, P, S>::elem(*(const Mesh<S>*)M, v, c, (const S*)U, w, *(const Cot<S>*)cot, (S*)Ub, st);
+    }
+    static cudaError_t face(const void* M, bool v, bool c, const VjpWork& w, cudaStream_t st) {
+      return VjpOps<D, P, S>::face(*(const Mesh<S>*)M, v, c, w, st);
+    }
+    static cudaError_t br1(const void* M, bool c, const VjpWork& w, void* Ub, cudaStream_t st) {
+      return VjpOps<D, P, S>::br1(*(const Mesh<S>*)M, c, w, (S*)Ub, st);
+    }
+    static cudaError_t gather(const void* M, bool v, const VjpWork& w, void* g, const void* cot, cudaStream_t st) {
+      return VjpOps<D, P, S>::gather(*(const Mesh<S>*)M, v, w, (S*)g, *(const Cot<S>*)cot, st);
+    }
+  };
+  static const VjpTable t = {&R::elem, &R::face, &R::br1, &R::gather};
+  return &t;
+}
+
+}  // namespace dgx

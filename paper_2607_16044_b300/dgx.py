@@ -41,7 +41,7 @@ _lib = None
 EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_nodes", "dgx_set_tableau",
            "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
            "dgx_status_string", "dgx_query", "dgx_profile_enable", "dgx_profile_read", "dgx_profile_reset",
-           "dgx_kernel_name"]
+           "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step"]
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -64,6 +64,8 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_rhs.argtypes = [vp, vp, vp, vp, vp]
     lib.dgx_rhs_vjp.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_ark_step.argtypes = [vp, vp, dbl, vp, vp]
+    lib.dgx_ark_step_stages.argtypes = [vp, vp, dbl, vp, vp, vp]
+    lib.dgx_ark_adjoint_step.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.dgx_check.argtypes = [vp]
     lib.dgx_status_string.argtypes = [i32]
     lib.dgx_status_string.restype = ctypes.c_char_p
@@ -171,12 +173,14 @@ class Solver:
         return torch.empty(self.shape, dtype=dtype or self.dtype, device=self.device)
 
     def set_tableau(self, A, b, c):
+        """Explicit tableau (e.g. ``tableaux.ars343_explicit()``)."""
         A = np.ascontiguousarray(A, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         c = np.ascontiguousarray(c, dtype=np.float64)
         _check(self.lib.dgx_set_tableau(self.h, len(b), _ptr(A), _ptr(b), _ptr(c)), "dgx_set_tableau")
         self.stages = len(b)
         self._ws.pop(OP_ARK, None)
+        self._ws.pop(OP_ARK_ADJOINT, None)
 
     # ------------------------------------------------------------------ compute
     def rhs(self, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
@@ -200,6 +204,33 @@ class Solver:
                                      _stream_ptr(stream)), "dgx_ark_step")
         return U64
 
+    def stage_buffer(self) -> torch.Tensor:
+        """Device buffer for the stage checkpoints y_1..y_s of one step."""
+        if not self.stages:
+            raise DGXError(7, "stage_buffer (no tableau)")
+        return torch.empty((self.stages,) + self.shape, dtype=self.dtype, device=self.device)
+
+    def ark_step_stages(self, U64: torch.Tensor, dt: float, stages: torch.Tensor, stream=None) -> torch.Tensor:
+        if not (stages.is_cuda and stages.dtype == self.dtype and stages.is_contiguous()
+                and tuple(stages.shape) == (self.stages,) + self.shape):
+            raise ValueError("stages must come from stage_buffer()")
+        ws = self.workspace(OP_ARK)
+        _check(self.lib.dgx_ark_step_stages(self.h, self._state(U64, "U64", torch.float64), float(dt),
+                                            ctypes.c_void_p(stages.data_ptr()), self._aligned(ws),
+                                            _stream_ptr(stream)), "dgx_ark_step_stages")
+        return U64
+
+    def ark_adjoint_step(self, stages: torch.Tensor, lam64: torch.Tensor, dt: float, stream=None) -> torch.Tensor:
+        """lam64: cotangent of U_{n+1} on entry, of U_n on exit (FP64, in place)."""
+        if not (stages.is_cuda and stages.dtype == self.dtype and stages.is_contiguous()
+                and tuple(stages.shape) == (self.stages,) + self.shape):
+            raise ValueError("stages must come from stage_buffer()")
+        ws = self.workspace(OP_ARK_ADJOINT)
+        _check(self.lib.dgx_ark_adjoint_step(self.h, ctypes.c_void_p(stages.data_ptr()),
+                                             self._state(lam64, "lam64", torch.float64), float(dt),
+                                             self._aligned(ws), _stream_ptr(stream)), "dgx_ark_adjoint_step")
+        return lam64
+
     def check(self):
         _check(self.lib.dgx_check(self.h), "dgx_check")
 
@@ -222,3 +253,47 @@ class Solver:
             if n.value:
                 out[name] = (n.value, ms.value)
         return out
+
+
+class Residual(torch.autograd.Function):
+    """f = dU/dt as a differentiable torch op; backward is the hand-written
+    adjoint kernel chain (dgx_rhs_vjp), not autograd of anything."""
+
+    @staticmethod
+    def forward(ctx, U, solver):
+        ctx.solver = solver
+        ctx.save_for_backward(U)
+        return solver.rhs(U.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (U,) = ctx.saved_tensors
+        return ctx.solver.rhs_vjp(U.contiguous(), grad_out.contiguous()), None
+
+
+def residual(U: torch.Tensor, solver: Solver) -> torch.Tensor:
+    return Residual.apply(U, solver)
+
+
+def adjoint_trajectory(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int, lam_final: torch.Tensor,
+                       checkpoints: Optional[list] = None):
+    """Gradient of <lam_final, U_N> w.r.t. U_0 through N explicit ARK steps.
+
+    Forward: store U_n (FP64) before every step (one checkpoint per step).
+    Reverse: for n = N-1 .. 0 recompute the step's stage states from U_n with
+    dgx_ark_step_stages and apply dgx_ark_adjoint_step.  Returns (U_N, lam_0).
+    """
+    U = U0.clone()
+    ckpt = checkpoints if checkpoints is not None else []
+    ckpt.clear()
+    for _ in range(nsteps):
+        ckpt.append(U.clone())
+        solver.ark_step(U, dt)
+    lam = lam_final.clone()
+    stages = solver.stage_buffer()
+    work = torch.empty_like(U)
+    for n in reversed(range(nsteps)):
+        work.copy_(ckpt[n])
+        solver.ark_step_stages(work, dt, stages)
+        solver.ark_adjoint_step(stages, lam, dt)
+    return U, lam
