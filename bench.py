@@ -91,50 +91,67 @@ def kernel_model(d, p, viscous, prec, stage_i=1, stages=4):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms (read only)."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event (throttle) reasons sampled every 2 ms through
+    NVML while the timed region runs (read-only queries)."""
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
 
-    def __init__(self, index=0):
-        self.index = index
+    def __init__(self, torch_device=0, period=0.002):
         self.rows = []
-        self.proc = None
+        self.period = period
+        self.dev = torch_device
+        self.nv = None
+        self.stop = threading.Event()
 
     def __enter__(self):
+        self.err = None
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
+            import pynvml as nv
+            nv.nvmlInit()
+            self.h = None
+            try:
+                import torch
+                props = torch.cuda.get_device_properties(self.dev)
+                bus = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+                self.h = nv.nvmlDeviceGetHandleByPciBusId(bus.encode())
+            except Exception:
+                vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+                idx = int(vis.split(",")[self.dev]) if vis and vis.split(",")[0].isdigit() else self.dev
+                self.h = nv.nvmlDeviceGetHandleByIndex(idx)
+            self.nv = nv
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+            self.thread = threading.Thread(target=self._run, daemon=True)
             self.thread.start()
-        except FileNotFoundError:
-            self.proc = None
+        except Exception as exc:  # no NVML: report no samples
+            self.err = repr(exc)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+    def _run(self):
+        nv = self.nv
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            try:
+                self.rows.append((nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM), int(get_reasons(self.h))))
+            except Exception as exc:
+                self.err = repr(exc)
+            time.sleep(self.period)
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self.stop.set()
+        if self.nv is not None:
+            self.thread.join(timeout=2)
 
     def summary(self):
-        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "error": self.err}
+        sm = [r[0] for r in self.rows]
+        mask = 0
         for r in self.rows:
-            for k, name in enumerate(names):
-                if len(r) > 4 + k and r[4 + k].lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            mask |= r[1]
+        reasons = sorted(k for k, bit in self.REASONS.items() if mask & bit)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(sm), "sampler": "NVML every 2 ms"}
 
 
 # ---------------------------------------------------------------------------
@@ -152,19 +169,21 @@ def make_solver(prec):
 
 
 def time_gpu(prec, steps, warmup, dt=1e-9):
+    """K timed steps; each step = one ARS(3,4,3) step keeping its stage states
+    + the discrete adjoint of that step (4 VJPs), L2 flushed between steps."""
     import torch
     s, mesh, phys, U0 = make_solver(prec)
     dev = torch.device("cuda", torch.cuda.current_device())
     U = torch.as_tensor(U0, device=dev).contiguous()
-    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape), device=dev)
+    lam0 = np.random.default_rng(102).standard_normal(U0.shape)
+    lam = torch.as_tensor(lam0, device=dev).contiguous()
+    stages = s.stage_buffer()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (126 MB)
     stream = torch.cuda.current_stream()
-    has_vjp = s.supports_adjoint()
 
     def step():
-        s.ark_step(U, dt)
-        if has_vjp:
-            s.ark_adjoint_step(U, lam, dt)
+        s.ark_step_stages(U, dt, stages)
+        s.ark_adjoint_step(stages, lam, dt)
 
     for _ in range(warmup):
         step()
@@ -187,11 +206,12 @@ def time_gpu(prec, steps, warmup, dt=1e-9):
     prof = s.profile_read()
     s.profile(False)
     s.check()
-    # end-to-end through the public API with pinned host buffers
-    host_in = torch.as_tensor(U0).pin_memory()
-    host_lam = lam.cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    host_lam_out = torch.empty_like(host_lam).pin_memory()
+    # end to end through the public API: pinned host U_n and lambda_{n+1} in,
+    # U_{n+1} and lambda_n out, every step
+    host_U = torch.as_tensor(U0).pin_memory()
+    host_lam = torch.as_tensor(lam0).pin_memory()
+    out_U = torch.empty_like(host_U).pin_memory()
+    out_lam = torch.empty_like(host_lam).pin_memory()
     e2e = []
     for k in range(max(3, steps // 2) + 1):
         flush.fill_(1)
@@ -199,27 +219,21 @@ def time_gpu(prec, steps, warmup, dt=1e-9):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        U.copy_(host_in, non_blocking=True)
-        if has_vjp:
-            lam.copy_(host_lam, non_blocking=True)
+        U.copy_(host_U, non_blocking=True)
+        lam.copy_(host_lam, non_blocking=True)
         step()
-        host_out.copy_(U, non_blocking=True)
-        if has_vjp:
-            host_lam_out.copy_(lam, non_blocking=True)
+        out_U.copy_(U, non_blocking=True)
+        out_lam.copy_(lam, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         if k:
             e2e.append(e0.elapsed_time(e1))
     s.check()
     nbytes_state = U.numel() * 8
-    h2d = nbytes_state * (2 if has_vjp else 1)
-    d2h = nbytes_state * (2 if has_vjp else 1)
     dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
-    evals_per_step = 4 * (2 if has_vjp else 1)
-    ms = float(np.mean(times))
-    return {"ms": ms, "ms_all": times, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
-            "evals_per_step": evals_per_step, "e2e_ms": float(np.mean(e2e)), "h2d": h2d, "d2h": d2h,
-            "mesh": mesh, "phys": phys, "has_vjp": has_vjp}
+    return {"ms": float(np.mean(times)), "ms_all": times, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
+            "evals_per_step": 8, "e2e_ms": float(np.mean(e2e)), "h2d": 2 * nbytes_state, "d2h": 2 * nbytes_state,
+            "mesh": mesh, "phys": phys, "steps": steps}
 
 
 def roofline(res, prec, pk):
@@ -326,6 +340,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="fp32,fp64", help="precisions to time (profiling runs may pick one)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -343,7 +358,15 @@ def main():
     pk = peaks()
     if world > 1:
         torch.distributed.barrier()
+    legs = args.legs.split(",")
+    if legs == ["fp64"]:
+        r = time_gpu("fp64", args.steps, args.warmup)
+        print(json.dumps({"leg": "fp64", "ms_per_step": r["ms"], "prof": r["prof"]}))
+        return
     r32 = time_gpu("fp32", args.steps, args.warmup)
+    if "fp64" not in legs:
+        print(json.dumps({"leg": "fp32", "ms_per_step": r32["ms"], "prof": r32["prof"]}))
+        return
     r64 = time_gpu("fp64", max(3, args.steps // 4), 3)
     ms = r32["ms"]
     if world > 1:
@@ -355,12 +378,13 @@ def main():
     e2e_value = evals / (r32["e2e_ms"] / 1e3) * world
     roof = roofline(r32, "fp32", pk)
     roof64 = roofline(r64, "fp64", pk)
-    launches = sum(v[0] for v in r32["prof"].values()) // max(1, args.steps)
+    launches = sum(v[0] for v in r32["prof"].values())
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
             "config": {"workload": WORKLOAD, "elements": r32["mesh"].n_elem, "dofs": r32["dofs"],
-                       "step": ("1 ARS(3,4,3) step + its adjoint" if r32["has_vjp"] else "1 ARS(3,4,3) step"),
+                       "step": "1 ARS(3,4,3) step (stage states kept) + its discrete adjoint (4 VJPs)",
+                       "kernel_launches_per_step": launches // max(1, args.steps),
                        "dof_evals_per_step": evals, "l2": "flushed (256 MB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "gpu_launches": int(launches),
