@@ -150,6 +150,20 @@ dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stag
 dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
                                 void* stream);
 
+/* Residual for callers that cannot allocate device memory (no counterpart in
+ * the paper; a deployment convenience).  Same result as dgx_rhs, but the
+ * scratch comes from a fixed array inside the library instead of a caller
+ * workspace, so the call allocates nothing: for hosts that reserve all device
+ * memory up front or plugin hosts that pass only inputs and outputs.
+ * Limit: dgx_workspace_bytes(h, DGX_OP_RHS) must not exceed
+ * DGX_NOALLOC_SCRATCH_BYTES (64 MiB), else DGX_EINVAL.  The array is held on
+ * every device that loads the library until the process exits.  The first
+ * call on each device looks up the array's device address (with that device
+ * current); make it before any stream capture.  All calls on a device share
+ * the array: calls that may overlap on the GPU race and must be serialised. */
+#define DGX_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+dgx_status dgx_rhs_noalloc(dgx_handle* h, const void* U, void* dUdt, void* stream);
+
 /* Synchronise with the device and report (then clear) device-side flags:
  * DGX_ENONFINITE if any residual value was NaN/Inf since the last check. */
 dgx_status dgx_check(dgx_handle* h);

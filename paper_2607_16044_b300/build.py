@@ -93,6 +93,7 @@ def _write_sources():
     _write_if_changed(path, DISPATCH.format(DECLS="\n".join(decls), FUNCS="\n".join(funcs)))
     units.append(path)
     units.append(os.path.join(CSRC, "host.cu"))
+    units.append(os.path.join(CSRC, "noalloc.cu"))
     return units
 
 

@@ -41,7 +41,7 @@ _lib = None
 EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_nodes", "dgx_set_tableau",
            "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
            "dgx_status_string", "dgx_query", "dgx_profile_enable", "dgx_profile_read", "dgx_profile_reset",
-           "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step"]
+           "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc"]
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_ark_step.argtypes = [vp, vp, dbl, vp, vp]
     lib.dgx_ark_step_stages.argtypes = [vp, vp, dbl, vp, vp, vp]
     lib.dgx_ark_adjoint_step.argtypes = [vp, vp, vp, dbl, vp, vp]
+    lib.dgx_rhs_noalloc.argtypes = [vp, vp, vp, vp]
     lib.dgx_check.argtypes = [vp]
     lib.dgx_status_string.argtypes = [i32]
     lib.dgx_status_string.restype = ctypes.c_char_p
@@ -188,6 +189,14 @@ class Solver:
         ws = self.workspace(OP_RHS)
         _check(self.lib.dgx_rhs(self.h, self._state(U), self._state(out, "out"), self._aligned(ws),
                                 _stream_ptr(stream)), "dgx_rhs")
+        return out
+
+    def rhs_noalloc(self, U: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """f = dU/dt without a workspace: for callers that may not allocate
+        device memory (the scratch is the library's fixed 64 MiB array, shared
+        by every call on the device; overlapping calls race)."""
+        _check(self.lib.dgx_rhs_noalloc(self.h, self._state(U), self._state(out, "out"), _stream_ptr(stream)),
+               "dgx_rhs_noalloc")
         return out
 
     def rhs_vjp(self, U: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
