@@ -134,10 +134,17 @@ dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* g
  * (FP32 handles evaluate f in FP32 on a rounded copy of the stage state). */
 dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, void* stream);
 
-/* The same step, also storing the stage states y_1..y_s it evaluates (stage
- * checkpointing for the adjoint): stages is a device buffer of s consecutive
- * states [s][E][nf][N] in the handle's precision (y_1 = U_n, rounded to FP32
- * on FP32 handles). */
+/* Bytes of one step's stage-checkpoint buffer (0 before dgx_set_tableau).  The
+ * buffer holds s equal slots of dgx_stage_bytes / s bytes; slot i (0-based)
+ * begins with the stage state y_{i+1} [E][nf][N] in the handle's precision,
+ * followed by that stage's face traces and (viscous) BR1 gradient, which the
+ * adjoint reuses instead of recomputing them. */
+size_t dgx_stage_bytes(const dgx_handle* h);
+
+/* The same step, also storing the stage states y_1..y_s it evaluates and their
+ * traces / gradients (stage checkpointing for the adjoint) in stages, a device
+ * buffer of dgx_stage_bytes(h) bytes, 256-byte aligned (y_1 = U_n, rounded to
+ * FP32 on FP32 handles). */
 dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, void* stream);
 
 /* Discrete adjoint of one explicit ARK step (reverse of the Sec. 4.2 stage

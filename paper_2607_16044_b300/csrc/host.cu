@@ -333,6 +333,22 @@ Layout layout(const dgx_handle* h, int op) {
   return L;
 }
 
+// Stage-checkpoint slot: y_i | TU_i | Q_i (viscous).
+struct Slot {
+  size_t y, TU, Q, bytes;
+};
+
+Slot slot_layout(const dgx_handle* h) {
+  const size_t face = (size_t)h->E * h->NF * h->nf * h->nfp * h->s;
+  const size_t state = (size_t)h->E * h->nf * h->N * h->s;
+  Slot S{};
+  S.y = 0;
+  S.TU = align256(state);
+  S.Q = S.TU + align256(face);
+  S.bytes = S.Q + (h->viscous ? align256(state * h->d) : 0);
+  return S;
+}
+
 dgx::Work work_at(const dgx_handle* h, void* ws, const Layout& L) {
   char* b = (char*)ws;
   dgx::Work w;
@@ -363,14 +379,17 @@ dgx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DGX_OK : DGX_E
 // nu = (df/dU)(U)^T mu with mu described by cot (see dgx::Cot).
 template <typename S>
 cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, const dgx::Cot<S>& fin, void* g,
-                      const dgx::VjpWork& vw, cudaStream_t st) {
+                      const dgx::VjpWork& vw, cudaStream_t st, bool have_forward = false) {
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   const dgx::VjpTable* v = (const dgx::VjpTable*)t->vjp;
   dgx::Work w{vw.TU, vw.FFb, vw.G, vw.Q};
-  cudaError_t err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
-  if (err == cudaSuccess && h->viscous)
-    err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+  cudaError_t err = cudaSuccess;
+  if (!have_forward) {  // recompute the forward traces and BR1 gradient
+    err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
+    if (err == cudaSuccess && h->viscous)
+      err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+  }
   if (err == cudaSuccess)
     err = launch(h, DGX_K_VJP_ELEM, st, [&] { return v->elem(M, h->viscous, h->curv, U, vw, &cot, g, st); });
   if (err == cudaSuccess)
@@ -390,15 +409,20 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
   S* Y = (S*)(base + L.Y);
   const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
   S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
-  const size_t state_b = (size_t)h->E * h->nf * h->N * h->s;
-  S* ys = (S*)stages;  // optional stage checkpoints y_1..y_s
-  S* first = ys ? ys : shadow;  // where the rounded (or copied) U_n goes
+  const Slot SL = slot_layout(h);
+  char* ck = (char*)stages;  // optional stage checkpoints (slots)
+  auto slot_y = [&](int i) { return (S*)(ck + SL.bytes * i + SL.y); };
+  auto slot_tu = [&](int i) { return (void*)(ck + SL.bytes * i + SL.TU); };
+  auto slot_q = [&](int i) { return (void*)(ck + SL.bytes * i + SL.Q); };
+  S* first = ck ? slot_y(0) : shadow;  // where the rounded (or copied) U_n goes
+  dgx::Work w0 = w;
+  if (ck) w0.TU = slot_tu(0);
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   cudaError_t err =
-      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w.TU, first, st); });
+      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w0.TU, first, st); });
   if (err != cudaSuccess) return DGX_ECUDA;
-  const S* y0 = (h->fp64 && !ys) ? (const S*)U64 : first;
+  const S* y0 = (h->fp64 && !ck) ? (const S*)U64 : first;
   const int s = h->stages;
   for (int i = 0; i < s; ++i) {
     dgx::Stage<S> sa{};
@@ -410,15 +434,20 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     for (int j = 0; j < s; ++j) sa.cb[j] = dt * h->b[j];
     sa.base = y0;
     sa.Un = U64;
-    sa.Y = (ys && !sa.last) ? ys + (state_b / sizeof(S)) * (i + 1) : Y;
+    sa.Y = (ck && !sa.last) ? slot_y(i + 1) : Y;
     sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
     sa.shadow = shadow;  // FP32: rounded U_{n+1} (unused by the next step, which re-rounds U64)
-    sa.TU = (S*)w.TU;
-    const S* Uin = (i == 0) ? y0 : (ys ? ys + (state_b / sizeof(S)) * i : Y);
-    if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, Uin, w, st); });
-    if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
+    dgx::Work wi = w;
+    if (ck) {
+      wi.TU = slot_tu(i);
+      wi.Q = h->viscous ? slot_q(i) : nullptr;
+    }
+    sa.TU = (S*)((ck && !sa.last) ? slot_tu(i + 1) : w.TU);
+    const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
+    if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, Uin, wi, st); });
+    if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, wi, st); });
     if (err == cudaSuccess)
-      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->viscous, h->curv, Uin, w, &sa, st); });
+      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->viscous, h->curv, Uin, wi, &sa, st); });
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -428,14 +457,18 @@ template <typename S>
 dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
                             cudaStream_t st) {
   const Layout L = layout(h, DGX_OP_ARK_ADJOINT);
-  const dgx::VjpWork vw = vjp_work_at(h, workspace, L);
+  dgx::VjpWork vw = vjp_work_at(h, workspace, L);
   const size_t state_b = (size_t)h->E * h->nf * h->N * h->s;
   const size_t state_a = align256(state_b);
   char* base = (char*)workspace;
   auto NU = [&](int j) { return (S*)(base + L.NU + state_a * j); };
+  const Slot SL = slot_layout(h);
   const int s = h->stages;
   for (int i = s - 1; i >= 0; --i) {
-    const void* y = (const char*)stages + state_b * i;
+    const char* slot = (const char*)stages + SL.bytes * i;
+    const void* y = slot + SL.y;
+    vw.TU = (void*)(slot + SL.TU);
+    vw.Q = h->viscous ? (void*)(slot + SL.Q) : nullptr;
     dgx::Cot<S> cot{}, fin{};
     cot.lam64 = lam64;
     cot.c_lam = dt * h->b[i];
@@ -451,7 +484,7 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
       fin.lam64_out = lam64;
       for (int j = 1; j < s; ++j) fin.nu_all[fin.n_all++] = NU(j);
     }
-    const cudaError_t err = vjp_chain<S>(h, y, cot, fin, NU(i), vw, st);
+    const cudaError_t err = vjp_chain<S>(h, y, cot, fin, NU(i), vw, st, /*have_forward=*/true);
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -713,6 +746,11 @@ dgx_status dgx_set_tableau(dgx_handle* h, int32_t stages, const double* A, const
   return DGX_OK;
 }
 
+size_t dgx_stage_bytes(const dgx_handle* h) {
+  if (!h || h->stages == 0) return 0;
+  return slot_layout(h).bytes * h->stages;
+}
+
 size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (!h) return 0;
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
@@ -770,6 +808,7 @@ dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, 
 
 dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, void* stream) {
   if (!h || !U64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
+  if (((uintptr_t)stages & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->fp64) return ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream);

@@ -41,7 +41,8 @@ _lib = None
 EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_nodes", "dgx_set_tableau",
            "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
            "dgx_status_string", "dgx_query", "dgx_profile_enable", "dgx_profile_read", "dgx_profile_reset",
-           "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc"]
+           "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc",
+           "dgx_stage_bytes"]
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -67,6 +68,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_ark_step_stages.argtypes = [vp, vp, dbl, vp, vp, vp]
     lib.dgx_ark_adjoint_step.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.dgx_rhs_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.dgx_stage_bytes.argtypes = [vp]
     lib.dgx_check.argtypes = [vp]
     lib.dgx_status_string.argtypes = [i32]
     lib.dgx_status_string.restype = ctypes.c_char_p
@@ -81,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
     lib.dgx_status_string.restype = ctypes.c_char_p
     lib.dgx_kernel_name.restype = ctypes.c_char_p
+    lib.dgx_stage_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -214,31 +217,57 @@ class Solver:
         return U64
 
     def stage_buffer(self) -> torch.Tensor:
-        """Device buffer for the stage checkpoints y_1..y_s of one step."""
-        if not self.stages:
+        """Device buffer for one step's stage checkpoints (dgx_stage_bytes)."""
+        nbytes = int(self.lib.dgx_stage_bytes(self.h))
+        if not nbytes:
             raise DGXError(7, "stage_buffer (no tableau)")
-        return torch.empty((self.stages,) + self.shape, dtype=self.dtype, device=self.device)
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        return raw[off:off + nbytes]
+
+    def stage_state(self, stages: torch.Tensor, i: int) -> torch.Tensor:
+        """View of the stage state y_{i+1} stored in a stage buffer."""
+        slot = stages.numel() // self.stages
+        nbytes = int(np.prod(self.shape)) * (8 if self.dtype == torch.float64 else 4)
+        return stages[slot * i: slot * i + nbytes].view(self.dtype).view(self.shape)
+
+    def _stages_ptr(self, stages):
+        if not (stages.is_cuda and stages.dtype == torch.uint8 and stages.is_contiguous()
+                and stages.numel() == int(self.lib.dgx_stage_bytes(self.h)) and stages.data_ptr() % 256 == 0):
+            raise ValueError("stages must come from stage_buffer()")
+        return ctypes.c_void_p(stages.data_ptr())
 
     def ark_step_stages(self, U64: torch.Tensor, dt: float, stages: torch.Tensor, stream=None) -> torch.Tensor:
-        if not (stages.is_cuda and stages.dtype == self.dtype and stages.is_contiguous()
-                and tuple(stages.shape) == (self.stages,) + self.shape):
-            raise ValueError("stages must come from stage_buffer()")
         ws = self.workspace(OP_ARK)
         _check(self.lib.dgx_ark_step_stages(self.h, self._state(U64, "U64", torch.float64), float(dt),
-                                            ctypes.c_void_p(stages.data_ptr()), self._aligned(ws),
-                                            _stream_ptr(stream)), "dgx_ark_step_stages")
+                                            self._stages_ptr(stages), self._aligned(ws), _stream_ptr(stream)),
+               "dgx_ark_step_stages")
         return U64
 
     def ark_adjoint_step(self, stages: torch.Tensor, lam64: torch.Tensor, dt: float, stream=None) -> torch.Tensor:
         """lam64: cotangent of U_{n+1} on entry, of U_n on exit (FP64, in place)."""
-        if not (stages.is_cuda and stages.dtype == self.dtype and stages.is_contiguous()
-                and tuple(stages.shape) == (self.stages,) + self.shape):
-            raise ValueError("stages must come from stage_buffer()")
         ws = self.workspace(OP_ARK_ADJOINT)
-        _check(self.lib.dgx_ark_adjoint_step(self.h, ctypes.c_void_p(stages.data_ptr()),
+        _check(self.lib.dgx_ark_adjoint_step(self.h, self._stages_ptr(stages),
                                              self._state(lam64, "lam64", torch.float64), float(dt),
                                              self._aligned(ws), _stream_ptr(stream)), "dgx_ark_adjoint_step")
         return lam64
+
+    def capture(self, fn, warmup: int = 2):
+        """Capture fn() -- any sequence of this library's calls on the current
+        stream, with fixed buffers and arguments -- into a CUDA graph.  The
+        workspaces must already exist (warm-up calls create them) and the
+        profiler must be off.  Returns a torch.cuda.CUDAGraph; replay() it."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                fn()
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
 
     def check(self):
         _check(self.lib.dgx_check(self.h), "dgx_check")
