@@ -50,46 +50,6 @@ def alu_peak_tflops(prec, sm_mhz=2032.0):
     return 1.25
 
 
-# ---------------------------------------------------------------------------
-# Algorithmic work per kernel launch (per element; s = bytes per scalar).
-# Bytes: each input read once and each output written once, as the kernel is
-# designed.  Flops: counted per node / face point from the operation list of
-# each kernel (FMA = 2 flops; a division or square root = 1).
-# ---------------------------------------------------------------------------
-def kernel_model(d, p, viscous, prec, stage_i=1, stages=4):
-    n = p + 1
-    N = n ** d
-    nf = d + 2
-    nfp = n ** (d - 1)
-    NF = 2 * d
-    s = 8 if prec == "fp64" else 4
-    state, face = nf * N, NF * nf * nfp
-    # pointwise flop counts
-    conv = 1 + 3 * d + 4 + d * (3 * d + 3)             # 1/rho, u, p, fluxes
-    visc = 1 + d + 2 + d * (6 + 4 * d) + d * d * 6 + d * (2 * d + 3)   # grads, tau, F^nu
-    llf = 2 * (1 + 4 * d + 6 + (3 * d + 4) + 3) + 2 + 3 * nf + (3 if d else 0)
-    m = {}
-    m["trace"] = {"bytes": state * 8 + state * s + face * s, "flops": face * 2 * n}
-    m["br1"] = {"bytes": state * s + 2 * face * s + d * state * s + face * s,
-                "flops": N * d * nf * 2 * n + N * d * nf * 6 + NF * nfp * nf * 3
-                + NF * nfp * (d * nf * 2 * n + visc)}
-    m["face"] = {"bytes": face * s * (2 + (1 if viscous else 0)),
-                 "flops": NF * nfp / 2 * (llf + (3 * nf if viscous else 0))}
-    stage_io = (2 + stage_i) * state * s + face * s
-    m["elem_stage"] = {"bytes": state * s + (d * state * s if viscous else 0) + face * s + stage_io,
-                       "flops": N * (conv + (visc + d * nf if viscous else 0) + d * nf * (2 * n + 6) + nf * 2 * (stage_i + 1))
-                       + face * 2 * n}
-    m["elem"] = {"bytes": state * s + (d * state * s if viscous else 0) + face * s + state * s,
-                 "flops": N * (conv + (visc + d * nf if viscous else 0) + d * nf * (2 * n + 6))}
-    # adjoint kernels (about 2-3x the forward pointwise work, same data movement pattern)
-    m["vjp_elem"] = {"bytes": 3 * state * s + (d * state * s if viscous else 0) + face * s,
-                     "flops": 2.5 * m["elem"]["flops"]}
-    m["vjp_face"] = {"bytes": 4 * face * s, "flops": 2.5 * m["face"]["flops"]}
-    m["vjp_br1"] = {"bytes": (3 + d) * state * s + 4 * face * s, "flops": 2.5 * m["br1"]["flops"]}
-    m["vjp_gather"] = {"bytes": 2 * state * s + 2 * face * s, "flops": face * 2 * n}
-    return m
-
-
 class ClockSampler:
     """SM clock and clock-event (throttle) reasons sampled every 2 ms while the
     timed region runs, through NVML (libnvidia-ml, read-only queries only)."""
@@ -261,38 +221,41 @@ def time_gpu(prec, steps, warmup, dt=1e-9):
     dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
     return {"ms": float(np.mean(gtimes)), "eager_ms": float(np.mean(times)), "ms_all": gtimes, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
             "evals_per_step": 8, "e2e_ms": float(np.mean(e2e)), "h2d": 2 * nbytes_state, "d2h": 2 * nbytes_state,
-            "mesh": mesh, "phys": phys, "steps": steps}
+            "mesh": mesh, "phys": phys, "steps": steps, "solver": s}
 
 
 def roofline(res, prec, pk):
-    mesh = res["mesh"]
-    model = kernel_model(mesh.dim, mesh.p, True, prec)
-    E = mesh.n_elem
-    best = None
-    for name, (launches, ms) in res["prof"].items():
-        if best is None or ms > best[2]:
-            best = (name, launches, ms)
-    name, launches, ms = best
+    """Roofline of the dominant kernel (largest summed device time): algorithmic
+    flops and bytes per launch from the library (dgx_kernel_work: counted
+    arithmetic, compulsory traffic) over the kernel's mean event-timed duration."""
+    s = res["solver"]
+    best = max(res["prof"].items(), key=lambda kv: kv[1][1])
+    name, (launches, ms) = best
     per_launch_s = ms / launches / 1e3
-    mdl = model[name]
-    bytes_l = mdl["bytes"] * E
-    flops_l = mdl["flops"] * E
+    flops_l, bytes_l = s.kernel_work(name)
     t_mem = bytes_l / (pk["hbm_gbs"] * 1e9)
     t_alu = flops_l / (alu_peak_tflops(prec) * 1e12)
-    shares = {k: round(v[1] / sum(x[1] for x in res["prof"].values()), 4) for k, v in res["prof"].items()}
+    total = sum(x[1] for x in res["prof"].values())
+    shares = {k: round(v[1] / total, 4) for k, v in res["prof"].items()}
+    per_kernel = {}
+    for k, (nl, kms) in res["prof"].items():
+        fl, by = s.kernel_work(k)
+        t = kms / nl / 1e3
+        per_kernel[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1), "TFLOP/s": round(fl / t / 1e12, 3)}
     if t_mem >= t_alu:
         ach = bytes_l / per_launch_s / 1e9
         out = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
-               "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": pk["source"]}
+               "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": pk["source"] + " (of measured copy bandwidth)"}
     else:
         ach = flops_l / per_launch_s / 1e12
         peak = alu_peak_tflops(prec)
         out = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-               "frac": round(ach / peak, 4), "peak_source": "derived (unit counts x 2032 MHz)" if prec == "fp32"
-               else "nominal B300 FP64"}
+               "frac": round(ach / peak, 4),
+               "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz" if prec == "fp32"
+               else "nominal B300 FP64 1.25 TFLOP/s"}
     out.update({"kernel": name, "launches": launches, "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "algorithmic_bytes": int(bytes_l), "algorithmic_flops": int(flops_l),
-                "traffic": None, "kernel_shares": shares})
+                "traffic": None, "kernel_shares": shares, "per_kernel": per_kernel})
     return out
 
 

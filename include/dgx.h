@@ -203,6 +203,52 @@ dgx_status dgx_profile_read(dgx_handle* h, int32_t kind, int64_t* launches, doub
 dgx_status dgx_profile_reset(dgx_handle* h);
 const char* dgx_kernel_name(int32_t kind);
 
+/* Algorithmic work of one launch of a kernel kind on this handle's mesh (for
+ * roofline reporting): flops counted from the implemented arithmetic (the
+ * pointwise physics is counted operation by operation, a fused multiply-add
+ * being two flops; contractions from their loop structure) and bytes of the
+ * kernel's compulsory traffic (each input read once, each output written once).
+ * The element-stage figures are averages over the stages of the tableau. */
+dgx_status dgx_kernel_work(const dgx_handle* h, int32_t kind, double* flops, double* bytes);
+
+/* Tile-size autotuner.  Tile kernels come in NVARIANTS = 3 variants of about
+ * 128 / 256 / 512 threads per CTA (tiles of max(1, threads / N) elements).
+ * dgx_autotune times every variant of every tile kernel (event profiler, reps
+ * timed repetitions of one ARK step and, when built, its adjoint, on a scratch
+ * copy of the device state U64) and keeps the fastest per kernel; variants
+ * whose shared memory exceeds the 227 KB per-CTA limit are skipped.  It is a
+ * set-up call: it allocates and frees its scratch and synchronises the stream.
+ * Requires a mesh and a tableau.  variants[] is indexed by dgx_kernel_kind. */
+dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream);
+dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants);
+dgx_status dgx_set_variants(dgx_handle* h, const int32_t* variants);
+
+/* Batched ensemble: many independent instances (meshes, degrees, physics)
+ * advanced together.  Instances are grouped by (dimension, degree, precision,
+ * physics, mesh kind); each group's meshes are concatenated into one internal
+ * handle, so every kernel launch covers all instances of a group and the
+ * tile variant is autotuned per group (per degree).  All instances must share
+ * the tableau.  The state of all instances is one packed FP64 buffer:
+ * instance i occupies doubles [offsets[i], offsets[i] + E_i nf_i N_i)
+ * (dgx_batch_layout, offsets has count + 1 entries).  Each instance has its own
+ * time step (dgx_batch_set_dt, host array of count doubles, uploaded once).
+ * The instance handles are only read by dgx_batch_create. */
+typedef struct dgx_batch dgx_batch;
+dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** out);
+dgx_status dgx_batch_destroy(dgx_batch* b);
+dgx_status dgx_batch_layout(const dgx_batch* b, int64_t* offsets, int32_t* groups);
+size_t dgx_batch_workspace_bytes(const dgx_batch* b);
+dgx_status dgx_batch_set_dt(dgx_batch* b, const double* dt);
+/* One explicit ARK step of every instance (enqueued kernel by kernel). */
+dgx_status dgx_batch_step(dgx_batch* b, double* U64, void* workspace, void* stream);
+/* The same step as one CUDA graph: captured (on a private stream) at the first
+ * call and whenever U64 or workspace change, then launched on the given
+ * stream; later dt changes need no recapture.  Make a dgx_batch_step or
+ * dgx_batch_autotune call first so kernel attributes are set outside capture. */
+dgx_status dgx_batch_step_graph(dgx_batch* b, double* U64, void* workspace, void* stream);
+/* Autotune every group on the packed state U64 (see dgx_autotune). */
+dgx_status dgx_batch_autotune(dgx_batch* b, const double* U64, int32_t reps, void* stream);
+
 /* Sizes the binding needs: element count, nodes per element, fields, face
  * points per face, the chosen element-tile size. */
 dgx_status dgx_query(const dgx_handle* h, int32_t* n_elem, int32_t* nodes, int32_t* fields,

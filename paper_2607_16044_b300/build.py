@@ -27,30 +27,32 @@ using Sc = {S};
 using O = Ops<{D}, {P}, Sc>;
 inline const Mesh<Sc>& m(const void* M) {{ return *(const Mesh<Sc>*)M; }}
 struct R {{
-  static cudaError_t trace(const void* M, const void* U, void* TU, cudaStream_t st) {{
-    return O::template trace<Sc>(m(M), (const Sc*)U, (Sc*)TU, nullptr, st);
+  static cudaError_t trace(const void* M, int V, const void* U, void* TU, cudaStream_t st) {{
+    return O::template trace<Sc>(m(M), V, (const Sc*)U, (Sc*)TU, nullptr, st);
   }}
-  static cudaError_t tr64(const void* M, const double* U, void* TU, void* sh, cudaStream_t st) {{
-    return O::template trace<double>(m(M), U, (Sc*)TU, (Sc*)sh, st);
+  static cudaError_t tr64(const void* M, int V, const double* U, void* TU, void* sh, cudaStream_t st) {{
+    return O::template trace<double>(m(M), V, U, (Sc*)TU, (Sc*)sh, st);
   }}
-  static cudaError_t br1(const void* M, bool c, const void* U, const Work& w, cudaStream_t st) {{
-    return O::br1(m(M), c, (const Sc*)U, w, st);
+  static cudaError_t br1(const void* M, int V, bool c, const void* U, const Work& w, cudaStream_t st) {{
+    return O::br1(m(M), V, c, (const Sc*)U, w, st);
   }}
   static cudaError_t face(const void* M, bool v, bool c, const Work& w, cudaStream_t st) {{
     return O::face(m(M), v, c, w, st);
   }}
-  static cudaError_t elem(const void* M, bool v, bool c, const void* U, const Work& w, void* out, cudaStream_t st) {{
+  static cudaError_t elem(const void* M, int V, bool v, bool c, const void* U, const Work& w, void* out,
+                          cudaStream_t st) {{
     Stage<Sc> none{{}};
-    return O::template elem<0>(m(M), v, c, (const Sc*)U, w, (Sc*)out, none, st);
+    return O::template elem<0>(m(M), V, v, c, (const Sc*)U, w, (Sc*)out, none, st);
   }}
-  static cudaError_t elem_stage(const void* M, bool v, bool c, const void* U, const Work& w, const void* sa,
+  static cudaError_t elem_stage(const void* M, int V, bool v, bool c, const void* U, const Work& w, const void* sa,
                                 cudaStream_t st) {{
-    return O::template elem<1>(m(M), v, c, (const Sc*)U, w, nullptr, *(const Stage<Sc>*)sa, st);
+    return O::template elem<1>(m(M), V, v, c, (const Sc*)U, w, nullptr, *(const Stage<Sc>*)sa, st);
   }}
+  static size_t smem(int kind, int V) {{ return O::smem(kind, V); }}
 }};
 }}  // namespace
 const Table* table_d{D}_{T}_p{P}() {{
-  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, {VJP_PTR}}};
+  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::smem, {VJP_PTR}}};
   return &t;
 }}
 }}  // namespace dgx

@@ -10,15 +10,18 @@
 namespace dgx {
 
 struct Table {
-  // Individual kernel launches (the host composes residuals, stages and adjoints).
-  cudaError_t (*trace)(const void* M, const void* U, void* TU, cudaStream_t st);
-  cudaError_t (*trace_from64)(const void* M, const double* U, void* TU, void* shadow, cudaStream_t st);
-  cudaError_t (*br1)(const void* M, bool curv, const void* U, const Work& w, cudaStream_t st);
+  // Individual kernel launches (the host composes residuals, stages and
+  // adjoints); V selects the tile variant of tile kernels.
+  cudaError_t (*trace)(const void* M, int V, const void* U, void* TU, cudaStream_t st);
+  cudaError_t (*trace_from64)(const void* M, int V, const double* U, void* TU, void* shadow, cudaStream_t st);
+  cudaError_t (*br1)(const void* M, int V, bool curv, const void* U, const Work& w, cudaStream_t st);
   cudaError_t (*face)(const void* M, bool visc, bool curv, const Work& w, cudaStream_t st);
-  cudaError_t (*elem)(const void* M, bool visc, bool curv, const void* U, const Work& w, void* out, cudaStream_t st);
-  cudaError_t (*elem_stage)(const void* M, bool visc, bool curv, const void* U, const Work& w, const void* stage,
-                            cudaStream_t st);
-  const void* vjp;  // adjoint launch table (VjpTable) or nullptr
+  cudaError_t (*elem)(const void* M, int V, bool visc, bool curv, const void* U, const Work& w, void* out,
+                      cudaStream_t st);
+  cudaError_t (*elem_stage)(const void* M, int V, bool visc, bool curv, const void* U, const Work& w,
+                            const void* stage, cudaStream_t st);
+  size_t (*smem)(int kind, int V);  // tile kernels: 0 trace, 1 br1, 2 elem
+  const void* vjp;                   // adjoint launch table (VjpTable) or nullptr
 };
 
 // Defined in the generated units: table for (D, P, S) or nullptr.

@@ -9,11 +9,13 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
 #include "../../include/dgx.h"
 #include "dispatch.h"
+#include "flops.h"
 #include "vjp.cuh"
 
 using dgx::Tab;
@@ -40,6 +42,8 @@ struct dgx_handle {
   void* d_SnF = nullptr;
   dgx::Mesh<double> mesh64{};   // device views passed to the launch table
   dgx::Mesh<float> mesh32{};
+  // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
+  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
   // per-kernel event profiler (tracing)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -47,6 +51,10 @@ struct dgx_handle {
   std::vector<int> ev_kind;
   int64_t prof_launches[DGX_KERNEL_KINDS] = {};
   double prof_ms[DGX_KERNEL_KINDS] = {};
+  // host copies of the mesh description (the batch runtime concatenates them)
+  std::vector<int> h_nb;
+  std::vector<int8_t> h_nbf, h_ori;
+  std::vector<double> h_lo, h_size, h_xyz;
   // tableau
   int stages = 0;
   double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
@@ -221,6 +229,9 @@ dgx_status upload_connectivity(dgx_handle* h, const int32_t* nb, const int8_t* n
   const size_t m = (size_t)h->E * h->NF;
   std::vector<int> vnb(nb, nb + m);
   std::vector<int8_t> vnbf(nbf, nbf + m), vori(ori, ori + m);
+  h->h_nb = vnb;
+  h->h_nbf = vnbf;
+  h->h_ori = vori;
   dgx_status s;
   if ((s = upload(vnb, (void**)&h->d_nb)) != DGX_OK) return s;
   if ((s = upload(vnbf, (void**)&h->d_nbf)) != DGX_OK) return s;
@@ -386,23 +397,24 @@ cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, cons
   dgx::Work w{vw.TU, vw.FFb, vw.G, vw.Q};
   cudaError_t err = cudaSuccess;
   if (!have_forward) {  // recompute the forward traces and BR1 gradient
-    err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
+    err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, h->var[DGX_K_TRACE], U, w.TU, st); });
     if (err == cudaSuccess && h->viscous)
-      err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+      err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, U, w, st); });
   }
   if (err == cudaSuccess)
-    err = launch(h, DGX_K_VJP_ELEM, st, [&] { return v->elem(M, h->viscous, h->curv, U, vw, &cot, g, st); });
+    err = launch(h, DGX_K_VJP_ELEM, st, [&] { return v->elem(M, h->var[DGX_K_VJP_ELEM], h->viscous, h->curv, U, vw, &cot, g, st); });
   if (err == cudaSuccess)
     err = launch(h, DGX_K_VJP_FACE, st, [&] { return v->face(M, h->viscous, h->curv, vw, st); });
   if (err == cudaSuccess && h->viscous)
-    err = launch(h, DGX_K_VJP_BR1, st, [&] { return v->br1(M, h->curv, vw, g, st); });
+    err = launch(h, DGX_K_VJP_BR1, st, [&] { return v->br1(M, h->var[DGX_K_VJP_BR1], h->curv, vw, g, st); });
   if (err == cudaSuccess)
-    err = launch(h, DGX_K_VJP_GATHER, st, [&] { return v->gather(M, h->viscous, vw, g, &fin, st); });
+    err = launch(h, DGX_K_VJP_GATHER, st, [&] { return v->gather(M, h->var[DGX_K_VJP_GATHER], h->viscous, vw, g, &fin, st); });
   return err;
 }
 
 template <typename S>
-dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st) {
+dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st,
+                    const double* dte = nullptr) {
   const Layout L = layout(h, DGX_OP_ARK);
   const dgx::Work w = work_at(h, workspace, L);
   char* base = (char*)workspace;
@@ -420,7 +432,7 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   cudaError_t err =
-      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, U64, w0.TU, first, st); });
+      launch(h, DGX_K_TRACE, st, [&] { return t->trace_from64(M, h->var[DGX_K_TRACE], U64, w0.TU, first, st); });
   if (err != cudaSuccess) return DGX_ECUDA;
   const S* y0 = (h->fp64 && !ck) ? (const S*)U64 : first;
   const int s = h->stages;
@@ -430,8 +442,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     sa.i = i;
     sa.last = (i == s - 1);
     if (!sa.last)
-      for (int j = 0; j <= i; ++j) sa.ca[j] = (S)(dt * h->A[(i + 1) * dgx::MAXSTAGES + j]);
-    for (int j = 0; j < s; ++j) sa.cb[j] = dt * h->b[j];
+      for (int j = 0; j <= i; ++j) sa.ca[j] = h->A[(i + 1) * dgx::MAXSTAGES + j];
+    for (int j = 0; j < s; ++j) sa.cb[j] = h->b[j];
+    sa.dt = dt;
+    sa.dte = dte;
     sa.base = y0;
     sa.Un = U64;
     sa.Y = (ck && !sa.last) ? slot_y(i + 1) : Y;
@@ -444,10 +458,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     }
     sa.TU = (S*)((ck && !sa.last) ? slot_tu(i + 1) : w.TU);
     const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
-    if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, Uin, wi, st); });
+    if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, Uin, wi, st); });
     if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, wi, st); });
     if (err == cudaSuccess)
-      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->viscous, h->curv, Uin, wi, &sa, st); });
+      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, &sa, st); });
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -490,7 +504,150 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
   return DGX_OK;
 }
 
+// ------------------------------------------------------------ work model
+struct Pointwise {
+  double conv, visc, visc_n, wall_visc, llf_unit, llf_area, conv_vjp, visc_vjp, visc_n_vjp, llf_unit_vjp,
+      llf_area_vjp;
+};
+
+template <int D>
+Pointwise count_pointwise() {
+  using C = dgx::Count;
+  dgx::Gas<C> g;
+  g.gamma = 1.4;
+  g.gm1 = 0.4;
+  g.mu = 1e-3;
+  g.lam = -2e-3 / 3;
+  g.kcv = 2e-3;
+  C U[D + 2], V[D + 2], Q[D][D + 2], nv[D], F[D][D + 2], G[D + 2], Ub[D + 2], Vb[D + 2], Qb[D][D + 2];
+  for (int f = 0; f < D + 2; ++f) {
+    U[f] = 1.0 + 0.1 * f;
+    V[f] = 1.05 + 0.09 * f;
+    G[f] = 0.3 - 0.05 * f;
+    Ub[f] = Vb[f] = 0.0;
+    for (int a = 0; a < D; ++a) {
+      Q[a][f] = 0.2 * (a + 1) - 0.03 * f;
+      Qb[a][f] = 0.0;
+      F[a][f] = 0.1 * (a - f);
+    }
+  }
+  U[D + 1] = V[D + 1] = 3.0;
+  for (int a = 0; a < D; ++a) nv[a] = 0.3 + 0.2 * a;
+  Pointwise pc{};
+  auto cnt = [](auto&& fn) {
+    dgx::Count::ops = 0;
+    fn();
+    return (double)dgx::Count::ops;
+  };
+  C Fo[D][D + 2], Go[D + 2];
+  pc.conv = cnt([&] { dgx::conv_flux_all<D, C>(U, g, Fo); });
+  pc.visc = cnt([&] { dgx::visc_flux_all<D, C>(U, Q, g, Fo); });
+  pc.visc_n = cnt([&] { dgx::visc_flux_normal<D, C>(U, Q, nv, g, Go); });
+  pc.wall_visc = cnt([&] { dgx::wall_visc_flux<D, C>(U, Q, nv, g, Go); });
+  pc.llf_unit = cnt([&] { dgx::llf_flux<D, C, true>(U, V, nv, g, Go); });
+  pc.llf_area = cnt([&] { dgx::llf_flux<D, C, false>(U, V, nv, g, Go); });
+  pc.conv_vjp = cnt([&] { dgx::conv_flux_all_vjp<D, C>(U, F, g, Ub); });
+  pc.visc_vjp = cnt([&] { dgx::visc_flux_all_vjp<D, C>(U, Q, F, g, Ub, Qb); });
+  pc.visc_n_vjp = cnt([&] { dgx::visc_flux_normal_vjp<D, C>(U, Q, nv, G, g, Ub, Qb); });
+  pc.llf_unit_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, true>(U, V, nv, G, g, Ub, Vb); });
+  pc.llf_area_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, false>(U, V, nv, G, g, Ub, Vb); });
+  return pc;
+}
+
+// Algorithmic flops and bytes of one launch of a kernel kind on this handle.
+void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
+  const Pointwise pc = h->d == 2 ? count_pointwise<2>() : count_pointwise<3>();
+  const double E = h->E, N = h->N, nf = h->nf, nfp = h->nfp, NF = h->NF, D = h->d, n = h->n, s = (double)h->s;
+  const double STATE = nf * N, FACE = NF * nf * nfp, F = h->nFaces;
+  const bool v = h->viscous, c = h->curv;
+  const double geo_node = c ? (D * D * N + N) * s : D * s;  // per element
+  const double geo_face = c ? NF * D * nfp * s : 0.0;
+  const int st = h->stages > 0 ? h->stages : 1;
+  flops = bytes = 0.0;
+  switch (kind) {
+    case DGX_K_TRACE:
+      flops = E * FACE * 2 * n;
+      bytes = E * (STATE + FACE) * s;
+      break;
+    case DGX_K_BR1:
+      flops = E * (NF * nfp * nf * 2 + N * D * nf * 2 * n + N * D * nf * (c ? (8 * D + 1) : 5) +
+                   NF * nfp * D * nf * 2 * n + NF * nfp * pc.visc_n);
+      bytes = E * ((STATE + 2 * FACE + D * STATE + FACE) * s + geo_node + geo_face);
+      break;
+    case DGX_K_FACE:
+      flops = F * nfp * ((c ? pc.llf_area : pc.llf_unit) + (v ? 3 * nf : 0));
+      bytes = E * FACE * s * (2 + (v ? 1 : 0)) + (c ? F * D * nfp * s : 0.0);
+      break;
+    case DGX_K_ELEM:
+    case DGX_K_ELEM_STAGE: {
+      flops = E * N * (pc.conv + (v ? pc.visc + D * nf : 0) + (c ? D * nf * (2 * D - 1) + nf : 0) +
+                       D * nf * (2 * n + 6));
+      bytes = E * ((STATE + (v ? D * STATE : 0) + FACE + (kind == DGX_K_ELEM ? STATE : 0)) * s + geo_node);
+      if (kind == DGX_K_ELEM_STAGE) {  // averaged over the stages of the tableau
+        double fl = 0, by = 0;
+        for (int i = 0; i < st; ++i) {
+          fl += E * STATE * 2 * (i + 1) + E * FACE * 2 * n;
+          const bool last = i == st - 1;
+          by += E * ((1 + i) * STATE * s + (last ? 16 * STATE : 2 * STATE * s) + FACE * s);
+        }
+        flops += fl / st;
+        bytes += by / st;
+      }
+      break;
+    }
+    case DGX_K_VJP_ELEM:
+      flops = E * (STATE * 2 * 2 + FACE * 2 * n + N * D * nf * 2 * n + N * (pc.conv_vjp + (v ? pc.visc_vjp : 0)) +
+                   (c ? N * D * D * nf * 2 + STATE : 0));
+      bytes = E * ((2 * STATE + STATE + (v ? 2 * D * STATE : 0) + FACE + STATE) * s + geo_node);
+      break;
+    case DGX_K_VJP_FACE:
+      flops = F * nfp * (nf + (c ? pc.llf_area_vjp : pc.llf_unit_vjp) + (v ? 2 * nf : 0));
+      bytes = E * FACE * s * (3 + (v ? 1 : 0)) + (c ? F * D * nfp * s : 0.0);
+      break;
+    case DGX_K_VJP_BR1:
+      flops = E * (NF * nfp * (D * nf * 2 * n + pc.visc_n_vjp) + N * D * nf * 4 * D + N * D * nf * (c ? 2 * D : 1) +
+                   N * nf * D * 2 * n + NF * nfp * nf * (c ? D * (2 * n + 2) : 2 * n + 1) + NF * nfp * nf * 2);
+      bytes = E * ((5 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);
+      break;
+    case DGX_K_VJP_GATHER:
+      flops = E * ((v ? FACE * 2 : 0) + STATE * 4 * D);
+      bytes = E * ((FACE + (v ? FACE : 0) + 2 * STATE) * s);
+      break;
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------ autotuning
+bool is_tile_kind(int k) { return k != DGX_K_FACE && k != DGX_K_VJP_FACE; }
+
+size_t tile_smem(const dgx_handle* h, int kind, int V) {
+  const dgx::Table* t = h->tab;
+  const dgx::VjpTable* v = (const dgx::VjpTable*)t->vjp;
+  switch (kind) {
+    case DGX_K_TRACE: return t->smem(0, V);
+    case DGX_K_BR1: return t->smem(1, V);
+    case DGX_K_ELEM:
+    case DGX_K_ELEM_STAGE: return t->smem(2, V);
+    case DGX_K_VJP_ELEM: return v ? v->smem(0, V) : 0;
+    case DGX_K_VJP_BR1: return v ? v->smem(1, V) : 0;
+    case DGX_K_VJP_GATHER: return v ? v->smem(2, V) : 0;
+    default: return 0;
+  }
+}
+
+template <typename T>
+struct DevBuf {  // scratch owned by a set-up call
+  T* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  bool alloc(size_t bytes) { return cudaMalloc((void**)&p, bytes ? bytes : 1) == cudaSuccess; }
+};
+
 }  // namespace
+
+int64_t dgx::Count::ops = 0;
 
 extern "C" {
 
@@ -517,6 +674,15 @@ dgx_status dgx_profile_read(dgx_handle* h, int32_t kind, int64_t* launches, doub
   profile_collect(h);
   if (launches) *launches = h->prof_launches[kind];
   if (ms) *ms = h->prof_ms[kind];
+  return DGX_OK;
+}
+
+dgx_status dgx_kernel_work(const dgx_handle* h, int32_t kind, double* flops, double* bytes) {
+  if (!h || kind < 0 || kind >= DGX_KERNEL_KINDS || !h->has_mesh) return DGX_EINVAL;
+  double f = 0, b = 0;
+  kernel_work(h, kind, f, b);
+  if (flops) *flops = f;
+  if (bytes) *bytes = b;
   return DGX_OK;
 }
 
@@ -629,6 +795,9 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   for (size_t i = 0; i < rh.size(); ++i) rh[i] = 2.0 / size[i];
   if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
   if ((st = upload_real(h, rh, &h->d_rh)) != DGX_OK) return st;
+  h->h_lo.assign(lo, lo + (size_t)E * d);
+  h->h_size.assign(size, size + (size_t)E * d);
+  h->h_xyz.clear();
   h->curv = false;
   h->has_mesh = true;
   h->mesh64 = mesh_view<double>(h);
@@ -725,6 +894,9 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
   if ((st = upload_real(h, iJ, &h->d_iJ)) != DGX_OK) return st;
   if ((st = upload_real(h, SnE, &h->d_SnE)) != DGX_OK) return st;
   if ((st = upload_real(h, SnF, &h->d_SnF)) != DGX_OK) return st;
+  h->h_xyz.assign(xyz, xyz + (size_t)E * d * N);
+  h->h_lo.clear();
+  h->h_size.clear();
   h->curv = true;
   h->has_mesh = true;
   h->mesh64 = mesh_view<double>(h);
@@ -769,12 +941,12 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
   cudaStream_t st = (cudaStream_t)stream;
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
-  cudaError_t err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, U, w.TU, st); });
+  cudaError_t err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, h->var[DGX_K_TRACE], U, w.TU, st); });
   if (err == cudaSuccess && h->viscous)
-    err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->curv, U, w, st); });
+    err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, U, w, st); });
   if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
   if (err == cudaSuccess)
-    err = launch(h, DGX_K_ELEM, st, [&] { return t->elem(M, h->viscous, h->curv, U, w, dUdt, st); });
+    err = launch(h, DGX_K_ELEM, st, [&] { return t->elem(M, h->var[DGX_K_ELEM], h->viscous, h->curv, U, w, dUdt, st); });
   return cuda_status(err);
 }
 
@@ -833,6 +1005,305 @@ dgx_status dgx_check(dgx_handle* h) {
   if (cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) return DGX_ECUDA;
   if (flags & 1u) return DGX_ENONFINITE;
   if (flags & 2u) return DGX_ETIMEOUT;
+  return DGX_OK;
+}
+
+dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream) {
+  if (!h || !U64 || reps < 1) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t state64 = (size_t)h->E * h->nf * h->N * 8;
+  const bool adj = h->tab->vjp != nullptr;
+  DevBuf<double> U, lam;
+  DevBuf<char> stages, ws_ark, ws_adj;
+  if (!U.alloc(state64) || !lam.alloc(state64) || !stages.alloc(dgx_stage_bytes(h) + 256) ||
+      !ws_ark.alloc(dgx_workspace_bytes(h, DGX_OP_ARK) + 256) ||
+      (adj && !ws_adj.alloc(dgx_workspace_bytes(h, DGX_OP_ARK_ADJOINT) + 256)))
+    return DGX_ENOMEM;
+  auto al = [](char* p) { return (void*)(((uintptr_t)p + 255) & ~(uintptr_t)255); };
+  const bool was_prof = h->prof;
+  dgx_status s = dgx_profile_enable(h, 1);
+  if (s != DGX_OK) return s;
+  const double dt = 1e-12;
+  double best[DGX_KERNEL_KINDS];
+  int choice[DGX_KERNEL_KINDS];
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+    best[k] = 1e300;
+    choice[k] = h->var[k];
+  }
+  for (int V = 0; V < dgx::NVARIANTS; ++V) {
+    bool valid[DGX_KERNEL_KINDS] = {};
+    for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+      if (!is_tile_kind(k)) continue;
+      valid[k] = tile_smem(h, k, V) <= dgx::SMEM_LIMIT;
+      h->var[k] = valid[k] ? V : choice[k];
+    }
+    for (int rep = -1; rep < reps; ++rep) {  // rep -1: warm-up
+      if (rep == 0) dgx_profile_reset(h);
+      if (cudaMemcpyAsync(U.p, U64, state64, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DGX_ECUDA;
+      if (cudaMemsetAsync(lam.p, 0, state64, st) != cudaSuccess) return DGX_ECUDA;
+      s = dgx_ark_step_stages(h, U.p, dt, al(stages.p), al(ws_ark.p), stream);
+      if (s == DGX_OK && adj) s = dgx_ark_adjoint_step(h, al(stages.p), lam.p, dt, al(ws_adj.p), stream);
+      if (s != DGX_OK) {
+        dgx_profile_enable(h, was_prof);
+        return s;
+      }
+    }
+    for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+      int64_t n = 0;
+      double ms = 0;
+      dgx_profile_read(h, k, &n, &ms);
+      if (valid[k] && n > 0 && ms / n < best[k]) {
+        best[k] = ms / n;
+        choice[k] = V;
+      }
+    }
+  }
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) h->var[k] = choice[k];
+  dgx_profile_reset(h);
+  dgx_profile_enable(h, was_prof);
+  return cudaStreamSynchronize(st) == cudaSuccess ? DGX_OK : DGX_ECUDA;
+}
+
+dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants) {
+  if (!h || !variants) return DGX_EINVAL;
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) variants[k] = h->var[k];
+  return DGX_OK;
+}
+
+dgx_status dgx_set_variants(dgx_handle* h, const int32_t* variants) {
+  if (!h || !variants) return DGX_EINVAL;
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+    if (variants[k] < 0 || variants[k] >= dgx::NVARIANTS) return DGX_EINVAL;
+    if (is_tile_kind(k) && h->has_mesh && tile_smem(h, k, variants[k]) > dgx::SMEM_LIMIT) return DGX_EINVAL;
+  }
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) h->var[k] = variants[k];
+  return DGX_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== batched runtime
+struct dgx_batch {
+  struct Group {
+    dgx_handle* h = nullptr;
+    int64_t off = 0;                 // offset (doubles) of the group in the packed state
+    std::vector<int> members;        // instance indices
+    std::vector<int64_t> elem_off;   // element offset of each member inside the group
+    double* d_dte = nullptr;         // per-element time step
+  };
+  int count = 0;
+  std::vector<int64_t> offset;       // per instance (doubles), offset[count] = total
+  std::vector<Group> groups;
+  std::vector<double> dt;
+  bool dt_set = false;
+  size_t ws_bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double* g_U = nullptr;
+  void* g_ws = nullptr;
+};
+
+namespace {
+bool same_group(const dgx_handle* a, const dgx_handle* b) {
+  return a->d == b->d && a->p == b->p && a->fp64 == b->fp64 && a->viscous == b->viscous && a->curv == b->curv &&
+         a->desc.gamma == b->desc.gamma && (!a->viscous || (a->desc.Re == b->desc.Re && a->desc.Pr == b->desc.Pr));
+}
+
+void batch_free(dgx_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (auto& g : b->groups) {
+    if (g.d_dte) cudaFree(g.d_dte);
+    if (g.h) dgx_destroy(g.h);
+  }
+  delete b;
+}
+
+dgx_status batch_run(dgx_batch* b, double* U64, void* ws, cudaStream_t st) {
+  for (auto& g : b->groups) {
+    dgx_handle* h = g.h;
+    const dgx_status s = h->fp64 ? ark_impl<double>(h, U64 + g.off, 0.0, nullptr, ws, st, g.d_dte)
+                                 : ark_impl<float>(h, U64 + g.off, 0.0, nullptr, ws, st, g.d_dte);
+    if (s != DGX_OK) return s;
+  }
+  return DGX_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** out) {
+  if (!out) return DGX_EINVAL;
+  *out = nullptr;
+  if (!inst || count < 1) return DGX_EINVAL;
+  const dgx_handle* h0 = inst[0];
+  for (int i = 0; i < count; ++i) {
+    const dgx_handle* h = inst[i];
+    if (!h) return DGX_EINVAL;
+    if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+    if (h->stages != h0->stages) return DGX_EINVAL;
+    for (int r = 0; r < dgx::MAXSTAGES * dgx::MAXSTAGES; ++r)
+      if (h->A[r] != h0->A[r]) return DGX_EINVAL;
+    for (int j = 0; j < h->stages; ++j)
+      if (h->b[j] != h0->b[j] || h->c[j] != h0->c[j]) return DGX_EINVAL;
+  }
+  dgx_batch* b = new (std::nothrow) dgx_batch();
+  if (!b) return DGX_ENOMEM;
+  b->count = count;
+  b->dt.assign(count, 0.0);
+  std::vector<int> group_of(count, -1);
+  std::vector<const dgx_handle*> rep;
+  for (int i = 0; i < count; ++i) {
+    int g = -1;
+    for (size_t k = 0; k < rep.size(); ++k)
+      if (same_group(rep[k], inst[i])) g = (int)k;
+    if (g < 0) {
+      g = (int)rep.size();
+      rep.push_back(inst[i]);
+      b->groups.emplace_back();
+    }
+    group_of[i] = g;
+    b->groups[g].members.push_back(i);
+  }
+  b->offset.assign(count + 1, 0);
+  int64_t off = 0;
+  dgx_status st = DGX_OK;
+  for (auto& g : b->groups) {
+    const dgx_handle* r = inst[g.members[0]];
+    const int d = r->d, NF = r->NF, N = r->N, nf = r->nf;
+    int64_t E = 0;
+    for (int i : g.members) {
+      g.elem_off.push_back(E);
+      E += inst[i]->E;
+    }
+    dgx_problem_desc desc = r->desc;
+    desc.n_elem = (int32_t)E;
+    if ((st = dgx_create(&desc, &g.h)) != DGX_OK) break;
+    std::vector<int32_t> nb;
+    std::vector<int8_t> nbf, ori;
+    std::vector<double> lo, size, xyz;
+    for (size_t m = 0; m < g.members.size(); ++m) {
+      const dgx_handle* h = inst[g.members[m]];
+      for (int x : h->h_nb) nb.push_back(x >= 0 ? (int32_t)(x + g.elem_off[m]) : x);
+      nbf.insert(nbf.end(), h->h_nbf.begin(), h->h_nbf.end());
+      ori.insert(ori.end(), h->h_ori.begin(), h->h_ori.end());
+      lo.insert(lo.end(), h->h_lo.begin(), h->h_lo.end());
+      size.insert(size.end(), h->h_size.begin(), h->h_size.end());
+      xyz.insert(xyz.end(), h->h_xyz.begin(), h->h_xyz.end());
+    }
+    (void)NF;
+    (void)d;
+    st = r->curv ? dgx_set_mesh_nodes(g.h, xyz.data(), nb.data(), nbf.data(), ori.data())
+                 : dgx_set_mesh_boxes(g.h, lo.data(), size.data(), nb.data(), nbf.data(), ori.data());
+    if (st != DGX_OK) break;
+    std::vector<double> A(r->stages * r->stages);
+    for (int i = 0; i < r->stages; ++i)
+      for (int j = 0; j < r->stages; ++j) A[i * r->stages + j] = r->A[i * dgx::MAXSTAGES + j];
+    if ((st = dgx_set_tableau(g.h, r->stages, A.data(), r->b, r->c)) != DGX_OK) break;
+    for (int k = 0; k < DGX_KERNEL_KINDS; ++k) g.h->var[k] = r->var[k];
+    if (cudaMalloc((void**)&g.d_dte, (size_t)E * sizeof(double)) != cudaSuccess) {
+      st = DGX_ENOMEM;
+      break;
+    }
+    if (cudaMemset(g.d_dte, 0, (size_t)E * sizeof(double)) != cudaSuccess) {
+      st = DGX_ECUDA;
+      break;
+    }
+    g.off = off;
+    for (size_t m = 0; m < g.members.size(); ++m) b->offset[g.members[m]] = off + g.elem_off[m] * nf * N;
+    off += E * nf * N;
+    b->ws_bytes = std::max(b->ws_bytes, dgx_workspace_bytes(g.h, DGX_OP_ARK));
+  }
+  b->offset[count] = off;
+  if (st == DGX_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = DGX_ECUDA;
+  if (st != DGX_OK) {
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return DGX_OK;
+}
+
+dgx_status dgx_batch_destroy(dgx_batch* b) {
+  if (!b) return DGX_EINVAL;
+  batch_free(b);
+  return DGX_OK;
+}
+
+dgx_status dgx_batch_layout(const dgx_batch* b, int64_t* offsets, int32_t* groups) {
+  if (!b) return DGX_EINVAL;
+  if (offsets)
+    for (int i = 0; i <= b->count; ++i) offsets[i] = b->offset[i];
+  if (groups) *groups = (int32_t)b->groups.size();
+  return DGX_OK;
+}
+
+size_t dgx_batch_workspace_bytes(const dgx_batch* b) { return b ? b->ws_bytes : 0; }
+
+dgx_status dgx_batch_set_dt(dgx_batch* b, const double* dt) {
+  if (!b || !dt) return DGX_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (!std::isfinite(dt[i])) return DGX_EINVAL;
+  for (auto& g : b->groups) {
+    std::vector<double> dte((size_t)g.h->E);
+    for (size_t m = 0; m < g.members.size(); ++m) {
+      const int64_t e0 = g.elem_off[m];
+      const int64_t e1 = (m + 1 < g.members.size()) ? g.elem_off[m + 1] : g.h->E;
+      for (int64_t e = e0; e < e1; ++e) dte[e] = dt[g.members[m]];
+    }
+    if (cudaMemcpy(g.d_dte, dte.data(), dte.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      return DGX_ECUDA;
+  }
+  for (int i = 0; i < b->count; ++i) b->dt[i] = dt[i];
+  b->dt_set = true;
+  return DGX_OK;
+}
+
+dgx_status dgx_batch_step(dgx_batch* b, double* U64, void* workspace, void* stream) {
+  if (!b || !U64 || !workspace || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (!b->dt_set) return DGX_ESTATE;
+  return batch_run(b, U64, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_batch_step_graph(dgx_batch* b, double* U64, void* workspace, void* stream) {
+  if (!b || !U64 || !workspace || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (!b->dt_set) return DGX_ESTATE;
+  if (!b->exec || b->g_U != U64 || b->g_ws != workspace) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return DGX_ECUDA;
+    const dgx_status s = batch_run(b, U64, workspace, b->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (s != DGX_OK || e != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return s != DGX_OK ? s : DGX_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      b->exec = nullptr;
+      return DGX_ECUDA;
+    }
+    b->g_U = U64;
+    b->g_ws = workspace;
+  }
+  return cudaGraphLaunch(b->exec, (cudaStream_t)stream) == cudaSuccess ? DGX_OK : DGX_ECUDA;
+}
+
+dgx_status dgx_batch_autotune(dgx_batch* b, const double* U64, int32_t reps, void* stream) {
+  if (!b || !U64) return DGX_EINVAL;
+  for (auto& g : b->groups) {
+    const dgx_status s = dgx_autotune(g.h, U64 + g.off, reps, stream);
+    if (s != DGX_OK) return s;
+  }
+  if (b->exec) {  // variants changed: capture again on the next graph step
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
   return DGX_OK;
 }
 

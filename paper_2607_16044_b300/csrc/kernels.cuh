@@ -26,14 +26,19 @@ namespace dgx {
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
-template <int D, int P>
+// Tile variants (chosen per kernel by the autotuner): about 128, 256 or 512
+// threads per CTA, i.e. T = max(1, 64 * 2^(V+1) / N) elements per tile.
+constexpr int NVARIANTS = 3;
+constexpr int variant_threads(int V) { return 64 << (V + 1); }
+
+template <int D, int P, int V = 1>
 struct Sh {
   static constexpr int n = P + 1;
   static constexpr int N = ipow(n, D);
   static constexpr int nf = D + 2;
   static constexpr int nfp = ipow(n, D - 1);
   static constexpr int NF = 2 * D;
-  static constexpr int T = (256 / N) > 0 ? (256 / N) : 1;
+  static constexpr int T = (variant_threads(V) / N) > 0 ? (variant_threads(V) / N) : 1;
   static constexpr int THREADS = ((T * N + 31) / 32) * 32;
   static constexpr int FACE = NF * nf * nfp;  // face values per element
   static constexpr int STATE = nf * N;        // state values per element
@@ -97,8 +102,10 @@ constexpr int MAXSTAGES = 8;
 template <typename S>
 struct Stage {
   const S* k[MAXSTAGES];   // k_0 .. k_{i-1}
-  S ca[MAXSTAGES];         // dt * a_{i+1, j}, j <= i
-  double cb[MAXSTAGES];    // dt * b_j (last stage)
+  double ca[MAXSTAGES];    // a_{i+1, j}, j <= i
+  double cb[MAXSTAGES];    // b_j (last stage)
+  double dt;               // time step, unless dte is given
+  const double* dte;       // per-element time step (batched instances) or nullptr
   int i;                   // this stage (0-based)
   int last;
   const S* base;           // y = base + sum ca_j k_j (FP64: U_n itself, FP32: fl32(U_n))
@@ -127,9 +134,9 @@ __device__ __forceinline__ void load_tab(const Tab<S>* tabs, int P, S* sD, S* sD
 }
 
 // Traces of a staged tile (us[t][f][q]) written in output order (coalesced).
-template <int D, int P, typename S>
+template <int D, int P, typename S, int V>
 __device__ __forceinline__ void tile_traces(const S* us, const S* lm, const S* lp, int nel, S* dst) {
-  using H = Sh<D, P>;
+  using H = Sh<D, P, V>;
   const int tot = nel * H::FACE;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int fp = i % H::nfp;
@@ -152,10 +159,11 @@ __device__ __forceinline__ void tile_traces(const S* us, const S* lm, const S* l
 // k_trace: TU = traces of U (input may be double while S is float: the FP32
 // ARK path converts the FP64 master state here and keeps the rounded copy).
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, typename Sin>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_trace(int E, const Sin* __restrict__ U, S* __restrict__ TU,
-                                                             S* __restrict__ shadow, const Tab<S>* tabs) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, typename Sin, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin* __restrict__ U,
+                                                                S* __restrict__ TU, S* __restrict__ shadow,
+                                                                const Tab<S>* tabs) {
+  using H = Sh<D, P, V>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(smem_raw);
   S* lm = us + H::T * H::STATE;
@@ -171,7 +179,7 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_trace(int E, const Sin* _
   }
   load_tab<S>(tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, H::n);
   __syncthreads();
-  tile_traces<D, P, S>(us, lm, lp, nel, TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, V>(us, lm, lp, nel, TU + (size_t)e0 * H::FACE);
 }
 
 // ---------------------------------------------------------------------------
@@ -181,11 +189,11 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_trace(int E, const Sin* _
 // viscous normal flux G = F^nu(U_f, Q_f) . n (wall: adiabatic wall flux).
 // Boxes use unit normals (the element kernel applies 2/h_a).
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool CURV>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
-                                                           const S* __restrict__ TU, S* __restrict__ Q,
-                                                           S* __restrict__ G) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, bool CURV, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
+                                                              const S* __restrict__ TU, S* __restrict__ Q,
+                                                              S* __restrict__ G) {
+  using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(smem_raw);     // [T][nf][N]
@@ -404,11 +412,11 @@ __global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ T
 // MODE 0 writes f; MODE 1 performs the ARK stage update and emits the next
 // stage state's traces.
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC, bool CURV, int MODE>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_elem(Mesh<S> M, const S* U,
-                                                            const S* __restrict__ Q, const S* __restrict__ FF,
-                                                            S* __restrict__ out, Stage<S> st) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, bool VISC, bool CURV, int MODE, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const S* U,
+                                                               const S* __restrict__ Q, const S* __restrict__ FF,
+                                                               S* __restrict__ out, Stage<S> st) {
+  using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* fs = reinterpret_cast<S*>(smem_raw);   // [T][D][nf][N]  (reused for the next state's traces)
@@ -513,12 +521,15 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_elem(Mesh<S> M, const S* 
   S y[nf];
   if (active) {
     const size_t off = (size_t)e * H::STATE + q;
+    const double dt = st.dte ? st.dte[e] : st.dt;
     if (!st.last) {
+      S ca[MAXSTAGES];
+      for (int j = 0; j <= st.i; ++j) ca[j] = (S)(dt * st.ca[j]);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         S acc = st.base[off + f * N];
-        for (int j = 0; j < st.i; ++j) acc += st.ca[j] * st.k[j][off + f * N];
-        acc += st.ca[st.i] * res[f];
+        for (int j = 0; j < st.i; ++j) acc += ca[j] * st.k[j][off + f * N];
+        acc += ca[st.i] * res[f];
         y[f] = acc;
         st.Kout[off + f * N] = res[f];
         st.Y[off + f * N] = acc;
@@ -528,12 +539,12 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_elem(Mesh<S> M, const S* 
       for (int f = 0; f < nf; ++f) {
         double un = st.Un[off + f * N];
         if (sizeof(S) == 8) {
-          for (int j = 0; j < st.i; ++j) un += st.cb[j] * (double)st.k[j][off + f * N];
-          un += st.cb[st.i] * (double)res[f];
+          for (int j = 0; j < st.i; ++j) un += (dt * st.cb[j]) * (double)st.k[j][off + f * N];
+          un += (dt * st.cb[st.i]) * (double)res[f];
         } else {
           S inc = S(0);
-          for (int j = 0; j < st.i; ++j) inc += (S)st.cb[j] * st.k[j][off + f * N];
-          inc += (S)st.cb[st.i] * res[f];
+          for (int j = 0; j < st.i; ++j) inc += (S)(dt * st.cb[j]) * st.k[j][off + f * N];
+          inc += (S)(dt * st.cb[st.i]) * res[f];
           un += (double)inc;
         }
         st.Un[off + f * N] = un;
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_elem(Mesh<S> M, const S* 
     for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
   }
   __syncthreads();
-  tile_traces<D, P, S>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
 }
 
 }  // namespace dgx

@@ -19,11 +19,15 @@ struct Gas {
 };
 
 template <typename S>
-__device__ __forceinline__ S dsqrt(S x) { return sqrt(x); }
+__host__ __device__ __forceinline__ S dsqrt(S x) {
+  using ::sqrt;
+  return sqrt(x);
+}
+using ::fabs;
 
 // Physical convective fluxes in all D directions: F[i][f].
 template <int D, typename S>
-__device__ __forceinline__ void conv_flux_all(const S (&U)[D + 2], const Gas<S>& g, S (&F)[D][D + 2]) {
+__host__ __device__ __forceinline__ void conv_flux_all(const S (&U)[D + 2], const Gas<S>& g, S (&F)[D][D + 2]) {
   const S ir = S(1) / U[0];
   S u[D];
   S mm = 0;
@@ -45,7 +49,7 @@ __device__ __forceinline__ void conv_flux_all(const S (&U)[D + 2], const Gas<S>&
 
 // Viscous fluxes in all D directions from U and Q = grad U.
 template <int D, typename S>
-__device__ __forceinline__ void visc_flux_all(const S (&U)[D + 2], const S (&Q)[D][D + 2], const Gas<S>& g,
+__host__ __device__ __forceinline__ void visc_flux_all(const S (&U)[D + 2], const S (&Q)[D][D + 2], const Gas<S>& g,
                                               S (&F)[D][D + 2]) {
   const S ir = S(1) / U[0];
   S u[D];
@@ -83,7 +87,7 @@ __device__ __forceinline__ void visc_flux_all(const S (&U)[D + 2], const S (&Q)[
 
 // Viscous flux through the vector nv:  G = sum_i F^nu_i nv_i.
 template <int D, typename S>
-__device__ __forceinline__ void visc_flux_normal(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void visc_flux_normal(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
                                                  const Gas<S>& g, S (&G)[D + 2]) {
   S F[D][D + 2];
   visc_flux_all<D, S>(U, Q, g, F);
@@ -99,7 +103,7 @@ __device__ __forceinline__ void visc_flux_normal(const S (&U)[D + 2], const S (&
 // Adiabatic no-slip wall: F^nu(U_w, Q).nv with U_w = (rho, 0, rho e_i) and q.n = 0,
 // i.e. (0, tau(U_w, Q) nv, 0) where d_a u_i = Q[a][1+i] / rho.
 template <int D, typename S>
-__device__ __forceinline__ void wall_visc_flux(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void wall_visc_flux(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
                                                const Gas<S>& g, S (&G)[D + 2]) {
   const S ir = S(1) / U[0];
   S gu[D][D];
@@ -126,7 +130,7 @@ __device__ __forceinline__ void wall_visc_flux(const S (&U)[D + 2], const S (&Q)
 
 // Mirror (reflected) state across a wall with normal nv: (rho, m - 2 (m.n) n, rho E).
 template <int D, typename S>
-__device__ __forceinline__ void mirror_state(const S (&U)[D + 2], const S (&nv)[D], S (&R)[D + 2]) {
+__host__ __device__ __forceinline__ void mirror_state(const S (&U)[D + 2], const S (&nv)[D], S (&R)[D + 2]) {
   S n2 = 0, mn = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -142,7 +146,7 @@ __device__ __forceinline__ void mirror_state(const S (&U)[D + 2], const S (&nv)[
 
 // No-slip wall state U_w = (rho, 0, .., 0, rho E - |m|^2 / (2 rho)).
 template <int D, typename S>
-__device__ __forceinline__ void wall_state(const S (&U)[D + 2], S (&W)[D + 2]) {
+__host__ __device__ __forceinline__ void wall_state(const S (&U)[D + 2], S (&W)[D + 2]) {
   S mm = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) mm += U[1 + i] * U[1 + i];
@@ -156,7 +160,7 @@ __device__ __forceinline__ void wall_state(const S (&U)[D + 2], S (&W)[D + 2]) {
 // F* = (F(UL) + F(UR)).nv / 2 - lam (UR - UL) / 2,
 // lam = max(|uL.nv| + cL |nv|, |uR.nv| + cR |nv|).
 template <int D, typename S, bool UNIT>
-__device__ __forceinline__ void llf_flux(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void llf_flux(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
                                          const Gas<S>& g, S (&F)[D + 2]) {
   S sJ = S(1);
   if (!UNIT) {
@@ -204,11 +208,11 @@ __device__ __forceinline__ void llf_flux(const S (&UL)[D + 2], const S (&UR)[D +
 namespace dgx {
 
 template <typename S>
-__device__ __forceinline__ S sgn(S x) { return x > S(0) ? S(1) : (x < S(0) ? S(-1) : S(0)); }
+__host__ __device__ __forceinline__ S sgn(S x) { return x > S(0) ? S(1) : (x < S(0) ? S(-1) : S(0)); }
 
 // Convective fluxes in all directions: Ub += (dF/dU)^T Fb.
 template <int D, typename S>
-__device__ __forceinline__ void conv_flux_all_vjp(const S (&U)[D + 2], const S (&Fb)[D][D + 2], const Gas<S>& g,
+__host__ __device__ __forceinline__ void conv_flux_all_vjp(const S (&U)[D + 2], const S (&Fb)[D][D + 2], const Gas<S>& g,
                                                   S (&Ub)[D + 2]) {
   const S ir = S(1) / U[0];
   S u[D], mm = 0;
@@ -256,7 +260,7 @@ __device__ __forceinline__ void conv_flux_all_vjp(const S (&U)[D + 2], const S (
 
 // Viscous fluxes in all directions: Ub += (dF/dU)^T Fb, Qb += (dF/dQ)^T Fb.
 template <int D, typename S>
-__device__ __forceinline__ void visc_flux_all_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&Fb)[D][D + 2],
+__host__ __device__ __forceinline__ void visc_flux_all_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&Fb)[D][D + 2],
                                                   const Gas<S>& g, S (&Ub)[D + 2], S (&Qb)[D][D + 2]) {
   const S ir = S(1) / U[0];
   S u[D];
@@ -337,7 +341,7 @@ __device__ __forceinline__ void visc_flux_all_vjp(const S (&U)[D + 2], const S (
 
 // G = sum_i F^nu_i nv_i: cotangent Gb -> (Ub, Qb).
 template <int D, typename S>
-__device__ __forceinline__ void visc_flux_normal_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void visc_flux_normal_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
                                                      const S (&Gb)[D + 2], const Gas<S>& g, S (&Ub)[D + 2],
                                                      S (&Qb)[D][D + 2]) {
   S Fb[D][D + 2];
@@ -350,7 +354,7 @@ __device__ __forceinline__ void visc_flux_normal_vjp(const S (&U)[D + 2], const 
 
 // Adiabatic wall flux (0, tau(U_w, Q) nv, 0), d_a u_i = Q[a][1+i] / rho.
 template <int D, typename S>
-__device__ __forceinline__ void wall_visc_flux_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void wall_visc_flux_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], const S (&nv)[D],
                                                    const S (&Gb)[D + 2], const Gas<S>& g, S (&Ub)[D + 2],
                                                    S (&Qb)[D][D + 2]) {
   const S ir = S(1) / U[0];
@@ -384,7 +388,7 @@ __device__ __forceinline__ void wall_visc_flux_vjp(const S (&U)[D + 2], const S 
 
 // Mirror state R = (rho, m - 2 (m.n) n / |n|^2, rho E): linear and symmetric in m.
 template <int D, typename S>
-__device__ __forceinline__ void mirror_state_vjp(const S (&nv)[D], const S (&Rb)[D + 2], S (&Ub)[D + 2]) {
+__host__ __device__ __forceinline__ void mirror_state_vjp(const S (&nv)[D], const S (&Rb)[D + 2], S (&Ub)[D + 2]) {
   S n2 = 0, rn = 0;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -400,7 +404,7 @@ __device__ __forceinline__ void mirror_state_vjp(const S (&nv)[D], const S (&Rb)
 
 // Wall state W = (rho, 0, rho E - |m|^2 / (2 rho)).
 template <int D, typename S>
-__device__ __forceinline__ void wall_state_vjp(const S (&U)[D + 2], const S (&Wb)[D + 2], S (&Ub)[D + 2]) {
+__host__ __device__ __forceinline__ void wall_state_vjp(const S (&U)[D + 2], const S (&Wb)[D + 2], S (&Ub)[D + 2]) {
   const S ir = S(1) / U[0];
   S mm = 0;
 #pragma unroll
@@ -413,7 +417,7 @@ __device__ __forceinline__ void wall_state_vjp(const S (&U)[D + 2], const S (&Wb
 
 // LLF flux: cotangent Fb -> (ULb, URb).
 template <int D, typename S, bool UNIT>
-__device__ __forceinline__ void llf_flux_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
+__host__ __device__ __forceinline__ void llf_flux_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
                                              const S (&Fb)[D + 2], const Gas<S>& g, S (&ULb)[D + 2],
                                              S (&URb)[D + 2]) {
   S sJ = S(1);

@@ -51,12 +51,12 @@ struct Cot {
 };
 
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC, bool CURV>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_elem(Mesh<S> M, const S* __restrict__ U,
-                                                                const S* __restrict__ Q, Cot<S> cot,
-                                                                S* __restrict__ FFb, S* __restrict__ Ub,
-                                                                S* __restrict__ Qb) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, bool VISC, bool CURV, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, const S* __restrict__ U,
+                                                                   const S* __restrict__ Q, Cot<S> cot,
+                                                                   S* __restrict__ FFb, S* __restrict__ Ub,
+                                                                   S* __restrict__ Qb) {
+  using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* mus = reinterpret_cast<S*>(smem_raw);  // [T][nf][N]
@@ -239,12 +239,12 @@ __global__ void __launch_bounds__(256) k_vjp_face(Mesh<S> M, const S* __restrict
 }
 
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool CURV>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_br1(Mesh<S> M, const S* __restrict__ TU,
-                                                               const S* __restrict__ Q, const S* __restrict__ Gb,
-                                                               S* __restrict__ Qb, S* __restrict__ TUb,
-                                                               S* __restrict__ JB, S* __restrict__ Ub) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, bool CURV, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, const S* __restrict__ TU,
+                                                                  const S* __restrict__ Q, const S* __restrict__ Gb,
+                                                                  S* __restrict__ Qb, S* __restrict__ TUb,
+                                                                  S* __restrict__ JB, S* __restrict__ Ub) {
+  using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* qs = reinterpret_cast<S*>(smem_raw);   // [T][D][nf][N]  forward Q, later dU_bar
@@ -426,10 +426,10 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_br1(Mesh<S> M, const 
 }
 
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC>
-__global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_gather(Mesh<S> M, const S* __restrict__ TUb,
-                                                                  const S* __restrict__ JB, S* g, Cot<S> cot) {
-  using H = Sh<D, P>;
+template <int D, int P, typename S, bool VISC, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, const S* __restrict__ TUb,
+                                                                     const S* __restrict__ JB, S* g, Cot<S> cot) {
+  using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* tub = reinterpret_cast<S*>(smem_raw);  // [T][NF][nf][nfp]
@@ -483,38 +483,59 @@ __global__ void __launch_bounds__(Sh<D, P>::THREADS) k_vjp_gather(Mesh<S> M, con
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S>
 struct VjpOps {
-  using H = Sh<D, P>;
-  static size_t smem_elem() { return sizeof(S) * (H::T * H::STATE + H::n * H::n + 2 * H::n); }
-  static size_t smem_br1() {
-    return sizeof(S) * (2 * H::T * D * H::STATE + H::T * H::NF * D * H::nf * H::nfp + H::T * H::FACE +
-                        H::n * H::n + 4 * H::n);
+  template <int V>
+  using H = Sh<D, P, V>;
+  template <int V>
+  static size_t smem_elem() {
+    return sizeof(S) * (H<V>::T * H<V>::STATE + H<V>::n * H<V>::n + 2 * H<V>::n);
   }
-  static size_t smem_gather() { return sizeof(S) * (H::T * H::FACE + 2 * H::n); }
-  static int blocks(int E) { return (E + H::T - 1) / H::T; }
-  template <typename K>
-  static void allow(K k, size_t b) {
-    if (b > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+  template <int V>
+  static size_t smem_br1() {
+    using h = H<V>;
+    return sizeof(S) * (2 * h::T * D * h::STATE + h::T * h::NF * D * h::nf * h::nfp + h::T * h::FACE +
+                        h::n * h::n + 4 * h::n);
+  }
+  template <int V>
+  static size_t smem_gather() {
+    return sizeof(S) * (H<V>::T * H<V>::FACE + 2 * H<V>::n);
+  }
+  template <int V>
+  static int blocks(int E) {
+    return (E + H<V>::T - 1) / H<V>::T;
+  }
+  // 0 elem, 1 br1, 2 gather
+  static size_t smem(int kind, int V) {
+    switch (V) {
+      case 0: return kind == 0 ? smem_elem<0>() : kind == 1 ? smem_br1<0>() : smem_gather<0>();
+      case 1: return kind == 0 ? smem_elem<1>() : kind == 1 ? smem_br1<1>() : smem_gather<1>();
+      default: return kind == 0 ? smem_elem<2>() : kind == 1 ? smem_br1<2>() : smem_gather<2>();
+    }
   }
 
-  static cudaError_t elem(const Mesh<S>& M, bool visc, bool curv, const S* U, const VjpWork& w, const Cot<S>& c,
-                          S* Ub, cudaStream_t st) {
-#define DGX_VE(V, C)                                                                                   \
-  {                                                                                                    \
-    auto k = k_vjp_elem<D, P, S, V, C>;                                                                \
-    allow(k, smem_elem());                                                                             \
-    k<<<blocks(M.E), H::THREADS, smem_elem(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb); \
-  }
-    if (visc) {
-      if (curv) DGX_VE(true, true) else DGX_VE(true, false)
-    } else {
-      if (curv) DGX_VE(false, true) else DGX_VE(false, false)
-    }
-#undef DGX_VE
+  template <bool VISC, bool CURV, int V>
+  static cudaError_t elem_v(const Mesh<S>& M, const S* U, const VjpWork& w, const Cot<S>& c, S* Ub,
+                            cudaStream_t st) {
+    static bool done = false;
+    auto k = k_vjp_elem<D, P, S, VISC, CURV, V>;
+    allow_smem_once(k, smem_elem<V>(), done);
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb);
     return cudaGetLastError();
+  }
+  template <bool VISC, bool CURV>
+  static cudaError_t elem_c(const Mesh<S>& M, int V, const S* U, const VjpWork& w, const Cot<S>& c, S* Ub,
+                            cudaStream_t st) {
+    if (V == 0) return elem_v<VISC, CURV, 0>(M, U, w, c, Ub, st);
+    if (V == 1) return elem_v<VISC, CURV, 1>(M, U, w, c, Ub, st);
+    return elem_v<VISC, CURV, 2>(M, U, w, c, Ub, st);
+  }
+  static cudaError_t elem(const Mesh<S>& M, int V, bool visc, bool curv, const S* U, const VjpWork& w,
+                          const Cot<S>& c, S* Ub, cudaStream_t st) {
+    if (visc) return curv ? elem_c<true, true>(M, V, U, w, c, Ub, st) : elem_c<true, false>(M, V, U, w, c, Ub, st);
+    return curv ? elem_c<false, true>(M, V, U, w, c, Ub, st) : elem_c<false, false>(M, V, U, w, c, Ub, st);
   }
 
   static cudaError_t face(const Mesh<S>& M, bool visc, bool curv, const VjpWork& w, cudaStream_t st) {
-    const int total = M.nFaces * H::nfp;
+    const int total = M.nFaces * Sh<D, P>::nfp;
     if (total == 0) return cudaSuccess;
     const int nb = (total + 255) / 256;
     const S* TU = (const S*)w.TU;
@@ -531,65 +552,78 @@ struct VjpOps {
     return cudaGetLastError();
   }
 
-  static cudaError_t br1(const Mesh<S>& M, bool curv, const VjpWork& w, S* Ub, cudaStream_t st) {
-    const size_t sm = smem_br1();
-    if (curv) {
-      auto k = k_vjp_br1<D, P, S, true>;
-      allow(k, sm);
-      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb, (S*)w.Qb,
-                                             (S*)w.TUb, (S*)w.JB, Ub);
-    } else {
-      auto k = k_vjp_br1<D, P, S, false>;
-      allow(k, sm);
-      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb, (S*)w.Qb,
-                                             (S*)w.TUb, (S*)w.JB, Ub);
-    }
+  template <bool CURV, int V>
+  static cudaError_t br1_v(const Mesh<S>& M, const VjpWork& w, S* Ub, cudaStream_t st) {
+    static bool done = false;
+    auto k = k_vjp_br1<D, P, S, CURV, V>;
+    allow_smem_once(k, smem_br1<V>(), done);
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb,
+                                                             (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub);
     return cudaGetLastError();
   }
-
-  static cudaError_t gather(const Mesh<S>& M, bool visc, const VjpWork& w, S* g, const Cot<S>& c,
-                            cudaStream_t st) {
-    const size_t sm = smem_gather();
-    if (visc) {
-      auto k = k_vjp_gather<D, P, S, true>;
-      allow(k, sm);
-      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
-    } else {
-      auto k = k_vjp_gather<D, P, S, false>;
-      allow(k, sm);
-      k<<<blocks(M.E), H::THREADS, sm, st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
+  static cudaError_t br1(const Mesh<S>& M, int V, bool curv, const VjpWork& w, S* Ub, cudaStream_t st) {
+    if (curv) {
+      if (V == 0) return br1_v<true, 0>(M, w, Ub, st);
+      if (V == 1) return br1_v<true, 1>(M, w, Ub, st);
+      return br1_v<true, 2>(M, w, Ub, st);
     }
+    if (V == 0) return br1_v<false, 0>(M, w, Ub, st);
+    if (V == 1) return br1_v<false, 1>(M, w, Ub, st);
+    return br1_v<false, 2>(M, w, Ub, st);
+  }
+
+  template <bool VISC, int V>
+  static cudaError_t gather_v(const Mesh<S>& M, const VjpWork& w, S* g, const Cot<S>& c, cudaStream_t st) {
+    static bool done = false;
+    auto k = k_vjp_gather<D, P, S, VISC, V>;
+    allow_smem_once(k, smem_gather<V>(), done);
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_gather<V>(), st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
     return cudaGetLastError();
+  }
+  static cudaError_t gather(const Mesh<S>& M, int V, bool visc, const VjpWork& w, S* g, const Cot<S>& c,
+                            cudaStream_t st) {
+    if (visc) {
+      if (V == 0) return gather_v<true, 0>(M, w, g, c, st);
+      if (V == 1) return gather_v<true, 1>(M, w, g, c, st);
+      return gather_v<true, 2>(M, w, g, c, st);
+    }
+    if (V == 0) return gather_v<false, 0>(M, w, g, c, st);
+    if (V == 1) return gather_v<false, 1>(M, w, g, c, st);
+    return gather_v<false, 2>(M, w, g, c, st);
   }
 };
 
-// Type-erased adjoint launch table (one per (D, P, S)).
+// Type-erased adjoint launch table (one per (D, P, S)); V = tile variant.
 struct VjpTable {
-  cudaError_t (*elem)(const void* M, bool visc, bool curv, const void* U, const VjpWork& w, const void* cot,
+  cudaError_t (*elem)(const void* M, int V, bool visc, bool curv, const void* U, const VjpWork& w, const void* cot,
                       void* Ub, cudaStream_t st);
   cudaError_t (*face)(const void* M, bool visc, bool curv, const VjpWork& w, cudaStream_t st);
-  cudaError_t (*br1)(const void* M, bool curv, const VjpWork& w, void* Ub, cudaStream_t st);
-  cudaError_t (*gather)(const void* M, bool visc, const VjpWork& w, void* g, const void* cot, cudaStream_t st);
+  cudaError_t (*br1)(const void* M, int V, bool curv, const VjpWork& w, void* Ub, cudaStream_t st);
+  cudaError_t (*gather)(const void* M, int V, bool visc, const VjpWork& w, void* g, const void* cot,
+                        cudaStream_t st);
+  size_t (*smem)(int kind, int V);  // 0 elem, 1 br1, 2 gather
 };
 
 template <int D, int P, typename S>
 const void* vjp_table() {
   struct R {
-    static cudaError_t elem(const void* M, bool v, bool c, const void* U, const VjpWork& w, const void* cot, void* Ub,
-                            cudaStream_t st) {
-      return VjpOps<D, P, S>::elem(*(const Mesh<S>*)M, v, c, (const S*)U, w, *(const Cot<S>*)cot, (S*)Ub, st);
+    static cudaError_t elem(const void* M, int V, bool v, bool c, const void* U, const VjpWork& w, const void* cot,
+                            void* Ub, cudaStream_t st) {
+      return VjpOps<D, P, S>::elem(*(const Mesh<S>*)M, V, v, c, (const S*)U, w, *(const Cot<S>*)cot, (S*)Ub, st);
     }
     static cudaError_t face(const void* M, bool v, bool c, const VjpWork& w, cudaStream_t st) {
       return VjpOps<D, P, S>::face(*(const Mesh<S>*)M, v, c, w, st);
     }
-    static cudaError_t br1(const void* M, bool c, const VjpWork& w, void* Ub, cudaStream_t st) {
-      return VjpOps<D, P, S>::br1(*(const Mesh<S>*)M, c, w, (S*)Ub, st);
+    static cudaError_t br1(const void* M, int V, bool c, const VjpWork& w, void* Ub, cudaStream_t st) {
+      return VjpOps<D, P, S>::br1(*(const Mesh<S>*)M, V, c, w, (S*)Ub, st);
     }
-    static cudaError_t gather(const void* M, bool v, const VjpWork& w, void* g, const void* cot, cudaStream_t st) {
-      return VjpOps<D, P, S>::gather(*(const Mesh<S>*)M, v, w, (S*)g, *(const Cot<S>*)cot, st);
+    static cudaError_t gather(const void* M, int V, bool v, const VjpWork& w, void* g, const void* cot,
+                              cudaStream_t st) {
+      return VjpOps<D, P, S>::gather(*(const Mesh<S>*)M, V, v, w, (S*)g, *(const Cot<S>*)cot, st);
     }
+    static size_t smem(int kind, int V) { return VjpOps<D, P, S>::smem(kind, V); }
   };
-  static const VjpTable t = {&R::elem, &R::face, &R::br1, &R::gather};
+  static const VjpTable t = {&R::elem, &R::face, &R::br1, &R::gather, &R::smem};
   return &t;
 }
 

@@ -42,7 +42,9 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_workspace_bytes", "dgx_rhs", "dgx_rhs_vjp", "dgx_ark_step", "dgx_check",
            "dgx_status_string", "dgx_query", "dgx_profile_enable", "dgx_profile_read", "dgx_profile_reset",
            "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc",
-           "dgx_stage_bytes"]
+           "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
+           "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
+           "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune"]
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -69,6 +71,18 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_ark_adjoint_step.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.dgx_rhs_noalloc.argtypes = [vp, vp, vp, vp]
     lib.dgx_stage_bytes.argtypes = [vp]
+    lib.dgx_kernel_work.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.dgx_autotune.argtypes = [vp, vp, i32, vp]
+    lib.dgx_get_variants.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.dgx_set_variants.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.dgx_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    lib.dgx_batch_destroy.argtypes = [vp]
+    lib.dgx_batch_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32)]
+    lib.dgx_batch_workspace_bytes.argtypes = [vp]
+    lib.dgx_batch_set_dt.argtypes = [vp, vp]
+    lib.dgx_batch_step.argtypes = [vp, vp, vp, vp]
+    lib.dgx_batch_step_graph.argtypes = [vp, vp, vp, vp]
+    lib.dgx_batch_autotune.argtypes = [vp, vp, i32, vp]
     lib.dgx_check.argtypes = [vp]
     lib.dgx_status_string.argtypes = [i32]
     lib.dgx_status_string.restype = ctypes.c_char_p
@@ -84,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_status_string.restype = ctypes.c_char_p
     lib.dgx_kernel_name.restype = ctypes.c_char_p
     lib.dgx_stage_bytes.restype = ctypes.c_size_t
+    lib.dgx_batch_workspace_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -282,6 +297,30 @@ class Solver:
     def profile_reset(self):
         _check(self.lib.dgx_profile_reset(self.h), "dgx_profile_reset")
 
+    def autotune(self, U64: torch.Tensor, reps: int = 3, stream=None):
+        """Pick the fastest tile variant per kernel on this state (set-up call)."""
+        _check(self.lib.dgx_autotune(self.h, self._state(U64, "U64", torch.float64), int(reps),
+                                     _stream_ptr(stream)), "dgx_autotune")
+        return self.variants()
+
+    def variants(self) -> dict:
+        v = (ctypes.c_int32 * len(KERNELS))()
+        _check(self.lib.dgx_get_variants(self.h, v), "dgx_get_variants")
+        return {k: v[i] for i, k in enumerate(KERNELS)}
+
+    def set_variants(self, variants: dict):
+        cur = self.variants()
+        cur.update(variants)
+        v = (ctypes.c_int32 * len(KERNELS))(*[cur[k] for k in KERNELS])
+        _check(self.lib.dgx_set_variants(self.h, v), "dgx_set_variants")
+
+    def kernel_work(self, name: str):
+        """(algorithmic flops, algorithmic bytes) of one launch of a kernel kind."""
+        fl, by = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.dgx_kernel_work(self.h, KERNELS.index(name), ctypes.byref(fl), ctypes.byref(by)),
+               "dgx_kernel_work")
+        return fl.value, by.value
+
     def profile_read(self) -> dict:
         """{kernel name: (launches, total device ms)} since the last reset."""
         out = {}
@@ -335,3 +374,82 @@ def adjoint_trajectory(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int,
         solver.ark_step_stages(work, dt, stages)
         solver.ark_adjoint_step(stages, lam, dt)
     return U, lam
+
+
+class Batch:
+    """Many independent instances advanced together (see dgx_batch_* in dgx.h).
+
+    ``solvers``: Solver objects with mesh and tableau set (the same tableau);
+    ``dt``: one time step per instance.  States live in one packed FP64 buffer
+    (``pack`` / ``unpack``)."""
+
+    def __init__(self, solvers, dt):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        handles = (ctypes.c_void_p * n)(*[s.h.value for s in self.solvers])
+        b = ctypes.c_void_p()
+        _check(self.lib.dgx_batch_create(handles, n, ctypes.byref(b)), "dgx_batch_create")
+        self.b = b
+        offs = (ctypes.c_int64 * (n + 1))()
+        ng = ctypes.c_int32()
+        _check(self.lib.dgx_batch_layout(b, offs, ctypes.byref(ng)), "dgx_batch_layout")
+        self.offsets = [offs[i] for i in range(n + 1)]
+        self.groups = ng.value
+        self.device = self.solvers[0].device
+        self.set_dt(dt)
+        nbytes = int(self.lib.dgx_batch_workspace_bytes(b))
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        self._ws_raw = raw
+        self.ws = ctypes.c_void_p(raw.data_ptr() + off)
+
+    def set_dt(self, dt):
+        arr = np.ascontiguousarray(dt, dtype=np.float64)
+        if arr.shape != (len(self.solvers),):
+            raise ValueError("one dt per instance")
+        _check(self.lib.dgx_batch_set_dt(self.b, _ptr(arr)), "dgx_batch_set_dt")
+        self.dt = arr
+
+    def empty(self):
+        return torch.empty(self.offsets[-1], dtype=torch.float64, device=self.device)
+
+    def _range(self, i):
+        n = int(np.prod(self.solvers[i].shape))
+        return self.offsets[i], self.offsets[i] + n
+
+    def pack(self, states):
+        """Packed FP64 state (instances are stored group by group, see dgx_batch_layout)."""
+        out = self.empty()
+        for i, U in enumerate(states):
+            a, b = self._range(i)
+            out[a:b] = torch.as_tensor(U, dtype=torch.float64).reshape(-1)
+        return out
+
+    def unpack(self, packed):
+        return [packed[slice(*self._range(i))].view(s.shape) for i, s in enumerate(self.solvers)]
+
+    def _packed(self, U):
+        if not (U.is_cuda and U.dtype == torch.float64 and U.is_contiguous() and U.numel() == self.offsets[-1]):
+            raise ValueError("packed state must come from Batch.empty()/pack()")
+        return ctypes.c_void_p(U.data_ptr())
+
+    def step(self, U, graph: bool = False, stream=None):
+        fn = self.lib.dgx_batch_step_graph if graph else self.lib.dgx_batch_step
+        _check(fn(self.b, self._packed(U), self.ws, _stream_ptr(stream)), "dgx_batch_step")
+        return U
+
+    def autotune(self, U, reps: int = 3, stream=None):
+        _check(self.lib.dgx_batch_autotune(self.b, self._packed(U), int(reps), _stream_ptr(stream)),
+               "dgx_batch_autotune")
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.dgx_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
