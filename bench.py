@@ -159,6 +159,7 @@ def time_gpu(prec, steps, warmup, dt=1e-9):
         s.ark_step_stages(U, dt, stages)
         s.ark_adjoint_step(stages, lam, dt)
 
+    variants = s.autotune(U, reps=3)        # set-up: fastest tile size per kernel
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
@@ -221,7 +222,7 @@ def time_gpu(prec, steps, warmup, dt=1e-9):
     dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
     return {"ms": float(np.mean(gtimes)), "eager_ms": float(np.mean(times)), "ms_all": gtimes, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
             "evals_per_step": 8, "e2e_ms": float(np.mean(e2e)), "h2d": 2 * nbytes_state, "d2h": 2 * nbytes_state,
-            "mesh": mesh, "phys": phys, "steps": steps, "solver": s}
+            "mesh": mesh, "phys": phys, "steps": steps, "solver": s, "variants": variants}
 
 
 def roofline(res, prec, pk):
@@ -377,6 +378,8 @@ def main():
                        "timing": "CUDA-graph replay of the step; per-kernel roofline from the eager profiled "
                                  "pass of the same steps",
                        "eager_ms_per_step": round(r32["eager_ms"], 4),
+                       "tile_variants": {k: v for k, v in r32["variants"].items()
+                                         if k not in ("face", "vjp_face")},
                        "step": "1 ARS(3,4,3) step (stage states kept) + its discrete adjoint (4 VJPs)",
                        "kernel_launches_per_step": launches // max(1, args.steps),
                        "dof_evals_per_step": evals, "l2": "flushed (256 MB write) between timed steps",

@@ -211,16 +211,26 @@ const char* dgx_kernel_name(int32_t kind);
  * The element-stage figures are averages over the stages of the tableau. */
 dgx_status dgx_kernel_work(const dgx_handle* h, int32_t kind, double* flops, double* bytes);
 
-/* Tile-size autotuner.  Tile kernels come in NVARIANTS = 3 variants of about
- * 128 / 256 / 512 threads per CTA (tiles of max(1, threads / N) elements).
+/* Tile-size autotuner.  Tile kernels come in 4 variants: 0..2 use one CTA of
+ * about 128 / 256 / 512 threads per tile of max(1, threads / N) elements;
+ * 3 (elements of at most 32 nodes) uses one warp per element with warp-level
+ * synchronisation only.
  * dgx_autotune times every variant of every tile kernel (event profiler, reps
  * timed repetitions of one ARK step and, when built, its adjoint, on a scratch
  * copy of the device state U64) and keeps the fastest per kernel; variants
- * whose shared memory exceeds the 227 KB per-CTA limit are skipped.  It is a
+ * whose shared memory exceeds the 227 KB per-CTA limit are skipped; it also
+ * keeps or drops the persistent TMA-fed element kernel (dgx_set_pipeline),
+ * whichever runs the stage faster.  It is a
  * set-up call: it allocates and frees its scratch and synchronises the stream.
  * Requires a mesh and a tableau.  variants[] is indexed by dgx_kernel_kind. */
 dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream);
 dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants);
+/* Persistent, TMA-fed kernels (default on): a grid of (SMs x resident CTAs)
+ * CTAs walks the element tiles; each tile's contiguous input blocks arrive by
+ * cp.async.bulk into a double buffer while the previous tile is computed.
+ * Used where every block is a 16-byte multiple and 16-byte aligned (else the
+ * one-CTA-per-tile kernels run).  Same arithmetic either way. */
+dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable);
 dgx_status dgx_set_variants(dgx_handle* h, const int32_t* variants);
 
 /* Batched ensemble: many independent instances (meshes, degrees, physics)

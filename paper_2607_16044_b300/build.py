@@ -48,11 +48,19 @@ struct R {{
                                 cudaStream_t st) {{
     return O::template elem<1>(m(M), V, v, c, (const Sc*)U, w, nullptr, *(const Stage<Sc>*)sa, st);
   }}
+  static cudaError_t elem_pipe(const void* M, int V, bool v, bool c, const void* U, const Work& w, void* out,
+                               const void* sa, int nsm, cudaStream_t st, bool* used) {{
+    if (sa) return O::template elem_pipe<1>(m(M), V, v, c, (const Sc*)U, w, nullptr, *(const Stage<Sc>*)sa, nsm, st,
+                                           *used);
+    Stage<Sc> none{{}};
+    return O::template elem_pipe<0>(m(M), V, v, c, (const Sc*)U, w, (Sc*)out, none, nsm, st, *used);
+  }}
   static size_t smem(int kind, int V) {{ return O::smem(kind, V); }}
 }};
 }}  // namespace
 const Table* table_d{D}_{T}_p{P}() {{
-  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::smem, {VJP_PTR}}};
+  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::elem_pipe, &R::smem,
+                          {VJP_PTR}}};
   return &t;
 }}
 }}  // namespace dgx

@@ -20,6 +20,9 @@ struct Table {
                       cudaStream_t st);
   cudaError_t (*elem_stage)(const void* M, int V, bool visc, bool curv, const void* U, const Work& w,
                             const void* stage, cudaStream_t st);
+  // persistent TMA-fed element kernel; *used = false when it cannot run (nothing launched)
+  cudaError_t (*elem_pipe)(const void* M, int V, bool visc, bool curv, const void* U, const Work& w, void* out,
+                           const void* stage, int nsm, cudaStream_t st, bool* used);
   size_t (*smem)(int kind, int V);  // tile kernels: 0 trace, 1 br1, 2 elem
   const void* vjp;                   // adjoint launch table (VjpTable) or nullptr
 };

@@ -42,8 +42,10 @@ struct dgx_handle {
   void* d_SnF = nullptr;
   dgx::Mesh<double> mesh64{};   // device views passed to the launch table
   dgx::Mesh<float> mesh32{};
+  int nsm = 148;          // SMs of the device (persistent grids)
+  bool pipeline = true;   // persistent TMA-fed kernels where the layout allows
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
-  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -461,7 +463,15 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, Uin, wi, st); });
     if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, wi, st); });
     if (err == cudaSuccess)
-      err = launch(h, DGX_K_ELEM_STAGE, st, [&] { return t->elem_stage(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, &sa, st); });
+      err = launch(h, DGX_K_ELEM_STAGE, st, [&] {
+        bool used = false;
+        if (h->pipeline) {
+          const cudaError_t e = t->elem_pipe(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, nullptr, &sa,
+                                             h->nsm, st, &used);
+          if (e != cudaSuccess || used) return e;
+        }
+        return t->elem_stage(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, &sa, st);
+      });
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -750,6 +760,20 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
     for (int p = 1; p <= 5; ++p) fill_tab(make_basis(p), t[p]);
     st = upload(t, &h->d_tabs);
   }
+  // default tile variant: about 256 threads, or the largest smaller one whose
+  // shared memory fits (small 3D elements in FP64)
+  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+    if (!is_tile_kind(k)) continue;
+    int v = 1;
+    while (v > 0 && tile_smem(h, k, v) > dgx::SMEM_LIMIT) --v;
+    h->var[k] = v;
+  }
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      h->nsm = nsm;
+  }
   if (st == DGX_OK && cudaMalloc((void**)&h->d_flags, sizeof(unsigned)) != cudaSuccess) st = DGX_ENOMEM;
   if (st == DGX_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) st = DGX_ECUDA;
   if (st != DGX_OK) {
@@ -946,7 +970,15 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
     err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, U, w, st); });
   if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
   if (err == cudaSuccess)
-    err = launch(h, DGX_K_ELEM, st, [&] { return t->elem(M, h->var[DGX_K_ELEM], h->viscous, h->curv, U, w, dUdt, st); });
+    err = launch(h, DGX_K_ELEM, st, [&] {
+      bool used = false;
+      if (h->pipeline) {
+        const cudaError_t e = t->elem_pipe(M, h->var[DGX_K_ELEM], h->viscous, h->curv, U, w, dUdt, nullptr, h->nsm,
+                                           st, &used);
+        if (e != cudaSuccess || used) return e;
+      }
+      return t->elem(M, h->var[DGX_K_ELEM], h->viscous, h->curv, U, w, dUdt, st);
+    });
   return cuda_status(err);
 }
 
@@ -1060,9 +1092,36 @@ dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* st
     }
   }
   for (int k = 0; k < DGX_KERNEL_KINDS; ++k) h->var[k] = choice[k];
+  // persistent TMA-fed element kernel or not: keep whichever is faster
+  double elem_ms[2] = {1e300, 1e300};
+  const bool was_pipe = h->pipeline;
+  for (int pipe = 0; pipe < 2; ++pipe) {
+    h->pipeline = pipe != 0;
+    for (int rep = -1; rep < reps; ++rep) {
+      if (rep == 0) dgx_profile_reset(h);
+      if (cudaMemcpyAsync(U.p, U64, state64, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return DGX_ECUDA;
+      s = dgx_ark_step_stages(h, U.p, dt, al(stages.p), al(ws_ark.p), stream);
+      if (s != DGX_OK) {
+        h->pipeline = was_pipe;
+        dgx_profile_enable(h, was_prof);
+        return s;
+      }
+    }
+    int64_t n = 0;
+    double ms = 0;
+    dgx_profile_read(h, DGX_K_ELEM_STAGE, &n, &ms);
+    if (n > 0) elem_ms[pipe] = ms / n;
+  }
+  h->pipeline = elem_ms[1] < elem_ms[0];
   dgx_profile_reset(h);
   dgx_profile_enable(h, was_prof);
   return cudaStreamSynchronize(st) == cudaSuccess ? DGX_OK : DGX_ECUDA;
+}
+
+dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable) {
+  if (!h) return DGX_EINVAL;
+  h->pipeline = enable != 0;
+  return DGX_OK;
 }
 
 dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants) {

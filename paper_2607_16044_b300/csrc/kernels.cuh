@@ -26,9 +26,14 @@ namespace dgx {
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
-// Tile variants (chosen per kernel by the autotuner): about 128, 256 or 512
-// threads per CTA, i.e. T = max(1, 64 * 2^(V+1) / N) elements per tile.
-constexpr int NVARIANTS = 3;
+// Tile variants (chosen per kernel by the autotuner).  V = 0, 1, 2: one CTA
+// per tile of T = max(1, 64 * 2^(V+1) / N) elements (about 128 / 256 / 512
+// threads), phases separated by __syncthreads.  V = 3 (elements of at most 32
+// nodes): one warp per element, WPB warps per CTA, each warp with its own
+// shared-memory slice and __syncwarp between phases -- no CTA barriers.
+constexpr int NVARIANTS = 4;
+constexpr int WARP_VARIANT = 3;
+constexpr int WPB = 8;
 constexpr int variant_threads(int V) { return 64 << (V + 1); }
 
 template <int D, int P, int V = 1>
@@ -38,8 +43,11 @@ struct Sh {
   static constexpr int nf = D + 2;
   static constexpr int nfp = ipow(n, D - 1);
   static constexpr int NF = 2 * D;
-  static constexpr int T = (variant_threads(V) / N) > 0 ? (variant_threads(V) / N) : 1;
-  static constexpr int THREADS = ((T * N + 31) / 32) * 32;
+  static constexpr bool WARP = (V == WARP_VARIANT);
+  static constexpr int T = WARP ? 1 : ((variant_threads(V) / N) > 0 ? (variant_threads(V) / N) : 1);
+  static constexpr int THREADS = WARP ? 32 * WPB : ((T * N + 31) / 32) * 32;
+  static constexpr int GROUPS = WARP ? WPB : 1;  // independent element groups per CTA
+  static constexpr bool VALID = !WARP || N <= 32;
   static constexpr int FACE = NF * nf * nfp;  // face values per element
   static constexpr int STATE = nf * N;        // state values per element
   __host__ __device__ static constexpr int pw(int a) { return a == 0 ? 1 : (a == 1 ? n : (a == 2 ? n * n : n * n * n)); }
@@ -51,6 +59,29 @@ struct Sh {
   }
   __device__ static __forceinline__ int qa(int q, int a) { return (q / pw(a)) % n; }
 };
+
+// Thread-group primitives: a group is the whole CTA (V < 3) or one warp (V = 3).
+template <int V>
+__device__ __forceinline__ int g_tid() {
+  return V == WARP_VARIANT ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+}
+template <int V>
+__device__ __forceinline__ int g_size() {
+  return V == WARP_VARIANT ? 32 : (int)blockDim.x;
+}
+template <int V>
+__device__ __forceinline__ int g_index() {
+  return V == WARP_VARIANT ? (int)(blockIdx.x * WPB + (threadIdx.x >> 5)) : (int)blockIdx.x;
+}
+template <int V>
+__device__ __forceinline__ void g_sync() {
+  if (V == WARP_VARIANT) __syncwarp();
+  else __syncthreads();
+}
+template <int V>
+__device__ __forceinline__ unsigned char* g_smem(unsigned char* base, size_t group_bytes) {
+  return V == WARP_VARIANT ? base + (threadIdx.x >> 5) * group_bytes : base;
+}
 
 // Own face point -> neighbour face point (orientation code, see dgx.h).
 template <int D, int n>
@@ -116,16 +147,16 @@ struct Stage {
   S* TU;                   // traces of the next stage state
 };
 
-template <typename S>
+template <typename S, int V = 1>
 __device__ __forceinline__ void load_tab(const Tab<S>* tabs, int P, S* sD, S* sDh, S* slm, S* slp, S* sLm, S* sLp,
                                          int n) {
   const Tab<S>& t = tabs[P];
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < n * n; i += g_size<V>()) {
     const int r = i / n, c = i % n;
     if (sD) sD[i] = t.D[r * 6 + c];
     if (sDh) sDh[i] = t.Dh[r * 6 + c];
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < n; i += g_size<V>()) {
     if (slm) slm[i] = t.lm[i];
     if (slp) slp[i] = t.lp[i];
     if (sLm) sLm[i] = t.Lm[i];
@@ -133,25 +164,57 @@ __device__ __forceinline__ void load_tab(const Tab<S>* tabs, int P, S* sD, S* sD
   }
 }
 
-// Traces of a staged tile (us[t][f][q]) written in output order (coalesced).
+// Shared-memory bytes of one element group (rounded to 16) for each tile kernel.
+constexpr size_t r16(size_t b) { return (b + 15) & ~(size_t)15; }
+template <int D, int P, typename S, int V>
+constexpr size_t smem_trace_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (h::T * h::STATE + 2 * h::n));
+}
+template <int D, int P, typename S, int V>
+constexpr size_t smem_br1_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (h::T * h::STATE + h::T * h::FACE + h::T * D * h::STATE + h::T * h::NF * D * h::nf * h::nfp +
+                          h::n * h::n + 4 * h::n));
+}
+template <int D, int P, typename S, int V>
+constexpr size_t smem_elem_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (h::T * D * h::STATE + h::T * h::FACE + h::n * h::n + 4 * h::n));
+}
+
+// Work items of a line pass along direction a: (element t, field f, line), the
+// line being the face-point index of the faces normal to a.
+template <int nf, int nfp>
+__device__ __forceinline__ void line_item(int i, int& t, int& f, int& line) {
+  line = i % nfp;
+  f = (i / nfp) % nf;
+  t = i / (nfp * nf);
+}
+
+// Traces of a staged tile (us[t][f][q]): one thread per (element, field, line)
+// and direction loads the line once and writes both end values.
 template <int D, int P, typename S, int V>
 __device__ __forceinline__ void tile_traces(const S* us, const S* lm, const S* lp, int nel, S* dst) {
   using H = Sh<D, P, V>;
-  const int tot = nel * H::FACE;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int fp = i % H::nfp;
-    int r = i / H::nfp;
-    const int f = r % H::nf;
-    r /= H::nf;
-    const int face = r % H::NF;
-    const int t = r / H::NF;
-    const int a = face >> 1;
-    const S* l = (face & 1) ? lp : lm;
-    const S* v = us + (t * H::nf + f) * H::N;
-    S acc = 0;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, N = H::N;
 #pragma unroll
-    for (int m = 0; m < H::n; ++m) acc += l[m] * v[H::node(m, fp, a)];
-    dst[i] = acc;
+  for (int a = 0; a < D; ++a) {
+    for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+      int t, f, line;
+      line_item<nf, nfp>(i, t, f, line);
+      const S* v = us + (t * nf + f) * N;
+      S sm = 0, sp = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const S x = v[H::node(m, line, a)];
+        sm += lm[m] * x;
+        sp += lp[m] * x;
+      }
+      S* o = dst + (size_t)t * H::FACE + f * nfp + line;
+      o[(2 * a) * nf * nfp] = sm;
+      o[(2 * a + 1) * nf * nfp] = sp;
+    }
   }
 }
 
@@ -165,20 +228,20 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
                                                                 const Tab<S>* tabs) {
   using H = Sh<D, P, V>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* us = reinterpret_cast<S*>(smem_raw);
+  S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_trace_g<D, P, S, V>()));
   S* lm = us + H::T * H::STATE;
   S* lp = lm + H::n;
-  const int e0 = blockIdx.x * H::T;
+  const int e0 = g_index<V>() * H::T;
   const int nel = min(H::T, E - e0);
   const Sin* src = U + (size_t)e0 * H::STATE;
   S* sh = shadow ? shadow + (size_t)e0 * H::STATE : nullptr;
-  for (int i = threadIdx.x; i < nel * H::STATE; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) {
     const S v = (S)src[i];
     us[i] = v;
     if (sh) sh[i] = v;
   }
-  load_tab<S>(tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, H::n);
-  __syncthreads();
+  load_tab<S, V>(tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, H::n);
+  g_sync<V>();
   tile_traces<D, P, S, V>(us, lm, lp, nel, TU + (size_t)e0 * H::FACE);
 }
 
@@ -187,7 +250,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
 //   Q_c(q) = (1/J) sum_b Ja[b][c] (D_b U)(q) + sum_faces l_{q_a}(+-1)/(w_{q_a} J) (Uhat - U^-) Sn_c
 // Uhat = (U^- + U^+)/2 inside, U_w on walls.  Writes Q and each own face's
 // viscous normal flux G = F^nu(U_f, Q_f) . n (wall: adiabatic wall flux).
-// Boxes use unit normals (the element kernel applies 2/h_a).
+// Boxes use unit normals (the element kernel applies 2/h_a).  Contractions run
+// one thread per line: the line is loaded once and all n outputs produced.
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool CURV, int V>
 __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
@@ -196,23 +260,24 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* us = reinterpret_cast<S*>(smem_raw);     // [T][nf][N]
-  S* js = us + T * H::STATE;                   // [T][NF][nf][nfp]
-  S* qs = js + T * H::FACE;                    // [T][D][nf][N]
-  S* sD = qs + T * D * H::STATE;
+  S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_br1_g<D, P, S, V>()));     // [T][nf][N]
+  S* js = us + T * H::STATE;                   // [T][NF][nf][nfp]     jumps
+  S* qs = js + T * H::FACE;                    // [T][D][nf][N]        Q
+  S* tq = qs + T * D * H::STATE;               // [T][NF][D][nf][nfp]  traces of Q
+  S* sD = tq + T * NF * D * nf * nfp;
   S* lm = sD + n * n;
   S* lp = lm + n;
   S* Lm = lp + n;
   S* Lp = Lm + n;
-  const int e0 = blockIdx.x * T;
+  const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   {
     const S* src = U + (size_t)e0 * H::STATE;
-    for (int i = threadIdx.x; i < nel * H::STATE; i += blockDim.x) us[i] = src[i];
+    for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) us[i] = src[i];
   }
-  load_tab<S>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
+  load_tab<S, V>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
   // jumps Uhat - U^- at every own face point
-  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int t = i / (nfp * NF);
@@ -235,35 +300,47 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
       for (int f = 0; f < nf; ++f) jd[f * nfp] = W[f] - UL[f];
     }
   }
-  __syncthreads();
-  const int t = threadIdx.x / N, q = threadIdx.x % N;
-  if (t < nel) {
-    const int e = e0 + t;
-    S dU[D][nf];
+  g_sync<V>();
+  // derivative lines along each direction (boxes: the Q_a of this direction, lift included)
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int fp = H::fpoint(q, a), qa = H::qa(q, a);
+  for (int a = 0; a < D; ++a) {
+    for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+      int t, f, line;
+      line_item<nf, nfp>(i, t, f, line);
+      const S* v = us + (t * nf + f) * N;
+      S x[n];
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        const S* v = us + (t * nf + f) * N;
-        S s = 0;
+      for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+      S* qo = qs + ((t * D + a) * nf + f) * N;
+      if (!CURV) {
+        const S r = M.geo.rh[(e0 + t) * D + a];
+        const S jm = js[((t * NF + 2 * a) * nf + f) * nfp + line];
+        const S jp = js[((t * NF + 2 * a + 1) * nf + f) * nfp + line];
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += sD[qa * n + m] * v[H::node(m, fp, a)];
-        dU[a][f] = s;
+        for (int k = 0; k < n; ++k) {
+          S d = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) d += sD[k * n + m] * x[m];
+          qo[H::node(k, line, a)] = r * (d + Lp[k] * jp - Lm[k] * jm);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          S d = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) d += sD[k * n + m] * x[m];
+          qo[H::node(k, line, a)] = d;  // D_a U, combined below
+        }
       }
     }
+  }
+  g_sync<V>();
+  if (CURV) {  // Q_c = (1/J) (sum_b Ja[b][c] D_b U + sum_faces lift (Uhat - U) Sn_c), per node
+    const int t = g_tid<V>() / N, q = g_tid<V>() % N;
+    const bool act = t < nel;
     S Qv[D][nf];
-    if (!CURV) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        const S r = M.geo.rh[e * D + c];
-        const int fp = H::fpoint(q, c), qc = H::qa(q, c);
-        const S* jm = js + (t * NF + 2 * c) * nf * nfp + fp;
-        const S* jp = js + (t * NF + 2 * c + 1) * nf * nfp + fp;
-#pragma unroll
-        for (int f = 0; f < nf; ++f) Qv[c][f] = r * (dU[c][f] + Lp[qc] * jp[f * nfp] - Lm[qc] * jm[f * nfp]);
-      }
-    } else {
+    if (act) {
+      const int e = e0 + t;
       const S iJ = M.geo.iJ[(size_t)e * N + q];
 #pragma unroll
       for (int c = 0; c < D; ++c)
@@ -271,7 +348,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
         for (int f = 0; f < nf; ++f) {
           S s = 0;
 #pragma unroll
-          for (int b = 0; b < D; ++b) s += M.geo.Ja[(((size_t)e * D + b) * D + c) * N + q] * dU[b][f];
+          for (int b = 0; b < D; ++b)
+            s += M.geo.Ja[(((size_t)e * D + b) * D + c) * N + q] * qs[((t * D + b) * nf + f) * N + q];
           Qv[c][f] = s;
         }
 #pragma unroll
@@ -295,24 +373,47 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
 #pragma unroll
         for (int f = 0; f < nf; ++f) Qv[c][f] *= iJ;
     }
-    S* qd = Q + (size_t)e * D * H::STATE + q;
+    g_sync<V>();  // every D_b U has been read
+    if (act) {
 #pragma unroll
-    for (int c = 0; c < D; ++c)
+      for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        qs[((t * D + c) * nf + f) * N + q] = Qv[c][f];
-        qd[(c * nf + f) * N] = Qv[c][f];
-      }
+        for (int f = 0; f < nf; ++f) qs[((t * D + c) * nf + f) * N + q] = Qv[c][f];
+    }
+    g_sync<V>();
   }
-  __syncthreads();
+  {
+    S* qd = Q + (size_t)e0 * D * H::STATE;
+    for (int i = g_tid<V>(); i < nel * D * H::STATE; i += g_size<V>()) qd[i] = qs[i];
+  }
+  // traces of Q: one thread per (face direction a, component c, field, line)
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
+      const int line = i % nfp;
+      const int f = (i / nfp) % nf;
+      const int c = (i / (nfp * nf)) % D;
+      const int t = i / (nfp * nf * D);
+      const S* v = qs + ((t * D + c) * nf + f) * N;
+      S sm = 0, sp = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const S x = v[H::node(m, line, a)];
+        sm += lm[m] * x;
+        sp += lp[m] * x;
+      }
+      tq[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + line] = sm;
+      tq[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + line] = sp;
+    }
+  }
+  g_sync<V>();
   // own-face viscous fluxes
-  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
-    const int tt = i / (nfp * NF);
-    const int e = e0 + tt;
+    const int t = i / (nfp * NF);
+    const int e = e0 + t;
     const int a = face >> 1;
-    const S* l = (face & 1) ? lp : lm;
     S UL[nf], TQ[D][nf], nv[D];
     const S* tl = TU + ((size_t)e * NF + face) * nf * nfp + fp;
 #pragma unroll
@@ -320,13 +421,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        const S* v = qs + ((tt * D + c) * nf + f) * N;
-        S s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += l[m] * v[H::node(m, fp, a)];
-        TQ[c][f] = s;
-      }
+      for (int f = 0; f < nf; ++f) TQ[c][f] = tq[(((t * NF + face) * D + c) * nf + f) * nfp + fp];
     if (CURV) {
 #pragma unroll
       for (int c = 0; c < D; ++c) nv[c] = M.geo.SnE[(((size_t)e * NF + face) * D + c) * nfp + fp];
@@ -419,23 +514,52 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* fs = reinterpret_cast<S*>(smem_raw);   // [T][D][nf][N]  (reused for the next state's traces)
+  S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N]  (reused for the next state's traces)
   S* ffs = fs + T * D * H::STATE;            // [T][NF][nf][nfp]
   S* sDh = ffs + T * H::FACE;
   S* lm = sDh + n * n;
   S* lp = lm + n;
   S* Lm = lp + n;
   S* Lp = Lm + n;
-  const int e0 = blockIdx.x * T;
+  const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   {
     const S* src = FF + (size_t)e0 * H::FACE;
-    for (int i = threadIdx.x; i < nel * H::FACE; i += blockDim.x) ffs[i] = src[i];
+    for (int i = g_tid<V>(); i < nel * H::FACE; i += g_size<V>()) ffs[i] = src[i];
   }
-  load_tab<S>(M.tabs, P, nullptr, sDh, lm, lp, Lm, Lp, n);
-  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  load_tab<S, V>(M.tabs, P, nullptr, sDh, lm, lp, Lm, Lp, n);
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool active = t < nel;
   const int e = e0 + t;
+  // stage-update inputs, read early so their latency overlaps the flux work:
+  // pre = base + sum_{j<i} dt a_{i+1,j} k_j (or, at the last stage, the FP64
+  // state and sum_{j<i} dt b_j k_j), summed in the same order as before
+  S pre[nf];
+  double pre64[nf];
+  if (MODE == 1 && active) {
+    const size_t off = (size_t)e * H::STATE + q;
+    const double dt = st.dte ? st.dte[e] : st.dt;
+    if (!st.last) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S acc = st.base[off + f * N];
+        for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * st.k[j][off + f * N];
+        pre[f] = acc;
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        double un = st.Un[off + f * N];
+        S inc = S(0);
+        for (int j = 0; j < st.i; ++j) {
+          if (sizeof(S) == 8) un += (dt * st.cb[j]) * (double)st.k[j][off + f * N];
+          else inc += (S)(dt * st.cb[j]) * st.k[j][off + f * N];
+        }
+        pre64[f] = un;
+        pre[f] = inc;
+      }
+    }
+  }
   S Uq[nf];
   if (active) {
     const S* up = U + (size_t)e * H::STATE + q;
@@ -477,27 +601,38 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
       }
     }
   }
-  __syncthreads();
+  g_sync<V>();
+  // weak divergence + lift, one thread per line and direction, in place in fs
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+      int tt, f, line;
+      line_item<nf, nfp>(i, tt, f, line);
+      S* v = fs + ((tt * D + a) * nf + f) * N;
+      S x[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+      const S ffm = ffs[((tt * NF + 2 * a) * nf + f) * nfp + line];
+      const S ffp = ffs[((tt * NF + 2 * a + 1) * nf + f) * nfp + line];
+      const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        S s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += sDh[k * n + m] * x[m];
+        v[H::node(k, line, a)] = r * (s - Lm[k] * ffm - Lp[k] * ffp);
+      }
+    }
+  }
+  g_sync<V>();
   S res[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) res[f] = S(0);
   if (active) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int fp = H::fpoint(q, a), qa = H::qa(q, a);
-      const S cm = Lm[qa], cp = Lp[qa];
-      const S r = CURV ? S(1) : M.geo.rh[e * D + a];
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        const S* v = fs + ((t * D + a) * nf + f) * N;
-        S s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sDh[qa * n + m] * v[H::node(m, fp, a)];
-        s -= cm * ffs[((t * NF + 2 * a) * nf + f) * nfp + fp];
-        s -= cp * ffs[((t * NF + 2 * a + 1) * nf + f) * nfp + fp];
-        res[f] += r * s;
-      }
-    }
+      for (int f = 0; f < nf; ++f) res[f] += fs[((t * D + a) * nf + f) * N + q];
     if (CURV) {
       const S iJ = M.geo.iJ[(size_t)e * N + q];
 #pragma unroll
@@ -523,13 +658,10 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
     const size_t off = (size_t)e * H::STATE + q;
     const double dt = st.dte ? st.dte[e] : st.dt;
     if (!st.last) {
-      S ca[MAXSTAGES];
-      for (int j = 0; j <= st.i; ++j) ca[j] = (S)(dt * st.ca[j]);
+      const S ci = (S)(dt * st.ca[st.i]);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        S acc = st.base[off + f * N];
-        for (int j = 0; j < st.i; ++j) acc += ca[j] * st.k[j][off + f * N];
-        acc += ca[st.i] * res[f];
+        const S acc = pre[f] + ci * res[f];
         y[f] = acc;
         st.Kout[off + f * N] = res[f];
         st.Y[off + f * N] = acc;
@@ -537,14 +669,11 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
     } else {
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        double un = st.Un[off + f * N];
+        double un = pre64[f];
         if (sizeof(S) == 8) {
-          for (int j = 0; j < st.i; ++j) un += (dt * st.cb[j]) * (double)st.k[j][off + f * N];
           un += (dt * st.cb[st.i]) * (double)res[f];
         } else {
-          S inc = S(0);
-          for (int j = 0; j < st.i; ++j) inc += (S)(dt * st.cb[j]) * st.k[j][off + f * N];
-          inc += (S)(dt * st.cb[st.i]) * res[f];
+          const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
           un += (double)inc;
         }
         st.Un[off + f * N] = un;
@@ -553,12 +682,12 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
       }
     }
   }
-  __syncthreads();  // everyone is done with fs
+  g_sync<V>();  // everyone is done with fs
   if (active) {
 #pragma unroll
     for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
   }
-  __syncthreads();
+  g_sync<V>();
   tile_traces<D, P, S, V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
 }
 

@@ -1,0 +1,240 @@
+// Persistent, TMA-fed variants of the tile kernels (see pipe.cuh).
+//
+// Same arithmetic as kernels.cuh, but every contiguous per-tile input arrives
+// by cp.async.bulk into a double buffer while the previous tile is computed;
+// used whenever each block's bytes per element are a multiple of 16 (always
+// in 2D; in 3D for an even node count N).
+#pragma once
+#include "kernels.cuh"
+#include "pipe.cuh"
+
+namespace dgx {
+
+// Bounded-wait step shared by the persistent kernels: returns false (all
+// threads) if the copy of buffer b did not complete; then the kernel flags a
+// timeout and returns after a bounded wait for the other buffer's copies.
+__device__ __forceinline__ bool pipe_acquire(PipeState& ps, int b, uint32_t& par, bool other_pending,
+                                             uint32_t other_par, unsigned* flags) {
+  if (threadIdx.x == 0) ps.abort = !mbar_wait_bounded(&ps.bar[b], par);
+  __syncthreads();
+  if (ps.abort) {
+    if (threadIdx.x == 0) {
+      atomicOr(flags, 2u);
+      if (other_pending) mbar_wait_bounded(&ps.bar[b ^ 1], other_par);
+    }
+    return false;
+  }
+  mbar_try(&ps.bar[b], par);  // acquire the completed phase in every thread
+  par ^= 1u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// k_elem_p: persistent k_elem.  Buffer layout per tile (T-element strides):
+//   U [nf][N] | Q [D][nf][N] (VISC) | FF [NF][nf][nfp] | geometry (CURV: Ja, iJ)
+//   | stage: base [nf][N] | k_0 .. k_{i-1} | U_n (double, last stage)
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC, bool CURV, int MODE, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, TileIn in, S* __restrict__ out,
+                                                                 Stage<S> st, int ntiles) {
+  using H = Sh<D, P, V>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ PipeState ps;
+  const uint32_t buf_bytes = in.bytes_per_elem * T;
+  unsigned char* bufs[2] = {smem_raw, smem_raw + buf_bytes};
+  S* fs = reinterpret_cast<S*>(smem_raw + 2 * buf_bytes);  // [T][D][nf][N]
+  S* sDh = fs + T * D * H::STATE;
+  S* lm = sDh + n * n;
+  S* lp = lm + n;
+  S* Lm = lp + n;
+  S* Lp = Lm + n;
+  if (threadIdx.x == 0) {
+    mbar_init(&ps.bar[0], 1);
+    mbar_init(&ps.bar[1], 1);
+    fence_mbar_init();
+  }
+  load_tab<S>(M.tabs, P, nullptr, sDh, lm, lp, Lm, Lp, n);
+  __syncthreads();
+  int tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) tile_issue(in, tile * T, min(T, M.E - tile * T), T, bufs[0], &ps.bar[0]);
+  uint32_t par[2] = {0u, 0u};
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int b = k & 1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles)
+      tile_issue(in, next * T, min(T, M.E - next * T), T, bufs[b ^ 1], &ps.bar[b ^ 1]);
+    if (!pipe_acquire(ps, b, par[b], next < ntiles, par[b ^ 1], M.flags)) return;
+    const int e0 = tile * T;
+    const int nel = min(T, M.E - e0);
+    // views into the buffer
+    const S* Us = reinterpret_cast<const S*>(bufs[b]);
+    const S* Qs = Us + T * H::STATE;
+    const S* FFs = VISC ? Qs + T * D * H::STATE : Qs;
+    const S* geo = FFs + T * H::FACE;
+    const S* Jas = geo;                                   // [T][D][D][N]
+    const S* iJs = geo + T * D * D * N;                   // [T][N]
+    const S* stg = CURV ? iJs + T * N : geo;
+    const S* bases = stg;
+    const S* kss = bases + T * H::STATE;                  // k_j: [i][T][nf][N]
+    const double* Uns = reinterpret_cast<const double*>(kss + (size_t)st.i * T * H::STATE);
+    const int t = threadIdx.x / N, q = threadIdx.x % N;
+    const bool active = t < nel;
+    const int e = e0 + t;
+    S pre[nf];
+    double pre64[nf];
+    if (MODE == 1 && active) {
+      const int off = t * H::STATE + q;
+      const double dt = st.dte ? st.dte[e] : st.dt;
+      if (!st.last) {
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          S acc = bases[off + f * N];
+          for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * kss[(size_t)j * T * H::STATE + off + f * N];
+          pre[f] = acc;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          double un = Uns[off + f * N];
+          S inc = S(0);
+          for (int j = 0; j < st.i; ++j) {
+            const S kv = kss[(size_t)j * T * H::STATE + off + f * N];
+            if (sizeof(S) == 8) un += (dt * st.cb[j]) * (double)kv;
+            else inc += (S)(dt * st.cb[j]) * kv;
+          }
+          pre64[f] = un;
+          pre[f] = inc;
+        }
+      }
+    }
+    if (active) {
+      S Uq[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Uq[f] = Us[t * H::STATE + f * N + q];
+      S F[D][nf];
+      conv_flux_all<D, S>(Uq, M.gas, F);
+      if (VISC) {
+        S Qv[D][nf], Fv[D][nf];
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) Qv[c][f] = Qs[t * D * H::STATE + (c * nf + f) * N + q];
+        visc_flux_all<D, S>(Uq, Qv, M.gas, Fv);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) F[c][f] -= Fv[c][f];
+      }
+      if (!CURV) {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = F[a][f];
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          S ja[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) ja[c] = Jas[((t * D + a) * D + c) * N + q];
+#pragma unroll
+          for (int f = 0; f < nf; ++f) {
+            S s = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += ja[c] * F[c][f];
+            fs[((t * D + a) * nf + f) * N + q] = s;
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      for (int i = threadIdx.x; i < nel * nf * nfp; i += blockDim.x) {
+        int tt, f, line;
+        line_item<nf, nfp>(i, tt, f, line);
+        S* v = fs + ((tt * D + a) * nf + f) * N;
+        S x[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+        const S ffm = FFs[((tt * NF + 2 * a) * nf + f) * nfp + line];
+        const S ffp = FFs[((tt * NF + 2 * a + 1) * nf + f) * nfp + line];
+        const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
+#pragma unroll
+        for (int kk = 0; kk < n; ++kk) {
+          S s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += sDh[kk * n + m] * x[m];
+          v[H::node(kk, line, a)] = r * (s - Lm[kk] * ffm - Lp[kk] * ffp);
+        }
+      }
+    }
+    __syncthreads();
+    S res[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) res[f] = S(0);
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) res[f] += fs[((t * D + a) * nf + f) * N + q];
+      if (CURV) {
+        const S iJ = iJs[t * N + q];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) res[f] *= iJ;
+      }
+      bool bad = false;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) bad |= !isfinite(res[f]);
+      if (bad) atomicOr(M.flags, 1u);
+    }
+    if (MODE == 0) {
+      if (active) {
+        S* op = out + (size_t)e * H::STATE + q;
+#pragma unroll
+        for (int f = 0; f < nf; ++f) op[f * N] = res[f];
+      }
+      __syncthreads();  // buffer and fs free for the next tile
+      continue;
+    }
+    S y[nf];
+    if (active) {
+      const size_t off = (size_t)e * H::STATE + q;
+      const double dt = st.dte ? st.dte[e] : st.dt;
+      if (!st.last) {
+        const S ci = (S)(dt * st.ca[st.i]);
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          const S acc = pre[f] + ci * res[f];
+          y[f] = acc;
+          st.Kout[off + f * N] = res[f];
+          st.Y[off + f * N] = acc;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          double un = pre64[f];
+          if (sizeof(S) == 8) {
+            un += (dt * st.cb[st.i]) * (double)res[f];
+          } else {
+            const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
+            un += (double)inc;
+          }
+          st.Un[off + f * N] = un;
+          y[f] = (S)un;
+          if (st.shadow) st.shadow[off + f * N] = y[f];
+        }
+      }
+    }
+    __syncthreads();  // everyone is done with fs
+    if (active) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
+    }
+    __syncthreads();
+    tile_traces<D, P, S, V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
+    __syncthreads();  // buffer and fs free for the next tile
+  }
+}
+
+}  // namespace dgx

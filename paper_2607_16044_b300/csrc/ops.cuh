@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "kernels_p.cuh"
 
 namespace dgx {
 
@@ -34,30 +35,36 @@ template <int D, int P, typename S>
 struct Ops {
   template <int V>
   using H = Sh<D, P, V>;
+  // dynamic shared memory of one CTA (all of its element groups)
   template <int V>
   static size_t smem_trace() {
-    return sizeof(S) * (H<V>::T * H<V>::STATE + 2 * H<V>::n);
+    return H<V>::GROUPS * smem_trace_g<D, P, S, V>();
   }
   template <int V>
   static size_t smem_br1() {
-    using h = H<V>;
-    return sizeof(S) * (h::T * h::STATE + h::T * h::FACE + h::T * D * h::STATE + h::n * h::n + 4 * h::n);
+    return H<V>::GROUPS * smem_br1_g<D, P, S, V>();
   }
   template <int V>
   static size_t smem_elem() {
-    using h = H<V>;
-    return sizeof(S) * (h::T * D * h::STATE + h::T * h::FACE + h::n * h::n + 4 * h::n);
+    return H<V>::GROUPS * smem_elem_g<D, P, S, V>();
   }
   template <int V>
   static int blocks(int E) {
-    return (E + H<V>::T - 1) / H<V>::T;
+    return H<V>::WARP ? (E + WPB - 1) / WPB : (E + H<V>::T - 1) / H<V>::T;
   }
-  // shared memory of a tile kernel kind (0 trace, 1 br1, 2 elem) for variant V
+  // shared memory of a tile kernel kind (0 trace, 1 br1, 2 elem) for variant V;
+  // a variant that cannot run here reports SIZE_MAX
+  template <int V>
+  static size_t smem_v(int kind) {
+    if (!H<V>::VALID) return (size_t)-1;
+    return kind == 0 ? smem_trace<V>() : kind == 1 ? smem_br1<V>() : smem_elem<V>();
+  }
   static size_t smem(int kind, int V) {
     switch (V) {
-      case 0: return kind == 0 ? smem_trace<0>() : kind == 1 ? smem_br1<0>() : smem_elem<0>();
-      case 1: return kind == 0 ? smem_trace<1>() : kind == 1 ? smem_br1<1>() : smem_elem<1>();
-      default: return kind == 0 ? smem_trace<2>() : kind == 1 ? smem_br1<2>() : smem_elem<2>();
+      case 0: return smem_v<0>(kind);
+      case 1: return smem_v<1>(kind);
+      case 2: return smem_v<2>(kind);
+      default: return smem_v<3>(kind);
     }
   }
 
@@ -73,7 +80,8 @@ struct Ops {
   static cudaError_t trace(const Mesh<S>& M, int V, const Sin* U, S* TU, S* shadow, cudaStream_t st) {
     if (V == 0) return trace_v<Sin, 0>(M, U, TU, shadow, st);
     if (V == 1) return trace_v<Sin, 1>(M, U, TU, shadow, st);
-    return trace_v<Sin, 2>(M, U, TU, shadow, st);
+    if (V == 2) return trace_v<Sin, 2>(M, U, TU, shadow, st);
+    return trace_v<Sin, 3>(M, U, TU, shadow, st);
   }
 
   template <bool CURV, int V>
@@ -88,11 +96,13 @@ struct Ops {
     if (curv) {
       if (V == 0) return br1_v<true, 0>(M, U, w, st);
       if (V == 1) return br1_v<true, 1>(M, U, w, st);
-      return br1_v<true, 2>(M, U, w, st);
+      if (V == 2) return br1_v<true, 2>(M, U, w, st);
+      return br1_v<true, 3>(M, U, w, st);
     }
     if (V == 0) return br1_v<false, 0>(M, U, w, st);
     if (V == 1) return br1_v<false, 1>(M, U, w, st);
-    return br1_v<false, 2>(M, U, w, st);
+    if (V == 2) return br1_v<false, 2>(M, U, w, st);
+    return br1_v<false, 3>(M, U, w, st);
   }
 
   static cudaError_t face(const Mesh<S>& M, bool visc, bool curv, const Work& w, cudaStream_t st) {
@@ -126,8 +136,76 @@ struct Ops {
                             cudaStream_t st) {
     if (V == 0) return elem_v<MODE, VISC, CURV, 0>(M, U, w, out, sa, st);
     if (V == 1) return elem_v<MODE, VISC, CURV, 1>(M, U, w, out, sa, st);
-    return elem_v<MODE, VISC, CURV, 2>(M, U, w, out, sa, st);
+    if (V == 2) return elem_v<MODE, VISC, CURV, 2>(M, U, w, out, sa, st);
+    return elem_v<MODE, VISC, CURV, 3>(M, U, w, out, sa, st);
   }
+  // ---- persistent TMA-fed element kernel
+  template <int MODE, bool VISC, bool CURV, int V>
+  static cudaError_t elem_p_v(const Mesh<S>& M, const TileIn& in, S* out, const Stage<S>& sa, int nsm,
+                              cudaStream_t st, bool& used) {
+    using h = H<V>;
+    const size_t smem = 2 * (size_t)h::T * in.bytes_per_elem + sizeof(S) * (h::T * D * h::STATE + h::n * h::n + 4 * h::n);
+    if (smem + sizeof(PipeState) > SMEM_LIMIT) {  // static pipeline state shares the per-CTA limit
+      used = false;
+      return cudaSuccess;
+    }
+    auto k = k_elem_p<D, P, S, VISC, CURV, MODE, V>;
+    static size_t raised = 48 * 1024;  // dynamic shared memory allowed so far for this kernel
+    if (smem > raised) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        used = false;
+        return cudaSuccess;
+      }
+      raised = smem;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, h::THREADS, smem) != cudaSuccess || occ < 1) {
+      used = false;
+      return cudaSuccess;
+    }
+    const int ntiles = blocks<V>(M.E);
+    const int grid = ntiles < nsm * occ ? ntiles : nsm * occ;
+    k<<<grid, h::THREADS, smem, st>>>(M, in, out, sa, ntiles);
+    used = true;
+    return cudaGetLastError();
+  }
+  template <int MODE, bool VISC, bool CURV>
+  static cudaError_t elem_p_c(const Mesh<S>& M, int V, const TileIn& in, S* out, const Stage<S>& sa, int nsm,
+                              cudaStream_t st, bool& used) {
+    if (V == 0) return elem_p_v<MODE, VISC, CURV, 0>(M, in, out, sa, nsm, st, used);
+    if (V == 1) return elem_p_v<MODE, VISC, CURV, 1>(M, in, out, sa, nsm, st, used);
+    if (V == 2) return elem_p_v<MODE, VISC, CURV, 2>(M, in, out, sa, nsm, st, used);
+    used = false;  // the warp-per-element variant has no persistent form
+    return cudaSuccess;
+  }
+  // Tries the persistent kernel; used = false (nothing launched) when a block
+  // cannot be streamed or the buffers do not fit.
+  template <int MODE>
+  static cudaError_t elem_pipe(const Mesh<S>& M, int V, bool visc, bool curv, const S* U, const Work& w, S* out,
+                               const Stage<S>& sa, int nsm, cudaStream_t st, bool& used) {
+    using h = Sh<D, P>;
+    const size_t s = sizeof(S);
+    TileIn in{};
+    bool ok = tilein_add(in, U, h::STATE * s);
+    if (visc) ok = ok && tilein_add(in, w.Q, D * h::STATE * s);
+    ok = ok && tilein_add(in, w.FF, h::FACE * s);
+    if (curv) ok = ok && tilein_add(in, M.geo.Ja, D * D * h::N * s) && tilein_add(in, M.geo.iJ, h::N * s);
+    if (MODE == 1) {
+      ok = ok && tilein_add(in, sa.base, h::STATE * s);
+      for (int j = 0; j < sa.i; ++j) ok = ok && tilein_add(in, sa.k[j], h::STATE * s);
+      if (sa.last) ok = ok && tilein_add(in, sa.Un, h::STATE * sizeof(double));
+    }
+    used = false;
+    if (!ok) return cudaSuccess;
+    if (visc) {
+      if (curv) return elem_p_c<MODE, true, true>(M, V, in, out, sa, nsm, st, used);
+      return elem_p_c<MODE, true, false>(M, V, in, out, sa, nsm, st, used);
+    }
+    if (curv) return elem_p_c<MODE, false, true>(M, V, in, out, sa, nsm, st, used);
+    return elem_p_c<MODE, false, false>(M, V, in, out, sa, nsm, st, used);
+  }
+
   template <int MODE>
   static cudaError_t elem(const Mesh<S>& M, int V, bool visc, bool curv, const S* U, const Work& w, S* out,
                           const Stage<S>& sa, cudaStream_t st) {

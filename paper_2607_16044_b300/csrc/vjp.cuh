@@ -34,6 +34,23 @@ struct VjpWork {
   void* Qb;   // gradient cotangents              [E][D][nf][N]
 };
 
+template <int D, int P, typename S, int V>
+constexpr size_t smem_velem_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (h::T * (D + 1) * h::STATE + h::n * h::n + 2 * h::n));
+}
+template <int D, int P, typename S, int V>
+constexpr size_t smem_vbr1_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (2 * h::T * D * h::STATE + 2 * h::T * h::NF * D * h::nf * h::nfp + h::T * h::FACE +
+                          h::n * h::n + 4 * h::n));
+}
+template <int D, int P, typename S, int V>
+constexpr size_t smem_vgather_g() {
+  using h = Sh<D, P, V>;
+  return r16(sizeof(S) * (h::T * h::FACE + 2 * h::n));
+}
+
 // Cotangent source of the element kernel: mu = c_lam * lam + sum_j c_j nu_j.
 template <typename S>
 struct Cot {
@@ -59,19 +76,35 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* mus = reinterpret_cast<S*>(smem_raw);  // [T][nf][N]
-  S* sDh = mus + T * H::STATE;
+  S* mus = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_velem_g<D, P, S, V>()));  // [T][nf][N]     cotangent / J
+  S* fb = mus + T * H::STATE;                // [T][D][nf][N]  contravariant flux cotangents
+  S* sDh = fb + T * D * H::STATE;
   S* Lm = sDh + n * n;
   S* Lp = Lm + n;
-  const int e0 = blockIdx.x * T;
+  const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S>(M.tabs, P, nullptr, sDh, nullptr, nullptr, Lm, Lp, n);
+  load_tab<S, V>(M.tabs, P, nullptr, sDh, nullptr, nullptr, Lm, Lp, n);
+  // per-node inputs of the pointwise adjoint, read first (latency overlaps the contractions)
+  const int tn = g_tid<V>() / N, qn = g_tid<V>() % N;
+  S Uq[nf], Qv[VISC ? D : 1][nf];
+  if (tn < nel) {
+    const S* up = U + (size_t)(e0 + tn) * H::STATE + qn;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) Uq[f] = up[f * N];
+    if (VISC) {
+      const S* qp = Q + (size_t)(e0 + tn) * D * H::STATE + qn;
+#pragma unroll
+      for (int c = 0; c < (VISC ? D : 1); ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) Qv[c][f] = qp[(c * nf + f) * N];
+    }
+  }
   {
     const size_t base = (size_t)e0 * H::STATE;
-    for (int i = threadIdx.x; i < nel * H::STATE; i += blockDim.x) {
+    for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) {
       double v = 0.0;
       if (cot.lam) v += cot.c_lam * (double)cot.lam[base + i];
-      if (cot.lam64) v += cot.c_lam * cot.lam64[base + i];
+      if (cot.lam64 && cot.c_lam != 0.0) v += cot.c_lam * cot.lam64[base + i];
       for (int j = 0; j < cot.n_nu; ++j) v += cot.c_nu[j] * (double)cot.nu[j][base + i];
       S s = (S)v;
       if (CURV) {
@@ -81,45 +114,45 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
       mus[i] = s;
     }
   }
-  __syncthreads();
-  // Fhat_bar[face][f][fp] = -rr_a sum_m L_side[m] mu[f](node(m, fp, a))   (output order)
-  {
-    S* dst = FFb + (size_t)e0 * H::FACE;
-    for (int i = threadIdx.x; i < nel * H::FACE; i += blockDim.x) {
-      const int fp = i % nfp;
-      int r = i / nfp;
-      const int f = r % nf;
-      r /= nf;
-      const int face = r % NF;
-      const int t = r / NF;
-      const int a = face >> 1;
-      const S* L = (face & 1) ? Lp : Lm;
-      const S* v = mus + (t * nf + f) * N;
-      S acc = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) acc += L[m] * v[H::node(m, fp, a)];
-      const S rr = CURV ? S(1) : M.geo.rh[(e0 + t) * D + a];
-      dst[i] = -rr * acc;
-    }
-  }
-  const int t = threadIdx.x / N, q = threadIdx.x % N;
-  if (t >= nel) return;
-  const int e = e0 + t;
-  // contravariant flux cotangent Ft_bar_a(q) = rr_a sum_m Dh[m][q_a] mu(node(m, fp_a(q), a))
-  S Fb[D][nf];
+  g_sync<V>();
+  // one thread per line and direction: transposed weak divergence
+  //   Ft_bar_a(m) = rr_a sum_k Dh[k][m] mu(k)   -> fb
+  // and transposed lift  Fhat_bar(a, side) = -rr_a sum_k L_side[k] mu(k) -> FFb
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const int fp = H::fpoint(q, a), qa = H::qa(q, a);
-    const S rr = CURV ? S(1) : M.geo.rh[e * D + a];
+    for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+      int tt, f, line;
+      line_item<nf, nfp>(i, tt, f, line);
+      const S* v = mus + (tt * nf + f) * N;
+      S x[n];
 #pragma unroll
-    for (int f = 0; f < nf; ++f) {
-      const S* v = mus + (t * nf + f) * N;
-      S s = 0;
+      for (int k = 0; k < n; ++k) x[k] = v[H::node(k, line, a)];
+      const S rr = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
+      S* fo = fb + ((tt * D + a) * nf + f) * N;
+      S sm = 0, sp = 0;
 #pragma unroll
-      for (int m = 0; m < n; ++m) s += sDh[m * n + qa] * v[H::node(m, fp, a)];
-      Fb[a][f] = rr * s;
+      for (int m = 0; m < n; ++m) {
+        S acc = 0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc += sDh[k * n + m] * x[k];
+        fo[H::node(m, line, a)] = rr * acc;
+        sm += Lm[m] * x[m];
+        sp += Lp[m] * x[m];
+      }
+      S* dst = FFb + (size_t)(e0 + tt) * H::FACE + f * nfp + line;
+      dst[(2 * a) * nf * nfp] = -rr * sm;
+      dst[(2 * a + 1) * nf * nfp] = -rr * sp;
     }
   }
+  g_sync<V>();
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
+  if (t >= nel) return;
+  const int e = e0 + t;
+  S Fb[D][nf];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int f = 0; f < nf; ++f) Fb[a][f] = fb[((t * D + a) * nf + f) * N + q];
   if (CURV) {  // physical flux cotangent F_bar_c = sum_a Ja[a][c] Ft_bar_a
     S Fc[D][nf];
 #pragma unroll
@@ -139,26 +172,21 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 #pragma unroll
       for (int f = 0; f < nf; ++f) Fb[c][f] = Fc[c][f];
   }
-  S Uq[nf], Ubq[nf];
-  const S* up = U + (size_t)e * H::STATE + q;
+  S Ubq[nf];
 #pragma unroll
-  for (int f = 0; f < nf; ++f) {
-    Uq[f] = up[f * N];
-    Ubq[f] = S(0);
-  }
+  for (int f = 0; f < nf; ++f) Ubq[f] = S(0);
   conv_flux_all_vjp<D, S>(Uq, Fb, M.gas, Ubq);
   if (VISC) {  // F = F^c - F^nu
-    S Qv[D][nf], Qbv[D][nf], Fm[D][nf];
-    const S* qp = Q + (size_t)e * D * H::STATE + q;
+    S Qbv[D][nf], Fm[D][nf], Qd[D][nf];
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        Qv[c][f] = qp[(c * nf + f) * N];
+        Qd[c][f] = Qv[VISC ? c : 0][f];
         Qbv[c][f] = S(0);
         Fm[c][f] = -Fb[c][f];
       }
-    visc_flux_all_vjp<D, S>(Uq, Qv, Fm, M.gas, Ubq, Qbv);
+    visc_flux_all_vjp<D, S>(Uq, Qd, Fm, M.gas, Ubq, Qbv);
     S* qb = Qb + (size_t)e * D * H::STATE + q;
 #pragma unroll
     for (int c = 0; c < D; ++c)
@@ -246,36 +274,59 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
                                                                   S* __restrict__ JB, S* __restrict__ Ub) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  constexpr int TQS = NF * D * nf * nfp;      // traces of Q per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* qs = reinterpret_cast<S*>(smem_raw);   // [T][D][nf][N]  forward Q, later dU_bar
+  S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V>()));   // [T][D][nf][N]  forward Q, later dU_bar and D^T dU_bar
   S* qbs = qs + T * D * H::STATE;            // [T][D][nf][N]  Q_bar (total), later P
-  S* tqb = qbs + T * D * H::STATE;           // [T][NF][D][nf][nfp] TQ_bar
-  S* tub = tqb + T * NF * D * nf * nfp;      // [T][NF][nf][nfp] own TU_bar
+  S* tq = qbs + T * D * H::STATE;            // [T][NF][D][nf][nfp] traces of Q, later J_bar [T][NF][nf][nfp]
+  S* tqb = tq + T * TQS;                     // [T][NF][D][nf][nfp] TQ_bar
+  S* tub = tqb + T * TQS;                    // [T][NF][nf][nfp] own TU_bar
   S* sD = tub + T * H::FACE;
   S* lm = sD + n * n;
   S* lp = lm + n;
   S* Lm = lp + n;
   S* Lp = Lm + n;
-  const int e0 = blockIdx.x * T;
+  S* js = tq;
+  const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
+  load_tab<S, V>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
   {
     const S* qsrc = Q + (size_t)e0 * D * H::STATE;
     const S* qbsrc = Qb + (size_t)e0 * D * H::STATE;
-    for (int i = threadIdx.x; i < nel * D * H::STATE; i += blockDim.x) {
+    for (int i = g_tid<V>(); i < nel * D * H::STATE; i += g_size<V>()) {
       qs[i] = qsrc[i];
       qbs[i] = qbsrc[i];
     }
   }
-  __syncthreads();
+  g_sync<V>();
+  // 0. traces of Q (line pass)
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
+      const int line = i % nfp;
+      const int f = (i / nfp) % nf;
+      const int c = (i / (nfp * nf)) % D;
+      const int t = i / (nfp * nf * D);
+      const S* v = qs + ((t * D + c) * nf + f) * N;
+      S sm = 0, sp = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const S x = v[H::node(m, line, a)];
+        sm += lm[m] * x;
+        sp += lp[m] * x;
+      }
+      tq[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + line] = sm;
+      tq[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + line] = sp;
+    }
+  }
+  g_sync<V>();
   // 1. viscous face-flux adjoint at every own face point
-  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int t = i / (nfp * NF);
     const int e = e0 + t;
     const int a = face >> 1;
-    const S* l = (face & 1) ? lp : lm;
     const size_t o = ((size_t)e * NF + face) * nf * nfp + fp;
     S UL[nf], TQ[D][nf], nv[D], gb[nf], ubf[nf], tqbv[D][nf];
 #pragma unroll
@@ -288,11 +339,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        const S* v = qs + ((t * D + c) * nf + f) * N;
-        S s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += l[m] * v[H::node(m, fp, a)];
-        TQ[c][f] = s;
+        TQ[c][f] = tq[(((t * NF + face) * D + c) * nf + f) * nfp + fp];
         tqbv[c][f] = S(0);
       }
     if (CURV) {
@@ -313,9 +360,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
       for (int f = 0; f < nf; ++f) tqb[(((t * NF + face) * D + c) * nf + f) * nfp + fp] = tqbv[c][f];
   }
-  __syncthreads();
+  g_sync<V>();
   // 2. Q_bar += transposed traces of TQ_bar; then P = (iJ) Q_bar in place
-  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool active = t < nel;
   const int e = e0 + t;
   if (active) {
@@ -334,7 +381,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         qbs[((t * D + c) * nf + f) * N + q] = s * iJ;
       }
   }
-  __syncthreads();
+  g_sync<V>();
   // 3. dU_bar_b(q) = (box) r_b P_b  |  (curv) sum_c Ja[b][c] P_c   -> qs (forward Q no longer needed)
   if (active) {
 #pragma unroll
@@ -353,57 +400,84 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         qs[((t * D + b) * nf + f) * N + q] = s;
       }
   }
-  __syncthreads();
-  // 4. U_bar += sum_b D_b^T dU_bar_b
+  g_sync<V>();
+  // 4. line passes: D_b^T dU_bar_b in place (qs), and the jump cotangents J_bar (js)
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+      int tt, f, line;
+      line_item<nf, nfp>(i, tt, f, line);
+      S* v = qs + ((tt * D + b) * nf + f) * N;
+      S x[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) x[k] = v[H::node(k, line, b)];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        S acc = 0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) acc += sD[k * n + m] * x[k];
+        v[H::node(m, line, b)] = acc;
+      }
+      // J_bar on the two faces normal to b: box: +-r_b sum_m L(+-)[m] P_b(m);
+      // curvilinear: sum_c Sn_c sum_m L(+-)[m] P_c(m)
+      S jm = 0, jp = 0;
+      if (CURV) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          const S* pc = qbs + ((tt * D + c) * nf + f) * N;
+          S sm = 0, sp = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) {
+            const S y = pc[H::node(m, line, b)];
+            sm += Lm[m] * y;
+            sp += Lp[m] * y;
+          }
+          const size_t ge = (size_t)(e0 + tt) * NF;
+          jm += M.geo.SnE[((ge + 2 * b) * D + c) * nfp + line] * sm;
+          jp += M.geo.SnE[((ge + 2 * b + 1) * D + c) * nfp + line] * sp;
+        }
+      } else {
+        const S* pb = qbs + ((tt * D + b) * nf + f) * N;
+        S sm = 0, sp = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const S y = pb[H::node(m, line, b)];
+          sm += Lm[m] * y;
+          sp += Lp[m] * y;
+        }
+        const S r = M.geo.rh[(e0 + tt) * D + b];
+        jm = -r * sm;
+        jp = r * sp;
+      }
+      js[((tt * NF + 2 * b) * nf + f) * nfp + line] = jm;
+      js[((tt * NF + 2 * b + 1) * nf + f) * nfp + line] = jp;
+    }
+  }
+  g_sync<V>();
+  // 5. U_bar += sum_b D_b^T dU_bar_b
   if (active) {
     S* ub = Ub + (size_t)e * H::STATE + q;
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       S s = 0;
 #pragma unroll
-      for (int b = 0; b < D; ++b) {
-        const int fp = H::fpoint(q, b), qb = H::qa(q, b);
-        const S* v = qs + ((t * D + b) * nf + f) * N;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += sD[m * n + qb] * v[H::node(m, fp, b)];
-      }
+      for (int b = 0; b < D; ++b) s += qs[((t * D + b) * nf + f) * N + q];
       ub[f * N] += s;
     }
   }
-  // 5. jump cotangents J_bar[face][f][fp] and the own trace cotangent
-  for (int i = threadIdx.x; i < nel * NF * nfp; i += blockDim.x) {
+  // 6. the own trace cotangent and the neighbour's share of each jump
+  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int tt = i / (nfp * NF);
     const int ee = e0 + tt;
-    const int a = face >> 1;
-    const S* L = (face & 1) ? Lp : Lm;
-    S jb[nf];
+    const size_t o = ((size_t)ee * NF + face) * nf * nfp + fp;
+    S jb[nf], ubf[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
-      S s = 0;
-      if (CURV) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const S sn = M.geo.SnE[(((size_t)ee * NF + face) * D + c) * nfp + fp];
-          const S* v = qbs + ((tt * D + c) * nf + f) * N;
-          S sc = 0;
-#pragma unroll
-          for (int m = 0; m < n; ++m) sc += L[m] * v[H::node(m, fp, a)];
-          s += sn * sc;
-        }
-      } else {
-        const S* v = qbs + ((tt * D + a) * nf + f) * N;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += L[m] * v[H::node(m, fp, a)];
-        s *= M.geo.rh[ee * D + a] * ((face & 1) ? S(1) : S(-1));
-      }
-      jb[f] = s;
+      jb[f] = js[((tt * NF + face) * nf + f) * nfp + fp];
+      ubf[f] = tub[((tt * NF + face) * nf + f) * nfp + fp];
     }
-    const size_t o = ((size_t)ee * NF + face) * nf * nfp + fp;
-    S ubf[nf];
-#pragma unroll
-    for (int f = 0; f < nf; ++f) ubf[f] = tub[((tt * NF + face) * nf + f) * nfp + fp];
     if (M.nb[ee * NF + face] >= 0) {
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
@@ -432,33 +506,40 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* tub = reinterpret_cast<S*>(smem_raw);  // [T][NF][nf][nfp]
+  S* tub = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vgather_g<D, P, S, V>()));  // [T][NF][nf][nfp]
   S* lm = tub + T * H::FACE;
   S* lp = lm + n;
-  const int e0 = blockIdx.x * T;
+  const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);
+  load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);
   {
     const S* src = TUb + (size_t)e0 * H::FACE;
-    for (int i = threadIdx.x; i < nel * H::FACE; i += blockDim.x) {
-      S v = src[i];
-      if (VISC) {
+    if (!VISC) {
+      for (int i = g_tid<V>(); i < nel * H::FACE; i += g_size<V>()) tub[i] = src[i];
+    } else {
+      // own trace cotangent plus half the neighbour's jump cotangent, per face point
+      for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
         const int fp = i % nfp;
-        const int f = (i / nfp) % nf;
-        const int face = (i / (nfp * nf)) % NF;
-        const int t = i / H::FACE;
+        const int face = (i / nfp) % NF;
+        const int t = i / (nfp * NF);
         const int e = e0 + t;
-        const int nbe = M.nb[e * NF + face];
+        const int k = e * NF + face;
+        const int nbe = M.nb[k];
+        const int o = (t * NF + face) * nf * nfp + fp;
         if (nbe >= 0) {
-          const int fpn = orient_map<D, n>(M.ori[e * NF + face], fp);
-          v += S(0.5) * JB[(((size_t)nbe * NF + M.nbf[e * NF + face]) * nf + f) * nfp + fpn];
+          const int fpn = orient_map<D, n>(M.ori[k], fp);
+          const S* jb = JB + (((size_t)nbe * NF + M.nbf[k]) * nf) * nfp + fpn;
+#pragma unroll
+          for (int f = 0; f < nf; ++f) tub[o + f * nfp] = src[o + f * nfp] + S(0.5) * jb[f * nfp];
+        } else {
+#pragma unroll
+          for (int f = 0; f < nf; ++f) tub[o + f * nfp] = src[o + f * nfp];
         }
       }
-      tub[i] = v;
     }
   }
-  __syncthreads();
-  const int t = threadIdx.x / N, q = threadIdx.x % N;
+  g_sync<V>();
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   if (t >= nel) return;
   const int e = e0 + t;
   const size_t off = (size_t)e * H::STATE + q;
@@ -487,28 +568,32 @@ struct VjpOps {
   using H = Sh<D, P, V>;
   template <int V>
   static size_t smem_elem() {
-    return sizeof(S) * (H<V>::T * H<V>::STATE + H<V>::n * H<V>::n + 2 * H<V>::n);
+    return H<V>::GROUPS * smem_velem_g<D, P, S, V>();
   }
   template <int V>
   static size_t smem_br1() {
-    using h = H<V>;
-    return sizeof(S) * (2 * h::T * D * h::STATE + h::T * h::NF * D * h::nf * h::nfp + h::T * h::FACE +
-                        h::n * h::n + 4 * h::n);
+    return H<V>::GROUPS * smem_vbr1_g<D, P, S, V>();
   }
   template <int V>
   static size_t smem_gather() {
-    return sizeof(S) * (H<V>::T * H<V>::FACE + 2 * H<V>::n);
+    return H<V>::GROUPS * smem_vgather_g<D, P, S, V>();
   }
   template <int V>
   static int blocks(int E) {
-    return (E + H<V>::T - 1) / H<V>::T;
+    return H<V>::WARP ? (E + WPB - 1) / WPB : (E + H<V>::T - 1) / H<V>::T;
   }
-  // 0 elem, 1 br1, 2 gather
+  // 0 elem, 1 br1, 2 gather; SIZE_MAX if the variant cannot run here
+  template <int V>
+  static size_t smem_v(int kind) {
+    if (!H<V>::VALID) return (size_t)-1;
+    return kind == 0 ? smem_elem<V>() : kind == 1 ? smem_br1<V>() : smem_gather<V>();
+  }
   static size_t smem(int kind, int V) {
     switch (V) {
-      case 0: return kind == 0 ? smem_elem<0>() : kind == 1 ? smem_br1<0>() : smem_gather<0>();
-      case 1: return kind == 0 ? smem_elem<1>() : kind == 1 ? smem_br1<1>() : smem_gather<1>();
-      default: return kind == 0 ? smem_elem<2>() : kind == 1 ? smem_br1<2>() : smem_gather<2>();
+      case 0: return smem_v<0>(kind);
+      case 1: return smem_v<1>(kind);
+      case 2: return smem_v<2>(kind);
+      default: return smem_v<3>(kind);
     }
   }
 
@@ -526,7 +611,8 @@ struct VjpOps {
                             cudaStream_t st) {
     if (V == 0) return elem_v<VISC, CURV, 0>(M, U, w, c, Ub, st);
     if (V == 1) return elem_v<VISC, CURV, 1>(M, U, w, c, Ub, st);
-    return elem_v<VISC, CURV, 2>(M, U, w, c, Ub, st);
+    if (V == 2) return elem_v<VISC, CURV, 2>(M, U, w, c, Ub, st);
+    return elem_v<VISC, CURV, 3>(M, U, w, c, Ub, st);
   }
   static cudaError_t elem(const Mesh<S>& M, int V, bool visc, bool curv, const S* U, const VjpWork& w,
                           const Cot<S>& c, S* Ub, cudaStream_t st) {
@@ -565,11 +651,13 @@ struct VjpOps {
     if (curv) {
       if (V == 0) return br1_v<true, 0>(M, w, Ub, st);
       if (V == 1) return br1_v<true, 1>(M, w, Ub, st);
-      return br1_v<true, 2>(M, w, Ub, st);
+      if (V == 2) return br1_v<true, 2>(M, w, Ub, st);
+      return br1_v<true, 3>(M, w, Ub, st);
     }
     if (V == 0) return br1_v<false, 0>(M, w, Ub, st);
     if (V == 1) return br1_v<false, 1>(M, w, Ub, st);
-    return br1_v<false, 2>(M, w, Ub, st);
+    if (V == 2) return br1_v<false, 2>(M, w, Ub, st);
+    return br1_v<false, 3>(M, w, Ub, st);
   }
 
   template <bool VISC, int V>
@@ -585,11 +673,13 @@ struct VjpOps {
     if (visc) {
       if (V == 0) return gather_v<true, 0>(M, w, g, c, st);
       if (V == 1) return gather_v<true, 1>(M, w, g, c, st);
-      return gather_v<true, 2>(M, w, g, c, st);
+      if (V == 2) return gather_v<true, 2>(M, w, g, c, st);
+      return gather_v<true, 3>(M, w, g, c, st);
     }
     if (V == 0) return gather_v<false, 0>(M, w, g, c, st);
     if (V == 1) return gather_v<false, 1>(M, w, g, c, st);
-    return gather_v<false, 2>(M, w, g, c, st);
+    if (V == 2) return gather_v<false, 2>(M, w, g, c, st);
+    return gather_v<false, 3>(M, w, g, c, st);
   }
 };
 

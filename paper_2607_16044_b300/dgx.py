@@ -44,7 +44,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc",
            "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
-           "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune"]
+           "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline"]
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_stage_bytes.argtypes = [vp]
     lib.dgx_kernel_work.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.dgx_autotune.argtypes = [vp, vp, i32, vp]
+    lib.dgx_set_pipeline.argtypes = [vp, i32]
     lib.dgx_get_variants.argtypes = [vp, ctypes.POINTER(i32)]
     lib.dgx_set_variants.argtypes = [vp, ctypes.POINTER(i32)]
     lib.dgx_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
@@ -302,6 +303,10 @@ class Solver:
         _check(self.lib.dgx_autotune(self.h, self._state(U64, "U64", torch.float64), int(reps),
                                      _stream_ptr(stream)), "dgx_autotune")
         return self.variants()
+
+    def set_pipeline(self, enable: bool):
+        """Select the persistent TMA-fed kernels (default) or the one-CTA-per-tile ones."""
+        _check(self.lib.dgx_set_pipeline(self.h, int(enable)), "dgx_set_pipeline")
 
     def variants(self) -> dict:
         v = (ctypes.c_int32 * len(KERNELS))()

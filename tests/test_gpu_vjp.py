@@ -208,3 +208,51 @@ def test_ark_adjoint_step_euler_periodic_fp32():
     err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
     record("ark-adjoint-fp32", rel=err)
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("case", ["2d-p2-euler", "2d-p3-ns", "2d-p4-ns-walls", "2d-p4-ns-curv", "3d-p1-ns", "3d-p2-ns"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_warp_variant_bit_identical(case, prec):
+    """Every tile kernel run one warp per element (variant 3) equals the
+    CTA-tile variant bit for bit: residual, VJP, ARK step and its adjoint."""
+    from paper_2607_16044_b300.dgx import KERNELS, Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    if case == "2d-p2-euler":
+        mesh, phys = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 9)] * 2, [True, True]), _euler()
+    elif case == "2d-p3-ns":
+        mesh, phys = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 7), I.uniform_edges(0, 1, 5)], [True, True]), _ns()
+    elif case == "2d-p4-ns-walls":
+        mesh = I.structured_box_mesh(4, [I.uniform_edges(0, 1, 11), I.wall_stretched_edges(3, 1.3)], [True, False])
+        phys = _ns()
+    elif case == "2d-p4-ns-curv":
+        mesh, phys = I.rotate_elements(I.warped_mesh(4, [5, 4], [1.0, 1.0], 0.04, periodic=[True, False]), 8), _ns()
+    elif case == "3d-p1-ns":
+        mesh = I.structured_box_mesh(1, [I.uniform_edges(0, 1, 5)] * 2 + [I.wall_stretched_edges(2, 1.2)],
+                                     [True, True, False])
+        phys = _ns()
+    else:
+        mesh = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 3)] * 2 + [I.wall_stretched_edges(1, 1.0)],
+                                     [True, True, False])
+        phys = _ns()
+    U0 = I.random_state(mesh, 88)
+    lam0 = I.gaussian_cotangent(U0.shape, 89)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    outs = []
+    for var in (None, 3):                   # the handle's default CTA variants, then warp per element
+        s = Solver(mesh, phys, prec)
+        s.set_tableau(*ars343_explicit())
+        if var is not None:
+            tile_kinds = [k for k in KERNELS if k not in ("face", "vjp_face")]
+            s.set_variants({k: var for k in tile_kinds})
+        Ud = torch.as_tensor(U0).to("cuda", dt).contiguous()
+        f = s.rhs(Ud)
+        g = s.rhs_vjp(Ud, torch.as_tensor(lam0).to("cuda", dt).contiguous())
+        U = torch.as_tensor(U0).cuda()
+        stages = s.stage_buffer()
+        s.ark_step_stages(U, 1e-4, stages)
+        lam = torch.as_tensor(lam0).cuda()
+        s.ark_adjoint_step(stages, lam, 1e-4)
+        s.check()
+        outs.append((f, g, U, lam))
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
