@@ -260,6 +260,133 @@ def roofline(res, prec, pk):
     return out
 
 
+# ---------------------------------------------------------------------------
+# Secondary workloads (reported beside the headline, not part of its step)
+# ---------------------------------------------------------------------------
+def _time_events(fn, reps, flush=None):
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def vortex_accuracy():
+    """16x16 periodic vortex, p = 3, 25 ARS(3,4,3) steps of dt = 0.01 (100
+    stages, t = 0.25): density L2 error against the exact translated vortex
+    and time per step, FP64 and FP32 (FP64 stage accumulation).  (dt = 0.02
+    exceeds the explicit stability limit dt_max ~ 0.018 of this operator:
+    spectral radius ~ 154, ARS(3,4,3) stability radius ~ 2.8.)"""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh, phys, U0 = I.vortex_workload()
+    w = np.outer(np.polynomial.legendre.leggauss(4)[1], np.polynomial.legendre.leggauss(4)[1]).reshape(-1)
+    Jel = np.prod(mesh.size / 2, axis=1)
+    exact = I.isentropic_vortex(mesh, 0.25, phys.gamma)[:, 0]
+    out = {}
+    for prec in ("fp64", "fp32"):
+        s = Solver(mesh, phys, prec)
+        s.set_tableau(*ars343_explicit())
+        U = torch.as_tensor(U0).cuda()
+        for _ in range(25):
+            s.ark_step(U, 0.01)
+        s.check()
+        rho = U[:, 0].cpu().numpy()
+        err = float(np.sqrt(np.sum((rho - exact) ** 2 * w[None, :] * Jel[:, None]) / 100.0))
+        U2 = torch.as_tensor(U0).cuda()
+        g = s.capture(lambda: s.ark_step(U2, 0.01))
+        ms = _time_events(g.replay, 20)
+        out[prec] = {"rho_L2_error": err, "ms_per_ark_step": round(ms, 4),
+                     "dof_evals_per_s": round(4 * U2.numel() / (ms / 1e3), 1)}
+    out["workload"] = "2D Euler vortex 16x16, p=3, 25 ARS(3,4,3) steps dt=0.01 (100 stages, t=0.25)"
+    return out
+
+
+def ensemble_perf(prec="fp32", reps=10):
+    """64 instances (8x8..96x96 quads, p in 2..5, Euler/NS) from the seeded
+    manifest, one batched ARK step per replay of its CUDA graph."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Batch, Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    specs = I.ensemble_manifest()
+    sol, states = [], []
+    for sp in specs:
+        mesh, phys, U = I.ensemble_instance(sp)
+        so = Solver(mesh, phys, prec)
+        so.set_tableau(*ars343_explicit())
+        sol.append(so)
+        states.append(U)
+    b = Batch(sol, [sp["dt"] for sp in specs])
+    U = b.pack(states)
+    b.autotune(U, reps=2)
+    b.step(U)
+    b.step(U, graph=True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ms = _time_events(lambda: b.step(U, graph=True), reps, flush)
+    dofs = sum(int(np.prod(so.shape)) for so in sol)
+    return {"workload": "64-instance ensemble (seeded manifest), 1 batched ARS(3,4,3) step as one CUDA graph",
+            "instances": len(specs), "groups": b.groups, "dofs": dofs, "ms_per_step": round(ms, 4),
+            "dof_evals_per_s": round(4 * dofs / (ms / 1e3), 1), "dtype": prec}
+
+
+def tgv_perf(reps=10):
+    """32^3 Taylor-Green vortex, p = 3: forward residual time, FP32 and FP64."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    mesh, phys, U0 = I.tgv_workload()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {"workload": "3D TGV 32^3, p=3, Re=1600, Ma=0.1 (forward residual)", "dofs": int(U0.size)}
+    for prec in ("fp32", "fp64"):
+        s = Solver(mesh, phys, prec)
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        U = torch.as_tensor(U0).to("cuda", dt).contiguous()
+        f = s.rhs(U)
+        ms = _time_events(lambda: s.rhs(U, out=f), reps, flush)
+        s.check()
+        out[prec] = {"ms_per_residual": round(ms, 4), "dof_evals_per_s": round(U.numel() / (ms / 1e3), 1)}
+    return out
+
+
+def channel3d_perf(reps=3):
+    """48^3 p = 5 wall-stretched 3D channel (24M nodes): one FP32 ARK step with
+    stage checkpoints and its adjoint."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh, phys, U0 = I.channel3d_workload()
+    s = Solver(mesh, phys, "fp32")
+    s.set_tableau(*ars343_explicit())
+    U = torch.as_tensor(U0).cuda()
+    lam = torch.as_tensor(np.random.default_rng(105).standard_normal(U0.shape)).cuda()
+    stages = s.stage_buffer()
+
+    def step():
+        s.ark_step_stages(U, 1e-9, stages)
+        s.ark_adjoint_step(stages, lam, 1e-9)
+    s.autotune(U, reps=1)
+    step()
+    ms = _time_events(step, reps)
+    s.check()
+    return {"workload": "3D NS channel 48^3, p=5 (216 nodes/element), z-stretching 1.1, FP32 step + adjoint",
+            "dofs": int(U0.size), "ms_per_step": round(ms, 3),
+            "dof_evals_per_s": round(8 * U0.size / (ms / 1e3), 1)}
+
+
 def cpu_baseline(steps_hint=1):
     """The FP64 oracle as it stands, on this host's cores: one residual of the
     full workload (bounded sample), scaled to DOF-evals/s."""
@@ -332,6 +459,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--legs", default="fp32,fp64", help="precisions to time (profiling runs may pick one)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -391,6 +519,11 @@ def main():
             "fp64": {"value": round(r64["dofs"] * r64["evals_per_step"] / (r64["ms"] / 1e3), 1), "unit": UNIT,
                      "ms_per_step": round(r64["ms"], 4), "eager_ms_per_step": round(r64["eager_ms"], 4),
                      "roofline": roof64, "clocks": r64["clocks"]}}
+    if not args.no_extra:
+        line["vortex_fp32_vs_fp64"] = vortex_accuracy()
+        line["ensemble"] = ensemble_perf()
+        line["tgv"] = tgv_perf()
+        line["channel3d"] = channel3d_perf()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

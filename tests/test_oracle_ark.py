@@ -114,3 +114,15 @@ def test_package_tableau_matches_oracle_tableau():
     A, b, c = ars343_explicit()
     A2, b2, c2 = ark.ars343()
     assert np.array_equal(A, A2) and np.array_equal(b, b2) and np.array_equal(c, c2)
+
+
+def test_ars343_explicit_stability_radius():
+    """|R(z)| <= 1 along the imaginary axis up to about 2.8 for the explicit
+    ARS(3,4,3) half; together with the vortex operator's spectral radius (~154
+    on the 16x16 p = 3 mesh) this bounds its stable dt near 0.018."""
+    A, b, c = ark.ars343()
+
+    def R(z):
+        return 1 + z * b @ np.linalg.solve(np.eye(4) - z * A, np.ones(4))
+    assert abs(R(2.7j)) <= 1.0 + 1e-12
+    assert abs(R(3.0j)) > 1.0
