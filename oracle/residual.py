@@ -279,3 +279,37 @@ def residual(mesh, gas, U, elems=None):
     op = DGOperator(mesh, gas)
     Ut = torch.as_tensor(U)
     return op.residual(Ut, elems)
+
+
+def submesh_around(mesh, elems, rings):
+    """The elements within ``rings`` neighbour steps of ``elems`` as a mesh of
+    their own (test infrastructure for sampled parity on very large meshes).
+
+    Returns (submesh, global ids of its elements, local ids of ``elems``).
+    Neighbours outside the kept set are replaced by the element itself; only
+    elements at the outermost ring see such faces, and their residuals and
+    gradients are never used by the sampled rows.
+    """
+    import dataclasses
+    keep = np.unique(np.asarray(elems, dtype=np.int64))
+    for _ in range(rings):
+        nb = mesh.neighbor[keep].reshape(-1)
+        keep = np.unique(np.concatenate([keep, nb[nb >= 0]]))
+    pos = np.full(mesh.n_elem, -1, dtype=np.int64)
+    pos[keep] = np.arange(len(keep))
+    nb = mesh.neighbor[keep].astype(np.int64)
+    inside = nb >= 0
+    mapped = np.where(inside, pos[np.where(inside, nb, 0)], nb)
+    outside = inside & (mapped < 0)
+    self_ids = np.repeat(np.arange(len(keep))[:, None], nb.shape[1], axis=1)
+    nbf = mesh.nbr_face[keep].copy()
+    ori = mesh.orient[keep].copy()
+    faces = np.tile(np.arange(nb.shape[1]), (len(keep), 1))
+    mapped = np.where(outside, self_ids, mapped)
+    nbf = np.where(outside, faces ^ 1, nbf)
+    ori = np.where(outside, 0, ori)
+    sub = dataclasses.replace(
+        mesh, n_elem=len(keep), xyz=mesh.xyz[keep], neighbor=mapped.astype(np.int32),
+        nbr_face=nbf.astype(np.int8), orient=ori.astype(np.int8),
+        lo=None if mesh.lo is None else mesh.lo[keep], size=None if mesh.size is None else mesh.size[keep])
+    return sub, keep, pos[np.asarray(elems, dtype=np.int64)]

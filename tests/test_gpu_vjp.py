@@ -256,3 +256,38 @@ def test_warp_variant_bit_identical(case, prec):
         outs.append((f, g, U, lam))
     for a, b in zip(outs[0], outs[1]):
         assert torch.equal(a, b)
+
+
+def test_channel3d_config_full_size_sampled_fp32():
+    """48^3 p = 5 wall-stretched 3D channel (24M nodes), FP32: sampled residual
+    rows and VJP rows against the oracle evaluated on the rings around them."""
+    from oracle.residual import DGOperator, submesh_around, term_scale
+    from oracle.vjp import vjp_rows
+    from paper_2607_16044_b300.dgx import Solver
+    from tests.parity_util import noise_floor, scaled_err
+    mesh, phys, U0 = I.channel3d_workload()
+    lam0 = I.gaussian_cotangent(U0.shape, 105)
+    s = Solver(mesh, phys, "fp32")
+    U32 = torch.as_tensor(U0).cuda().float()
+    f = s.rhs(U32).double().cpu().numpy()
+    g = s.rhs_vjp(U32, torch.as_tensor(lam0).cuda().float()).double().cpu().numpy()
+    s.check()
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, 6, replace=False), [0, mesh.n_elem - 1]]))
+    Uq, lq = quantize32(U0), quantize32(lam0)
+    gas = gas_of(phys)
+    # forward rows: residuals need the 2-ring (BR1)
+    sub, keep, loc = submesh_around(mesh, rows, 3)
+    op = DGOperator(sub, gas)
+    Ut = torch.as_tensor(Uq[keep])
+    ref = op.residual(Ut, loc).numpy()
+    T = term_scale(op, Ut, loc).numpy()
+    ferr = scaled_err(f[rows], ref, T)
+    # VJP rows: g_e collects the residuals of the 2-ring of e, each depending on its own 2-ring
+    sub4, keep4, loc4 = submesh_around(mesh, rows, 5)
+    op4 = DGOperator(sub4, gas)
+    gref = vjp_rows(op4, torch.as_tensor(Uq[keep4]), torch.as_tensor(lq[keep4]), loc4).numpy()
+    gerr = rel_err(g[rows], gref)
+    record("channel3d-fp32", scaled=ferr, vjp_rel=gerr, sampled=len(rows))
+    assert ferr < 1e-5, ferr
+    assert gerr < 1e-4, gerr
