@@ -343,21 +343,47 @@ def ensemble_perf(prec="fp32", reps=10):
 
 
 def tgv_perf(reps=10):
-    """32^3 Taylor-Green vortex, p = 3: forward residual time, FP32 and FP64."""
+    """32^3 Taylor-Green vortex, p = 3: forward residual time in FP64 and in FP32
+    with each contraction engine of the element kernel (CUDA cores, TF32 and
+    3xTF32 tensor cores); per FP32 leg the element kernel's own time (event
+    profiler) and the max-norm deviation of the residual from the FP64 residual
+    relative to the FP64 residual's max norm over all fields."""
     import torch
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
     mesh, phys, U0 = I.tgv_workload()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {"workload": "3D TGV 32^3, p=3, Re=1600, Ma=0.1 (forward residual)", "dofs": int(U0.size)}
-    for prec in ("fp32", "fp64"):
+    ref = None
+    for leg in ("fp64", "fp32", "fp32-tf32", "fp32-3xtf32"):
+        prec = leg.split("-")[0]
         s = Solver(mesh, phys, prec)
+        if "-" in leg:
+            s.set_contraction(leg.split("-")[1])
         dt = torch.float32 if prec == "fp32" else torch.float64
         U = torch.as_tensor(U0).to("cuda", dt).contiguous()
         f = s.rhs(U)
         ms = _time_events(lambda: s.rhs(U, out=f), reps, flush)
+        s.profile(True)
+        s.profile_reset()
+        for _ in range(reps):
+            flush.fill_(1)
+            s.rhs(U, out=f)
+        torch.cuda.synchronize()
+        launches, elem_ms = s.profile_read()["elem"]
+        s.profile(False)
         s.check()
-        out[prec] = {"ms_per_residual": round(ms, 4), "dof_evals_per_s": round(U.numel() / (ms / 1e3), 1)}
+        r = {"ms_per_residual": round(ms, 4), "dof_evals_per_s": round(U.numel() / (ms / 1e3), 1),
+             "elem_kernel_ms": round(elem_ms / launches, 4)}
+        fd = f.double()
+        if ref is None:
+            ref = fd
+        else:
+            # normalised by the largest FP64 residual entry of any field: the TGV
+            # density residual is near zero (divergence-free start), so a per-field
+            # normalisation would divide by round-off
+            r["max_dev_vs_fp64"] = float((fd - ref).abs().max() / ref.abs().max())
+        out[leg] = r
     return out
 
 

@@ -233,9 +233,31 @@ dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants);
 dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable);
 dgx_status dgx_set_variants(dgx_handle* h, const int32_t* variants);
 
+/* Engine of the 1D differentiation contractions of the forward element kernel
+ * (the volume term of the Sec. 3.3 weak form together with the surface lift), an
+ * opt-in for FP32 handles:
+ *   DGX_CONTRACT_CUDA_CORE  FP32 (or FP64) fused multiply-adds (default);
+ *   DGX_CONTRACT_TF32       tcgen05 tensor cores, operands rounded to TF32
+ *                           (10-bit mantissa), FP32 accumulation: relative
+ *                           error of the residual about 1e-3;
+ *   DGX_CONTRACT_3XTF32     tcgen05, every operand split into two TF32 parts
+ *                           and three products accumulated: close to FP32.
+ * Each (direction, element, field, line) is one row of a GEMM against the
+ * fixed [Dh | -L(-1) | -L(+1)] operand (K = n + 2 <= 8, M = 128 rows per
+ * MMA, accumulator in tensor memory).  Applies to dgx_rhs and the ARK stage
+ * kernels of this handle (and of batches created from it); the adjoint
+ * kernels always contract on CUDA cores, so with a tensor-core contraction
+ * the adjoint step differentiates the CUDA-core residual at the stage states
+ * the tensor-core forward produced.  DGX_EUNSUPPORTED for FP64 handles,
+ * DGX_EINVAL for another mode.  The element tile is the 256-thread shape
+ * whatever the autotuned variant, and the persistent pipeline is bypassed. */
+typedef enum { DGX_CONTRACT_CUDA_CORE = 0, DGX_CONTRACT_TF32 = 1, DGX_CONTRACT_3XTF32 = 3 } dgx_contraction;
+dgx_status dgx_set_contraction(dgx_handle* h, int32_t mode);
+dgx_status dgx_get_contraction(const dgx_handle* h, int32_t* mode);
+
 /* Batched ensemble: many independent instances (meshes, degrees, physics)
  * advanced together.  Instances are grouped by (dimension, degree, precision,
- * physics, mesh kind); each group's meshes are concatenated into one internal
+ * physics, mesh kind, contraction engine); each group's meshes are concatenated into one internal
  * handle, so every kernel launch covers all instances of a group and the
  * tile variant is autotuned per group (per degree).  All instances must share
  * the tableau.  The state of all instances is one packed FP64 buffer:

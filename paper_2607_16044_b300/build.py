@@ -21,6 +21,7 @@ DEGREES = (1, 2, 3, 4, 5)
 UNIT = """// generated by build.py: instantiation of the (D={D}, S={S}, P={P}) launch table
 #include "dispatch.h"
 {VJP_INCLUDE}
+{TC_INCLUDE}
 namespace dgx {{
 namespace {{
 using Sc = {S};
@@ -55,16 +56,22 @@ struct R {{
     Stage<Sc> none{{}};
     return O::template elem_pipe<0>(m(M), V, v, c, (const Sc*)U, w, (Sc*)out, none, nsm, st, *used);
   }}
+{TC_FN}
   static size_t smem(int kind, int V) {{ return O::smem(kind, V); }}
 }};
 }}  // namespace
 const Table* table_d{D}_{T}_p{P}() {{
-  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::elem_pipe, &R::smem,
-                          {VJP_PTR}}};
+  static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::elem_pipe,
+                          {TC_PTR}, &R::smem, {VJP_PTR}}};
   return &t;
 }}
 }}  // namespace dgx
 """
+
+TC_FN = """  static cudaError_t elem_tc(const void* M, int tc, bool v, bool c, const void* U, const Work& w, void* out,
+                             const void* sa, cudaStream_t st) {{
+    return TcOps<{D}, {P}>::elem(m(M), tc, v, c, (const float*)U, w, (float*)out, (const Stage<float>*)sa, st);
+  }}"""
 
 DISPATCH = """// generated by build.py: degree dispatch
 #include "dispatch.h"
@@ -93,7 +100,11 @@ def _write_sources():
                 cases.append(f"    case {P}: return {name}();")
                 vjp_inc = '#include "vjp.cuh"' if vjp else ""
                 vjp_ptr = f"vjp_table<{D}, {P}, {S}>()" if vjp else "nullptr"
-                src = UNIT.format(D=D, S=S, P=P, T=T, VJP_INCLUDE=vjp_inc, VJP_PTR=vjp_ptr)
+                f32 = S == "float"
+                src = UNIT.format(D=D, S=S, P=P, T=T, VJP_INCLUDE=vjp_inc, VJP_PTR=vjp_ptr,
+                                  TC_INCLUDE='#include "kernels_tc.cuh"' if f32 else "",
+                                  TC_FN=TC_FN.format(D=D, P=P) if f32 else "",
+                                  TC_PTR="&R::elem_tc" if f32 else "nullptr")
                 path = os.path.join(BUILD, f"unit_d{D}_{T}_p{P}.cu")
                 _write_if_changed(path, src)
                 units.append(path)

@@ -23,6 +23,10 @@ struct Table {
   // persistent TMA-fed element kernel; *used = false when it cannot run (nothing launched)
   cudaError_t (*elem_pipe)(const void* M, int V, bool visc, bool curv, const void* U, const Work& w, void* out,
                            const void* stage, int nsm, cudaStream_t st, bool* used);
+  // tensor-core element kernel (FP32 tables only, else nullptr): tc = 1 TF32, 3 3xTF32;
+  // stage == nullptr writes f to out, otherwise performs the ARK stage update
+  cudaError_t (*elem_tc)(const void* M, int tc, bool visc, bool curv, const void* U, const Work& w, void* out,
+                         const void* stage, cudaStream_t st);
   size_t (*smem)(int kind, int V);  // tile kernels: 0 trace, 1 br1, 2 elem
   const void* vjp;                   // adjoint launch table (VjpTable) or nullptr
 };

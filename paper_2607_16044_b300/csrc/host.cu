@@ -44,6 +44,7 @@ struct dgx_handle {
   dgx::Mesh<float> mesh32{};
   int nsm = 148;          // SMs of the device (persistent grids)
   bool pipeline = true;   // persistent TMA-fed kernels where the layout allows
+  int contraction = DGX_CONTRACT_CUDA_CORE;  // engine of the forward element kernel
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
   int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
@@ -464,6 +465,8 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, wi, st); });
     if (err == cudaSuccess)
       err = launch(h, DGX_K_ELEM_STAGE, st, [&] {
+        if (h->contraction != DGX_CONTRACT_CUDA_CORE)
+          return t->elem_tc(M, h->contraction, h->viscous, h->curv, Uin, wi, nullptr, &sa, st);
         bool used = false;
         if (h->pipeline) {
           const cudaError_t e = t->elem_pipe(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, nullptr, &sa,
@@ -971,6 +974,8 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
   if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, w, st); });
   if (err == cudaSuccess)
     err = launch(h, DGX_K_ELEM, st, [&] {
+      if (h->contraction != DGX_CONTRACT_CUDA_CORE)
+        return t->elem_tc(M, h->contraction, h->viscous, h->curv, U, w, dUdt, nullptr, st);
       bool used = false;
       if (h->pipeline) {
         const cudaError_t e = t->elem_pipe(M, h->var[DGX_K_ELEM], h->viscous, h->curv, U, w, dUdt, nullptr, h->nsm,
@@ -1124,6 +1129,20 @@ dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable) {
   return DGX_OK;
 }
 
+dgx_status dgx_set_contraction(dgx_handle* h, int32_t mode) {
+  if (!h) return DGX_EINVAL;
+  if (mode != DGX_CONTRACT_CUDA_CORE && mode != DGX_CONTRACT_TF32 && mode != DGX_CONTRACT_3XTF32) return DGX_EINVAL;
+  if (mode != DGX_CONTRACT_CUDA_CORE && (h->fp64 || !h->tab->elem_tc)) return DGX_EUNSUPPORTED;
+  h->contraction = mode;
+  return DGX_OK;
+}
+
+dgx_status dgx_get_contraction(const dgx_handle* h, int32_t* mode) {
+  if (!h || !mode) return DGX_EINVAL;
+  *mode = h->contraction;
+  return DGX_OK;
+}
+
 dgx_status dgx_get_variants(const dgx_handle* h, int32_t* variants) {
   if (!h || !variants) return DGX_EINVAL;
   for (int k = 0; k < DGX_KERNEL_KINDS; ++k) variants[k] = h->var[k];
@@ -1166,6 +1185,7 @@ struct dgx_batch {
 namespace {
 bool same_group(const dgx_handle* a, const dgx_handle* b) {
   return a->d == b->d && a->p == b->p && a->fp64 == b->fp64 && a->viscous == b->viscous && a->curv == b->curv &&
+         a->contraction == b->contraction &&
          a->desc.gamma == b->desc.gamma && (!a->viscous || (a->desc.Re == b->desc.Re && a->desc.Pr == b->desc.Pr));
 }
 
@@ -1261,6 +1281,7 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
       for (int j = 0; j < r->stages; ++j) A[i * r->stages + j] = r->A[i * dgx::MAXSTAGES + j];
     if ((st = dgx_set_tableau(g.h, r->stages, A.data(), r->b, r->c)) != DGX_OK) break;
     for (int k = 0; k < DGX_KERNEL_KINDS; ++k) g.h->var[k] = r->var[k];
+    g.h->contraction = r->contraction;
     if (cudaMalloc((void**)&g.d_dte, (size_t)E * sizeof(double)) != cudaSuccess) {
       st = DGX_ENOMEM;
       break;

@@ -502,6 +502,121 @@ __global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ T
 }
 
 // ---------------------------------------------------------------------------
+// Per-node pieces shared by the element kernels (k_elem, k_elem_p, k_elem_tc).
+// ---------------------------------------------------------------------------
+
+// ARK stage inputs of one node, read before the flux work so their latency
+// overlaps it: pre = base + sum_{j<i} dt a_{i+1,j} k_j, or at the last stage
+// pre64 = U_n (FP64 path: + sum_{j<i} dt b_j k_j) and pre = the FP32
+// increment sum_{j<i} dt b_j k_j.  base(f), kj(j, f), un(f) fetch the inputs.
+template <int nf, typename S, typename Base, typename Kj, typename Un>
+__device__ __forceinline__ void stage_prefix(const Stage<S>& st, double dt, Base base, Kj kj, Un un, S (&pre)[nf],
+                                             double (&pre64)[nf]) {
+  if (!st.last) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      S acc = base(f);
+      for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * kj(j, f);
+      pre[f] = acc;
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      double u = un(f);
+      S inc = S(0);
+      for (int j = 0; j < st.i; ++j) {
+        const S kv = kj(j, f);
+        if (sizeof(S) == 8) u += (dt * st.cb[j]) * (double)kv;
+        else inc += (S)(dt * st.cb[j]) * kv;
+      }
+      pre64[f] = u;
+      pre[f] = inc;
+    }
+  }
+}
+
+// Volume flux of one node along each reference direction a:
+// Fa[a] = sum_c Ja[a][c] (F^c - F^nu)_c (boxes: Fa[a] = (F^c - F^nu)_a).
+// q(c, f) fetches the lifted gradient, ja(a, c) the metric term.
+template <int D, typename S, bool VISC, bool CURV, typename Qf, typename Jf>
+__device__ __forceinline__ void node_flux(const Gas<S>& gas, const S (&Uq)[D + 2], Qf q, Jf ja, S (&Fa)[D][D + 2]) {
+  constexpr int nf = D + 2;
+  S F[D][nf];
+  conv_flux_all<D, S>(Uq, gas, F);
+  if (VISC) {
+    S Qv[D][nf], Fv[D][nf];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Qv[c][f] = q(c, f);
+    visc_flux_all<D, S>(Uq, Qv, gas, Fv);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) F[c][f] -= Fv[c][f];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (!CURV) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fa[a][f] = F[a][f];
+    } else {
+      S j[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) j[c] = ja(a, c);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S s = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += j[c] * F[c][f];
+        Fa[a][f] = s;
+      }
+    }
+  }
+}
+
+// ARK stage update of one node (Sec. 4.2): k_i = res; y_{i+1} = pre + dt a_{i+1,i} k_i,
+// or at the last stage U_{n+1} = U_n + sum_j dt b_j k_j accumulated in FP64.
+// off is the node's offset in the global [E][nf][N] arrays; returns y.
+template <int nf, typename S>
+__device__ __forceinline__ void stage_update(const Stage<S>& st, double dt, size_t off, int N, const S (&res)[nf],
+                                             const S (&pre)[nf], const double (&pre64)[nf], S (&y)[nf]) {
+  if (!st.last) {
+    const S ci = (S)(dt * st.ca[st.i]);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      const S acc = pre[f] + ci * res[f];
+      y[f] = acc;
+      st.Kout[off + f * N] = res[f];
+      st.Y[off + f * N] = acc;
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      double un = pre64[f];
+      if (sizeof(S) == 8) {
+        un += (dt * st.cb[st.i]) * (double)res[f];
+      } else {
+        const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
+        un += (double)inc;
+      }
+      st.Un[off + f * N] = un;
+      y[f] = (S)un;
+      if (st.shadow) st.shadow[off + f * N] = y[f];
+    }
+  }
+}
+
+// non-finite check of a node's residual (flag bit 0)
+template <int nf, typename S>
+__device__ __forceinline__ void flag_nonfinite(const S (&res)[nf], unsigned* flags) {
+  bool bad = false;
+#pragma unroll
+  for (int f = 0; f < nf; ++f) bad |= !isfinite(res[f]);
+  if (bad) atomicOr(flags, 1u);
+}
+
+// ---------------------------------------------------------------------------
 // k_elem: f_q = (1/J) [ sum_a sum_m Dh[q_a][m] (F^c - F^nu)~_a(m) - sum_faces L_{q_a}(+-1) Fhat ]
 // (boxes: (F^c - F^nu)~_a = F_a with the factor 2/h_a applied per direction).
 // MODE 0 writes f; MODE 1 performs the ARK stage update and emits the next
@@ -538,68 +653,23 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   double pre64[nf];
   if (MODE == 1 && active) {
     const size_t off = (size_t)e * H::STATE + q;
-    const double dt = st.dte ? st.dte[e] : st.dt;
-    if (!st.last) {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        S acc = st.base[off + f * N];
-        for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * st.k[j][off + f * N];
-        pre[f] = acc;
-      }
-    } else {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        double un = st.Un[off + f * N];
-        S inc = S(0);
-        for (int j = 0; j < st.i; ++j) {
-          if (sizeof(S) == 8) un += (dt * st.cb[j]) * (double)st.k[j][off + f * N];
-          else inc += (S)(dt * st.cb[j]) * st.k[j][off + f * N];
-        }
-        pre64[f] = un;
-        pre[f] = inc;
-      }
-    }
+    stage_prefix<nf, S>(
+        st, st.dte ? st.dte[e] : st.dt, [&](int f) { return st.base[off + f * N]; },
+        [&](int j, int f) { return st.k[j][off + f * N]; }, [&](int f) { return st.Un[off + f * N]; }, pre, pre64);
   }
-  S Uq[nf];
   if (active) {
     const S* up = U + (size_t)e * H::STATE + q;
+    S Uq[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) Uq[f] = up[f * N];
-    S F[D][nf];
-    conv_flux_all<D, S>(Uq, M.gas, F);
-    if (VISC) {
-      S Qv[D][nf], Fv[D][nf];
-      const S* qp = Q + (size_t)e * D * H::STATE + q;
+    S Fa[D][nf];
+    node_flux<D, S, VISC, CURV>(
+        M.gas, Uq, [&](int c, int f) { return Q[(size_t)e * D * H::STATE + (c * nf + f) * N + q]; },
+        [&](int a, int c) { return M.geo.Ja[(((size_t)e * D + a) * D + c) * N + q]; }, Fa);
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+    for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) Qv[c][f] = qp[(c * nf + f) * N];
-      visc_flux_all<D, S>(Uq, Qv, M.gas, Fv);
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int f = 0; f < nf; ++f) F[c][f] -= Fv[c][f];
-    }
-    if (!CURV) {
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = F[a][f];
-    } else {
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        S ja[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) ja[c] = M.geo.Ja[(((size_t)e * D + a) * D + c) * N + q];
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          S s = 0;
-#pragma unroll
-          for (int c = 0; c < D; ++c) s += ja[c] * F[c][f];
-          fs[((t * D + a) * nf + f) * N + q] = s;
-        }
-      }
-    }
+      for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = Fa[a][f];
   }
   g_sync<V>();
   // weak divergence + lift, one thread per line and direction, in place in fs
@@ -638,10 +708,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
 #pragma unroll
       for (int f = 0; f < nf; ++f) res[f] *= iJ;
     }
-    bool bad = false;
-#pragma unroll
-    for (int f = 0; f < nf; ++f) bad |= !isfinite(res[f]);
-    if (bad) atomicOr(M.flags, 1u);
+    flag_nonfinite<nf>(res, M.flags);
   }
   if (MODE == 0) {
     if (active) {
@@ -654,34 +721,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   // ---- ARK stage update (Sec. 4.2): k_i = f(y_i); y_{i+1} = base + sum_{j<=i} dt a_{i+1,j} k_j;
   //      last stage: U_{n+1} = U_n + sum_j dt b_j k_j in FP64.
   S y[nf];
-  if (active) {
-    const size_t off = (size_t)e * H::STATE + q;
-    const double dt = st.dte ? st.dte[e] : st.dt;
-    if (!st.last) {
-      const S ci = (S)(dt * st.ca[st.i]);
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        const S acc = pre[f] + ci * res[f];
-        y[f] = acc;
-        st.Kout[off + f * N] = res[f];
-        st.Y[off + f * N] = acc;
-      }
-    } else {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        double un = pre64[f];
-        if (sizeof(S) == 8) {
-          un += (dt * st.cb[st.i]) * (double)res[f];
-        } else {
-          const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
-          un += (double)inc;
-        }
-        st.Un[off + f * N] = un;
-        y[f] = (S)un;
-        if (st.shadow) st.shadow[off + f * N] = y[f];
-      }
-    }
-  }
+  if (active)
+    stage_update<nf, S>(st, st.dte ? st.dte[e] : st.dt, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
   g_sync<V>();  // everyone is done with fs
   if (active) {
 #pragma unroll

@@ -85,67 +85,23 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
     double pre64[nf];
     if (MODE == 1 && active) {
       const int off = t * H::STATE + q;
-      const double dt = st.dte ? st.dte[e] : st.dt;
-      if (!st.last) {
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          S acc = bases[off + f * N];
-          for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * kss[(size_t)j * T * H::STATE + off + f * N];
-          pre[f] = acc;
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          double un = Uns[off + f * N];
-          S inc = S(0);
-          for (int j = 0; j < st.i; ++j) {
-            const S kv = kss[(size_t)j * T * H::STATE + off + f * N];
-            if (sizeof(S) == 8) un += (dt * st.cb[j]) * (double)kv;
-            else inc += (S)(dt * st.cb[j]) * kv;
-          }
-          pre64[f] = un;
-          pre[f] = inc;
-        }
-      }
+      stage_prefix<nf, S>(
+          st, st.dte ? st.dte[e] : st.dt, [&](int f) { return bases[off + f * N]; },
+          [&](int j, int f) { return kss[(size_t)j * T * H::STATE + off + f * N]; },
+          [&](int f) { return Uns[off + f * N]; }, pre, pre64);
     }
     if (active) {
       S Uq[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) Uq[f] = Us[t * H::STATE + f * N + q];
-      S F[D][nf];
-      conv_flux_all<D, S>(Uq, M.gas, F);
-      if (VISC) {
-        S Qv[D][nf], Fv[D][nf];
+      S Fa[D][nf];
+      node_flux<D, S, VISC, CURV>(
+          M.gas, Uq, [&](int c, int f) { return Qs[t * D * H::STATE + (c * nf + f) * N + q]; },
+          [&](int a, int c) { return Jas[((t * D + a) * D + c) * N + q]; }, Fa);
 #pragma unroll
-        for (int c = 0; c < D; ++c)
+      for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int f = 0; f < nf; ++f) Qv[c][f] = Qs[t * D * H::STATE + (c * nf + f) * N + q];
-        visc_flux_all<D, S>(Uq, Qv, M.gas, Fv);
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-          for (int f = 0; f < nf; ++f) F[c][f] -= Fv[c][f];
-      }
-      if (!CURV) {
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-          for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = F[a][f];
-      } else {
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          S ja[D];
-#pragma unroll
-          for (int c = 0; c < D; ++c) ja[c] = Jas[((t * D + a) * D + c) * N + q];
-#pragma unroll
-          for (int f = 0; f < nf; ++f) {
-            S s = 0;
-#pragma unroll
-            for (int c = 0; c < D; ++c) s += ja[c] * F[c][f];
-            fs[((t * D + a) * nf + f) * N + q] = s;
-          }
-        }
-      }
+        for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = Fa[a][f];
     }
     __syncthreads();
 #pragma unroll
@@ -183,10 +139,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
 #pragma unroll
         for (int f = 0; f < nf; ++f) res[f] *= iJ;
       }
-      bool bad = false;
-#pragma unroll
-      for (int f = 0; f < nf; ++f) bad |= !isfinite(res[f]);
-      if (bad) atomicOr(M.flags, 1u);
+      flag_nonfinite<nf>(res, M.flags);
     }
     if (MODE == 0) {
       if (active) {
@@ -198,34 +151,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
       continue;
     }
     S y[nf];
-    if (active) {
-      const size_t off = (size_t)e * H::STATE + q;
-      const double dt = st.dte ? st.dte[e] : st.dt;
-      if (!st.last) {
-        const S ci = (S)(dt * st.ca[st.i]);
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          const S acc = pre[f] + ci * res[f];
-          y[f] = acc;
-          st.Kout[off + f * N] = res[f];
-          st.Y[off + f * N] = acc;
-        }
-      } else {
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          double un = pre64[f];
-          if (sizeof(S) == 8) {
-            un += (dt * st.cb[st.i]) * (double)res[f];
-          } else {
-            const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
-            un += (double)inc;
-          }
-          st.Un[off + f * N] = un;
-          y[f] = (S)un;
-          if (st.shadow) st.shadow[off + f * N] = y[f];
-        }
-      }
-    }
+    if (active)
+      stage_update<nf, S>(st, st.dte ? st.dte[e] : st.dt, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
     __syncthreads();  // everyone is done with fs
     if (active) {
 #pragma unroll

@@ -44,7 +44,9 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_kernel_name", "dgx_ark_step_stages", "dgx_ark_adjoint_step", "dgx_rhs_noalloc",
            "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
-           "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline"]
+           "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
+           "dgx_set_contraction", "dgx_get_contraction"]
+CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -74,6 +76,8 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_kernel_work.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     lib.dgx_autotune.argtypes = [vp, vp, i32, vp]
     lib.dgx_set_pipeline.argtypes = [vp, i32]
+    lib.dgx_set_contraction.argtypes = [vp, i32]
+    lib.dgx_get_contraction.argtypes = [vp, ctypes.POINTER(i32)]
     lib.dgx_get_variants.argtypes = [vp, ctypes.POINTER(i32)]
     lib.dgx_set_variants.argtypes = [vp, ctypes.POINTER(i32)]
     lib.dgx_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
@@ -307,6 +311,19 @@ class Solver:
     def set_pipeline(self, enable: bool):
         """Select the persistent TMA-fed kernels (default) or the one-CTA-per-tile ones."""
         _check(self.lib.dgx_set_pipeline(self.h, int(enable)), "dgx_set_pipeline")
+
+    def set_contraction(self, mode: str):
+        """Contraction engine of the forward element kernel: "cuda_core" (default),
+        "tf32" or "3xtf32" (tcgen05 tensor cores, FP32 handles only)."""
+        if mode not in CONTRACTIONS:
+            raise ValueError(f"contraction must be one of {sorted(CONTRACTIONS)}")
+        _check(self.lib.dgx_set_contraction(self.h, CONTRACTIONS[mode]), "dgx_set_contraction")
+
+    @property
+    def contraction(self) -> str:
+        v = ctypes.c_int32()
+        _check(self.lib.dgx_get_contraction(self.h, ctypes.byref(v)), "dgx_get_contraction")
+        return {c: k for k, c in CONTRACTIONS.items()}[v.value]
 
     def variants(self) -> dict:
         v = (ctypes.c_int32 * len(KERNELS))()
