@@ -299,7 +299,7 @@ void profile_collect(dgx_handle* h) {
 }
 
 struct Layout {
-  size_t TU, FF, G, Q, Y, K, SH, TUb, Gb, JB, Qb, NU, total;
+  size_t TU, FF, G, Q, Y, K, SH, TUb, Gb, JB, Qb, NU, LAM, total;
 };
 
 Layout layout(const dgx_handle* h, int op) {
@@ -332,6 +332,10 @@ Layout layout(const dgx_handle* h, int op) {
   if (op == DGX_OP_ARK_ADJOINT) {
     L.NU = off;
     off += align256(state) * (h->stages > 0 ? h->stages : 1);
+    if (!h->fp64) {  // lambda_{n+1} rounded to FP32 once per adjoint step
+      L.LAM = off;
+      off += align256(state);
+    }
   }
   if (op == DGX_OP_ARK) {
     L.Y = off;
@@ -447,6 +451,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     if (!sa.last)
       for (int j = 0; j <= i; ++j) sa.ca[j] = h->A[(i + 1) * dgx::MAXSTAGES + j];
     for (int j = 0; j < s; ++j) sa.cb[j] = h->b[j];
+    for (int j = 0; j < s; ++j) {
+      sa.caf[j] = (S)(dt * sa.ca[j]);
+      sa.cbf[j] = (S)(dt * sa.cb[j]);
+    }
     sa.dt = dt;
     sa.dte = dte;
     sa.base = y0;
@@ -497,13 +505,20 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
     vw.TU = (void*)(slot + SL.TU);
     vw.Q = h->viscous ? (void*)(slot + SL.Q) : nullptr;
     dgx::Cot<S> cot{}, fin{};
-    cot.lam64 = lam64;
-    cot.c_lam = dt * h->b[i];
+    if (h->fp64) {
+      cot.lam64 = lam64;
+    } else if (i == s - 1) {  // first reverse stage: read lambda_{n+1} in FP64, keep an FP32 copy
+      cot.lam64 = lam64;
+      cot.lam_out = (S*)(base + L.LAM);
+    } else {
+      cot.lam = (const S*)(base + L.LAM);
+    }
+    cot.c_lam = (S)(dt * h->b[i]);
     for (int j = i + 1; j < s; ++j) {
       const double a = h->A[j * dgx::MAXSTAGES + i];
       if (a != 0.0) {
         cot.nu[cot.n_nu] = NU(j);
-        cot.c_nu[cot.n_nu] = dt * a;
+        cot.c_nu[cot.n_nu] = (S)(dt * a);
         ++cot.n_nu;
       }
     }
@@ -608,11 +623,32 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       }
       break;
     }
-    case DGX_K_VJP_ELEM:
-      flops = E * (STATE * 2 * 2 + FACE * 2 * n + N * D * nf * 2 * n + N * (pc.conv_vjp + (v ? pc.visc_vjp : 0)) +
+    case DGX_K_VJP_ELEM: {
+      flops = E * (FACE * 2 * n + N * D * nf * 2 * n + N * (pc.conv_vjp + (v ? pc.visc_vjp : 0)) +
                    (c ? N * D * D * nf * 2 + STATE : 0));
-      bytes = E * ((2 * STATE + STATE + (v ? 2 * D * STATE : 0) + FACE + STATE) * s + geo_node);
+      bytes = E * ((STATE + (v ? 2 * D * STATE : 0) + FACE + STATE) * s + geo_node);
+      // cotangent combination mu = c_lam lambda + sum_j c_j nu_j, averaged over the
+      // reverse stages of the ARK adjoint (plain VJP without a tableau: lambda only)
+      double fl = 0, by = 0;
+      if (h->stages > 0) {
+        for (int i = 0; i < st; ++i) {
+          int nnu = 0;
+          for (int j = i + 1; j < st; ++j) nnu += h->A[j * dgx::MAXSTAGES + i] != 0.0;
+          const bool first = i == st - 1;
+          const double lam_b = h->fp64 ? (h->b[i] != 0.0 ? 8.0 : 0.0) : (first ? 8.0 + 4.0 : (h->b[i] != 0.0 ? 4.0 : 0.0));
+          fl += E * STATE * 2 * (1 + nnu);
+          by += E * STATE * (lam_b + nnu * s);
+        }
+        fl /= st;
+        by /= st;
+      } else {
+        fl = E * STATE * 2;
+        by = E * STATE * s;
+      }
+      flops += fl;
+      bytes += by;
       break;
+    }
     case DGX_K_VJP_FACE:
       flops = F * nfp * (nf + (c ? pc.llf_area_vjp : pc.llf_unit_vjp) + (v ? 2 * nf : 0));
       bytes = E * FACE * s * (3 + (v ? 1 : 0)) + (c ? F * D * nfp * s : 0.0);

@@ -135,6 +135,8 @@ struct Stage {
   const S* k[MAXSTAGES];   // k_0 .. k_{i-1}
   double ca[MAXSTAGES];    // a_{i+1, j}, j <= i
   double cb[MAXSTAGES];    // b_j (last stage)
+  S caf[MAXSTAGES];        // S(dt a_{i+1, j}) and S(dt b_j), rounded once on the host (used
+  S cbf[MAXSTAGES];        // unless dte is given: FP64 arithmetic is slow on this part)
   double dt;               // time step, unless dte is given
   const double* dte;       // per-element time step (batched instances) or nullptr
   int i;                   // this stage (0-based)
@@ -508,29 +510,33 @@ __global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ T
 // ARK stage inputs of one node, read before the flux work so their latency
 // overlaps it: pre = base + sum_{j<i} dt a_{i+1,j} k_j, or at the last stage
 // pre64 = U_n (FP64 path: + sum_{j<i} dt b_j k_j) and pre = the FP32
-// increment sum_{j<i} dt b_j k_j.  base(f), kj(j, f), un(f) fetch the inputs.
+// increment sum_{j<i} dt b_j k_j.  base(f), kj(j, f), un(f) fetch the inputs;
+// each k_j term is added in the same order (j ascending) for every field.
 template <int nf, typename S, typename Base, typename Kj, typename Un>
 __device__ __forceinline__ void stage_prefix(const Stage<S>& st, double dt, Base base, Kj kj, Un un, S (&pre)[nf],
                                              double (&pre64)[nf]) {
   if (!st.last) {
 #pragma unroll
-    for (int f = 0; f < nf; ++f) {
-      S acc = base(f);
-      for (int j = 0; j < st.i; ++j) acc += (S)(dt * st.ca[j]) * kj(j, f);
-      pre[f] = acc;
+    for (int f = 0; f < nf; ++f) pre[f] = base(f);
+    for (int j = 0; j < st.i; ++j) {
+      const S c = st.dte ? (S)(dt * st.ca[j]) : st.caf[j];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
     }
   } else {
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
-      double u = un(f);
-      S inc = S(0);
-      for (int j = 0; j < st.i; ++j) {
+      pre64[f] = un(f);
+      pre[f] = S(0);
+    }
+    for (int j = 0; j < st.i; ++j) {
+      const S c = st.dte ? (S)(dt * st.cb[j]) : st.cbf[j];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
         const S kv = kj(j, f);
-        if (sizeof(S) == 8) u += (dt * st.cb[j]) * (double)kv;
-        else inc += (S)(dt * st.cb[j]) * kv;
+        if (sizeof(S) == 8) pre64[f] += (double)c * (double)kv;
+        else pre[f] += c * kv;
       }
-      pre64[f] = u;
-      pre[f] = inc;
     }
   }
 }
@@ -582,7 +588,7 @@ template <int nf, typename S>
 __device__ __forceinline__ void stage_update(const Stage<S>& st, double dt, size_t off, int N, const S (&res)[nf],
                                              const S (&pre)[nf], const double (&pre64)[nf], S (&y)[nf]) {
   if (!st.last) {
-    const S ci = (S)(dt * st.ca[st.i]);
+    const S ci = st.dte ? (S)(dt * st.ca[st.i]) : st.caf[st.i];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       const S acc = pre[f] + ci * res[f];
@@ -591,13 +597,14 @@ __device__ __forceinline__ void stage_update(const Stage<S>& st, double dt, size
       st.Y[off + f * N] = acc;
     }
   } else {
+    const S cbi = st.dte ? (S)(dt * st.cb[st.i]) : st.cbf[st.i];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       double un = pre64[f];
       if (sizeof(S) == 8) {
-        un += (dt * st.cb[st.i]) * (double)res[f];
+        un += (double)cbi * (double)res[f];
       } else {
-        const S inc = pre[f] + (S)(dt * st.cb[st.i]) * res[f];
+        const S inc = pre[f] + cbi * res[f];
         un += (double)inc;
       }
       st.Un[off + f * N] = un;

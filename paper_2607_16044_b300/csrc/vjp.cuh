@@ -54,11 +54,13 @@ constexpr size_t smem_vgather_g() {
 // Cotangent source of the element kernel: mu = c_lam * lam + sum_j c_j nu_j.
 template <typename S>
 struct Cot {
-  const S* lam;        // plain VJP cotangent (S), or nullptr
+  const S* lam;        // cotangent in the handle's precision (plain VJP; FP32 ARK adjoint after
+                       // its first reverse stage: the FP32 copy of lambda_{n+1}), or nullptr
   const double* lam64; // ARK adjoint: lambda_{n+1} (double), or nullptr
-  double c_lam;
-  const S* nu[MAXSTAGES];
-  double c_nu[MAXSTAGES];
+  S* lam_out;          // FP32 ARK adjoint, first reverse stage: S(lambda_{n+1}) is written here
+  S c_lam;             // coefficients rounded to S on the host (FP32 kernels do no FP64 math
+  const S* nu[MAXSTAGES];  // in the combination: FP64 is ~1/64 of the FP32 rate here)
+  S c_nu[MAXSTAGES];
   int n_nu;
   // ARK adjoint finish (gather kernel of the last reverse stage):
   // lam64_out = lam64 + g + sum_j nu_j
@@ -102,11 +104,15 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
   {
     const size_t base = (size_t)e0 * H::STATE;
     for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) {
-      double v = 0.0;
-      if (cot.lam) v += cot.c_lam * (double)cot.lam[base + i];
-      if (cot.lam64 && cot.c_lam != 0.0) v += cot.c_lam * cot.lam64[base + i];
-      for (int j = 0; j < cot.n_nu; ++j) v += cot.c_nu[j] * (double)cot.nu[j][base + i];
-      S s = (S)v;
+      S lv = S(0);
+      if (cot.lam) {
+        lv = cot.lam[base + i];
+      } else if (cot.lam64 && (cot.c_lam != S(0) || cot.lam_out)) {
+        lv = (S)cot.lam64[base + i];
+        if (cot.lam_out) cot.lam_out[base + i] = lv;
+      }
+      S s = cot.c_lam * lv;
+      for (int j = 0; j < cot.n_nu; ++j) s += cot.c_nu[j] * cot.nu[j][base + i];
       if (CURV) {
         const int t = i / H::STATE, q = i % N;
         s *= M.geo.iJ[(size_t)(e0 + t) * N + q];
@@ -553,10 +559,16 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
       s += lp[qa] * tub[((t * NF + 2 * a + 1) * nf + f) * nfp + fp];
     }
     g[off + f * N] = s;
-    if (cot.lam64_out) {  // ARK adjoint: lambda_n = lambda_{n+1} + sum_j nu_j (FP64)
-      double acc = cot.lam64_out[off + f * N] + (double)s;
-      for (int j = 0; j < cot.n_all; ++j) acc += (double)cot.nu_all[j][off + f * N];
-      cot.lam64_out[off + f * N] = acc;
+    if (cot.lam64_out) {  // ARK adjoint: lambda_n = lambda_{n+1} + sum_j nu_j, accumulated in FP64
+      if (sizeof(S) == 8) {
+        double acc = cot.lam64_out[off + f * N] + (double)s;
+        for (int j = 0; j < cot.n_all; ++j) acc += (double)cot.nu_all[j][off + f * N];
+        cot.lam64_out[off + f * N] = acc;
+      } else {  // FP32 increment, one FP64 add (as the forward's last stage)
+        S inc = s;
+        for (int j = 0; j < cot.n_all; ++j) inc += cot.nu_all[j][off + f * N];
+        cot.lam64_out[off + f * N] += (double)inc;
+      }
     }
   }
 }
