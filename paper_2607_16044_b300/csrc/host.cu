@@ -66,89 +66,41 @@ struct dgx_handle {
 namespace {
 
 // ---------------------------------------------------------------- 1D basis
-// Gauss-Legendre nodes by Newton's method on P_n (three-term recurrence),
-// weights 2/((1-x^2) P_n'(x)^2); Lagrange derivative matrix from barycentric
-// weights, diagonal = -(sum of the row's off-diagonal entries).
+// The compile-time basis of basis1d.h (the kernels use the same tables).
 struct Basis {
   int n;
   std::vector<double> x, w, D, lm, lp;
 };
 
-void legendre(int n, double x, double& p, double& dp) {
-  double p0 = 1.0, p1 = x;
-  if (n == 0) {
-    p = 1.0;
-    dp = 0.0;
-    return;
-  }
-  for (int k = 1; k < n; ++k) {
-    const double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
-    p0 = p1;
-    p1 = p2;
-  }
-  p = p1;
-  dp = n * (p0 - x * p1) / (1.0 - x * x);
-}
-
 Basis make_basis(int p) {
+  const dgx::Basis1 b = dgx::make_basis1(p);
   Basis B;
-  const int n = p + 1;
+  const int n = b.n;
   B.n = n;
-  B.x.resize(n);
-  B.w.resize(n);
-  for (int j = 0; j < n; ++j) {
-    double x = -std::cos(M_PI * (j + 0.75) / (n + 0.5));
-    for (int it = 0; it < 100; ++it) {
-      double P, dP;
-      legendre(n, x, P, dP);
-      const double dx = P / dP;
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
-    }
-    double P, dP;
-    legendre(n, x, P, dP);
-    B.x[j] = x;
-    B.w[j] = 2.0 / ((1.0 - x * x) * dP * dP);
-  }
-  std::vector<double> bw(n, 1.0);
-  for (int j = 0; j < n; ++j)
-    for (int k = 0; k < n; ++k)
-      if (k != j) bw[j] /= (B.x[j] - B.x[k]);
+  B.x.assign(b.x, b.x + n);
+  B.w.assign(b.w, b.w + n);
+  B.lm.assign(b.lm, b.lm + n);
+  B.lp.assign(b.lp, b.lp + n);
   B.D.assign(n * n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double diag = 0.0;
-    for (int j = 0; j < n; ++j)
-      if (i != j) {
-        B.D[i * n + j] = (bw[j] / bw[i]) / (B.x[i] - B.x[j]);
-        diag -= B.D[i * n + j];
-      }
-    B.D[i * n + i] = diag;
-  }
-  B.lm.assign(n, 1.0);
-  B.lp.assign(n, 1.0);
-  for (int j = 0; j < n; ++j)
-    for (int k = 0; k < n; ++k)
-      if (k != j) {
-        B.lm[j] *= (-1.0 - B.x[k]) / (B.x[j] - B.x[k]);
-        B.lp[j] *= (1.0 - B.x[k]) / (B.x[j] - B.x[k]);
-      }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) B.D[i * n + j] = b.D[i][j];
   return B;
 }
 
 template <typename S>
-void fill_tab(const Basis& B, Tab<S>& t) {
+void fill_tab(int p, Tab<S>& t) {
   std::memset(&t, 0, sizeof(t));
-  const int n = B.n;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      t.D[i * 6 + j] = (S)B.D[i * n + j];
-      t.Dh[i * 6 + j] = (S)(B.w[j] * B.D[j * n + i] / B.w[i]);
+  const dgx::Tab1<S> c = dgx::make_tab1<S>(p);
+  for (int i = 0; i < dgx::MAXN; ++i)
+    for (int j = 0; j < dgx::MAXN; ++j) {
+      t.D[i * 6 + j] = c.D[i][j];
+      t.Dh[i * 6 + j] = c.Dh[i][j];
     }
-  for (int j = 0; j < n; ++j) {
-    t.lm[j] = (S)B.lm[j];
-    t.lp[j] = (S)B.lp[j];
-    t.Lm[j] = (S)(B.lm[j] / B.w[j]);
-    t.Lp[j] = (S)(B.lp[j] / B.w[j]);
+  for (int j = 0; j < dgx::MAXN; ++j) {
+    t.lm[j] = c.lm[j];
+    t.lp[j] = c.lp[j];
+    t.Lm[j] = c.Lm[j];
+    t.Lp[j] = c.Lp[j];
   }
 }
 
@@ -792,11 +744,11 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   dgx_status st = DGX_OK;
   if (h->fp64) {
     std::vector<Tab<double>> t(6);
-    for (int p = 1; p <= 5; ++p) fill_tab(make_basis(p), t[p]);
+    for (int p = 1; p <= 5; ++p) fill_tab(p, t[p]);
     st = upload(t, &h->d_tabs);
   } else {
     std::vector<Tab<float>> t(6);
-    for (int p = 1; p <= 5; ++p) fill_tab(make_basis(p), t[p]);
+    for (int p = 1; p <= 5; ++p) fill_tab(p, t[p]);
     st = upload(t, &h->d_tabs);
   }
   // default tile variant: about 256 threads, or the largest smaller one whose

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "basis1d.h"
 #include "physics.cuh"
 
 namespace dgx {
@@ -197,9 +198,10 @@ __device__ __forceinline__ void line_item(int i, int& t, int& f, int& line) {
 // Traces of a staged tile (us[t][f][q]): one thread per (element, field, line)
 // and direction loads the line once and writes both end values.
 template <int D, int P, typename S, int V>
-__device__ __forceinline__ void tile_traces(const S* us, const S* lm, const S* lp, int nel, S* dst) {
+__device__ __forceinline__ void tile_traces(const S* us, int nel, S* dst) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, N = H::N;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
@@ -210,8 +212,8 @@ __device__ __forceinline__ void tile_traces(const S* us, const S* lm, const S* l
 #pragma unroll
       for (int m = 0; m < n; ++m) {
         const S x = v[H::node(m, line, a)];
-        sm += lm[m] * x;
-        sp += lp[m] * x;
+        sm += tb.lm[m] * x;
+        sp += tb.lp[m] * x;
       }
       S* o = dst + (size_t)t * H::FACE + f * nfp + line;
       o[(2 * a) * nf * nfp] = sm;
@@ -242,9 +244,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
     us[i] = v;
     if (sh) sh[i] = v;
   }
-  load_tab<S, V>(tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, H::n);
   g_sync<V>();
-  tile_traces<D, P, S, V>(us, lm, lp, nel, TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, V>(us, nel, TU + (size_t)e0 * H::FACE);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
                                                               S* __restrict__ G) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_br1_g<D, P, S, V>()));     // [T][nf][N]
   S* js = us + T * H::STATE;                   // [T][NF][nf][nfp]     jumps
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
     const S* src = U + (size_t)e0 * H::STATE;
     for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) us[i] = src[i];
   }
-  load_tab<S, V>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
+  load_tab<S, V>(M.tabs, P, nullptr, nullptr, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
   // jumps Uhat - U^- at every own face point
   for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
     const int fp = i % nfp;
@@ -322,15 +324,15 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
         for (int k = 0; k < n; ++k) {
           S d = 0;
 #pragma unroll
-          for (int m = 0; m < n; ++m) d += sD[k * n + m] * x[m];
-          qo[H::node(k, line, a)] = r * (d + Lp[k] * jp - Lm[k] * jm);
+          for (int m = 0; m < n; ++m) d += tb.D[k][m] * x[m];
+          qo[H::node(k, line, a)] = r * (d + tb.Lp[k] * jp - tb.Lm[k] * jm);
         }
       } else {
 #pragma unroll
         for (int k = 0; k < n; ++k) {
           S d = 0;
 #pragma unroll
-          for (int m = 0; m < n; ++m) d += sD[k * n + m] * x[m];
+          for (int m = 0; m < n; ++m) d += tb.D[k][m] * x[m];
           qo[H::node(k, line, a)] = d;  // D_a U, combined below
         }
       }
@@ -401,8 +403,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
 #pragma unroll
       for (int m = 0; m < n; ++m) {
         const S x = v[H::node(m, line, a)];
-        sm += lm[m] * x;
-        sp += lp[m] * x;
+        sm += tb.lm[m] * x;
+        sp += tb.lp[m] * x;
       }
       tq[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + line] = sm;
       tq[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + line] = sp;
@@ -635,6 +637,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
                                                                S* __restrict__ out, Stage<S> st) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N]  (reused for the next state's traces)
   S* ffs = fs + T * D * H::STATE;            // [T][NF][nf][nfp]
@@ -649,7 +652,6 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
     const S* src = FF + (size_t)e0 * H::FACE;
     for (int i = g_tid<V>(); i < nel * H::FACE; i += g_size<V>()) ffs[i] = src[i];
   }
-  load_tab<S, V>(M.tabs, P, nullptr, sDh, lm, lp, Lm, Lp, n);
   const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool active = t < nel;
   const int e = e0 + t;
@@ -696,8 +698,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
       for (int k = 0; k < n; ++k) {
         S s = 0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += sDh[k * n + m] * x[m];
-        v[H::node(k, line, a)] = r * (s - Lm[k] * ffm - Lp[k] * ffp);
+        for (int m = 0; m < n; ++m) s += tb.Dh[k][m] * x[m];
+        v[H::node(k, line, a)] = r * (s - tb.Lm[k] * ffm - tb.Lp[k] * ffp);
       }
     }
   }
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
     for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
   }
   g_sync<V>();
-  tile_traces<D, P, S, V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, V>(fs, nel, st.TU + (size_t)e0 * H::FACE);
 }
 
 }  // namespace dgx

@@ -39,10 +39,11 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
                                                                  Stage<S> st, int ntiles) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PipeState ps;
   const uint32_t buf_bytes = in.bytes_per_elem * T;
-  unsigned char* bufs[2] = {smem_raw, smem_raw + buf_bytes};
+  auto buf = [&](int b) { return smem_raw + (size_t)b * buf_bytes; };  // the two tile buffers
   S* fs = reinterpret_cast<S*>(smem_raw + 2 * buf_bytes);  // [T][D][nf][N]
   S* sDh = fs + T * D * H::STATE;
   S* lm = sDh + n * n;
@@ -54,21 +55,20 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
     mbar_init(&ps.bar[1], 1);
     fence_mbar_init();
   }
-  load_tab<S>(M.tabs, P, nullptr, sDh, lm, lp, Lm, Lp, n);
   __syncthreads();
   int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) tile_issue(in, tile * T, min(T, M.E - tile * T), T, bufs[0], &ps.bar[0]);
+  if (threadIdx.x == 0 && tile < ntiles) tile_issue(in, tile * T, min(T, M.E - tile * T), T, buf(0), &ps.bar[0]);
   uint32_t par[2] = {0u, 0u};
   for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
     const int b = k & 1;
     const int next = tile + gridDim.x;
     if (threadIdx.x == 0 && next < ntiles)
-      tile_issue(in, next * T, min(T, M.E - next * T), T, bufs[b ^ 1], &ps.bar[b ^ 1]);
+      tile_issue(in, next * T, min(T, M.E - next * T), T, buf(b ^ 1), &ps.bar[b ^ 1]);
     if (!pipe_acquire(ps, b, par[b], next < ntiles, par[b ^ 1], M.flags)) return;
     const int e0 = tile * T;
     const int nel = min(T, M.E - e0);
     // views into the buffer
-    const S* Us = reinterpret_cast<const S*>(bufs[b]);
+    const S* Us = reinterpret_cast<const S*>(buf(b));
     const S* Qs = Us + T * H::STATE;
     const S* FFs = VISC ? Qs + T * D * H::STATE : Qs;
     const S* geo = FFs + T * H::FACE;
@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
         for (int kk = 0; kk < n; ++kk) {
           S s = 0;
 #pragma unroll
-          for (int m = 0; m < n; ++m) s += sDh[kk * n + m] * x[m];
-          v[H::node(kk, line, a)] = r * (s - Lm[kk] * ffm - Lp[kk] * ffp);
+          for (int m = 0; m < n; ++m) s += tb.Dh[kk][m] * x[m];
+          v[H::node(kk, line, a)] = r * (s - tb.Lm[kk] * ffm - tb.Lp[kk] * ffp);
         }
       }
     }
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
       for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
     }
     __syncthreads();
-    tile_traces<D, P, S, V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
+    tile_traces<D, P, S, V>(fs, nel, st.TU + (size_t)e0 * H::FACE);
     __syncthreads();  // buffer and fs free for the next tile
   }
 }

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
   using H = Sh<D, P, TC_V>;
   using C = TcShape<D, P, TC>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, T = H::T;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* Ah = smem_raw;                                // [BLOCKS x 128 rows][K], K-major
   unsigned char* Al = smem_raw + C::A_BYTES;                   // lo parts (TC = 3)
   unsigned char* Bh = smem_raw + C::SPLIT * C::A_BYTES;        // [16 rows][K]
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
     for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
   }
   __syncthreads();
-  tile_traces<D, P, S, TC_V>(fs, lm, lp, nel, st.TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, TC_V>(fs, nel, st.TU + (size_t)e0 * H::FACE);
 }
 
 // Launch layer of the tensor-core element kernel (FP32 handles only).

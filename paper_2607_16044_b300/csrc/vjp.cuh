@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
                                                                    S* __restrict__ Qb) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* mus = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_velem_g<D, P, S, V>()));  // [T][nf][N]     cotangent / J
   S* fb = mus + T * H::STATE;                // [T][D][nf][N]  contravariant flux cotangents
@@ -85,7 +86,6 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
   S* Lp = Lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S, V>(M.tabs, P, nullptr, sDh, nullptr, nullptr, Lm, Lp, n);
   // per-node inputs of the pointwise adjoint, read first (latency overlaps the contractions)
   const int tn = g_tid<V>() / N, qn = g_tid<V>() % N;
   S Uq[nf], Qv[VISC ? D : 1][nf];
@@ -140,10 +140,10 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
       for (int m = 0; m < n; ++m) {
         S acc = 0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc += sDh[k * n + m] * x[k];
+        for (int k = 0; k < n; ++k) acc += tb.Dh[k][m] * x[k];
         fo[H::node(m, line, a)] = rr * acc;
-        sm += Lm[m] * x[m];
-        sp += Lp[m] * x[m];
+        sm += tb.Lm[m] * x[m];
+        sp += tb.Lp[m] * x[m];
       }
       S* dst = FFb + (size_t)(e0 + tt) * H::FACE + f * nfp + line;
       dst[(2 * a) * nf * nfp] = -rr * sm;
@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
                                                                   S* __restrict__ JB, S* __restrict__ Ub) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
+  constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   constexpr int TQS = NF * D * nf * nfp;      // traces of Q per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V>()));   // [T][D][nf][N]  forward Q, later dU_bar and D^T dU_bar
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   S* js = tq;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S, V>(M.tabs, P, sD, nullptr, lm, lp, Lm, Lp, n);
+  load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);  // node-indexed traces
   {
     const S* qsrc = Q + (size_t)e0 * D * H::STATE;
     const S* qbsrc = Qb + (size_t)e0 * D * H::STATE;
@@ -318,8 +319,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
       for (int m = 0; m < n; ++m) {
         const S x = v[H::node(m, line, a)];
-        sm += lm[m] * x;
-        sp += lp[m] * x;
+        sm += tb.lm[m] * x;
+        sp += tb.lp[m] * x;
       }
       tq[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + line] = sm;
       tq[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + line] = sp;
@@ -373,6 +374,15 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   const int e = e0 + t;
   if (active) {
     const S iJ = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
+    S lmq[D], lpq[D];
+    int fpq[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int qa = H::qa(q, a);
+      lmq[a] = lm[qa];
+      lpq[a] = lp[qa];
+      fpq[a] = H::fpoint(q, a);
+    }
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -380,9 +390,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         S s = qbs[((t * D + c) * nf + f) * N + q];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          const int fp = H::fpoint(q, a), qa = H::qa(q, a);
-          s += lm[qa] * tqb[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + fp];
-          s += lp[qa] * tqb[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + fp];
+          s += lmq[a] * tqb[(((t * NF + 2 * a) * D + c) * nf + f) * nfp + fpq[a]];
+          s += lpq[a] * tqb[(((t * NF + 2 * a + 1) * D + c) * nf + f) * nfp + fpq[a]];
         }
         qbs[((t * D + c) * nf + f) * N + q] = s * iJ;
       }
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       for (int m = 0; m < n; ++m) {
         S acc = 0;
 #pragma unroll
-        for (int k = 0; k < n; ++k) acc += sD[k * n + m] * x[k];
+        for (int k = 0; k < n; ++k) acc += tb.D[k][m] * x[k];
         v[H::node(m, line, b)] = acc;
       }
       // J_bar on the two faces normal to b: box: +-r_b sum_m L(+-)[m] P_b(m);
@@ -435,8 +444,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
           for (int m = 0; m < n; ++m) {
             const S y = pc[H::node(m, line, b)];
-            sm += Lm[m] * y;
-            sp += Lp[m] * y;
+            sm += tb.Lm[m] * y;
+            sp += tb.Lp[m] * y;
           }
           const size_t ge = (size_t)(e0 + tt) * NF;
           jm += M.geo.SnE[((ge + 2 * b) * D + c) * nfp + line] * sm;
@@ -448,8 +457,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
         for (int m = 0; m < n; ++m) {
           const S y = pb[H::node(m, line, b)];
-          sm += Lm[m] * y;
-          sp += Lp[m] * y;
+          sm += tb.Lm[m] * y;
+          sp += tb.Lp[m] * y;
         }
         const S r = M.geo.rh[(e0 + tt) * D + b];
         jm = -r * sm;
@@ -549,14 +558,22 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   if (t >= nel) return;
   const int e = e0 + t;
   const size_t off = (size_t)e * H::STATE + q;
+  S lmq[D], lpq[D];
+  int fpq[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int qa = H::qa(q, a);
+    lmq[a] = lm[qa];
+    lpq[a] = lp[qa];
+    fpq[a] = H::fpoint(q, a);
+  }
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
     S s = g[off + f * N];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const int fp = H::fpoint(q, a), qa = H::qa(q, a);
-      s += lm[qa] * tub[((t * NF + 2 * a) * nf + f) * nfp + fp];
-      s += lp[qa] * tub[((t * NF + 2 * a + 1) * nf + f) * nfp + fp];
+      s += lmq[a] * tub[((t * NF + 2 * a) * nf + f) * nfp + fpq[a]];
+      s += lpq[a] * tub[((t * NF + 2 * a + 1) * nf + f) * nfp + fpq[a]];
     }
     g[off + f * N] = s;
     if (cot.lam64_out) {  // ARK adjoint: lambda_n = lambda_{n+1} + sum_j nu_j, accumulated in FP64
