@@ -101,24 +101,33 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
         for (int f = 0; f < nf; ++f) Qv[c][f] = qp[(c * nf + f) * N];
     }
   }
-  {
-    const size_t base = (size_t)e0 * H::STATE;
-    for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) {
-      S lv = S(0);
-      if (cot.lam) {
-        lv = cot.lam[base + i];
-      } else if (cot.lam64 && (cot.c_lam != S(0) || cot.lam_out)) {
-        lv = (S)cot.lam64[base + i];
-        if (cot.lam_out) cot.lam_out[base + i] = lv;
+  if (tn < nel) {  // mu = c_lam lambda + sum_j c_j nu_j at this node, every field's loads issued together
+    const size_t off = (size_t)(e0 + tn) * H::STATE + qn;
+    S s[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) s[f] = S(0);
+    if (cot.lam) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] = cot.lam[off + f * N];
+    } else if (cot.lam64 && (cot.c_lam != S(0) || cot.lam_out)) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] = (S)cot.lam64[off + f * N];
+      if (cot.lam_out) {
+#pragma unroll
+        for (int f = 0; f < nf; ++f) cot.lam_out[off + f * N] = s[f];
       }
-      S s = cot.c_lam * lv;
-      for (int j = 0; j < cot.n_nu; ++j) s += cot.c_nu[j] * cot.nu[j][base + i];
-      if (CURV) {
-        const int t = i / H::STATE, q = i % N;
-        s *= M.geo.iJ[(size_t)(e0 + t) * N + q];
-      }
-      mus[i] = s;
     }
+#pragma unroll
+    for (int f = 0; f < nf; ++f) s[f] *= cot.c_lam;
+    for (int j = 0; j < cot.n_nu; ++j) {
+      const S c = cot.c_nu[j];
+      const S* nu = cot.nu[j] + off;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+    }
+    const S ij = CURV ? M.geo.iJ[(size_t)(e0 + tn) * N + qn] : S(1);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) mus[(tn * nf + f) * N + qn] = CURV ? s[f] * ij : s[f];
   }
   g_sync<V>();
   // one thread per line and direction: transposed weak divergence
@@ -397,21 +406,46 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       }
   }
   g_sync<V>();
-  // 3. dU_bar_b(q) = (box) r_b P_b  |  (curv) sum_c Ja[b][c] P_c   -> qs (forward Q no longer needed)
+  if (!CURV) {
+    // 3+4 (boxes): dU_bar_b = r_b P_b, so one pass over the lines of P_b gives
+    // r_b D_b^T P_b (-> qs, the forward Q is no longer needed) and the jump
+    // cotangents J_bar = -+r_b sum_m L(-+)[m] P_b(m) on the two faces normal to b
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
+        int tt, f, line;
+        line_item<nf, nfp>(i, tt, f, line);
+        const S* pb = qbs + ((tt * D + b) * nf + f) * N;
+        S* v = qs + ((tt * D + b) * nf + f) * N;
+        const S r = M.geo.rh[(e0 + tt) * D + b];
+        S x[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k) x[k] = pb[H::node(k, line, b)];
+        S sm = 0, sp = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          S acc = 0;
+#pragma unroll
+          for (int k = 0; k < n; ++k) acc += tb.D[k][m] * x[k];
+          v[H::node(m, line, b)] = r * acc;
+          sm += tb.Lm[m] * x[m];
+          sp += tb.Lp[m] * x[m];
+        }
+        js[((tt * NF + 2 * b) * nf + f) * nfp + line] = -r * sm;
+        js[((tt * NF + 2 * b + 1) * nf + f) * nfp + line] = r * sp;
+      }
+    }
+  } else {
+  // 3. dU_bar_b(q) = sum_c Ja[b][c] P_c   -> qs (forward Q no longer needed)
   if (active) {
 #pragma unroll
     for (int b = 0; b < D; ++b)
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        S s;
-        if (CURV) {
-          s = 0;
+        S s = 0;
 #pragma unroll
-          for (int c = 0; c < D; ++c)
-            s += M.geo.Ja[(((size_t)e * D + b) * D + c) * N + q] * qbs[((t * D + c) * nf + f) * N + q];
-        } else {
-          s = M.geo.rh[e * D + b] * qbs[((t * D + b) * nf + f) * N + q];
-        }
+        for (int c = 0; c < D; ++c)
+          s += M.geo.Ja[(((size_t)e * D + b) * D + c) * N + q] * qbs[((t * D + c) * nf + f) * N + q];
         qs[((t * D + b) * nf + f) * N + q] = s;
       }
   }
@@ -433,40 +467,26 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         for (int k = 0; k < n; ++k) acc += tb.D[k][m] * x[k];
         v[H::node(m, line, b)] = acc;
       }
-      // J_bar on the two faces normal to b: box: +-r_b sum_m L(+-)[m] P_b(m);
-      // curvilinear: sum_c Sn_c sum_m L(+-)[m] P_c(m)
+      // J_bar on the two faces normal to b: sum_c Sn_c sum_m L(+-)[m] P_c(m)
       S jm = 0, jp = 0;
-      if (CURV) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const S* pc = qbs + ((tt * D + c) * nf + f) * N;
-          S sm = 0, sp = 0;
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const S y = pc[H::node(m, line, b)];
-            sm += tb.Lm[m] * y;
-            sp += tb.Lp[m] * y;
-          }
-          const size_t ge = (size_t)(e0 + tt) * NF;
-          jm += M.geo.SnE[((ge + 2 * b) * D + c) * nfp + line] * sm;
-          jp += M.geo.SnE[((ge + 2 * b + 1) * D + c) * nfp + line] * sp;
-        }
-      } else {
-        const S* pb = qbs + ((tt * D + b) * nf + f) * N;
+      for (int c = 0; c < D; ++c) {
+        const S* pc = qbs + ((tt * D + c) * nf + f) * N;
         S sm = 0, sp = 0;
 #pragma unroll
         for (int m = 0; m < n; ++m) {
-          const S y = pb[H::node(m, line, b)];
+          const S y = pc[H::node(m, line, b)];
           sm += tb.Lm[m] * y;
           sp += tb.Lp[m] * y;
         }
-        const S r = M.geo.rh[(e0 + tt) * D + b];
-        jm = -r * sm;
-        jp = r * sp;
+        const size_t ge = (size_t)(e0 + tt) * NF;
+        jm += M.geo.SnE[((ge + 2 * b) * D + c) * nfp + line] * sm;
+        jp += M.geo.SnE[((ge + 2 * b + 1) * D + c) * nfp + line] * sp;
       }
       js[((tt * NF + 2 * b) * nf + f) * nfp + line] = jm;
       js[((tt * NF + 2 * b + 1) * nf + f) * nfp + line] = jp;
     }
+  }
   }
   g_sync<V>();
   // 5. U_bar += sum_b D_b^T dU_bar_b
@@ -527,6 +547,15 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);
+  // this thread's node: its running cotangent is read first (latency overlaps the face phase)
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
+  const bool act = t < nel;
+  const size_t off = (size_t)(e0 + t) * H::STATE + q;
+  S gq[nf];
+  if (act) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) gq[f] = g[off + f * N];
+  }
   {
     const S* src = TUb + (size_t)e0 * H::FACE;
     if (!VISC) {
@@ -554,10 +583,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
     }
   }
   g_sync<V>();
-  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
-  if (t >= nel) return;
-  const int e = e0 + t;
-  const size_t off = (size_t)e * H::STATE + q;
+  if (!act) return;
   S lmq[D], lpq[D];
   int fpq[D];
 #pragma unroll
@@ -569,7 +595,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   }
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
-    S s = g[off + f * N];
+    S s = gq[f];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       s += lmq[a] * tub[((t * NF + 2 * a) * nf + f) * nfp + fpq[a]];
