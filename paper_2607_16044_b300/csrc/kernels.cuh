@@ -195,6 +195,40 @@ __device__ __forceinline__ void line_item(int i, int& t, int& f, int& line) {
   t = i / (nfp * nf);
 }
 
+// Tile staging, one thread per node (rows of [T][ROWS][N] tile arrays) or per
+// face point (rows of [T][NF][nf][nfp]): each thread issues all of its loads
+// before its first store, so their latencies overlap.
+template <int D, int P, typename S, int V, int ROWS, typename Sin>
+__device__ __forceinline__ void stage_nodes(S* dst, const Sin* src, int nel, S* copy = nullptr) {
+  using H = Sh<D, P, V>;
+  constexpr int N = H::N;
+  const int t = g_tid<V>() / N, q = g_tid<V>() % N;
+  if (t >= nel) return;
+  S v[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) v[r] = (S)src[(t * ROWS + r) * N + q];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) dst[(t * ROWS + r) * N + q] = v[r];
+  if (copy) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) copy[(t * ROWS + r) * N + q] = v[r];
+  }
+}
+
+template <int D, int P, typename S, int V>
+__device__ __forceinline__ void stage_faces(S* dst, const S* src, int nel) {
+  using H = Sh<D, P, V>;
+  constexpr int nf = H::nf, nfp = H::nfp, NF = H::NF;
+  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+    const int fp = i % nfp, tf = i / nfp;  // tf = t * NF + face
+    S v[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) v[f] = src[(tf * nf + f) * nfp + fp];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) dst[(tf * nf + f) * nfp + fp] = v[f];
+  }
+}
+
 // Traces of a staged tile (us[t][f][q]): one thread per (element, field, line)
 // and direction loads the line once and writes both end values.
 template <int D, int P, typename S, int V>
@@ -237,13 +271,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
   S* lp = lm + H::n;
   const int e0 = g_index<V>() * H::T;
   const int nel = min(H::T, E - e0);
-  const Sin* src = U + (size_t)e0 * H::STATE;
-  S* sh = shadow ? shadow + (size_t)e0 * H::STATE : nullptr;
-  for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) {
-    const S v = (S)src[i];
-    us[i] = v;
-    if (sh) sh[i] = v;
-  }
+  stage_nodes<D, P, S, V, H::nf>(us, U + (size_t)e0 * H::STATE, nel,
+                                  shadow ? shadow + (size_t)e0 * H::STATE : nullptr);
   g_sync<V>();
   tile_traces<D, P, S, V>(us, nel, TU + (size_t)e0 * H::FACE);
 }
@@ -275,10 +304,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   S* Lp = Lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  {
-    const S* src = U + (size_t)e0 * H::STATE;
-    for (int i = g_tid<V>(); i < nel * H::STATE; i += g_size<V>()) us[i] = src[i];
-  }
+  stage_nodes<D, P, S, V, nf>(us, U + (size_t)e0 * H::STATE, nel);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
   // jumps Uhat - U^- at every own face point
   for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
@@ -648,10 +674,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   S* Lp = Lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  {
-    const S* src = FF + (size_t)e0 * H::FACE;
-    for (int i = g_tid<V>(); i < nel * H::FACE; i += g_size<V>()) ffs[i] = src[i];
-  }
+  stage_faces<D, P, S, V>(ffs, FF + (size_t)e0 * H::FACE, nel);
   const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool active = t < nel;
   const int e = e0 + t;

@@ -306,14 +306,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);  // node-indexed traces
-  {
-    const S* qsrc = Q + (size_t)e0 * D * H::STATE;
-    const S* qbsrc = Qb + (size_t)e0 * D * H::STATE;
-    for (int i = g_tid<V>(); i < nel * D * H::STATE; i += g_size<V>()) {
-      qs[i] = qsrc[i];
-      qbs[i] = qbsrc[i];
-    }
-  }
+  stage_nodes<D, P, S, V, D * nf>(qs, Q + (size_t)e0 * D * H::STATE, nel);
+  stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
   g_sync<V>();
   // 0. traces of Q (line pass)
 #pragma unroll
@@ -559,7 +553,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   {
     const S* src = TUb + (size_t)e0 * H::FACE;
     if (!VISC) {
-      for (int i = g_tid<V>(); i < nel * H::FACE; i += g_size<V>()) tub[i] = src[i];
+      stage_faces<D, P, S, V>(tub, src, nel);
     } else {
       // own trace cotangent plus half the neighbour's jump cotangent, per face point
       for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
