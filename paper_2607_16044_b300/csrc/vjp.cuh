@@ -30,7 +30,9 @@ struct VjpWork {
   void* Q;    // forward BR1 gradient            [E][D][nf][N]
   void* TUb;  // trace cotangents                 [E][2D][nf][nfp]
   void* Gb;   // viscous face-flux cotangents     [E][2D][nf][nfp]
-  void* JB;   // BR1 jump cotangents              [E][2D][nf][nfp]
+  void* JB;   // BR1 jump cotangents, stored in the layout of the element that receives them:
+              // [E][2D][nf][nfp] at (e, face, fp) holds the cotangent of the jump seen by the
+              // neighbour across that face (zero on walls)
   void* Qb;   // gradient cotangents              [E][D][nf][N]
 };
 
@@ -507,11 +509,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       jb[f] = js[((tt * NF + face) * nf + f) * nfp + fp];
       ubf[f] = tub[((tt * NF + face) * nf + f) * nfp + fp];
     }
-    if (M.nb[ee * NF + face] >= 0) {
+    const int k = ee * NF + face;
+    const int nbe = M.nb[k];
+    if (nbe >= 0) {  // scatter into the neighbour's own face slot (its gather reads it there)
+      const size_t on = ((size_t)nbe * NF + M.nbf[k]) * nf * nfp + orient_map<D, n>(M.ori[k], fp);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         ubf[f] -= S(0.5) * jb[f];
-        JB[o + f * nfp] = jb[f];
+        JB[on + f * nfp] = jb[f];
       }
     } else {
       S UL[nf];
@@ -555,24 +560,18 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
     if (!VISC) {
       stage_faces<D, P, S, V>(tub, src, nel);
     } else {
-      // own trace cotangent plus half the neighbour's jump cotangent, per face point
+      // own trace cotangent plus half the jump cotangent the neighbour scattered here
       for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
-        const int fp = i % nfp;
-        const int face = (i / nfp) % NF;
-        const int t = i / (nfp * NF);
-        const int e = e0 + t;
-        const int k = e * NF + face;
-        const int nbe = M.nb[k];
-        const int o = (t * NF + face) * nf * nfp + fp;
-        if (nbe >= 0) {
-          const int fpn = orient_map<D, n>(M.ori[k], fp);
-          const S* jb = JB + (((size_t)nbe * NF + M.nbf[k]) * nf) * nfp + fpn;
+        const int fp = i % nfp, tf = i / nfp;  // tf = t * NF + face
+        const S* jb = JB + (size_t)e0 * H::FACE;
+        S a[nf], c[nf];
 #pragma unroll
-          for (int f = 0; f < nf; ++f) tub[o + f * nfp] = src[o + f * nfp] + S(0.5) * jb[f * nfp];
-        } else {
-#pragma unroll
-          for (int f = 0; f < nf; ++f) tub[o + f * nfp] = src[o + f * nfp];
+        for (int f = 0; f < nf; ++f) {
+          a[f] = src[(tf * nf + f) * nfp + fp];
+          c[f] = jb[(tf * nf + f) * nfp + fp];
         }
+#pragma unroll
+        for (int f = 0; f < nf; ++f) tub[(tf * nf + f) * nfp + fp] = a[f] + S(0.5) * c[f];
       }
     }
   }
