@@ -348,8 +348,11 @@ dgx_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DGX_OK : DGX_E
 // Forward recompute (traces, BR1) then the four adjoint kernels.  g receives
 // nu = (df/dU)(U)^T mu with mu described by cot (see dgx::Cot).
 template <typename S>
+// One VJP of the residual: [traces, BR1 gradient,] element, face, BR1 adjoint and
+// (unless gather == false: the ARK adjoint defers it into the next reverse
+// stage's element kernel) the gather that finishes g.
 cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, const dgx::Cot<S>& fin, void* g,
-                      const dgx::VjpWork& vw, cudaStream_t st, bool have_forward = false) {
+                      const dgx::VjpWork& vw, cudaStream_t st, bool have_forward = false, bool gather = true) {
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   const dgx::VjpTable* v = (const dgx::VjpTable*)t->vjp;
@@ -366,7 +369,7 @@ cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, cons
     err = launch(h, DGX_K_VJP_FACE, st, [&] { return v->face(M, h->viscous, h->curv, vw, st); });
   if (err == cudaSuccess && h->viscous)
     err = launch(h, DGX_K_VJP_BR1, st, [&] { return v->br1(M, h->var[DGX_K_VJP_BR1], h->curv, vw, g, st); });
-  if (err == cudaSuccess)
+  if (err == cudaSuccess && gather)
     err = launch(h, DGX_K_VJP_GATHER, st, [&] { return v->gather(M, h->var[DGX_K_VJP_GATHER], h->viscous, vw, g, &fin, st); });
   return err;
 }
@@ -466,7 +469,11 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
       cot.lam = (const S*)(base + L.LAM);
     }
     cot.c_lam = (S)(dt * h->b[i]);
-    for (int j = i + 1; j < s; ++j) {
+    if (i < s - 1) {  // the element kernel finishes nu_{i+1} (its gather) and uses it directly
+      cot.nu_prev = NU(i + 1);
+      cot.c_prev = (S)(dt * h->A[(i + 1) * dgx::MAXSTAGES + i]);
+    }
+    for (int j = i + 2; j < s; ++j) {
       const double a = h->A[j * dgx::MAXSTAGES + i];
       if (a != 0.0) {
         cot.nu[cot.n_nu] = NU(j);
@@ -478,7 +485,7 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
       fin.lam64_out = lam64;
       for (int j = 1; j < s; ++j) fin.nu_all[fin.n_all++] = NU(j);
     }
-    const cudaError_t err = vjp_chain<S>(h, y, cot, fin, NU(i), vw, st, /*have_forward=*/true);
+    const cudaError_t err = vjp_chain<S>(h, y, cot, fin, NU(i), vw, st, /*have_forward=*/true, /*gather=*/i == 0);
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -584,12 +591,16 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       double fl = 0, by = 0;
       if (h->stages > 0) {
         for (int i = 0; i < st; ++i) {
+          const bool first = i == st - 1;  // first reverse stage: no gather to finish
           int nnu = 0;
-          for (int j = i + 1; j < st; ++j) nnu += h->A[j * dgx::MAXSTAGES + i] != 0.0;
-          const bool first = i == st - 1;
+          for (int j = i + (first ? 1 : 2); j < st; ++j) nnu += h->A[j * dgx::MAXSTAGES + i] != 0.0;
           const double lam_b = h->fp64 ? (h->b[i] != 0.0 ? 8.0 : 0.0) : (first ? 8.0 + 4.0 : (h->b[i] != 0.0 ? 4.0 : 0.0));
-          fl += E * STATE * 2 * (1 + nnu);
+          fl += E * STATE * 2 * (1 + nnu + (first ? 0 : 1));
           by += E * STATE * (lam_b + nnu * s);
+          if (!first) {  // fused gather of nu_{i+1}: trace cotangents (+ jump cotangents), nu read + written
+            fl += E * (STATE * 4 * D + (v ? FACE * 2 : 0));
+            by += E * ((FACE * (v ? 2 : 1) + 2 * STATE) * s);
+          }
         }
         fl /= st;
         by /= st;

@@ -69,23 +69,33 @@ struct Cot {
   double* lam64_out;
   const S* nu_all[MAXSTAGES];
   int n_all;
+  // ARK adjoint, fused gather (k_vjp_elem<GATHER>): nu_prev = the previous reverse
+  // stage's partial nu (volume part, finished here with its trace cotangents and
+  // written back), entering mu with coefficient c_prev
+  S* nu_prev;
+  S c_prev;
 };
 
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC, bool CURV, int V>
+// GATHER (ARK adjoint, every reverse stage but the first): the kernel first
+// finishes the previous reverse stage's nu (the gather of k_vjp_gather, from
+// TUb and JB of that stage, which are still in the workspace) and uses it
+// directly in this stage's mu.
+template <int D, int P, typename S, bool VISC, bool CURV, int V, bool GATHER>
 __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, const S* __restrict__ U,
                                                                    const S* __restrict__ Q, Cot<S> cot,
                                                                    S* __restrict__ FFb, S* __restrict__ Ub,
-                                                                   S* __restrict__ Qb) {
+                                                                   S* __restrict__ Qb, const S* __restrict__ TUbp,
+                                                                   const S* __restrict__ JBp) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* mus = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_velem_g<D, P, S, V>()));  // [T][nf][N]     cotangent / J
   S* fb = mus + T * H::STATE;                // [T][D][nf][N]  contravariant flux cotangents
-  S* sDh = fb + T * D * H::STATE;
-  S* Lm = sDh + n * n;
-  S* Lp = Lm + n;
+  S* tubs = fb;                              // GATHER: [T][NF][nf][nfp] trace cotangents (before fb is written)
+  S* lms = fb + T * D * H::STATE;            // node-indexed trace weights (GATHER)
+  S* lps = lms + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   // per-node inputs of the pointwise adjoint, read first (latency overlaps the contractions)
@@ -101,6 +111,50 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
       for (int c = 0; c < (VISC ? D : 1); ++c)
 #pragma unroll
         for (int f = 0; f < nf; ++f) Qv[c][f] = qp[(c * nf + f) * N];
+    }
+  }
+  S nuq[nf];  // GATHER: the finished nu of the previous reverse stage at this node
+  if (GATHER) {
+    const size_t off = (size_t)(e0 + tn) * H::STATE + qn;
+    if (tn < nel) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) nuq[f] = cot.nu_prev[off + f * N];
+    }
+    load_tab<S, V>(M.tabs, P, nullptr, nullptr, lms, lps, nullptr, nullptr, n);
+    // own trace cotangent plus half the jump cotangent the neighbour scattered here
+    const S* tsrc = TUbp + (size_t)e0 * H::FACE;
+    const S* jsrc = JBp + (size_t)e0 * H::FACE;
+    for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+      const int fp = i % nfp, tf = i / nfp;  // tf = t * NF + face
+      S a[nf], c[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        a[f] = tsrc[(tf * nf + f) * nfp + fp];
+        c[f] = VISC ? jsrc[(tf * nf + f) * nfp + fp] : S(0);
+      }
+#pragma unroll
+      for (int f = 0; f < nf; ++f) tubs[(tf * nf + f) * nfp + fp] = a[f] + S(0.5) * c[f];
+    }
+    g_sync<V>();
+    if (tn < nel) {
+      S lmq[D], lpq[D];
+      int fpq[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int qa = H::qa(qn, a);
+        lmq[a] = lms[qa];
+        lpq[a] = lps[qa];
+        fpq[a] = H::fpoint(qn, a);
+      }
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          nuq[f] += lmq[a] * tubs[((tn * NF + 2 * a) * nf + f) * nfp + fpq[a]];
+          nuq[f] += lpq[a] * tubs[((tn * NF + 2 * a + 1) * nf + f) * nfp + fpq[a]];
+        }
+        cot.nu_prev[off + f * N] = nuq[f];
+      }
     }
   }
   if (tn < nel) {  // mu = c_lam lambda + sum_j c_j nu_j at this node, every field's loads issued together
@@ -121,6 +175,10 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
     }
 #pragma unroll
     for (int f = 0; f < nf; ++f) s[f] *= cot.c_lam;
+    if (GATHER) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] += cot.c_prev * nuq[f];
+    }
     for (int j = 0; j < cot.n_nu; ++j) {
       const S c = cot.c_nu[j];
       const S* nu = cot.nu[j] + off;
@@ -648,10 +706,19 @@ struct VjpOps {
   template <bool VISC, bool CURV, int V>
   static cudaError_t elem_v(const Mesh<S>& M, const S* U, const VjpWork& w, const Cot<S>& c, S* Ub,
                             cudaStream_t st) {
-    static bool done = false;
-    auto k = k_vjp_elem<D, P, S, VISC, CURV, V>;
-    allow_smem_once(k, smem_elem<V>(), done);
-    k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb);
+    if (c.nu_prev) {
+      static bool done = false;
+      auto k = k_vjp_elem<D, P, S, VISC, CURV, V, true>;
+      allow_smem_once(k, smem_elem<V>(), done);
+      k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb,
+                                                               (const S*)w.TUb, (const S*)w.JB);
+    } else {
+      static bool done = false;
+      auto k = k_vjp_elem<D, P, S, VISC, CURV, V, false>;
+      allow_smem_once(k, smem_elem<V>(), done);
+      k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb,
+                                                               nullptr, nullptr);
+    }
     return cudaGetLastError();
   }
   template <bool VISC, bool CURV>
