@@ -270,6 +270,26 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
             "mesh": mesh, "phys": phys, "steps": steps, "solver": s, "variants": variants}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant FP32 kernel from one ncu capture of the bench workload (summary and
+# command in profiles/), valid only while the kernel sources hash to `sources`.
+NCU_TRAFFIC = {"kernel": "vjp_br1", "bytes": 105577216,
+               "sources": "3f9c525632a65dd3702700d63ceeeb5ae0149a3515885934ca70521ec9dd031c"}
+
+
+def sources_hash():
+    """sha256 over the CUDA sources and the C header the library is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_2607_16044_b300", "csrc"), os.path.join(ROOT, "include")):
+        for name in sorted(os.listdir(d)):
+            if name.endswith((".cu", ".cuh", ".h")):
+                h.update(name.encode())
+                with open(os.path.join(d, name), "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()
+
+
 def roofline(res, prec, pk):
     """Roofline of the dominant kernel (largest summed device time): algorithmic
     flops and bytes per launch from the library (dgx_kernel_work: counted
@@ -302,6 +322,9 @@ def roofline(res, prec, pk):
     out.update({"kernel": name, "launches": launches, "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "algorithmic_bytes": int(bytes_l), "algorithmic_flops": int(flops_l),
                 "traffic": None, "kernel_shares": shares, "per_kernel": per_kernel})
+    if prec == "fp32" and name == NCU_TRAFFIC["kernel"] and sources_hash() == NCU_TRAFFIC["sources"]:
+        out["traffic"] = NCU_TRAFFIC["bytes"]
+        out["traffic_source"] = "ncu capture (profiles/k_vjp_br1_channel2d_p4_fp32.md), bytes per launch"
     return out
 
 
@@ -387,7 +410,7 @@ def ensemble_perf(prec="fp32", reps=10):
             "dof_evals_per_s": round(4 * dofs / (ms / 1e3), 1), "dtype": prec}
 
 
-def tgv_perf(reps=10):
+def tgv_perf(reps=10, profile_range=False):
     """32^3 Taylor-Green vortex, p = 3: forward residual time in FP64 and in FP32
     with each contraction engine of the element kernel (CUDA cores, TF32 and
     3xTF32 tensor cores); per FP32 leg the element kernel's own time (event
@@ -409,6 +432,12 @@ def tgv_perf(reps=10):
         U = torch.as_tensor(U0).to("cuda", dt).contiguous()
         f = s.rhs(U)
         ms = _time_events(lambda: s.rhs(U, out=f), reps, flush)
+        if profile_range and prec == "fp32":   # one FP32 residual per engine inside the profiler range
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+            s.rhs(U, out=f)
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
         s.profile(True)
         s.profile_reset()
         for _ in range(reps):
@@ -531,7 +560,8 @@ def main():
     ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--legs", default="fp32,fp64", help="precisions to time (profiling runs may pick one)")
+    ap.add_argument("--legs", default="fp32,fp64",
+                    help="precisions to time (profiling runs may pick one), or 'tgv' for the TGV engine comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -552,6 +582,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     legs = args.legs.split(",")
+    if legs == ["tgv"]:   # the TGV contraction-engine comparison alone (profiling runs)
+        print(json.dumps({"tgv": tgv_perf(profile_range=args.profile_range)}))
+        return
     if legs == ["fp64"]:
         r = time_gpu("fp64", args.steps, args.warmup, profile_range=args.profile_range)
         print(json.dumps({"leg": "fp64", "ms_per_step": r["ms"], "prof": r["prof"]}))
