@@ -376,7 +376,7 @@ cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, cons
 
 template <typename S>
 dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st,
-                    const double* dte = nullptr) {
+                    const S* dte = nullptr) {
   const Layout L = layout(h, DGX_OP_ARK);
   const dgx::Work w = work_at(h, workspace, L);
   char* base = (char*)workspace;
@@ -404,13 +404,13 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     sa.i = i;
     sa.last = (i == s - 1);
     if (!sa.last)
-      for (int j = 0; j <= i; ++j) sa.ca[j] = h->A[(i + 1) * dgx::MAXSTAGES + j];
-    for (int j = 0; j < s; ++j) sa.cb[j] = h->b[j];
+      for (int j = 0; j <= i; ++j) sa.ca[j] = (S)h->A[(i + 1) * dgx::MAXSTAGES + j];
+    for (int j = 0; j < s; ++j) sa.cb[j] = (S)h->b[j];
+    const S dts = (S)dt;  // the kernels form the same S products from a per-element dt
     for (int j = 0; j < s; ++j) {
-      sa.caf[j] = (S)(dt * sa.ca[j]);
-      sa.cbf[j] = (S)(dt * sa.cb[j]);
+      sa.caf[j] = dts * sa.ca[j];
+      sa.cbf[j] = dts * sa.cb[j];
     }
-    sa.dt = dt;
     sa.dte = dte;
     sa.base = y0;
     sa.Un = U64;
@@ -1167,7 +1167,7 @@ struct dgx_batch {
     int64_t off = 0;                 // offset (doubles) of the group in the packed state
     std::vector<int> members;        // instance indices
     std::vector<int64_t> elem_off;   // element offset of each member inside the group
-    double* d_dte = nullptr;         // per-element time step
+    void* d_dte = nullptr;           // per-element time step in the group's precision
   };
   int count = 0;
   std::vector<int64_t> offset;       // per instance (doubles), offset[count] = total
@@ -1201,8 +1201,8 @@ void batch_free(dgx_batch* b) {
 dgx_status batch_run(dgx_batch* b, double* U64, void* ws, cudaStream_t st) {
   for (auto& g : b->groups) {
     dgx_handle* h = g.h;
-    const dgx_status s = h->fp64 ? ark_impl<double>(h, U64 + g.off, 0.0, nullptr, ws, st, g.d_dte)
-                                 : ark_impl<float>(h, U64 + g.off, 0.0, nullptr, ws, st, g.d_dte);
+    const dgx_status s = h->fp64 ? ark_impl<double>(h, U64 + g.off, 0.0, nullptr, ws, st, (const double*)g.d_dte)
+                                 : ark_impl<float>(h, U64 + g.off, 0.0, nullptr, ws, st, (const float*)g.d_dte);
     if (s != DGX_OK) return s;
   }
   return DGX_OK;
@@ -1281,11 +1281,11 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
     if ((st = dgx_set_tableau(g.h, r->stages, A.data(), r->b, r->c)) != DGX_OK) break;
     for (int k = 0; k < DGX_KERNEL_KINDS; ++k) g.h->var[k] = r->var[k];
     g.h->contraction = r->contraction;
-    if (cudaMalloc((void**)&g.d_dte, (size_t)E * sizeof(double)) != cudaSuccess) {
+    if (cudaMalloc((void**)&g.d_dte, (size_t)E * g.h->s) != cudaSuccess) {
       st = DGX_ENOMEM;
       break;
     }
-    if (cudaMemset(g.d_dte, 0, (size_t)E * sizeof(double)) != cudaSuccess) {
+    if (cudaMemset(g.d_dte, 0, (size_t)E * g.h->s) != cudaSuccess) {
       st = DGX_ECUDA;
       break;
     }
@@ -1331,8 +1331,14 @@ dgx_status dgx_batch_set_dt(dgx_batch* b, const double* dt) {
       const int64_t e1 = (m + 1 < g.members.size()) ? g.elem_off[m + 1] : g.h->E;
       for (int64_t e = e0; e < e1; ++e) dte[e] = dt[g.members[m]];
     }
-    if (cudaMemcpy(g.d_dte, dte.data(), dte.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-      return DGX_ECUDA;
+    cudaError_t err;
+    if (g.h->fp64) {
+      err = cudaMemcpy(g.d_dte, dte.data(), dte.size() * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+      const std::vector<float> dtf(dte.begin(), dte.end());
+      err = cudaMemcpy(g.d_dte, dtf.data(), dtf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (err != cudaSuccess) return DGX_ECUDA;
   }
   for (int i = 0; i < b->count; ++i) b->dt[i] = dt[i];
   b->dt_set = true;

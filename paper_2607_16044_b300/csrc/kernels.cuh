@@ -134,12 +134,15 @@ constexpr int MAXSTAGES = 8;
 template <typename S>
 struct Stage {
   const S* k[MAXSTAGES];   // k_0 .. k_{i-1}
-  double ca[MAXSTAGES];    // a_{i+1, j}, j <= i
-  double cb[MAXSTAGES];    // b_j (last stage)
-  S caf[MAXSTAGES];        // S(dt a_{i+1, j}) and S(dt b_j), rounded once on the host (used
-  S cbf[MAXSTAGES];        // unless dte is given: FP64 arithmetic is slow on this part)
-  double dt;               // time step, unless dte is given
-  const double* dte;       // per-element time step (batched instances) or nullptr
+  // Stage coefficients in the working precision, formed as products of S
+  // values (S(dt) * S(a)) so that per-element and uniform time steps give
+  // identical numbers and FP32 kernels do no FP64 arithmetic (FP64 runs at
+  // ~1/64 of the FP32 rate on this part):
+  S caf[MAXSTAGES];        // S(dt) S(a_{i+1, j}), j <= i      (uniform dt)
+  S cbf[MAXSTAGES];        // S(dt) S(b_j)  (last stage)      (uniform dt)
+  S ca[MAXSTAGES];         // S(a_{i+1, j})                    (with dte)
+  S cb[MAXSTAGES];         // S(b_j)                           (with dte)
+  const S* dte;            // per-element time step in S (batched instances) or nullptr
   int i;                   // this stage (0-based)
   int last;
   const S* base;           // y = base + sum ca_j k_j (FP64: U_n itself, FP32: fl32(U_n))
@@ -180,10 +183,36 @@ constexpr size_t smem_br1_g() {
   return r16(sizeof(S) * (h::T * h::STATE + h::T * h::FACE + h::T * D * h::STATE + h::T * h::NF * D * h::nf * h::nfp +
                           h::n * h::n + 4 * h::n));
 }
+// Element strides (in scalars) of the element kernels' shared tiles, padded so
+// that the line passes of neighbouring elements fall in different banks: the
+// [T][D][nf][N] flux tile and the [T][nf][N] state tile whose traces are
+// emitted.  Pads minimise the mean wavefronts per warp access of the line
+// passes (threads over (element, field, line), line fastest) for each tile
+// shape of the CTA variants, found by enumerating the 32 residues.
+template <int D, int P, int V>
+constexpr int flux_pad() {
+  if (V > 2) return 0;  // one element per warp: nothing to separate
+  constexpr int p2[6] = {0, 1, 28, 5, 28, 15};
+  constexpr int p3[6] = {0, 15, 18, 5, 30, 15};
+  return D == 2 ? p2[P] : (P == 4 && V == 0) || (P == 5 && V < 2) ? 0 : p3[P];
+}
+template <int D, int P, int V>
+constexpr int state_pad() {
+  if (V > 2) return 0;
+  return (D == 2 && (P == 3 || P == 5)) ? (P == 3 ? 5 : 1) : (D == 3 && (P == 1 || P == 3)) ? (P == 1 ? 1 : 5) : 0;
+}
+template <int D, int P, int V>
+constexpr int elem_flux_stride() {
+  return D * Sh<D, P, V>::STATE + flux_pad<D, P, V>();
+}
+template <int D, int P, int V>
+constexpr int elem_state_stride() {
+  return Sh<D, P, V>::STATE + state_pad<D, P, V>();
+}
 template <int D, int P, typename S, int V>
 constexpr size_t smem_elem_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (h::T * D * h::STATE + h::T * h::FACE + h::n * h::n + 4 * h::n));
+  return r16(sizeof(S) * (h::T * elem_flux_stride<D, P, V>() + h::T * h::FACE + h::n * h::n + 4 * h::n));
 }
 
 // Work items of a line pass along direction a: (element t, field f, line), the
@@ -231,8 +260,8 @@ __device__ __forceinline__ void stage_faces(S* dst, const S* src, int nel) {
 
 // Traces of a staged tile (us[t][f][q]): one thread per (element, field, line)
 // and direction loads the line once and writes both end values.
-template <int D, int P, typename S, int V>
-__device__ __forceinline__ void tile_traces(const S* us, int nel, S* dst) {
+template <int D, int P, typename S, int V, int ES = Sh<D, P, V>::STATE>
+__device__ __forceinline__ void tile_traces(const S* us, int nel, S* dst) {  // us: [T][nf][N], element stride ES
   using H = Sh<D, P, V>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, N = H::N;
   constexpr Tab1<S> tb = make_tab1<S>(P);
@@ -241,7 +270,7 @@ __device__ __forceinline__ void tile_traces(const S* us, int nel, S* dst) {
     for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
       int t, f, line;
       line_item<nf, nfp>(i, t, f, line);
-      const S* v = us + (t * nf + f) * N;
+      const S* v = us + t * ES + f * N;
       S sm = 0, sp = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
@@ -541,13 +570,14 @@ __global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ T
 // increment sum_{j<i} dt b_j k_j.  base(f), kj(j, f), un(f) fetch the inputs;
 // each k_j term is added in the same order (j ascending) for every field.
 template <int nf, typename S, typename Base, typename Kj, typename Un>
-__device__ __forceinline__ void stage_prefix(const Stage<S>& st, double dt, Base base, Kj kj, Un un, S (&pre)[nf],
+__device__ __forceinline__ void stage_prefix(const Stage<S>& st, int e, Base base, Kj kj, Un un, S (&pre)[nf],
                                              double (&pre64)[nf]) {
+  const S dte = st.dte ? st.dte[e] : S(0);
   if (!st.last) {
 #pragma unroll
     for (int f = 0; f < nf; ++f) pre[f] = base(f);
     for (int j = 0; j < st.i; ++j) {
-      const S c = st.dte ? (S)(dt * st.ca[j]) : st.caf[j];
+      const S c = st.dte ? dte * st.ca[j] : st.caf[j];
 #pragma unroll
       for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
     }
@@ -558,7 +588,7 @@ __device__ __forceinline__ void stage_prefix(const Stage<S>& st, double dt, Base
       pre[f] = S(0);
     }
     for (int j = 0; j < st.i; ++j) {
-      const S c = st.dte ? (S)(dt * st.cb[j]) : st.cbf[j];
+      const S c = st.dte ? dte * st.cb[j] : st.cbf[j];
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         const S kv = kj(j, f);
@@ -613,10 +643,11 @@ __device__ __forceinline__ void node_flux(const Gas<S>& gas, const S (&Uq)[D + 2
 // or at the last stage U_{n+1} = U_n + sum_j dt b_j k_j accumulated in FP64.
 // off is the node's offset in the global [E][nf][N] arrays; returns y.
 template <int nf, typename S>
-__device__ __forceinline__ void stage_update(const Stage<S>& st, double dt, size_t off, int N, const S (&res)[nf],
+__device__ __forceinline__ void stage_update(const Stage<S>& st, int e, size_t off, int N, const S (&res)[nf],
                                              const S (&pre)[nf], const double (&pre64)[nf], S (&y)[nf]) {
+  const S dte = st.dte ? st.dte[e] : S(0);
   if (!st.last) {
-    const S ci = st.dte ? (S)(dt * st.ca[st.i]) : st.caf[st.i];
+    const S ci = st.dte ? dte * st.ca[st.i] : st.caf[st.i];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       const S acc = pre[f] + ci * res[f];
@@ -625,7 +656,7 @@ __device__ __forceinline__ void stage_update(const Stage<S>& st, double dt, size
       st.Y[off + f * N] = acc;
     }
   } else {
-    const S cbi = st.dte ? (S)(dt * st.cb[st.i]) : st.cbf[st.i];
+    const S cbi = st.dte ? dte * st.cb[st.i] : st.cbf[st.i];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       double un = pre64[f];
@@ -665,8 +696,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N]  (reused for the next state's traces)
-  S* ffs = fs + T * D * H::STATE;            // [T][NF][nf][nfp]
+  constexpr int FES = elem_flux_stride<D, P, V>(), SES = elem_state_stride<D, P, V>();
+  S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N] (stride FES), then the next state [T][nf][N] (stride SES)
+  S* ffs = fs + T * FES;                     // [T][NF][nf][nfp]
   S* sDh = ffs + T * H::FACE;
   S* lm = sDh + n * n;
   S* lp = lm + n;
@@ -686,7 +718,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   if (MODE == 1 && active) {
     const size_t off = (size_t)e * H::STATE + q;
     stage_prefix<nf, S>(
-        st, st.dte ? st.dte[e] : st.dt, [&](int f) { return st.base[off + f * N]; },
+        st, e, [&](int f) { return st.base[off + f * N]; },
         [&](int j, int f) { return st.k[j][off + f * N]; }, [&](int f) { return st.Un[off + f * N]; }, pre, pre64);
   }
   if (active) {
@@ -701,7 +733,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = Fa[a][f];
+      for (int f = 0; f < nf; ++f) fs[t * FES + (a * nf + f) * N + q] = Fa[a][f];
   }
   g_sync<V>();
   // weak divergence + lift, one thread per line and direction, in place in fs
@@ -710,7 +742,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
     for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
       int tt, f, line;
       line_item<nf, nfp>(i, tt, f, line);
-      S* v = fs + ((tt * D + a) * nf + f) * N;
+      S* v = fs + tt * FES + (a * nf + f) * N;
       S x[n];
 #pragma unroll
       for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
@@ -734,7 +766,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) res[f] += fs[((t * D + a) * nf + f) * N + q];
+      for (int f = 0; f < nf; ++f) res[f] += fs[t * FES + (a * nf + f) * N + q];
     if (CURV) {
       const S iJ = M.geo.iJ[(size_t)e * N + q];
 #pragma unroll
@@ -754,14 +786,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   //      last stage: U_{n+1} = U_n + sum_j dt b_j k_j in FP64.
   S y[nf];
   if (active)
-    stage_update<nf, S>(st, st.dte ? st.dte[e] : st.dt, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
+    stage_update<nf, S>(st, e, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
   g_sync<V>();  // everyone is done with fs
   if (active) {
 #pragma unroll
-    for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
+    for (int f = 0; f < nf; ++f) fs[t * SES + f * N + q] = y[f];
   }
   g_sync<V>();
-  tile_traces<D, P, S, V>(fs, nel, st.TU + (size_t)e0 * H::FACE);
+  tile_traces<D, P, S, V, SES>(fs, nel, st.TU + (size_t)e0 * H::FACE);
 }
 
 }  // namespace dgx

@@ -44,8 +44,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
   __shared__ PipeState ps;
   const uint32_t buf_bytes = in.bytes_per_elem * T;
   auto buf = [&](int b) { return smem_raw + (size_t)b * buf_bytes; };  // the two tile buffers
-  S* fs = reinterpret_cast<S*>(smem_raw + 2 * buf_bytes);  // [T][D][nf][N]
-  S* sDh = fs + T * D * H::STATE;
+  constexpr int FES = elem_flux_stride<D, P, V>(), SES = elem_state_stride<D, P, V>();
+  S* fs = reinterpret_cast<S*>(smem_raw + 2 * buf_bytes);  // [T][D][nf][N] (stride FES), then [T][nf][N] (stride SES)
+  S* sDh = fs + T * FES;
   S* lm = sDh + n * n;
   S* lp = lm + n;
   S* Lm = lp + n;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
     if (MODE == 1 && active) {
       const int off = t * H::STATE + q;
       stage_prefix<nf, S>(
-          st, st.dte ? st.dte[e] : st.dt, [&](int f) { return bases[off + f * N]; },
+          st, e, [&](int f) { return bases[off + f * N]; },
           [&](int j, int f) { return kss[(size_t)j * T * H::STATE + off + f * N]; },
           [&](int f) { return Uns[off + f * N]; }, pre, pre64);
     }
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) fs[((t * D + a) * nf + f) * N + q] = Fa[a][f];
+        for (int f = 0; f < nf; ++f) fs[t * FES + (a * nf + f) * N + q] = Fa[a][f];
     }
     __syncthreads();
 #pragma unroll
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
       for (int i = threadIdx.x; i < nel * nf * nfp; i += blockDim.x) {
         int tt, f, line;
         line_item<nf, nfp>(i, tt, f, line);
-        S* v = fs + ((tt * D + a) * nf + f) * N;
+        S* v = fs + tt * FES + (a * nf + f) * N;
         S x[n];
 #pragma unroll
         for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) res[f] += fs[((t * D + a) * nf + f) * N + q];
+        for (int f = 0; f < nf; ++f) res[f] += fs[t * FES + (a * nf + f) * N + q];
       if (CURV) {
         const S iJ = iJs[t * N + q];
 #pragma unroll
@@ -152,14 +153,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
     }
     S y[nf];
     if (active)
-      stage_update<nf, S>(st, st.dte ? st.dte[e] : st.dt, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
+      stage_update<nf, S>(st, e, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
     __syncthreads();  // everyone is done with fs
     if (active) {
 #pragma unroll
-      for (int f = 0; f < nf; ++f) fs[(t * nf + f) * N + q] = y[f];
+      for (int f = 0; f < nf; ++f) fs[t * SES + f * N + q] = y[f];
     }
     __syncthreads();
-    tile_traces<D, P, S, V>(fs, nel, st.TU + (size_t)e0 * H::FACE);
+    tile_traces<D, P, S, V, SES>(fs, nel, st.TU + (size_t)e0 * H::FACE);
     __syncthreads();  // buffer and fs free for the next tile
   }
 }

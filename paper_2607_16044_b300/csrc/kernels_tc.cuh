@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
   if (MODE == 1 && active) {
     const size_t off = (size_t)e * H::STATE + q;
     stage_prefix<nf, S>(
-        st, st.dte ? st.dte[e] : st.dt, [&](int f) { return st.base[off + f * N]; },
+        st, e, [&](int f) { return st.base[off + f * N]; },
         [&](int j, int f) { return st.k[j][off + f * N]; }, [&](int f) { return st.Un[off + f * N]; }, pre, pre64);
   }
   if (active) {
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
   }
   S y[nf];
   if (active)
-    stage_update<nf, S>(st, st.dte ? st.dte[e] : st.dt, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
+    stage_update<nf, S>(st, e, (size_t)e * H::STATE + q, N, res, pre, pre64, y);
   __syncthreads();  // everyone is done with fs
   if (active) {
 #pragma unroll

@@ -144,7 +144,8 @@ struct Ops {
   static cudaError_t elem_p_v(const Mesh<S>& M, const TileIn& in, S* out, const Stage<S>& sa, int nsm,
                               cudaStream_t st, bool& used) {
     using h = H<V>;
-    const size_t smem = 2 * (size_t)h::T * in.bytes_per_elem + sizeof(S) * (h::T * D * h::STATE + h::n * h::n + 4 * h::n);
+    const size_t smem =
+        2 * (size_t)h::T * in.bytes_per_elem + sizeof(S) * (h::T * elem_flux_stride<D, P, V>() + h::n * h::n + 4 * h::n);
     if (smem + sizeof(PipeState) > SMEM_LIMIT) {  // static pipeline state shares the per-CTA limit
       used = false;
       return cudaSuccess;
