@@ -431,11 +431,11 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       for (int f = 0; f < nf; ++f) tqb[(((t * NF + face) * D + c) * nf + f) * nfp + fp] = tqbv[c][f];
   }
   g_sync<V>();
-  // 2. Q_bar += transposed traces of TQ_bar; then P = (iJ) Q_bar in place
+  // 2. (curvilinear) Q_bar += transposed traces of TQ_bar; then P = iJ Q_bar in place
   const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool active = t < nel;
   const int e = e0 + t;
-  if (active) {
+  if (CURV && active) {
     const S iJ = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
     S lmq[D], lpq[D];
     int fpq[D];
@@ -459,11 +459,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         qbs[((t * D + c) * nf + f) * N + q] = s * iJ;
       }
   }
-  g_sync<V>();
+  if (CURV) g_sync<V>();
   if (!CURV) {
-    // 3+4 (boxes): dU_bar_b = r_b P_b, so one pass over the lines of P_b gives
-    // r_b D_b^T P_b (-> qs, the forward Q is no longer needed) and the jump
-    // cotangents J_bar = -+r_b sum_m L(-+)[m] P_b(m) on the two faces normal to b
+    // 2+3+4 (boxes): only component b of P feeds direction b, so each line of
+    // P_b = Q_bar_b + (transposed traces of TQ_bar)_b is assembled where it is
+    // used; one pass then gives r_b D_b^T P_b (-> qs, the forward Q is no
+    // longer needed) and the jump cotangents J_bar = -+r_b sum_m L(-+)[m] P_b(m)
+    // on the two faces normal to b.  Along a line the index in every other
+    // direction a is constant, so each such face contributes one weight pair.
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
@@ -472,9 +475,22 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
         const S* pb = qbs + ((tt * D + b) * nf + f) * N;
         S* v = qs + ((tt * D + b) * nf + f) * N;
         const S r = M.geo.rh[(e0 + tt) * D + b];
+        auto tqb_at = [&](int face, int fp) { return tqb[(((tt * NF + face) * D + b) * nf + f) * nfp + fp]; };
+        const S tbm = tqb_at(2 * b, line), tbp = tqb_at(2 * b + 1, line);
         S x[n];
 #pragma unroll
-        for (int k = 0; k < n; ++k) x[k] = pb[H::node(k, line, b)];
+        for (int k = 0; k < n; ++k) x[k] = pb[H::node(k, line, b)] + tb.lm[k] * tbm + tb.lp[k] * tbp;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          if (a == b) continue;
+          const int qa = H::qa(H::node(0, line, b), a);
+          const S wm = lm[qa], wp = lp[qa];
+#pragma unroll
+          for (int k = 0; k < n; ++k) {
+            const int fpk = H::fpoint(H::node(k, line, b), a);
+            x[k] += wm * tqb_at(2 * a, fpk) + wp * tqb_at(2 * a + 1, fpk);
+          }
+        }
         S sm = 0, sp = 0;
 #pragma unroll
         for (int m = 0; m < n; ++m) {
