@@ -291,3 +291,55 @@ def test_channel3d_config_full_size_sampled_fp32():
     record("channel3d-fp32", scaled=ferr, vjp_rel=gerr, sampled=len(rows))
     assert ferr < 1e-5, ferr
     assert gerr < 1e-4, gerr
+
+
+def _ark_adjoint_vs_oracle(mesh, phys, prec, dt, seed, ys_from_gpu=False):
+    """One ARS(3,4,3) step with stage checkpoints, then its adjoint, against the
+    oracle's reverse recurrence (FP32: linearised at the GPU's own stage states)."""
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    U0 = I.random_state(mesh, seed)
+    lam0 = I.gaussian_cotangent(U0.shape, seed + 1)
+    s = Solver(mesh, phys, prec)
+    s.set_tableau(*ars343_explicit())
+    U = torch.as_tensor(U0).cuda()
+    stages = s.stage_buffer()
+    s.ark_step_stages(U, dt, stages)
+    lam = torch.as_tensor(lam0).cuda()
+    s.ark_adjoint_step(stages, lam, dt)
+    s.check()
+    op = DGOperator(mesh, gas_of(phys))
+    A, b, c = ark.ars343()
+    if ys_from_gpu:
+        ys = [torch.as_tensor(s.stage_state(stages, i).double().cpu().numpy()) for i in range(4)]
+    else:
+        _, ys, _ = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b, return_stages=True)
+    ref = ark.erk_adjoint_step(lambda y, mu: vjp(op, y, mu), ys, torch.as_tensor(lam0), dt, A, b).numpy()
+    return rel_err(lam.cpu().numpy() - lam0, ref - lam0)
+
+
+def test_ark_adjoint_3d_curvilinear_rotated_ns_fp64():
+    """Reverse stages with the fused gather on a rotated curved 3D mesh (every
+    face-orientation code, scattered jump cotangents, metric terms)."""
+    mesh = I.rotate_elements(I.warped_mesh(2, [2, 3, 2], [1.0, 1.0, 1.0], 0.03, periodic=[True, True, False]), 73)
+    err = _ark_adjoint_vs_oracle(mesh, _ns(), "fp64", 1e-4, 31)
+    record("ark-adjoint-3d-curv-fp64", rel=err)
+    assert err < 1e-10, err
+
+
+def test_ark_adjoint_ns_walls_fp32():
+    """FP32 viscous adjoint step on a wall-bounded box mesh (box line-assembly of
+    P_b, FP32 stage coefficients, FP64 lambda update)."""
+    mesh = I.structured_box_mesh(4, [I.uniform_edges(0, 1, 7), I.wall_stretched_edges(3, 1.3)], [True, False])
+    err = _ark_adjoint_vs_oracle(mesh, _ns(), "fp32", 2e-5, 41, ys_from_gpu=True)
+    record("ark-adjoint-ns-walls-fp32", rel=err)
+    assert err < 1e-5, err
+
+
+def test_ark_adjoint_self_periodic_ns_fp64():
+    """One element across a periodic direction: the element is its own neighbour
+    there, so jump cotangents are scattered into its own opposite face."""
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 1), I.wall_stretched_edges(2, 1.2)], [True, False])
+    err = _ark_adjoint_vs_oracle(mesh, _ns(), "fp64", 1e-4, 51)
+    record("ark-adjoint-self-periodic-fp64", rel=err)
+    assert err < 1e-10, err
