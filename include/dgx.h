@@ -208,7 +208,9 @@ const char* dgx_kernel_name(int32_t kind);
  * pointwise physics is counted operation by operation, a fused multiply-add
  * being two flops; contractions from their loop structure) and bytes of the
  * kernel's compulsory traffic (each input read once, each output written once).
- * The element-stage figures are averages over the stages of the tableau. */
+ * With a tableau set, the element-stage and VJP-element figures are averages
+ * over the (reverse) stages of an ARK step and its adjoint, and the gather
+ * figure includes the adjoint step's lambda update. */
 dgx_status dgx_kernel_work(const dgx_handle* h, int32_t kind, double* flops, double* bytes);
 
 /* Tile-size autotuner.  Tile kernels come in 4 variants: 0..2 use one CTA of

@@ -624,6 +624,10 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
     case DGX_K_VJP_GATHER:
       flops = E * ((v ? FACE * 2 : 0) + STATE * 4 * D);
       bytes = E * ((FACE + (v ? FACE : 0) + 2 * STATE) * s);
+      if (h->stages > 0) {  // ARK adjoint: the one gather per step also forms lambda_n = lambda_{n+1} + sum_j nu_j
+        flops += E * STATE * st;
+        bytes += E * STATE * (16.0 + (st - 1) * s);
+      }
       break;
     default:
       break;
