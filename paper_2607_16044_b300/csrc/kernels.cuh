@@ -375,13 +375,20 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
         const S r = M.geo.rh[(e0 + t) * D + a];
         const S jm = js[((t * NF + 2 * a) * nf + f) * nfp + line];
         const S jp = js[((t * NF + 2 * a + 1) * nf + f) * nfp + line];
+        S sm = 0, sp = 0;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
           S d = 0;
 #pragma unroll
           for (int m = 0; m < n; ++m) d += tb.D[k][m] * x[m];
-          qo[H::node(k, line, a)] = r * (d + tb.Lp[k] * jp - tb.Lm[k] * jm);
+          const S qk = r * (d + tb.Lp[k] * jp - tb.Lm[k] * jm);
+          qo[H::node(k, line, a)] = qk;
+          sm += tb.lm[k] * qk;
+          sp += tb.lp[k] * qk;
         }
+        // this line ends on the two faces normal to a: the traces of Q_a there
+        tq[(((t * NF + 2 * a) * D + a) * nf + f) * nfp + line] = sm;
+        tq[(((t * NF + 2 * a + 1) * D + a) * nf + f) * nfp + line] = sp;
       } else {
 #pragma unroll
         for (int k = 0; k < n; ++k) {
@@ -445,14 +452,17 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
     S* qd = Q + (size_t)e0 * D * H::STATE;
     for (int i = g_tid<V>(); i < nel * D * H::STATE; i += g_size<V>()) qd[i] = qs[i];
   }
-  // traces of Q: one thread per (face direction a, component c, field, line)
+  // traces of Q: one thread per (face direction a, component c, field, line);
+  // on boxes the component c = a came out of the derivative lines already
+  constexpr int NC = CURV ? D : D - 1;  // components per face direction left to trace
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
+    for (int i = g_tid<V>(); i < nel * NC * nf * nfp; i += g_size<V>()) {
       const int line = i % nfp;
       const int f = (i / nfp) % nf;
-      const int c = (i / (nfp * nf)) % D;
-      const int t = i / (nfp * nf * D);
+      const int cc = (i / (nfp * nf)) % NC;
+      const int c = CURV ? cc : cc + (cc >= a);
+      const int t = i / (nfp * nf * NC);
       const S* v = qs + ((t * D + c) * nf + f) * N;
       S sm = 0, sp = 0;
 #pragma unroll
