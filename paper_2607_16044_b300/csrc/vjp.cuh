@@ -179,11 +179,23 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 #pragma unroll
       for (int f = 0; f < nf; ++f) s[f] += cot.c_prev * nuq[f];
     }
-    for (int j = 0; j < cot.n_nu; ++j) {
-      const S c = cot.c_nu[j];
-      const S* nu = cot.nu[j] + off;
+    if (sizeof(S) == 4) {  // FP32: fixed trip count, every nu load of the node in flight together
 #pragma unroll
-      for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+      for (int j = 0; j < MAXSTAGES - 1; ++j) {
+        if (j < cot.n_nu) {
+          const S c = cot.c_nu[j];
+          const S* nu = cot.nu[j] + off;
+#pragma unroll
+          for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+        }
+      }
+    } else {  // FP64: bound by its arithmetic, the plain loop
+      for (int j = 0; j < cot.n_nu; ++j) {
+        const S c = cot.c_nu[j];
+        const S* nu = cot.nu[j] + off;
+#pragma unroll
+        for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+      }
     }
     const S ij = CURV ? M.geo.iJ[(size_t)(e0 + tn) * N + qn] : S(1);
 #pragma unroll
@@ -625,9 +637,27 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   const bool act = t < nel;
   const size_t off = (size_t)(e0 + t) * H::STATE + q;
   S gq[nf];
+  double l64[nf];  // ARK adjoint: lambda_{n+1} and the sum of the other stages' nu, read early too
+  S nsum[nf];
   if (act) {
 #pragma unroll
     for (int f = 0; f < nf; ++f) gq[f] = g[off + f * N];
+    if (cot.lam64_out) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        l64[f] = cot.lam64_out[off + f * N];
+        nsum[f] = S(0);
+      }
+      if (sizeof(S) != 8) {
+#pragma unroll
+        for (int j = 0; j < MAXSTAGES - 1; ++j) {
+          if (j < cot.n_all) {
+#pragma unroll
+            for (int f = 0; f < nf; ++f) nsum[f] += cot.nu_all[j][off + f * N];
+          }
+        }
+      }
+    }
   }
   {
     const S* src = TUb + (size_t)e0 * H::FACE;
@@ -671,13 +701,11 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
     g[off + f * N] = s;
     if (cot.lam64_out) {  // ARK adjoint: lambda_n = lambda_{n+1} + sum_j nu_j, accumulated in FP64
       if (sizeof(S) == 8) {
-        double acc = cot.lam64_out[off + f * N] + (double)s;
+        double acc = l64[f] + (double)s;
         for (int j = 0; j < cot.n_all; ++j) acc += (double)cot.nu_all[j][off + f * N];
         cot.lam64_out[off + f * N] = acc;
       } else {  // FP32 increment, one FP64 add (as the forward's last stage)
-        S inc = s;
-        for (int j = 0; j < cot.n_all; ++j) inc += cot.nu_all[j][off + f * N];
-        cot.lam64_out[off + f * N] += (double)inc;
+        cot.lam64_out[off + f * N] = l64[f] + (double)(s + nsum[f]);
       }
     }
   }
