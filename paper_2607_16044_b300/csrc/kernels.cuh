@@ -583,13 +583,27 @@ template <int nf, typename S, typename Base, typename Kj, typename Un>
 __device__ __forceinline__ void stage_prefix(const Stage<S>& st, int e, Base base, Kj kj, Un un, S (&pre)[nf],
                                              double (&pre64)[nf]) {
   const S dte = st.dte ? st.dte[e] : S(0);
+  // FP32: a fixed trip count (stages beyond i predicated off) puts every k_j
+  // load of the node in flight together; FP64 is bound by its arithmetic
+  constexpr int JMAX = sizeof(S) == 4 ? MAXSTAGES - 1 : 0;
   if (!st.last) {
 #pragma unroll
     for (int f = 0; f < nf; ++f) pre[f] = base(f);
-    for (int j = 0; j < st.i; ++j) {
-      const S c = st.dte ? dte * st.ca[j] : st.caf[j];
+    if (JMAX) {
 #pragma unroll
-      for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
+      for (int j = 0; j < JMAX; ++j) {
+        if (j < st.i) {
+          const S c = st.dte ? dte * st.ca[j] : st.caf[j];
+#pragma unroll
+          for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
+        }
+      }
+    } else {
+      for (int j = 0; j < st.i; ++j) {
+        const S c = st.dte ? dte * st.ca[j] : st.caf[j];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
+      }
     }
   } else {
 #pragma unroll
@@ -597,13 +611,20 @@ __device__ __forceinline__ void stage_prefix(const Stage<S>& st, int e, Base bas
       pre64[f] = un(f);
       pre[f] = S(0);
     }
-    for (int j = 0; j < st.i; ++j) {
-      const S c = st.dte ? dte * st.cb[j] : st.cbf[j];
+    if (JMAX) {
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        const S kv = kj(j, f);
-        if (sizeof(S) == 8) pre64[f] += (double)c * (double)kv;
-        else pre[f] += c * kv;
+      for (int j = 0; j < JMAX; ++j) {
+        if (j < st.i) {
+          const S c = st.dte ? dte * st.cb[j] : st.cbf[j];
+#pragma unroll
+          for (int f = 0; f < nf; ++f) pre[f] += c * kj(j, f);
+        }
+      }
+    } else {
+      for (int j = 0; j < st.i; ++j) {
+        const S c = st.dte ? dte * st.cb[j] : st.cbf[j];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) pre64[f] += (double)c * (double)kj(j, f);
       }
     }
   }
