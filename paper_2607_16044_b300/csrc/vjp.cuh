@@ -378,6 +378,25 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);  // node-indexed traces
+  // When every own face point of the tile has a thread of its own, that
+  // thread's inputs of the face phase (1) are requested now, so their latency
+  // overlaps the staging and the trace pass.
+  constexpr bool ONE = T * NF * nfp <= (H::WARP ? 32 : H::THREADS);
+  S pUL[nf], pgb[nf], pub[nf];
+  int pnb = -1;
+  const bool has1 = ONE && g_tid<V>() < nel * NF * nfp;
+  if (has1) {
+    const int i = g_tid<V>();
+    const int e = e0 + i / (nfp * NF), face = (i / nfp) % NF;
+    const size_t o = ((size_t)e * NF + face) * nf * nfp + i % nfp;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      pUL[f] = TU[o + f * nfp];
+      pgb[f] = Gb[o + f * nfp];
+      pub[f] = TUb[o + f * nfp];
+    }
+    pnb = M.nb[e * NF + face];
+  }
   stage_nodes<D, P, S, V, D * nf>(qs, Q + (size_t)e0 * D * H::STATE, nel);
   stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
   g_sync<V>();
@@ -403,20 +422,13 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   }
   g_sync<V>();
   // 1. viscous face-flux adjoint at every own face point
-  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+  auto face_vjp = [&](int i, S (&UL)[nf], S (&gb)[nf], S (&ubf)[nf], int nbe) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int t = i / (nfp * NF);
     const int e = e0 + t;
     const int a = face >> 1;
-    const size_t o = ((size_t)e * NF + face) * nf * nfp + fp;
-    S UL[nf], TQ[D][nf], nv[D], gb[nf], ubf[nf], tqbv[D][nf];
-#pragma unroll
-    for (int f = 0; f < nf; ++f) {
-      UL[f] = TU[o + f * nfp];
-      gb[f] = Gb[o + f * nfp];
-      ubf[f] = TUb[o + f * nfp];
-    }
+    S TQ[D][nf], nv[D], tqbv[D][nf];
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
       for (int c = 0; c < D; ++c) nv[c] = (c == a) ? ((face & 1) ? S(1) : S(-1)) : S(0);
     }
-    if (M.nb[e * NF + face] >= 0)
+    if (nbe >= 0)
       visc_flux_normal_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
     else
       wall_visc_flux_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
@@ -441,6 +453,22 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int f = 0; f < nf; ++f) tqb[(((t * NF + face) * D + c) * nf + f) * nfp + fp] = tqbv[c][f];
+  };
+  if (ONE) {
+    if (has1) face_vjp(g_tid<V>(), pUL, pgb, pub, pnb);
+  } else {
+    for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+      const int e = e0 + i / (nfp * NF), face = (i / nfp) % NF;
+      const size_t o = ((size_t)e * NF + face) * nf * nfp + i % nfp;
+      S UL[nf], gb[nf], ubf[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        UL[f] = TU[o + f * nfp];
+        gb[f] = Gb[o + f * nfp];
+        ubf[f] = TUb[o + f * nfp];
+      }
+      face_vjp(i, UL, gb, ubf, M.nb[e * NF + face]);
+    }
   }
   g_sync<V>();
   // 2. (curvilinear) Q_bar += transposed traces of TQ_bar; then P = iJ Q_bar in place
