@@ -335,17 +335,21 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   const int nel = min(T, M.E - e0);
   stage_nodes<D, P, S, V, nf>(us, U + (size_t)e0 * H::STATE, nel);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
-  // jumps Uhat - U^- at every own face point
-  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+  // jumps Uhat - U^- at every own face point.  When one thread covers one face
+  // point, it keeps that point's trace U^- and neighbour for the flux phase.
+  constexpr bool ONE = T * NF * nfp <= (H::WARP ? 32 : H::THREADS);
+  auto load_face = [&](int i, S (&UL)[nf], int& nbe) {
+    const int e = e0 + i / (nfp * NF), face = (i / nfp) % NF;
+    const S* tl = TU + ((size_t)e * NF + face) * nf * nfp + i % nfp;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) UL[f] = tl[f * nfp];
+    nbe = M.nb[e * NF + face];
+  };
+  auto jump_at = [&](int i, const S (&UL)[nf], int nbe) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int t = i / (nfp * NF);
     const int e = e0 + t;
-    const S* tl = TU + ((size_t)e * NF + face) * nf * nfp + fp;
-    S UL[nf];
-#pragma unroll
-    for (int f = 0; f < nf; ++f) UL[f] = tl[f * nfp];
-    const int nbe = M.nb[e * NF + face];
     S* jd = js + (t * NF + face) * nf * nfp + fp;
     if (nbe >= 0) {
       const int fpn = orient_map<D, n>(M.ori[e * NF + face], fp);
@@ -357,6 +361,22 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
       wall_state<D, S>(UL, W);
 #pragma unroll
       for (int f = 0; f < nf; ++f) jd[f * nfp] = W[f] - UL[f];
+    }
+  };
+  S pUL[nf];
+  int pnb = -1;
+  const bool has1 = ONE && g_tid<V>() < nel * NF * nfp;
+  if (ONE) {
+    if (has1) {
+      load_face(g_tid<V>(), pUL, pnb);
+      jump_at(g_tid<V>(), pUL, pnb);
+    }
+  } else {
+    for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+      S UL[nf];
+      int nbe;
+      load_face(i, UL, nbe);
+      jump_at(i, UL, nbe);
     }
   }
   g_sync<V>();
@@ -477,16 +497,13 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   }
   g_sync<V>();
   // own-face viscous fluxes
-  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+  auto flux_at = [&](int i, const S (&UL)[nf], int nbe) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int t = i / (nfp * NF);
     const int e = e0 + t;
     const int a = face >> 1;
-    S UL[nf], TQ[D][nf], nv[D];
-    const S* tl = TU + ((size_t)e * NF + face) * nf * nfp + fp;
-#pragma unroll
-    for (int f = 0; f < nf; ++f) UL[f] = tl[f * nfp];
+    S TQ[D][nf], nv[D];
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -499,13 +516,23 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
       for (int c = 0; c < D; ++c) nv[c] = (c == a) ? ((face & 1) ? S(1) : S(-1)) : S(0);
     }
     S Gv[nf];
-    if (M.nb[e * NF + face] >= 0)
+    if (nbe >= 0)
       visc_flux_normal<D, S>(UL, TQ, nv, M.gas, Gv);
     else
       wall_visc_flux<D, S>(UL, TQ, nv, M.gas, Gv);
     S* gd = G + ((size_t)e * NF + face) * nf * nfp + fp;
 #pragma unroll
     for (int f = 0; f < nf; ++f) gd[f * nfp] = Gv[f];
+  };
+  if (ONE) {
+    if (has1) flux_at(g_tid<V>(), pUL, pnb);
+  } else {
+    for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+      S UL[nf];
+      int nbe;
+      load_face(i, UL, nbe);
+      flux_at(i, UL, nbe);
+    }
   }
 }
 
