@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   // overlaps the staging and the trace pass.
   constexpr bool ONE = T * NF * nfp <= (H::WARP ? 32 : H::THREADS);
   S pUL[nf], pgb[nf], pub[nf];
-  int pnb = -1;
+  int pnb = -1, pnbf = 0, pori = 0;  // neighbour, its face, orientation (reused by phase 6)
   const bool has1 = ONE && g_tid<V>() < nel * NF * nfp;
   if (has1) {
     const int i = g_tid<V>();
@@ -396,6 +396,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       pub[f] = TUb[o + f * nfp];
     }
     pnb = M.nb[e * NF + face];
+    pnbf = M.nbf[e * NF + face];
+    pori = M.ori[e * NF + face];
   }
   stage_nodes<D, P, S, V, D * nf>(qs, Q + (size_t)e0 * D * H::STATE, nel);
   stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     }
   }
   // 6. the own trace cotangent and the neighbour's share of each jump
-  for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+  auto finish_at = [&](int i, int nbe, int nbf, int ori, const S* ULw) {
     const int fp = i % nfp;
     const int face = (i / nfp) % NF;
     const int tt = i / (nfp * NF);
@@ -623,10 +625,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       jb[f] = js[((tt * NF + face) * nf + f) * nfp + fp];
       ubf[f] = tub[((tt * NF + face) * nf + f) * nfp + fp];
     }
-    const int k = ee * NF + face;
-    const int nbe = M.nb[k];
     if (nbe >= 0) {  // scatter into the neighbour's own face slot (its gather reads it there)
-      const size_t on = ((size_t)nbe * NF + M.nbf[k]) * nf * nfp + orient_map<D, n>(M.ori[k], fp);
+      const size_t on = ((size_t)nbe * NF + nbf) * nf * nfp + orient_map<D, n>(ori, fp);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         ubf[f] -= S(0.5) * jb[f];
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       S UL[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        UL[f] = TU[o + f * nfp];
+        UL[f] = ULw ? ULw[f] : TU[o + f * nfp];
         ubf[f] -= jb[f];
         JB[o + f * nfp] = S(0);
       }
@@ -644,6 +644,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     }
 #pragma unroll
     for (int f = 0; f < nf; ++f) TUb[o + f * nfp] = ubf[f];
+  };
+  if (ONE) {
+    if (has1) finish_at(g_tid<V>(), pnb, pnbf, pori, pUL);
+  } else {
+    for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
+      const int k = (e0 + i / (nfp * NF)) * NF + (i / nfp) % NF;
+      finish_at(i, M.nb[k], M.nbf[k], M.ori[k], nullptr);
+    }
   }
 }
 
