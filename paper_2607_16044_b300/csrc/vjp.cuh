@@ -113,6 +113,45 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
         for (int f = 0; f < nf; ++f) Qv[c][f] = qp[(c * nf + f) * N];
     }
   }
+  // mu = c_lam lambda + sum_j c_j nu_j at this node, every field's loads issued
+  // together and ahead of the gather phase, whose latency they overlap
+  S s[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) s[f] = S(0);
+  if (tn < nel) {
+    const size_t off = (size_t)(e0 + tn) * H::STATE + qn;
+    if (cot.lam) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] = cot.lam[off + f * N];
+    } else if (cot.lam64 && (cot.c_lam != S(0) || cot.lam_out)) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) s[f] = (S)cot.lam64[off + f * N];
+      if (cot.lam_out) {
+#pragma unroll
+        for (int f = 0; f < nf; ++f) cot.lam_out[off + f * N] = s[f];
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < nf; ++f) s[f] *= cot.c_lam;
+    if (sizeof(S) == 4) {  // FP32: fixed trip count, every nu load of the node in flight together
+#pragma unroll
+      for (int j = 0; j < MAXSTAGES - 1; ++j) {
+        if (j < cot.n_nu) {
+          const S c = cot.c_nu[j];
+          const S* nu = cot.nu[j] + off;
+#pragma unroll
+          for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+        }
+      }
+    } else {  // FP64: bound by its arithmetic, the plain loop
+      for (int j = 0; j < cot.n_nu; ++j) {
+        const S c = cot.c_nu[j];
+        const S* nu = cot.nu[j] + off;
+#pragma unroll
+        for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
+      }
+    }
+  }
   S nuq[nf];  // GATHER: the finished nu of the previous reverse stage at this node
   if (GATHER) {
     const size_t off = (size_t)(e0 + tn) * H::STATE + qn;
@@ -157,45 +196,10 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
       }
     }
   }
-  if (tn < nel) {  // mu = c_lam lambda + sum_j c_j nu_j at this node, every field's loads issued together
-    const size_t off = (size_t)(e0 + tn) * H::STATE + qn;
-    S s[nf];
-#pragma unroll
-    for (int f = 0; f < nf; ++f) s[f] = S(0);
-    if (cot.lam) {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) s[f] = cot.lam[off + f * N];
-    } else if (cot.lam64 && (cot.c_lam != S(0) || cot.lam_out)) {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) s[f] = (S)cot.lam64[off + f * N];
-      if (cot.lam_out) {
-#pragma unroll
-        for (int f = 0; f < nf; ++f) cot.lam_out[off + f * N] = s[f];
-      }
-    }
-#pragma unroll
-    for (int f = 0; f < nf; ++f) s[f] *= cot.c_lam;
+  if (tn < nel) {
     if (GATHER) {
 #pragma unroll
       for (int f = 0; f < nf; ++f) s[f] += cot.c_prev * nuq[f];
-    }
-    if (sizeof(S) == 4) {  // FP32: fixed trip count, every nu load of the node in flight together
-#pragma unroll
-      for (int j = 0; j < MAXSTAGES - 1; ++j) {
-        if (j < cot.n_nu) {
-          const S c = cot.c_nu[j];
-          const S* nu = cot.nu[j] + off;
-#pragma unroll
-          for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
-        }
-      }
-    } else {  // FP64: bound by its arithmetic, the plain loop
-      for (int j = 0; j < cot.n_nu; ++j) {
-        const S c = cot.c_nu[j];
-        const S* nu = cot.nu[j] + off;
-#pragma unroll
-        for (int f = 0; f < nf; ++f) s[f] += c * nu[f * N];
-      }
     }
     const S ij = CURV ? M.geo.iJ[(size_t)(e0 + tn) * N + qn] : S(1);
 #pragma unroll
