@@ -56,7 +56,7 @@ typedef enum {
   DGX_ECUDA = 3,        /* a CUDA runtime call failed                               */
   DGX_ENONFINITE = 4,   /* a kernel produced NaN/Inf (reported by dgx_check)        */
   DGX_ETIMEOUT = 5,     /* a bounded device wait gave up (reported by dgx_check)    */
-  DGX_EUNSUPPORTED = 6, /* valid request this build does not implement              */
+  DGX_EUNSUPPORTED = 6, /* valid request the library does not implement            */
   DGX_ESTATE = 7        /* call out of order (e.g. compute before a mesh is set)    */
 } dgx_status;
 
