@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   constexpr int TQS = NF * D * nf * nfp;      // traces of Q per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V>()));   // [T][D][nf][N]  forward Q, later dU_bar and D^T dU_bar
+  S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V>()));   // [T][D][nf][N]  dU_bar and D^T dU_bar
   S* qbs = qs + T * D * H::STATE;            // [T][D][nf][N]  Q_bar (total), later P
   S* tq = qbs + T * D * H::STATE;            // [T][NF][D][nf][nfp] traces of Q, later J_bar [T][NF][nf][nfp]
   S* tqb = tq + T * TQS;                     // [T][NF][D][nf][nfp] TQ_bar
@@ -403,10 +403,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     pnbf = M.nbf[e * NF + face];
     pori = M.ori[e * NF + face];
   }
-  stage_nodes<D, P, S, V, D * nf>(qs, Q + (size_t)e0 * D * H::STATE, nel);
   stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
-  g_sync<V>();
-  // 0. traces of Q (line pass)
+  // 0. traces of Q, each line read straight from global memory (the forward Q
+  //    is needed only here; qs is scratch for the later phases)
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
@@ -414,7 +413,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       const int f = (i / nfp) % nf;
       const int c = (i / (nfp * nf)) % D;
       const int t = i / (nfp * nf * D);
-      const S* v = qs + ((t * D + c) * nf + f) * N;
+      const S* v = Q + (size_t)(e0 + t) * D * H::STATE + (c * nf + f) * N;
       S sm = 0, sp = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
@@ -509,8 +508,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   if (!CURV) {
     // 2+3+4 (boxes): only component b of P feeds direction b, so each line of
     // P_b = Q_bar_b + (transposed traces of TQ_bar)_b is assembled where it is
-    // used; one pass then gives r_b D_b^T P_b (-> qs, the forward Q is no
-    // longer needed) and the jump cotangents J_bar = -+r_b sum_m L(-+)[m] P_b(m)
+    // used; one pass then gives r_b D_b^T P_b (-> qs) and the jump
+    // cotangents J_bar = -+r_b sum_m L(-+)[m] P_b(m)
     // on the two faces normal to b.  Along a line the index in every other
     // direction a is constant, so each such face contributes one weight pair.
 #pragma unroll
@@ -552,7 +551,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       }
     }
   } else {
-  // 3. dU_bar_b(q) = sum_c Ja[b][c] P_c   -> qs (forward Q no longer needed)
+  // 3. dU_bar_b(q) = sum_c Ja[b][c] P_c   -> qs
   if (active) {
 #pragma unroll
     for (int b = 0; b < D; ++b)
