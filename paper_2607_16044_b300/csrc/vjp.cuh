@@ -403,7 +403,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     pnbf = M.nbf[e * NF + face];
     pori = M.ori[e * NF + face];
   }
-  stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
+  // Q_bar: curvilinear meshes combine its components node by node (staged
+  // tile); on boxes each line of Q_bar_b is read once, from global memory
+  if (CURV) stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
   // 0. traces of Q, each line read straight from global memory (the forward Q
   //    is needed only here; qs is scratch for the later phases)
 #pragma unroll
@@ -517,7 +519,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
         int tt, f, line;
         line_item<nf, nfp>(i, tt, f, line);
-        const S* pb = qbs + ((tt * D + b) * nf + f) * N;
+        const S* pb = Qb + (size_t)(e0 + tt) * D * H::STATE + (b * nf + f) * N;
         S* v = qs + ((tt * D + b) * nf + f) * N;
         const S r = M.geo.rh[(e0 + tt) * D + b];
         auto tqb_at = [&](int face, int fp) { return tqb[(((tt * NF + face) * D + b) * nf + f) * nfp + fp]; };
