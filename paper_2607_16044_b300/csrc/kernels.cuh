@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
 #pragma unroll
       for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
       S* qo = qs + ((t * D + a) * nf + f) * N;
+      S* qg = Q + ((size_t)(e0 + t) * D + a) * H::STATE + f * N;  // the same row in global memory
       if (!CURV) {
         const S r = M.geo.rh[(e0 + t) * D + a];
         const S jm = js[((t * NF + 2 * a) * nf + f) * nfp + line];
@@ -403,6 +404,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
           for (int m = 0; m < n; ++m) d += tb.D[k][m] * x[m];
           const S qk = r * (d + tb.Lp[k] * jp - tb.Lm[k] * jm);
           qo[H::node(k, line, a)] = qk;
+          qg[H::node(k, line, a)] = qk;
           sm += tb.lm[k] * qk;
           sp += tb.lp[k] * qk;
         }
@@ -461,16 +463,16 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
     }
     g_sync<V>();  // every D_b U has been read
     if (act) {
+      S* qg = Q + (size_t)(e0 + t) * D * H::STATE + q;
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) qs[((t * D + c) * nf + f) * N + q] = Qv[c][f];
+        for (int f = 0; f < nf; ++f) {
+          qs[((t * D + c) * nf + f) * N + q] = Qv[c][f];
+          qg[(c * nf + f) * N] = Qv[c][f];
+        }
     }
     g_sync<V>();
-  }
-  {
-    S* qd = Q + (size_t)e0 * D * H::STATE;
-    for (int i = g_tid<V>(); i < nel * D * H::STATE; i += g_size<V>()) qd[i] = qs[i];
   }
   // traces of Q: one thread per (face direction a, component c, field, line);
   // on boxes the component c = a came out of the derivative lines already
