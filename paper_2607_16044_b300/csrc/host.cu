@@ -555,6 +555,9 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
     case DGX_K_TRACE:
       flops = E * FACE * 2 * n;
       bytes = E * (STATE + FACE) * s;
+      // ARK step: the trace kernel reads the FP64 master state and also writes
+      // the working-precision copy of it that the first stage evaluates
+      if (h->stages > 0) bytes = E * (STATE * 8.0 + FACE * s + STATE * s);
       break;
     case DGX_K_BR1:
       flops = E * (NF * nfp * nf * 2 + N * D * nf * 2 * n + N * D * nf * (c ? (8 * D + 1) : 5) +
