@@ -209,8 +209,10 @@ const char* dgx_kernel_name(int32_t kind);
  * being two flops; contractions from their loop structure) and bytes of the
  * kernel's compulsory traffic (each input read once, each output written once).
  * With a tableau set, the element-stage and VJP-element figures are averages
- * over the (reverse) stages of an ARK step and its adjoint, and the gather
- * figure includes the adjoint step's lambda update. */
+ * over the (reverse) stages of an ARK step and its adjoint, the gather
+ * figure includes the adjoint step's lambda update, and the trace figure is
+ * that of the step's first kernel (FP64 state in, traces and the
+ * working-precision state out). */
 dgx_status dgx_kernel_work(const dgx_handle* h, int32_t kind, double* flops, double* bytes);
 
 /* Tile-size autotuner.  Tile kernels come in 4 variants: 0..2 use one CTA of
