@@ -154,14 +154,8 @@ struct Stage {
 };
 
 template <typename S, int V = 1>
-__device__ __forceinline__ void load_tab(const Tab<S>* tabs, int P, S* sD, S* sDh, S* slm, S* slp, S* sLm, S* sLp,
-                                         int n) {
+__device__ __forceinline__ void load_tab(const Tab<S>* tabs, int P, S* slm, S* slp, S* sLm, S* sLp, int n) {
   const Tab<S>& t = tabs[P];
-  for (int i = g_tid<V>(); i < n * n; i += g_size<V>()) {
-    const int r = i / n, c = i % n;
-    if (sD) sD[i] = t.D[r * 6 + c];
-    if (sDh) sDh[i] = t.Dh[r * 6 + c];
-  }
   for (int i = g_tid<V>(); i < n; i += g_size<V>()) {
     if (slm) slm[i] = t.lm[i];
     if (slp) slp[i] = t.lp[i];
@@ -175,13 +169,13 @@ constexpr size_t r16(size_t b) { return (b + 15) & ~(size_t)15; }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_trace_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (h::T * h::STATE + 2 * h::n));
+  return r16(sizeof(S) * h::T * h::STATE);
 }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_br1_g() {
   using h = Sh<D, P, V>;
   return r16(sizeof(S) * (h::T * h::STATE + h::T * h::FACE + h::T * D * h::STATE + h::T * h::NF * D * h::nf * h::nfp +
-                          h::n * h::n + 4 * h::n));
+                          2 * h::n));
 }
 // Element strides (in scalars) of the element kernels' shared tiles, padded so
 // that the line passes of neighbouring elements fall in different banks: the
@@ -212,7 +206,7 @@ constexpr int elem_state_stride() {
 template <int D, int P, typename S, int V>
 constexpr size_t smem_elem_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (h::T * elem_flux_stride<D, P, V>() + h::T * h::FACE + h::n * h::n + 4 * h::n));
+  return r16(sizeof(S) * (h::T * elem_flux_stride<D, P, V>() + h::T * h::FACE));
 }
 
 // Work items of a line pass along direction a: (element t, field f, line), the
@@ -296,8 +290,6 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
   using H = Sh<D, P, V>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_trace_g<D, P, S, V>()));
-  S* lm = us + H::T * H::STATE;
-  S* lp = lm + H::n;
   const int e0 = g_index<V>() * H::T;
   const int nel = min(H::T, E - e0);
   stage_nodes<D, P, S, V, H::nf>(us, U + (size_t)e0 * H::STATE, nel,
@@ -326,15 +318,12 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   S* js = us + T * H::STATE;                   // [T][NF][nf][nfp]     jumps
   S* qs = js + T * H::FACE;                    // [T][D][nf][N]        Q
   S* tq = qs + T * D * H::STATE;               // [T][NF][D][nf][nfp]  traces of Q
-  S* sD = tq + T * NF * D * nf * nfp;
-  S* lm = sD + n * n;
-  S* lp = lm + n;
-  S* Lm = lp + n;
+  S* Lm = tq + T * NF * D * nf * nfp;         // node-indexed lift weights (curvilinear)
   S* Lp = Lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   stage_nodes<D, P, S, V, nf>(us, U + (size_t)e0 * H::STATE, nel);
-  load_tab<S, V>(M.tabs, P, nullptr, nullptr, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
+  load_tab<S, V>(M.tabs, P, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
   // jumps Uhat - U^- at every own face point.  When one thread covers one face
   // point, it keeps that point's trace U^- and neighbour for the flux phase.
   constexpr bool ONE = T * NF * nfp <= (H::WARP ? 32 : H::THREADS);
@@ -759,11 +748,6 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   constexpr int FES = elem_flux_stride<D, P, V>(), SES = elem_state_stride<D, P, V>();
   S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N] (stride FES), then the next state [T][nf][N] (stride SES)
   S* ffs = fs + T * FES;                     // [T][NF][nf][nfp]
-  S* sDh = ffs + T * H::FACE;
-  S* lm = sDh + n * n;
-  S* lp = lm + n;
-  S* Lm = lp + n;
-  S* Lp = Lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   stage_faces<D, P, S, V>(ffs, FF + (size_t)e0 * H::FACE, nel);

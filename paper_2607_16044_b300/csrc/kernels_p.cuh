@@ -46,11 +46,6 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
   auto buf = [&](int b) { return smem_raw + (size_t)b * buf_bytes; };  // the two tile buffers
   constexpr int FES = elem_flux_stride<D, P, V>(), SES = elem_state_stride<D, P, V>();
   S* fs = reinterpret_cast<S*>(smem_raw + 2 * buf_bytes);  // [T][D][nf][N] (stride FES), then [T][nf][N] (stride SES)
-  S* sDh = fs + T * FES;
-  S* lm = sDh + n * n;
-  S* lp = lm + n;
-  S* Lm = lp + n;
-  S* Lp = Lm + n;
   if (threadIdx.x == 0) {
     mbar_init(&ps.bar[0], 1);
     mbar_init(&ps.bar[1], 1);

@@ -145,7 +145,7 @@ struct Ops {
                               cudaStream_t st, bool& used) {
     using h = H<V>;
     const size_t smem =
-        2 * (size_t)h::T * in.bytes_per_elem + sizeof(S) * (h::T * elem_flux_stride<D, P, V>() + h::n * h::n + 4 * h::n);
+        2 * (size_t)h::T * in.bytes_per_elem + sizeof(S) * h::T * elem_flux_stride<D, P, V>();
     if (smem + sizeof(PipeState) > SMEM_LIMIT) {  // static pipeline state shares the per-CTA limit
       used = false;
       return cudaSuccess;

@@ -39,13 +39,13 @@ struct VjpWork {
 template <int D, int P, typename S, int V>
 constexpr size_t smem_velem_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (h::T * (D + 1) * h::STATE + h::n * h::n + 2 * h::n));
+  return r16(sizeof(S) * (h::T * (D + 1) * h::STATE + 2 * h::n));
 }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_vbr1_g() {
   using h = Sh<D, P, V>;
   return r16(sizeof(S) * (2 * h::T * D * h::STATE + 2 * h::T * h::NF * D * h::nf * h::nfp + h::T * h::FACE +
-                          h::n * h::n + 4 * h::n));
+                          2 * h::n));
 }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_vgather_g() {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 #pragma unroll
       for (int f = 0; f < nf; ++f) nuq[f] = cot.nu_prev[off + f * N];
     }
-    load_tab<S, V>(M.tabs, P, nullptr, nullptr, lms, lps, nullptr, nullptr, n);
+    load_tab<S, V>(M.tabs, P, lms, lps, nullptr, nullptr, n);
     // own trace cotangent plus half the jump cotangent the neighbour scattered here
     const S* tsrc = TUbp + (size_t)e0 * H::FACE;
     const S* jsrc = JBp + (size_t)e0 * H::FACE;
@@ -373,15 +373,12 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   S* tq = qbs + T * D * H::STATE;            // [T][NF][D][nf][nfp] traces of Q, later J_bar [T][NF][nf][nfp]
   S* tqb = tq + T * TQS;                     // [T][NF][D][nf][nfp] TQ_bar
   S* tub = tqb + T * TQS;                    // [T][NF][nf][nfp] own TU_bar
-  S* sD = tub + T * H::FACE;
-  S* lm = sD + n * n;
+  S* lm = tub + T * H::FACE;                 // node-indexed trace weights
   S* lp = lm + n;
-  S* Lm = lp + n;
-  S* Lp = Lm + n;
   S* js = tq;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);  // node-indexed traces
+  load_tab<S, V>(M.tabs, P, lm, lp, nullptr, nullptr, n);  // node-indexed traces
   // When every own face point of the tile has a thread of its own, that
   // thread's inputs of the face phase (1) are requested now, so their latency
   // overlaps the staging and the trace pass.
@@ -672,7 +669,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_gather(Mesh<S> M, 
   S* lp = lm + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
-  load_tab<S, V>(M.tabs, P, nullptr, nullptr, lm, lp, nullptr, nullptr, n);
+  load_tab<S, V>(M.tabs, P, lm, lp, nullptr, nullptr, n);
   // this thread's node: its running cotangent is read first (latency overlaps the face phase)
   const int t = g_tid<V>() / N, q = g_tid<V>() % N;
   const bool act = t < nel;
