@@ -36,10 +36,27 @@ struct VjpWork {
   void* Qb;   // gradient cotangents              [E][D][nf][N]
 };
 
+// Element strides (in scalars) of k_vjp_elem's [T][nf][N] cotangent tile and
+// [T][D][nf][N] flux-cotangent tile, padded so that the line passes and node
+// phases of neighbouring elements fall in different banks (pads minimise the
+// mean wavefronts per warp access over both phases for each CTA tile shape,
+// found by enumerating the 32 x 32 residue pairs; one element per tile needs none).
+template <int D, int P, int V>
+constexpr int vjp_mu_stride() {
+  constexpr int p2[6] = {0, 1, 0, 5, 0, 1}, p3[6] = {0, 0, 20, 5, 0, 0};
+  const int pad = V > 2 ? 0 : D == 2 ? (P == 2 ? (V == 0 ? 1 : V == 1 ? 17 : 7) : p2[P]) : p3[P];
+  return Sh<D, P, V>::STATE + pad;
+}
+template <int D, int P, int V>
+constexpr int vjp_fb_stride() {
+  constexpr int p2[6] = {0, 3, 0, 5, 17, 15}, p3[6] = {0, 16, 6, 5, 10, 16};
+  const int pad = V > 2 ? 0 : D == 2 ? (P == 2 ? (V == 1 ? 13 : 3) : p2[P]) : p3[P];
+  return D * Sh<D, P, V>::STATE + pad;
+}
 template <int D, int P, typename S, int V>
 constexpr size_t smem_velem_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (h::T * (D + 1) * h::STATE + 2 * h::n));
+  return r16(sizeof(S) * (h::T * (vjp_mu_stride<D, P, V>() + vjp_fb_stride<D, P, V>()) + 2 * h::n));
 }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_vbr1_g() {
@@ -91,10 +108,11 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* mus = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_velem_g<D, P, S, V>()));  // [T][nf][N]     cotangent / J
-  S* fb = mus + T * H::STATE;                // [T][D][nf][N]  contravariant flux cotangents
+  constexpr int MS = vjp_mu_stride<D, P, V>(), FBS = vjp_fb_stride<D, P, V>();
+  S* mus = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_velem_g<D, P, S, V>()));  // [T][nf][N] (stride MS)  cotangent / J
+  S* fb = mus + T * MS;                      // [T][D][nf][N] (stride FBS)  contravariant flux cotangents
   S* tubs = fb;                              // GATHER: [T][NF][nf][nfp] trace cotangents (before fb is written)
-  S* lms = fb + T * D * H::STATE;            // node-indexed trace weights (GATHER)
+  S* lms = fb + T * FBS;                     // node-indexed trace weights (GATHER)
   S* lps = lms + n;
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
@@ -203,7 +221,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
     }
     const S ij = CURV ? M.geo.iJ[(size_t)(e0 + tn) * N + qn] : S(1);
 #pragma unroll
-    for (int f = 0; f < nf; ++f) mus[(tn * nf + f) * N + qn] = CURV ? s[f] * ij : s[f];
+    for (int f = 0; f < nf; ++f) mus[tn * MS + f * N + qn] = CURV ? s[f] * ij : s[f];
   }
   g_sync<V>();
   // one thread per line and direction: transposed weak divergence
@@ -214,12 +232,12 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
     for (int i = g_tid<V>(); i < nel * nf * nfp; i += g_size<V>()) {
       int tt, f, line;
       line_item<nf, nfp>(i, tt, f, line);
-      const S* v = mus + (tt * nf + f) * N;
+      const S* v = mus + tt * MS + f * N;
       S x[n];
 #pragma unroll
       for (int k = 0; k < n; ++k) x[k] = v[H::node(k, line, a)];
       const S rr = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
-      S* fo = fb + ((tt * D + a) * nf + f) * N;
+      S* fo = fb + tt * FBS + (a * nf + f) * N;
       S sm = 0, sp = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
-    for (int f = 0; f < nf; ++f) Fb[a][f] = fb[((t * D + a) * nf + f) * N + q];
+    for (int f = 0; f < nf; ++f) Fb[a][f] = fb[t * FBS + (a * nf + f) * N + q];
   if (CURV) {  // physical flux cotangent F_bar_c = sum_a Ja[a][c] Ft_bar_a
     S Fc[D][nf];
 #pragma unroll
