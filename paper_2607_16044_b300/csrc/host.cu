@@ -251,7 +251,7 @@ void profile_collect(dgx_handle* h) {
 }
 
 struct Layout {
-  size_t TU, FF, G, Q, Y, K, SH, TUb, Gb, JB, Qb, NU, LAM, total;
+  size_t TU, FF, G, Q, Y, K, SH, TUb, JB, Qb, NU, LAM, total;
 };
 
 Layout layout(const dgx_handle* h, int op) {
@@ -273,8 +273,6 @@ Layout layout(const dgx_handle* h, int op) {
     L.TUb = off;
     off += align256(face);
     if (h->viscous) {
-      L.Gb = off;
-      off += align256(face);
       L.JB = off;
       off += align256(face);
       L.Qb = off;
@@ -337,7 +335,6 @@ dgx::VjpWork vjp_work_at(const dgx_handle* h, void* ws, const Layout& L) {
   w.G = h->viscous ? b + L.G : nullptr;
   w.Q = h->viscous ? b + L.Q : nullptr;
   w.TUb = b + L.TUb;
-  w.Gb = h->viscous ? b + L.Gb : nullptr;
   w.JB = h->viscous ? b + L.JB : nullptr;
   w.Qb = h->viscous ? b + L.Qb : nullptr;
   return w;
@@ -616,13 +613,14 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       break;
     }
     case DGX_K_VJP_FACE:
-      flops = F * nfp * (nf + (c ? pc.llf_area_vjp : pc.llf_unit_vjp) + (v ? 2 * nf : 0));
-      bytes = E * FACE * s * (3 + (v ? 1 : 0)) + (c ? F * D * nfp * s : 0.0);
+      flops = F * nfp * (nf + (c ? pc.llf_area_vjp : pc.llf_unit_vjp));
+      bytes = E * FACE * s * 3 + (c ? F * D * nfp * s : 0.0);
       break;
     case DGX_K_VJP_BR1:
       flops = E * (NF * nfp * (D * nf * 2 * n + pc.visc_n_vjp) + N * D * nf * 4 * D + N * D * nf * (c ? 2 * D : 1) +
-                   N * nf * D * 2 * n + NF * nfp * nf * (c ? D * (2 * n + 2) : 2 * n + 1) + NF * nfp * nf * 2);
-      bytes = E * ((5 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);
+                   N * nf * D * 2 * n + NF * nfp * nf * (c ? D * (2 * n + 2) : 2 * n + 1) + NF * nfp * nf * 4);
+      // face arrays: TU, both sides' Fhat_bar, TU_bar read and written, JB written
+      bytes = E * ((6 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);
       break;
     case DGX_K_VJP_GATHER:
       flops = E * ((v ? FACE * 2 : 0) + STATE * 4 * D);

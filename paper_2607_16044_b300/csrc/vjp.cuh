@@ -5,8 +5,9 @@
 //   k_vjp_elem    lambda -> Fhat_bar (transposed lift), U_bar (transposed
 //                 weak-divergence contraction and flux Jacobians^T), Q_bar
 //   k_vjp_face    per unique face point: LLF (and mirror-state) adjoint, written
-//                 to both sides' trace cotangents, and the viscous-flux cotangents
-//   k_vjp_br1     (NS) viscous face-flux adjoint, transposed Q traces, transposed
+//                 to both sides' trace cotangents
+//   k_vjp_br1     (NS) viscous face-flux adjoint (its cotangent formed from both
+//                 sides' Fhat_bar), transposed Q traces, transposed
 //                 derivative contraction and BR1 lift adjoint; the neighbour's
 //                 share of each jump cotangent goes to a per-face buffer
 //   k_vjp_gather  transposed traces: g += sum_faces l(+-1) TU_bar (+ neighbours'
@@ -29,7 +30,6 @@ struct VjpWork {
   void* G;    // forward viscous face flux (unused by the adjoint, written by k_br1)
   void* Q;    // forward BR1 gradient            [E][D][nf][N]
   void* TUb;  // trace cotangents                 [E][2D][nf][nfp]
-  void* Gb;   // viscous face-flux cotangents     [E][2D][nf][nfp]
   void* JB;   // BR1 jump cotangents, stored in the layout of the element that receives them:
               // [E][2D][nf][nfp] at (e, face, fp) holds the cotangent of the jump seen by the
               // neighbour across that face (zero on walls)
@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 }
 
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC, bool CURV>
+template <int D, int P, typename S, bool CURV>
 __global__ void __launch_bounds__(256, 6) k_vjp_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ FFb,
-                                                  S* __restrict__ TUb, S* __restrict__ Gb) {
+                                                  S* __restrict__ TUb) {
   using H = Sh<D, P>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,28 +357,17 @@ __global__ void __launch_bounds__(256, 6) k_vjp_face(Mesh<S> M, const S* __restr
       TUb[oL + f * nfp] = ULb[f];
       TUb[oR + f * nfp] = URb[f];
     }
-    if (VISC) {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        Gb[oL + f * nfp] = -S(0.5) * sig[f];
-        Gb[oR + f * nfp] = S(0.5) * sig[f];
-      }
-    }
   } else {
     mirror_state_vjp<D, S>(nv, URb, ULb);
 #pragma unroll
     for (int f = 0; f < nf; ++f) TUb[oL + f * nfp] = ULb[f];
-    if (VISC) {
-#pragma unroll
-      for (int f = 0; f < nf; ++f) Gb[oL + f * nfp] = -sig[f];
-    }
   }
 }
 
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool CURV, int V>
 __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, const S* __restrict__ TU,
-                                                                  const S* __restrict__ Q, const S* __restrict__ Gb,
+                                                                  const S* __restrict__ Q, const S* __restrict__ FFb,
                                                                   S* __restrict__ Qb, S* __restrict__ TUb,
                                                                   S* __restrict__ JB, S* __restrict__ Ub) {
   using H = Sh<D, P, V>;
@@ -397,6 +386,19 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   const int e0 = g_index<V>() * T;
   const int nel = min(T, M.E - e0);
   load_tab<S, V>(M.tabs, P, lm, lp, nullptr, nullptr, n);  // node-indexed traces
+  // Cotangent of the own viscous face flux G at a face point.  The face flux
+  // is Fhat = LLF - (G_own - G_nb) / 2 (wall: LLF - G_own), so with the lift
+  // cotangents of both sides G_own_bar = -(FFb_own - FFb_nb) / 2 (wall: -FFb_own).
+  auto g_bar = [&](const S (&own)[nf], int nbe, int nbf, int ori, int fp, S (&gb)[nf]) {
+    if (nbe >= 0) {
+      const S* fn = FFb + ((size_t)nbe * NF + nbf) * nf * nfp + orient_map<D, n>(ori, fp);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) gb[f] = -S(0.5) * (own[f] - fn[f * nfp]);
+    } else {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) gb[f] = -own[f];
+    }
+  };
   // When every own face point of the tile has a thread of its own, that
   // thread's inputs of the face phase (1) are requested now, so their latency
   // overlaps the staging and the trace pass.
@@ -408,15 +410,17 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     const int i = g_tid<V>();
     const int e = e0 + i / (nfp * NF), face = (i / nfp) % NF;
     const size_t o = ((size_t)e * NF + face) * nf * nfp + i % nfp;
+    S own[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       pUL[f] = TU[o + f * nfp];
-      pgb[f] = Gb[o + f * nfp];
+      own[f] = FFb[o + f * nfp];
       pub[f] = TUb[o + f * nfp];
     }
     pnb = M.nb[e * NF + face];
     pnbf = M.nbf[e * NF + face];
     pori = M.ori[e * NF + face];
+    g_bar(own, pnb, pnbf, pori, i % nfp, pgb);
   }
   // Q_bar: curvilinear meshes combine its components node by node (staged
   // tile); on boxes each line of Q_bar_b is read once, from global memory
@@ -482,14 +486,16 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
     for (int i = g_tid<V>(); i < nel * NF * nfp; i += g_size<V>()) {
       const int e = e0 + i / (nfp * NF), face = (i / nfp) % NF;
       const size_t o = ((size_t)e * NF + face) * nf * nfp + i % nfp;
-      S UL[nf], gb[nf], ubf[nf];
+      S UL[nf], own[nf], gb[nf], ubf[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         UL[f] = TU[o + f * nfp];
-        gb[f] = Gb[o + f * nfp];
+        own[f] = FFb[o + f * nfp];
         ubf[f] = TUb[o + f * nfp];
       }
-      face_vjp(i, UL, gb, ubf, M.nb[e * NF + face]);
+      const int nbe = M.nb[e * NF + face];
+      g_bar(own, nbe, M.nbf[e * NF + face], M.ori[e * NF + face], i % nfp, gb);
+      face_vjp(i, UL, gb, ubf, nbe);
     }
   }
   g_sync<V>();
@@ -835,21 +841,15 @@ struct VjpOps {
     return curv ? elem_c<false, true>(M, V, U, w, c, Ub, st) : elem_c<false, false>(M, V, U, w, c, Ub, st);
   }
 
-  static cudaError_t face(const Mesh<S>& M, bool visc, bool curv, const VjpWork& w, cudaStream_t st) {
+  static cudaError_t face(const Mesh<S>& M, bool /*visc*/, bool curv, const VjpWork& w, cudaStream_t st) {
     const int total = M.nFaces * Sh<D, P>::nfp;
     if (total == 0) return cudaSuccess;
     const int nb = (total + 255) / 256;
     const S* TU = (const S*)w.TU;
     const S* FFb = (const S*)w.FFb;
     S* TUb = (S*)w.TUb;
-    S* Gb = (S*)w.Gb;
-    if (visc) {
-      if (curv) k_vjp_face<D, P, S, true, true><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
-      else k_vjp_face<D, P, S, true, false><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
-    } else {
-      if (curv) k_vjp_face<D, P, S, false, true><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
-      else k_vjp_face<D, P, S, false, false><<<nb, 256, 0, st>>>(M, TU, FFb, TUb, Gb);
-    }
+    if (curv) k_vjp_face<D, P, S, true><<<nb, 256, 0, st>>>(M, TU, FFb, TUb);
+    else k_vjp_face<D, P, S, false><<<nb, 256, 0, st>>>(M, TU, FFb, TUb);
     return cudaGetLastError();
   }
 
@@ -858,7 +858,7 @@ struct VjpOps {
     static bool done = false;
     auto k = k_vjp_br1<D, P, S, CURV, V>;
     allow_smem_once(k, smem_br1<V>(), done);
-    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.Gb,
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.FFb,
                                                              (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub);
     return cudaGetLastError();
   }
