@@ -221,8 +221,10 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
     prof = s.profile_read()
     s.profile(False)
     s.check()
-    # the same step replayed as one CUDA graph (launch overhead removed)
-    graph = s.capture(step)
+    # the same step through the one-call entry point (the kernels that form
+    # U_{n+1} overlap the adjoint on the handle's second stream), replayed as
+    # one CUDA graph (launch overhead removed)
+    graph = s.capture(lambda: s.ark_step_adjoint(U, lam, dt, stages))
     gtimes = []
     dist_barrier()
     torch.cuda.synchronize()
@@ -283,20 +285,19 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
     # over independent requests runs it: device U and lambda are double-buffered,
     # one copy stream uploads step k+1's inputs while step k computes, another
     # downloads step k's results, and the compute stream runs the L2 flush and
-    # the two graphs of each step in order.  Timed over K steps from the first
+    # the one-call step's graph of each step in order.  Timed over K steps from the first
     # upload to the last download; per step = total / K.
     Ud = [U, torch.empty_like(U)]
     Ld = [lam, torch.empty_like(lam)]
     Ud[1].copy_(U)
     Ld[1].copy_(lam)
-    g_f = [g_fwd, s.capture(lambda: s.ark_step_stages(Ud[1], dt, stages))]
-    g_a = [g_adj, s.capture(lambda: s.ark_adjoint_step(stages, Ld[1], dt))]
+    g_s = [s.capture(lambda sl=sl: s.ark_step_adjoint(Ud[sl], Ld[sl], dt, stages)) for sl in range(2)]
     outU = [out_U, torch.empty_like(host_U).pin_memory()]
     outL = [out_lam, torch.empty_like(host_lam).pin_memory()]
     h2d, d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def pipelined(K):
-        up_U, up_L, fwd, adj, dn_U, dn_L = ([torch.cuda.Event() for _ in range(K)] for _ in range(6))
+        up_U, up_L, fwd, dn_U, dn_L = ([torch.cuda.Event() for _ in range(K)] for _ in range(5))
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -315,16 +316,13 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
                 up_L[k].record(h2d)
             flush.fill_(1)
             stream.wait_event(up_U[k])
-            g_f[sl].replay()
-            fwd[k].record(stream)
             stream.wait_event(up_L[k])
-            g_a[sl].replay()
-            adj[k].record(stream)
+            g_s[sl].replay()
+            fwd[k].record(stream)
             with torch.cuda.stream(d2h):
                 d2h.wait_event(fwd[k])
                 outU[sl].copy_(Ud[sl], non_blocking=True)
                 dn_U[k].record(d2h)
-                d2h.wait_event(adj[k])
                 outL[sl].copy_(Ld[sl], non_blocking=True)
                 dn_L[k].record(d2h)
         stream.wait_event(dn_U[K - 1])
@@ -705,8 +703,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
             "config": {"workload": WORKLOAD, "elements": r32["mesh"].n_elem, "dofs": r32["dofs"],
-                       "timing": "CUDA-graph replay of the step; per-kernel roofline from the eager profiled "
-                                 "pass of the same steps",
+                       "timing": "CUDA-graph replay of the one-call step (dgx_ark_step_adjoint: the kernels "
+                                 "that form U_{n+1} overlap the adjoint on a second stream); per-kernel roofline "
+                                 "from an eager profiled pass of the same steps as separate calls on one stream",
                        "eager_ms_per_step": round(r32["eager_ms"], 4),
                        "tile_variants": {k: v for k, v in r32["variants"].items()
                                          if k not in ("face", "vjp_face")},
@@ -722,7 +721,7 @@ def main():
                     "frac_of_copy_bound": round(dist_max(r32["copy_ms"]) / dist_max(r32["e2e_ms"]), 3),
                     "schedule": "consecutive steps pipelined: double-buffered device U and lambda, step k+1's "
                                 "pinned-host uploads on one copy stream and step k's downloads on another "
-                                "overlap step k's forward + adjoint graphs (L2 flushed before each step)",
+                                "overlap step k's one-call forward + adjoint graph (L2 flushed before each step)",
                     "serial_value": round(e2e_serial, 1),
                     "serial_schedule": "one step at a time: U_n upload, forward step (lambda upload on a "
                                        "second stream), adjoint (U_{n+1} download on the second stream), "

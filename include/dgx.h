@@ -63,7 +63,13 @@ typedef enum {
 typedef enum { DGX_FP64 = 0, DGX_FP32 = 1 } dgx_precision;
 
 /* Workspace kinds for dgx_workspace_bytes. */
-typedef enum { DGX_OP_RHS = 0, DGX_OP_VJP = 1, DGX_OP_ARK = 2, DGX_OP_ARK_ADJOINT = 3 } dgx_op;
+typedef enum {
+  DGX_OP_RHS = 0,
+  DGX_OP_VJP = 1,
+  DGX_OP_ARK = 2,
+  DGX_OP_ARK_ADJOINT = 3,
+  DGX_OP_ARK_STEP_ADJOINT = 4 /* dgx_ark_step_adjoint */
+} dgx_op;
 
 /* Problem statement (Sec. 2): dimension, polynomial degree k = p, element
  * count, viscous (Navier-Stokes, 1) or inviscid (Euler, 0), arithmetic
@@ -155,6 +161,19 @@ dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stag
  * double [E][nf][N]) holds lambda_{n+1} on entry and lambda_n on exit; the
  * accumulation into lam64 is in FP64. */
 dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                                void* stream);
+
+/* One ARK step and its discrete adjoint in one call: the same results, bit for
+ * bit, as dgx_ark_step_stages(h, U64, dt, stages, ...) followed by
+ * dgx_ark_adjoint_step(h, stages, lam64, dt, ...) (U64: U_n in, U_{n+1} out;
+ * lam64: lambda_{n+1} in, lambda_n out; stages as for those calls).  The
+ * reverse stages need only the stage checkpoints, not U_{n+1}, so the last
+ * stage's face and element kernels, which form U_{n+1}, run on a second
+ * stream owned by the handle while the adjoint runs on `stream`; that stream
+ * waits for them before the call's work ends (fork and join by events, so the
+ * call can be captured into a CUDA graph).  Workspace:
+ * dgx_workspace_bytes(h, DGX_OP_ARK_STEP_ADJOINT), 256-byte aligned. */
+dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, double dt, void* stages, void* workspace,
                                 void* stream);
 
 /* Residual for callers that cannot allocate device memory (no counterpart in

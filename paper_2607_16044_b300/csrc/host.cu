@@ -45,6 +45,9 @@ struct dgx_handle {
   int nsm = 148;          // SMs of the device (persistent grids)
   bool pipeline = true;   // persistent TMA-fed kernels where the layout allows
   int contraction = DGX_CONTRACT_CUDA_CORE;  // engine of the forward element kernel
+  // second stream and fork / join events of dgx_ark_step_adjoint
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
   int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
@@ -371,9 +374,12 @@ cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, cons
   return err;
 }
 
+// One ARK step.  With fork set, the last stage's face and element kernels (the
+// ones that form U_{n+1}) go to the handle's second stream after an event on
+// st; the caller joins it through h->ev_join.
 template <typename S>
 dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st,
-                    const S* dte = nullptr) {
+                    const S* dte = nullptr, bool fork = false) {
   const Layout L = layout(h, DGX_OP_ARK);
   const dgx::Work w = work_at(h, workspace, L);
   char* base = (char*)workspace;
@@ -422,6 +428,12 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     sa.TU = (S*)((ck && !sa.last) ? slot_tu(i + 1) : w.TU);
     const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
     if (h->viscous) err = launch(h, DGX_K_BR1, st, [&] { return t->br1(M, h->var[DGX_K_BR1], h->curv, Uin, wi, st); });
+    cudaStream_t st_main = st;
+    if (fork && sa.last && err == cudaSuccess) {  // U_{n+1} on the second stream
+      err = cudaEventRecord(h->ev_fork, st);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      st = h->side;
+    }
     if (err == cudaSuccess) err = launch(h, DGX_K_FACE, st, [&] { return t->face(M, h->viscous, h->curv, wi, st); });
     if (err == cudaSuccess)
       err = launch(h, DGX_K_ELEM_STAGE, st, [&] {
@@ -435,6 +447,10 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
         }
         return t->elem_stage(M, h->var[DGX_K_ELEM_STAGE], h->viscous, h->curv, Uin, wi, &sa, st);
       });
+    if (st != st_main) {
+      if (err == cudaSuccess) err = cudaEventRecord(h->ev_join, st);
+      st = st_main;
+    }
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   return DGX_OK;
@@ -783,6 +799,10 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   }
   if (st == DGX_OK && cudaMalloc((void**)&h->d_flags, sizeof(unsigned)) != cudaSuccess) st = DGX_ENOMEM;
   if (st == DGX_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) st = DGX_ECUDA;
+  if (st == DGX_OK && (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    st = DGX_ECUDA;
   if (st != DGX_OK) {
     dgx_destroy(h);
     return st;
@@ -797,6 +817,9 @@ dgx_status dgx_destroy(dgx_handle* h) {
   free_mesh(h);
   if (h->d_tabs) cudaFree(h->d_tabs);
   if (h->d_flags) cudaFree(h->d_flags);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   delete h;
   return DGX_OK;
 }
@@ -957,9 +980,11 @@ size_t dgx_stage_bytes(const dgx_handle* h) {
 size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (!h) return 0;
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
-  if (op == DGX_OP_ARK_ADJOINT && h->stages == 0) return 0;
-  if (op < DGX_OP_RHS || op > DGX_OP_ARK_ADJOINT) return 0;
-  if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT) && !h->tab->vjp) return 0;
+  if ((op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && h->stages == 0) return 0;
+  if (op < DGX_OP_RHS || op > DGX_OP_ARK_STEP_ADJOINT) return 0;
+  if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && !h->tab->vjp) return 0;
+  if (op == DGX_OP_ARK_STEP_ADJOINT)  // the forward's and the adjoint's workspaces side by side
+    return layout(h, DGX_OP_ARK).total + layout(h, DGX_OP_ARK_ADJOINT).total;
   return layout(h, op).total;
 }
 
@@ -1036,6 +1061,27 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->fp64) return ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
   return ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, double dt, void* stages, void* workspace,
+                                void* stream) {
+  if (!h || !U64 || !lam64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
+  if (((uintptr_t)stages & 255) != 0 || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws_adj = (char*)workspace + layout(h, DGX_OP_ARK).total;  // a multiple of 256 bytes
+  dgx_status s = h->fp64 ? ark_impl<double>(h, U64, dt, stages, workspace, st, nullptr, /*fork=*/true)
+                         : ark_impl<float>(h, U64, dt, stages, workspace, st, nullptr, /*fork=*/true);
+  if (s != DGX_OK) {  // whatever reached the second stream still joins the caller's
+    cudaEventRecord(h->ev_join, h->side);
+    cudaStreamWaitEvent(st, h->ev_join, 0);
+    return s;
+  }
+  s = h->fp64 ? ark_adjoint_impl<double>(h, stages, lam64, dt, ws_adj, st)
+              : ark_adjoint_impl<float>(h, stages, lam64, dt, ws_adj, st);
+  if (cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess && s == DGX_OK) s = DGX_ECUDA;
+  return s;
 }
 
 dgx_status dgx_check(dgx_handle* h) {

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdgx.so")
 
 FP64, FP32 = 0, 1
-OP_RHS, OP_VJP, OP_ARK, OP_ARK_ADJOINT = 0, 1, 2, 3
+OP_RHS, OP_VJP, OP_ARK, OP_ARK_ADJOINT, OP_ARK_STEP_ADJOINT = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite residual",
           5: "device wait timed out", 6: "unsupported", 7: "call out of order"}
 
@@ -45,7 +45,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
-           "dgx_set_contraction", "dgx_get_contraction"]
+           "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint"]
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_ark_step.argtypes = [vp, vp, dbl, vp, vp]
     lib.dgx_ark_step_stages.argtypes = [vp, vp, dbl, vp, vp, vp]
     lib.dgx_ark_adjoint_step.argtypes = [vp, vp, vp, dbl, vp, vp]
+    lib.dgx_ark_step_adjoint.argtypes = [vp, vp, vp, dbl, vp, vp, vp]
     lib.dgx_rhs_noalloc.argtypes = [vp, vp, vp, vp]
     lib.dgx_stage_bytes.argtypes = [vp]
     lib.dgx_kernel_work.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -205,6 +206,7 @@ class Solver:
         self.stages = len(b)
         self._ws.pop(OP_ARK, None)
         self._ws.pop(OP_ARK_ADJOINT, None)
+        self._ws.pop(OP_ARK_STEP_ADJOINT, None)
 
     # ------------------------------------------------------------------ compute
     def rhs(self, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
@@ -271,6 +273,18 @@ class Solver:
                                              self._state(lam64, "lam64", torch.float64), float(dt),
                                              self._aligned(ws), _stream_ptr(stream)), "dgx_ark_adjoint_step")
         return lam64
+
+    def ark_step_adjoint(self, U64: torch.Tensor, lam64: torch.Tensor, dt: float, stages: torch.Tensor,
+                         stream=None):
+        """One ARK step (U64: U_n -> U_{n+1}, stage checkpoints in stages) and
+        its discrete adjoint (lam64: lambda_{n+1} -> lambda_n) in one call; the
+        kernels that form U_{n+1} overlap the adjoint on a second stream."""
+        ws = self.workspace(OP_ARK_STEP_ADJOINT)
+        _check(self.lib.dgx_ark_step_adjoint(self.h, self._state(U64, "U64", torch.float64),
+                                             self._state(lam64, "lam64", torch.float64), float(dt),
+                                             self._stages_ptr(stages), self._aligned(ws), _stream_ptr(stream)),
+               "dgx_ark_step_adjoint")
+        return U64, lam64
 
     def capture(self, fn, warmup: int = 2):
         """Capture fn() -- any sequence of this library's calls on the current
