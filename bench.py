@@ -284,20 +284,22 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
     # The same end-to-end job with consecutive steps pipelined, as a serving loop
     # over independent requests runs it: device U and lambda are double-buffered,
     # one copy stream uploads step k+1's inputs while step k computes, another
-    # downloads step k's results, and the compute stream runs the L2 flush and
-    # the one-call step's graph of each step in order.  Timed over K steps from the first
+    # downloads step k's results (U_{n+1} as soon as the forward graph ends),
+    # and the compute stream runs the L2 flush and each step's forward and
+    # adjoint graphs in order.  Timed over K steps from the first
     # upload to the last download; per step = total / K.
     Ud = [U, torch.empty_like(U)]
     Ld = [lam, torch.empty_like(lam)]
     Ud[1].copy_(U)
     Ld[1].copy_(lam)
-    g_s = [s.capture(lambda sl=sl: s.ark_step_adjoint(Ud[sl], Ld[sl], dt, stages)) for sl in range(2)]
+    g_f = [g_fwd, s.capture(lambda: s.ark_step_stages(Ud[1], dt, stages))]
+    g_a = [g_adj, s.capture(lambda: s.ark_adjoint_step(stages, Ld[1], dt))]
     outU = [out_U, torch.empty_like(host_U).pin_memory()]
     outL = [out_lam, torch.empty_like(host_lam).pin_memory()]
     h2d, d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
     def pipelined(K):
-        up_U, up_L, fwd, dn_U, dn_L = ([torch.cuda.Event() for _ in range(K)] for _ in range(5))
+        up_U, up_L, fwd, adj, dn_U, dn_L = ([torch.cuda.Event() for _ in range(K)] for _ in range(6))
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -316,13 +318,16 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
                 up_L[k].record(h2d)
             flush.fill_(1)
             stream.wait_event(up_U[k])
-            stream.wait_event(up_L[k])
-            g_s[sl].replay()
+            g_f[sl].replay()
             fwd[k].record(stream)
+            stream.wait_event(up_L[k])
+            g_a[sl].replay()
+            adj[k].record(stream)
             with torch.cuda.stream(d2h):
-                d2h.wait_event(fwd[k])
+                d2h.wait_event(fwd[k])                 # U_{n+1} leaves while the adjoint runs
                 outU[sl].copy_(Ud[sl], non_blocking=True)
                 dn_U[k].record(d2h)
+                d2h.wait_event(adj[k])
                 outL[sl].copy_(Ld[sl], non_blocking=True)
                 dn_L[k].record(d2h)
         stream.wait_event(dn_U[K - 1])
@@ -369,8 +374,8 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant FP32 kernel from one ncu capture of the bench workload (summary and
 # command in profiles/), valid only while the kernel sources hash to `sources`.
-NCU_TRAFFIC = {"kernel": "vjp_br1", "bytes": 105836288,
-               "sources": "5cd9e42f93792c3d38d94dd64efd9892b06b2f9f7471a092a3feeec6aa7e14ce"}
+NCU_TRAFFIC = {"kernel": "vjp_br1", "bytes": 105437440,
+               "sources": "87a0c5e1f51927724a4c65678308401b4466a878bcc990dd016d0cf92abcca55"}
 
 
 def sources_hash():
@@ -573,8 +578,7 @@ def channel3d_perf(reps=3):
     stages = s.stage_buffer()
 
     def step():
-        s.ark_step_stages(U, 1e-9, stages)
-        s.ark_adjoint_step(stages, lam, 1e-9)
+        s.ark_step_adjoint(U, lam, 1e-9, stages)
     s.autotune(U, reps=1)
     step()
     ms = _time_events(step, reps)
@@ -721,7 +725,8 @@ def main():
                     "frac_of_copy_bound": round(dist_max(r32["copy_ms"]) / dist_max(r32["e2e_ms"]), 3),
                     "schedule": "consecutive steps pipelined: double-buffered device U and lambda, step k+1's "
                                 "pinned-host uploads on one copy stream and step k's downloads on another "
-                                "overlap step k's one-call forward + adjoint graph (L2 flushed before each step)",
+                                "overlap step k's forward and adjoint graphs, U_{n+1} downloaded during the "
+                                "adjoint (L2 flushed before each step)",
                     "serial_value": round(e2e_serial, 1),
                     "serial_schedule": "one step at a time: U_n upload, forward step (lambda upload on a "
                                        "second stream), adjoint (U_{n+1} download on the second stream), "

@@ -393,8 +393,9 @@ def adjoint_trajectory(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int,
     """Gradient of <lam_final, U_N> w.r.t. U_0 through N explicit ARK steps.
 
     Forward: store U_n (FP64) before every step (one checkpoint per step).
-    Reverse: for n = N-1 .. 0 recompute the step's stage states from U_n with
-    dgx_ark_step_stages and apply dgx_ark_adjoint_step.  Returns (U_N, lam_0).
+    Reverse: for n = N-1 .. 0 recompute the step's stage states from U_n and
+    apply the step's adjoint, both by dgx_ark_step_adjoint (the recomputed
+    U_{n+1} is not needed and overlaps the adjoint).  Returns (U_N, lam_0).
     """
     U = U0.clone()
     ckpt = checkpoints if checkpoints is not None else []
@@ -407,8 +408,7 @@ def adjoint_trajectory(solver: Solver, U0: torch.Tensor, dt: float, nsteps: int,
     work = torch.empty_like(U)
     for n in reversed(range(nsteps)):
         work.copy_(ckpt[n])
-        solver.ark_step_stages(work, dt, stages)
-        solver.ark_adjoint_step(stages, lam, dt)
+        solver.ark_step_adjoint(work, lam, dt, stages)
     return U, lam
 
 
