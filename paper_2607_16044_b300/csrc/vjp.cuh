@@ -425,8 +425,16 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   // Q_bar: curvilinear meshes combine its components node by node (staged
   // tile); on boxes each line of Q_bar_b is read once, from global memory
   if (CURV) stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
-  // 0. traces of Q, each line read straight from global memory (the forward Q
-  //    is needed only here; qs is scratch for the later phases)
+  // 0. traces of Q (the forward Q is needed only here).  2D: each line read
+  //    straight from global memory (every value is read twice); 3D: every
+  //    value is read three times, so Q is staged once into qs (scratch for
+  //    the later phases) and the lines are read from there.
+  const S* qsrc = Q + (size_t)e0 * D * H::STATE;
+  if (D == 3) {
+    stage_nodes<D, P, S, V, D * nf>(qs, qsrc, nel);
+    g_sync<V>();
+    qsrc = qs;
+  }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
@@ -434,7 +442,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
       const int f = (i / nfp) % nf;
       const int c = (i / (nfp * nf)) % D;
       const int t = i / (nfp * nf * D);
-      const S* v = Q + (size_t)(e0 + t) * D * H::STATE + (c * nf + f) * N;
+      const S* v = qsrc + (size_t)t * D * H::STATE + (c * nf + f) * N;
       S sm = 0, sp = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
