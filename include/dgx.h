@@ -287,7 +287,10 @@ dgx_status dgx_get_contraction(const dgx_handle* h, int32_t* mode);
  * instance i occupies doubles [offsets[i], offsets[i] + E_i nf_i N_i)
  * (dgx_batch_layout, offsets has count + 1 entries).  Each instance has its own
  * time step (dgx_batch_set_dt, host array of count doubles, uploaded once).
- * The instance handles are only read by dgx_batch_create. */
+ * The groups of a step run concurrently, each on a stream of the batch,
+ * forked from and joined back to the caller's stream by events; the workspace
+ * holds one slice per group.  The instance handles are only read by
+ * dgx_batch_create. */
 typedef struct dgx_batch dgx_batch;
 dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** out);
 dgx_status dgx_batch_destroy(dgx_batch* b);

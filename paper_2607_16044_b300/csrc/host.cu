@@ -1219,6 +1219,9 @@ struct dgx_batch {
     std::vector<int> members;        // instance indices
     std::vector<int64_t> elem_off;   // element offset of each member inside the group
     void* d_dte = nullptr;           // per-element time step in the group's precision
+    size_t ws_off = 0;               // the group's slice of the batch workspace
+    cudaStream_t st = nullptr;       // groups run concurrently, each on its own stream
+    cudaEvent_t done = nullptr;      // the group's work is complete (joins the caller's stream)
   };
   int count = 0;
   std::vector<int64_t> offset;       // per instance (doubles), offset[count] = total
@@ -1227,6 +1230,7 @@ struct dgx_batch {
   bool dt_set = false;
   size_t ws_bytes = 0;
   cudaStream_t cap = nullptr;
+  cudaEvent_t start = nullptr;       // fork point on the caller's stream
   cudaGraphExec_t exec = nullptr;
   double* g_U = nullptr;
   void* g_ws = nullptr;
@@ -1242,21 +1246,35 @@ bool same_group(const dgx_handle* a, const dgx_handle* b) {
 void batch_free(dgx_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->start) cudaEventDestroy(b->start);
   for (auto& g : b->groups) {
     if (g.d_dte) cudaFree(g.d_dte);
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.st) cudaStreamDestroy(g.st);
     if (g.h) dgx_destroy(g.h);
   }
   delete b;
 }
 
+// Every group's step on its own stream (disjoint state ranges and workspace
+// slices), forked from and joined back to st by events, so small groups'
+// kernels overlap instead of running one group after another.
 dgx_status batch_run(dgx_batch* b, double* U64, void* ws, cudaStream_t st) {
+  if (cudaEventRecord(b->start, st) != cudaSuccess) return DGX_ECUDA;
+  dgx_status s = DGX_OK;
   for (auto& g : b->groups) {
     dgx_handle* h = g.h;
-    const dgx_status s = h->fp64 ? ark_impl<double>(h, U64 + g.off, 0.0, nullptr, ws, st, (const double*)g.d_dte)
-                                 : ark_impl<float>(h, U64 + g.off, 0.0, nullptr, ws, st, (const float*)g.d_dte);
-    if (s != DGX_OK) return s;
+    void* wg = (char*)ws + g.ws_off;
+    if (cudaStreamWaitEvent(g.st, b->start, 0) != cudaSuccess) s = DGX_ECUDA;
+    if (s == DGX_OK)
+      s = h->fp64 ? ark_impl<double>(h, U64 + g.off, 0.0, nullptr, wg, g.st, (const double*)g.d_dte)
+                  : ark_impl<float>(h, U64 + g.off, 0.0, nullptr, wg, g.st, (const float*)g.d_dte);
+    // every stream that was forked joins back, also after an error
+    if (cudaEventRecord(g.done, g.st) != cudaSuccess && s == DGX_OK) s = DGX_ECUDA;
+    if (cudaStreamWaitEvent(st, g.done, 0) != cudaSuccess && s == DGX_OK) s = DGX_ECUDA;
+    if (s != DGX_OK) break;
   }
-  return DGX_OK;
+  return s;
 }
 }  // namespace
 
@@ -1340,13 +1358,20 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
       st = DGX_ECUDA;
       break;
     }
+    if (cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess) {
+      st = DGX_ECUDA;
+      break;
+    }
     g.off = off;
     for (size_t m = 0; m < g.members.size(); ++m) b->offset[g.members[m]] = off + g.elem_off[m] * nf * N;
     off += E * nf * N;
-    b->ws_bytes = std::max(b->ws_bytes, dgx_workspace_bytes(g.h, DGX_OP_ARK));
+    g.ws_off = b->ws_bytes;  // group workspaces side by side (each a multiple of 256 bytes)
+    b->ws_bytes += dgx_workspace_bytes(g.h, DGX_OP_ARK);
   }
   b->offset[count] = off;
   if (st == DGX_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = DGX_ECUDA;
+  if (st == DGX_OK && cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess) st = DGX_ECUDA;
   if (st != DGX_OK) {
     batch_free(b);
     return st;
