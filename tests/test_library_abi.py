@@ -38,3 +38,14 @@ def test_library_loads_without_gpu():
     assert lib.dgx_workspace_bytes(None, 0) == 0
     for name in declared():
         assert hasattr(lib, name)
+
+
+@pytest.mark.skipif(not os.path.exists(LIB), reason="library not built")
+def test_host_validation_without_gpu():
+    """Host-side argument checks answer before any device work."""
+    from paper_2607_16044_b300 import dgx
+    lib = dgx.load_library()
+    assert lib.dgx_ark_step_adjoint(None, None, None, 1e-3, None, None, None) == 1
+    assert lib.dgx_ark_step_stages(None, None, 1e-3, None, None, None) == 1
+    assert lib.dgx_ark_adjoint_step(None, None, None, 1e-3, None, None) == 1
+    assert lib.dgx_workspace_bytes(None, dgx.OP_ARK_STEP_ADJOINT) == 0
