@@ -375,20 +375,29 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
 # dominant FP32 kernel from one ncu capture of the bench workload (summary and
 # command in profiles/), valid only while the kernel sources hash to `sources`.
 NCU_TRAFFIC = {"kernel": "vjp_br1", "bytes": 105344512,
-               "sources": "8aeab4446364924a0206a37c7d327d48eaab79d2f41b99bb4a608492f7842f01"}
+               "sources": "3bed97b8d2fd92740430ac59a44bbfaf622df4a5e80e8b156cc2e8442075df2a"}
 
 
-def sources_hash():
-    """sha256 over the device-code headers (the kernels' source; host.cu only
-    composes launches)."""
+def sources_hash(root_header="vjp.cuh"):
+    """sha256 over the device-code headers the captured kernel is built from:
+    the header that defines it and everything it includes, transitively
+    (host.cu only composes launches)."""
     import hashlib
-    h = hashlib.sha256()
+    import re
     d = os.path.join(ROOT, "paper_2607_16044_b300", "csrc")
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cuh", ".h")):
-            h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+    seen, todo = set(), [root_header]
+    while todo:
+        name = todo.pop()
+        if name in seen or not os.path.exists(os.path.join(d, name)):
+            continue
+        seen.add(name)
+        with open(os.path.join(d, name)) as f:
+            todo += re.findall(r'^#include "([^"]+)"', f.read(), flags=re.M)
+    h = hashlib.sha256()
+    for name in sorted(seen):
+        h.update(name.encode())
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 
@@ -514,8 +523,8 @@ def ensemble_perf(prec="fp32", reps=10):
 
 def tgv_perf(reps=10, profile_range=False):
     """32^3 Taylor-Green vortex, p = 3: forward residual time in FP64 and in FP32
-    with each contraction engine of the element kernel (CUDA cores, TF32 and
-    3xTF32 tensor cores); per FP32 leg the element kernel's own time (event
+    with each contraction engine of the element kernel (CUDA cores, TF32, BF16
+    and 3xTF32 tensor cores); per FP32 leg the element kernel's own time (event
     profiler) and the max-norm deviation of the residual from the FP64 residual
     relative to the FP64 residual's max norm over all fields."""
     import torch
@@ -525,7 +534,7 @@ def tgv_perf(reps=10, profile_range=False):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {"workload": "3D TGV 32^3, p=3, Re=1600, Ma=0.1 (forward residual)", "dofs": int(U0.size)}
     ref = None
-    for leg in ("fp64", "fp32", "fp32-tf32", "fp32-3xtf32"):
+    for leg in ("fp64", "fp32", "fp32-tf32", "fp32-bf16", "fp32-3xtf32"):
         prec = leg.split("-")[0]
         s = Solver(mesh, phys, prec)
         if "-" in leg:

@@ -263,18 +263,27 @@ dgx_status dgx_set_variants(dgx_handle* h, const int32_t* variants);
  *   DGX_CONTRACT_TF32       tcgen05 tensor cores, operands rounded to TF32
  *                           (10-bit mantissa), FP32 accumulation: relative
  *                           error of the residual about 1e-3;
+ *   DGX_CONTRACT_BF16       tcgen05 kind::f16, operands rounded to BF16
+ *                           (7-bit mantissa), FP32 accumulation: relative
+ *                           error of the residual about 1e-2;
  *   DGX_CONTRACT_3XTF32     tcgen05, every operand split into two TF32 parts
  *                           and three products accumulated: close to FP32.
  * Each (direction, element, field, line) is one row of a GEMM against the
- * fixed [Dh | -L(-1) | -L(+1)] operand (K = n + 2 <= 8, M = 128 rows per
- * MMA, accumulator in tensor memory).  Applies to dgx_rhs and the ARK stage
+ * fixed [Dh | -L(-1) | -L(+1)] operand (n + 2 <= 8 columns, zero-padded to the
+ * MMA's K of 8 (TF32) or 16 (BF16); M = 128 rows per MMA, accumulator in
+ * tensor memory).  Applies to dgx_rhs and the ARK stage
  * kernels of this handle (and of batches created from it); the adjoint
  * kernels always contract on CUDA cores, so with a tensor-core contraction
  * the adjoint step differentiates the CUDA-core residual at the stage states
  * the tensor-core forward produced.  DGX_EUNSUPPORTED for FP64 handles,
  * DGX_EINVAL for another mode.  The element tile is the 256-thread shape
  * whatever the autotuned variant, and the persistent pipeline is bypassed. */
-typedef enum { DGX_CONTRACT_CUDA_CORE = 0, DGX_CONTRACT_TF32 = 1, DGX_CONTRACT_3XTF32 = 3 } dgx_contraction;
+typedef enum {
+  DGX_CONTRACT_CUDA_CORE = 0,
+  DGX_CONTRACT_TF32 = 1,
+  DGX_CONTRACT_BF16 = 2,
+  DGX_CONTRACT_3XTF32 = 3
+} dgx_contraction;
 dgx_status dgx_set_contraction(dgx_handle* h, int32_t mode);
 dgx_status dgx_get_contraction(const dgx_handle* h, int32_t* mode);
 

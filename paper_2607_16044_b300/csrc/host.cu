@@ -1181,7 +1181,9 @@ dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable) {
 
 dgx_status dgx_set_contraction(dgx_handle* h, int32_t mode) {
   if (!h) return DGX_EINVAL;
-  if (mode != DGX_CONTRACT_CUDA_CORE && mode != DGX_CONTRACT_TF32 && mode != DGX_CONTRACT_3XTF32) return DGX_EINVAL;
+  if (mode != DGX_CONTRACT_CUDA_CORE && mode != DGX_CONTRACT_TF32 && mode != DGX_CONTRACT_BF16 &&
+      mode != DGX_CONTRACT_3XTF32)
+    return DGX_EINVAL;
   if (mode != DGX_CONTRACT_CUDA_CORE && (h->fp64 || !h->tab->elem_tc)) return DGX_EUNSUPPORTED;
   h->contraction = mode;
   return DGX_OK;

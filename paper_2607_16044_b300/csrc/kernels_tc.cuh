@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, kind::tf32) variant of the element kernel, FP32 only.
+// Tensor-core (tcgen05, kind::tf32 or kind::f16) variant of the element kernel, FP32 only.
 //
 // The weak divergence plus lift of k_elem is, for every (direction a, element,
 // field, line along a), the same small affine map of the line's values
@@ -19,9 +19,13 @@
 // traces of the next stage state).
 //
 // TC = 1: operands rounded to TF32 (about 11 significant bits).
+// TC = 2: operands rounded to BF16 (8 significant bits), kind::f16 MMAs with
+//         K = 16 (columns n + 2 .. 15 zero), FP32 accumulation.
 // TC = 3: 3xTF32, x = hi + lo with both parts TF32; hi*hi + hi*lo + lo*hi
 //         accumulated in FP32 recovers (nearly) FP32 accuracy.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "ops.cuh"
 #include "umma.cuh"
 
@@ -32,16 +36,17 @@ constexpr int TC_V = 1;  // tile shape of the tensor-core element kernel (about 
 template <int D, int P, int TC>
 struct TcShape {
   using H = Sh<D, P, TC_V>;
-  static constexpr int K = 8;                              // kind::tf32: K = 8 per MMA
+  static constexpr int ES = TC == 2 ? 2 : 4;               // operand element bytes (BF16 / TF32)
+  static constexpr int K = 32 / ES;                        // K per MMA: 8 (kind::tf32), 16 (kind::f16)
   static constexpr int PADK = K - (H::n + 2);              // zero columns after the lift columns
   static constexpr int ROWS = D * H::T * H::nf * H::nfp;   // (direction, element, field, line)
   static constexpr int BLOCKS = (ROWS + 127) / 128;        // M = 128 rows per MMA
   static constexpr int COLS = 16 * BLOCKS;                 // N = 16 accumulator columns per block
   static constexpr uint32_t TMEM_COLS = COLS <= 32 ? 32 : COLS <= 64 ? 64 : COLS <= 128 ? 128 : COLS <= 256 ? 256 : 512;
   static constexpr int SPLIT = TC == 3 ? 2 : 1;            // 3xTF32 keeps hi and lo operands
-  static constexpr size_t BLOCK_BYTES = 128 * K * 4;
+  static constexpr size_t BLOCK_BYTES = 128 * K * ES;
   static constexpr size_t A_BYTES = (size_t)BLOCKS * BLOCK_BYTES;
-  static constexpr size_t B_BYTES = 16 * K * 4;
+  static constexpr size_t B_BYTES = 16 * K * ES;
   static constexpr size_t SMEM = SPLIT * (A_BYTES + B_BYTES) + r16(sizeof(float) * 2 * H::n) + 16;
   static_assert(PADK >= 0, "line length plus two lift columns must fit one MMA K step");
   static_assert(COLS <= 512, "accumulator exceeds tensor memory");
@@ -78,12 +83,17 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
     mbar_init(bar, 1);
     fence_mbar_init();
   }
-  auto put = [&](int row, int k, float v) {
-    const uint32_t o = umma_off_k8(row, k);
-    const float hi = tf32_rna(v);
-    *reinterpret_cast<float*>(Ah + o) = hi;
-    if (TC == 3) *reinterpret_cast<float*>(Al + o) = tf32_rna(v - hi);
+  // one operand element: BF16 (round to nearest even) or TF32 hi (and lo for 3xTF32)
+  auto store = [&](unsigned char* hi_base, unsigned char* lo_base, uint32_t o, float v) {
+    if constexpr (TC == 2) {
+      *reinterpret_cast<__nv_bfloat16*>(hi_base + o) = __float2bfloat16_rn(v);
+    } else {
+      const float hi = tf32_rna(v);
+      *reinterpret_cast<float*>(hi_base + o) = hi;
+      if (TC == 3) *reinterpret_cast<float*>(lo_base + o) = tf32_rna(v - hi);
+    }
   };
+  auto put = [&](int row, int k, float v) { store(Ah, Al, umma_off32<C::ES>(row, k), v); };
   // rows are independent, so only the padding columns need defined (zero) values
   if constexpr (C::PADK > 0) {
     for (int i = tid; i < C::BLOCKS * 128 * C::PADK; i += blockDim.x) put(i / C::PADK, n + 2 + i % C::PADK, 0.f);
@@ -94,10 +104,7 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
       const int k = i / C::K, m = i % C::K;
       S v = 0;
       if (k < n) v = m < n ? tb.Dh[k * 6 + m] : (m == n ? -tb.Lm[k] : (m == n + 1 ? -tb.Lp[k] : S(0)));
-      const uint32_t o = umma_off_k8(k, m);
-      const float hi = tf32_rna(v);
-      *reinterpret_cast<float*>(Bh + o) = hi;
-      if (TC == 3) *reinterpret_cast<float*>(Bl + o) = tf32_rna(v - hi);
+      store(Bh, Bl, umma_off32<C::ES>(k, m), v);
     }
     for (int i = tid; i < n; i += blockDim.x) {
       lm[i] = tb.lm[i];
@@ -143,13 +150,16 @@ __global__ void __launch_bounds__(Sh<D, P, TC_V>::THREADS)
   tc_fence_after();
   const uint32_t tmem = *tslot;
   if (tid == 0) {
-    const uint32_t idesc = umma_idesc_tf32(128, 16);
+    const uint32_t idesc = TC == 2 ? umma_idesc_bf16(128, 16) : umma_idesc_tf32(128, 16);
     const uint64_t bh = umma_smem_desc(smem_u32(Bh), 128, 256);
     const uint64_t bl = umma_smem_desc(smem_u32(Bl), 128, 256);
     for (int b = 0; b < C::BLOCKS; ++b) {
       const uint32_t d = tmem + 16 * b;
       const uint64_t ah = umma_smem_desc(smem_u32(Ah + b * C::BLOCK_BYTES), 128, 256);
-      umma_tf32(d, ah, bh, idesc, 0u);
+      if (TC == 2)
+        umma_bf16(d, ah, bh, idesc, 0u);
+      else
+        umma_tf32(d, ah, bh, idesc, 0u);
       if (TC == 3) {
         const uint64_t al = umma_smem_desc(smem_u32(Al + b * C::BLOCK_BYTES), 128, 256);
         umma_tf32(d, ah, bl, idesc, 1u);
@@ -251,16 +261,18 @@ struct TcOps {
     if (curv) return run<MODE, false, true, TC>(M, U, w, out, sa, st);
     return run<MODE, false, false, TC>(M, U, w, out, sa, st);
   }
-  // tc: 1 = TF32, 3 = 3xTF32; stage == nullptr writes f to out, otherwise the ARK stage update
+  // tc: 1 = TF32, 2 = BF16, 3 = 3xTF32; stage == nullptr writes f to out, otherwise the ARK stage update
   static cudaError_t elem(const Mesh<float>& M, int tc, bool visc, bool curv, const float* U, const Work& w,
                           float* out, const Stage<float>* stage, cudaStream_t st) {
-    if (tc != 1 && tc != 3) return cudaErrorInvalidValue;
+    if (tc != 1 && tc != 2 && tc != 3) return cudaErrorInvalidValue;
     if (stage) {
       if (tc == 1) return mode_tc<1, 1>(M, visc, curv, U, w, nullptr, *stage, st);
+      if (tc == 2) return mode_tc<1, 2>(M, visc, curv, U, w, nullptr, *stage, st);
       return mode_tc<1, 3>(M, visc, curv, U, w, nullptr, *stage, st);
     }
     Stage<float> none{};
     if (tc == 1) return mode_tc<0, 1>(M, visc, curv, U, w, out, none, st);
+    if (tc == 2) return mode_tc<0, 2>(M, visc, curv, U, w, out, none, st);
     return mode_tc<0, 3>(M, visc, curv, U, w, out, none, st);
   }
 };

@@ -1,11 +1,14 @@
 // Minimal tcgen05 (5th-generation tensor core) building blocks, inline PTX.
 //
-// One CTA computes D[M x N] = A[M x K] * B[N x K]^T with kind::tf32, both
-// operands K-major in shared memory (no swizzle), the FP32 accumulator in
-// tensor memory (TMEM).  Canonical no-swizzle K-major layout: 8-row x 16-byte
-// core matrices; element (r, k) of an operand with rows grouped by 8 sits at
-//   (r / 8) * SBO + (k / 4) * LBO + (r % 8) * 16 + (k % 4) * 4   bytes,
-// here with LBO = 128 (next 4 K-values) and SBO = 128 * (K / 4) (next 8 rows).
+// One CTA computes D[M x N] = A[M x K] * B[N x K]^T with kind::tf32 (K = 8
+// per MMA) or kind::f16 with BF16 operands (K = 16 per MMA), both operands
+// K-major in shared memory (no swizzle), the FP32 accumulator in tensor memory
+// (TMEM).  Canonical no-swizzle K-major layout: 8-row x 16-byte core matrices;
+// with e-byte elements, element (r, k) of an operand whose K extent is 32
+// bytes sits at
+//   (r / 8) * SBO + (k / (16 / e)) * LBO + (r % 8) * 16 + (k % (16 / e)) * e
+// bytes, with LBO = 128 (the next core matrix along K) and SBO = 256 (the
+// next 8 rows): TF32 with K = 8 and BF16 with K = 16 have the same bytes.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -14,9 +17,11 @@
 
 namespace dgx {
 
-// byte offset of (row, k) in a K-major no-swizzle operand with K = 8
-__host__ __device__ constexpr uint32_t umma_off_k8(int row, int k) {
-  return (uint32_t)((row >> 3) * 256 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// byte offset of (row, k) in a K-major no-swizzle operand of 32 bytes per row
+// along K with ES-byte elements (ES = 4: TF32, K = 8; ES = 2: BF16, K = 16)
+template <int ES>
+__host__ __device__ constexpr uint32_t umma_off32(int row, int k) {
+  return (uint32_t)((row >> 3) * 256 + (k / (16 / ES)) * 128 + (row & 7) * 16 + (k % (16 / ES)) * ES);
 }
 
 // 64-bit shared-memory matrix descriptor (sm_100 family): start address,
@@ -30,6 +35,12 @@ __host__ __device__ constexpr uint64_t umma_smem_desc(uint32_t saddr, uint32_t l
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 32-bit instruction descriptor for kind::f16 with BF16 operands: D = F32,
+// A = B = BF16 (format 1; both operands always the same type), both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {  // whole warp
@@ -48,6 +59,15 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }

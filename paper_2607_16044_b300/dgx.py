@@ -46,7 +46,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint"]
-CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "3xtf32": 3}
+CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
 
@@ -328,7 +328,7 @@ class Solver:
 
     def set_contraction(self, mode: str):
         """Contraction engine of the forward element kernel: "cuda_core" (default),
-        "tf32" or "3xtf32" (tcgen05 tensor cores, FP32 handles only)."""
+        "tf32", "bf16" or "3xtf32" (tcgen05 tensor cores, FP32 handles only)."""
         if mode not in CONTRACTIONS:
             raise ValueError(f"contraction must be one of {sorted(CONTRACTIONS)}")
         _check(self.lib.dgx_set_contraction(self.h, CONTRACTIONS[mode]), "dgx_set_contraction")
