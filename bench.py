@@ -418,7 +418,8 @@ def roofline(res, prec, pk):
     for k, (nl, kms) in res["prof"].items():
         fl, by = s.kernel_work(k)
         t = kms / nl / 1e3
-        per_kernel[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1), "TFLOP/s": round(fl / t / 1e12, 3)}
+        per_kernel[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1), "TFLOP/s": round(fl / t / 1e12, 3),
+                         "frac_hbm": round(by / t / 1e9 / pk["hbm_gbs"], 3)}
     if t_mem >= t_alu:
         ach = bytes_l / per_launch_s / 1e9
         out = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
