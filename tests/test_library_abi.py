@@ -49,3 +49,25 @@ def test_host_validation_without_gpu():
     assert lib.dgx_ark_step_stages(None, None, 1e-3, None, None, None) == 1
     assert lib.dgx_ark_adjoint_step(None, None, None, 1e-3, None, None) == 1
     assert lib.dgx_workspace_bytes(None, dgx.OP_ARK_STEP_ADJOINT) == 0
+
+
+def _enum_values(prefix):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_constants_match_header():
+    """The Python binding's operation, contraction and kernel-kind numbers are
+    the ones include/dgx.h declares."""
+    from paper_2607_16044_b300 import dgx
+    ops = _enum_values("DGX_OP_")
+    assert (dgx.OP_RHS, dgx.OP_VJP, dgx.OP_ARK, dgx.OP_ARK_ADJOINT, dgx.OP_ARK_STEP_ADJOINT) == (
+        ops["DGX_OP_RHS"], ops["DGX_OP_VJP"], ops["DGX_OP_ARK"], ops["DGX_OP_ARK_ADJOINT"],
+        ops["DGX_OP_ARK_STEP_ADJOINT"])
+    con = _enum_values("DGX_CONTRACT_")
+    assert dgx.CONTRACTIONS == {"cuda_core": con["DGX_CONTRACT_CUDA_CORE"], "tf32": con["DGX_CONTRACT_TF32"],
+                                "bf16": con["DGX_CONTRACT_BF16"], "3xtf32": con["DGX_CONTRACT_3XTF32"]}
+    kinds = _enum_values("DGX_K")
+    assert len(dgx.KERNELS) == kinds["DGX_KERNEL_KINDS"]
+    for i, name in enumerate(dgx.KERNELS):
+        assert kinds["DGX_K_" + name.upper()] == i
