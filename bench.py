@@ -1,16 +1,21 @@
 """Benchmark: DG residual DOF-evaluations per second on one B300.
 
-Workload: the 2D compressible Navier-Stokes channel -- x in [0, 5) periodic
-with 256 columns, y in [-1, 1] with 2 x 64 rows grown from each wall by ratio
-1.15 (aspect ratios up to ~1e3), adiabatic walls, p = 4 (25 Gauss nodes per
-element, 3,276,800 DOFs), Re = 1000, Ma = 0.3, Pr = 0.72, BR1 viscous flux,
-Poiseuille state with a seeded 1e-3 perturbation (synthetic, seeded).
+Headline workload (the largest single-GPU configuration): the 3D compressible
+Navier-Stokes channel -- x, y in [0, 2 pi) periodic with 48 columns each,
+z in [-1, 1] with 2 x 24 layers grown from each wall by ratio 1.1, adiabatic
+walls, p = 5 (216 Gauss nodes per element, 110,592 elements, 23.9 M nodes,
+119.4 M DOFs), Re = 1000, Ma = 0.3, Pr = 0.72, BR1 viscous flux, LLF
+convective flux, Poiseuille state with a seeded 1e-3 perturbation (synthetic).
 
 One step = one explicit ARS(3,4,3) step (4 fused residual + stage-update
-evaluations) followed by its discrete adjoint (reverse stage recurrence: 4
-vector-Jacobian products of the residual), i.e. 8 DOF-residual evaluations
-per DOF.  The headline runs the FP32 path (FP64 stage accumulation); the FP64
-path is measured the same way and reported beside it.
+evaluations, stage states kept as checkpoints) followed by its discrete
+adjoint (reverse stage recurrence: 4 vector-Jacobian products), i.e. 8
+DOF-residual evaluations per DOF.  The headline runs in FP64 (the paper's
+arithmetic); the FP32 path (FP64 stage accumulation) of the same workload is
+reported in the same line as the precision variant, with its deviation from
+the FP64 step.  Secondary workloads (2D channel, vortex accuracy FP32 vs FP64,
+64-instance ensemble, TGV contraction engines, 50-step checkpointed adjoint)
+follow as extra keys.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dgx|reference]
 Prints one JSON line (rank 0).
@@ -31,7 +36,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DG residual DOF-evals/s (fwd+VJP), % HBM roofline, FP32 vs FP64 at stated L2 err"
 UNIT = "DOF-evals/s"
-WORKLOAD = "2D NS channel 256x128 quads, wall stretching 1.15 (AR~1e3), p=4, Re=1000, Ma=0.3, Pr=0.72, BR1+LLF"
+WORKLOAD = ("3D NS channel 48x48x48 hexes (x, y periodic; z wall-stretched, ratio 1.1), p=5 (216 nodes/element, "
+            "23.9M nodes, 119.4M DOFs), Re=1000, Ma=0.3, Pr=0.72, BR1+LLF")
+WORKLOAD_2D = "2D NS channel 256x128 quads, wall stretching 1.15 (AR~1e3), p=4, Re=1000, Ma=0.3, Pr=0.72, BR1+LLF"
+# state-size vectors the method must move per step (residual: read U, write f;
+# VJP: read U and lambda, write g; ARS(3,4,3) stage updates: 2 + i in stage i)
+METHOD_VECTORS_PER_STEP = 4 * 2 + 4 * 3 + (2 + 3 + 4 + 5)
 
 
 def peaks():
@@ -42,12 +52,22 @@ def peaks():
     return {"hbm_gbs": 6400.0, "source": "fallback", "sm_max_mhz": 2032.0}
 
 
-# ALU peaks derived from unit counts and the maximum SM clock (2032 MHz):
-# FP32: 148 SMs x 128 lanes x 2 flop/FMA; FP64: the nominal 1.25 TFLOP/s of B300.
-def alu_peak_tflops(prec, sm_mhz=2032.0):
-    if prec == "fp32":
-        return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    return 1.25
+# ALU peaks: measured in this run by an FMA-chain kernel (dgx_probe_fma, CUDA
+# events, best of 5); the unit-count figures are kept beside them for context:
+# FP32 148 SMs x 128 lanes x 2 flop x 2032 MHz = 77.0 TFLOP/s, FP64 the
+# nominal 1.25 TFLOP/s of B300.
+_ALU = {}
+
+
+def alu_peak_tflops(prec):
+    if prec not in _ALU:
+        from paper_2607_16044_b300.dgx import measure_fma_peak
+        _ALU[prec] = measure_fma_peak(prec)
+    return _ALU[prec]
+
+
+def alu_peak_derived(prec, sm_mhz=2032.0):
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12 if prec == "fp32" else 1.25
 
 
 class ClockSampler:
@@ -163,22 +183,22 @@ def aggregate_rate(units_per_rank, ms_max, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def make_solver(prec):
+def make_solver(prec, workload="channel3d"):
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
     from paper_2607_16044_b300.tableaux import ars343_explicit
-    mesh, phys, U0 = I.channel2d_workload()
+    mesh, phys, U0 = I.channel3d_workload() if workload == "channel3d" else I.channel2d_workload()
     s = Solver(mesh, phys, prec)
     A, b, c = ars343_explicit()
     s.set_tableau(A, b, c)
     return s, mesh, phys, U0
 
 
-def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
+def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channel3d", e2e=True):
     """K timed steps; each step = one ARS(3,4,3) step keeping its stage states
     + the discrete adjoint of that step (4 VJPs), L2 flushed between steps."""
     import torch
-    s, mesh, phys, U0 = make_solver(prec)
+    s, mesh, phys, U0 = make_solver(prec, workload)
     dev = torch.device("cuda", torch.cuda.current_device())
     U = torch.as_tensor(U0, device=dev).contiguous()
     lam0 = np.random.default_rng(102).standard_normal(U0.shape)
@@ -191,7 +211,7 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
         s.ark_step_stages(U, dt, stages)
         s.ark_adjoint_step(stages, lam, dt)
 
-    variants = s.autotune(U, reps=3)        # set-up: fastest tile size per kernel
+    variants = s.autotune(U, reps=1 if workload == "channel3d" else 3)   # set-up: fastest tile size per kernel
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
@@ -241,6 +261,19 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
     torch.cuda.synchronize()
     dist_barrier()
     s.check()
+    nbytes_state = U.numel() * 8
+    dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
+    # one step from U_n (after the timed steps) kept for the FP32-vs-FP64 comparison
+    U.copy_(torch.as_tensor(U0))
+    s.ark_step_stages(U, dt, stages)
+    increment = (U - torch.as_tensor(U0, device=dev)).cpu().numpy()
+    U.copy_(torch.as_tensor(U0))
+    base = {"ms": float(np.mean(gtimes)), "eager_ms": float(np.mean(times)), "ms_all": gtimes, "prof": prof,
+            "clocks": clocks.summary(), "dofs": dofs, "evals_per_step": 8, "mesh": mesh, "phys": phys,
+            "steps": steps, "solver": s, "variants": variants, "increment": increment,
+            "state_bytes": mesh.n_elem * (mesh.dim + 2) * mesh.N * (8 if prec == "fp64" else 4)}
+    if not e2e:
+        return base
     # end to end through the public API: pinned host U_n and lambda_{n+1} in,
     # U_{n+1} and lambda_n out, every step.  The adjoint needs lambda only after
     # the forward step and leaves U untouched, so a second stream uploads lambda
@@ -363,12 +396,9 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False):
     e2e_pipe = pipelined(max(4, steps))
     copy_ms = copies_only()
     s.check()
-    nbytes_state = U.numel() * 8
-    dofs = mesh.n_elem * (mesh.dim + 2) * mesh.N
-    return {"ms": float(np.mean(gtimes)), "eager_ms": float(np.mean(times)), "ms_all": gtimes, "prof": prof, "clocks": clocks.summary(), "dofs": dofs,
-            "evals_per_step": 8, "e2e_ms": e2e_pipe, "e2e_serial_ms": float(np.mean(e2e)), "copy_ms": copy_ms,
-            "h2d": 2 * nbytes_state, "d2h": 2 * nbytes_state,
-            "mesh": mesh, "phys": phys, "steps": steps, "solver": s, "variants": variants}
+    base.update({"e2e_ms": e2e_pipe, "e2e_serial_ms": float(np.mean(e2e)), "copy_ms": copy_ms,
+                 "h2d": 2 * nbytes_state, "d2h": 2 * nbytes_state})
+    return base
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
@@ -404,36 +434,53 @@ def sources_hash(root_header="vjp.cuh"):
 def roofline(res, prec, pk):
     """Roofline of the dominant kernel (largest summed device time): algorithmic
     flops and bytes per launch from the library (dgx_kernel_work: counted
-    arithmetic, compulsory traffic) over the kernel's mean event-timed duration."""
+    arithmetic, compulsory traffic) over the kernel's mean event-timed duration,
+    plus the whole step against the method's minimum traffic (state-size
+    vectors per step) and against the ALU peak (summed counted flops)."""
     s = res["solver"]
     best = max(res["prof"].items(), key=lambda kv: kv[1][1])
     name, (launches, ms) = best
     per_launch_s = ms / launches / 1e3
     flops_l, bytes_l = s.kernel_work(name)
+    alu = alu_peak_tflops(prec)
     t_mem = bytes_l / (pk["hbm_gbs"] * 1e9)
-    t_alu = flops_l / (alu_peak_tflops(prec) * 1e12)
+    t_alu = flops_l / (alu * 1e12)
     total = sum(x[1] for x in res["prof"].values())
     shares = {k: round(v[1] / total, 4) for k, v in res["prof"].items()}
     per_kernel = {}
+    step_flops = 0.0
     for k, (nl, kms) in res["prof"].items():
         fl, by = s.kernel_work(k)
         t = kms / nl / 1e3
+        step_flops += fl * nl / res["steps"]
         per_kernel[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1), "TFLOP/s": round(fl / t / 1e12, 3),
-                         "frac_hbm": round(by / t / 1e9 / pk["hbm_gbs"], 3)}
+                         "frac_hbm": round(by / t / 1e9 / pk["hbm_gbs"], 3), "frac_alu": round(fl / t / 1e12 / alu, 3)}
+    alu_src = (f"measured in this run: FMA chains (dgx_probe_fma), {prec.upper()}, best of 5; unit-count figure "
+               f"{alu_peak_derived(prec):.2f} TFLOP/s")
     if t_mem >= t_alu:
         ach = bytes_l / per_launch_s / 1e9
         out = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                "frac": round(ach / pk["hbm_gbs"], 4), "peak_source": pk["source"] + " (of measured copy bandwidth)"}
     else:
         ach = flops_l / per_launch_s / 1e12
-        peak = alu_peak_tflops(prec)
-        out = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-               "frac": round(ach / peak, 4),
-               "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz" if prec == "fp32"
-               else "nominal B300 FP64 1.25 TFLOP/s"}
+        out = {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu, 3), "unit": "TFLOP/s",
+               "frac": round(ach / alu, 4), "peak_source": alu_src}
+    step_s = res["ms"] / 1e3
+    method_bytes = METHOD_VECTORS_PER_STEP * res["state_bytes"]
     out.update({"kernel": name, "launches": launches, "avg_launch_us": round(per_launch_s * 1e6, 2),
                 "algorithmic_bytes": int(bytes_l), "algorithmic_flops": int(flops_l),
-                "traffic": None, "kernel_shares": shares, "per_kernel": per_kernel})
+                "traffic": None, "kernel_shares": shares, "per_kernel": per_kernel,
+                # the whole step against the method's minimum traffic: 2 state vectors per residual,
+                # 3 per VJP, 2 + i per ARS(3,4,3) stage update (34 per step), in the handle's precision
+                "method_bytes_per_step": int(method_bytes),
+                "frac_method": round(method_bytes / step_s / 1e9 / pk["hbm_gbs"], 4),
+                "frac_method_note": "34 state vectors per step (4 x 2 residual, 4 x 3 VJP, 14 stage update) / "
+                                    "graph-replayed step time / measured HBM copy bandwidth",
+                # the whole step against the ALU peak: counted flops of every launch of the step
+                "step_flops": int(step_flops),
+                "frac_alu_step": round(step_flops / step_s / 1e12 / alu, 4),
+                "alu_peak_tflops": round(alu, 3), "alu_peak_source": alu_src,
+                "hbm_peak_gbs": pk["hbm_gbs"]})
     if prec == "fp32" and name == NCU_TRAFFIC["kernel"] and sources_hash() == NCU_TRAFFIC["sources"]:
         out["traffic"] = NCU_TRAFFIC["bytes"]
         out["traffic_source"] = "ncu capture (profiles/k_vjp_br1_channel2d_p4_fp32.md), bytes per launch"
@@ -573,36 +620,21 @@ def tgv_perf(reps=10, profile_range=False):
     return out
 
 
-def channel3d_perf(reps=3):
-    """48^3 p = 5 wall-stretched 3D channel (24M nodes): one FP32 ARK step with
-    stage checkpoints and its adjoint."""
+def channel3d_trajectory(prec="fp32", nsteps=50):
+    """48^3 p = 5 wall-stretched 3D channel: the workload's full form, the
+    gradient through 50 ARK steps with one FP64 checkpoint per step (forward
+    sweep: 4 residuals per step; reverse sweep: the step's 4 stages recomputed
+    from its checkpoint and its 4 VJPs)."""
     import torch
     from paper_2607_16044_b300 import inputs as I
-    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.dgx import Solver, adjoint_trajectory
     from paper_2607_16044_b300.tableaux import ars343_explicit
     mesh, phys, U0 = I.channel3d_workload()
-    s = Solver(mesh, phys, "fp32")
+    s = Solver(mesh, phys, prec)
     s.set_tableau(*ars343_explicit())
     U = torch.as_tensor(U0).cuda()
     lam = torch.as_tensor(np.random.default_rng(105).standard_normal(U0.shape)).cuda()
-    stages = s.stage_buffer()
-
-    def step():
-        s.ark_step_adjoint(U, lam, 1e-9, stages)
     s.autotune(U, reps=1)
-    step()
-    ms = _time_events(step, reps)
-    s.check()
-    out = {"workload": "3D NS channel 48^3, p=5 (216 nodes/element), z-stretching 1.1, FP32 step + adjoint",
-           "dofs": int(U0.size), "ms_per_step": round(ms, 3),
-           "dof_evals_per_s": round(8 * U0.size / (ms / 1e3), 1)}
-    # the workload's full form: gradient through 50 ARK steps with one FP64
-    # checkpoint per step (forward sweep: 4 residuals per step; reverse sweep:
-    # the step's 4 stages recomputed from its checkpoint and its 4 VJPs)
-    from paper_2607_16044_b300.dgx import adjoint_trajectory
-    nsteps = 50
-    del stages
-    U.copy_(torch.as_tensor(U0))
     ckpt = []
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -612,74 +644,83 @@ def channel3d_perf(reps=3):
     torch.cuda.synchronize()
     s.check()
     tms = e0.elapsed_time(e1)
-    out["trajectory"] = {"steps": nsteps, "ms": round(tms, 1), "checkpoint_GB": round(nsteps * U0.size * 8 / 1e9, 1),
-                         "dof_evals_per_step": "12 (4 forward + 4 recomputed + 4 VJP)",
-                         "dof_evals_per_s": round(12 * nsteps * U0.size / (tms / 1e3), 1)}
     ckpt.clear()
-    return out
+    return {"workload": "3D NS channel 48^3, p=5: gradient through 50 ARS(3,4,3) steps, one FP64 checkpoint per step",
+            "dtype": prec, "steps": nsteps, "ms": round(tms, 1),
+            "checkpoint_GB": round(nsteps * U0.size * 8 / 1e9, 1),
+            "dof_evals_per_step": "12 (4 forward + 4 recomputed + 4 VJP)",
+            "dof_evals_per_s": round(12 * nsteps * U0.size / (tms / 1e3), 1)}
 
 
-def cpu_baseline(steps_hint=1):
-    """The FP64 oracle as it stands, on this host's cores: one residual of the
-    full workload (bounded sample), scaled to DOF-evals/s."""
+def _oracle_sample(n_rows=16, seed=7):
+    """The headline mesh and a bounded sample of it for the CPU oracle: n_rows
+    elements (both walls included) with the sub-meshes their residual rows
+    (3 rings: BR1 reaches two neighbours) and VJP rows (5 rings) need."""
     import torch
     from oracle.physics import Gas
-    from oracle.residual import DGOperator
-    from oracle.vjp import vjp
+    from oracle.residual import DGOperator, submesh_around
     from paper_2607_16044_b300 import inputs as I
-    mesh, phys, U0 = I.channel2d_workload()
-    op = DGOperator(mesh, Gas(phys.gamma, Re=phys.Re, Pr=phys.Pr, viscous=phys.viscous))
-    U = torch.as_tensor(U0)
+    mesh, phys, U0 = I.channel3d_workload()
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, n_rows - 2, replace=False), [0, mesh.n_elem - 1]]))
+    gas = Gas(phys.gamma, Re=phys.Re, Pr=phys.Pr, viscous=phys.viscous)
+    lam0 = np.random.default_rng(105).standard_normal(U0.shape)
+    sub3, keep3, loc3 = submesh_around(mesh, rows, 3)
+    sub5, keep5, loc5 = submesh_around(mesh, rows, 5)
+    op3, op5 = DGOperator(sub3, gas), DGOperator(sub5, gas)
+    return {"rows": rows, "per_elem_dofs": (mesh.dim + 2) * mesh.N, "E": mesh.n_elem,
+            "fwd": (op3, torch.as_tensor(U0[keep3]), loc3),
+            "vjp": (op5, torch.as_tensor(U0[keep5]), torch.as_tensor(lam0[keep5]), loc5)}
+
+
+def _oracle_step(smp):
+    """4 residual evaluations + 4 VJPs of the sampled rows (one ARK step and its adjoint)."""
+    from oracle.vjp import vjp_rows
+    op3, U3, loc3 = smp["fwd"]
+    op5, U5, l5, loc5 = smp["vjp"]
+    for _ in range(4):
+        op3.residual(U3, loc3)
+    for _ in range(4):
+        vjp_rows(op5, U5, l5, loc5)
+
+
+def cpu_baseline():
+    """The FP64 oracle as it stands, on this host's cores: one sampled step of
+    the headline workload (bounded sample), scaled to DOF-evals/s."""
+    import torch
+    smp = _oracle_sample()
     t0 = time.perf_counter()
-    op.residual(U)
-    t1 = time.perf_counter()
-    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape))
-    vjp(op, U, lam)
-    t2 = time.perf_counter()
-    dofs = U.numel()
-    return {"value": round(2 * dofs / (t2 - t0), 1), "unit": UNIT, "cores": torch.get_num_threads(),
+    _oracle_step(smp)
+    t = time.perf_counter() - t0
+    n = len(smp["rows"])
+    return {"value": round(8 * n * smp["per_elem_dofs"] / t, 1), "unit": UNIT, "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": f"one residual ({t1 - t0:.1f} s) + one VJP ({t2 - t1:.1f} s) of the full 256x128 p=4 "
-                      f"channel, FP64 torch CPU oracle"}
+            "sample": f"4 residual rows + 4 VJP rows of {n} of the {smp['E']} elements of the 48^3 p=5 channel "
+                      f"(each on the sub-mesh of rings it needs), FP64 torch CPU oracle, {t:.1f} s"}
 
 
 def reference_arm(args):
     """--impl reference: the CPU oracle timed on the host cores, each step a
-    bounded sample of the workload (a fixed 1/32 element subset: 4 residuals
-    + 4 VJPs of the subset, as in one ARK step and its adjoint)."""
+    bounded sample of the headline workload (4 residuals + 4 VJPs of a fixed
+    set of sampled elements, as in one ARK step and its adjoint)."""
     import torch
-    from oracle.physics import Gas
-    from oracle.residual import DGOperator
-    from oracle.vjp import vjp_rows
-    from paper_2607_16044_b300 import inputs as I
-    mesh, phys, U0 = I.channel2d_workload()
-    op = DGOperator(mesh, Gas(phys.gamma, Re=phys.Re, Pr=phys.Pr, viscous=phys.viscous))
-    U = torch.as_tensor(U0)
-    lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape))
-    elems = np.arange(0, mesh.n_elem, 32)
-    per_elem_dofs = (mesh.dim + 2) * mesh.N
-
-    def step():
-        for _ in range(4):
-            op.residual(U, elems)
-        for _ in range(4):
-            vjp_rows(op, U, lam, elems)
-
+    smp = _oracle_sample()
     for _ in range(args.warmup):
-        step()
+        _oracle_step(smp)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        _oracle_step(smp)
     dt = (time.perf_counter() - t0) / args.steps
-    value = 8 * len(elems) * per_elem_dofs / dt
+    n = len(smp["rows"])
+    value = 8 * n * smp["per_elem_dofs"] / dt
     cores = torch.get_num_threads()
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
-            "config": {"workload": WORKLOAD, "sample": f"{len(elems)} of {mesh.n_elem} elements per step"},
+            "config": {"workload": WORKLOAD, "sample": f"{n} of {smp['E']} elements per step"},
             "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"4 residuals + 4 VJPs on {len(elems)} elements (every 32nd) per step"},
+                             "sample": f"4 residual rows + 4 VJP rows of {n} sampled elements per step"},
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -692,8 +733,9 @@ def main():
     ap.add_argument("--impl", default="dgx", choices=["dgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
-    ap.add_argument("--legs", default="fp32,fp64",
-                    help="precisions to time (profiling runs may pick one), or 'tgv' for the TGV engine comparison")
+    ap.add_argument("--legs", default="fp64,fp32",
+                    help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' alone (profiling "
+                         "runs), or 'tgv' for the TGV engine comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -717,43 +759,58 @@ def main():
     if legs == ["tgv"]:   # the TGV contraction-engine comparison alone (profiling runs)
         print(json.dumps({"tgv": tgv_perf(profile_range=args.profile_range)}))
         return
-    if legs == ["fp64"]:
-        r = time_gpu("fp64", args.steps, args.warmup, profile_range=args.profile_range)
-        print(json.dumps({"leg": "fp64", "ms_per_step": r["ms"], "prof": r["prof"]}))
+    if len(legs) == 1:    # one precision of one workload alone (profiling runs)
+        prec, _, wl = legs[0].partition(":")
+        r = time_gpu(prec, args.steps, args.warmup, profile_range=args.profile_range, workload=wl or "channel3d",
+                     e2e=False)
+        print(json.dumps({"leg": legs[0], "ms_per_step": r["ms"], "prof": r["prof"]}))
         return
-    r32 = time_gpu("fp32", args.steps, args.warmup, profile_range=args.profile_range)
-    if "fp64" not in legs:
-        print(json.dumps({"leg": "fp32", "ms_per_step": r32["ms"], "prof": r32["prof"]}))
-        return
-    r64 = time_gpu("fp64", max(3, args.steps // 4), 3)
-    ms = dist_max(r32["ms"])
-    evals = r32["dofs"] * r32["evals_per_step"]
+    # headline: the 48^3 p = 5 channel in FP64
+    r64 = time_gpu("fp64", args.steps, args.warmup)
+    ms = dist_max(r64["ms"])
+    evals = r64["dofs"] * r64["evals_per_step"]
     value = aggregate_rate(evals, ms, world)
-    e2e_value = aggregate_rate(evals, dist_max(r32["e2e_ms"]), world)
-    e2e_serial = aggregate_rate(evals, dist_max(r32["e2e_serial_ms"]), world)
-    roof = roofline(r32, "fp32", pk)
-    roof64 = roofline(r64, "fp64", pk)
-    launches = sum(v[0] for v in r32["prof"].values())
+    e2e_value = aggregate_rate(evals, dist_max(r64["e2e_ms"]), world)
+    e2e_serial = aggregate_rate(evals, dist_max(r64["e2e_serial_ms"]), world)
+    roof = roofline(r64, "fp64", pk)
+    launches = sum(v[0] for v in r64["prof"].values())
+    inc64 = r64.pop("increment")
+    r64["solver"].close()
+    del r64["solver"]
+    import torch
+    torch.cuda.empty_cache()
+    # precision variant: the same workload and step in FP32 (FP64 stage accumulation)
+    r32 = time_gpu("fp32", args.steps, args.warmup, e2e=False)
+    inc32 = r32.pop("increment")
+    roof32 = roofline(r32, "fp32", pk)
+    r32["solver"].close()
+    del r32["solver"]
+    torch.cuda.empty_cache()
+    # deviation of the FP32 step from the FP64 step (the increment U_{n+1} - U_n of
+    # one step from the same U_n), per field relative to the FP64 increment's max
+    dev32 = max(float(np.abs(inc32[:, f] - inc64[:, f]).max() / np.abs(inc64[:, f]).max())
+                for f in range(inc64.shape[1]))
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
-            "config": {"workload": WORKLOAD, "elements": r32["mesh"].n_elem, "dofs": r32["dofs"],
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Poiseuille + 1e-3 perturbation)",
+            "config": {"workload": WORKLOAD, "elements": r64["mesh"].n_elem, "dofs": r64["dofs"],
                        "timing": "CUDA-graph replay of the one-call step (dgx_ark_step_adjoint: the kernels "
                                  "that form U_{n+1} overlap the adjoint on a second stream); per-kernel roofline "
                                  "from an eager profiled pass of the same steps as separate calls on one stream",
-                       "eager_ms_per_step": round(r32["eager_ms"], 4),
-                       "tile_variants": {k: v for k, v in r32["variants"].items()
+                       "eager_ms_per_step": round(r64["eager_ms"], 4),
+                       "tile_variants": {k: v for k, v in r64["variants"].items()
                                          if k not in ("face", "vjp_face")},
                        "step": "1 ARS(3,4,3) step (stage states kept) + its discrete adjoint (4 VJPs)",
                        "kernel_launches_per_step": launches // max(1, args.steps),
-                       "dof_evals_per_step": evals, "l2": "flushed (256 MB write) between timed steps",
+                       "dof_evals_per_step": evals,
+                       "l2": "flushed (256 MB write) between timed steps; the state (955 MB FP64) exceeds L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "gpu_launches": int(launches),
-            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": r32["h2d"],
-                    "d2h_bytes_per_step": r32["d2h"],
-                    "ms_per_step": round(dist_max(r32["e2e_ms"]), 4),
-                    "copy_bound_ms": round(dist_max(r32["copy_ms"]), 4),
-                    "frac_of_copy_bound": round(dist_max(r32["copy_ms"]) / dist_max(r32["e2e_ms"]), 3),
+            "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": r64["h2d"],
+                    "d2h_bytes_per_step": r64["d2h"],
+                    "ms_per_step": round(dist_max(r64["e2e_ms"]), 4),
+                    "copy_bound_ms": round(dist_max(r64["copy_ms"]), 4),
+                    "frac_of_copy_bound": round(dist_max(r64["copy_ms"]) / dist_max(r64["e2e_ms"]), 3),
                     "schedule": "consecutive steps pipelined: double-buffered device U and lambda, step k+1's "
                                 "pinned-host uploads on one copy stream and step k's downloads on another "
                                 "overlap step k's forward and adjoint graphs, U_{n+1} downloaded during the "
@@ -762,15 +819,28 @@ def main():
                     "serial_schedule": "one step at a time: U_n upload, forward step (lambda upload on a "
                                        "second stream), adjoint (U_{n+1} download on the second stream), "
                                        "lambda_n download, synchronise"},
-            "clocks": r32["clocks"],
-            "fp64": {"value": round(r64["dofs"] * r64["evals_per_step"] / (r64["ms"] / 1e3), 1), "unit": UNIT,
-                     "ms_per_step": round(r64["ms"], 4), "eager_ms_per_step": round(r64["eager_ms"], 4),
-                     "roofline": roof64, "clocks": r64["clocks"]}}
+            "clocks": r64["clocks"],
+            "fp32": {"value": round(aggregate_rate(evals, dist_max(r32["ms"]), world), 1), "unit": UNIT,
+                     "dtype": "f32 (FP64 stage accumulation)", "ms_per_step": round(r32["ms"], 4),
+                     "eager_ms_per_step": round(r32["eager_ms"], 4), "roofline": roof32, "clocks": r32["clocks"],
+                     "step_increment_deviation_vs_fp64": dev32,
+                     "error_note": "max over fields of |dU_fp32 - dU_fp64|_inf / |dU_fp64|_inf for one step "
+                                   "dU = U_{n+1} - U_n from the same U_n; the FP64 path matches the oracle to "
+                                   "1e-12 and the FP32 residual to 1e-5 (parity tests)"}}
     if not args.no_extra:
+        c2 = {}
+        for prec in ("fp32", "fp64"):
+            r = time_gpu(prec, max(3, args.steps // 2), 3, workload="channel2d", e2e=False)
+            r.pop("increment")
+            c2[prec] = {"value": round(r["dofs"] * 8 / (r["ms"] / 1e3), 1), "unit": UNIT,
+                        "ms_per_step": round(r["ms"], 4), "roofline": roofline(r, prec, pk)}
+            r["solver"].close()
+        c2["workload"] = WORKLOAD_2D + ", 1 ARS(3,4,3) step + adjoint"
+        line["channel2d"] = c2
         line["vortex_fp32_vs_fp64"] = vortex_accuracy()
         line["ensemble"] = ensemble_perf()
         line["tgv"] = tgv_perf()
-        line["channel3d"] = channel3d_perf()
+        line["channel3d_trajectory"] = channel3d_trajectory()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

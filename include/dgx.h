@@ -182,13 +182,28 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
  * workspace, so the call allocates nothing: for hosts that reserve all device
  * memory up front or plugin hosts that pass only inputs and outputs.
  * Limit: dgx_workspace_bytes(h, DGX_OP_RHS) must not exceed
- * DGX_NOALLOC_SCRATCH_BYTES (64 MiB), else DGX_EINVAL.  The array is held on
- * every device that loads the library until the process exits.  The first
- * call on each device looks up the array's device address (with that device
- * current); make it before any stream capture.  All calls on a device share
- * the array: calls that may overlap on the GPU race and must be serialised. */
+ * DGX_NOALLOC_SCRATCH_BYTES (64 MiB), else DGX_EINVAL.  The handle's device
+ * (the one current at dgx_create) must be current, else DGX_EINVAL.  Under
+ * CUDA's default lazy module loading the 64 MiB array is created on a device
+ * by the first call there and then held until the process exits; that first
+ * call also looks up the array's device address (cached per device and
+ * context; a call in a new context, e.g. after cudaDeviceReset, looks it up
+ * again).  Make the first call on each device as a warm-up, before reserving
+ * the rest of device memory and before any stream capture.  All calls on a
+ * device share the array: calls that may overlap on the GPU race and must be
+ * serialised. */
 #define DGX_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 dgx_status dgx_rhs_noalloc(dgx_handle* h, const void* U, void* dUdt, void* stream);
+
+/* Arithmetic-throughput probe (measurement only; no counterpart in the paper):
+ * one launch of threads (a positive multiple of 256) threads, each running
+ * eight independent chains of iters fused multiply-adds in the given precision
+ * (DGX_FP64 or DGX_FP32) and storing one value to out (device, threads
+ * elements of that precision).  *flops = 16 * iters * threads, the launch's
+ * exact flop count; the caller times the launch (CUDA events on stream) to
+ * obtain the device's measured FMA peak, the denominator of ALU-bound roofline
+ * fractions.  DGX_EINVAL for bad sizes or precision. */
+dgx_status dgx_probe_fma(int32_t precision, int64_t iters, void* out, int64_t threads, double* flops, void* stream);
 
 /* Synchronise with the device and report (then clear) device-side flags:
  * DGX_ENONFINITE if any residual value was NaN/Inf since the last check. */

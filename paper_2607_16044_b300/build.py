@@ -115,6 +115,7 @@ def _write_sources():
     units.append(path)
     units.append(os.path.join(CSRC, "host.cu"))
     units.append(os.path.join(CSRC, "noalloc.cu"))
+    units.append(os.path.join(CSRC, "probe.cu"))
     return units
 
 

@@ -43,6 +43,7 @@ struct dgx_handle {
   dgx::Mesh<double> mesh64{};   // device views passed to the launch table
   dgx::Mesh<float> mesh32{};
   int nsm = 148;          // SMs of the device (persistent grids)
+  int dev = 0;            // device that was current at dgx_create (owns every device table)
   bool pipeline = true;   // persistent TMA-fed kernels where the layout allows
   int contraction = DGX_CONTRACT_CUDA_CORE;  // engine of the forward element kernel
   // second stream and fork / join events of dgx_ark_step_adjoint
@@ -743,6 +744,11 @@ const char* dgx_status_string(dgx_status s) {
   return "unknown status";
 }
 
+// Device of a handle, for the allocation-free entry point in noalloc.cu (not part of the C ABI).
+__attribute__((visibility("hidden"))) int dgx_internal_handle_device(const dgx_handle* h) {
+  return h ? h->dev : -1;
+}
+
 dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   if (!out) return DGX_EINVAL;
   *out = nullptr;
@@ -793,9 +799,10 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   }
   {
     int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
-      h->nsm = nsm;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      h->dev = dev;
+      if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) h->nsm = nsm;
+    }
   }
   if (st == DGX_OK && cudaMalloc((void**)&h->d_flags, sizeof(unsigned)) != cudaSuccess) st = DGX_ENOMEM;
   if (st == DGX_OK && cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) st = DGX_ECUDA;
@@ -1095,9 +1102,7 @@ dgx_status dgx_check(dgx_handle* h) {
   return DGX_OK;
 }
 
-dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream) {
-  if (!h || !U64 || reps < 1) return DGX_EINVAL;
-  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+static dgx_status autotune_impl(dgx_handle* h, const double* U64, int32_t reps, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const size_t state64 = (size_t)h->E * h->nf * h->N * 8;
   const bool adj = h->tab->vjp != nullptr;
@@ -1171,6 +1176,23 @@ dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* st
   dgx_profile_reset(h);
   dgx_profile_enable(h, was_prof);
   return cudaStreamSynchronize(st) == cudaSuccess ? DGX_OK : DGX_ECUDA;
+}
+
+// On any failure the handle keeps the tile variants, pipeline choice and
+// profiler state it had before the call.
+dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream) {
+  if (!h || !U64 || reps < 1) return DGX_EINVAL;
+  if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  int saved[DGX_KERNEL_KINDS];
+  std::copy(h->var, h->var + DGX_KERNEL_KINDS, saved);
+  const bool saved_pipe = h->pipeline, saved_prof = h->prof;
+  const dgx_status s = autotune_impl(h, U64, reps, stream);
+  if (s != DGX_OK) {
+    std::copy(saved, saved + DGX_KERNEL_KINDS, h->var);
+    h->pipeline = saved_pipe;
+    dgx_profile_enable(h, saved_prof);
+  }
+  return s;
 }
 
 dgx_status dgx_set_pipeline(dgx_handle* h, int32_t enable) {

@@ -243,9 +243,9 @@ struct TcOps {
                          cudaStream_t st) {
     using C = TcShape<D, P, TC>;
     using H = Sh<D, P, TC_V>;
-    static bool done = false;
+    static SmemGate done;
     auto k = k_elem_tc<D, P, VISC, CURV, MODE, TC>;
-    allow_smem_once(k, C::SMEM, done);
+    if (const cudaError_t e = allow_smem_once(k, C::SMEM, done)) return e;
     const int blocks = (M.E + H::T - 1) / H::T;
     if (blocks == 0) return cudaSuccess;
     k<<<blocks, H::THREADS, C::SMEM, st>>>(M, U, (const float*)w.Q, (const float*)w.FF, out, sa);

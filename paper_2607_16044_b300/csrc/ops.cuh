@@ -7,6 +7,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 #include "kernels_p.cuh"
 
@@ -21,14 +23,29 @@ struct Work {            // caller-owned scratch, in the handle's precision
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;  // opt-in shared memory per CTA on sm_103a
 
-// Raise a kernel's dynamic shared-memory limit once (first launch); later
-// launches -- including ones inside a stream capture -- skip the call.
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute is per device): the first launch on each device sets it, later
+// launches -- including ones inside a stream capture -- skip the call.  The
+// gate keeps one bit per device ordinal (0..63) and reports the attribute
+// call's error.
+struct SmemGate {
+  std::atomic<unsigned long long> done{0};
+};
+inline int current_device_bit() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  return dev & 63;
+}
 template <typename K>
-inline void allow_smem_once(K kernel, size_t bytes, bool& done) {
-  if (!done) {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    done = true;
+inline cudaError_t allow_smem_once(K kernel, size_t bytes, SmemGate& gate) {
+  const unsigned long long bit = 1ull << current_device_bit();
+  if (gate.done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  if (bytes > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
   }
+  gate.done.fetch_or(bit, std::memory_order_acq_rel);
+  return cudaSuccess;
 }
 
 template <int D, int P, typename S>
@@ -70,9 +87,9 @@ struct Ops {
 
   template <typename Sin, int V>
   static cudaError_t trace_v(const Mesh<S>& M, const Sin* U, S* TU, S* shadow, cudaStream_t st) {
-    static bool done = false;
+    static SmemGate done;
     auto k = k_trace<D, P, S, Sin, V>;
-    allow_smem_once(k, smem_trace<V>(), done);
+    if (const cudaError_t e = allow_smem_once(k, smem_trace<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_trace<V>(), st>>>(M.E, U, TU, shadow, M.tabs);
     return cudaGetLastError();
   }
@@ -86,9 +103,9 @@ struct Ops {
 
   template <bool CURV, int V>
   static cudaError_t br1_v(const Mesh<S>& M, const S* U, const Work& w, cudaStream_t st) {
-    static bool done = false;
+    static SmemGate done;
     auto k = k_br1<D, P, S, CURV, V>;
-    allow_smem_once(k, smem_br1<V>(), done);
+    if (const cudaError_t e = allow_smem_once(k, smem_br1<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, U, (const S*)w.TU, (S*)w.Q, (S*)w.G);
     return cudaGetLastError();
   }
@@ -125,9 +142,9 @@ struct Ops {
   template <int MODE, bool VISC, bool CURV, int V>
   static cudaError_t elem_v(const Mesh<S>& M, const S* U, const Work& w, S* out, const Stage<S>& sa,
                             cudaStream_t st) {
-    static bool done = false;
+    static SmemGate done;
     auto k = k_elem<D, P, S, VISC, CURV, MODE, V>;
-    allow_smem_once(k, smem_elem<V>(), done);
+    if (const cudaError_t e = allow_smem_once(k, smem_elem<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, (const S*)w.FF, out, sa);
     return cudaGetLastError();
   }
@@ -151,14 +168,15 @@ struct Ops {
       return cudaSuccess;
     }
     auto k = k_elem_p<D, P, S, VISC, CURV, MODE, V>;
-    static size_t raised = 48 * 1024;  // dynamic shared memory allowed so far for this kernel
-    if (smem > raised) {
+    static size_t raised[64] = {};  // dynamic shared memory allowed so far for this kernel, per device
+    const int dv = current_device_bit();
+    if (smem > 48 * 1024 && smem > raised[dv]) {
       if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         used = false;
         return cudaSuccess;
       }
-      raised = smem;
+      raised[dv] = smem;
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, h::THREADS, smem) != cudaSuccess || occ < 1) {

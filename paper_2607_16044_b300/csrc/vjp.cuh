@@ -821,15 +821,15 @@ struct VjpOps {
   static cudaError_t elem_v(const Mesh<S>& M, const S* U, const VjpWork& w, const Cot<S>& c, S* Ub,
                             cudaStream_t st) {
     if (c.nu_prev) {
-      static bool done = false;
+      static SmemGate done;
       auto k = k_vjp_elem<D, P, S, VISC, CURV, V, true>;
-      allow_smem_once(k, smem_elem<V>(), done);
+      if (const cudaError_t e = allow_smem_once(k, smem_elem<V>(), done)) return e;
       k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb,
                                                                (const S*)w.TUb, (const S*)w.JB);
     } else {
-      static bool done = false;
+      static SmemGate done;
       auto k = k_vjp_elem<D, P, S, VISC, CURV, V, false>;
-      allow_smem_once(k, smem_elem<V>(), done);
+      if (const cudaError_t e = allow_smem_once(k, smem_elem<V>(), done)) return e;
       k<<<blocks<V>(M.E), H<V>::THREADS, smem_elem<V>(), st>>>(M, U, (const S*)w.Q, c, (S*)w.FFb, Ub, (S*)w.Qb,
                                                                nullptr, nullptr);
     }
@@ -863,9 +863,9 @@ struct VjpOps {
 
   template <bool CURV, int V>
   static cudaError_t br1_v(const Mesh<S>& M, const VjpWork& w, S* Ub, cudaStream_t st) {
-    static bool done = false;
+    static SmemGate done;
     auto k = k_vjp_br1<D, P, S, CURV, V>;
-    allow_smem_once(k, smem_br1<V>(), done);
+    if (const cudaError_t e = allow_smem_once(k, smem_br1<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.FFb,
                                                              (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub);
     return cudaGetLastError();
@@ -885,9 +885,9 @@ struct VjpOps {
 
   template <bool VISC, int V>
   static cudaError_t gather_v(const Mesh<S>& M, const VjpWork& w, S* g, const Cot<S>& c, cudaStream_t st) {
-    static bool done = false;
+    static SmemGate done;
     auto k = k_vjp_gather<D, P, S, VISC, V>;
-    allow_smem_once(k, smem_gather<V>(), done);
+    if (const cudaError_t e = allow_smem_once(k, smem_gather<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_gather<V>(), st>>>(M, (const S*)w.TUb, (const S*)w.JB, g, c);
     return cudaGetLastError();
   }

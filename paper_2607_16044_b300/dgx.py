@@ -45,7 +45,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
-           "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint"]
+           "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma"]
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_profile_reset.argtypes = [vp]
     lib.dgx_kernel_name.argtypes = [i32]
     lib.dgx_kernel_name.restype = ctypes.c_char_p
+    lib.dgx_probe_fma.argtypes = [i32, ctypes.c_int64, vp, ctypes.c_int64, ctypes.POINTER(dbl), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
@@ -107,6 +108,32 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_batch_workspace_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
+
+
+def measure_fma_peak(precision: str, reps: int = 5, iters: Optional[int] = None) -> float:
+    """Measured FMA throughput (TFLOP/s, best of ``reps``) of the current CUDA
+    device in "fp64" or "fp32": dgx_probe_fma launches, each timed with CUDA
+    events on the current stream (the denominator of ALU-bound roofline
+    fractions)."""
+    lib = load_library()
+    prec = FP64 if precision == "fp64" else FP32
+    iters = iters or (4096 if prec == FP64 else 65536)     # launches of ~10 ms
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    threads = nsm * 2048
+    out = torch.empty(threads, dtype=torch.float64 if prec == FP64 else torch.float32, device="cuda")
+    flops = ctypes.c_double()
+    stream = torch.cuda.current_stream()
+    best = 0.0
+    for k in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(lib.dgx_probe_fma(prec, iters, ctypes.c_void_p(out.data_ptr()), threads, ctypes.byref(flops),
+                                 ctypes.c_void_p(stream.cuda_stream)), "dgx_probe_fma")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k:   # the first launch is a warm-up
+            best = max(best, flops.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def _check(code, where):

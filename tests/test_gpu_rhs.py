@@ -136,6 +136,16 @@ def test_channel2d_config_full_size_sampled(prec):
         assert serr < max(TOL[prec], 4.0 * floor), (serr, floor)
 
 
+def test_channel2d_full_size_perturbed_fp32():
+    """256 x 128 wall-stretched channel, p = 4, FP32, on a well-conditioned
+    state (the Poiseuille profile with 10 % seeded perturbations instead of
+    1e-3): sampled elements incl. both walls at the plain FP32 target."""
+    mesh, phys, _ = I.channel2d_workload()
+    U = I.channel_state(mesh, phys, 2, amp=0.1)
+    err, serr = _sampled(mesh, phys, U, "fp32", 48, 1, "channel2d-perturbed-fp32")
+    assert err < TOL["fp32"] and serr < TOL["fp32"], (err, serr)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_tgv_config_full_size_sampled(prec):
     """32^3 Taylor-Green vortex at Ma 0.1 (p_inf = 71): ill-conditioned in the

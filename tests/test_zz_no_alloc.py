@@ -5,8 +5,9 @@ all device memory at start-up, plugin hosts that pass only inputs and
 outputs); dgx_rhs_noalloc serves them from a fixed scratch array inside the
 library.  These tests call it through the C ABI and compare with the
 workspace-based dgx_rhs on two consecutive calls (the scratch keeps the first
-call's contents, which must not leak into the second), and check that a mesh
-too large for the fixed scratch is rejected.  This file is collected last.
+call's contents, which must not leak into the second; the device's free
+memory must not change across the second call), and check that a mesh too
+large for the fixed scratch is rejected.  This file is collected last.
 """
 import ctypes
 
@@ -38,12 +39,23 @@ def test_noalloc_matches_rhs_on_two_calls(prec):
     phys = I.Physics(gamma=1.4, Re=300.0, Pr=0.72, Ma=0.3, viscous=True)
     s = _solver(mesh, phys, prec)
     dt = torch.float64 if prec == "fp64" else torch.float32
-    for seed in (1, 2):                      # two calls in a row, different states
-        U = torch.as_tensor(I.random_state(mesh, seed)).to("cuda", dt).contiguous()
-        ref = s.rhs(U).double().cpu().numpy()
-        out = torch.full_like(U, float("nan"))
-        assert _noalloc(s, U, out) == 0
-        s.check()
+    # every tensor the test needs exists before the first call, so nothing
+    # else allocates device memory between the two calls
+    Us = [torch.as_tensor(I.random_state(mesh, seed)).to("cuda", dt).contiguous() for seed in (1, 2)]
+    refs = [s.rhs(U).double().cpu().numpy() for U in Us]
+    outs = [torch.full_like(U, float("nan")) for U in Us]
+    torch.cuda.synchronize()
+    # first call: the warm-up that creates the fixed array under lazy loading
+    assert _noalloc(s, Us[0], outs[0]) == 0
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    # second call in a row, on another state: must allocate nothing
+    assert _noalloc(s, Us[1], outs[1]) == 0
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)
+    s.check()
+    for out, ref in zip(outs, refs):
         got = out.double().cpu().numpy()
         assert rel_err(got, ref) < TOL[prec]
 
