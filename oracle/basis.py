@@ -68,6 +68,14 @@ def lagrange_eval(x, xe):
     return L
 
 
+def lagrange_derivative_at(x, e):
+    """l_j'(e) for every j at a point e that is not a node:
+    l_j'(e) = l_j(e) sum_{k != j} 1 / (e - x_k)."""
+    n = len(x)
+    L = lagrange_eval(x, e)[0]
+    return np.array([L[j] * sum(1.0 / (e - x[k]) for k in range(n) if k != j) for j in range(n)])
+
+
 def derivative_matrix(x):
     """D[i, j] = l_j'(x_i)."""
     n = len(x)
@@ -91,3 +99,5 @@ class Basis1D:
         self.D = derivative_matrix(self.x)
         self.lm = lagrange_eval(self.x, -1.0)[0]   # l_j(-1)
         self.lp = lagrange_eval(self.x, +1.0)[0]   # l_j(+1)
+        self.dlm = lagrange_derivative_at(self.x, -1.0)   # l_j'(-1)
+        self.dlp = lagrange_derivative_at(self.x, +1.0)   # l_j'(+1)

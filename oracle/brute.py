@@ -243,3 +243,163 @@ class BruteDG:
     def Ainv_T(Ainv):
         # d l / d x_c = sum_a d l / d xi_a * d xi_a / d x_c = gref @ Ainv
         return Ainv
+
+
+class BruteSIPG(BruteDG):
+    """Dense brute-force evaluation of the DG-IP weak form of Sec. 3.3 (the
+    Vijayasundaram flux + symmetric interior penalty, with the farfield and
+    adiabatic-wall forms of App. B.1 and the explicit side of the interface
+    form of Sec. 4.1.1) on tiny affine meshes; pins ``sipg``.
+
+    Independent of ``sipg``'s discretisation code: its own Lagrange
+    polynomials, the gradient of each element's polynomial evaluated from
+    them at any point (no traces of metric terms), the characteristic length
+    from the affine map (|T| = |det A| 2^d, |dT| = sum |Sn| 2^(d-1)), the
+    neighbour's value found by locating the physical point, every face term
+    -- including the adjoint-consistency term int grad l_q . H ds -- integrated
+    against the basis (and its gradient) with a higher-order rule, and the
+    dense mass matrix.  Pointwise quantities are collocated at the Gauss
+    nodes (volume) and the face Gauss points (faces) and interpolated, as in
+    the collocated scheme; shared with ``sipg``: only the pointwise physics.
+    """
+
+    def residual_sipg(self, U, alpha=1.0, U_inf=None, explicit=None, U_im=None):
+        d, n, N, nf = self.d, self.n, self.N, self.nf
+        mesh, gas = self.mesh, self.gas
+        E = mesh.n_elem
+        U = np.asarray(U, dtype=np.float64)
+        if explicit is not None:
+            U = np.where(np.asarray(explicit, dtype=bool)[:, None, None], U, np.asarray(U_im, dtype=np.float64))
+        quad = list(itertools.product(range(len(self.xq)), repeat=d))
+        qpts = [(np.array([self.xq[i[a]] for a in range(d)]), np.prod([self.wq[i[a]] for a in range(d)]))
+                for i in quad]
+        tab = [self.basis_at(x) for x, _ in qpts]
+        Ainvs = [np.linalg.inv(self.A[e]) for e in range(E)]
+        Js = [abs(np.linalg.det(self.A[e])) for e in range(E)]
+        mass = [sum(w * np.outer(phi, phi) for (x, w), (phi, _) in zip(qpts, tab)) * Js[e] for e in range(E)]
+        nodes_ref = [np.array([self.L.x[m[a]] for a in range(d)]) for m in self.multi]
+
+        def value(e, xi):
+            phi, _ = self.basis_at(xi)
+            return U[e] @ phi
+
+        def grad(e, xi):                          # [nf][c] gradient of the element's polynomial
+            _, gref = self.basis_at(xi)
+            return U[e] @ (gref @ Ainvs[e])
+
+        # characteristic lengths from the affine maps
+        inv_l = np.zeros(E)
+        for e in range(E):
+            area = sum(np.linalg.norm(self.normal(e, a, s)) * 2.0 ** (d - 1) for a in range(d) for s in (0, 1))
+            inv_l[e] = area / (Js[e] * 2.0 ** d)
+        ex = np.ones(E, dtype=bool) if explicit is None else np.asarray(explicit, dtype=bool)
+
+        def T(x):
+            return _t(np.asarray(x)[None])
+
+        def visc(Uf, G, Sn=None, wall=False):
+            if wall:
+                return ph.adiabatic_viscous_flux(T(Uf), T(G), T(Sn), gas, d).numpy()[0]
+            return ph.viscous_flux(T(Uf), T(G), gas, d).numpy()[0]      # [i][nf]
+
+        def outer(delta, Sn):
+            return np.outer(Sn, delta)                                    # [i][nf]
+
+        f_out = np.zeros((E, nf, N))
+        for e in range(E):
+            if not ex[e]:
+                continue
+            B = np.zeros((nf, N))
+            # volume: - int (F^c - F^nu(U, grad U)) : grad l_q, nodal fluxes interpolated
+            Fn = np.zeros((N, d, nf))
+            for r in range(N):
+                Ur = U[e][:, r]
+                Fr = ph.convective_flux(T(Ur), gas, d).numpy()[0]
+                if gas.viscous:
+                    Fr = Fr - visc(Ur, grad(e, nodes_ref[r]).T)
+                Fn[r] = Fr
+            for (x, w), (phi, gref) in zip(qpts, tab):
+                gx = gref @ Ainvs[e]
+                Fx = np.einsum("r,rif->if", phi, Fn)
+                B -= w * Js[e] * np.einsum("if,qi->fq", Fx, gx)
+            for a in range(d):
+                for side in (0, 1):
+                    fid = 2 * a + side
+                    pts, rest = self.face_points(a, side)
+                    Sn = self.normal(e, a, side)
+                    nbe = mesh.neighbor[e, fid]
+                    vals = np.zeros((len(pts), nf))
+                    hv = np.zeros((len(pts), d, nf))
+                    for m, (xi, _) in enumerate(pts):
+                        Um = value(e, xi)
+                        Gm = grad(e, xi).T                                   # [c][nf]
+                        if nbe >= 0:
+                            nb, xin, Up = neighbour_value(self, e, a, side, xi, U, value)
+                            Gp = grad(nb, xin).T
+                            an = int(np.argmax(np.abs(xin)))
+                            Snb = self.normal(nb, an, 1 if xin[an] > 0 else 0)
+                            Sb = 0.5 * (Sn - Snb)
+                            sJ = np.linalg.norm(Sb)
+                            tau = alpha * (mesh.p + 1) ** 2 * max(inv_l[e], inv_l[nb])
+                            F = ph.vijayasundaram_flux(T(Um), T(Up), T(Sb), gas, d).numpy()[0]
+                            dl = Um - Up
+                            KL, KR = visc(Um, outer(dl, Sb)), visc(Up, outer(dl, Sb))
+                            F = F - 0.5 * (visc(Um, Gm).T @ Sn - visc(Up, Gp).T @ Snb) \
+                                + tau / sJ * 0.5 * (KL + KR).T @ Sb
+                            hv[m] = 0.5 * (KL + KR) if not ex[nb] else 0.5 * KL
+                        elif nbe == -1:                                       # adiabatic wall
+                            tau = alpha * (mesh.p + 1) ** 2 * inv_l[e]
+                            sJ = np.linalg.norm(Sn)
+                            Ur = ph.mirror_state(T(Um), T(Sn), d).numpy()[0]
+                            Uw = ph.wall_state(T(Um), d).numpy()[0]
+                            Kw = visc(Um, outer(Um - Uw, Sn), Sn, True)
+                            F = ph.vijayasundaram_flux(T(Um), T(Ur), T(Sn), gas, d).numpy()[0] \
+                                - visc(Um, Gm, Sn, True).T @ Sn + tau / sJ * Kw.T @ Sn
+                            hv[m] = Kw
+                        else:                                                 # farfield
+                            tau = alpha * (mesh.p + 1) ** 2 * inv_l[e]
+                            sJ = np.linalg.norm(Sn)
+                            Ui = np.asarray(U_inf, dtype=np.float64)
+                            UG = ph.farfield_boundary_state(T(Um), T(Ui), T(Sn), gas, d).numpy()[0]
+                            Ki = visc(Ui, outer(Um - Ui, Sn))
+                            F = ph.normal_convective_flux(T(UG), T(Sn), gas, d).numpy()[0] \
+                                - visc(Ui, Gm).T @ Sn + tau / sJ * Ki.T @ Sn
+                            hv[m] = Ki
+                        vals[m] = F
+                    B += self._face_integral(e, a, side, pts, rest, vals, None)
+                    if gas.viscous:
+                        B -= self._face_integral(e, a, side, pts, rest, None, hv, Ainvs[e])
+            f_out[e] = -np.linalg.solve(mass[e], B.T).T
+        return f_out
+
+    def _face_integral(self, e, a, side, pts, rest, vals, hv, Ainv=None):
+        """int_F (face interpolant of vals) l_q ds, or int_F grad l_q . (face
+        interpolant of hv) ds, with the higher rule on the reference face (the
+        area factor is inside vals / hv, which carry the area normal)."""
+        d, N = self.d, self.N
+        nf = self.nf
+        out = np.zeros((nf, N))
+        for iq in itertools.product(range(len(self.xq)), repeat=d - 1):
+            xi = np.zeros(d)
+            xi[a] = -1.0 if side == 0 else 1.0
+            wt = 1.0
+            for k, b in enumerate(rest):
+                xi[b] = self.xq[iq[k]]
+                wt *= self.wq[iq[k]]
+            face_phi = np.array([np.prod([self.L.val(xi[b])[idx[k]] for k, b in enumerate(rest)])
+                                 for (_, idx) in pts])
+            phi, gref = self.basis_at(xi)
+            if vals is not None:
+                out += wt * np.outer(vals.T @ face_phi, phi)
+            else:
+                Hx = np.einsum("m,mcf->cf", face_phi, hv)            # [c][nf]
+                gx = gref @ Ainv                                     # [N][c]
+                out += wt * np.einsum("cf,qc->fq", Hx, gx)
+        return out
+
+
+def neighbour_value(brute, e, a, side, xi, U, value):
+    nb = brute.mesh.neighbor[e, 2 * a + side]
+    x = brute.x0[e] + brute.A[e] @ xi
+    xin = brute.locate(nb, x)
+    return nb, xin, value(nb, xin)

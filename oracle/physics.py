@@ -168,3 +168,111 @@ def adiabatic_wall_viscous_flux(U, Q, Sn, gas, d):
         comps.append(sum(tau[i][j] * Sn[:, i] for i in range(d)))
     comps.append(torch.zeros_like(U[:, 0]))
     return torch.stack(comps, 1)
+
+
+# ---------------------------------------------------------------------------
+# Characteristic splitting of the normal inviscid Jacobian (Sec. 3.2) and the
+# numerical fluxes built on it (Sec. 3.3, App. B.1.1).
+#
+# A_n = A_i n_i = P Lambda P^{-1} with eigenvalues u.n - c|n|, u.n (d-fold),
+# u.n + c|n| for the (area-weighted) normal n.  With r_k, l_k the right and
+# left eigenvectors (l_k r_m = delta_km), P Lambda^{+-} P^{-1} =
+# sum_k lambda_k^{+-} r_k l_k^T.  The d-fold eigenvalue's eigenvectors are
+# combined through their spectral projector I - r_- l_-^T - r_+ l_+^T (the
+# sum of all r_k l_k^T is the identity), so only the two acoustic pairs are
+# written out (unit normal nh = n/|n|, enthalpy H = (rho E + p)/rho):
+#   r_+- = (1, u +- c nh, H +- c u.nh),
+#   l_+- = ((gamma-1)|u|^2/2 -+ c u.nh, -(gamma-1) u +- c nh, gamma-1) / (2 c^2).
+# ---------------------------------------------------------------------------
+
+def posr(x):
+    """max(x, 0), branching on the real part (complex-step differentiable)."""
+    return torch.where(x.real > 0, x, torch.zeros_like(x))
+
+
+def negr(x):
+    """min(x, 0), branching on the real part."""
+    return torch.where(x.real < 0, x, torch.zeros_like(x))
+
+
+def acoustic_eigenvectors(U, Sn, gas, d):
+    """Eigenvalues (lam_minus, lam_0, lam_plus) of A_n for the area normal Sn
+    and the acoustic eigenvector pairs (r_-, l_-), (r_+, l_+) ([k][nf] each)."""
+    rho, u, p, rE = primitives(U, gas, d)
+    g = gas.gamma
+    sJ = torch.sqrt(sum(Sn[:, i] * Sn[:, i] for i in range(d)))
+    nh = Sn / sJ.unsqueeze(1)
+    c = torch.sqrt(g * p / rho)
+    H = (rE + p) / rho
+    un = sum(u[:, i] * nh[:, i] for i in range(d))
+    q2 = sum(u[:, i] * u[:, i] for i in range(d))
+    r, l = {}, {}
+    for s in (-1.0, 1.0):
+        r[s] = torch.stack([torch.ones_like(rho)] + [u[:, i] + s * c * nh[:, i] for i in range(d)]
+                           + [H + s * c * un], 1)
+        l[s] = torch.stack([0.5 * (g - 1.0) * q2 - s * c * un]
+                           + [-(g - 1.0) * u[:, i] + s * c * nh[:, i] for i in range(d)]
+                           + [torch.full_like(rho, g - 1.0)], 1) / (2.0 * c * c).unsqueeze(1)
+    lam = ((un - c) * sJ, un * sJ, (un + c) * sJ)
+    return lam, r, l
+
+
+def split_jacobian(U, Sn, gas, d):
+    """A_n^+ and A_n^- ([k][nf][nf]) at state U for the area normal Sn: the
+    eigen-splitting P Lambda^{+-} P^{-1} of Sec. 3.2 written with spectral
+    projectors (see the block comment above)."""
+    lam, r, l = acoustic_eigenvectors(U, Sn, gas, d)
+    nf = d + 2
+    Pm = r[-1.0].unsqueeze(2) * l[-1.0].unsqueeze(1)
+    Pp = r[1.0].unsqueeze(2) * l[1.0].unsqueeze(1)
+    I = torch.eye(nf, dtype=U.dtype).expand(U.shape[0], nf, nf)
+    P0 = I - Pm - Pp
+    out = []
+    for part in (posr, negr):
+        out.append(part(lam[0])[:, None, None] * Pm + part(lam[1])[:, None, None] * P0
+                   + part(lam[2])[:, None, None] * Pp)
+    return out[0], out[1]
+
+
+def vijayasundaram_flux(Uown, Unb, Sn, gas, d):
+    """F*_n = A_n^+(Ubar) U_own + A_n^-(Ubar) U_nb with Ubar = (U_own + U_nb)/2
+    (Sec. 3.3, Eq. upwinding_Vijayasundaram_sdg), through the area normal Sn
+    (own side outward)."""
+    Ubar = 0.5 * (Uown + Unb)
+    Ap, Am = split_jacobian(Ubar, Sn, gas, d)
+    return (Ap @ Uown.unsqueeze(2)).squeeze(2) + (Am @ Unb.unsqueeze(2)).squeeze(2)
+
+
+def farfield_boundary_state(U, Uinf, Sn, gas, d):
+    """U_Gamma of App. B.1.1: A_n(U) U_Gamma = A_n^+(U) U + A_n^-(U) U_inf, i.e.
+    the characteristic components with lambda_k >= 0 (outgoing, and the
+    undetermined lambda_k = 0) taken from the interior state U, those with
+    lambda_k < 0 from the free stream U_inf; eigen-quantities at U."""
+    lam, r, l = acoustic_eigenvectors(U, Sn, gas, d)
+    nf = d + 2
+    Pm = r[-1.0].unsqueeze(2) * l[-1.0].unsqueeze(1)
+    Pp = r[1.0].unsqueeze(2) * l[1.0].unsqueeze(1)
+    I = torch.eye(nf, dtype=U.dtype).expand(U.shape[0], nf, nf)
+    P0 = I - Pm - Pp
+
+    def out_ind(x):
+        return (x.real >= 0).to(U.dtype)[:, None, None]
+    Pout = out_ind(lam[0]) * Pm + out_ind(lam[1]) * P0 + out_ind(lam[2]) * Pp
+    return Uinf + (Pout @ (U - Uinf).unsqueeze(2)).squeeze(2)
+
+
+def adiabatic_viscous_flux(U, Q, Sn, gas, d):
+    """F^{nu,w}[k][i][field] = K_w(U) grad U (App. B.1.2): the viscous flux with the
+    normal component of the heat flux removed (q.n = 0 for the unit normal of Sn)."""
+    u, gu, ge = velocity_temperature_gradients(U, Q, gas, d)
+    sJ2 = sum(Sn[:, i] * Sn[:, i] for i in range(d))
+    gn = sum(ge[:, i] * Sn[:, i] for i in range(d)) / sJ2
+    ge = ge - gn.unsqueeze(1) * Sn
+    tau = stress(gu, gas, d)
+    F = []
+    for i in range(d):
+        comps = [torch.zeros_like(tau[i][0])]
+        comps += [tau[i][j] for j in range(d)]
+        comps.append(sum(tau[i][j] * u[:, j] for j in range(d)) + gas.k_over_cv * ge[:, i])
+        F.append(torch.stack(comps, 1))
+    return torch.stack(F, 1)
