@@ -26,7 +26,8 @@
  *   state is always double).
  * Mesh tables (host arrays, copied): neighbor[E][2d] = element across local face
  *   f (faces 2a: xi_a = -1, 2a+1: xi_a = +1) or -(1+tag) on a boundary
- *   (tag 0 = adiabatic no-slip wall); nbr_face[E][2d] = the neighbour's local
+ *   (tag 0 = adiabatic no-slip wall, tag 1 = farfield (DG-IP scheme only));
+ *   nbr_face[E][2d] = the neighbour's local
  *   face; orient[E][2d] maps the own face point (s, t) -- the two remaining
  *   local indices in increasing axis order, index s + n t -- to the
  *   neighbour's (u, v): bit 2 swaps s and t first, bit 0 reverses u, bit 1
@@ -71,19 +72,38 @@ typedef enum {
   DGX_OP_ARK_STEP_ADJOINT = 4 /* dgx_ark_step_adjoint */
 } dgx_op;
 
+/* Spatial scheme: convective numerical flux and viscous discretisation.
+ *   DGX_FLUX_LLF + DGX_VISC_BR1: local Lax-Friedrichs and BR1 (the default);
+ *   DGX_FLUX_VIJAYASUNDARAM + DGX_VISC_SIPG: the paper's DG-IP operator (Sec. 3.3,
+ *     Eq. bilinear_form_interior_sdg): the Vijayasundaram flux
+ *     A_n^+({U}) U^+ + A_n^-({U}) U^- of the Sec. 3.2 eigen-split and the symmetric
+ *     interior penalty (viscous surface term, adjoint-consistency term and penalty
+ *     tau = alpha (k+1)^2 / l, l = |T| / |dT|, the face taking the larger 1/l of its
+ *     two elements) with the element's own (broken) gradient; adiabatic walls by
+ *     App. B.1.2 (K_w: no normal heat flux; the convective flux against the mirror
+ *     state), farfield boundaries (tag 1) by App. B.1.1.  Axis-aligned box meshes. */
+typedef enum { DGX_FLUX_LLF = 0, DGX_FLUX_VIJAYASUNDARAM = 1 } dgx_conv_flux;
+typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
+
 /* Problem statement (Sec. 2): dimension, polynomial degree k = p, element
  * count, viscous (Navier-Stokes, 1) or inviscid (Euler, 0), arithmetic
  * precision and the nondimensional parameters.  With rho_ref = |u_ref| =
  * L_ref = 1 and theta_inf = 1: R = 1/(gamma Ma^2), mu = 1/Re (constant),
  * kappa = c_p mu / Pr, lambda = -2 mu / 3 (Stokes).  Re, Pr are ignored when
- * viscous = 0; Ma only fixes R, which the operator does not depend on. */
+ * viscous = 0; Ma only fixes R, which the operator does not depend on.
+ * conv_flux / visc_flux select the scheme (LLF + BR1 or Vijayasundaram +
+ * SIPG; other pairs give DGX_EUNSUPPORTED; visc_flux is ignored when
+ * viscous = 0); penalty_alpha is the SIPG alpha (0 means the paper's 1). */
 typedef struct {
   int32_t dim;        /* 2 or 3                                  */
   int32_t p;          /* 1 .. 5                                  */
   int32_t n_elem;     /* E >= 1                                  */
-  int32_t viscous;    /* 0 Euler, 1 Navier-Stokes (BR1)          */
+  int32_t viscous;    /* 0 Euler, 1 Navier-Stokes                */
   int32_t precision;  /* dgx_precision                           */
   double gamma, Re, Pr, Ma;
+  int32_t conv_flux;  /* dgx_conv_flux                           */
+  int32_t visc_flux;  /* dgx_visc_flux                           */
+  double penalty_alpha;
 } dgx_problem_desc;
 
 typedef struct dgx_handle dgx_handle;
@@ -205,6 +225,35 @@ dgx_status dgx_rhs_noalloc(dgx_handle* h, const void* U, void* dUdt, void* strea
  * fractions.  DGX_EINVAL for bad sizes or precision. */
 dgx_status dgx_probe_fma(int32_t precision, int64_t iters, void* out, int64_t threads, double* flops, void* stream);
 
+/* Farfield state U_inf (App. B.1.1, Eq. farfield_state) of the DG-IP scheme:
+ * conservative (rho, rho u, .., rho E), nf host doubles, copied.  Required
+ * before a residual on a mesh with farfield faces (else DGX_ESTATE). */
+dgx_status dgx_set_farfield(dgx_handle* h, const double* U_inf);
+
+/* Geometry split of Sec. 4.1 (Eq. union_mesh) for the DG-IP scheme: mask[E]
+ * (host, copied) is 1 for the elements of the explicit region T^ex and 0 for
+ * the implicit region T^im; NULL removes the split.  With a split set,
+ * dgx_rhs_split evaluates the explicit residual R^DG(U^ex, U^im) of Sec. 4.2.1
+ * (Eq. semidiscrete_time_sdg; Algorithm 1 calls it with y_i^ex and y_{i-1}^im):
+ * explicit elements read U_ex, implicit ones U_im (both device [E][nf][N] in
+ * the handle's precision; only the elements of each region are read); faces
+ * between the regions are the DG side of the interface (Sec. 4.1.1, Eq.
+ * interface_bilinearform_explicit): treated like interior faces against the
+ * implicit element's polynomial (state and gradient), with the averaged
+ * diffusion matrix {K} in the adjoint-consistency term, and only the explicit
+ * side receives the flux.  dUdt is f on explicit elements and 0 on implicit
+ * ones.  Workspace: dgx_workspace_bytes(h, DGX_OP_RHS). */
+dgx_status dgx_set_explicit_mask(dgx_handle* h, const int8_t* mask);
+dgx_status dgx_rhs_split(dgx_handle* h, const void* U_ex, const void* U_im, void* dUdt, void* workspace,
+                         void* stream);
+
+/* Manufactured-solution source of Sec. 5.1.1 (the MMS of Gassner et al.,
+ * U_e = (s+4, s+4, s+4, (s+4)^2), s = sin(pi (kx x + ky y) - omega pi t), 2D):
+ * dUdt += S(x, t) = dU_e/dt + div(F^c - F^nu)(U_e) at every node, with the
+ * handle's gamma, mu = 1/Re, Pr (mu = 0 for Euler).  Box meshes; dUdt device
+ * [E][nf][N] in the handle's precision. */
+dgx_status dgx_mms_source(dgx_handle* h, double t, double kx, double ky, double omega, void* dUdt, void* stream);
+
 /* Synchronise with the device and report (then clear) device-side flags:
  * DGX_ENONFINITE if any residual value was NaN/Inf since the last check. */
 dgx_status dgx_check(dgx_handle* h);
@@ -222,7 +271,13 @@ typedef enum {
   DGX_K_VJP_FACE = 6,    /* adjoint of the face fluxes                          */
   DGX_K_VJP_BR1 = 7,     /* adjoint of the BR1 gradient and viscous face fluxes */
   DGX_K_VJP_GATHER = 8,  /* adjoint of the traces (gather into the element)     */
-  DGX_KERNEL_KINDS = 9
+  DGX_K_DGIP_TRACE = 9,  /* DG-IP: traces and own-face viscous normal fluxes     */
+  DGX_K_DGIP_FACE = 10,  /* DG-IP: numerical flux and adjoint-term vectors       */
+  DGX_K_DGIP_ELEM = 11,  /* DG-IP: volume + lift + adjoint term + inverse mass   */
+  DGX_K_DGIP_VJP_ELEM = 12,   /* DG-IP adjoint: element part and face cotangents */
+  DGX_K_DGIP_VJP_FACE = 13,   /* DG-IP adjoint: face function (dual numbers)     */
+  DGX_K_DGIP_VJP_GATHER = 14, /* DG-IP adjoint: traces and face gradients        */
+  DGX_KERNEL_KINDS = 15
 } dgx_kernel_kind;
 
 /* Per-kernel device timing (tracing).  While enabled, every kernel the

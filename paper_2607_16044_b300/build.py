@@ -22,6 +22,7 @@ UNIT = """// generated by build.py: instantiation of the (D={D}, S={S}, P={P}) l
 #include "dispatch.h"
 {VJP_INCLUDE}
 {TC_INCLUDE}
+#include "dgip.cuh"
 namespace dgx {{
 namespace {{
 using Sc = {S};
@@ -62,7 +63,7 @@ struct R {{
 }}  // namespace
 const Table* table_d{D}_{T}_p{P}() {{
   static const Table t = {{&R::trace, &R::tr64, &R::br1, &R::face, &R::elem, &R::elem_stage, &R::elem_pipe,
-                          {TC_PTR}, &R::smem, {VJP_PTR}}};
+                          {TC_PTR}, &R::smem, {VJP_PTR}, dgip_table<{D}, {P}, Sc>()}};
   return &t;
 }}
 }}  // namespace dgx

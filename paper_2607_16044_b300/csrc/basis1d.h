@@ -19,12 +19,16 @@ constexpr int MAXN = 6;  // p <= 5
 
 struct Basis1 {
   int n;
-  double x[MAXN], w[MAXN], D[MAXN][MAXN], lm[MAXN], lp[MAXN];
+  double x[MAXN], w[MAXN], D[MAXN][MAXN], lm[MAXN], lp[MAXN], dlm[MAXN], dlp[MAXN];
 };
 
+// dlm / dlp: l_j'(-1), l_j'(+1); dLm / dLp: the same divided by w_j (the
+// normal derivative of a test function at a face, as the interior-penalty
+// adjoint-consistency term lifts it).
 template <typename S>
 struct Tab1 {
-  S D[MAXN][MAXN], Dh[MAXN][MAXN], lm[MAXN], lp[MAXN], Lm[MAXN], Lp[MAXN];
+  S D[MAXN][MAXN], Dh[MAXN][MAXN], lm[MAXN], lp[MAXN], Lm[MAXN], Lp[MAXN], dlm[MAXN], dlp[MAXN], dLm[MAXN],
+      dLp[MAXN];
 };
 
 // cos(t) for t in [0, pi] by its Taylor series (36 terms: remainder < 1e-30)
@@ -99,6 +103,17 @@ constexpr Basis1 make_basis1(int p) {
         B.lp[j] *= (1.0 - B.x[k]) / (B.x[j] - B.x[k]);
       }
   }
+  // l_j'(e) = l_j(e) sum_{k != j} 1 / (e - x_k) at the ends e = -1, +1 (not nodes)
+  for (int j = 0; j < n; ++j) {
+    double sm = 0.0, sp = 0.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) {
+        sm += 1.0 / (-1.0 - B.x[k]);
+        sp += 1.0 / (1.0 - B.x[k]);
+      }
+    B.dlm[j] = B.lm[j] * sm;
+    B.dlp[j] = B.lp[j] * sp;
+  }
   return B;
 }
 
@@ -117,6 +132,10 @@ constexpr Tab1<S> make_tab1(int p) {
     t.lp[j] = (S)B.lp[j];
     t.Lm[j] = (S)(B.lm[j] / B.w[j]);
     t.Lp[j] = (S)(B.lp[j] / B.w[j]);
+    t.dlm[j] = (S)B.dlm[j];
+    t.dlp[j] = (S)B.dlp[j];
+    t.dLm[j] = (S)(B.dlm[j] / B.w[j]);
+    t.dLp[j] = (S)(B.dlp[j] / B.w[j]);
   }
   return t;
 }

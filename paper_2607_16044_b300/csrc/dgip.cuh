@@ -1,0 +1,1062 @@
+// Kernels of the paper's own explicit operator, DG-IP (sm_103a): the
+// Vijayasundaram convective flux and the symmetric interior-penalty viscous
+// terms of Sec. 3.3 (B_I of Eq. bilinear_form_interior_sdg, penalty
+// tau = alpha (k+1)^2 / l of Eq. penalty_coefficient_ip), the farfield and
+// adiabatic-wall forms of App. B.1 and the DG side of the geometry-split
+// interface of Sec. 4.1.1 (Eq. interface_bilinearform_explicit), on
+// axis-aligned box meshes with the collocated Gauss-node basis.
+//
+// Per residual:
+//   k_dgip_trace  U -> TU, G     face traces of U and each own face's viscous
+//                                normal flux G = F^nu(U_f, grad U_f).n with the
+//                                element's own (broken) gradient at the face
+//   k_dgip_face   TU, G -> FF, HA  one thread per unique face point: the
+//                                numerical flux (written +- to both sides) and
+//                                each side's adjoint-consistency vector
+//                                H = c K(U)(delta (x) n) (all directions)
+//   k_dgip_elem   U, FF, HA -> f volume flux F^c - F^nu(U, grad U) (gradient
+//                                from the element's own lines, never stored),
+//                                weak divergence, lift of FF, the adjoint-
+//                                consistency term (normal part lifted with
+//                                l'(+-1)/w, tangential part folded into the
+//                                volume flux before the divergence), inverse
+//                                mass; optionally the ARK stage update.
+// With unit normals on boxes (r_a = 2/h_a), node q of an element gets
+//   f_q = sum_a r_a [ sum_m Dh[q_a][m] Fa(m) - L(-)[q_a] FF(2a) - L(+)[q_a] FF(2a+1)
+//                     + r_a (dL(-)[q_a] H_a(2a) + dL(+)[q_a] H_a(2a+1)) ],
+//   Fa(r) = (F^c - F^nu)_a(r) + sum_{a0 != a} r_a0 sum_side L(side)[r_a0] H_a(face(a0, side), r),
+// L = l(+-1)/w, dL = l'(+-1)/w; this is the oracle's
+//   (1/(w_q J)) sum_faces sum_f w_f grad l_q(x_f) . H(f)
+// written out for boxes.  The adjoint kernels reverse the three steps; the
+// face step is differentiated exactly with forward-mode dual numbers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dgip_physics.cuh"
+#include "kernels.cuh"
+#include "ops.cuh"
+
+namespace dgx {
+
+template <typename S>
+struct Dgip {
+  const S* il;          // [E] 1/l = |dT| / |T| of every element (boxes: 2 sum_a 1/h_a)
+  S tk2;                // alpha (k+1)^2
+  const int8_t* mask;   // [E] 1 = explicit element; nullptr: every element explicit
+  const S* Uim;         // states of the implicit elements ([E][nf][N] layout) or nullptr
+  S Uinf[5];            // farfield state (conservative)
+};
+
+template <int D, int P>
+using HD = Sh<D, P, 1>;  // one CTA of ~256 threads per tile of T elements
+
+template <typename S>
+__device__ __forceinline__ bool dgip_explicit(const Dgip<S>& dp, int e) {
+  return !dp.mask || dp.mask[e] != 0;
+}
+
+// stride of tangential direction c inside the face-point index of faces normal to a0
+template <int D, int P>
+__device__ __forceinline__ int tan_stride(int c, int a0) {
+  return c < a0 ? HD<D, P>::pw(c) : HD<D, P>::pw(c - 1);
+}
+
+// Physical (broken) gradient of an element's polynomial at one of its own face
+// points: the normal derivative from the line through the point, tangential
+// ones from the face's traced values (boxes: scaled by 2/h).
+template <int D, int P, typename S>
+__device__ __forceinline__ void face_gradient(const S* us, const S* tu, const S* rh, int face, int fp,
+                                              S (&Q)[D][D + 2]) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  const int a0 = face >> 1, side = face & 1;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const S r = rh[c];
+    if (c == a0) {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S s = 0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) s += (side ? tb.dlp[j] : tb.dlm[j]) * us[f * N + H::node(j, fp, a0)];
+        Q[c][f] = r * s;
+      }
+    } else {
+      const int st = tan_stride<D, P>(c, a0);
+      const int ic = (fp / st) % n;
+      const int base = fp - ic * st;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += tb.D[ic][m] * tu[f * nfp + base + m * st];
+        Q[c][f] = r * s;
+      }
+    }
+  }
+}
+
+template <int D, typename S>
+__device__ __forceinline__ void unit_normal(int face, S (&nv)[D]) {
+#pragma unroll
+  for (int c = 0; c < D; ++c) nv[c] = (c == (face >> 1)) ? ((face & 1) ? S(1) : S(-1)) : S(0);
+}
+
+template <typename S>
+__device__ __forceinline__ Gas<S> gas_no_heat(const Gas<S>& g) {
+  Gas<S> w = g;
+  w.kcv = S(0);
+  return w;
+}
+
+// ---------------------------------------------------------------------------
+// k_dgip_trace: TU = traces of U; G = each own face's viscous normal flux
+// (interior: F^nu(U_f, grad U_f).n; wall: the same with kappa = 0 (q.n = 0);
+// farfield: F^nu(U_inf, grad U_f).n).
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
+                                                                  S* __restrict__ TU, S* __restrict__ G) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
+                FACE = H::FACE;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* us = reinterpret_cast<S*>(smem_raw);  // [T][nf][N]
+  S* tu = us + T * STATE;                  // [T][NF][nf][nfp]
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  const int tid = threadIdx.x;
+  {
+    const int t = tid / N, q = tid % N;
+    if (t < nel) {
+      const int e = e0 + t;
+      const S* src = (dgip_explicit(dp, e) ? U : dp.Uim) + (size_t)e * STATE + q;
+      S v[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) v[f] = src[f * N];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) us[t * STATE + f * N + q] = v[f];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+      int t, f, line;
+      line_item<nf, nfp>(i, t, f, line);
+      const S* v = us + t * STATE + f * N;
+      S sm = 0, sp = 0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        const S x = v[H::node(m, line, a)];
+        sm += tb.lm[m] * x;
+        sp += tb.lp[m] * x;
+      }
+      const int om = (t * NF + 2 * a) * nf * nfp + f * nfp + line, op = om + nf * nfp;
+      tu[om] = sm;
+      tu[op] = sp;
+      TU[(size_t)e0 * FACE + om] = sm;
+      TU[(size_t)e0 * FACE + op] = sp;
+    }
+  }
+  if (!VISC) return;
+  __syncthreads();
+  const Gas<S> gw = gas_no_heat(M.gas);
+  for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
+    const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
+    const int e = e0 + t;
+    const S* tf = tu + (t * NF + face) * nf * nfp;
+    S Uf[nf], Q[D][nf], nv[D], Gv[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) Uf[f] = tf[f * nfp + fp];
+    face_gradient<D, P, S>(us + t * STATE, tf, M.geo.rh + (size_t)e * D, face, fp, Q);
+    unit_normal<D, S>(face, nv);
+    const int nbk = M.nb[e * NF + face];
+    if (nbk >= 0) {
+      visc_flux_normal<D, S>(Uf, Q, nv, M.gas, Gv);
+    } else if (nbk == -1) {
+      visc_flux_normal<D, S>(Uf, Q, nv, gw, Gv);
+    } else {
+      S Ui[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Ui[f] = dp.Uinf[f];
+      visc_flux_normal<D, S>(Ui, Q, nv, M.gas, Gv);
+    }
+    S* gd = G + ((size_t)e * NF + face) * nf * nfp + fp;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) gd[f * nfp] = Gv[f];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_dgip_face: one thread per unique face point (unit normals on boxes).
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const S* __restrict__ TU,
+                                                   const S* __restrict__ G, S* __restrict__ FF, S* __restrict__ HA) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= M.nFaces * nfp) return;
+  const int F = gid / nfp, fp = gid % nfp;
+  const int4 rec = M.faces[F];
+  const int em = rec.x, ep = rec.y;
+  const int fm = rec.z & 0xff, fo = (rec.z >> 8) & 0xff, code = (rec.z >> 16) & 0xff;
+  const bool exm = dgip_explicit(dp, em);
+  const bool exp_ = ep >= 0 && dgip_explicit(dp, ep);
+  if (!exm && !exp_) return;
+  S nv[D];
+  unit_normal<D, S>(fm, nv);
+  S UL[nf], UR[nf], Fv[nf], HL[D][nf], HR[D][nf];
+  const S* tl = TU + ((size_t)em * NF + fm) * nf * nfp + fp;
+#pragma unroll
+  for (int f = 0; f < nf; ++f) UL[f] = tl[f * nfp];
+  const Gas<S> gw = gas_no_heat(M.gas);
+  int fpn = 0;
+  if (ep >= 0) {
+    fpn = orient_map<D, n>(code, fp);
+    const S* tr = TU + ((size_t)ep * NF + fo) * nf * nfp + fpn;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) UR[f] = tr[f * nfp];
+    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]);
+    dgip_face_fn<D, S, S, VISC, DGIP_INTERIOR>(UL, UR, nv, M.gas, gw, tau, exm && !exp_, exp_ && !exm, Fv, HL, HR);
+    if (VISC) {
+      const S* gl = G + ((size_t)em * NF + fm) * nf * nfp + fp;
+      const S* gr = G + ((size_t)ep * NF + fo) * nf * nfp + fpn;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fv[f] -= S(0.5) * (gl[f * nfp] - gr[f * nfp]);
+    }
+  } else {
+    const S tau = dp.tk2 * dp.il[em];
+    if (ep == -1) {
+      dgip_face_fn<D, S, S, VISC, DGIP_WALL>(UL, UL, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
+    } else {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) UR[f] = dp.Uinf[f];
+      dgip_face_fn<D, S, S, VISC, DGIP_FARFIELD>(UL, UR, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
+    }
+    if (VISC) {
+      const S* gl = G + ((size_t)em * NF + fm) * nf * nfp + fp;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fv[f] -= gl[f * nfp];
+    }
+  }
+  if (exm) {
+    S* ol = FF + ((size_t)em * NF + fm) * nf * nfp + fp;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) ol[f * nfp] = Fv[f];
+    if (VISC) {
+      S* hl = HA + ((size_t)em * NF + fm) * D * nf * nfp + fp;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) hl[(c * nf + f) * nfp] = HL[c][f];
+    }
+  }
+  if (exp_) {
+    S* orr = FF + ((size_t)ep * NF + fo) * nf * nfp + fpn;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) orr[f * nfp] = -Fv[f];
+    if (VISC) {
+      S* hr = HA + ((size_t)ep * NF + fo) * D * nf * nfp + fpn;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) hr[(c * nf + f) * nfp] = HR[c][f];
+    }
+  }
+}
+
+template <int D, int P, typename S, bool VISC>
+constexpr size_t smem_dgip_elem() {
+  using H = HD<D, P>;
+  return r16(sizeof(S) * (H::T * H::STATE + (VISC ? 2 : 1) * H::T * D * H::STATE + H::T * H::FACE +
+                          (VISC ? H::T * D * H::FACE : 0)));
+}
+
+// ---------------------------------------------------------------------------
+// k_dgip_elem: residual of every explicit element (0 on implicit ones).
+// MODE 0 writes f; MODE 1 performs the ARK stage update (Sec. 4.2).
+// ---------------------------------------------------------------------------
+template <int D, int P, typename S, bool VISC, int MODE>
+__global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
+                                                                 const S* __restrict__ FF, const S* __restrict__ HA,
+                                                                 S* __restrict__ out, Stage<S> st) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
+                FACE = H::FACE;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* us = reinterpret_cast<S*>(smem_raw);        // [T][nf][N]
+  S* fs = us + T * STATE;                        // [T][D][nf][N]  flux, then divergence lines
+  S* gs = fs + T * D * STATE;                    // [T][D][nf][N]  gradient (viscous)
+  S* ffs = gs + (VISC ? T * D * STATE : 0);      // [T][NF][nf][nfp]
+  S* has = ffs + T * FACE;                       // [T][NF][D][nf][nfp] (viscous)
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  const int tid = threadIdx.x;
+  const int t = tid / N, q = tid % N;
+  const bool active = t < nel;
+  const int e = e0 + t;
+  const bool expl = active && dgip_explicit(dp, e);
+  for (int i = tid; i < nel * FACE; i += blockDim.x) {
+    const bool x = dgip_explicit(dp, e0 + i / FACE);
+    ffs[i] = x ? FF[(size_t)e0 * FACE + i] : S(0);
+  }
+  if (VISC) {
+    for (int i = tid; i < nel * D * FACE; i += blockDim.x) {
+      const bool x = dgip_explicit(dp, e0 + i / (D * FACE));
+      has[i] = x ? HA[(size_t)e0 * D * FACE + i] : S(0);
+    }
+  }
+  S Uq[nf];
+  if (active) {
+    const S* src = (dgip_explicit(dp, e) ? U : dp.Uim) + (size_t)e * STATE + q;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      Uq[f] = src[f * N];
+      us[t * STATE + f * N + q] = Uq[f];
+    }
+  }
+  S pre[nf];
+  double pre64[nf];
+  if (MODE == 1 && active) {
+    const size_t off = (size_t)e * STATE + q;
+    stage_prefix<nf, S>(
+        st, e, [&](int f) { return st.base[off + f * N]; }, [&](int j, int f) { return st.k[j][off + f * N]; },
+        [&](int f) { return st.Un[off + f * N]; }, pre, pre64);
+  }
+  __syncthreads();
+  if (VISC) {  // broken gradient: one thread per (element, field, line) and direction
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+        int tt, f, line;
+        line_item<nf, nfp>(i, tt, f, line);
+        const S* v = us + tt * STATE + f * N;
+        S x[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+        const S r = M.geo.rh[(e0 + tt) * D + a];
+        S* o = gs + (tt * D + a) * STATE + f * N;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          S s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += tb.D[k][m] * x[m];
+          o[H::node(k, line, a)] = r * s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (active) {
+    S Fa[D][nf];
+    node_flux<D, S, VISC, false>(
+        M.gas, Uq, [&](int c, int f) { return gs[(t * D + c) * STATE + f * N + q]; },
+        [&](int, int) { return S(0); }, Fa);
+    if (VISC) {  // tangential part of the adjoint-consistency term
+#pragma unroll
+      for (int a0 = 0; a0 < D; ++a0) {
+        const S r0 = M.geo.rh[e * D + a0];
+        const int fp = H::fpoint(q, a0), k0 = H::qa(q, a0);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const S L = r0 * (side ? tb.Lp[k0] : tb.Lm[k0]);
+          const S* hf = has + (t * NF + 2 * a0 + side) * D * nf * nfp + fp;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            if (a == a0) continue;
+#pragma unroll
+            for (int f = 0; f < nf; ++f) Fa[a][f] += L * hf[(a * nf + f) * nfp];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) fs[(t * D + a) * STATE + f * N + q] = Fa[a][f];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+      int tt, f, line;
+      line_item<nf, nfp>(i, tt, f, line);
+      S* v = fs + (tt * D + a) * STATE + f * N;
+      S x[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+      const S ffm = ffs[((tt * NF + 2 * a) * nf + f) * nfp + line];
+      const S ffp = ffs[((tt * NF + 2 * a + 1) * nf + f) * nfp + line];
+      S hm = 0, hp = 0;
+      if (VISC) {
+        hm = has[(((tt * NF + 2 * a) * D + a) * nf + f) * nfp + line];
+        hp = has[(((tt * NF + 2 * a + 1) * D + a) * nf + f) * nfp + line];
+      }
+      const S r = M.geo.rh[(e0 + tt) * D + a];
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        S s = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) s += tb.Dh[k][m] * x[m];
+        S val = s - tb.Lm[k] * ffm - tb.Lp[k] * ffp;
+        if (VISC) val += r * (tb.dLm[k] * hm + tb.dLp[k] * hp);
+        v[H::node(k, line, a)] = r * val;
+      }
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  S res[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    S s = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) s += fs[(t * D + a) * STATE + f * N + q];
+    res[f] = expl ? s : S(0);
+  }
+  if (expl) flag_nonfinite<nf>(res, M.flags);
+  if (MODE == 0) {
+    S* op = out + (size_t)e * STATE + q;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) op[f * N] = res[f];
+    return;
+  }
+  S y[nf];
+  stage_update<nf, S>(st, e, (size_t)e * STATE + q, N, res, pre, pre64, y);
+}
+
+// ===========================================================================
+// Adjoint (vector-Jacobian product g = (df/dU)^T lambda), every element explicit.
+// ===========================================================================
+
+template <int D, int P, typename S, bool VISC>
+constexpr size_t smem_dgip_vjp_elem() {
+  using H = HD<D, P>;
+  return r16(sizeof(S) * (2 * H::T * H::STATE + (VISC ? 3 : 1) * H::T * D * H::STATE));
+}
+
+// k_dgip_vjp_elem: from lambda, the cotangents of the face quantities (FFb, HAb)
+// and the element-local part of g (volume flux and gradient).
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, const S* __restrict__ U,
+                                                                     const S* __restrict__ lam, S* __restrict__ gpart,
+                                                                     S* __restrict__ FFb, S* __restrict__ HAb) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
+                FACE = H::FACE;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* us = reinterpret_cast<S*>(smem_raw);   // [T][nf][N]
+  S* ls = us + T * STATE;                   // [T][nf][N]  lambda, later the cotangent of U
+  S* fb = ls + T * STATE;                   // [T][D][nf][N]  cotangent of the volume flux
+  S* gs = fb + T * D * STATE;               // [T][D][nf][N]  gradient (viscous)
+  S* qb = gs + (VISC ? T * D * STATE : 0);  // [T][D][nf][N]  its cotangent (viscous)
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  const int tid = threadIdx.x;
+  const int t = tid / N, q = tid % N;
+  const bool active = t < nel;
+  const int e = e0 + t;
+  S Uq[nf];
+  if (active) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      Uq[f] = U[(size_t)e * STATE + f * N + q];
+      us[t * STATE + f * N + q] = Uq[f];
+      ls[t * STATE + f * N + q] = lam[(size_t)e * STATE + f * N + q];
+    }
+  }
+  __syncthreads();
+  // transposed divergence / lift / normal adjoint-term lines along each direction
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+      int tt, f, line;
+      line_item<nf, nfp>(i, tt, f, line);
+      const S* v = ls + tt * STATE + f * N;
+      S y[n];
+#pragma unroll
+      for (int k = 0; k < n; ++k) y[k] = v[H::node(k, line, a)];
+      const S r = M.geo.rh[(e0 + tt) * D + a];
+      S* o = fb + (tt * D + a) * STATE + f * N;
+      S sm = 0, sp = 0, dm = 0, dpp = 0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        sm += tb.Lm[k] * y[k];
+        sp += tb.Lp[k] * y[k];
+        dm += tb.dLm[k] * y[k];
+        dpp += tb.dLp[k] * y[k];
+      }
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        S s = 0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) s += tb.Dh[k][m] * y[k];
+        o[H::node(m, line, a)] = r * s;
+      }
+      const size_t fo = ((size_t)(e0 + tt) * NF + 2 * a) * nf * nfp + f * nfp + line;
+      FFb[fo] = -r * sm;
+      FFb[fo + nf * nfp] = -r * sp;
+      if (VISC) {
+        const size_t ho = (((size_t)(e0 + tt) * NF + 2 * a) * D + a) * nf * nfp + f * nfp + line;
+        HAb[ho] = r * r * dm;
+        HAb[ho + D * nf * nfp] = r * r * dpp;
+      }
+    }
+  }
+  if (VISC) {  // forward gradient of the element (for the viscous flux adjoint)
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+        int tt, f, line;
+        line_item<nf, nfp>(i, tt, f, line);
+        const S* v = us + tt * STATE + f * N;
+        S x[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+        const S r = M.geo.rh[(e0 + tt) * D + a];
+        S* o = gs + (tt * D + a) * STATE + f * N;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          S s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += tb.D[k][m] * x[m];
+          o[H::node(k, line, a)] = r * s;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (VISC) {  // tangential adjoint-term cotangents: HAb[a0,side][a] = r_a0 sum_k L(side)[k] Fb_a(line along a0)
+    constexpr int ITEMS = NF * (D - 1) * nf * nfp;
+    for (int i = tid; i < nel * ITEMS; i += blockDim.x) {
+      const int fp = i % nfp;
+      const int f = (i / nfp) % nf;
+      const int ai = (i / (nfp * nf)) % (D - 1);
+      const int face = (i / (nfp * nf * (D - 1))) % NF;
+      const int tt = i / ITEMS;
+      const int a0 = face >> 1, side = face & 1;
+      const int a = ai + (ai >= a0);
+      const S r0 = M.geo.rh[(e0 + tt) * D + a0];
+      const S* v = fb + (tt * D + a) * STATE + f * N;
+      S s = 0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) s += (side ? tb.Lp[k] : tb.Lm[k]) * v[H::node(k, fp, a0)];
+      HAb[((((size_t)(e0 + tt) * NF + face) * D + a) * nf + f) * nfp + fp] = r0 * s;
+    }
+  }
+  // pointwise flux adjoint: F = F^c - F^nu(U, Q)
+  S Ub[nf];
+  if (active) {
+    S Fb[D][nf];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fb[a][f] = fb[(t * D + a) * STATE + f * N + q];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) Ub[f] = S(0);
+    conv_flux_all_vjp<D, S>(Uq, Fb, M.gas, Ub);
+    if (VISC) {
+      S Q[D][nf], Fn[D][nf], Qb[D][nf];
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          Q[c][f] = gs[(t * D + c) * STATE + f * N + q];
+          Fn[c][f] = -Fb[c][f];
+          Qb[c][f] = S(0);
+        }
+      visc_flux_all_vjp<D, S>(Uq, Q, Fn, M.gas, Ub, Qb);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) qb[(t * D + c) * STATE + f * N + q] = Qb[c][f];
+    }
+  }
+  __syncthreads();  // everyone is done with ls (lambda) and the line reads
+  if (active) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) ls[t * STATE + f * N + q] = Ub[f];
+  }
+  if (VISC) {  // gradient adjoint: Ub += r_a D_a^T Qb_a, one direction per pass
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      __syncthreads();
+      for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+        int tt, f, line;
+        line_item<nf, nfp>(i, tt, f, line);
+        const S* v = qb + (tt * D + a) * STATE + f * N;
+        S x[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+        const S r = M.geo.rh[(e0 + tt) * D + a];
+        S* o = ls + tt * STATE + f * N;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+          S s = 0;
+#pragma unroll
+          for (int m = 0; m < n; ++m) s += tb.D[m][k] * x[m];
+          o[H::node(k, line, a)] += r * s;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) gpart[(size_t)e * STATE + f * N + q] = ls[t * STATE + f * N + q];
+  }
+}
+
+// Cotangents of one face point's inputs by forward-mode differentiation of
+// dgip_face_fn: one dual pass per input component.
+template <int D, typename S, bool VISC, int KIND>
+__device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
+                                                 const Gas<S>& g, const Gas<S>& gw, S tau, bool ifL, bool ifR,
+                                                 const S (&Fb)[D + 2], const S (&HLb)[D][D + 2],
+                                                 const S (&HRb)[D][D + 2], S (&ULb)[D + 2], S (&URb)[D + 2]) {
+  constexpr int nf = D + 2;
+  using T = Dual<S, 1>;
+  const Gas<T> gd = gas_as<T, S>(g), gwd = gas_as<T, S>(gw);
+  constexpr int NIN = KIND == DGIP_INTERIOR ? 2 * nf : nf;
+#pragma unroll 1
+  for (int k = 0; k < NIN; ++k) {
+    T L[nf], R[nf], F[nf], HL[D][nf], HR[D][nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      L[f] = T(UL[f]);
+      R[f] = T(UR[f]);
+    }
+    if (k < nf) L[k].d[0] = S(1);
+    else R[k - nf].d[0] = S(1);
+    dgip_face_fn<D, T, S, VISC, KIND>(L, R, nv, gd, gwd, tau, ifL, ifR, F, HL, HR);
+    S s = 0;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) s += F[f].d[0] * Fb[f];
+    if (VISC) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          s += HL[c][f].d[0] * HLb[c][f];
+          if (KIND == DGIP_INTERIOR) s += HR[c][f].d[0] * HRb[c][f];
+        }
+    }
+    if (k < nf) ULb[k] = s;
+    else URb[k - nf] = s;
+  }
+}
+
+// Host twin of dgip_face_fn_vjp (interior face, no interface) for the
+// operation-counting work model.
+template <int D, typename S, bool VISC>
+inline void dgip_face_fn_vjp_host(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D], const Gas<S>& g,
+                                  S tau, const S (&Fb)[D + 2], const S (&HLb)[D][D + 2], const S (&HRb)[D][D + 2],
+                                  S (&ULb)[D + 2], S (&URb)[D + 2]) {
+  constexpr int nf = D + 2;
+  using T = Dual<S, 1>;
+  const Gas<T> gd = gas_as<T, S>(g);
+  for (int k = 0; k < 2 * nf; ++k) {
+    T L[nf], R[nf], F[nf], HL[D][nf], HR[D][nf];
+    for (int f = 0; f < nf; ++f) {
+      L[f] = T(UL[f]);
+      R[f] = T(UR[f]);
+    }
+    if (k < nf) L[k].d[0] = S(1);
+    else R[k - nf].d[0] = S(1);
+    dgip_face_fn<D, T, S, VISC, DGIP_INTERIOR>(L, R, nv, gd, gd, tau, false, false, F, HL, HR);
+    S s = S(0);
+    for (int f = 0; f < nf; ++f) s += F[f].d[0] * Fb[f];
+    if (VISC)
+      for (int c = 0; c < D; ++c)
+        for (int f = 0; f < nf; ++f) s += HL[c][f].d[0] * HLb[c][f] + HR[c][f].d[0] * HRb[c][f];
+    if (k < nf) ULb[k] = s;
+    else URb[k - nf] = s;
+  }
+}
+
+// k_dgip_vjp_face: one thread per unique face point: cotangents of both sides'
+// traces (TUb) and viscous normal fluxes (Gb) from those of FF and HA.
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, const S* __restrict__ TU,
+                                                       const S* __restrict__ FFb, const S* __restrict__ HAb,
+                                                       S* __restrict__ TUb, S* __restrict__ Gb) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= M.nFaces * nfp) return;
+  const int F = gid / nfp, fp = gid % nfp;
+  const int4 rec = M.faces[F];
+  const int em = rec.x, ep = rec.y;
+  const int fm = rec.z & 0xff, fo = (rec.z >> 8) & 0xff, code = (rec.z >> 16) & 0xff;
+  S nv[D];
+  unit_normal<D, S>(fm, nv);
+  const Gas<S> gw = gas_no_heat(M.gas);
+  const size_t ol = ((size_t)em * NF + fm) * nf * nfp + fp;
+  S UL[nf], UR[nf], Fbar[nf], HLb[D][nf], HRb[D][nf], ULb[nf], URb[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    UL[f] = TU[ol + f * nfp];
+    Fbar[f] = FFb[ol + f * nfp];
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      HLb[c][f] = VISC ? HAb[((size_t)em * NF + fm) * D * nf * nfp + (c * nf + f) * nfp + fp] : S(0);
+      HRb[c][f] = S(0);
+    }
+  if (ep >= 0) {
+    const int fpn = orient_map<D, n>(code, fp);
+    const size_t orr = ((size_t)ep * NF + fo) * nf * nfp + fpn;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      UR[f] = TU[orr + f * nfp];
+      Fbar[f] -= FFb[orr + f * nfp];  // FF_R = -F
+    }
+    if (VISC) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) HRb[c][f] = HAb[((size_t)ep * NF + fo) * D * nf * nfp + (c * nf + f) * nfp + fpn];
+    }
+    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]);
+    dgip_face_fn_vjp<D, S, VISC, DGIP_INTERIOR>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      TUb[ol + f * nfp] = ULb[f];
+      TUb[orr + f * nfp] = URb[f];
+      if (VISC) {
+        Gb[ol + f * nfp] = -S(0.5) * Fbar[f];
+        Gb[orr + f * nfp] = S(0.5) * Fbar[f];
+      }
+    }
+  } else {
+    const S tau = dp.tk2 * dp.il[em];
+    if (ep == -1) {
+      dgip_face_fn_vjp<D, S, VISC, DGIP_WALL>(UL, UL, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
+    } else {
+#pragma unroll
+      for (int f = 0; f < nf; ++f) UR[f] = dp.Uinf[f];
+      dgip_face_fn_vjp<D, S, VISC, DGIP_FARFIELD>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb,
+                                                 URb);
+    }
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      TUb[ol + f * nfp] = ULb[f];
+      if (VISC) Gb[ol + f * nfp] = -Fbar[f];
+    }
+  }
+}
+
+template <int D, int P, typename S, bool VISC>
+constexpr size_t smem_dgip_gather() {
+  using H = HD<D, P>;
+  return r16(sizeof(S) * (2 * H::T * H::STATE + 2 * H::T * H::FACE + (VISC ? H::T * D * H::FACE : 0)));
+}
+
+// k_dgip_vjp_gather: g = gpart + the adjoint of the traces and of each own
+// face's viscous normal flux G = F^nu(U_f, grad U_f).n.
+template <int D, int P, typename S, bool VISC>
+__global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
+                                                                       const S* __restrict__ TUb,
+                                                                       const S* __restrict__ Gb,
+                                                                       const S* __restrict__ gpart,
+                                                                       S* __restrict__ g) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
+                FACE = H::FACE;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* us = reinterpret_cast<S*>(smem_raw);   // [T][nf][N]   U
+  S* ub = us + T * STATE;                   // [T][nf][N]   g being assembled
+  S* tu = ub + T * STATE;                   // [T][NF][nf][nfp]  traces of U
+  S* tub = tu + T * FACE;                   // [T][NF][nf][nfp]  trace cotangents
+  S* qfb = tub + T * FACE;                  // [T][NF][D][nf][nfp]  face-gradient cotangents (viscous)
+  const int e0 = blockIdx.x * T;
+  const int nel = min(T, M.E - e0);
+  const int tid = threadIdx.x;
+  {
+    const int t = tid / N, q = tid % N;
+    if (t < nel) {
+      const size_t off = (size_t)(e0 + t) * STATE + q;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        us[t * STATE + f * N + q] = U[off + f * N];
+        ub[t * STATE + f * N + q] = gpart[off + f * N];
+      }
+    }
+  }
+  for (int i = tid; i < nel * FACE; i += blockDim.x) tub[i] = TUb[(size_t)e0 * FACE + i];
+  __syncthreads();
+  if (VISC) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+        int t, f, line;
+        line_item<nf, nfp>(i, t, f, line);
+        const S* v = us + t * STATE + f * N;
+        S sm = 0, sp = 0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const S x = v[H::node(m, line, a)];
+          sm += tb.lm[m] * x;
+          sp += tb.lp[m] * x;
+        }
+        tu[(t * NF + 2 * a) * nf * nfp + f * nfp + line] = sm;
+        tu[(t * NF + 2 * a + 1) * nf * nfp + f * nfp + line] = sp;
+      }
+    }
+    __syncthreads();
+    const Gas<S> gw = gas_no_heat(M.gas);
+    // adjoint of G at every own face point: its U_f part goes to the trace
+    // cotangent (own entry), its gradient part to qfb
+    for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
+      const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
+      const int e = e0 + t;
+      const S* tf = tu + (t * NF + face) * nf * nfp;
+      S Uf[nf], Q[D][nf], nv[D], Gbar[nf], Ufb[nf], Qb[D][nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        Uf[f] = tf[f * nfp + fp];
+        Gbar[f] = Gb[((size_t)e * NF + face) * nf * nfp + f * nfp + fp];
+        Ufb[f] = S(0);
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) Qb[c][f] = S(0);
+      face_gradient<D, P, S>(us + t * STATE, tf, M.geo.rh + (size_t)e * D, face, fp, Q);
+      unit_normal<D, S>(face, nv);
+      const int nbk = M.nb[e * NF + face];
+      if (nbk >= 0) {
+        visc_flux_normal_vjp<D, S>(Uf, Q, nv, Gbar, M.gas, Ufb, Qb);
+      } else if (nbk == -1) {
+        visc_flux_normal_vjp<D, S>(Uf, Q, nv, Gbar, gw, Ufb, Qb);
+      } else {
+        S Ui[nf], Uib[nf];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          Ui[f] = dp.Uinf[f];
+          Uib[f] = S(0);
+        }
+        visc_flux_normal_vjp<D, S>(Ui, Q, nv, Gbar, M.gas, Uib, Qb);
+      }
+      S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) tb_[f * nfp] += Ufb[f];
+      S* qo = qfb + (t * NF + face) * D * nf * nfp + fp;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) qo[(c * nf + f) * nfp] = Qb[c][f];
+    }
+    __syncthreads();
+    // tangential face derivatives, transposed (a gather along each tangential line)
+    for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
+      const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
+      const int a0 = face >> 1;
+      const S* qo = qfb + (t * NF + face) * D * nf * nfp;
+      S acc[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) acc[f] = S(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (c == a0) continue;
+        const S r = M.geo.rh[(e0 + t) * D + c];
+        const int st = tan_stride<D, P>(c, a0);
+        const int ic = (fp / st) % n;
+        const int base = fp - ic * st;
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          S s = 0;
+#pragma unroll
+          for (int j = 0; j < n; ++j) s += tb.D[j][ic] * qo[(c * nf + f) * nfp + base + j * st];
+          acc[f] += r * s;
+        }
+      }
+      // qfb is only read in this pass and each thread writes only its own tub entry
+      S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) tb_[f * nfp] += acc[f];
+    }
+  }
+  __syncthreads();
+  // transposed traces (and the normal face-gradient part), one direction per pass
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
+      int t, f, line;
+      line_item<nf, nfp>(i, t, f, line);
+      const S bm = tub[(t * NF + 2 * a) * nf * nfp + f * nfp + line];
+      const S bp = tub[(t * NF + 2 * a + 1) * nf * nfp + f * nfp + line];
+      S qm = 0, qp = 0;
+      if (VISC) {
+        const S r = M.geo.rh[(e0 + t) * D + a];
+        qm = r * qfb[((t * NF + 2 * a) * D + a) * nf * nfp + f * nfp + line];
+        qp = r * qfb[((t * NF + 2 * a + 1) * D + a) * nf * nfp + f * nfp + line];
+      }
+      S* o = ub + t * STATE + f * N;
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        S v = tb.lm[j] * bm + tb.lp[j] * bp;
+        if (VISC) v += tb.dlm[j] * qm + tb.dlp[j] * qp;
+        o[H::node(j, line, a)] += v;
+      }
+    }
+    __syncthreads();
+  }
+  {
+    const int t = tid / N, q = tid % N;
+    if (t < nel) {
+      const size_t off = (size_t)(e0 + t) * STATE + q;
+#pragma unroll
+      for (int f = 0; f < nf; ++f) g[off + f * N] = ub[t * STATE + f * N + q];
+    }
+  }
+}
+
+}  // namespace dgx
+
+namespace dgx {
+
+// ---------------------------------------------------------------------------
+// Launch layer of the DG-IP kernels for one (D, P, S).
+// ---------------------------------------------------------------------------
+struct DgipWork {       // caller-owned scratch, in the handle's precision
+  void* TU;             // [E][2D][nf][nfp]  traces of U
+  void* G;              // [E][2D][nf][nfp]  own-face viscous normal fluxes
+  void* FF;             // [E][2D][nf][nfp]  numerical flux      (VJP: its cotangent)
+  void* HA;             // [E][2D][D][nf][nfp] adjoint-term vectors (VJP: their cotangents)
+  void* TUb;            // VJP: trace cotangents
+  void* Gb;             // VJP: cotangents of G
+  void* gpart;          // VJP: element-local part of g [E][nf][N]
+};
+
+template <int D, int P, typename S>
+struct DgipOps {
+  using H = HD<D, P>;
+  static int blocks(int E) { return (E + H::T - 1) / H::T; }
+  static size_t smem_trace() { return r16(sizeof(S) * (H::T * H::STATE + H::T * H::FACE)); }
+
+  template <bool VISC>
+  static cudaError_t trace_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, cudaStream_t st) {
+    static SmemGate done;
+    auto k = k_dgip_trace<D, P, S, VISC>;
+    if (const cudaError_t e = allow_smem_once(k, smem_trace(), done)) return e;
+    k<<<blocks(M.E), H::THREADS, smem_trace(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G);
+    return cudaGetLastError();
+  }
+  static cudaError_t trace(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w,
+                           cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    const Dgip<S>& p = *(const Dgip<S>*)dp;
+    return visc ? trace_v<true>(m, p, (const S*)U, w, st) : trace_v<false>(m, p, (const S*)U, w, st);
+  }
+  static cudaError_t face(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    const Dgip<S>& p = *(const Dgip<S>*)dp;
+    const int total = m.nFaces * H::nfp;
+    if (total == 0) return cudaSuccess;
+    const int nb = (total + 127) / 128;
+    if (visc) k_dgip_face<D, P, S, true><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.G, (S*)w.FF, (S*)w.HA);
+    else k_dgip_face<D, P, S, false><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.G, (S*)w.FF, (S*)w.HA);
+    return cudaGetLastError();
+  }
+  template <bool VISC, int MODE>
+  static cudaError_t elem_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, S* out,
+                            const Stage<S>& sa, cudaStream_t st) {
+    static SmemGate done;
+    auto k = k_dgip_elem<D, P, S, VISC, MODE>;
+    constexpr size_t sm = smem_dgip_elem<D, P, S, VISC>();
+    if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
+    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.FF, (const S*)w.HA, out, sa);
+    return cudaGetLastError();
+  }
+  // stage == nullptr: write f to out; otherwise the ARK stage update
+  static cudaError_t elem(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* out,
+                          const void* stage, cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    const Dgip<S>& p = *(const Dgip<S>*)dp;
+    if (stage) {
+      const Stage<S>& sa = *(const Stage<S>*)stage;
+      return visc ? elem_v<true, 1>(m, p, (const S*)U, w, nullptr, sa, st)
+                  : elem_v<false, 1>(m, p, (const S*)U, w, nullptr, sa, st);
+    }
+    Stage<S> none{};
+    return visc ? elem_v<true, 0>(m, p, (const S*)U, w, (S*)out, none, st)
+                : elem_v<false, 0>(m, p, (const S*)U, w, (S*)out, none, st);
+  }
+  template <bool VISC>
+  static cudaError_t vjp_elem_v(const Mesh<S>& M, const S* U, const S* lam, const DgipWork& w, cudaStream_t st) {
+    static SmemGate done;
+    auto k = k_dgip_vjp_elem<D, P, S, VISC>;
+    constexpr size_t sm = smem_dgip_vjp_elem<D, P, S, VISC>();
+    if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
+    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, U, lam, (S*)w.gpart, (S*)w.FF, (S*)w.HA);
+    return cudaGetLastError();
+  }
+  static cudaError_t vjp_elem(const void* M, bool visc, const void* U, const void* lam, const DgipWork& w,
+                              cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    return visc ? vjp_elem_v<true>(m, (const S*)U, (const S*)lam, w, st)
+                : vjp_elem_v<false>(m, (const S*)U, (const S*)lam, w, st);
+  }
+  static cudaError_t vjp_face(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    const Dgip<S>& p = *(const Dgip<S>*)dp;
+    const int total = m.nFaces * H::nfp;
+    if (total == 0) return cudaSuccess;
+    const int nb = (total + 127) / 128;
+    if (visc)
+      k_dgip_vjp_face<D, P, S, true><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.FF, (const S*)w.HA,
+                                                          (S*)w.TUb, (S*)w.Gb);
+    else
+      k_dgip_vjp_face<D, P, S, false><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.FF, (const S*)w.HA,
+                                                           (S*)w.TUb, (S*)w.Gb);
+    return cudaGetLastError();
+  }
+  template <bool VISC>
+  static cudaError_t gather_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, S* g,
+                              cudaStream_t st) {
+    static SmemGate done;
+    auto k = k_dgip_vjp_gather<D, P, S, VISC>;
+    constexpr size_t sm = smem_dgip_gather<D, P, S, VISC>();
+    if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
+    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.TUb, (const S*)w.Gb, (const S*)w.gpart, g);
+    return cudaGetLastError();
+  }
+  static cudaError_t vjp_gather(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* g,
+                                cudaStream_t st) {
+    const Mesh<S>& m = *(const Mesh<S>*)M;
+    const Dgip<S>& p = *(const Dgip<S>*)dp;
+    return visc ? gather_v<true>(m, p, (const S*)U, w, (S*)g, st) : gather_v<false>(m, p, (const S*)U, w, (S*)g, st);
+  }
+};
+
+struct DgipTable {
+  cudaError_t (*trace)(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, cudaStream_t st);
+  cudaError_t (*face)(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st);
+  cudaError_t (*elem)(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* out,
+                      const void* stage, cudaStream_t st);
+  cudaError_t (*vjp_elem)(const void* M, bool visc, const void* U, const void* lam, const DgipWork& w,
+                          cudaStream_t st);
+  cudaError_t (*vjp_face)(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st);
+  cudaError_t (*vjp_gather)(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* g,
+                            cudaStream_t st);
+};
+
+template <int D, int P, typename S>
+const DgipTable* dgip_table() {
+  using O = DgipOps<D, P, S>;
+  static const DgipTable t = {&O::trace, &O::face, &O::elem, &O::vjp_elem, &O::vjp_face, &O::vjp_gather};
+  return &t;
+}
+
+}  // namespace dgx

@@ -1,0 +1,357 @@
+// Pointwise physics of the paper's DG-IP operator (device and host).
+//
+// * vij_flux: the Vijayasundaram flux of Sec. 3.3 (Eq.
+//   upwinding_Vijayasundaram_sdg), A_n^+(Ubar) U^+ + A_n^-(Ubar) U^-,
+//   Ubar = (U^+ + U^-)/2, with the characteristic splitting of Sec. 3.2.  Since
+//   the Euler flux is homogeneous of degree one, A_n(Ubar) Ubar = F_n(Ubar), and
+//   A^+ U^+ + A^- U^- = F_n(Ubar) + |A_n(Ubar)| (U^+ - U^-) / 2.  |A_n| dU is
+//   evaluated as the sum over characteristic waves |lambda_k| alpha_k r_k,
+//   alpha_k = l_k . dU: the two acoustic waves (lambda = u.n -+ c, wave
+//   strengths alpha_-+ = (dp -+ rho c du_n) / (2 c^2) with the pressure and
+//   normal-velocity jumps linearised at Ubar, eigenvectors
+//   r_-+ = (1, u -+ c n, H -+ c u_n)) and the d-fold wave lambda = u.n, whose
+//   part of dU is what the acoustic waves leave:
+//   |A| dU = |u_n| dU + (|u_n - c| - |u_n|) alpha_- r_- + (|u_n + c| - |u_n|) alpha_+ r_+.
+// * farfield_state: U_Gamma of App. B.1.1, A_n(U) U_Gamma = A_n^+(U) U +
+//   A_n^-(U) U_inf: the waves with lambda_k >= 0 of U - U_inf kept, so
+//   U_Gamma = U_inf + [u_n - c >= 0] alpha_- r_- + [u_n + c >= 0] alpha_+ r_+
+//            + [u_n >= 0] (dU - alpha_- r_- - alpha_+ r_+),  dU = U - U_inf.
+// * K-products: the viscous flux is linear in its gradient argument, so
+//   K(U)(delta (x) n) = F^nu(U, grad U := n (x) delta) (visc_flux_all with
+//   Q[c][f] = n_c delta_f).  On adiabatic walls K_w removes the normal heat
+//   flux; for a gradient argument delta (x) n the heat flux is parallel to n,
+//   so K_w(U)(delta (x) n) is the viscous flux with kappa = 0, and so is the
+//   normal component of F^{nu,w}(U, grad U).
+// * Dual<S, K>: forward-mode dual numbers (value + K tangents) used by the
+//   adjoint face kernel to differentiate the face function exactly.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "physics.cuh"
+
+namespace dgx {
+
+template <typename S, int K>
+struct Dual {
+  S v;
+  S d[K];
+  __host__ __device__ Dual() : v(0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = S(0);
+  }
+  template <typename X>
+  __host__ __device__ Dual(X x) : v((S)x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = S(0);
+  }
+  friend __host__ __device__ __forceinline__ Dual operator+(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+  }
+  friend __host__ __device__ __forceinline__ Dual operator-(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+  }
+  friend __host__ __device__ __forceinline__ Dual operator-(const Dual& a) {
+    Dual r;
+    r.v = -a.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = -a.d[k];
+    return r;
+  }
+  friend __host__ __device__ __forceinline__ Dual operator*(const Dual& a, const Dual& b) {
+    Dual r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+  }
+  friend __host__ __device__ __forceinline__ Dual operator/(const Dual& a, const Dual& b) {
+    Dual r;
+    const S ib = S(1) / b.v;
+    r.v = a.v * ib;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+    return r;
+  }
+  __host__ __device__ __forceinline__ Dual& operator+=(const Dual& b) { return *this = *this + b; }
+  __host__ __device__ __forceinline__ Dual& operator-=(const Dual& b) { return *this = *this - b; }
+  __host__ __device__ __forceinline__ Dual& operator*=(const Dual& b) { return *this = *this * b; }
+  friend __host__ __device__ __forceinline__ bool operator>(const Dual& a, const Dual& b) { return a.v > b.v; }
+  friend __host__ __device__ __forceinline__ bool operator>=(const Dual& a, const Dual& b) { return a.v >= b.v; }
+  friend __host__ __device__ __forceinline__ bool operator<(const Dual& a, const Dual& b) { return a.v < b.v; }
+  friend __host__ __device__ __forceinline__ Dual sqrt(const Dual& a) {
+    Dual r;
+    using ::sqrt;
+    r.v = sqrt(a.v);
+    const S h = S(0.5) / r.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * h;
+    return r;
+  }
+  // d|x|/dx = sign(x), sign(0) = 0
+  friend __host__ __device__ __forceinline__ Dual fabs(const Dual& a) {
+    const S s = a.v > S(0) ? S(1) : (a.v < S(0) ? S(-1) : S(0));
+    Dual r;
+    r.v = a.v < S(0) ? -a.v : a.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = s * a.d[k];
+    return r;
+  }
+};
+
+template <typename T, typename S>
+__host__ __device__ __forceinline__ Gas<T> gas_as(const Gas<S>& g) {
+  Gas<T> r;
+  r.gamma = T(g.gamma);
+  r.gm1 = T(g.gm1);
+  r.mu = T(g.mu);
+  r.lam = T(g.lam);
+  r.kcv = T(g.kcv);
+  return r;
+}
+
+// Normal convective flux F^c . nv.
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void conv_flux_normal(const T (&U)[D + 2], const N (&nv)[D], const Gas<T>& g,
+                                                          T (&F)[D + 2]) {
+  const T ir = T(1) / U[0];
+  T un = T(0), mm = T(0), mn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const T ui = U[1 + i] * ir;
+    un += ui * T(nv[i]);
+    mm += U[1 + i] * ui;
+    mn += U[1 + i] * T(nv[i]);
+  }
+  const T p = g.gm1 * (U[D + 1] - T(0.5) * mm);
+  F[0] = mn;
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = U[1 + j] * un + p * T(nv[j]);
+  F[D + 1] = (U[D + 1] + p) * un;
+}
+
+// Characteristic quantities of a state along the unit normal nh and the two
+// acoustic wave strengths of a jump dU (see the header comment).
+template <int D, typename T, typename N>
+struct Waves {
+  T u[D], un, c, H, am, ap;
+  __host__ __device__ __forceinline__ Waves(const T (&U)[D + 2], const T (&dU)[D + 2], const N (&nh)[D],
+                                            const Gas<T>& g) {
+    const T rho = U[0];
+    const T ir = T(1) / rho;
+    T q2 = T(0);
+    un = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      u[i] = U[1 + i] * ir;
+      q2 += u[i] * u[i];
+      un += u[i] * T(nh[i]);
+    }
+    const T p = g.gm1 * (U[D + 1] - T(0.5) * rho * q2);
+    const T c2 = g.gamma * p * ir;
+    c = dsqrt(c2);
+    H = (U[D + 1] + p) * ir;
+    T udm = T(0), ndm = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      udm += u[i] * dU[1 + i];
+      ndm += T(nh[i]) * dU[1 + i];
+    }
+    const T dp = g.gm1 * (T(0.5) * q2 * dU[0] - udm + dU[D + 1]);
+    const T rdun = ndm - un * dU[0];  // rho * (linearised normal-velocity jump)
+    const T i2c2 = T(0.5) / c2;
+    am = (dp - c * rdun) * i2c2;
+    ap = (dp + c * rdun) * i2c2;
+  }
+  // r_s for s = -1 / +1
+  __host__ __device__ __forceinline__ void r(int s, const N (&nh)[D], T (&R)[D + 2]) const {
+    const T sc = s > 0 ? c : -c;
+    R[0] = T(1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) R[1 + i] = u[i] + sc * T(nh[i]);
+    R[D + 1] = H + sc * un;
+  }
+};
+
+// Vijayasundaram flux through the area normal nv (own side UL outward).
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void vij_flux(const T (&UL)[D + 2], const T (&UR)[D + 2], const N (&nv)[D],
+                                                  const Gas<T>& g, T (&F)[D + 2]) {
+  constexpr int nf = D + 2;
+  N n2 = N(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
+  using ::sqrt;
+  const N sJ = sqrt(n2);
+  N nh[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  T Ub[nf], dU[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    Ub[f] = T(0.5) * (UL[f] + UR[f]);
+    dU[f] = UL[f] - UR[f];
+  }
+  conv_flux_normal<D, T, N>(Ub, nv, g, F);
+  const Waves<D, T, N> w(Ub, dU, nh, g);
+  const T l0 = fabs(w.un), lm = fabs(w.un - w.c), lp = fabs(w.un + w.c);
+  T rm[nf], rp[nf];
+  w.r(-1, nh, rm);
+  w.r(1, nh, rp);
+  const T cm = (lm - l0) * w.am, cp = (lp - l0) * w.ap;
+  const T hs = T(0.5) * T(sJ);
+#pragma unroll
+  for (int f = 0; f < nf; ++f) F[f] += hs * (l0 * dU[f] + cm * rm[f] + cp * rp[f]);
+}
+
+// Farfield boundary state U_Gamma (App. B.1.1) for the area normal nv.
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void farfield_state(const T (&U)[D + 2], const T (&Ui)[D + 2], const N (&nv)[D],
+                                                        const Gas<T>& g, T (&UG)[D + 2]) {
+  constexpr int nf = D + 2;
+  N n2 = N(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
+  using ::sqrt;
+  const N sJ = sqrt(n2);
+  N nh[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  T dU[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) dU[f] = U[f] - Ui[f];
+  const Waves<D, T, N> w(U, dU, nh, g);
+  T rm[nf], rp[nf];
+  w.r(-1, nh, rm);
+  w.r(1, nh, rp);
+  const bool om = !(w.un - w.c < T(0)), o0 = !(w.un < T(0)), op = !(w.un + w.c < T(0));
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    const T am = w.am * rm[f], ap = w.ap * rp[f];
+    T v = Ui[f];
+    if (om) v += am;
+    if (op) v += ap;
+    if (o0) v += dU[f] - am - ap;
+    UG[f] = v;
+  }
+}
+
+// K(U)(delta (x) nv) in every direction: F^nu(U, Q[c][f] = nv_c delta_f).
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void k_product(const T (&U)[D + 2], const T (&delta)[D + 2], const N (&nv)[D],
+                                                   const Gas<T>& g, T (&K)[D][D + 2]) {
+  T Q[D][D + 2];
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int f = 0; f < D + 2; ++f) Q[c][f] = T(nv[c]) * delta[f];
+  visc_flux_all<D, T>(U, Q, g, K);
+}
+
+// Mirror state (rho, m - 2 (m.n) n, rho E) for a normal of another scalar type.
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void mirror_state_n(const T (&U)[D + 2], const N (&nv)[D], T (&R)[D + 2]) {
+  N n2 = N(0);
+  T mn = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    n2 += nv[i] * nv[i];
+    mn += U[1 + i] * T(nv[i]);
+  }
+  const T c = T(2) * mn / T(n2);
+  R[0] = U[0];
+#pragma unroll
+  for (int i = 0; i < D; ++i) R[1 + i] = U[1 + i] - c * T(nv[i]);
+  R[D + 1] = U[D + 1];
+}
+
+// Kinds of face for the face function.
+enum { DGIP_INTERIOR = 0, DGIP_WALL = 1, DGIP_FARFIELD = 2 };
+
+// The state-dependent part of the DG-IP numerical flux of one face point and
+// the adjoint-consistency vectors of both sides (unit or area normal nv, own
+// side L outward), excluding the viscous average -(G^L - G^R)/2 (linear in the
+// gradient traces, added by the callers):
+//   interior: F = Vij(UL, UR) + tau (K(UL) + K(UR))(delta (x) n).n / (2|n|),
+//             HL = cL K(UL)(delta (x) n) (interface: (K(UL) + K(UR))/2 ...),
+//   wall:     F = Vij(UL, mirror(UL)) + tau K_w(UL)(dw (x) n).n / |n|, HL = K_w(UL)(dw (x) n),
+//   farfield: F = F^c(U_Gamma).n + tau K(U_inf)(di (x) n).n / |n|, HL = K(U_inf)(di (x) n),
+// delta = UL - UR, dw = UL - U_w(UL), di = UL - U_inf.  gw: the gas with kappa = 0.
+template <int D, typename T, typename N, bool VISC, int KIND>
+__host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], const T (&UR)[D + 2], const N (&nv)[D],
+                                                      const Gas<T>& g, const Gas<T>& gw, N tau_over_s, bool ifL,
+                                                      bool ifR, T (&F)[D + 2], T (&HL)[D][D + 2],
+                                                      T (&HR)[D][D + 2]) {
+  constexpr int nf = D + 2;
+  if (KIND == DGIP_INTERIOR) {
+    vij_flux<D, T, N>(UL, UR, nv, g, F);
+    if (VISC) {
+      T dl[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) dl[f] = UL[f] - UR[f];
+      T KL[D][nf], KR[D][nf];
+      k_product<D, T, N>(UL, dl, nv, g, KL);
+      k_product<D, T, N>(UR, dl, nv, g, KR);
+      const T h = T(0.5) * T(tau_over_s);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += (KL[c][f] + KR[c][f]) * T(nv[c]);
+        F[f] += h * s;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          const T avg = T(0.5) * (KL[c][f] + KR[c][f]);
+          HL[c][f] = ifL ? avg : T(0.5) * KL[c][f];
+          HR[c][f] = ifR ? avg : T(0.5) * KR[c][f];
+        }
+    }
+  } else if (KIND == DGIP_WALL) {
+    T Um[nf];
+    mirror_state_n<D, T, N>(UL, nv, Um);
+    vij_flux<D, T, N>(UL, Um, nv, g, F);
+    if (VISC) {
+      T Uw[nf], dw[nf];
+      wall_state<D, T>(UL, Uw);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) dw[f] = UL[f] - Uw[f];
+      k_product<D, T, N>(UL, dw, nv, gw, HL);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += HL[c][f] * T(nv[c]);
+        F[f] += T(tau_over_s) * s;
+      }
+    }
+  } else {  // farfield: UR holds U_inf
+    T UG[nf];
+    farfield_state<D, T, N>(UL, UR, nv, g, UG);
+    conv_flux_normal<D, T, N>(UG, nv, g, F);
+    if (VISC) {
+      T di[nf];
+#pragma unroll
+      for (int f = 0; f < nf; ++f) di[f] = UL[f] - UR[f];
+      k_product<D, T, N>(UR, di, nv, g, HL);
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += HL[c][f] * T(nv[c]);
+        F[f] += T(tau_over_s) * s;
+      }
+    }
+  }
+}
+
+}  // namespace dgx

@@ -29,6 +29,7 @@ struct Table {
                          const void* stage, cudaStream_t st);
   size_t (*smem)(int kind, int V);  // tile kernels: 0 trace, 1 br1, 2 elem
   const void* vjp;                   // adjoint launch table (VjpTable) or nullptr
+  const void* dgip;                  // DG-IP scheme launch table (DgipTable) or nullptr
 };
 
 // Defined in the generated units: table for (D, P, S) or nullptr.

@@ -17,6 +17,8 @@
 #include "dispatch.h"
 #include "flops.h"
 #include "vjp.cuh"
+#include "dgip.cuh"
+#include "mms.cuh"
 
 using dgx::Tab;
 
@@ -50,7 +52,7 @@ struct dgx_handle {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
-  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
+  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -62,6 +64,17 @@ struct dgx_handle {
   std::vector<int> h_nb;
   std::vector<int8_t> h_nbf, h_ori;
   std::vector<double> h_lo, h_size, h_xyz;
+  // the paper's DG-IP scheme (Vijayasundaram + SIPG), box meshes
+  bool dgip = false;
+  double alpha = 1.0;          // SIPG penalty factor
+  void* d_il = nullptr;        // [E] 1/l = |dT| / |T|, handle precision
+  double* d_lo = nullptr;      // [E][d] box corners and sizes, FP64 (node coordinates)
+  double* d_size = nullptr;
+  bool has_farfield = false;   // the mesh has farfield faces (tag 1)
+  bool has_uinf = false;
+  double Uinf[5] = {};
+  int8_t* d_mask = nullptr;    // explicit-element mask of the geometry split
+  const dgx::DgipTable* dtab = nullptr;
   // tableau
   int stages = 0;
   double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
@@ -145,9 +158,13 @@ dgx_status upload_real(dgx_handle* h, const std::vector<double>& v, void** dst) 
 }
 
 void free_mesh(dgx_handle* h) {
-  void* ptrs[] = {h->d_nb, h->d_nbf, h->d_ori, h->d_faces, h->d_rh, h->d_Ja, h->d_iJ, h->d_SnE, h->d_SnF};
+  void* ptrs[] = {h->d_nb, h->d_nbf, h->d_ori, h->d_faces, h->d_rh, h->d_Ja, h->d_iJ, h->d_SnE, h->d_SnF,
+                  h->d_il, h->d_lo, h->d_size};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  h->d_il = nullptr;
+  h->d_lo = h->d_size = nullptr;
+  h->has_farfield = false;
   h->d_nb = nullptr;
   h->d_nbf = nullptr;
   h->d_ori = nullptr;
@@ -167,7 +184,8 @@ dgx_status check_connectivity(dgx_handle* h, const int32_t* nb, const int8_t* nb
       const int k = e * NF + f;
       const int o = nb[k];
       if (o < 0) {
-        if (o != -1) return DGX_EUNSUPPORTED;  // only tag 0 (adiabatic wall) is implemented
+        // tag 0 (adiabatic wall); tag 1 (farfield) with the DG-IP scheme only
+        if (o != -1 && !(o == -2 && h->dgip)) return DGX_EUNSUPPORTED;
         faces.push_back(make_int4(e, o, f, 0));
         continue;
       }
@@ -197,6 +215,8 @@ dgx_status upload_connectivity(dgx_handle* h, const int32_t* nb, const int8_t* n
   if ((s = upload(vori, (void**)&h->d_ori)) != DGX_OK) return s;
   if ((s = upload(faces, (void**)&h->d_faces)) != DGX_OK) return s;
   h->nFaces = (int)faces.size();
+  h->has_farfield = false;
+  for (const int4& r : faces) h->has_farfield |= (r.y == -2);
   return DGX_OK;
 }
 
@@ -255,10 +275,76 @@ void profile_collect(dgx_handle* h) {
 }
 
 struct Layout {
-  size_t TU, FF, G, Q, Y, K, SH, TUb, JB, Qb, NU, LAM, total;
+  size_t TU, FF, G, Q, Y, K, SH, TUb, JB, Qb, NU, LAM, HA, GB, GP, total;
 };
 
+// DG-IP scheme: TU, FF (+ G, HA viscous); the VJP adds TUb (+ Gb) and the
+// element-local part of g; the ARK step adds Y, k_0..k_{s-2} and the FP32 shadow.
+Layout layout_dgip(const dgx_handle* h, int op) {
+  Layout L{};
+  const size_t face = (size_t)h->E * h->NF * h->nf * h->nfp * h->s;
+  const size_t state = (size_t)h->E * h->nf * h->N * h->s;
+  size_t off = 0;
+  L.TU = off;
+  off += align256(face);
+  L.FF = off;
+  off += align256(face);
+  if (h->viscous) {
+    L.G = off;
+    off += align256(face);
+    L.HA = off;
+    off += align256(face * h->d);
+  }
+  if (op == DGX_OP_VJP) {
+    L.TUb = off;
+    off += align256(face);
+    if (h->viscous) {
+      L.GB = off;
+      off += align256(face);
+    }
+    L.GP = off;
+    off += align256(state);
+  }
+  if (op == DGX_OP_ARK) {
+    L.Y = off;
+    off += align256(state);
+    L.K = off;
+    off += align256(state) * (h->stages > 1 ? h->stages - 1 : 0);
+    if (!h->fp64) {
+      L.SH = off;
+      off += align256(state);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+dgx::DgipWork dgip_work_at(const dgx_handle* h, void* ws, const Layout& L) {
+  char* b = (char*)ws;
+  dgx::DgipWork w{};
+  w.TU = b + L.TU;
+  w.FF = b + L.FF;
+  w.G = h->viscous ? b + L.G : nullptr;
+  w.HA = h->viscous ? b + L.HA : nullptr;
+  w.TUb = L.TUb ? b + L.TUb : nullptr;
+  w.Gb = (L.GB && h->viscous) ? b + L.GB : nullptr;
+  w.gpart = L.GP ? b + L.GP : nullptr;
+  return w;
+}
+
+template <typename S>
+dgx::Dgip<S> dgip_params(const dgx_handle* h, const int8_t* mask, const void* Uim) {
+  dgx::Dgip<S> p{};
+  p.il = (const S*)h->d_il;
+  p.tk2 = (S)(h->alpha * (h->p + 1) * (h->p + 1));
+  p.mask = mask;
+  p.Uim = (const S*)Uim;
+  for (int f = 0; f < 5; ++f) p.Uinf[f] = (S)h->Uinf[f];
+  return p;
+}
+
 Layout layout(const dgx_handle* h, int op) {
+  if (h->dgip) return layout_dgip(h, op);
   Layout L{};
   const size_t face = (size_t)h->E * h->NF * h->nf * h->nfp * h->s;
   const size_t state = (size_t)h->E * h->nf * h->N * h->s;
@@ -505,10 +591,89 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
   return DGX_OK;
 }
 
+// ------------------------------------------------------------ DG-IP scheme
+// One residual (traces and own-face viscous fluxes, face fluxes, element):
+// f to out, or with stage != nullptr the fused ARK stage update.
+template <typename S>
+cudaError_t dgip_residual(dgx_handle* h, const void* U, const int8_t* mask, const void* Uim, void* out,
+                          const dgx::DgipWork& w, const void* stage, cudaStream_t st) {
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  const dgx::Dgip<S> dp = dgip_params<S>(h, mask, Uim);
+  const dgx::DgipTable* t = h->dtab;
+  cudaError_t err = launch(h, DGX_K_DGIP_TRACE, st, [&] { return t->trace(M, &dp, h->viscous, U, w, st); });
+  if (err == cudaSuccess) err = launch(h, DGX_K_DGIP_FACE, st, [&] { return t->face(M, &dp, h->viscous, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_DGIP_ELEM, st, [&] { return t->elem(M, &dp, h->viscous, U, w, out, stage, st); });
+  return err;
+}
+
+// g = (df/dU)^T lam: forward traces, then the element, face and gather adjoints.
+template <typename S>
+cudaError_t dgip_vjp(dgx_handle* h, const void* U, const void* lam, void* g, const dgx::DgipWork& w,
+                     cudaStream_t st) {
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  const dgx::Dgip<S> dp = dgip_params<S>(h, nullptr, nullptr);
+  const dgx::DgipTable* t = h->dtab;
+  cudaError_t err = launch(h, DGX_K_DGIP_TRACE, st, [&] { return t->trace(M, &dp, h->viscous, U, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_DGIP_VJP_ELEM, st, [&] { return t->vjp_elem(M, h->viscous, U, lam, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_DGIP_VJP_FACE, st, [&] { return t->vjp_face(M, &dp, h->viscous, w, st); });
+  if (err == cudaSuccess)
+    err = launch(h, DGX_K_DGIP_VJP_GATHER, st, [&] { return t->vjp_gather(M, &dp, h->viscous, U, w, g, st); });
+  return err;
+}
+
+// One explicit ARK step of the DG-IP scheme (stage states optionally kept as
+// checkpoints, as dgx_ark_step_stages describes).
+template <typename S>
+dgx_status dgip_ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st) {
+  const Layout L = layout(h, DGX_OP_ARK);
+  const dgx::DgipWork w = dgip_work_at(h, workspace, L);
+  char* base = (char*)workspace;
+  S* Y = (S*)(base + L.Y);
+  const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
+  S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
+  const Slot SL = slot_layout(h);
+  char* ck = (char*)stages;
+  auto slot_y = [&](int i) { return (S*)(ck + SL.bytes * i + SL.y); };
+  S* first = ck ? slot_y(0) : shadow;  // the working-precision (or checkpointed) copy of U_n
+  const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
+  cudaError_t err = cudaSuccess;
+  if (first)
+    err = launch(h, DGX_K_TRACE, st,
+                 [&] { return h->tab->trace_from64(M, h->var[DGX_K_TRACE], U64, w.TU, first, st); });
+  if (err != cudaSuccess) return DGX_ECUDA;
+  const S* y0 = (h->fp64 && !ck) ? (const S*)U64 : first;
+  const int s = h->stages;
+  for (int i = 0; i < s && err == cudaSuccess; ++i) {
+    dgx::Stage<S> sa{};
+    for (int j = 0; j < i; ++j) sa.k[j] = (const S*)(base + L.K + state * j);
+    sa.i = i;
+    sa.last = (i == s - 1);
+    if (!sa.last)
+      for (int j = 0; j <= i; ++j) sa.ca[j] = (S)h->A[(i + 1) * dgx::MAXSTAGES + j];
+    for (int j = 0; j < s; ++j) sa.cb[j] = (S)h->b[j];
+    const S dts = (S)dt;
+    for (int j = 0; j < s; ++j) {
+      sa.caf[j] = dts * sa.ca[j];
+      sa.cbf[j] = dts * sa.cb[j];
+    }
+    sa.base = y0;
+    sa.Un = U64;
+    sa.Y = (ck && !sa.last) ? slot_y(i + 1) : Y;
+    sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
+    sa.shadow = shadow;
+    const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
+    err = dgip_residual<S>(h, Uin, nullptr, nullptr, nullptr, w, &sa, st);
+  }
+  return cuda_status(err);
+}
+
 // ------------------------------------------------------------ work model
 struct Pointwise {
   double conv, visc, visc_n, wall_visc, llf_unit, llf_area, conv_vjp, visc_vjp, visc_n_vjp, llf_unit_vjp,
-      llf_area_vjp;
+      llf_area_vjp, dgip_face, dgip_face_euler, dgip_face_vjp, dgip_face_euler_vjp;
 };
 
 template <int D>
@@ -552,6 +717,23 @@ Pointwise count_pointwise() {
   pc.visc_n_vjp = cnt([&] { dgx::visc_flux_normal_vjp<D, C>(U, Q, nv, G, g, Ub, Qb); });
   pc.llf_unit_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, true>(U, V, nv, G, g, Ub, Vb); });
   pc.llf_area_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, false>(U, V, nv, G, g, Ub, Vb); });
+  {  // DG-IP face function (interior face point), forward and its dual-number adjoint
+    C HL[D][D + 2], HR[D][D + 2], Fb[D + 2], Hb[D][D + 2];
+    for (int f = 0; f < D + 2; ++f) {
+      Fb[f] = 0.1;
+      for (int a = 0; a < D; ++a) Hb[a][f] = 0.2;
+    }
+    const C tau = 10.0;
+    pc.dgip_face = cnt([&] { dgx::dgip_face_fn<D, C, C, true, dgx::DGIP_INTERIOR>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
+    pc.dgip_face_euler =
+        cnt([&] { dgx::dgip_face_fn<D, C, C, false, dgx::DGIP_INTERIOR>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
+    pc.dgip_face_vjp = cnt([&] {
+      dgx::dgip_face_fn_vjp_host<D, C, true>(U, V, nv, g, tau, Fb, Hb, Hb, Ub, Vb);
+    });
+    pc.dgip_face_euler_vjp = cnt([&] {
+      dgx::dgip_face_fn_vjp_host<D, C, false>(U, V, nv, g, tau, Fb, Hb, Hb, Ub, Vb);
+    });
+  }
   return pc;
 }
 
@@ -639,6 +821,33 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       // face arrays: TU, both sides' Fhat_bar, TU_bar read and written, JB written
       bytes = E * ((6 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);
       break;
+    case DGX_K_DGIP_TRACE:  // traces; face gradients and own-face viscous fluxes
+      flops = E * FACE * 2 * n + (v ? E * NF * nfp * (D * nf * 2 * n + pc.visc_n) : 0.0);
+      bytes = E * ((STATE + FACE + (v ? FACE : 0)) * s + D * s);
+      break;
+    case DGX_K_DGIP_FACE:  // both sides' traces and G read; FF and HA of both sides written
+      flops = F * nfp * ((v ? pc.dgip_face : pc.dgip_face_euler) + (v ? 3 * nf : 0));
+      bytes = E * FACE * s * (2 + (v ? 1 + D : 0));
+      break;
+    case DGX_K_DGIP_ELEM:  // U, FF (+ HA) in, f out; gradient lines, flux, tangential terms, divergence + lift
+      flops = E * N * (pc.conv + (v ? pc.visc + D * nf * 2 * n + (D - 1) * D * nf * 4 : 0) + D * nf * (2 * n + 6) +
+                       (v ? D * nf * 4 : 0));
+      bytes = E * ((2 * STATE + FACE + (v ? D * FACE : 0)) * s + D * s);
+      break;
+    case DGX_K_DGIP_VJP_ELEM:  // U, lambda in; the local part of g, FFb (+ HAb) out
+      flops = E * N * (pc.conv_vjp + D * nf * 2 * n + D * nf * 8 + (v ? pc.visc_vjp + 2 * D * nf * 2 * n : 0)) +
+              (v ? E * NF * (D - 1) * nf * nfp * 2 * n : 0.0);
+      bytes = E * ((3 * STATE + FACE + (v ? D * FACE : 0)) * s + D * s);
+      break;
+    case DGX_K_DGIP_VJP_FACE:  // traces, FFb (+ HAb) of both sides read; TUb (+ Gb) written
+      flops = F * nfp * (v ? pc.dgip_face_vjp : pc.dgip_face_euler_vjp);
+      bytes = E * FACE * s * (3 + (v ? D + 1 : 0));
+      break;
+    case DGX_K_DGIP_VJP_GATHER:  // U, gpart, TUb (+ Gb) in, g out
+      flops = E * (FACE * 2 * n + STATE * 2 * D +
+                   (v ? NF * nfp * (D * nf * 2 * n + pc.visc_n_vjp + (D - 1) * nf * 2 * n + 2 * n * nf) : 0));
+      bytes = E * ((3 * STATE + FACE + (v ? FACE : 0)) * s + D * s);
+      break;
     case DGX_K_VJP_GATHER:
       flops = E * ((v ? FACE * 2 : 0) + STATE * 4 * D);
       bytes = E * ((FACE + (v ? FACE : 0) + 2 * STATE) * s);
@@ -653,7 +862,7 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
 }
 
 // ------------------------------------------------------------ autotuning
-bool is_tile_kind(int k) { return k != DGX_K_FACE && k != DGX_K_VJP_FACE; }
+bool is_tile_kind(int k) { return k != DGX_K_FACE && k != DGX_K_VJP_FACE && k < DGX_K_DGIP_TRACE; }
 
 size_t tile_smem(const dgx_handle* h, int kind, int V) {
   const dgx::Table* t = h->tab;
@@ -686,8 +895,10 @@ int64_t dgx::Count::ops = 0;
 extern "C" {
 
 const char* dgx_kernel_name(int32_t kind) {
-  static const char* names[DGX_KERNEL_KINDS] = {"trace", "br1", "face", "elem", "elem_stage",
-                                                "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"};
+  static const char* names[DGX_KERNEL_KINDS] = {"trace",      "br1",           "face",          "elem",
+                                                "elem_stage", "vjp_elem",      "vjp_face",      "vjp_br1",
+                                                "vjp_gather", "dgip_trace",    "dgip_face",     "dgip_elem",
+                                                "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather"};
   return (kind >= 0 && kind < DGX_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 
@@ -758,6 +969,12 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   if (desc->precision != DGX_FP64 && desc->precision != DGX_FP32) return DGX_EINVAL;
   if (!(desc->gamma > 1.0)) return DGX_EINVAL;
   if (desc->viscous && (!(desc->Re > 0.0) || !(desc->Pr > 0.0))) return DGX_EINVAL;
+  if (desc->conv_flux != DGX_FLUX_LLF && desc->conv_flux != DGX_FLUX_VIJAYASUNDARAM) return DGX_EINVAL;
+  if (desc->visc_flux != DGX_VISC_BR1 && desc->visc_flux != DGX_VISC_SIPG) return DGX_EINVAL;
+  if (!(desc->penalty_alpha >= 0.0) || !std::isfinite(desc->penalty_alpha)) return DGX_EINVAL;
+  const bool dgip = desc->conv_flux == DGX_FLUX_VIJAYASUNDARAM;
+  // the schemes are LLF + BR1 and Vijayasundaram + SIPG
+  if (desc->viscous && (desc->visc_flux == DGX_VISC_SIPG) != dgip) return DGX_EUNSUPPORTED;
   dgx_handle* h = new (std::nothrow) dgx_handle();
   if (!h) return DGX_ENOMEM;
   h->desc = *desc;
@@ -773,12 +990,15 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   h->viscous = desc->viscous != 0;
   h->fp64 = desc->precision == DGX_FP64;
   h->s = h->fp64 ? 8 : 4;
+  h->dgip = dgip;
+  h->alpha = desc->penalty_alpha > 0.0 ? desc->penalty_alpha : 1.0;
   if (h->d == 2) h->tab = h->fp64 ? dgx::table_d2_f64(h->p) : dgx::table_d2_f32(h->p);
   else h->tab = h->fp64 ? dgx::table_d3_f64(h->p) : dgx::table_d3_f32(h->p);
-  if (!h->tab) {
+  if (!h->tab || (h->dgip && !h->tab->dgip)) {
     delete h;
     return DGX_EUNSUPPORTED;
   }
+  h->dtab = (const dgx::DgipTable*)h->tab->dgip;
   dgx_status st = DGX_OK;
   if (h->fp64) {
     std::vector<Tab<double>> t(6);
@@ -822,6 +1042,7 @@ dgx_status dgx_destroy(dgx_handle* h) {
   if (!h) return DGX_EINVAL;
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_mesh(h);
+  if (h->d_mask) cudaFree(h->d_mask);
   if (h->d_tabs) cudaFree(h->d_tabs);
   if (h->d_flags) cudaFree(h->d_flags);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -856,6 +1077,15 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   for (size_t i = 0; i < rh.size(); ++i) rh[i] = 2.0 / size[i];
   if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
   if ((st = upload_real(h, rh, &h->d_rh)) != DGX_OK) return st;
+  {  // 1/l = |dT| / |T| = 2 sum_a 1/h_a for a box (SIPG penalty), FP64 corners and sizes
+    std::vector<double> il(E, 0.0);
+    for (int e = 0; e < E; ++e)
+      for (int a = 0; a < d; ++a) il[e] += 2.0 / size[(size_t)e * d + a];
+    std::vector<double> vlo(lo, lo + (size_t)E * d), vsz(size, size + (size_t)E * d);
+    if ((st = upload_real(h, il, &h->d_il)) != DGX_OK) return st;
+    if ((st = upload(vlo, (void**)&h->d_lo)) != DGX_OK) return st;
+    if ((st = upload(vsz, (void**)&h->d_size)) != DGX_OK) return st;
+  }
   h->h_lo.assign(lo, lo + (size_t)E * d);
   h->h_size.assign(size, size + (size_t)E * d);
   h->h_xyz.clear();
@@ -869,6 +1099,7 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
 dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
                               const int8_t* orient) {
   if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
+  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels take box meshes
   const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
   for (size_t i = 0; i < (size_t)E * d * N; ++i)
     if (!std::isfinite(xyz[i])) return DGX_EINVAL;
@@ -989,6 +1220,7 @@ size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
   if ((op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && h->stages == 0) return 0;
   if (op < DGX_OP_RHS || op > DGX_OP_ARK_STEP_ADJOINT) return 0;
+  if (h->dgip && (op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT)) return 0;
   if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && !h->tab->vjp) return 0;
   if (op == DGX_OP_ARK_STEP_ADJOINT)  // the forward's and the adjoint's workspaces side by side
     return layout(h, DGX_OP_ARK).total + layout(h, DGX_OP_ARK_ADJOINT).total;
@@ -999,6 +1231,13 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
   if (!h || !U || !dUdt || !workspace || U == dUdt) return DGX_EINVAL;
   if (!h->has_mesh) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip) {
+    if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
+    cudaStream_t st = (cudaStream_t)stream;
+    return cuda_status(h->fp64 ? dgip_residual<double>(h, U, nullptr, nullptr, dUdt, w, nullptr, st)
+                               : dgip_residual<float>(h, U, nullptr, nullptr, dUdt, w, nullptr, st));
+  }
   const Layout L = layout(h, DGX_OP_RHS);
   const dgx::Work w = work_at(h, workspace, L);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1028,6 +1267,12 @@ dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* g
   if (!h->has_mesh) return DGX_ESTATE;
   if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip) {
+    if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_VJP));
+    cudaStream_t st = (cudaStream_t)stream;
+    return cuda_status(h->fp64 ? dgip_vjp<double>(h, U, lambda, gU, w, st) : dgip_vjp<float>(h, U, lambda, gU, w, st));
+  }
   const Layout L = layout(h, DGX_OP_VJP);
   const dgx::VjpWork vw = vjp_work_at(h, workspace, L);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1047,6 +1292,11 @@ dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, 
   if (!h || !U64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip) {
+    if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    return h->fp64 ? dgip_ark_impl<double>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream)
+                   : dgip_ark_impl<float>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
+  }
   if (h->fp64) return ark_impl<double>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
   return ark_impl<float>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
 }
@@ -1056,6 +1306,11 @@ dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stag
   if (((uintptr_t)stages & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip) {
+    if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    return h->fp64 ? dgip_ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream)
+                   : dgip_ark_impl<float>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
+  }
   if (h->fp64) return ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
   return ark_impl<float>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
 }
@@ -1064,7 +1319,7 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
                                 void* stream) {
   if (!h || !stages || !lam64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp || h->dgip) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->fp64) return ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
   return ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
@@ -1075,7 +1330,7 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
   if (!h || !U64 || !lam64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (((uintptr_t)stages & 255) != 0 || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp || h->dgip) return DGX_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   char* ws_adj = (char*)workspace + layout(h, DGX_OP_ARK).total;  // a multiple of 256 bytes
   dgx_status s = h->fp64 ? ark_impl<double>(h, U64, dt, stages, workspace, st, nullptr, /*fork=*/true)
@@ -1089,6 +1344,68 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
               : ark_adjoint_impl<float>(h, stages, lam64, dt, ws_adj, st);
   if (cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess && s == DGX_OK) s = DGX_ECUDA;
   return s;
+}
+
+dgx_status dgx_set_farfield(dgx_handle* h, const double* U_inf) {
+  if (!h || !U_inf) return DGX_EINVAL;
+  if (!h->dgip) return DGX_EUNSUPPORTED;
+  for (int f = 0; f < h->nf; ++f)
+    if (!std::isfinite(U_inf[f])) return DGX_EINVAL;
+  double m2 = 0.0;
+  for (int i = 0; i < h->d; ++i) m2 += U_inf[1 + i] * U_inf[1 + i];
+  const double p = (h->desc.gamma - 1.0) * (U_inf[h->d + 1] - 0.5 * m2 / U_inf[0]);
+  if (!(U_inf[0] > 0.0) || !(p > 0.0)) return DGX_EINVAL;  // not a physical state
+  for (int f = 0; f < 5; ++f) h->Uinf[f] = f < h->nf ? U_inf[f] : 0.0;
+  h->has_uinf = true;
+  return DGX_OK;
+}
+
+dgx_status dgx_set_explicit_mask(dgx_handle* h, const int8_t* mask) {
+  if (!h) return DGX_EINVAL;
+  if (!h->dgip) return DGX_EUNSUPPORTED;
+  if (!mask) {
+    if (h->d_mask) cudaFree(h->d_mask);
+    h->d_mask = nullptr;
+    return DGX_OK;
+  }
+  std::vector<int8_t> m(mask, mask + h->E);
+  for (int8_t& v : m) v = v ? 1 : 0;
+  return upload(m, (void**)&h->d_mask);
+}
+
+dgx_status dgx_rhs_split(dgx_handle* h, const void* U_ex, const void* U_im, void* dUdt, void* workspace,
+                         void* stream) {
+  if (!h || !U_ex || !U_im || !dUdt || !workspace || dUdt == U_ex || dUdt == U_im) return DGX_EINVAL;
+  if (!h->dgip) return DGX_EUNSUPPORTED;
+  if (!h->has_mesh || !h->d_mask) return DGX_ESTATE;
+  if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
+  cudaStream_t st = (cudaStream_t)stream;
+  return cuda_status(h->fp64 ? dgip_residual<double>(h, U_ex, h->d_mask, U_im, dUdt, w, nullptr, st)
+                             : dgip_residual<float>(h, U_ex, h->d_mask, U_im, dUdt, w, nullptr, st));
+}
+
+dgx_status dgx_mms_source(dgx_handle* h, double t, double kx, double ky, double omega, void* dUdt, void* stream) {
+  if (!h || !dUdt || !std::isfinite(t) || !std::isfinite(kx) || !std::isfinite(ky) || !std::isfinite(omega))
+    return DGX_EINVAL;
+  if (h->d != 2) return DGX_EUNSUPPORTED;
+  if (!h->has_mesh || h->curv || !h->d_lo) return DGX_ESTATE;
+  dgx::MmsNodes nodes{};
+  const dgx::Basis1 b = dgx::make_basis1(h->p);
+  for (int i = 0; i < b.n; ++i) nodes.xi[i] = b.x[i];
+  const double mu = h->viscous ? 1.0 / h->desc.Re : 0.0;
+  const double kcv = h->viscous ? h->desc.gamma * mu / h->desc.Pr : 0.0;
+  const long long total = (long long)h->E * h->N;
+  const int blocks = (int)((total + 255) / 256);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->fp64)
+    dgx::k_mms_source<double><<<blocks, 256, 0, st>>>(h->E, h->n, nodes, h->d_lo, h->d_size, t, kx, ky, omega,
+                                                      h->desc.gamma - 1.0, kcv, (double*)dUdt);
+  else
+    dgx::k_mms_source<float><<<blocks, 256, 0, st>>>(h->E, h->n, nodes, h->d_lo, h->d_size, t, kx, ky, omega,
+                                                     h->desc.gamma - 1.0, kcv, (float*)dUdt);
+  return cuda_status(cudaGetLastError());
 }
 
 dgx_status dgx_check(dgx_handle* h) {
@@ -1183,6 +1500,7 @@ static dgx_status autotune_impl(dgx_handle* h, const double* U64, int32_t reps, 
 dgx_status dgx_autotune(dgx_handle* h, const double* U64, int32_t reps, void* stream) {
   if (!h || !U64 || reps < 1) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
+  if (h->dgip) return DGX_OK;  // the DG-IP kernels have one tile shape: nothing to choose
   int saved[DGX_KERNEL_KINDS];
   std::copy(h->var, h->var + DGX_KERNEL_KINDS, saved);
   const bool saved_pipe = h->pipeline, saved_prof = h->prof;
@@ -1312,6 +1630,7 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
   for (int i = 0; i < count; ++i) {
     const dgx_handle* h = inst[i];
     if (!h) return DGX_EINVAL;
+    if (h->dgip) return DGX_EUNSUPPORTED;  // batches run the LLF/BR1 scheme
     if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
     if (h->stages != h0->stages) return DGX_EINVAL;
     for (int r = 0; r < dgx::MAXSTAGES * dgx::MAXSTAGES; ++r)

@@ -17,7 +17,15 @@ __global__ void __launch_bounds__(256) k_fma_chain(int64_t iters, S m, S c, S* _
   S x[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) x[k] = S(1) + S(1e-3) * (S)((tid + k) & 255);
-  for (int64_t i = 0; i < iters; ++i) {
+  // four iterations per trip so loop control takes a negligible share of issue slots
+  int64_t i = 0;
+  for (; i + 4 <= iters; i += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fma(x[k], m, c);
+  }
+  for (; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[k] = fma(x[k], m, c);
   }

@@ -33,7 +33,8 @@ class _Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("p", ctypes.c_int32), ("n_elem", ctypes.c_int32),
                 ("viscous", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("gamma", ctypes.c_double), ("Re", ctypes.c_double), ("Pr", ctypes.c_double),
-                ("Ma", ctypes.c_double)]
+                ("Ma", ctypes.c_double), ("conv_flux", ctypes.c_int32), ("visc_flux", ctypes.c_int32),
+                ("penalty_alpha", ctypes.c_double)]
 
 
 _lib = None
@@ -45,9 +46,12 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_stage_bytes", "dgx_kernel_work", "dgx_autotune", "dgx_get_variants", "dgx_set_variants",
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
-           "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma"]
+           "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
+           "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source"]
+SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
-KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather"]
+KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
+           "dgip_trace", "dgip_face", "dgip_elem", "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -99,6 +103,10 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_kernel_name.argtypes = [i32]
     lib.dgx_kernel_name.restype = ctypes.c_char_p
     lib.dgx_probe_fma.argtypes = [i32, ctypes.c_int64, vp, ctypes.c_int64, ctypes.POINTER(dbl), vp]
+    lib.dgx_set_farfield.argtypes = [vp, vp]
+    lib.dgx_set_explicit_mask.argtypes = [vp, vp]
+    lib.dgx_rhs_split.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.dgx_mms_source.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp]
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
@@ -157,7 +165,8 @@ class Solver:
     :class:`inputs.Physics`.  ``precision`` is "fp64" or "fp32".
     """
 
-    def __init__(self, mesh, phys, precision: str = "fp64", device: Optional[torch.device] = None):
+    def __init__(self, mesh, phys, precision: str = "fp64", device: Optional[torch.device] = None,
+                 scheme: str = "llf-br1", alpha: float = 1.0, U_inf=None):
         if not torch.cuda.is_available():
             raise RuntimeError("dgx needs a CUDA device; there is no CPU fallback")
         self.lib = load_library()
@@ -166,8 +175,10 @@ class Solver:
         self.precision = precision
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.device = device or torch.device("cuda", torch.cuda.current_device())
+        conv, visc = SCHEMES[scheme]
+        self.scheme = scheme
         desc = _Desc(mesh.dim, mesh.p, mesh.n_elem, int(phys.viscous), FP64 if precision == "fp64" else FP32,
-                     phys.gamma, phys.Re if phys.viscous else 0.0, phys.Pr, phys.Ma)
+                     phys.gamma, phys.Re if phys.viscous else 0.0, phys.Pr, phys.Ma, conv, visc, float(alpha))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.dgx_create(ctypes.byref(desc), ctypes.byref(h)), "dgx_create")
@@ -186,6 +197,21 @@ class Solver:
             _check(self.lib.dgx_set_mesh_nodes(h, _ptr(xyz), _ptr(nb), _ptr(nbf), _ptr(ori)), "dgx_set_mesh_nodes")
         self._ws = {}
         self.stages = 0
+        if U_inf is not None:
+            self.set_farfield(U_inf)
+
+    def set_farfield(self, U_inf):
+        """Free-stream state (conservative) of the farfield boundaries (DG-IP scheme)."""
+        u = np.ascontiguousarray(U_inf, dtype=np.float64)
+        _check(self.lib.dgx_set_farfield(self.h, _ptr(u)), "dgx_set_farfield")
+
+    def set_explicit_mask(self, mask):
+        """Explicit-region element mask of the geometry split (None removes it)."""
+        if mask is None:
+            _check(self.lib.dgx_set_explicit_mask(self.h, None), "dgx_set_explicit_mask")
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool), dtype=np.int8)
+        _check(self.lib.dgx_set_explicit_mask(self.h, _ptr(m)), "dgx_set_explicit_mask")
 
     def close(self):
         if getattr(self, "h", None):
@@ -241,6 +267,23 @@ class Solver:
         ws = self.workspace(OP_RHS)
         _check(self.lib.dgx_rhs(self.h, self._state(U), self._state(out, "out"), self._aligned(ws),
                                 _stream_ptr(stream)), "dgx_rhs")
+        return out
+
+    def rhs_split(self, U_ex: torch.Tensor, U_im: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+        """R^DG(U_ex, U_im) of the geometry split (explicit elements read U_ex,
+        implicit ones U_im; f = 0 on implicit elements)."""
+        out = self.empty_state() if out is None else out
+        ws = self.workspace(OP_RHS)
+        _check(self.lib.dgx_rhs_split(self.h, self._state(U_ex, "U_ex"), self._state(U_im, "U_im"),
+                                      self._state(out, "out"), self._aligned(ws), _stream_ptr(stream)),
+               "dgx_rhs_split")
+        return out
+
+    def mms_source(self, t: float, out: torch.Tensor, kx=2.0, ky=2.0, omega=200.0, stream=None) -> torch.Tensor:
+        """out += the manufactured-solution source S(x, t) (2D, box meshes)."""
+        _check(self.lib.dgx_mms_source(self.h, float(t), float(kx), float(ky), float(omega),
+                                       self._state(out, "out"), _stream_ptr(stream)), "dgx_mms_source")
         return out
 
     def rhs_noalloc(self, U: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:

@@ -1,0 +1,244 @@
+"""GPU parity of the paper's DG-IP operator (Vijayasundaram flux + symmetric
+interior penalty; farfield and adiabatic-wall forms; geometry-split interface;
+manufactured-solution source; ARK step) against the FP64 oracle (oracle.sipg)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ark
+from oracle.residual import submesh_around
+from oracle.sipg import SIPGOperator
+from paper_2607_16044_b300 import inputs as I
+from tests import mms_sympy
+from tests.parity_util import TOL, gas_of, quantize32, record, rel_err
+
+pytestmark = pytest.mark.gpu
+
+UINF2 = np.array([1.1, 0.4, -0.3, 2.0 / 0.4 + 0.5 * (0.4 ** 2 + 0.3 ** 2) / 1.1])
+
+
+def _solver(mesh, phys, prec, **kw):
+    from paper_2607_16044_b300.dgx import Solver
+    return Solver(mesh, phys, prec, scheme="dgip", **kw)
+
+
+def _euler():
+    return I.Physics(gamma=1.4, viscous=False)
+
+
+def _ns(Re=200.0):
+    return I.Physics(gamma=1.4, Re=Re, Pr=0.72, Ma=0.3, viscous=True)
+
+
+def _dt(prec):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def _oracle(mesh, phys, U, U_inf=None, explicit=None, U_im=None):
+    op = SIPGOperator(mesh, gas_of(phys), U_inf=U_inf, explicit=explicit)
+    return op.residual(torch.as_tensor(U), None if U_im is None else torch.as_tensor(U_im)).numpy()
+
+
+def _check(mesh, phys, U, prec, name, U_inf=None):
+    s = _solver(mesh, phys, prec, U_inf=U_inf)
+    f = s.rhs(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    Uref = U if prec == "fp64" else quantize32(U)
+    ref = _oracle(mesh, phys, Uref, U_inf)
+    err = rel_err(f.double().cpu().numpy(), ref)
+    record(name, rel=err, E=mesh.n_elem)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_dgip_2d_euler_periodic(p, prec):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(-1, 1, 7), I.uniform_edges(0, 1.3, 5)], [True, True])
+    _check(mesh, _euler(), I.random_state(mesh, 600 + p), prec, f"dgip-2d-euler-p{p}-{prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_dgip_2d_ns_walls_stretched(p, prec):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 7), I.wall_stretched_edges(3, 1.5)], [True, False])
+    _check(mesh, _ns(), I.random_state(mesh, 610 + p), prec, f"dgip-2d-ns-walls-p{p}-{prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_dgip_3d_boxes_walls(p, viscous, prec):
+    cells = {1: 3, 2: 3, 3: 2, 4: 2, 5: 2}[p]
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells), I.uniform_edges(0, 1.2, cells + 1),
+                                     I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    _check(mesh, _ns() if viscous else _euler(), I.random_state(mesh, 620 + p), prec,
+           f"dgip-3d-{'ns' if viscous else 'euler'}-p{p}-{prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_dgip_farfield(viscous, prec):
+    """Farfield boundaries (tag 1, App. B.1.1) on both ends of y."""
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 6), I.uniform_edges(0, 1, 4)], [True, False], wall_tag=1)
+    _check(mesh, _ns() if viscous else _euler(), I.random_state(mesh, 630), prec,
+           f"dgip-farfield-{'ns' if viscous else 'euler'}-{prec}", U_inf=UINF2)
+
+
+def test_dgip_single_element_self_periodic():
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 1), I.uniform_edges(0, 2, 1)], [True, True])
+    _check(mesh, _ns(), I.random_state(mesh, 7), "fp64", "dgip-self-periodic")
+
+
+def _vjp_check(mesh, phys, prec, name, U_inf=None, seed=640):
+    from oracle.vjp import vjp
+    U = I.random_state(mesh, seed)
+    lam = I.gaussian_cotangent(U.shape, seed + 1)
+    s = _solver(mesh, phys, prec, U_inf=U_inf)
+    g = s.rhs_vjp(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous(),
+                  torch.as_tensor(lam).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    if prec == "fp32":
+        U, lam = quantize32(U), quantize32(lam)
+    op = SIPGOperator(mesh, gas_of(phys), U_inf=U_inf)
+    ref = vjp(op, torch.as_tensor(U), torch.as_tensor(lam)).numpy()
+    err = rel_err(g.double().cpu().numpy(), ref)
+    record(name, rel=err, E=mesh.n_elem)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_dgip_vjp_2d_walls(p, viscous, prec):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])
+    _vjp_check(mesh, _ns() if viscous else _euler(), prec, f"dgip-vjp-2d-{viscous}-p{p}-{prec}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dgip_vjp_3d_walls(p, prec):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1.2, 3),
+                                     I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    _vjp_check(mesh, _ns(), prec, f"dgip-vjp-3d-p{p}-{prec}")
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_dgip_vjp_farfield(viscous):
+    mesh = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 4), I.uniform_edges(0, 1, 3)], [True, False], wall_tag=1)
+    _vjp_check(mesh, _ns() if viscous else _euler(), "fp64", f"dgip-vjp-farfield-{viscous}", U_inf=UINF2)
+
+
+def test_dgip_vjp_adjoint_identity_central_differences():
+    """<lambda, J v> by central differences of the GPU residual (step 1e-6 of
+    the state scale) against <J^T lambda, v> from the GPU adjoint."""
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 4), I.wall_stretched_edges(2, 1.3)], [True, False])
+    U = I.random_state(mesh, 650)
+    lam = I.gaussian_cotangent(U.shape, 651)
+    v = I.gaussian_cotangent(U.shape, 652) * np.abs(U)
+    s = _solver(mesh, _ns(), "fp64")
+    Ud = torch.as_tensor(U).cuda()
+    g = s.rhs_vjp(Ud, torch.as_tensor(lam).cuda()).cpu().numpy()
+    eps = 1e-6
+    fp = s.rhs(torch.as_tensor(U + eps * v).cuda()).cpu().numpy()
+    fm = s.rhs(torch.as_tensor(U - eps * v).cuda()).cpu().numpy()
+    s.check()
+    jv = (fp - fm) / (2 * eps)
+    lhs, rhs = float((lam * jv).sum()), float((g * v).sum())
+    record("dgip-adjoint-fd", rel=abs(lhs - rhs) / abs(rhs))
+    assert abs(lhs - rhs) < 1e-6 * abs(rhs), (lhs, rhs)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dgip_geometry_split_interface(dim, prec):
+    """R^DG(U^ex, U^im) with an implicit strip (Sec. 4.1): explicit elements
+    read U_ex, implicit ones U_im; interface faces against the implicit side."""
+    if dim == 2:
+        mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 6), I.wall_stretched_edges(2, 1.3)], [True, False])
+        col = np.arange(mesh.n_elem) % 6
+        explicit = (col != 2) & (col != 3)
+    else:
+        mesh = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 4), I.uniform_edges(0, 1, 2),
+                                         I.wall_stretched_edges(1, 1.0)], [True, True, False])
+        col = np.arange(mesh.n_elem) % 4
+        explicit = col != 1
+    phys = _ns()
+    Uex = I.random_state(mesh, 660)
+    Uim = I.random_state(mesh, 661)
+    s = _solver(mesh, phys, prec)
+    s.set_explicit_mask(explicit)
+    f = s.rhs_split(torch.as_tensor(Uex).to("cuda", _dt(prec)).contiguous(),
+                    torch.as_tensor(Uim).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    if prec == "fp32":
+        Uex, Uim = quantize32(Uex), quantize32(Uim)
+    ref = _oracle(mesh, phys, Uex, explicit=explicit, U_im=Uim)
+    got = f.double().cpu().numpy()
+    assert np.all(got[~explicit] == 0)
+    err = rel_err(got[explicit], ref[explicit])
+    record(f"dgip-split-{dim}d-{prec}", rel=err)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_mms_source_matches_symbolic(viscous, prec):
+    """The device source of Sec. 5.1.1 against dU_e/dt + div(F^c - F^nu)(U_e)
+    differentiated symbolically (sympy) from the fluxes of Sec. 2."""
+    mu = 0.01
+    phys = I.Physics(gamma=1.4, Re=1 / mu, Pr=0.72, Ma=0.3, viscous=viscous)
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 8)] * 2, [True, True])
+    fns = mms_sympy.build(2, 1.4, mu if viscous else 0.0, 0.72)
+    t = 0.0037
+    want = mms_sympy.evaluate(fns["Ut"], mesh.xyz, t) + mms_sympy.evaluate(fns["divFc"], mesh.xyz, t) \
+        - mms_sympy.evaluate(fns["divFv"], mesh.xyz, t)
+    for scheme in ("dgip", "llf-br1"):
+        from paper_2607_16044_b300.dgx import Solver
+        s = Solver(mesh, phys, prec, scheme=scheme)
+        out = torch.zeros(s.shape, dtype=_dt(prec), device="cuda")
+        s.mms_source(t, out)
+        s.check()
+        err = rel_err(out.double().cpu().numpy(), want)
+        assert err < (1e-13 if prec == "fp64" else 1e-6), (scheme, err)
+
+
+def test_dgip_ark_step_matches_oracle():
+    """One ARS(3,4,3) step of the DG-IP operator (fused stage updates, FP64
+    accumulation) against the oracle's ERK step."""
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.3)], [True, False])
+    phys = _ns()
+    U0 = I.random_state(mesh, 670)
+    dt = 2e-5
+    for prec in ("fp64", "fp32"):
+        s = _solver(mesh, phys, prec)
+        s.set_tableau(*ars343_explicit())
+        U = torch.as_tensor(U0).cuda()
+        s.ark_step(U, dt)
+        s.check()
+        op = SIPGOperator(mesh, gas_of(phys))
+        A, b, c = ark.ars343()
+        Uref = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b).numpy()
+        err = rel_err(U.cpu().numpy() - U0, Uref - U0)
+        record(f"dgip-ark-{prec}", rel=err)
+        assert err < TOL[prec], (prec, err)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dgip_channel2d_full_size_sampled(prec):
+    """256 x 128 wall-stretched channel, p = 4 (the 2D NS configuration), DG-IP:
+    sampled elements incl. both walls against the oracle on their 2-ring
+    sub-mesh; FP32 on the 10 %-perturbed state (well conditioned)."""
+    mesh, phys, _ = I.channel2d_workload()
+    U = I.channel_state(mesh, phys, 2, amp=0.1 if prec == "fp32" else 1e-3)
+    s = _solver(mesh, phys, prec)
+    f = s.rhs(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous()).double().cpu().numpy()
+    s.check()
+    rng = np.random.default_rng(9)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, 24, replace=False), [0, mesh.n_elem - 1]]))
+    Uref = U if prec == "fp64" else quantize32(U)
+    sub, keep, loc = submesh_around(mesh, rows, 2)
+    ref = SIPGOperator(sub, gas_of(phys)).residual(torch.as_tensor(Uref[keep])).numpy()[loc]
+    err = rel_err(f[rows], ref)
+    record(f"dgip-channel2d-{prec}", rel=err, sampled=len(rows))
+    assert err < TOL[prec], err
