@@ -225,6 +225,15 @@ dgx_status dgx_rhs_noalloc(dgx_handle* h, const void* U, void* dUdt, void* strea
  * fractions.  DGX_EINVAL for bad sizes or precision. */
 dgx_status dgx_probe_fma(int32_t precision, int64_t iters, void* out, int64_t threads, double* flops, void* stream);
 
+/* Bound of the consumer waits of the persistent TMA-fed kernels (polls of
+ * mbarrier.try_wait; default 2^22, the largest allowed; polls < 0 restores
+ * it).  A wait that runs out makes the CTA raise the timeout flag (dgx_check
+ * then returns DGX_ETIMEOUT), wait with the default bound for its own copies
+ * still in flight and return; the residual of its remaining tiles is not
+ * written.  Meant for exercising the timeout path: with polls = 0 every
+ * persistent CTA gives up at its first wait. */
+dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls);
+
 /* Farfield state U_inf (App. B.1.1, Eq. farfield_state) of the DG-IP scheme:
  * conservative (rho, rho u, .., rho E), nf host doubles, copied.  Required
  * before a residual on a mesh with farfield faces (else DGX_ESTATE). */

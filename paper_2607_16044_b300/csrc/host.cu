@@ -46,6 +46,7 @@ struct dgx_handle {
   dgx::Mesh<float> mesh32{};
   int nsm = 148;          // SMs of the device (persistent grids)
   int dev = 0;            // device that was current at dgx_create (owns every device table)
+  uint32_t wait_polls = 1u << 22;  // consumer-wait bound of the persistent kernels
   bool pipeline = true;   // persistent TMA-fed kernels where the layout allows
   int contraction = DGX_CONTRACT_CUDA_CORE;  // engine of the forward element kernel
   // second stream and fork / join events of dgx_ark_step_adjoint
@@ -243,6 +244,7 @@ dgx::Mesh<S> mesh_view(const dgx_handle* h) {
   M.gas.lam = (S)(-2.0 * mu / 3.0);
   M.gas.kcv = (S)(h->viscous ? g * mu / h->desc.Pr : 0.0);
   M.flags = h->d_flags;
+  M.wait_polls = h->wait_polls;
   return M;
 }
 
@@ -1344,6 +1346,14 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
               : ark_adjoint_impl<float>(h, stages, lam64, dt, ws_adj, st);
   if (cudaStreamWaitEvent(st, h->ev_join, 0) != cudaSuccess && s == DGX_OK) s = DGX_ECUDA;
   return s;
+}
+
+dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls) {
+  if (!h) return DGX_EINVAL;
+  h->wait_polls = polls < 0 ? (1u << 22) : (uint32_t)std::min<int64_t>(polls, 1u << 22);
+  h->mesh64.wait_polls = h->wait_polls;
+  h->mesh32.wait_polls = h->wait_polls;
+  return DGX_OK;
 }
 
 dgx_status dgx_set_farfield(dgx_handle* h, const double* U_inf) {

@@ -126,7 +126,8 @@ struct Mesh {
   Geo<S> geo;
   const Tab<S>* tabs;  // indexed by p
   Gas<S> gas;
-  unsigned* flags;     // bit 0: non-finite residual
+  unsigned* flags;     // bit 0: non-finite residual, bit 1: a bounded device wait gave up
+  uint32_t wait_polls; // bound of the persistent kernels' consumer waits (polls)
 };
 
 constexpr int MAXSTAGES = 8;

@@ -11,15 +11,18 @@
 namespace dgx {
 
 // Bounded-wait step shared by the persistent kernels: returns false (all
-// threads) if the copy of buffer b did not complete; then the kernel flags a
-// timeout and returns after a bounded wait for the other buffer's copies.
+// threads) if the copy of buffer b did not complete within `polls` polls; then
+// the kernel flags a timeout and returns after waiting (with the default
+// bound, whatever `polls` is) for the copies still in flight into both
+// buffers, so that no CTA leaves with a bulk copy outstanding.
 __device__ __forceinline__ bool pipe_acquire(PipeState& ps, int b, uint32_t& par, bool other_pending,
-                                             uint32_t other_par, unsigned* flags) {
-  if (threadIdx.x == 0) ps.abort = !mbar_wait_bounded(&ps.bar[b], par);
+                                             uint32_t other_par, unsigned* flags, uint32_t polls) {
+  if (threadIdx.x == 0) ps.abort = !mbar_wait_bounded(&ps.bar[b], par, polls);
   __syncthreads();
   if (ps.abort) {
     if (threadIdx.x == 0) {
       atomicOr(flags, 2u);
+      mbar_wait_bounded(&ps.bar[b], par);
       if (other_pending) mbar_wait_bounded(&ps.bar[b ^ 1], other_par);
     }
     return false;
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem_p(Mesh<S> M, Tile
     const int next = tile + gridDim.x;
     if (threadIdx.x == 0 && next < ntiles)
       tile_issue(in, next * T, min(T, M.E - next * T), T, buf(b ^ 1), &ps.bar[b ^ 1]);
-    if (!pipe_acquire(ps, b, par[b], next < ntiles, par[b ^ 1], M.flags)) return;
+    if (!pipe_acquire(ps, b, par[b], next < ntiles, par[b ^ 1], M.flags, M.wait_polls)) return;
     const int e0 = tile * T;
     const int nel = min(T, M.E - e0);
     // views into the buffer

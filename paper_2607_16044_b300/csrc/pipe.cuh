@@ -68,8 +68,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait (each try_wait suspends for a hardware-defined interval).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+constexpr uint32_t WAIT_POLLS = 1u << 22;  // default bound
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t polls = WAIT_POLLS) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (mbar_try(bar, parity)) return true;
   return false;
 }

@@ -47,7 +47,8 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_batch_create", "dgx_batch_destroy", "dgx_batch_layout", "dgx_batch_workspace_bytes",
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
-           "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source"]
+           "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source",
+           "dgx_set_wait_limit"]
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_kernel_name.restype = ctypes.c_char_p
     lib.dgx_probe_fma.argtypes = [i32, ctypes.c_int64, vp, ctypes.c_int64, ctypes.POINTER(dbl), vp]
     lib.dgx_set_farfield.argtypes = [vp, vp]
+    lib.dgx_set_wait_limit.argtypes = [vp, ctypes.c_int64]
     lib.dgx_set_explicit_mask.argtypes = [vp, vp]
     lib.dgx_rhs_split.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_mms_source.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp]

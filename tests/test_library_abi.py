@@ -46,6 +46,9 @@ def test_host_validation_without_gpu():
     from paper_2607_16044_b300 import dgx
     lib = dgx.load_library()
     assert lib.dgx_ark_step_adjoint(None, None, None, 1e-3, None, None, None) == 1
+    assert lib.dgx_set_wait_limit(None, 0) == 1
+    assert lib.dgx_rhs_split(None, None, None, None, None, None) == 1
+    assert lib.dgx_set_farfield(None, None) == 1
     assert lib.dgx_ark_step_stages(None, None, 1e-3, None, None, None) == 1
     assert lib.dgx_ark_adjoint_step(None, None, None, 1e-3, None, None) == 1
     assert lib.dgx_workspace_bytes(None, dgx.OP_ARK_STEP_ADJOINT) == 0
