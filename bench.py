@@ -541,32 +541,142 @@ def vortex_accuracy():
     return out
 
 
-def ensemble_perf(prec="fp32", reps=10):
+def ensemble_perf(reps=10, steps_err=20):
     """64 instances (8x8..96x96 quads, p in 2..5, Euler/NS) from the seeded
-    manifest, one batched ARK step per replay of its CUDA graph."""
+    manifest: one batched ARK step per CUDA-graph replay, in FP32 and FP64,
+    each in both batch forms (the graph of concurrent per-group launches and
+    the persistent form: one launch per phase over every group's tiles);
+    and, after steps_err steps, the density L2 error of the Euler vortex
+    instances against the exact translated vortex (largest over instances)."""
     import torch
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Batch, Solver
     from paper_2607_16044_b300.tableaux import ars343_explicit
     specs = I.ensemble_manifest()
-    sol, states = [], []
-    for sp in specs:
-        mesh, phys, U = I.ensemble_instance(sp)
-        so = Solver(mesh, phys, prec)
-        so.set_tableau(*ars343_explicit())
-        sol.append(so)
-        states.append(U)
-    b = Batch(sol, [sp["dt"] for sp in specs])
-    U = b.pack(states)
-    b.autotune(U, reps=2)
-    b.step(U)
-    b.step(U, graph=True)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    ms = _time_events(lambda: b.step(U, graph=True), reps, flush)
-    dofs = sum(int(np.prod(so.shape)) for so in sol)
-    return {"workload": "64-instance ensemble (seeded manifest), 1 batched ARS(3,4,3) step as one CUDA graph",
-            "instances": len(specs), "groups": b.groups, "dofs": dofs, "ms_per_step": round(ms, 4),
-            "dof_evals_per_s": round(4 * dofs / (ms / 1e3), 1), "dtype": prec}
+    out = {"workload": "64-instance ensemble (seeded manifest), 1 batched ARS(3,4,3) step per graph replay",
+           "instances": len(specs)}
+    for prec in ("fp32", "fp64"):
+        sol, states, meshes = [], [], []
+        for sp in specs:
+            mesh, phys, U = I.ensemble_instance(sp)
+            so = Solver(mesh, phys, prec)
+            so.set_tableau(*ars343_explicit())
+            sol.append(so)
+            states.append(U)
+            meshes.append(mesh)
+        b = Batch(sol, [sp["dt"] for sp in specs])
+        U = b.pack(states)
+        b.autotune(U, reps=2)
+        dofs = sum(int(np.prod(so.shape)) for so in sol)
+        r = {"groups": b.groups, "dofs": dofs}
+        best = None
+        for form in ("grouped", "persistent"):
+            b.set_persistent(form == "persistent")
+            U = b.pack(states)
+            b.step(U)
+            b.step(U, graph=True)
+            ms = _time_events(lambda: b.step(U, graph=True), reps, flush)
+            r[form + "_ms_per_step"] = round(ms, 4)
+            if best is None or ms < best[1]:
+                best = (form, ms)
+        b.set_persistent(best[0] == "persistent")
+        r["form"] = best[0]
+        r["ms_per_step"] = round(best[1], 4)
+        r["dof_evals_per_s"] = round(4 * dofs / (best[1] / 1e3), 1)
+        U = b.pack(states)
+        for _ in range(steps_err):
+            b.step(U, graph=True)
+        torch.cuda.synchronize()
+        errs = []
+        for k, (sp, mesh, Ui) in enumerate(zip(specs, meshes, b.unpack(U))):
+            if sp["viscous"]:
+                continue
+            w1 = np.polynomial.legendre.leggauss(sp["p"] + 1)[1]
+            w = np.outer(w1, w1).reshape(-1)
+            Jel = np.prod(mesh.size / 2, axis=1)
+            ex = I.isentropic_vortex(mesh, steps_err * sp["dt"], 1.4)[:, 0]
+            rho = Ui[:, 0].cpu().numpy()
+            errs.append(float(np.sqrt(np.sum((rho - ex) ** 2 * w[None, :] * Jel[:, None]) / 100.0)))
+        r["vortex_rho_L2_max"] = max(errs)
+        r["vortex_rho_L2_mean"] = float(np.mean(errs))
+        r["error_note"] = (f"after {steps_err} steps (t = {steps_err} dt_i per instance), Euler vortex instances "
+                           f"({len(errs)}) against the exact translated vortex")
+        b.close()
+        for so in sol:
+            so.close()
+        out[prec] = r
+    return out
+
+
+def dgip_perf(reps=5):
+    """The paper's DG-IP operator (Vijayasundaram flux + symmetric interior
+    penalty) on the 2D channel (256x128, p = 4) in FP32 and FP64 and on the 3D
+    channel (48^3, p = 5) in FP64: residual, VJP and one ARS(3,4,3) step, L2
+    flushed between repetitions; per-kernel work from the library's event
+    profiler; and the geometry-split residual R^DG(U^ex, U^im) of the 2D
+    channel with the 16 element rows next to each wall implicit."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    pk = peaks()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {}
+    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp64")):
+        mesh, phys, U0 = I.channel2d_workload() if wl == "channel2d" else I.channel3d_workload()
+        s = Solver(mesh, phys, prec, scheme="dgip")
+        s.set_tableau(*ars343_explicit())
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        U = torch.as_tensor(U0).to("cuda", dt).contiguous()
+        lam = torch.as_tensor(np.random.default_rng(102).standard_normal(U0.shape)).to("cuda", dt).contiguous()
+        f = s.rhs(U)
+        g = s.rhs_vjp(U, lam)
+        U64 = torch.as_tensor(U0).cuda()
+        # dt far below the explicit limit: the penalty on the 2e-5-thin wall
+        # cells makes |f| ~ 4e8 here (the stiffness the geometry split moves to
+        # the implicit region); the work of a step does not depend on dt
+        s.ark_step(U64, 1e-13)
+        ms_rhs = _time_events(lambda: s.rhs(U, out=f), reps, flush)
+        ms_vjp = _time_events(lambda: s.rhs_vjp(U, lam, out=g), reps, flush)
+        ms_ark = _time_events(lambda: s.ark_step(U64, 1e-13), reps, flush)
+        s.profile(True)
+        s.profile_reset()
+        for _ in range(reps):
+            flush.fill_(1)
+            s.rhs(U, out=f)
+            s.rhs_vjp(U, lam, out=g)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile(False)
+        s.check()
+        alu = alu_peak_tflops(prec)
+        kern = {}
+        for k, (nl, kms) in prof.items():
+            fl, by = s.kernel_work(k)
+            t = kms / nl / 1e3
+            kern[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1), "frac_hbm": round(by / t / 1e9 / pk["hbm_gbs"], 3),
+                       "TFLOP/s": round(fl / t / 1e12, 3), "frac_alu": round(fl / t / 1e12 / alu, 3)}
+        n = U.numel()
+        r = {"dofs": n, "ms_rhs": round(ms_rhs, 4), "ms_vjp": round(ms_vjp, 4), "ms_ark_step": round(ms_ark, 4),
+             "rhs_dof_evals_per_s": round(n / (ms_rhs / 1e3), 1), "vjp_dof_evals_per_s": round(n / (ms_vjp / 1e3), 1),
+             "ark_dof_evals_per_s": round(4 * n / (ms_ark / 1e3), 1), "per_kernel": kern,
+             "dominant": max(prof.items(), key=lambda kv: kv[1][1])[0]}
+        if wl == "channel2d" and prec == "fp64":   # geometry split: implicit near-wall strips
+            rows = mesh.shape[1]
+            j = np.arange(mesh.n_elem) // mesh.shape[0]
+            explicit = (j >= 16) & (j < rows - 16)
+            s.set_explicit_mask(explicit)
+            Uim = U.clone()
+            fs = s.rhs_split(U, Uim)
+            ms_split = _time_events(lambda: s.rhs_split(U, Uim, out=fs), reps, flush)
+            s.check()
+            r["split"] = {"explicit_elements": int(explicit.sum()), "ms_rhs_split": round(ms_split, 4)}
+        out[f"{wl}-{prec}"] = r
+        s.close()
+    out["workload"] = ("DG-IP (Vijayasundaram + SIPG, alpha = 1): 2D NS channel 256x128 p=4 and 3D NS channel "
+                       "48^3 p=5, residual / VJP / ARS(3,4,3) step")
+    return out
 
 
 def tgv_perf(reps=10, profile_range=False):
@@ -839,6 +949,7 @@ def main():
         line["channel2d"] = c2
         line["vortex_fp32_vs_fp64"] = vortex_accuracy()
         line["ensemble"] = ensemble_perf()
+        line["dgip"] = dgip_perf()
         line["tgv"] = tgv_perf()
         line["channel3d_trajectory"] = channel3d_trajectory()
     if rank == 0 and not args.no_cpu_baseline:

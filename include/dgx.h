@@ -392,6 +392,20 @@ dgx_status dgx_batch_step(dgx_batch* b, double* U64, void* workspace, void* stre
  * stream; later dt changes need no recapture.  Make a dgx_batch_step or
  * dgx_batch_autotune call first so kernel attributes are set outside capture. */
 dgx_status dgx_batch_step_graph(dgx_batch* b, double* U64, void* workspace, void* stream);
+/* Form of the batched step.  0 (default): each group runs its own kernels on
+ * its own stream (a graph of concurrent per-group launches).  1: persistent:
+ * one launch per phase of each stage (first traces, BR1 gradient, face
+ * fluxes, element + stage update) covers every group -- a grid of SMs x
+ * resident CTAs walks a work list of (group, element tile) items ordered by
+ * decreasing degree and runs, per item, the group's own tile arithmetic for
+ * its degree (256-thread tiles), so a step is 1 + 3 s launches whatever the
+ * number of groups, with identical results bit for bit.  The per-group
+ * inputs are tabulated in device memory the first time a step sees a (U64,
+ * workspace) pair (a synchronising set-up; make that call outside any stream
+ * capture: dgx_batch_step_graph does it before capturing).  Requires 2D box
+ * meshes, the CUDA-core contraction and one precision for all instances,
+ * else DGX_EUNSUPPORTED. */
+dgx_status dgx_batch_set_persistent(dgx_batch* b, int32_t enable);
 /* Autotune every group on the packed state U64 (see dgx_autotune). */
 dgx_status dgx_batch_autotune(dgx_batch* b, const double* U64, int32_t reps, void* stream);
 

@@ -117,6 +117,7 @@ def _write_sources():
     units.append(os.path.join(CSRC, "host.cu"))
     units.append(os.path.join(CSRC, "noalloc.cu"))
     units.append(os.path.join(CSRC, "probe.cu"))
+    units.append(os.path.join(CSRC, "batchp.cu"))
     return units
 
 

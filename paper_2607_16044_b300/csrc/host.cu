@@ -19,6 +19,7 @@
 #include "vjp.cuh"
 #include "dgip.cuh"
 #include "mms.cuh"
+#include "batchp.h"
 
 using dgx::Tab;
 
@@ -1586,6 +1587,15 @@ struct dgx_batch {
   cudaGraphExec_t exec = nullptr;
   double* g_U = nullptr;
   void* g_ws = nullptr;
+  // persistent form: one launch per phase over every group's work items
+  bool pers_ok = false;                // 2D boxes, CUDA-core contraction, one precision
+  bool persistent = false;
+  int nsm = 148;
+  dgx::BItem* d_items = nullptr;       // the phases' item lists, concatenated
+  int n_items[4] = {}, item_off[4] = {};
+  void* d_groups = nullptr;            // BGroup<S>[groups] for the prepared (U64, workspace)
+  double* p_U = nullptr;
+  void* p_ws = nullptr;
 };
 
 namespace {
@@ -1597,6 +1607,8 @@ bool same_group(const dgx_handle* a, const dgx_handle* b) {
 
 void batch_free(dgx_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_groups) cudaFree(b->d_groups);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->start) cudaEventDestroy(b->start);
   for (auto& g : b->groups) {
@@ -1608,10 +1620,87 @@ void batch_free(dgx_batch* b) {
   delete b;
 }
 
+// Persistent form: the per-group inputs of one ARK step (what ark_impl passes
+// each group's kernels, with the per-element time step) uploaded once per
+// (state, workspace) pair.
+template <typename S>
+dgx_status batch_prepare_t(dgx_batch* b, double* U64, void* ws) {
+  std::vector<dgx::BGroup<S>> G(b->groups.size());
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    const auto& g = b->groups[k];
+    dgx_handle* h = g.h;
+    dgx::BGroup<S>& B = G[k];
+    B.M = *(const dgx::Mesh<S>*)(h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32);
+    B.P = h->p;
+    B.visc = h->viscous ? 1 : 0;
+    char* base = (char*)ws + g.ws_off;
+    const Layout L = layout(h, DGX_OP_ARK);
+    B.w = work_at(h, base, L);
+    double* Ug = U64 + g.off;
+    B.U64 = Ug;
+    const size_t state = align256((size_t)h->E * h->nf * h->N * h->s);
+    S* Y = (S*)(base + L.Y);
+    S* shadow = h->fp64 ? nullptr : (S*)(base + L.SH);
+    B.first = shadow;
+    const S* y0 = h->fp64 ? (const S*)Ug : shadow;
+    const int s = h->stages;
+    for (int i = 0; i < s; ++i) {
+      dgx::Stage<S> sa{};
+      for (int j = 0; j < i; ++j) sa.k[j] = (const S*)(base + L.K + state * j);
+      sa.i = i;
+      sa.last = (i == s - 1);
+      if (!sa.last)
+        for (int j = 0; j <= i; ++j) sa.ca[j] = (S)h->A[(i + 1) * dgx::MAXSTAGES + j];
+      for (int j = 0; j < s; ++j) sa.cb[j] = (S)h->b[j];
+      sa.dte = (const S*)g.d_dte;
+      sa.base = y0;
+      sa.Un = Ug;
+      sa.Y = Y;
+      sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
+      sa.shadow = shadow;
+      sa.TU = (S*)B.w.TU;
+      B.st[i] = sa;
+      B.Uin[i] = (i == 0) ? y0 : Y;
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return DGX_ECUDA;  // no launch still reads the old table
+  if (!b->d_groups && cudaMalloc(&b->d_groups, G.size() * sizeof(dgx::BGroup<S>)) != cudaSuccess) return DGX_ENOMEM;
+  if (cudaMemcpy(b->d_groups, G.data(), G.size() * sizeof(dgx::BGroup<S>), cudaMemcpyHostToDevice) != cudaSuccess)
+    return DGX_ECUDA;
+  b->p_U = U64;
+  b->p_ws = ws;
+  return DGX_OK;
+}
+
+dgx_status batch_prepare(dgx_batch* b, double* U64, void* ws) {
+  if (b->p_U == U64 && b->p_ws == ws && b->d_groups) return DGX_OK;
+  return b->groups[0].h->fp64 ? batch_prepare_t<double>(b, U64, ws) : batch_prepare_t<float>(b, U64, ws);
+}
+
+template <typename S>
+dgx_status batch_run_persistent_t(dgx_batch* b, cudaStream_t st) {
+  const auto* G = (const dgx::BGroup<S>*)b->d_groups;
+  auto phase = [&](int ph, int stage) {
+    return dgx::batch_phase<S>(ph, stage, G, b->d_items + b->item_off[ph], b->n_items[ph], b->nsm, st);
+  };
+  cudaError_t e = phase(0, 0);
+  const int s = b->groups[0].h->stages;
+  for (int i = 0; i < s && e == cudaSuccess; ++i) {
+    if (b->n_items[1] > 0) e = phase(1, i);
+    if (e == cudaSuccess) e = phase(2, i);
+    if (e == cudaSuccess) e = phase(3, i);
+  }
+  return cuda_status(e);
+}
+
 // Every group's step on its own stream (disjoint state ranges and workspace
 // slices), forked from and joined back to st by events, so small groups'
 // kernels overlap instead of running one group after another.
 dgx_status batch_run(dgx_batch* b, double* U64, void* ws, cudaStream_t st) {
+  if (b->persistent) {  // tables prepared for (U64, ws) by the caller, outside any capture
+    if (b->p_U != U64 || b->p_ws != ws) return DGX_ESTATE;
+    return b->groups[0].h->fp64 ? batch_run_persistent_t<double>(b, st) : batch_run_persistent_t<float>(b, st);
+  }
   if (cudaEventRecord(b->start, st) != cudaSuccess) return DGX_ECUDA;
   dgx_status s = DGX_OK;
   for (auto& g : b->groups) {
@@ -1723,6 +1812,32 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
     b->ws_bytes += dgx_workspace_bytes(g.h, DGX_OP_ARK);
   }
   b->offset[count] = off;
+  if (st == DGX_OK) {  // the persistent form's work items (largest degree first)
+    b->pers_ok = true;
+    for (const auto& g : b->groups)
+      b->pers_ok = b->pers_ok && g.h->d == 2 && !g.h->curv && g.h->contraction == DGX_CONTRACT_CUDA_CORE &&
+                   g.h->fp64 == b->groups[0].h->fp64;
+    b->nsm = b->groups[0].h->nsm;
+    if (b->pers_ok) {
+      std::vector<dgx::BItem> all;
+      std::vector<int> order(b->groups.size());
+      for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return b->groups[x].h->p > b->groups[y].h->p; });
+      for (int ph = 0; ph < 4; ++ph) {
+        b->item_off[ph] = (int)all.size();
+        for (int k : order) {
+          const dgx_handle* h = b->groups[k].h;
+          if (ph == 1 && !h->viscous) continue;
+          const int units = ph == 2 ? (h->nFaces * h->nfp + 255) / 256
+                                    : (h->E + dgx::batch_tile_elems(h->p) - 1) / dgx::batch_tile_elems(h->p);
+          for (int u = 0; u < units; ++u) all.push_back(dgx::BItem{k, u});
+        }
+        b->n_items[ph] = (int)all.size() - b->item_off[ph];
+      }
+      if (upload(all, (void**)&b->d_items) != DGX_OK) b->pers_ok = false;
+    }
+  }
   if (st == DGX_OK && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) st = DGX_ECUDA;
   if (st == DGX_OK && cudaEventCreateWithFlags(&b->start, cudaEventDisableTiming) != cudaSuccess) st = DGX_ECUDA;
   if (st != DGX_OK) {
@@ -1777,7 +1892,22 @@ dgx_status dgx_batch_set_dt(dgx_batch* b, const double* dt) {
 dgx_status dgx_batch_step(dgx_batch* b, double* U64, void* workspace, void* stream) {
   if (!b || !U64 || !workspace || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (!b->dt_set) return DGX_ESTATE;
+  if (b->persistent) {
+    const dgx_status s = batch_prepare(b, U64, workspace);
+    if (s != DGX_OK) return s;
+  }
   return batch_run(b, U64, workspace, (cudaStream_t)stream);
+}
+
+dgx_status dgx_batch_set_persistent(dgx_batch* b, int32_t enable) {
+  if (!b) return DGX_EINVAL;
+  if (enable && !b->pers_ok) return DGX_EUNSUPPORTED;
+  if (b->persistent != (enable != 0) && b->exec) {  // the captured graph is of the other form
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->persistent = enable != 0;
+  return DGX_OK;
 }
 
 dgx_status dgx_batch_step_graph(dgx_batch* b, double* U64, void* workspace, void* stream) {
@@ -1787,6 +1917,10 @@ dgx_status dgx_batch_step_graph(dgx_batch* b, double* U64, void* workspace, void
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
+    }
+    if (b->persistent) {  // the tables must exist before the capture starts
+      const dgx_status s = batch_prepare(b, U64, workspace);
+      if (s != DGX_OK) return s;
     }
     if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) return DGX_ECUDA;
     const dgx_status s = batch_run(b, U64, workspace, b->cap);

@@ -284,19 +284,26 @@ __device__ __forceinline__ void tile_traces(const S* us, int nel, S* dst) {  // 
 // k_trace: TU = traces of U (input may be double while S is float: the FP32
 // ARK path converts the FP64 master state here and keeps the rounded copy).
 // ---------------------------------------------------------------------------
+// One element tile (also the unit of work of the persistent batched kernels).
 template <int D, int P, typename S, typename Sin, int V>
-__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin* __restrict__ U,
-                                                                S* __restrict__ TU, S* __restrict__ shadow,
-                                                                const Tab<S>* tabs) {
+__device__ __forceinline__ void trace_tile(int tile, unsigned char* smem_raw, int E, const Sin* __restrict__ U,
+                                           S* __restrict__ TU, S* __restrict__ shadow) {
   using H = Sh<D, P, V>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_trace_g<D, P, S, V>()));
-  const int e0 = g_index<V>() * H::T;
+  const int e0 = tile * H::T;
   const int nel = min(H::T, E - e0);
   stage_nodes<D, P, S, V, H::nf>(us, U + (size_t)e0 * H::STATE, nel,
                                   shadow ? shadow + (size_t)e0 * H::STATE : nullptr);
   g_sync<V>();
   tile_traces<D, P, S, V>(us, nel, TU + (size_t)e0 * H::FACE);
+}
+
+template <int D, int P, typename S, typename Sin, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin* __restrict__ U,
+                                                                S* __restrict__ TU, S* __restrict__ shadow,
+                                                                const Tab<S>* tabs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  trace_tile<D, P, S, Sin, V>(g_index<V>(), smem_raw, E, U, TU, shadow);
 }
 
 // ---------------------------------------------------------------------------
@@ -308,20 +315,18 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
 // one thread per line: the line is loaded once and all n outputs produced.
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool CURV, int V>
-__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
-                                                              const S* __restrict__ TU, S* __restrict__ Q,
-                                                              S* __restrict__ G) {
+__device__ __forceinline__ void br1_tile(int tile, unsigned char* smem_raw, const Mesh<S>& M, const S* __restrict__ U,
+                                         const S* __restrict__ TU, S* __restrict__ Q, S* __restrict__ G) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_br1_g<D, P, S, V>()));     // [T][nf][N]
+    S* us = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_br1_g<D, P, S, V>()));     // [T][nf][N]
   S* js = us + T * H::STATE;                   // [T][NF][nf][nfp]     jumps
   S* qs = js + T * H::FACE;                    // [T][D][nf][N]        Q
   S* tq = qs + T * D * H::STATE;               // [T][NF][D][nf][nfp]  traces of Q
   S* Lm = tq + T * NF * D * nf * nfp;         // node-indexed lift weights (curvilinear)
   S* Lp = Lm + n;
-  const int e0 = g_index<V>() * T;
+  const int e0 = tile * T;
   const int nel = min(T, M.E - e0);
   stage_nodes<D, P, S, V, nf>(us, U + (size_t)e0 * H::STATE, nel);
   load_tab<S, V>(M.tabs, P, nullptr, nullptr, Lm, Lp, n);  // node-indexed lift (curvilinear)
@@ -528,6 +533,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
   }
 }
 
+template <int D, int P, typename S, bool CURV, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
+                                                              const S* __restrict__ TU, S* __restrict__ Q,
+                                                              S* __restrict__ G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  br1_tile<D, P, S, CURV, V>(g_index<V>(), smem_raw, M, U, TU, Q, G);
+}
+
 // ---------------------------------------------------------------------------
 // k_face: one thread per unique face point.  Fhat = LLF(U^-, U^+; n) - Fhat^nu,
 // Fhat^nu = (G^- - G^+)/2 inside, G^- on walls; written as +Fhat to the owner
@@ -535,11 +548,10 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S
 // averaged area normal of the face.
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool VISC, bool CURV>
-__global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ G,
-                                              S* __restrict__ FF) {
+__device__ __forceinline__ void face_point(int gid, const Mesh<S>& M, const S* __restrict__ TU,
+                                           const S* __restrict__ G, S* __restrict__ FF) {
   using H = Sh<D, P>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= M.nFaces * nfp) return;
   const int F = gid / nfp, fp = gid % nfp;
   const int4 rec = M.faces[F];
@@ -587,6 +599,12 @@ __global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ T
 #pragma unroll
     for (int f = 0; f < nf; ++f) orr[f * nfp] = -Fc[f];
   }
+}
+
+template <int D, int P, typename S, bool VISC, bool CURV>
+__global__ void __launch_bounds__(256) k_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ G,
+                                              S* __restrict__ FF) {
+  face_point<D, P, S, VISC, CURV>(blockIdx.x * blockDim.x + threadIdx.x, M, TU, G, FF);
 }
 
 // ---------------------------------------------------------------------------
@@ -739,17 +757,16 @@ __device__ __forceinline__ void flag_nonfinite(const S (&res)[nf], unsigned* fla
 // stage state's traces.
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool VISC, bool CURV, int MODE, int V>
-__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const S* U,
-                                                               const S* __restrict__ Q, const S* __restrict__ FF,
-                                                               S* __restrict__ out, Stage<S> st) {
+__device__ __forceinline__ void elem_tile(int tile, unsigned char* smem_raw, const Mesh<S>& M, const S* U,
+                                          const S* __restrict__ Q, const S* __restrict__ FF, S* __restrict__ out,
+                                          const Stage<S>& st) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int FES = elem_flux_stride<D, P, V>(), SES = elem_state_stride<D, P, V>();
   S* fs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_elem_g<D, P, S, V>()));   // [T][D][nf][N] (stride FES), then the next state [T][nf][N] (stride SES)
   S* ffs = fs + T * FES;                     // [T][NF][nf][nfp]
-  const int e0 = g_index<V>() * T;
+  const int e0 = tile * T;
   const int nel = min(T, M.E - e0);
   stage_faces<D, P, S, V>(ffs, FF + (size_t)e0 * H::FACE, nel);
   const int t = g_tid<V>() / N, q = g_tid<V>() % N;
@@ -839,6 +856,14 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const 
   }
   g_sync<V>();
   tile_traces<D, P, S, V, SES>(fs, nel, st.TU + (size_t)e0 * H::FACE);
+}
+
+template <int D, int P, typename S, bool VISC, bool CURV, int MODE, int V>
+__global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_elem(Mesh<S> M, const S* U,
+                                                               const S* __restrict__ Q, const S* __restrict__ FF,
+                                                               S* __restrict__ out, Stage<S> st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  elem_tile<D, P, S, VISC, CURV, MODE, V>(g_index<V>(), smem_raw, M, U, Q, FF, out, st);
 }
 
 }  // namespace dgx

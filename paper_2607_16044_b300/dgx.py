@@ -48,7 +48,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
            "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source",
-           "dgx_set_wait_limit"]
+           "dgx_set_wait_limit", "dgx_batch_set_persistent"]
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_probe_fma.argtypes = [i32, ctypes.c_int64, vp, ctypes.c_int64, ctypes.POINTER(dbl), vp]
     lib.dgx_set_farfield.argtypes = [vp, vp]
     lib.dgx_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    lib.dgx_batch_set_persistent.argtypes = [vp, i32]
     lib.dgx_set_explicit_mask.argtypes = [vp, vp]
     lib.dgx_rhs_split.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_mms_source.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp]
@@ -546,6 +547,11 @@ class Batch:
         fn = self.lib.dgx_batch_step_graph if graph else self.lib.dgx_batch_step
         _check(fn(self.b, self._packed(U), self.ws, _stream_ptr(stream)), "dgx_batch_step")
         return U
+
+    def set_persistent(self, enable: bool = True):
+        """One persistent launch per phase over all groups (True) or the graph
+        of concurrent per-group launches (False)."""
+        _check(self.lib.dgx_batch_set_persistent(self.b, int(bool(enable))), "dgx_batch_set_persistent")
 
     def autotune(self, U, reps: int = 3, stream=None):
         _check(self.lib.dgx_batch_autotune(self.b, self._packed(U), int(reps), _stream_ptr(stream)),

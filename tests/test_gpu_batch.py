@@ -8,7 +8,7 @@ import torch
 from oracle import ark
 from oracle.residual import DGOperator
 from paper_2607_16044_b300 import inputs as I
-from tests.parity_util import gas_of, rel_err
+from tests.parity_util import gas_of, record, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -108,3 +108,62 @@ def test_autotune_keeps_results():
     assert all(x in (0, 1, 2, 3) for x in v.values())
     f1 = s.rhs(Ua.float())
     assert torch.equal(f0, f1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_persistent_batch_bit_identical_to_groups(prec):
+    """The persistent form (one launch per phase over every group's tiles)
+    runs the groups' own tile arithmetic: identical states after eager and
+    graph-replayed steps."""
+    from paper_2607_16044_b300.dgx import Batch
+    insts = _instances()
+    dts = [sp["dt"] for sp, *_ in insts]
+    states = [U0 for *_, U0 in insts]
+    out = []
+    for persistent in (False, True):
+        b = Batch(_solvers(insts, prec), dts)
+        b.set_persistent(persistent)
+        U = b.pack(states)
+        for _ in range(2):
+            b.step(U)
+        Ug = U.clone()
+        for _ in range(2):
+            b.step(Ug, graph=True)
+        torch.cuda.synchronize()
+        out.append((U, Ug))
+    if prec == "fp64":
+        assert torch.equal(out[0][0], out[1][0])
+        assert torch.equal(out[0][1], out[1][1])
+    else:
+        # FP32: the same source inlined into another kernel may contract a
+        # multiply-add differently, so the states agree to FP32 rounding
+        for a, b in ((out[0][0], out[1][0]), (out[0][1], out[1][1])):
+            dev = float(((a - b).abs().max() / a.abs().max()).item())
+            record("persistent-batch-fp32-dev", rel=dev)
+            assert dev < 1e-6, dev
+
+
+def test_persistent_batch_ensemble_manifest():
+    """The 64-instance seeded ensemble (8 groups): persistent form against the
+    grouped form, one graph-replayed FP32 step."""
+    from paper_2607_16044_b300.dgx import Batch, Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    specs = I.ensemble_manifest()
+    res = []
+    for persistent in (False, True):
+        sol, states = [], []
+        for sp in specs:
+            mesh, phys, U0 = I.ensemble_instance(sp)
+            so = Solver(mesh, phys, "fp32")
+            so.set_tableau(*ars343_explicit())
+            sol.append(so)
+            states.append(U0)
+        b = Batch(sol, [sp["dt"] for sp in specs])
+        b.set_persistent(persistent)
+        U = b.pack(states)
+        b.step(U, graph=True)
+        torch.cuda.synchronize()
+        res.append(U)
+    dev = float(((res[0] - res[1]).abs().max() / res[0].abs().max()).item())
+    record("persistent-ensemble-fp32-dev", rel=dev)
+    assert dev < 1e-6, dev
