@@ -403,3 +403,106 @@ def neighbour_value(brute, e, a, side, xi, U, value):
     x = brute.x0[e] + brute.A[e] @ xi
     xin = brute.locate(nb, x)
     return nb, xin, value(nb, xin)
+
+
+class BruteHDG(BruteSIPG):
+    """Dense brute-force evaluation of the HDG-IP element and facet forms of
+    Sec. 3.4 (App. B.2 on boundaries) on tiny affine meshes; pins ``hdg``.
+    Independent of ``hdg``/``sipg``: its own Lagrange polynomials and
+    quadrature (as ``BruteSIPG``), and the flux split A_n^{+-}(Uhat) from a
+    numerical eigen-decomposition of the Jacobian obtained by differentiating
+    the normal flux (not from the closed-form eigenvectors).  Returns the
+    element residual (the form tested with each nodal basis function, before
+    any mass inverse) and the facet residual (tested with each face-point
+    basis function), in ``hdg``'s layouts.  |A| is the principal square root
+    of A^2 (Schur-based ``scipy.linalg.sqrtm``; A has real eigenvalues and is
+    diagonalisable), A^{+-} = (A +- |A|)/2."""
+
+    def _split(self, Uh, Sn):
+        import scipy.linalg
+        d = self.d
+        f = lambda u: ph.normal_convective_flux(u[None], _t(Sn[None]), self.gas, d)[0]
+        A = torch.autograd.functional.jacobian(f, _t(Uh)).numpy()
+        absA = np.real(scipy.linalg.sqrtm(A @ A))
+        return 0.5 * (A + absA), 0.5 * (A - absA)
+
+    def residual_hdg(self, U, Uhat, alpha=10.0, U_inf=None):
+        d, n, N, nf = self.d, self.n, self.N, self.nf
+        mesh, gas = self.mesh, self.gas
+        E = mesh.n_elem
+        nfp = n ** (d - 1)
+        U = np.asarray(U, dtype=np.float64)
+        Uhat = np.asarray(Uhat, dtype=np.float64)
+        quad = list(itertools.product(range(len(self.xq)), repeat=d))
+        qpts = [(np.array([self.xq[i[a]] for a in range(d)]), np.prod([self.wq[i[a]] for a in range(d)]))
+                for i in quad]
+        tab = [self.basis_at(x) for x, _ in qpts]
+        Ainvs = [np.linalg.inv(self.A[e]) for e in range(E)]
+        Js = [abs(np.linalg.det(self.A[e])) for e in range(E)]
+        nodes_ref = [np.array([self.L.x[m[a]] for a in range(d)]) for m in self.multi]
+        _, wg = np.polynomial.legendre.leggauss(n)
+        gw = ph.Gas(gas.gamma, Re=1.0 / gas.mu if gas.mu > 0 else 0.0, Pr=gas.Pr, viscous=gas.viscous)
+        gw.k_over_cv = 0.0
+
+        def T(x):
+            return _t(np.asarray(x)[None])
+
+        def visc(Uf, G, g):
+            return ph.viscous_flux(T(Uf), T(G), g, d).numpy()[0]
+
+        R = np.zeros((E, nf, N))
+        H = np.zeros((E, 2 * d, nf, nfp))
+        for e in range(E):
+            B = np.zeros((nf, N))
+            Fn = np.zeros((N, d, nf))
+            for r in range(N):
+                Ur = U[e][:, r]
+                _, gref = self.basis_at(nodes_ref[r])
+                Fr = ph.convective_flux(T(Ur), gas, d).numpy()[0]
+                if gas.viscous:
+                    Fr = Fr - visc(Ur, (U[e] @ (gref @ Ainvs[e])).T, gas)
+                Fn[r] = Fr
+            for (x, w), (phi, gref) in zip(qpts, tab):
+                gx = gref @ Ainvs[e]
+                B -= w * Js[e] * np.einsum("if,qi->fq", np.einsum("r,rif->if", phi, Fn), gx)
+            area = sum(np.linalg.norm(self.normal(e, a, s)) * 2.0 ** (d - 1) for a in range(d) for s in (0, 1))
+            tau = alpha * (mesh.p + 1) ** 2 * area / (Js[e] * 2.0 ** d)
+            for a in range(d):
+                for side in (0, 1):
+                    fid = 2 * a + side
+                    pts, rest = self.face_points(a, side)
+                    Sn = self.normal(e, a, side)
+                    sJ = np.linalg.norm(Sn)
+                    kind = mesh.neighbor[e, fid]
+                    g = gw if kind == -1 else gas
+                    vals = np.zeros((len(pts), nf))
+                    hv = np.zeros((len(pts), d, nf))
+                    for m, (xi, idx) in enumerate(pts):
+                        # hdg's face-point index: the first remaining direction fastest
+                        fp = sum(idx[k] * n ** k for k in range(d - 1))
+                        Uh = Uhat[e, fid, :, fp]
+                        phi, gref = self.basis_at(xi)
+                        Um = U[e] @ phi
+                        Gm = (U[e] @ (gref @ Ainvs[e])).T
+                        Ap, Am = self._split(Uh, Sn)
+                        dl = Um - Uh
+                        Kd = visc(Uh, outer_(dl, Sn), g)
+                        vals[m] = Ap @ Um + Am @ Uh - visc(Uh, Gm, g).T @ Sn + tau / sJ * Kd.T @ Sn
+                        hv[m] = Kd
+                        wf = np.prod([wg[i] for i in idx]) if d > 1 else 1.0
+                        if kind == -1:
+                            H[e, fid, :, fp] = wf * sJ * (Uh - ph.wall_state(T(Um), d).numpy()[0])
+                        elif kind == -2:
+                            Ui = np.asarray(U_inf, dtype=np.float64)
+                            H[e, fid, :, fp] = wf * (Ap @ (Uh - Um) - Am @ (Uh - Ui))
+                        else:
+                            H[e, fid, :, fp] = -wf * vals[m]
+                    B += self._face_integral(e, a, side, pts, rest, vals, None)
+                    if gas.viscous:
+                        B -= self._face_integral(e, a, side, pts, rest, None, hv, Ainvs[e])
+            R[e] = B
+        return R, H
+
+
+def outer_(delta, Sn):
+    return np.outer(Sn, delta)
