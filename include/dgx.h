@@ -69,7 +69,8 @@ typedef enum {
   DGX_OP_VJP = 1,
   DGX_OP_ARK = 2,
   DGX_OP_ARK_ADJOINT = 3,
-  DGX_OP_ARK_STEP_ADJOINT = 4 /* dgx_ark_step_adjoint */
+  DGX_OP_ARK_STEP_ADJOINT = 4, /* dgx_ark_step_adjoint */
+  DGX_OP_HDG = 5               /* dgx_hdg_condense */
 } dgx_op;
 
 /* Spatial scheme: convective numerical flux and viscous discretisation.
@@ -233,6 +234,38 @@ dgx_status dgx_probe_fma(int32_t precision, int64_t iters, void* out, int64_t th
  * written.  Meant for exercising the timeout path: with polls = 0 every
  * persistent CTA gives up at its first wait. */
 dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls);
+
+/* Element-local blocks of the implicit region's Newton system (Sec. 4.3) for
+ * the HDG-IP discretisation of Sec. 3.4 (no mixed variables: the element
+ * unknowns are U), FP64 handles on 2D box meshes (else DGX_EUNSUPPORTED):
+ * for every element T, with its nodal state U (device [E][nf][N]) and the
+ * facet state Uhat on its faces (device [E][2d][nf][n], the element's own
+ * face-point order), the element form R_T (Eq.
+ * bilinear_form_interior_hdg_ip_element with the HDG flux of Eq.
+ * inviscid_numerical_flux, S_c = A_n^+(Uhat); K_w on adiabatic walls) and the
+ * facet form h_T (Eq. bilinear_form_interior_hdg_ip_facet; the farfield and
+ * no-slip transmission conditions of App. B.2 on boundary facets), both tested
+ * with the nodal / facet basis, and the blocks of an SDIRK stage
+ * M y + gamma R(y, yhat) = rhs (gamma = dt a_ii, M = diag(w_q J_q)):
+ *   K = M + gamma dR/dU [E][nu][nu],  C = gamma dR/dUhat [E][nu][nh],
+ *   D = dh/dU [E][nh][nu],            A33 = dh/dUhat [E][nh][nh]
+ * (row-major; nu = nf N element DOFs in U's order, nh = 2d nf n facet DOFs in
+ * Uhat's order; see dgx_hdg_sizes), by forward-mode differentiation of the
+ * forms (one thread per element and column).  tau = 10 (k+1)^2 / l (the
+ * paper's HDG-IP alpha).  R and h (device [E][nu], [E][nh]) receive the forms'
+ * values when not NULL.  The global facet assembly and solve are the
+ * caller's. */
+dgx_status dgx_hdg_sizes(const dgx_handle* h, int32_t* nu, int32_t* nh);
+dgx_status dgx_hdg_blocks(dgx_handle* h, const double* U, const double* Uhat, double gamma, double* K, double* C,
+                          double* D, double* A33, double* R, double* hres, void* stream);
+/* Static condensation of the element blocks (Eq. SchurCompliment,
+ * local_solve_static_condensation): KinvC = K^{-1} C [E][nu][nh] (the local
+ * recovery operator) and S = A33 - D K^{-1} C [E][nh][nh] (the element's
+ * contribution to the Schur complement), by Gauss-Jordan elimination with
+ * partial pivoting, one CTA per element.  Workspace: E nu nu doubles
+ * (dgx_workspace_bytes(h, DGX_OP_HDG)), 256-byte aligned. */
+dgx_status dgx_hdg_condense(dgx_handle* h, const double* K, const double* C, const double* D, const double* A33,
+                            double* KinvC, double* S, void* workspace, void* stream);
 
 /* Farfield state U_inf (App. B.1.1, Eq. farfield_state) of the DG-IP scheme:
  * conservative (rho, rho u, .., rho E), nf host doubles, copied.  Required

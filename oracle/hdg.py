@@ -153,10 +153,10 @@ class HDGIPLocal(SIPGOperator):
             R, h = self.forms(u.reshape(U.shape), uh.reshape(Uhat.shape))
             return R.reshape(E, nu), h.reshape(E, nh)
 
-        JR_u = torch.autograd.functional.jacobian(lambda u: fn(u, Uhat.reshape(-1))[0], U.reshape(-1))
-        JR_h = torch.autograd.functional.jacobian(lambda uh: fn(U.reshape(-1), uh)[0], Uhat.reshape(-1))
-        Jh_u = torch.autograd.functional.jacobian(lambda u: fn(u, Uhat.reshape(-1))[1], U.reshape(-1))
-        Jh_h = torch.autograd.functional.jacobian(lambda uh: fn(U.reshape(-1), uh)[1], Uhat.reshape(-1))
+        JR_u = torch.autograd.functional.jacobian(lambda u: fn(u, Uhat.reshape(-1))[0], U.reshape(-1), vectorize=True)
+        JR_h = torch.autograd.functional.jacobian(lambda uh: fn(U.reshape(-1), uh)[0], Uhat.reshape(-1), vectorize=True)
+        Jh_u = torch.autograd.functional.jacobian(lambda u: fn(u, Uhat.reshape(-1))[1], U.reshape(-1), vectorize=True)
+        Jh_h = torch.autograd.functional.jacobian(lambda uh: fn(U.reshape(-1), uh)[1], Uhat.reshape(-1), vectorize=True)
         # element-diagonal blocks: rows of element e against its own columns
         ar = torch.arange(E)
         JR_u = JR_u.reshape(E, nu, E, nu)[ar, :, ar]

@@ -118,6 +118,7 @@ def _write_sources():
     units.append(os.path.join(CSRC, "noalloc.cu"))
     units.append(os.path.join(CSRC, "probe.cu"))
     units.append(os.path.join(CSRC, "batchp.cu"))
+    units.append(os.path.join(CSRC, "hdg.cu"))
     return units
 
 

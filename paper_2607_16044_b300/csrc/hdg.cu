@@ -1,0 +1,332 @@
+// Element-local blocks of the implicit region's HDG-IP Newton system
+// (Sec. 3.4 element and facet forms, Sec. 4.3 static condensation), FP64,
+// 2D box meshes.
+//
+// k_hdg_jacobian: one thread per (element, input column).  The element's
+// residual R_T (the HDG-IP element form tested with each nodal basis
+// function) and facet residual h_T (the transmission form tested with each
+// facet basis function) are evaluated serially by that thread with
+// forward-mode dual numbers seeded on its column (an element DOF or a facet
+// DOF), which yields column j of
+//   K = M + gamma dR/dU,  C = gamma dR/dUhat,  D = dh/dU,  A33_T = dh/dUhat.
+// With unit normals on boxes (r_a = 2/h_a, J = prod h_a/2, area factor
+// J r_a0 on a face normal to a0) the element form is written like the DG-IP
+// element kernel's strong form f, R = -M f, with, per own face point,
+//   FF = Fhat*_n(U_f, Uhat) - F^nu(Uhat, grad U_f).n + tau F^nu(Uhat; (U_f - Uhat) (x) n).n,
+//   H  = F^nu(Uhat; (U_f - Uhat) (x) n)      (weight 1; walls with kappa = 0),
+//   Fhat*_n = F_n(Uhat) + A_n^+(Uhat)(U_f - Uhat)  (= A^+ U_f + A^- Uhat),
+// tau = 10 (k+1)^2 / l of the element, and the facet residual (face weight w_f,
+// area factor s_J) -w_f s_J FF inside, w_f s_J (Uhat - U_w(U_f)) on walls,
+// w_f s_J (A^+(Uhat)(Uhat - U_f) - A^-(Uhat)(Uhat - U_inf)) on farfield faces.
+//
+// k_hdg_condense: one CTA per element: Gauss-Jordan elimination with partial
+// pivoting of [K | C] (K^{-1} C in place of C), then S_T = A33_T - D K^{-1} C.
+#include <cuda_runtime.h>
+
+#include "dgip_physics.cuh"
+#include "hdg.h"
+#include "kernels.cuh"
+
+namespace dgx {
+namespace {
+
+template <typename T, typename S, int D>
+__device__ __forceinline__ void split_apply(const T (&Us)[D + 2], const T (&dU)[D + 2], const S (&nh)[D],
+                                            const Gas<T>& g, int sign, T (&out)[D + 2]) {
+  // A_n^+ dU (sign > 0), A_n^- dU (sign < 0) or A_n dU (sign == 0) at the state Us
+  constexpr int nf = D + 2;
+  const Waves<D, T, S> w(Us, dU, nh, g);
+  T rm[nf], rp[nf];
+  w.r(-1, nh, rm);
+  w.r(1, nh, rp);
+  auto part = [&](const T& x) {
+    if (sign == 0) return x;
+    if (sign > 0) return x > T(0) ? x : T(0);
+    return x < T(0) ? x : T(0);
+  };
+  const T l0 = part(w.un), lm = part(w.un - w.c), lp = part(w.un + w.c);
+#pragma unroll
+  for (int f = 0; f < nf; ++f) out[f] = l0 * dU[f] + (lm - l0) * w.am * rm[f] + (lp - l0) * w.ap * rp[f];
+}
+
+template <int P, typename T>
+__device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R, T* hres) {
+  constexpr int D = 2, n = P + 1, N = n * n, nf = 4, nfp = n, NF = 4;
+  using H = Sh<D, P, 1>;
+  constexpr Tab1<double> tb = make_tab1<double>(P);
+  const double rh[2] = {a.rh[e * 2], a.rh[e * 2 + 1]};
+  const double J = 1.0 / (rh[0] * rh[1]);  // prod(h_a / 2) = 1 / prod(r_a)
+  const double tau = a.tk2 * a.il[e];
+  const Gas<T> g = gas_as<T, double>(a.gas);
+  Gas<double> gw0 = a.gas;
+  gw0.kcv = 0.0;
+  const Gas<T> gw = gas_as<T, double>(gw0);
+  // traces of U
+  T TU[NF][nf][nfp];
+  for (int face = 0; face < NF; ++face)
+    for (int f = 0; f < nf; ++f)
+      for (int fp = 0; fp < nfp; ++fp) {
+        T s = T(0);
+        for (int m = 0; m < n; ++m) s += T((face & 1) ? tb.lp[m] : tb.lm[m]) * u[f * N + H::node(m, fp, face >> 1)];
+        TU[face][f][fp] = s;
+      }
+  // face quantities
+  T FF[NF][nf][nfp], HA[NF][D][nf][nfp];
+  for (int face = 0; face < NF; ++face) {
+    const int a0 = face >> 1, side = face & 1, c = 1 - a0;
+    const int kind = a.nb[e * NF + face];
+    const double sJ = J * rh[a0];
+    double nv[D] = {0.0, 0.0};
+    nv[a0] = side ? 1.0 : -1.0;
+    for (int fp = 0; fp < nfp; ++fp) {
+      T Uf[nf], Uhf[nf], Q[D][nf], dl[nf];
+      for (int f = 0; f < nf; ++f) {
+        Uf[f] = TU[face][f][fp];
+        Uhf[f] = uh[(face * nf + f) * nfp + fp];
+        dl[f] = Uf[f] - Uhf[f];
+        T sn = T(0), st = T(0);
+        for (int j = 0; j < n; ++j) sn += T(side ? tb.dlp[j] : tb.dlm[j]) * u[f * N + H::node(j, fp, a0)];
+        for (int m = 0; m < n; ++m) st += T(tb.D[fp][m]) * TU[face][f][m];
+        Q[a0][f] = T(rh[a0]) * sn;
+        Q[c][f] = T(rh[c]) * st;
+      }
+      const Gas<T>& gk = (kind == -1) ? gw : g;
+      T Fn[nf], Ad[nf], Vg[D][nf], Kd[D][nf], Qd[D][nf];
+      conv_flux_normal<D, T, double>(Uhf, nv, g, Fn);
+      split_apply<T, double, D>(Uhf, dl, nv, g, 1, Ad);
+      visc_flux_all<D, T>(Uhf, Q, gk, Vg);
+      for (int cc = 0; cc < D; ++cc)
+        for (int f = 0; f < nf; ++f) Qd[cc][f] = T(nv[cc]) * dl[f];
+      visc_flux_all<D, T>(Uhf, Qd, gk, Kd);
+      T ff[nf];
+      for (int f = 0; f < nf; ++f) {
+        T vn = T(0), kn = T(0);
+        for (int cc = 0; cc < D; ++cc) {
+          vn += Vg[cc][f] * T(nv[cc]);
+          kn += Kd[cc][f] * T(nv[cc]);
+        }
+        ff[f] = Fn[f] + Ad[f] - vn + T(tau) * kn;
+        FF[face][f][fp] = ff[f];
+        for (int cc = 0; cc < D; ++cc) HA[face][cc][f][fp] = Kd[cc][f];
+      }
+      // facet residual
+      const double wf = a.w[fp] * sJ;
+      T hv[nf];
+      if (kind >= 0) {
+        for (int f = 0; f < nf; ++f) hv[f] = -ff[f];
+      } else if (kind == -1) {
+        T Uw[nf];
+        wall_state<D, T>(Uf, Uw);
+        for (int f = 0; f < nf; ++f) hv[f] = Uhf[f] - Uw[f];
+      } else {
+        T d1[nf], d2[nf], p1[nf], m2[nf];
+        for (int f = 0; f < nf; ++f) {
+          d1[f] = Uhf[f] - Uf[f];
+          d2[f] = Uhf[f] - T(a.Uinf[f]);
+        }
+        split_apply<T, double, D>(Uhf, d1, nv, g, 1, p1);
+        split_apply<T, double, D>(Uhf, d2, nv, g, -1, m2);
+        for (int f = 0; f < nf; ++f) hv[f] = p1[f] - m2[f];
+      }
+      for (int f = 0; f < nf; ++f) hres[(face * nf + f) * nfp + fp] = T(wf) * hv[f];
+    }
+  }
+  // element residual: the DG-IP strong form with these face quantities, R = -M f
+  T Q[D][nf][N], Fa[D][nf][N];
+  for (int cc = 0; cc < D; ++cc)
+    for (int f = 0; f < nf; ++f)
+      for (int q = 0; q < N; ++q) {
+        const int line = H::fpoint(q, cc), k = H::qa(q, cc);
+        T s = T(0);
+        for (int m = 0; m < n; ++m) s += T(tb.D[k][m]) * u[f * N + H::node(m, line, cc)];
+        Q[cc][f][q] = T(rh[cc]) * s;
+      }
+  for (int q = 0; q < N; ++q) {
+    T Uq[nf], Qq[D][nf], F[D][nf], V[D][nf];
+    for (int f = 0; f < nf; ++f) {
+      Uq[f] = u[f * N + q];
+      for (int cc = 0; cc < D; ++cc) Qq[cc][f] = Q[cc][f][q];
+    }
+    conv_flux_all<D, T>(Uq, g, F);
+    visc_flux_all<D, T>(Uq, Qq, g, V);
+    for (int aa = 0; aa < D; ++aa)
+      for (int f = 0; f < nf; ++f) {
+        T x = F[aa][f] - V[aa][f];
+        const int a0 = 1 - aa;  // the other direction's faces carry the tangential part
+        const int fp = H::fpoint(q, a0), k0 = H::qa(q, a0);
+        x += T(rh[a0] * tb.Lm[k0]) * HA[2 * a0][aa][f][fp] + T(rh[a0] * tb.Lp[k0]) * HA[2 * a0 + 1][aa][f][fp];
+        Fa[aa][f][q] = x;
+      }
+  }
+  for (int q = 0; q < N; ++q)
+    for (int f = 0; f < nf; ++f) {
+      T s = T(0);
+      for (int aa = 0; aa < D; ++aa) {
+        const int line = H::fpoint(q, aa), k = H::qa(q, aa);
+        T v = T(0);
+        for (int m = 0; m < n; ++m) v += T(tb.Dh[k][m]) * Fa[aa][f][H::node(m, line, aa)];
+        v -= T(tb.Lm[k]) * FF[2 * aa][f][line] + T(tb.Lp[k]) * FF[2 * aa + 1][f][line];
+        v += T(rh[aa]) * (T(tb.dLm[k]) * HA[2 * aa][aa][f][line] + T(tb.dLp[k]) * HA[2 * aa + 1][aa][f][line]);
+        s += T(rh[aa]) * v;
+      }
+      const double wq = a.w[q % n] * a.w[q / n];
+      R[f * N + q] = -T(wq * J) * s;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* __restrict__ U,
+                                                      const double* __restrict__ Uh, double gamma, double* K,
+                                                      double* C, double* Dm, double* A33, double* Rv, double* hv) {
+  constexpr int n = P + 1, N = n * n, nf = 4, NU = nf * N, NH = 4 * nf * n;
+  using T = Dual<double, 1>;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)a.E * (NU + NH)) return;
+  const int e = (int)(gid / (NU + NH)), col = (int)(gid % (NU + NH));
+  T u[NU], uh[NH], R[NU], h[NH];
+  for (int i = 0; i < NU; ++i) u[i] = T(U[(size_t)e * NU + i]);
+  for (int i = 0; i < NH; ++i) uh[i] = T(Uh[(size_t)e * NH + i]);
+  if (col < NU) u[col].d[0] = 1.0;
+  else uh[col - NU].d[0] = 1.0;
+  hdg_forms<P, T>(a, e, u, uh, R, h);
+  if (col == 0 && Rv) {  // the forms' values (any column's value part)
+    for (int i = 0; i < NU; ++i) Rv[(size_t)e * NU + i] = R[i].v;
+    for (int k = 0; k < NH; ++k) hv[(size_t)e * NH + k] = h[k].v;
+  }
+  if (col < NU) {
+    const double J = 1.0 / (a.rh[e * 2] * a.rh[e * 2 + 1]);
+    for (int i = 0; i < NU; ++i) {
+      const int q = i % N;
+      const double m = (i == col) ? a.w[q % n] * a.w[q / n] * J : 0.0;
+      K[((size_t)e * NU + i) * NU + col] = m + gamma * R[i].d[0];
+    }
+    for (int k = 0; k < NH; ++k) Dm[((size_t)e * NH + k) * NU + col] = h[k].d[0];
+  } else {
+    const int j = col - NU;
+    for (int i = 0; i < NU; ++i) C[((size_t)e * NU + i) * NH + j] = gamma * R[i].d[0];
+    for (int k = 0; k < NH; ++k) A33[((size_t)e * NH + k) * NH + j] = h[k].d[0];
+  }
+}
+
+// Gauss-Jordan with partial pivoting of [W | X] (W = K copied into the
+// workspace, X = C copied into KinvC), then S = A33 - D X.
+__global__ void __launch_bounds__(256) k_hdg_condense(int E, int NU, int NH, const double* __restrict__ K,
+                                                      const double* __restrict__ C, const double* __restrict__ Dm,
+                                                      const double* __restrict__ A33, double* __restrict__ X,
+                                                      double* __restrict__ S, double* __restrict__ Wbuf) {
+  const int e = blockIdx.x;
+  if (e >= E) return;
+  double* W = Wbuf + (size_t)e * NU * NU;
+  double* Xe = X + (size_t)e * NU * NH;
+  const double* Ke = K + (size_t)e * NU * NU;
+  const double* Ce = C + (size_t)e * NU * NH;
+  for (int i = threadIdx.x; i < NU * NU; i += blockDim.x) W[i] = Ke[i];
+  for (int i = threadIdx.x; i < NU * NH; i += blockDim.x) Xe[i] = Ce[i];
+  __shared__ double sval[256];
+  __shared__ int sidx[256];
+  __shared__ double piv_inv;
+  __syncthreads();
+  for (int k = 0; k < NU; ++k) {
+    // pivot: the largest |W[i][k]| over i >= k
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < NU; i += blockDim.x) {
+      const double v = fabs(W[(size_t)i * NU + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        const double o = sval[threadIdx.x + s];
+        const int oi = sidx[threadIdx.x + s];
+        if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+          sval[threadIdx.x] = o;
+          sidx[threadIdx.x] = oi;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = sidx[0];
+    if (p != k) {  // swap rows k and p of W (columns >= k) and X
+      for (int j = k + threadIdx.x; j < NU; j += blockDim.x) {
+        const double t = W[(size_t)k * NU + j];
+        W[(size_t)k * NU + j] = W[(size_t)p * NU + j];
+        W[(size_t)p * NU + j] = t;
+      }
+      for (int j = threadIdx.x; j < NH; j += blockDim.x) {
+        const double t = Xe[(size_t)k * NH + j];
+        Xe[(size_t)k * NH + j] = Xe[(size_t)p * NH + j];
+        Xe[(size_t)p * NH + j] = t;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) piv_inv = 1.0 / W[(size_t)k * NU + k];
+    __syncthreads();
+    const double pinv = piv_inv;
+    for (int j = k + threadIdx.x; j < NU; j += blockDim.x) W[(size_t)k * NU + j] *= pinv;
+    for (int j = threadIdx.x; j < NH; j += blockDim.x) Xe[(size_t)k * NH + j] *= pinv;
+    __syncthreads();
+    // eliminate column k from every other row
+    const int cols = (NU - k - 1) + NH;
+    for (int t = threadIdx.x; t < (NU - 1) * cols; t += blockDim.x) {
+      int i = t / cols;
+      if (i >= k) ++i;  // skip the pivot row
+      const int jj = t % cols;
+      const double f = W[(size_t)i * NU + k];
+      if (jj < NU - k - 1) {
+        const int j = k + 1 + jj;
+        W[(size_t)i * NU + j] -= f * W[(size_t)k * NU + j];
+      } else {
+        const int j = jj - (NU - k - 1);
+        Xe[(size_t)i * NH + j] -= f * Xe[(size_t)k * NH + j];
+      }
+    }
+    __syncthreads();
+  }
+  // S = A33 - D X
+  const double* De = Dm + (size_t)e * NH * NU;
+  const double* Ae = A33 + (size_t)e * NH * NH;
+  double* Se = S + (size_t)e * NH * NH;
+  for (int t = threadIdx.x; t < NH * NH; t += blockDim.x) {
+    const int r = t / NH, c = t % NH;
+    double s = Ae[t];
+    for (int m = 0; m < NU; ++m) s -= De[(size_t)r * NU + m] * Xe[(size_t)m * NH + c];
+    Se[t] = s;
+  }
+}
+
+template <int P>
+cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, double gamma, double* K, double* C,
+                       double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
+  constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n;
+  const long long total = (long long)a.E * (NU + NH);
+  k_hdg_jacobian<P><<<(int)((total + 127) / 128), 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t hdg_jacobian(int P, const HdgArgs& a, const double* U, const double* Uh, double gamma, double* K,
+                         double* C, double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
+  switch (P) {
+    case 1: return launch_jac<1>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, st);
+    case 2: return launch_jac<2>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, st);
+    case 3: return launch_jac<3>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, st);
+    case 4: return launch_jac<4>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, st);
+    default: return launch_jac<5>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, st);
+  }
+}
+
+cudaError_t hdg_condense(int E, int NU, int NH, const double* K, const double* C, const double* Dm, const double* A33,
+                         double* X, double* S, double* W, cudaStream_t st) {
+  if (E == 0) return cudaSuccess;
+  k_hdg_condense<<<E, 256, 0, st>>>(E, NU, NH, K, C, Dm, A33, X, S, W);
+  return cudaGetLastError();
+}
+
+}  // namespace dgx

@@ -20,6 +20,7 @@
 #include "dgip.cuh"
 #include "mms.cuh"
 #include "batchp.h"
+#include "hdg.h"
 
 using dgx::Tab;
 
@@ -1222,6 +1223,11 @@ size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   if (!h) return 0;
   if (op == DGX_OP_ARK && h->stages == 0) return 0;
   if ((op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && h->stages == 0) return 0;
+  if (op == DGX_OP_HDG) {
+    if (!h->fp64 || h->d != 2) return 0;
+    const size_t nu = (size_t)h->nf * h->N;
+    return align256((size_t)h->E * nu * nu * sizeof(double));
+  }
   if (op < DGX_OP_RHS || op > DGX_OP_ARK_STEP_ADJOINT) return 0;
   if (h->dgip && (op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT)) return 0;
   if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && !h->tab->vjp) return 0;
@@ -1355,6 +1361,43 @@ dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls) {
   h->mesh64.wait_polls = h->wait_polls;
   h->mesh32.wait_polls = h->wait_polls;
   return DGX_OK;
+}
+
+dgx_status dgx_hdg_sizes(const dgx_handle* h, int32_t* nu, int32_t* nh) {
+  if (!h) return DGX_EINVAL;
+  if (nu) *nu = h->nf * h->N;
+  if (nh) *nh = h->NF * h->nf * h->nfp;
+  return DGX_OK;
+}
+
+dgx_status dgx_hdg_blocks(dgx_handle* h, const double* U, const double* Uhat, double gamma, double* K, double* C,
+                          double* D, double* A33, double* R, double* hres, void* stream) {
+  if (!h || !U || !Uhat || !K || !C || !D || !A33 || !std::isfinite(gamma) || (!R) != (!hres)) return DGX_EINVAL;
+  if (!h->fp64 || h->d != 2) return DGX_EUNSUPPORTED;
+  if (!h->has_mesh || h->curv) return h->curv ? DGX_EUNSUPPORTED : DGX_ESTATE;
+  if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+  dgx::HdgArgs a{};
+  a.E = h->E;
+  a.rh = (const double*)h->d_rh;
+  a.il = (const double*)h->d_il;
+  a.nb = h->d_nb;
+  a.tk2 = 10.0 * (h->p + 1) * (h->p + 1);
+  const dgx::Basis1 b = dgx::make_basis1(h->p);
+  for (int i = 0; i < b.n; ++i) a.w[i] = b.w[i];
+  for (int f = 0; f < 4; ++f) a.Uinf[f] = h->Uinf[f];
+  a.gas = h->mesh64.gas;
+  return cuda_status(dgx::hdg_jacobian(h->p, a, U, Uhat, gamma, K, C, D, A33, R, hres, (cudaStream_t)stream));
+}
+
+dgx_status dgx_hdg_condense(dgx_handle* h, const double* K, const double* C, const double* D, const double* A33,
+                            double* KinvC, double* S, void* workspace, void* stream) {
+  if (!h || !K || !C || !D || !A33 || !KinvC || !S || !workspace) return DGX_EINVAL;
+  if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (!h->fp64 || h->d != 2) return DGX_EUNSUPPORTED;
+  if (!h->has_mesh) return DGX_ESTATE;
+  const int nu = h->nf * h->N, nh = h->NF * h->nf * h->nfp;
+  return cuda_status(dgx::hdg_condense(h->E, nu, nh, K, C, D, A33, KinvC, S, (double*)workspace,
+                                       (cudaStream_t)stream));
 }
 
 dgx_status dgx_set_farfield(dgx_handle* h, const double* U_inf) {

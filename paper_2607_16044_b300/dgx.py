@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdgx.so")
 
 FP64, FP32 = 0, 1
-OP_RHS, OP_VJP, OP_ARK, OP_ARK_ADJOINT, OP_ARK_STEP_ADJOINT = 0, 1, 2, 3, 4
+OP_RHS, OP_VJP, OP_ARK, OP_ARK_ADJOINT, OP_ARK_STEP_ADJOINT, OP_HDG = 0, 1, 2, 3, 4, 5
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "non-finite residual",
           5: "device wait timed out", 6: "unsupported", 7: "call out of order"}
 
@@ -48,7 +48,8 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_batch_set_dt", "dgx_batch_step", "dgx_batch_step_graph", "dgx_batch_autotune", "dgx_set_pipeline",
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
            "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source",
-           "dgx_set_wait_limit", "dgx_batch_set_persistent"]
+           "dgx_set_wait_limit", "dgx_batch_set_persistent", "dgx_hdg_sizes", "dgx_hdg_blocks",
+           "dgx_hdg_condense"]
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_set_farfield.argtypes = [vp, vp]
     lib.dgx_set_wait_limit.argtypes = [vp, ctypes.c_int64]
     lib.dgx_batch_set_persistent.argtypes = [vp, i32]
+    lib.dgx_hdg_sizes.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.dgx_hdg_blocks.argtypes = [vp, vp, vp, dbl, vp, vp, vp, vp, vp, vp, vp]
+    lib.dgx_hdg_condense.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dgx_set_explicit_mask.argtypes = [vp, vp]
     lib.dgx_rhs_split.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_mms_source.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp]
@@ -288,6 +292,37 @@ class Solver:
         _check(self.lib.dgx_mms_source(self.h, float(t), float(kx), float(ky), float(omega),
                                        self._state(out, "out"), _stream_ptr(stream)), "dgx_mms_source")
         return out
+
+    def hdg_blocks(self, U: torch.Tensor, Uhat: torch.Tensor, gamma: float, forms: bool = False, stream=None):
+        """Element-local HDG-IP Newton blocks (K, C, D, A33[, R, h]) of an SDIRK
+        stage with gamma = dt a_ii (FP64, 2D boxes); Uhat is [E][2d][nf][n]."""
+        nu, nh = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.dgx_hdg_sizes(self.h, ctypes.byref(nu), ctypes.byref(nh)), "dgx_hdg_sizes")
+        E = self.shape[0]
+        dev = self.device
+        K = torch.empty((E, nu.value, nu.value), dtype=torch.float64, device=dev)
+        C = torch.empty((E, nu.value, nh.value), dtype=torch.float64, device=dev)
+        D = torch.empty((E, nh.value, nu.value), dtype=torch.float64, device=dev)
+        A = torch.empty((E, nh.value, nh.value), dtype=torch.float64, device=dev)
+        R = torch.empty((E, nu.value), dtype=torch.float64, device=dev) if forms else None
+        h = torch.empty((E, nh.value), dtype=torch.float64, device=dev) if forms else None
+        if not (U.is_cuda and U.dtype == torch.float64 and U.is_contiguous() and Uhat.is_cuda
+                and Uhat.dtype == torch.float64 and Uhat.is_contiguous() and Uhat.numel() == E * nh.value):
+            raise ValueError("U and Uhat must be contiguous CUDA float64 tensors")
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(self.lib.dgx_hdg_blocks(self.h, p(U), p(Uhat), float(gamma), p(K), p(C), p(D), p(A), p(R), p(h),
+                                       _stream_ptr(stream)), "dgx_hdg_blocks")
+        return (K, C, D, A, R, h) if forms else (K, C, D, A)
+
+    def hdg_condense(self, K, C, D, A33, stream=None):
+        """(K^{-1} C, A33 - D K^{-1} C) per element."""
+        KinvC = torch.empty_like(C)
+        S = torch.empty_like(A33)
+        ws = self.workspace(OP_HDG)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        _check(self.lib.dgx_hdg_condense(self.h, p(K), p(C), p(D), p(A33), p(KinvC), p(S), self._aligned(ws),
+                                         _stream_ptr(stream)), "dgx_hdg_condense")
+        return KinvC, S
 
     def rhs_noalloc(self, U: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
         """f = dU/dt without a workspace: for callers that may not allocate
