@@ -187,7 +187,11 @@ def make_solver(prec, workload="channel3d"):
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
     from paper_2607_16044_b300.tableaux import ars343_explicit
-    mesh, phys, U0 = I.channel3d_workload() if workload == "channel3d" else I.channel2d_workload()
+    if workload.startswith("channel3d-"):   # a smaller 3D channel, "channel3d-<cells in x, y>-<layers per wall>"
+        nxy, nh = (int(v) for v in workload.split("-")[1:3])
+        mesh, phys, U0 = I.channel3d_workload(nxy=nxy, n_half=nh)
+    else:
+        mesh, phys, U0 = I.channel3d_workload() if workload == "channel3d" else I.channel2d_workload()
     s = Solver(mesh, phys, prec)
     A, b, c = ars343_explicit()
     s.set_tableau(A, b, c)
@@ -211,7 +215,7 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
         s.ark_step_stages(U, dt, stages)
         s.ark_adjoint_step(stages, lam, dt)
 
-    variants = s.autotune(U, reps=1 if workload == "channel3d" else 3)   # set-up: fastest tile size per kernel
+    variants = s.autotune(U, reps=1 if workload.startswith("channel3d") else 3)   # set-up: fastest tile size per kernel
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
@@ -844,8 +848,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--legs", default="fp64,fp32",
-                    help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' alone (profiling "
-                         "runs), or 'tgv' for the TGV engine comparison")
+                    help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' / "
+                         "'fp64:channel3d-<nxy>-<layers>' alone (profiling runs), or 'tgv' for the TGV engine "
+                         "comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
