@@ -406,10 +406,14 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant FP32 kernel from one ncu capture of the bench workload (summary and
-# command in profiles/), valid only while the kernel sources hash to `sources`.
-NCU_TRAFFIC = {"kernel": "vjp_br1", "bytes": 105344512,
-               "sources": "3bed97b8d2fd92740430ac59a44bbfaf622df4a5e80e8b156cc2e8442075df2a"}
+# headline's dominant kernel (k_vjp_br1, FP64) from one ncu capture of the same
+# step on the 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2),
+# scaled to the 48^3 launch by the element count (the kernel's traffic is per
+# element tile): 1,833,356,032 B x 110,592 / 16,384.  Summary and command in
+# profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
+# sources hash to `sources`.
+NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375153216,
+               "sources": "745a6328d7a9e4c610c8c74d738bce96b4062ab4664f305144fd4ac356cf4bab"}
 
 
 def sources_hash(root_header="vjp.cuh"):
@@ -485,9 +489,11 @@ def roofline(res, prec, pk):
                 "frac_alu_step": round(step_flops / step_s / 1e12 / alu, 4),
                 "alu_peak_tflops": round(alu, 3), "alu_peak_source": alu_src,
                 "hbm_peak_gbs": pk["hbm_gbs"]})
-    if prec == "fp32" and name == NCU_TRAFFIC["kernel"] and sources_hash() == NCU_TRAFFIC["sources"]:
+    if (prec == NCU_TRAFFIC["prec"] and name == NCU_TRAFFIC["kernel"] and res["mesh"].n_elem == 110592
+            and sources_hash() == NCU_TRAFFIC["sources"]):
         out["traffic"] = NCU_TRAFFIC["bytes"]
-        out["traffic_source"] = "ncu capture (profiles/k_vjp_br1_channel2d_p4_fp32.md), bytes per launch"
+        out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 32x32x16 "
+                                 "channel scaled by the element count (profiles/k_vjp_br1_channel3d_p5_fp64.md)")
     return out
 
 
