@@ -689,6 +689,49 @@ def dgip_perf(reps=5):
     return out
 
 
+def hdg_perf(cells=64, reps=3):
+    """Element-local HDG-IP Newton blocks of the implicit region (the paper's
+    HDG-IP, FP64) on a cells x cells periodic 2D NS mesh, degrees 1..5: the
+    blocks K, C, D, A33 by forward-mode differentiation of the element and
+    facet forms, and their static condensation (K^-1 C and the element Schur
+    contribution, Gauss-Jordan with partial pivoting), per element; counted
+    flops of the condensation (nu^2 (nu + nh) multiply-adds of the
+    elimination and nh^2 nu of D K^-1 C, two flops each) against the
+    measured FP64 peak."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    out = {"workload": f"HDG-IP element blocks, {cells}x{cells} periodic 2D NS quads, Re 100, FP64"}
+    alu = alu_peak_tflops("fp64")
+    for p in (1, 2, 3, 4, 5):
+        mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells)] * 2, [True, True])
+        phys = I.Physics(gamma=1.4, Re=100.0, Pr=0.72, Ma=0.3, viscous=True)
+        s = Solver(mesh, phys, "fp64")
+        U0 = I.random_state(mesh, 3)
+        U = torch.as_tensor(U0).cuda()
+        # facet state: each element's own traces, perturbed
+        n = p + 1
+        Uh = torch.as_tensor(np.random.default_rng(4).uniform(0.95, 1.05, (mesh.n_elem, 4, 4, n)), device="cuda")
+        Uh *= torch.as_tensor(U0.mean(2)[:, None, :, None], device="cuda")
+        Uh = Uh.contiguous()
+        K, C, D, A = s.hdg_blocks(U, Uh, 0.01)
+        KinvC, S = s.hdg_condense(K, C, D, A)
+        ms_b = _time_events(lambda: s.hdg_blocks(U, Uh, 0.01), reps)
+        ms_c = _time_events(lambda: s.hdg_condense(K, C, D, A), reps)
+        s.check()
+        nu, nh = 4 * n * n, 16 * n
+        fl = 2.0 * mesh.n_elem * (nu * nu * (nu + nh) + nh * nh * nu)
+        out[f"p{p}"] = {"elements": mesh.n_elem, "nu": nu, "nh": nh, "ms_blocks": round(ms_b, 3),
+                        "ms_condense": round(ms_c, 3),
+                        "elements_per_s": round(mesh.n_elem / ((ms_b + ms_c) / 1e3), 1),
+                        "condense_TFLOP_s": round(fl / (ms_c / 1e3) / 1e12, 3),
+                        "condense_frac_fp64": round(fl / (ms_c / 1e3) / 1e12 / alu, 3)}
+        del K, C, D, A, KinvC, S
+        s.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def tgv_perf(reps=10, profile_range=False):
     """32^3 Taylor-Green vortex, p = 3: forward residual time in FP64 and in FP32
     with each contraction engine of the element kernel (CUDA cores, TF32, BF16
@@ -961,6 +1004,7 @@ def main():
         line["vortex_fp32_vs_fp64"] = vortex_accuracy()
         line["ensemble"] = ensemble_perf()
         line["dgip"] = dgip_perf()
+        line["hdg"] = hdg_perf()
         line["tgv"] = tgv_perf()
         line["channel3d_trajectory"] = channel3d_trajectory()
     if rank == 0 and not args.no_cpu_baseline:
