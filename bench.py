@@ -650,6 +650,12 @@ def dgip_perf(reps=5):
         ms_rhs = _time_events(lambda: s.rhs(U, out=f), reps, flush)
         ms_vjp = _time_events(lambda: s.rhs_vjp(U, lam, out=g), reps, flush)
         ms_ark = _time_events(lambda: s.ark_step(U64, 1e-13), reps, flush)
+        # the headline's step on this operator: one ARS(3,4,3) step with its
+        # stage states kept + its discrete adjoint (4 VJPs), 8 DOF-evals per DOF
+        lam64 = torch.as_tensor(np.random.default_rng(105).standard_normal(U0.shape)).cuda()
+        stages = s.stage_buffer()
+        s.ark_step_adjoint(U64, lam64, 1e-13, stages)
+        ms_sa = _time_events(lambda: s.ark_step_adjoint(U64, lam64, 1e-13, stages), reps, flush)
         s.profile(True)
         s.profile_reset()
         for _ in range(reps):
@@ -670,7 +676,8 @@ def dgip_perf(reps=5):
         n = U.numel()
         r = {"dofs": n, "ms_rhs": round(ms_rhs, 4), "ms_vjp": round(ms_vjp, 4), "ms_ark_step": round(ms_ark, 4),
              "rhs_dof_evals_per_s": round(n / (ms_rhs / 1e3), 1), "vjp_dof_evals_per_s": round(n / (ms_vjp / 1e3), 1),
-             "ark_dof_evals_per_s": round(4 * n / (ms_ark / 1e3), 1), "per_kernel": kern,
+             "ark_dof_evals_per_s": round(4 * n / (ms_ark / 1e3), 1), "ms_step_adjoint": round(ms_sa, 4),
+             "step_adjoint_dof_evals_per_s": round(8 * n / (ms_sa / 1e3), 1), "per_kernel": kern,
              "dominant": max(prof.items(), key=lambda kv: kv[1][1])[0]}
         if wl == "channel2d" and prec == "fp64":   # geometry split: implicit near-wall strips
             rows = mesh.shape[1]

@@ -164,8 +164,9 @@ dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, 
 /* Bytes of one step's stage-checkpoint buffer (0 before dgx_set_tableau).  The
  * buffer holds s equal slots of dgx_stage_bytes / s bytes; slot i (0-based)
  * begins with the stage state y_{i+1} [E][nf][N] in the handle's precision,
- * followed by that stage's face traces and (viscous) BR1 gradient, which the
- * adjoint reuses instead of recomputing them. */
+ * followed (LLF/BR1 scheme) by that stage's face traces and (viscous) BR1
+ * gradient, which the adjoint reuses instead of recomputing them; DG-IP slots
+ * hold the stage state only. */
 size_t dgx_stage_bytes(const dgx_handle* h);
 
 /* The same step, also storing the stage states y_1..y_s it evaluates and their
@@ -180,7 +181,8 @@ dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stag
  *   lam_n = lam + sum_i nu_i,   i = s .. 1.
  * stages = the y_i of the step (from dgx_ark_step_stages); lam64 (device,
  * double [E][nf][N]) holds lambda_{n+1} on entry and lambda_n on exit; the
- * accumulation into lam64 is in FP64. */
+ * accumulation into lam64 is in FP64.  DG-IP scheme: composed from single
+ * VJPs (mu_i formed in FP64 and rounded to the working precision). */
 dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
                                 void* stream);
 
@@ -192,7 +194,8 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
  * stage's face and element kernels, which form U_{n+1}, run on a second
  * stream owned by the handle while the adjoint runs on `stream`; that stream
  * waits for them before the call's work ends (fork and join by events, so the
- * call can be captured into a CUDA graph).  Workspace:
+ * call can be captured into a CUDA graph).  DG-IP scheme: the step, then its
+ * adjoint, both on `stream`.  Workspace:
  * dgx_workspace_bytes(h, DGX_OP_ARK_STEP_ADJOINT), 256-byte aligned. */
 dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, double dt, void* stages, void* workspace,
                                 void* stream);

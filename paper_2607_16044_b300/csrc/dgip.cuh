@@ -1040,6 +1040,39 @@ struct DgipOps {
   }
 };
 
+// Linear combinations of state vectors for the composed ARK adjoint:
+// out = (S)(c_lam lam + sum_j c_j in_j) (sums in FP64), and/or
+// acc64 += sum_j c_j in_j in FP64.
+template <typename S>
+struct LinComb {
+  size_t n;
+  const double* lam;   // FP64 input (or nullptr)
+  double c_lam;
+  int m;
+  const S* in[MAXSTAGES];
+  double c[MAXSTAGES];
+  S* out;              // or nullptr
+  double* acc64;       // or nullptr
+};
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_lincomb(LinComb<S> a) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = a.lam ? a.c_lam * a.lam[i] : 0.0;
+    for (int j = 0; j < a.m; ++j) v += a.c[j] * (double)a.in[j][i];
+    if (a.out) a.out[i] = (S)v;
+    if (a.acc64) a.acc64[i] += v;
+  }
+}
+
+template <typename S>
+inline cudaError_t lincomb(const LinComb<S>& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  const size_t blocks = (a.n + 255) / 256;
+  k_lincomb<S><<<(unsigned)(blocks < 148 * 16 ? blocks : 148 * 16), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 struct DgipTable {
   cudaError_t (*trace)(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, cudaStream_t st);
   cudaError_t (*face)(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st);

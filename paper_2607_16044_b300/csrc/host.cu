@@ -299,7 +299,7 @@ Layout layout_dgip(const dgx_handle* h, int op) {
     L.HA = off;
     off += align256(face * h->d);
   }
-  if (op == DGX_OP_VJP) {
+  if (op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT) {
     L.TUb = off;
     off += align256(face);
     if (h->viscous) {
@@ -307,6 +307,12 @@ Layout layout_dgip(const dgx_handle* h, int op) {
       off += align256(face);
     }
     L.GP = off;
+    off += align256(state);
+  }
+  if (op == DGX_OP_ARK_ADJOINT) {  // nu_0 .. nu_{s-1}, then mu
+    L.NU = off;
+    off += align256(state) * (h->stages > 0 ? h->stages : 1);
+    L.LAM = off;
     off += align256(state);
   }
   if (op == DGX_OP_ARK) {
@@ -405,6 +411,11 @@ Slot slot_layout(const dgx_handle* h) {
   const size_t state = (size_t)h->E * h->nf * h->N * h->s;
   Slot S{};
   S.y = 0;
+  if (h->dgip) {  // the DG-IP adjoint recomputes traces from y_i: slots hold the stage states only
+    S.TU = S.Q = 0;
+    S.bytes = align256(state);
+    return S;
+  }
   S.TU = align256(state);
   S.Q = S.TU + align256(face);
   S.bytes = S.Q + (h->viscous ? align256(state * h->d) : 0);
@@ -672,6 +683,52 @@ dgx_status dgip_ark_impl(dgx_handle* h, double* U64, double dt, void* stages, vo
     err = dgip_residual<S>(h, Uin, nullptr, nullptr, nullptr, w, &sa, st);
   }
   return cuda_status(err);
+}
+
+// Discrete adjoint of one DG-IP ARK step (the reverse stage recurrence of
+// Sec. 4.2 composed from single VJPs): for i = s .. 1,
+// mu_i = dt (b_i lam + sum_{j>i} a_ji nu_j) formed in FP64 and rounded to the
+// working precision, nu_i = (df/dU)(y_i)^T mu_i; then lam += sum_i nu_i in FP64.
+template <typename S>
+dgx_status dgip_ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                                 cudaStream_t st) {
+  const Layout L = layout(h, DGX_OP_ARK_ADJOINT);
+  const dgx::DgipWork w = dgip_work_at(h, workspace, L);
+  const size_t n = (size_t)h->E * h->nf * h->N;
+  const size_t state_a = align256(n * h->s);
+  char* base = (char*)workspace;
+  auto NU = [&](int j) { return (S*)(base + L.NU + state_a * j); };
+  S* mu = (S*)(base + L.LAM);
+  const Slot SL = slot_layout(h);
+  const int s = h->stages;
+  for (int i = s - 1; i >= 0; --i) {
+    dgx::LinComb<S> lc{};
+    lc.n = n;
+    lc.lam = lam64;
+    lc.c_lam = dt * h->b[i];
+    for (int j = i + 1; j < s; ++j) {
+      const double a = h->A[j * dgx::MAXSTAGES + i];
+      if (a != 0.0) {
+        lc.in[lc.m] = NU(j);
+        lc.c[lc.m] = dt * a;
+        ++lc.m;
+      }
+    }
+    lc.out = mu;
+    cudaError_t err = dgx::lincomb<S>(lc, st);
+    const void* y = (const char*)stages + SL.bytes * i + SL.y;
+    if (err == cudaSuccess) err = dgip_vjp<S>(h, y, mu, NU(i), w, st);
+    if (err != cudaSuccess) return DGX_ECUDA;
+  }
+  dgx::LinComb<S> fin{};
+  fin.n = n;
+  fin.acc64 = lam64;
+  for (int j = 0; j < s; ++j) {
+    fin.in[fin.m] = NU(j);
+    fin.c[fin.m] = 1.0;
+    ++fin.m;
+  }
+  return cuda_status(dgx::lincomb<S>(fin, st));
 }
 
 // ------------------------------------------------------------ work model
@@ -1229,7 +1286,6 @@ size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
     return align256((size_t)h->E * nu * nu * sizeof(double));
   }
   if (op < DGX_OP_RHS || op > DGX_OP_ARK_STEP_ADJOINT) return 0;
-  if (h->dgip && (op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT)) return 0;
   if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && !h->tab->vjp) return 0;
   if (op == DGX_OP_ARK_STEP_ADJOINT)  // the forward's and the adjoint's workspaces side by side
     return layout(h, DGX_OP_ARK).total + layout(h, DGX_OP_ARK_ADJOINT).total;
@@ -1328,8 +1384,11 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
                                 void* stream) {
   if (!h || !stages || !lam64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp || h->dgip) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip)
+    return h->fp64 ? dgip_ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream)
+                   : dgip_ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
   if (h->fp64) return ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
   return ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
 }
@@ -1339,8 +1398,17 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
   if (!h || !U64 || !lam64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (((uintptr_t)stages & 255) != 0 || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp || h->dgip) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->dgip) {  // the step, then its adjoint, on the caller's stream
+    char* ws2 = (char*)workspace + layout(h, DGX_OP_ARK).total;
+    dgx_status s = h->fp64 ? dgip_ark_impl<double>(h, U64, dt, stages, workspace, st)
+                           : dgip_ark_impl<float>(h, U64, dt, stages, workspace, st);
+    if (s == DGX_OK)
+      s = h->fp64 ? dgip_ark_adjoint_impl<double>(h, stages, lam64, dt, ws2, st)
+                  : dgip_ark_adjoint_impl<float>(h, stages, lam64, dt, ws2, st);
+    return s;
+  }
   char* ws_adj = (char*)workspace + layout(h, DGX_OP_ARK).total;  // a multiple of 256 bytes
   dgx_status s = h->fp64 ? ark_impl<double>(h, U64, dt, stages, workspace, st, nullptr, /*fork=*/true)
                          : ark_impl<float>(h, U64, dt, stages, workspace, st, nullptr, /*fork=*/true);

@@ -242,3 +242,39 @@ def test_dgip_channel2d_full_size_sampled(prec):
     err = rel_err(f[rows], ref)
     record(f"dgip-channel2d-{prec}", rel=err, sampled=len(rows))
     assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dgip_ark_adjoint_matches_oracle(prec):
+    """Discrete adjoint of one DG-IP ARS(3,4,3) step (reverse stage recurrence
+    composed from single VJPs) against the oracle's recurrence, linearised at
+    the oracle's stage states (FP32: rounded to FP32); the one-call step +
+    adjoint equals the separate calls bit for bit."""
+    from oracle.vjp import vjp
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.3)], [True, False])
+    phys = _ns()
+    U0 = I.random_state(mesh, 680)
+    lam0 = I.gaussian_cotangent(U0.shape, 681)
+    dt = 2e-5
+    s = _solver(mesh, phys, prec)
+    s.set_tableau(*ars343_explicit())
+    U = torch.as_tensor(U0).cuda()
+    stages = s.stage_buffer()
+    s.ark_step_stages(U, dt, stages)
+    lam = torch.as_tensor(lam0).cuda()
+    s.ark_adjoint_step(stages, lam, dt)
+    U2 = torch.as_tensor(U0).cuda()
+    lam2 = torch.as_tensor(lam0).cuda()
+    s.ark_step_adjoint(U2, lam2, dt, s.stage_buffer())
+    s.check()
+    assert torch.equal(U, U2) and torch.equal(lam, lam2)
+    op = SIPGOperator(mesh, gas_of(phys))
+    A, b, c = ark.ars343()
+    _, ys, _ = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b, return_stages=True)
+    if prec == "fp32":
+        ys = [torch.as_tensor(quantize32(y.numpy())) for y in ys]
+    ref = ark.erk_adjoint_step(lambda y, mu: vjp(op, y, mu), ys, torch.as_tensor(lam0), dt, A, b).numpy()
+    err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
+    record(f"dgip-ark-adjoint-{prec}", rel=err)
+    assert err < TOL[prec], err
