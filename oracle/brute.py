@@ -372,6 +372,117 @@ class BruteSIPG(BruteDG):
             f_out[e] = -np.linalg.solve(mass[e], B.T).T
         return f_out
 
+    def residual_sipg_oi(self, U, M, alpha=1.0, U_inf=None, explicit=None, U_im=None):
+        """The DG-IP weak form with every volume and face integrand evaluated
+        pointwise (the degree-k state, its gradient and the fluxes at each
+        point of the rule) and integrated by the M-point Gauss rule per
+        direction (Sec. 5: the rule of order 3k); exact dense mass matrix.
+        Pins ``sipg.OverIntegratedSIPG`` (which goes through collocation at
+        the M points instead)."""
+        d, N, nf = self.d, self.N, self.nf
+        mesh, gas = self.mesh, self.gas
+        E = mesh.n_elem
+        U = np.asarray(U, dtype=np.float64)
+        if explicit is not None:
+            U = np.where(np.asarray(explicit, dtype=bool)[:, None, None], U, np.asarray(U_im, dtype=np.float64))
+        ex = np.ones(E, dtype=bool) if explicit is None else np.asarray(explicit, dtype=bool)
+        z, wz = np.polynomial.legendre.leggauss(M)
+        vol = [(np.array([z[i[a]] for a in range(d)]), np.prod([wz[i[a]] for a in range(d)]))
+               for i in itertools.product(range(M), repeat=d)]
+        exact = list(itertools.product(range(len(self.xq)), repeat=d))
+        Ainvs = [np.linalg.inv(self.A[e]) for e in range(E)]
+        Js = [abs(np.linalg.det(self.A[e])) for e in range(E)]
+        mass = []
+        for e in range(E):
+            Mm = np.zeros((N, N))
+            for i in exact:
+                phi, _ = self.basis_at(np.array([self.xq[i[a]] for a in range(d)]))
+                Mm += np.prod([self.wq[i[a]] for a in range(d)]) * np.outer(phi, phi)
+            mass.append(Mm * Js[e])
+        inv_l = np.zeros(E)
+        for e in range(E):
+            area = sum(np.linalg.norm(self.normal(e, a, s)) * 2.0 ** (d - 1) for a in range(d) for s in (0, 1))
+            inv_l[e] = area / (Js[e] * 2.0 ** d)
+
+        def value(e, xi):
+            phi, _ = self.basis_at(xi)
+            return U[e] @ phi
+
+        def grad(e, xi):                                  # [c][nf]
+            _, gref = self.basis_at(xi)
+            return (U[e] @ (gref @ Ainvs[e])).T
+
+        def T(x):
+            return _t(np.asarray(x)[None])
+
+        def visc(Uf, G, Sn=None, wall=False):
+            if wall:
+                return ph.adiabatic_viscous_flux(T(Uf), T(G), T(Sn), gas, d).numpy()[0]
+            return ph.viscous_flux(T(Uf), T(G), gas, d).numpy()[0]
+
+        tk2 = alpha * (mesh.p + 1) ** 2
+        f_out = np.zeros((E, nf, N))
+        for e in range(E):
+            if not ex[e]:
+                continue
+            B = np.zeros((nf, N))
+            for x, w in vol:                              # - int (F^c - F^nu) : grad l_q
+                phi, gref = self.basis_at(x)
+                Ux = U[e] @ phi
+                Fx = ph.convective_flux(T(Ux), gas, d).numpy()[0]
+                if gas.viscous:
+                    Fx = Fx - visc(Ux, grad(e, x))
+                B -= w * Js[e] * np.einsum("if,qi->fq", Fx, gref @ Ainvs[e])
+            for a in range(d):
+                rest = [b for b in range(d) if b != a]
+                for side in (0, 1):
+                    Sn = self.normal(e, a, side)
+                    nbe = mesh.neighbor[e, 2 * a + side]
+                    for iq in itertools.product(range(M), repeat=d - 1):
+                        xi = np.zeros(d)
+                        xi[a] = 1.0 if side else -1.0
+                        wt = 1.0
+                        for k, b in enumerate(rest):
+                            xi[b] = z[iq[k]]
+                            wt *= wz[iq[k]]
+                        Um, Gm = value(e, xi), grad(e, xi)
+                        if nbe >= 0:
+                            nb, xin, Up = neighbour_value(self, e, a, side, xi, U, value)
+                            Gp = grad(nb, xin)
+                            an = int(np.argmax(np.abs(xin)))
+                            Snb = self.normal(nb, an, 1 if xin[an] > 0 else 0)
+                            Sb = 0.5 * (Sn - Snb)
+                            tau = tk2 * max(inv_l[e], inv_l[nb])
+                            F = ph.vijayasundaram_flux(T(Um), T(Up), T(Sb), gas, d).numpy()[0]
+                            if gas.viscous:
+                                dl = np.outer(Sb, Um - Up)
+                                KL, KR = visc(Um, dl), visc(Up, dl)
+                                F = F - 0.5 * (visc(Um, Gm).T @ Sn - visc(Up, Gp).T @ Snb) \
+                                    + tau / np.linalg.norm(Sb) * 0.5 * (KL + KR).T @ Sb
+                                H = 0.5 * KL if ex[nb] else 0.5 * (KL + KR)
+                        elif nbe == -1:                   # adiabatic wall
+                            Ur = ph.mirror_state(T(Um), T(Sn), d).numpy()[0]
+                            F = ph.vijayasundaram_flux(T(Um), T(Ur), T(Sn), gas, d).numpy()[0]
+                            if gas.viscous:
+                                tau = tk2 * inv_l[e]
+                                Uw = ph.wall_state(T(Um), d).numpy()[0]
+                                H = visc(Um, np.outer(Sn, Um - Uw), Sn, True)
+                                F = F - visc(Um, Gm, Sn, True).T @ Sn + tau / np.linalg.norm(Sn) * H.T @ Sn
+                        else:                             # farfield
+                            Ui = np.asarray(U_inf, dtype=np.float64)
+                            UG = ph.farfield_boundary_state(T(Um), T(Ui), T(Sn), gas, d).numpy()[0]
+                            F = ph.normal_convective_flux(T(UG), T(Sn), gas, d).numpy()[0]
+                            if gas.viscous:
+                                tau = tk2 * inv_l[e]
+                                H = visc(Ui, np.outer(Sn, Um - Ui))
+                                F = F - visc(Ui, Gm).T @ Sn + tau / np.linalg.norm(Sn) * H.T @ Sn
+                        phi, gref = self.basis_at(xi)
+                        B += wt * np.outer(F, phi)
+                        if gas.viscous:                   # - int grad l_q . H
+                            B -= wt * np.einsum("cf,qc->fq", H, gref @ Ainvs[e])
+            f_out[e] = -np.linalg.solve(mass[e], B.T).T
+        return f_out
+
     def _face_integral(self, e, a, side, pts, rest, vals, hv, Ainv=None):
         """int_F (face interpolant of vals) l_q ds, or int_F grad l_q . (face
         interpolant of hv) ds, with the higher rule on the reference face (the

@@ -66,7 +66,7 @@ WALL, FARFIELD = 0, 1
 
 
 class SIPGOperator(DGOperator):
-    def __init__(self, mesh, gas, alpha=1.0, U_inf=None, explicit=None):
+    def __init__(self, mesh, gas, alpha=1.0, U_inf=None, explicit=None, k_penalty=None):
         super().__init__(mesh, gas)
         d, n, E = self.d, self.n, self.E
         self.alpha = float(alpha)
@@ -96,7 +96,7 @@ class SIPGOperator(DGOperator):
                 sJ = torch.sqrt((geo.Sn[:, 2 * a0 + side] ** 2).sum(1))       # [E][nfp]
                 area = area + (sJ * wf).sum(1)
         self.inv_l = area / vol                                               # [E]
-        k = mesh.p
+        k = mesh.p if k_penalty is None else k_penalty      # the solution degree of tau = alpha (k+1)^2 / l
         inv_l_nb = self.inv_l[self.nb.clamp(min=0)]
         face_inv_l = torch.where(self.nb >= 0, torch.maximum(self.inv_l[:, None], inv_l_nb),
                                  self.inv_l[:, None].expand(-1, 2 * d))
@@ -293,3 +293,76 @@ class SIPGOperator(DGOperator):
         if return_parts:
             return f, {"Fhat": Fhat, "H": H, "Q": Q, "TU": TU}
         return f
+
+
+
+def over_integration_points(p):
+    """M = ceil((3k + 1) / 2) Gauss points per direction: exact for degree 3k (Sec. 5)."""
+    return (3 * p + 2) // 2
+
+
+class OverIntegratedSIPG:
+    """The DG-IP operator with its volume and face integrals taken by the
+    M-point Gauss rule per direction (Sec. 5: the nonlinear terms are
+    integrated by a rule of order 3k, M = ceil((3k+1)/2) by default) on the
+    degree-k solution space of box meshes; the mass matrix is the Gauss-node
+    one, exact on boxes.
+
+    Written through an identity.  Every degree-k test function l_q lies in
+    the degree-(M-1) Lagrange space of the M Gauss points,
+    l_q = sum_r l_q(z_r) L_r, and the weak form is linear in the test
+    function, so the over-integrated form tested with l_q is
+    sum_r l_q(z_r) B'_r, where B'_r is the collocated degree-(M-1) form of
+    the same polynomial state tested with L_r: collocation at the M points
+    is exactly the M-point rule, and the state's values, traces and
+    gradients there are those of the degree-k polynomial.  With
+    B'_r = -omega_r J f'_r this gives f = Pi f'(I U): I interpolates U to the
+    M points (I[m][j] = l_j(z_m)), f' is the collocated DG-IP operator there
+    with the penalty of the true degree, tau = alpha (k+1)^2 / l, and
+    Pi[q][m] = omega_m l_q(z_m) / w_q projects back.  Pinned by
+    ``brute.BruteSIPG.residual_sipg_oi``, which evaluates every integrand
+    pointwise at the M-point rule instead.
+    """
+
+    def __init__(self, mesh, gas, alpha=1.0, U_inf=None, explicit=None, M=None):
+        import dataclasses
+        from .basis import gauss_legendre, lagrange_eval
+        if mesh.kind != "boxes":
+            raise ValueError("the over-integrated operator takes box meshes")
+        self.mesh, self.gas, self.p = mesh, gas, mesh.p
+        self.d = d = mesh.dim
+        self.n = n = mesh.p + 1
+        self.M = M = over_integration_points(mesh.p) if M is None else int(M)
+        if M < n:
+            raise ValueError("the rule needs at least p + 1 points")
+        x, w = (np.asarray(v) for v in gauss_legendre(n))
+        z, om = (np.asarray(v) for v in gauss_legendre(M))
+        self.I = torch.as_tensor(lagrange_eval(x, z))                           # [M][n]
+        self.Pi = torch.as_tensor(om[None, :] * lagrange_eval(x, z).T / w[:, None])  # [n][M]
+        qi = [(np.arange(M ** d) // M ** a) % M for a in range(d)]             # direction a: stride M^a
+        xyz = np.empty((mesh.n_elem, d, M ** d))
+        for a in range(d):
+            xyz[:, a, :] = mesh.lo[:, a:a + 1] + 0.5 * (1.0 + z[qi[a]])[None, :] * mesh.size[:, a:a + 1]
+        self.mesh_q = dataclasses.replace(mesh, p=M - 1, xyz=xyz)
+        self.inner = SIPGOperator(self.mesh_q, gas, alpha=alpha, U_inf=U_inf, explicit=explicit,
+                                  k_penalty=mesh.p)
+
+    def _apply(self, V, Mat, m_in, m_out):
+        """Mat ([m_out][m_in]) applied along every reference direction."""
+        d = self.d
+        k, c = V.shape[:2]
+        X = V.reshape((k, c) + (m_in,) * d)
+        for a in range(d):
+            X = along(X, a, d, Mat.to(V.dtype))
+        return X.reshape(k, c, m_out ** d)
+
+    def interpolate(self, U):
+        return self._apply(torch.as_tensor(U), self.I, self.n, self.M)
+
+    def project(self, F):
+        return self._apply(torch.as_tensor(F), self.Pi, self.M, self.n)
+
+    def residual(self, U, U_im=None):
+        Uq = self.interpolate(U)
+        Uimq = None if U_im is None else self.interpolate(U_im)
+        return self.project(self.inner.residual(Uq, Uimq))

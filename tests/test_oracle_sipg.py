@@ -10,7 +10,7 @@ import torch
 
 from oracle import physics as ph
 from oracle.brute import BruteSIPG
-from oracle.sipg import SIPGOperator
+from oracle.sipg import OverIntegratedSIPG, SIPGOperator, over_integration_points
 from paper_2607_16044_b300 import inputs as I
 from tests import mms_sympy
 
@@ -317,3 +317,91 @@ def test_manufactured_solution_truncation_order(p, viscous):
         errs.append(np.sqrt(np.mean((f - exact) ** 2)) / np.sqrt(np.mean(exact ** 2)))
     rate = np.log2(errs[0] / errs[1])
     assert rate > (p - 1 if viscous else p) - 0.4, (errs, rate)
+
+
+# ---------------------------------------------------------------- over-integration
+# The order-3k rule of Sec. 5 on the degree-k space: the oracle goes through
+# collocation at the M points; the brute force integrates every volume and face
+# integrand pointwise at the M-point rule, with its own basis and mass matrix.
+
+def test_over_integration_points_are_order_3k():
+    for p in range(1, 6):
+        M = over_integration_points(p)
+        assert 2 * M - 1 >= 3 * p and 2 * (M - 1) - 1 < 3 * p
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("p,M", [(1, 3), (2, 3), (2, 4), (3, 5)])
+def test_over_integration_brute_force_2d_walls(p, M, viscous):
+    m = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 3), I.wall_stretched_edges(2, 1.0)], [True, False])
+    U = I.random_state(m, 20 + p)
+    f1 = OverIntegratedSIPG(m, _gas(viscous), M=M).residual(torch.as_tensor(U)).numpy()
+    f2 = BruteSIPG(m, _gas(viscous), period=[1.0, 100.0]).residual_sipg_oi(U, M)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+def test_over_integration_brute_force_3d():
+    m = I.structured_box_mesh(1, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1.5, 2),
+                                  I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    U = I.random_state(m, 23)
+    f1 = OverIntegratedSIPG(m, _gas(True), M=3).residual(torch.as_tensor(U)).numpy()
+    f2 = BruteSIPG(m, _gas(True), period=[1.0, 1.5, 100.0]).residual_sipg_oi(U, 3)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_over_integration_brute_force_farfield(viscous):
+    m = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 3), I.uniform_edges(0, 1, 2)], [True, False], wall_tag=1)
+    Uinf = np.array([1.1, 0.4, -0.3, 2.0 / 0.4 + 0.5 * (0.4 ** 2 + 0.3 ** 2) / 1.1])
+    U = I.random_state(m, 24)
+    f1 = OverIntegratedSIPG(m, _gas(viscous), U_inf=Uinf).residual(torch.as_tensor(U)).numpy()
+    f2 = BruteSIPG(m, _gas(viscous), period=[1.0, 100.0]).residual_sipg_oi(U, 4, U_inf=Uinf)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+def test_over_integration_brute_force_interface():
+    m = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 4), I.wall_stretched_edges(1, 1.0)], [True, False])
+    explicit = (np.arange(m.n_elem) % 4) != 2
+    U, Uim = I.random_state(m, 25), I.random_state(m, 26)
+    f1 = OverIntegratedSIPG(m, _gas(), explicit=explicit).residual(torch.as_tensor(U), torch.as_tensor(Uim)).numpy()
+    f2 = BruteSIPG(m, _gas(), period=[1.0, 100.0]).residual_sipg_oi(U, 4, explicit=explicit, U_im=Uim)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+    assert np.all(f1[~explicit] == 0)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_over_integration_with_p_plus_1_points_is_the_collocated_operator(viscous):
+    """M = k + 1: the M points are the solution nodes, interpolation and
+    projection are identities, and the operator is the collocated one."""
+    m = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 3), I.wall_stretched_edges(2, 1.0)], [True, False])
+    U = torch.as_tensor(I.random_state(m, 27))
+    f1 = OverIntegratedSIPG(m, _gas(viscous), M=4).residual(U)
+    f0 = SIPGOperator(m, _gas(viscous)).residual(U)
+    assert torch.equal(f1, f0)
+
+
+def test_over_integration_free_stream_and_conservation():
+    m = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 3), I.wall_stretched_edges(3, 1.6, 0.0, 1.0)],
+                              [True, True])
+    op = OverIntegratedSIPG(m, _gas(True))
+    U = np.zeros((m.n_elem, 4, m.N))
+    U[:, 0], U[:, 1], U[:, 2], U[:, 3] = 1.2, 0.3, -0.2, 3.0
+    assert op.residual(torch.as_tensor(U)).abs().max() < 1e-13 * 4.0 / 5e-3
+    f = op.residual(torch.as_tensor(I.random_state(m, 28)))
+    _, w = np.polynomial.legendre.leggauss(3)
+    W = torch.as_tensor(np.multiply.outer(w, w).reshape(-1) * np.prod(m.size, 1)[:, None] / 4.0)
+    tot = (f * W.unsqueeze(1)).sum((0, 2))
+    scale = (f.abs() * W.unsqueeze(1)).sum((0, 2))
+    assert (tot.abs() / scale).max() < 1e-13
+
+
+def test_over_integration_changes_the_aliased_operator():
+    """The rule matters: for a rough state the M-point operator differs from
+    the collocated one (aliasing of the nonlinear fluxes), and raising M
+    further changes it less and less (convergence to the exact integrals)."""
+    m = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 3), I.uniform_edges(0, 1, 2)], [True, True])
+    U = torch.as_tensor(I.random_state(m, 29))
+    f = {M: OverIntegratedSIPG(m, _gas(True), M=M).residual(U) for M in (3, 4, 6, 8, 10)}
+    d = [float((f[M] - f[10]).abs().max() / f[10].abs().max()) for M in (3, 4, 6, 8)]
+    assert d[0] > 1e-4
+    assert d[0] > d[1] > d[2] > d[3]
