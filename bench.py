@@ -696,6 +696,70 @@ def dgip_perf(reps=5):
     return out
 
 
+def oi_perf(reps=5):
+    """The DG-IP operator over-integrated by the order-3k rule (Sec. 5; p = 3,
+    M = 5 Gauss points per direction) next to the collocated one on the same
+    state: the 2D NS channel 256x128 (FP32, FP64) and the 3D NS channel 32^3
+    (FP64); residual, VJP and ARS(3,4,3) step + adjoint, L2 flushed between
+    repetitions; per-kernel times from the library's event profiler."""
+    import torch
+    from paper_2607_16044_b300 import inputs as I
+    from paper_2607_16044_b300.dgx import Solver
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    pk = peaks()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = {}
+    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp64")):
+        alu = alu_peak_tflops(prec)
+        if wl == "channel2d":
+            mesh, phys, U0 = I.channel2d_workload(p=3)
+        else:
+            mesh, phys, U0 = I.channel3d_workload(p=3, nxy=32, n_half=16)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        U = torch.as_tensor(U0).to("cuda", dt).contiguous()
+        lam = torch.as_tensor(np.random.default_rng(106).standard_normal(U0.shape)).to("cuda", dt).contiguous()
+        r = {"dofs": U.numel()}
+        for name, M in (("collocated", None), ("3k", "3k")):
+            s = Solver(mesh, phys, prec, scheme="dgip", quad_points=M)
+            s.set_tableau(*ars343_explicit())
+            f = s.rhs(U)
+            g = s.rhs_vjp(U, lam)
+            U64 = torch.as_tensor(U0).cuda()
+            lam64 = torch.as_tensor(np.random.default_rng(107).standard_normal(U0.shape)).cuda()
+            stages = s.stage_buffer()
+            s.ark_step_adjoint(U64, lam64, 1e-13, stages)
+            ms_rhs = _time_events(lambda: s.rhs(U, out=f), reps, flush)
+            ms_vjp = _time_events(lambda: s.rhs_vjp(U, lam, out=g), reps, flush)
+            ms_sa = _time_events(lambda: s.ark_step_adjoint(U64, lam64, 1e-13, stages), reps, flush)
+            s.profile(True)
+            s.profile_reset()
+            for _ in range(reps):
+                flush.fill_(1)
+                s.rhs(U, out=f)
+                s.rhs_vjp(U, lam, out=g)
+            torch.cuda.synchronize()
+            prof = s.profile_read()
+            s.profile(False)
+            s.check()
+            kern = {}
+            for k, (nl, kms) in prof.items():
+                fl, by = s.kernel_work(k)
+                t = kms / nl / 1e3
+                kern[k] = {"us": round(t * 1e6, 2), "GB/s": round(by / t / 1e9, 1),
+                           "frac_hbm": round(by / t / 1e9 / pk["hbm_gbs"], 3),
+                           "TFLOP/s": round(fl / t / 1e12, 3), "frac_alu": round(fl / t / 1e12 / alu, 3)}
+            n = U.numel()
+            r[name] = {"M": s.quad_points or mesh.p + 1, "ms_rhs": round(ms_rhs, 4), "ms_vjp": round(ms_vjp, 4),
+                       "ms_step_adjoint": round(ms_sa, 4), "rhs_dof_evals_per_s": round(n / (ms_rhs / 1e3), 1),
+                       "step_adjoint_dof_evals_per_s": round(8 * n / (ms_sa / 1e3), 1), "per_kernel": kern}
+            s.close()
+        r["rhs_cost_ratio"] = round(r["3k"]["ms_rhs"] / r["collocated"]["ms_rhs"], 3)
+        out[f"{wl}-{prec}"] = r
+    out["workload"] = ("DG-IP p=3, collocated (4 points) vs over-integrated (5 points per direction, order 3k): "
+                       "2D NS channel 256x128, 3D NS channel 32^3")
+    return out
+
+
 def hdg_perf(cells=64, reps=3):
     """Element-local HDG-IP Newton blocks of the implicit region (the paper's
     HDG-IP, FP64) on a cells x cells periodic 2D NS mesh, degrees 1..5: the
@@ -905,8 +969,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--legs", default="fp64,fp32",
                     help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' / "
-                         "'fp64:channel3d-<nxy>-<layers>' alone (profiling runs), or 'tgv' for the TGV engine "
-                         "comparison")
+                         "'fp64:channel3d-<nxy>-<layers>' alone (profiling runs), 'tgv' for the TGV engine "
+                         "comparison, 'dgip' for the DG-IP legs, or 'oi' for the over-integrated DG-IP comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -929,6 +993,12 @@ def main():
     legs = args.legs.split(",")
     if legs == ["tgv"]:   # the TGV contraction-engine comparison alone (profiling runs)
         print(json.dumps({"tgv": tgv_perf(profile_range=args.profile_range)}))
+        return
+    if legs == ["oi"]:    # the over-integrated DG-IP comparison alone
+        print(json.dumps({"dgip_over_integrated": oi_perf()}))
+        return
+    if legs == ["dgip"]:  # the DG-IP operator's legs alone
+        print(json.dumps({"dgip": dgip_perf()}))
         return
     if len(legs) == 1:    # one precision of one workload alone (profiling runs)
         prec, _, wl = legs[0].partition(":")
@@ -1011,6 +1081,7 @@ def main():
         line["vortex_fp32_vs_fp64"] = vortex_accuracy()
         line["ensemble"] = ensemble_perf()
         line["dgip"] = dgip_perf()
+        line["dgip_over_integrated"] = oi_perf()
         line["hdg"] = hdg_perf()
         line["tgv"] = tgv_perf()
         line["channel3d_trajectory"] = channel3d_trajectory()

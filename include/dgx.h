@@ -94,7 +94,21 @@ typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
  * viscous = 0; Ma only fixes R, which the operator does not depend on.
  * conv_flux / visc_flux select the scheme (LLF + BR1 or Vijayasundaram +
  * SIPG; other pairs give DGX_EUNSUPPORTED; visc_flux is ignored when
- * viscous = 0); penalty_alpha is the SIPG alpha (0 means the paper's 1). */
+ * viscous = 0); penalty_alpha is the SIPG alpha (0 means the paper's 1).
+ *
+ * quad_points (DG-IP scheme, box meshes): 0 = collocated (the volume and face
+ * integrals by the (p+1)-point Gauss rule of the nodes); M in [p+1, 6] = the
+ * nonlinear terms integrated by the M-point Gauss rule per direction (Sec. 5:
+ * a rule of order 3k, M = ceil((3p+1)/2), which is 2, 4, 5 for p = 1, 2, 3;
+ * p = 4, 5 need more points than the kernels have).  The handle then
+ * evaluates f = Pi f'(I U): I interpolates U to the M points, f' is the
+ * collocated DG-IP operator of degree M-1 there with the penalty of degree p,
+ * tau = alpha (p+1)^2 / l, and Pi[q][m] = omega_m l_q(z_m) / w_q projects back
+ * (exact: the degree-p test functions lie in the degree-(M-1) space).  States
+ * stay on the (p+1)^d nodes; every residual, VJP and ARK entry point applies
+ * the rule; dgx_set_mesh_nodes, the HDG entry points and the batch runtime
+ * return DGX_EUNSUPPORTED for such a handle; dgx_mms_source still samples the
+ * source at the nodes.  quad_points is read only by dgx_create. */
 typedef struct {
   int32_t dim;        /* 2 or 3                                  */
   int32_t p;          /* 1 .. 5                                  */
@@ -105,6 +119,7 @@ typedef struct {
   int32_t conv_flux;  /* dgx_conv_flux                           */
   int32_t visc_flux;  /* dgx_visc_flux                           */
   double penalty_alpha;
+  int32_t quad_points;  /* 0 collocated, else M (over-integration)  */
 } dgx_problem_desc;
 
 typedef struct dgx_handle dgx_handle;
@@ -322,7 +337,9 @@ typedef enum {
   DGX_K_DGIP_VJP_ELEM = 12,   /* DG-IP adjoint: element part and face cotangents */
   DGX_K_DGIP_VJP_FACE = 13,   /* DG-IP adjoint: face function (dual numbers)     */
   DGX_K_DGIP_VJP_GATHER = 14, /* DG-IP adjoint: traces and face gradients        */
-  DGX_KERNEL_KINDS = 15
+  DGX_K_OI_TO_QUAD = 15,      /* over-integration: nodes -> M points (I, Pi^T)   */
+  DGX_K_OI_TO_NODES = 16,     /* over-integration: M points -> nodes (Pi, I^T)   */
+  DGX_KERNEL_KINDS = 17
 } dgx_kernel_kind;
 
 /* Per-kernel device timing (tracing).  While enabled, every kernel the

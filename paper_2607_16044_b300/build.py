@@ -119,6 +119,7 @@ def _write_sources():
     units.append(os.path.join(CSRC, "probe.cu"))
     units.append(os.path.join(CSRC, "batchp.cu"))
     units.append(os.path.join(CSRC, "hdg.cu"))
+    units.append(os.path.join(CSRC, "oi.cu"))
     return units
 
 
@@ -133,7 +134,7 @@ def _deps_hash():
     h = hashlib.sha256()
     for root in (CSRC, os.path.join(os.path.dirname(HERE), "include")):
         for name in sorted(os.listdir(root)):
-            if name.endswith((".cu", ".cuh", ".h")):
+            if name.endswith((".cuh", ".h")):  # headers; each unit's own text is in its key
                 h.update(name.encode())
                 h.update(open(os.path.join(root, name), "rb").read())
     h.update(" ".join(ARCH + FLAGS).encode())

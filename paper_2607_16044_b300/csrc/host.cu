@@ -21,6 +21,7 @@
 #include "mms.cuh"
 #include "batchp.h"
 #include "hdg.h"
+#include "oi.h"
 
 using dgx::Tab;
 
@@ -55,7 +56,7 @@ struct dgx_handle {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
-  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
+  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -78,6 +79,15 @@ struct dgx_handle {
   double Uinf[5] = {};
   int8_t* d_mask = nullptr;    // explicit-element mask of the geometry split
   const dgx::DgipTable* dtab = nullptr;
+  int pen_k = -1;              // degree k of tau = alpha (k+1)^2 / l (-1: this handle's p)
+  // over-integration by an M-point rule: the degree-(M-1) DG-IP handle that
+  // evaluates the collocated operator at the M points, and the 1D transfers
+  dgx_handle* inner = nullptr;
+  int Mq = 0;
+  double oiI[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};   // [M][n]  l_j(z_m)
+  double oiP[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};   // [n][M]  omega_m l_q(z_m) / w_q
+  double oiPT[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};  // [M][n]  Pi^T
+  double oiIT[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};  // [n][M]  I^T
   // tableau
   int stages = 0;
   double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
@@ -346,7 +356,8 @@ template <typename S>
 dgx::Dgip<S> dgip_params(const dgx_handle* h, const int8_t* mask, const void* Uim) {
   dgx::Dgip<S> p{};
   p.il = (const S*)h->d_il;
-  p.tk2 = (S)(h->alpha * (h->p + 1) * (h->p + 1));
+  const int k = h->pen_k >= 0 ? h->pen_k : h->p;
+  p.tk2 = (S)(h->alpha * (k + 1) * (k + 1));
   p.mask = mask;
   p.Uim = (const S*)Uim;
   for (int f = 0; f < 5; ++f) p.Uinf[f] = (S)h->Uinf[f];
@@ -731,6 +742,211 @@ dgx_status dgip_ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam6
   return cuda_status(dgx::lincomb<S>(fin, st));
 }
 
+// ------------------------------------------------------------ over-integration
+// f = Pi f'(I U) (Sec. 5, the rule of order 3k): the states live on the
+// (p+1)^d nodes, h->inner evaluates the collocated DG-IP operator of degree
+// M-1 at the M^d points.  Workspace: the interpolated state, the point
+// residual (or cotangent), the point gradient, the U_im interpolant of the
+// split form, then the ARK / adjoint stage arrays at the nodes, then the
+// inner handle's own workspace.
+struct OiLayout {
+  size_t Uq, Fq, Gq, Xq, Y, K, NU, MU, inner, total;
+};
+
+OiLayout layout_oi(const dgx_handle* h, int op) {
+  const dgx_handle* q = h->inner;
+  const size_t sq = align256((size_t)q->E * q->nf * q->N * q->s);
+  const size_t sp = align256((size_t)h->E * h->nf * h->N * h->s);
+  const int s = h->stages > 0 ? h->stages : 1;
+  OiLayout L{};
+  size_t off = 0;
+  L.Uq = off;
+  off += sq;
+  L.Fq = off;
+  off += sq;
+  if (op == DGX_OP_RHS) {
+    L.Xq = off;
+    off += sq;
+  }
+  if (op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT) {
+    L.Gq = off;
+    off += sq;
+  }
+  if (op == DGX_OP_ARK) {
+    L.Y = off;
+    off += sp;
+    L.K = off;
+    off += sp * s;
+  }
+  if (op == DGX_OP_ARK_ADJOINT) {
+    L.NU = off;
+    off += sp * s;
+    L.MU = off;
+    off += sp;
+  }
+  L.inner = off;
+  const int iop = op == DGX_OP_ARK ? DGX_OP_RHS : (op == DGX_OP_ARK_ADJOINT ? DGX_OP_VJP : op);
+  off += layout(q, iop).total;
+  L.total = off;
+  return L;
+}
+
+// one transfer: the [no][ni] matrix a along every direction of each element
+cudaError_t oi_transfer(dgx_handle* h, int kind, const void* in, void* out, bool to_quad, const double* a,
+                        cudaStream_t st) {
+  const int ni = to_quad ? h->n : h->Mq, no = to_quad ? h->Mq : h->n;
+  return launch(h, kind, st,
+                [&] { return dgx::oi_apply(h->d, h->fp64, in, out, h->E, h->nf, ni, no, a, h->nsm, st); });
+}
+
+// f = Pi f'(I U) into out (U_im: the implicit state of the split form, or nullptr)
+template <typename S>
+cudaError_t oi_residual(dgx_handle* h, const void* U, const void* Uim, void* out, char* base, const OiLayout& L,
+                        cudaStream_t st) {
+  dgx_handle* q = h->inner;
+  void* Uq = base + L.Uq;
+  void* Fq = base + L.Fq;
+  void* Xq = Uim ? base + L.Xq : nullptr;
+  cudaError_t err = oi_transfer(h, DGX_K_OI_TO_QUAD, U, Uq, true, h->oiI, st);
+  if (err == cudaSuccess && Uim) err = oi_transfer(h, DGX_K_OI_TO_QUAD, Uim, Xq, true, h->oiI, st);
+  if (err == cudaSuccess) {
+    const dgx::DgipWork w = dgip_work_at(q, base + L.inner, layout(q, DGX_OP_RHS));
+    err = dgip_residual<S>(q, Uq, Uim ? h->d_mask : nullptr, Xq, Fq, w, nullptr, st);
+  }
+  if (err == cudaSuccess) err = oi_transfer(h, DGX_K_OI_TO_NODES, Fq, out, false, h->oiP, st);
+  return err;
+}
+
+// g = I^T (df'/dU')^T (Pi^T lam)
+template <typename S>
+cudaError_t oi_vjp(dgx_handle* h, const void* U, const void* lam, void* g, char* base, const OiLayout& L,
+                   cudaStream_t st) {
+  dgx_handle* q = h->inner;
+  void* Uq = base + L.Uq;
+  void* Lq = base + L.Fq;
+  void* Gq = base + L.Gq;
+  cudaError_t err = oi_transfer(h, DGX_K_OI_TO_QUAD, U, Uq, true, h->oiI, st);
+  if (err == cudaSuccess) err = oi_transfer(h, DGX_K_OI_TO_QUAD, lam, Lq, true, h->oiPT, st);
+  if (err == cudaSuccess) {
+    const dgx::DgipWork w = dgip_work_at(q, base + L.inner, layout(q, DGX_OP_VJP));
+    err = dgip_vjp<S>(q, Uq, Lq, Gq, w, st);
+  }
+  if (err == cudaSuccess) err = oi_transfer(h, DGX_K_OI_TO_NODES, Gq, g, false, h->oiIT, st);
+  return err;
+}
+
+// One explicit ARK step with the over-integrated operator: y_i = U_n +
+// dt sum_{j<i} a_ij k_j formed in FP64 and rounded to the working precision
+// (kept in the stage slots when given), k_i = f(y_i), then
+// U_{n+1} = U_n + dt sum_j b_j k_j accumulated in FP64.
+template <typename S>
+dgx_status oi_ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* workspace, cudaStream_t st) {
+  const OiLayout L = layout_oi(h, DGX_OP_ARK);
+  char* base = (char*)workspace;
+  const size_t n = (size_t)h->E * h->nf * h->N;
+  const size_t sp = align256(n * h->s);
+  auto K = [&](int j) { return (S*)(base + L.K + sp * j); };
+  const Slot SL = slot_layout(h);
+  const int s = h->stages;
+  cudaError_t err = cudaSuccess;
+  for (int i = 0; i < s && err == cudaSuccess; ++i) {
+    S* y = stages ? (S*)((char*)stages + SL.bytes * i + SL.y) : (S*)(base + L.Y);
+    const S* in = y;
+    if (i == 0 && h->fp64 && !stages) {
+      in = (const S*)U64;
+    } else {
+      dgx::LinComb<S> lc{};
+      lc.n = n;
+      lc.lam = U64;
+      lc.c_lam = 1.0;
+      for (int j = 0; j < i; ++j) {
+        const double a = h->A[i * dgx::MAXSTAGES + j];
+        if (a != 0.0) {
+          lc.in[lc.m] = K(j);
+          lc.c[lc.m] = dt * a;
+          ++lc.m;
+        }
+      }
+      lc.out = y;
+      err = dgx::lincomb<S>(lc, st);
+    }
+    if (err == cudaSuccess) err = oi_residual<S>(h, in, nullptr, K(i), base, L, st);
+  }
+  if (err != cudaSuccess) return DGX_ECUDA;
+  dgx::LinComb<S> fin{};
+  fin.n = n;
+  fin.acc64 = U64;
+  for (int j = 0; j < s; ++j)
+    if (h->b[j] != 0.0) {
+      fin.in[fin.m] = K(j);
+      fin.c[fin.m] = dt * h->b[j];
+      ++fin.m;
+    }
+  return cuda_status(dgx::lincomb<S>(fin, st));
+}
+
+// Its discrete adjoint, the reverse stage recurrence of the DG-IP scheme
+// with the over-integrated VJP.
+template <typename S>
+dgx_status oi_ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, double dt, void* workspace,
+                               cudaStream_t st) {
+  const OiLayout L = layout_oi(h, DGX_OP_ARK_ADJOINT);
+  char* base = (char*)workspace;
+  const size_t n = (size_t)h->E * h->nf * h->N;
+  const size_t sp = align256(n * h->s);
+  auto NU = [&](int j) { return (S*)(base + L.NU + sp * j); };
+  S* mu = (S*)(base + L.MU);
+  const Slot SL = slot_layout(h);
+  const int s = h->stages;
+  for (int i = s - 1; i >= 0; --i) {
+    dgx::LinComb<S> lc{};
+    lc.n = n;
+    lc.lam = lam64;
+    lc.c_lam = dt * h->b[i];
+    for (int j = i + 1; j < s; ++j) {
+      const double a = h->A[j * dgx::MAXSTAGES + i];
+      if (a != 0.0) {
+        lc.in[lc.m] = NU(j);
+        lc.c[lc.m] = dt * a;
+        ++lc.m;
+      }
+    }
+    lc.out = mu;
+    cudaError_t err = dgx::lincomb<S>(lc, st);
+    const void* y = (const char*)stages + SL.bytes * i + SL.y;
+    if (err == cudaSuccess) err = oi_vjp<S>(h, y, mu, NU(i), base, L, st);
+    if (err != cudaSuccess) return DGX_ECUDA;
+  }
+  dgx::LinComb<S> fin{};
+  fin.n = n;
+  fin.acc64 = lam64;
+  for (int j = 0; j < s; ++j) {
+    fin.in[fin.m] = NU(j);
+    fin.c[fin.m] = 1.0;
+    ++fin.m;
+  }
+  return cuda_status(dgx::lincomb<S>(fin, st));
+}
+
+// The 1D transfers of an M-point rule on the degree-p nodes (FP64, from the
+// compile-time Gauss rules of basis1d.h): I[m][j] = l_j(z_m),
+// Pi[q][m] = omega_m l_q(z_m) / w_q, and their transposes.
+void oi_matrices(dgx_handle* h) {
+  const dgx::Basis1 b = dgx::make_basis1(h->p), z = dgx::make_basis1(h->Mq - 1);
+  const int n = b.n, M = z.n;
+  for (int m = 0; m < M; ++m)
+    for (int j = 0; j < n; ++j) {
+      double l = 1.0;
+      for (int k = 0; k < n; ++k)
+        if (k != j) l *= (z.x[m] - b.x[k]) / (b.x[j] - b.x[k]);
+      h->oiI[m * n + j] = l;
+      h->oiIT[j * M + m] = l;
+      const double pq = z.w[m] * l / b.w[j];
+      h->oiP[j * M + m] = pq;
+      h->oiPT[m * n + j] = pq;
+    }
+}
+
 // ------------------------------------------------------------ work model
 struct Pointwise {
   double conv, visc, visc_n, wall_visc, llf_unit, llf_area, conv_vjp, visc_vjp, visc_n_vjp, llf_unit_vjp,
@@ -800,6 +1016,25 @@ Pointwise count_pointwise() {
 
 // Algorithmic flops and bytes of one launch of a kernel kind on this handle.
 void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
+  if (h->inner && kind >= DGX_K_DGIP_TRACE && kind <= DGX_K_DGIP_VJP_GATHER) {  // run at the M points
+    kernel_work(h->inner, kind, flops, bytes);
+    return;
+  }
+  if (kind == DGX_K_OI_TO_QUAD || kind == DGX_K_OI_TO_NODES) {  // one transfer: values in and out
+    flops = bytes = 0.0;
+    if (!h->inner) return;
+    const int ni = kind == DGX_K_OI_TO_QUAD ? h->n : h->Mq, no = kind == DGX_K_OI_TO_QUAD ? h->Mq : h->n;
+    double macs = 0.0, ext = 1.0;  // pass a: no x (no^a ni^(d-1-a)) outputs of ni terms each
+    for (int a = 0; a < h->d; ++a) {
+      double pts = 1.0;
+      for (int b = 0; b < h->d; ++b) pts *= b <= a ? no : ni;
+      macs += pts * ni;
+      ext = pts;
+    }
+    flops = 2.0 * h->E * h->nf * macs;
+    bytes = (double)h->E * h->nf * (ext + std::pow((double)ni, h->d)) * h->s;
+    return;
+  }
   const Pointwise pc = h->d == 2 ? count_pointwise<2>() : count_pointwise<3>();
   const double E = h->E, N = h->N, nf = h->nf, nfp = h->nfp, NF = h->NF, D = h->d, n = h->n, s = (double)h->s;
   const double STATE = nf * N, FACE = NF * nf * nfp, F = h->nFaces;
@@ -959,7 +1194,8 @@ const char* dgx_kernel_name(int32_t kind) {
   static const char* names[DGX_KERNEL_KINDS] = {"trace",      "br1",           "face",          "elem",
                                                 "elem_stage", "vjp_elem",      "vjp_face",      "vjp_br1",
                                                 "vjp_gather", "dgip_trace",    "dgip_face",     "dgip_elem",
-                                                "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather"};
+                                                "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather",
+                                                "oi_to_quad",    "oi_to_nodes"};
   return (kind >= 0 && kind < DGX_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 
@@ -972,14 +1208,23 @@ dgx_status dgx_profile_enable(dgx_handle* h, int32_t enable) {
   }
   if (!enable && h->prof) profile_collect(h);
   h->prof = enable != 0;
-  return DGX_OK;
+  return h->inner ? dgx_profile_enable(h->inner, enable) : DGX_OK;
 }
 
 dgx_status dgx_profile_read(dgx_handle* h, int32_t kind, int64_t* launches, double* ms) {
   if (!h || kind < 0 || kind >= DGX_KERNEL_KINDS) return DGX_EINVAL;
   profile_collect(h);
-  if (launches) *launches = h->prof_launches[kind];
-  if (ms) *ms = h->prof_ms[kind];
+  int64_t nl = h->prof_launches[kind];
+  double t = h->prof_ms[kind];
+  if (h->inner) {  // the point operator's kernels
+    int64_t il = 0;
+    double im = 0.0;
+    dgx_profile_read(h->inner, kind, &il, &im);
+    nl += il;
+    t += im;
+  }
+  if (launches) *launches = nl;
+  if (ms) *ms = t;
   return DGX_OK;
 }
 
@@ -999,7 +1244,7 @@ dgx_status dgx_profile_reset(dgx_handle* h) {
     h->prof_launches[k] = 0;
     h->prof_ms[k] = 0.0;
   }
-  return DGX_OK;
+  return h->inner ? dgx_profile_reset(h->inner) : DGX_OK;
 }
 
 const char* dgx_status_string(dgx_status s) {
@@ -1036,6 +1281,10 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   const bool dgip = desc->conv_flux == DGX_FLUX_VIJAYASUNDARAM;
   // the schemes are LLF + BR1 and Vijayasundaram + SIPG
   if (desc->viscous && (desc->visc_flux == DGX_VISC_SIPG) != dgip) return DGX_EUNSUPPORTED;
+  if (desc->quad_points != 0) {  // over-integration: DG-IP, p + 1 <= M <= the kernels' largest n
+    if (desc->quad_points < desc->p + 1) return DGX_EINVAL;
+    if (!dgip || desc->quad_points > dgx::OI_MAXQ) return DGX_EUNSUPPORTED;
+  }
   dgx_handle* h = new (std::nothrow) dgx_handle();
   if (!h) return DGX_ENOMEM;
   h->desc = *desc;
@@ -1091,6 +1340,17 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
                        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess))
     st = DGX_ECUDA;
+  if (st == DGX_OK && desc->quad_points != 0) {  // the degree-(M-1) operator at the M points
+    dgx_problem_desc dq = *desc;
+    dq.p = desc->quad_points - 1;
+    dq.quad_points = 0;
+    st = dgx_create(&dq, &h->inner);
+    if (st == DGX_OK) {
+      h->inner->pen_k = h->p;
+      h->Mq = desc->quad_points;
+      oi_matrices(h);
+    }
+  }
   if (st != DGX_OK) {
     dgx_destroy(h);
     return st;
@@ -1101,6 +1361,7 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
 
 dgx_status dgx_destroy(dgx_handle* h) {
   if (!h) return DGX_EINVAL;
+  if (h->inner) dgx_destroy(h->inner);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_mesh(h);
   if (h->d_mask) cudaFree(h->d_mask);
@@ -1151,16 +1412,17 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   h->h_size.assign(size, size + (size_t)E * d);
   h->h_xyz.clear();
   h->curv = false;
-  h->has_mesh = true;
   h->mesh64 = mesh_view<double>(h);
   h->mesh32 = mesh_view<float>(h);
+  if (h->inner && (st = dgx_set_mesh_boxes(h->inner, lo, size, neighbor, nbr_face, orient)) != DGX_OK) return st;
+  h->has_mesh = true;
   return DGX_OK;
 }
 
 dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
                               const int8_t* orient) {
   if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
-  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels take box meshes
+  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels (and their over-integration) take box meshes
   const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
   for (size_t i = 0; i < (size_t)E * d * N; ++i)
     if (!std::isfinite(xyz[i])) return DGX_EINVAL;
@@ -1287,6 +1549,10 @@ size_t dgx_workspace_bytes(const dgx_handle* h, int32_t op) {
   }
   if (op < DGX_OP_RHS || op > DGX_OP_ARK_STEP_ADJOINT) return 0;
   if ((op == DGX_OP_VJP || op == DGX_OP_ARK_ADJOINT || op == DGX_OP_ARK_STEP_ADJOINT) && !h->tab->vjp) return 0;
+  if (h->inner) {
+    if (op == DGX_OP_ARK_STEP_ADJOINT) return layout_oi(h, DGX_OP_ARK).total + layout_oi(h, DGX_OP_ARK_ADJOINT).total;
+    return layout_oi(h, op).total;
+  }
   if (op == DGX_OP_ARK_STEP_ADJOINT)  // the forward's and the adjoint's workspaces side by side
     return layout(h, DGX_OP_ARK).total + layout(h, DGX_OP_ARK_ADJOINT).total;
   return layout(h, op).total;
@@ -1298,8 +1564,13 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
-    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->inner) {
+      const OiLayout L = layout_oi(h, DGX_OP_RHS);
+      return cuda_status(h->fp64 ? oi_residual<double>(h, U, nullptr, dUdt, (char*)workspace, L, st)
+                                 : oi_residual<float>(h, U, nullptr, dUdt, (char*)workspace, L, st));
+    }
+    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
     return cuda_status(h->fp64 ? dgip_residual<double>(h, U, nullptr, nullptr, dUdt, w, nullptr, st)
                                : dgip_residual<float>(h, U, nullptr, nullptr, dUdt, w, nullptr, st));
   }
@@ -1334,8 +1605,13 @@ dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* g
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
-    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_VJP));
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->inner) {
+      const OiLayout L = layout_oi(h, DGX_OP_VJP);
+      return cuda_status(h->fp64 ? oi_vjp<double>(h, U, lambda, gU, (char*)workspace, L, st)
+                                 : oi_vjp<float>(h, U, lambda, gU, (char*)workspace, L, st));
+    }
+    const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_VJP));
     return cuda_status(h->fp64 ? dgip_vjp<double>(h, U, lambda, gU, w, st) : dgip_vjp<float>(h, U, lambda, gU, w, st));
   }
   const Layout L = layout(h, DGX_OP_VJP);
@@ -1359,6 +1635,9 @@ dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, 
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    if (h->inner)
+      return h->fp64 ? oi_ark_impl<double>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream)
+                     : oi_ark_impl<float>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
     return h->fp64 ? dgip_ark_impl<double>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream)
                    : dgip_ark_impl<float>(h, U64, dt, nullptr, workspace, (cudaStream_t)stream);
   }
@@ -1373,6 +1652,9 @@ dgx_status dgx_ark_step_stages(dgx_handle* h, double* U64, double dt, void* stag
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+    if (h->inner)
+      return h->fp64 ? oi_ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream)
+                     : oi_ark_impl<float>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
     return h->fp64 ? dgip_ark_impl<double>(h, U64, dt, stages, workspace, (cudaStream_t)stream)
                    : dgip_ark_impl<float>(h, U64, dt, stages, workspace, (cudaStream_t)stream);
   }
@@ -1386,6 +1668,10 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
+  if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+  if (h->inner)
+    return h->fp64 ? oi_ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream)
+                   : oi_ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
   if (h->dgip)
     return h->fp64 ? dgip_ark_adjoint_impl<double>(h, stages, lam64, dt, workspace, (cudaStream_t)stream)
                    : dgip_ark_adjoint_impl<float>(h, stages, lam64, dt, workspace, (cudaStream_t)stream);
@@ -1400,6 +1686,16 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
   if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
+  if (h->inner) {  // the step, then its adjoint, on the caller's stream
+    char* ws2 = (char*)workspace + layout_oi(h, DGX_OP_ARK).total;
+    dgx_status s = h->fp64 ? oi_ark_impl<double>(h, U64, dt, stages, workspace, st)
+                           : oi_ark_impl<float>(h, U64, dt, stages, workspace, st);
+    if (s == DGX_OK)
+      s = h->fp64 ? oi_ark_adjoint_impl<double>(h, stages, lam64, dt, ws2, st)
+                  : oi_ark_adjoint_impl<float>(h, stages, lam64, dt, ws2, st);
+    return s;
+  }
   if (h->dgip) {  // the step, then its adjoint, on the caller's stream
     char* ws2 = (char*)workspace + layout(h, DGX_OP_ARK).total;
     dgx_status s = h->fp64 ? dgip_ark_impl<double>(h, U64, dt, stages, workspace, st)
@@ -1428,7 +1724,7 @@ dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls) {
   h->wait_polls = polls < 0 ? (1u << 22) : (uint32_t)std::min<int64_t>(polls, 1u << 22);
   h->mesh64.wait_polls = h->wait_polls;
   h->mesh32.wait_polls = h->wait_polls;
-  return DGX_OK;
+  return h->inner ? dgx_set_wait_limit(h->inner, polls) : DGX_OK;
 }
 
 dgx_status dgx_hdg_sizes(const dgx_handle* h, int32_t* nu, int32_t* nh) {
@@ -1441,7 +1737,7 @@ dgx_status dgx_hdg_sizes(const dgx_handle* h, int32_t* nu, int32_t* nh) {
 dgx_status dgx_hdg_blocks(dgx_handle* h, const double* U, const double* Uhat, double gamma, double* K, double* C,
                           double* D, double* A33, double* R, double* hres, void* stream) {
   if (!h || !U || !Uhat || !K || !C || !D || !A33 || !std::isfinite(gamma) || (!R) != (!hres)) return DGX_EINVAL;
-  if (!h->fp64 || h->d != 2) return DGX_EUNSUPPORTED;
+  if (!h->fp64 || h->d != 2 || h->inner) return DGX_EUNSUPPORTED;
   if (!h->has_mesh || h->curv) return h->curv ? DGX_EUNSUPPORTED : DGX_ESTATE;
   if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   dgx::HdgArgs a{};
@@ -1461,7 +1757,7 @@ dgx_status dgx_hdg_condense(dgx_handle* h, const double* K, const double* C, con
                             double* KinvC, double* S, void* workspace, void* stream) {
   if (!h || !K || !C || !D || !A33 || !KinvC || !S || !workspace) return DGX_EINVAL;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
-  if (!h->fp64 || h->d != 2) return DGX_EUNSUPPORTED;
+  if (!h->fp64 || h->d != 2 || h->inner) return DGX_EUNSUPPORTED;
   if (!h->has_mesh) return DGX_ESTATE;
   const int nu = h->nf * h->N, nh = h->NF * h->nf * h->nfp;
   return cuda_status(dgx::hdg_condense(h->E, nu, nh, K, C, D, A33, KinvC, S, (double*)workspace,
@@ -1479,7 +1775,7 @@ dgx_status dgx_set_farfield(dgx_handle* h, const double* U_inf) {
   if (!(U_inf[0] > 0.0) || !(p > 0.0)) return DGX_EINVAL;  // not a physical state
   for (int f = 0; f < 5; ++f) h->Uinf[f] = f < h->nf ? U_inf[f] : 0.0;
   h->has_uinf = true;
-  return DGX_OK;
+  return h->inner ? dgx_set_farfield(h->inner, U_inf) : DGX_OK;
 }
 
 dgx_status dgx_set_explicit_mask(dgx_handle* h, const int8_t* mask) {
@@ -1502,8 +1798,13 @@ dgx_status dgx_rhs_split(dgx_handle* h, const void* U_ex, const void* U_im, void
   if (!h->has_mesh || !h->d_mask) return DGX_ESTATE;
   if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
-  const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->inner) {
+    const OiLayout L = layout_oi(h, DGX_OP_RHS);
+    return cuda_status(h->fp64 ? oi_residual<double>(h, U_ex, U_im, dUdt, (char*)workspace, L, st)
+                               : oi_residual<float>(h, U_ex, U_im, dUdt, (char*)workspace, L, st));
+  }
+  const dgx::DgipWork w = dgip_work_at(h, workspace, layout(h, DGX_OP_RHS));
   return cuda_status(h->fp64 ? dgip_residual<double>(h, U_ex, h->d_mask, U_im, dUdt, w, nullptr, st)
                              : dgip_residual<float>(h, U_ex, h->d_mask, U_im, dUdt, w, nullptr, st));
 }
@@ -1536,6 +1837,12 @@ dgx_status dgx_check(dgx_handle* h) {
   unsigned flags = 0;
   if (cudaMemcpy(&flags, h->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return DGX_ECUDA;
   if (cudaMemset(h->d_flags, 0, sizeof(unsigned)) != cudaSuccess) return DGX_ECUDA;
+  if (h->inner) {  // the point residuals' flags
+    const dgx_status si = dgx_check(h->inner);
+    if (si == DGX_ECUDA) return si;
+    if (si == DGX_ENONFINITE) flags |= 1u;
+    if (si == DGX_ETIMEOUT) flags |= 2u;
+  }
   if (flags & 1u) return DGX_ENONFINITE;
   if (flags & 2u) return DGX_ETIMEOUT;
   return DGX_OK;

@@ -1,0 +1,17 @@
+// Over-integration of the DG-IP operator by an M-point Gauss rule (see oi.cu):
+// host interface of the tensor-product transfer between the solution nodes
+// and the quadrature points.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dgx {
+
+constexpr int OI_MAXQ = 6;  // points per direction (the kernels' largest degree + 1)
+
+// out[e][f] = (A x A [x A]) in[e][f]: the [no][ni] matrix A applied along
+// every reference direction of each element's nodal field ([E][nf][ni^D] in,
+// [E][nf][no^D] out, direction 0 fastest).  a is row-major in FP64.
+cudaError_t oi_apply(int D, bool fp64, const void* in, void* out, int E, int nf, int ni, int no, const double* a,
+                     int nsm, cudaStream_t st);
+
+}  // namespace dgx

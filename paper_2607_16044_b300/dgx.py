@@ -34,7 +34,7 @@ class _Desc(ctypes.Structure):
                 ("viscous", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("gamma", ctypes.c_double), ("Re", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("Ma", ctypes.c_double), ("conv_flux", ctypes.c_int32), ("visc_flux", ctypes.c_int32),
-                ("penalty_alpha", ctypes.c_double)]
+                ("penalty_alpha", ctypes.c_double), ("quad_points", ctypes.c_int32)]
 
 
 _lib = None
@@ -53,7 +53,8 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
-           "dgip_trace", "dgip_face", "dgip_elem", "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather"]
+           "dgip_trace", "dgip_face", "dgip_elem", "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather",
+           "oi_to_quad", "oi_to_nodes"]
 
 
 def load_library(path: str = LIB_PATH):
@@ -170,10 +171,13 @@ class Solver:
 
     ``mesh`` is a :class:`paper_2607_16044_b300.inputs.Mesh`; ``phys`` an
     :class:`inputs.Physics`.  ``precision`` is "fp64" or "fp32".
+    ``quad_points`` (DG-IP scheme, box meshes): None for the collocated
+    operator, "3k" for the over-integration rule of order 3k (M = (3p+2)//2
+    Gauss points per direction), or an explicit M in [p+1, 6].
     """
 
     def __init__(self, mesh, phys, precision: str = "fp64", device: Optional[torch.device] = None,
-                 scheme: str = "llf-br1", alpha: float = 1.0, U_inf=None):
+                 scheme: str = "llf-br1", alpha: float = 1.0, U_inf=None, quad_points=None):
         if not torch.cuda.is_available():
             raise RuntimeError("dgx needs a CUDA device; there is no CPU fallback")
         self.lib = load_library()
@@ -184,8 +188,12 @@ class Solver:
         self.device = device or torch.device("cuda", torch.cuda.current_device())
         conv, visc = SCHEMES[scheme]
         self.scheme = scheme
+        if quad_points == "3k":
+            quad_points = (3 * mesh.p + 2) // 2
+        self.quad_points = int(quad_points or 0)
         desc = _Desc(mesh.dim, mesh.p, mesh.n_elem, int(phys.viscous), FP64 if precision == "fp64" else FP32,
-                     phys.gamma, phys.Re if phys.viscous else 0.0, phys.Pr, phys.Ma, conv, visc, float(alpha))
+                     phys.gamma, phys.Re if phys.viscous else 0.0, phys.Pr, phys.Ma, conv, visc, float(alpha),
+                     self.quad_points)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.dgx_create(ctypes.byref(desc), ctypes.byref(h)), "dgx_create")

@@ -1,0 +1,212 @@
+"""GPU parity of the over-integrated DG-IP operator (the nonlinear terms by the
+M-point Gauss rule of order 3k, Sec. 5) against the FP64 oracle
+(oracle.sipg.OverIntegratedSIPG): residual, VJP, geometry-split form, ARK step
+and its adjoint, and the M = p+1 case, which is the collocated operator bit
+for bit."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ark
+from oracle.residual import submesh_around
+from oracle.sipg import OverIntegratedSIPG, SIPGOperator
+from oracle.vjp import vjp
+from paper_2607_16044_b300 import inputs as I
+from tests.parity_util import TOL, gas_of, quantize32, record, rel_err
+
+pytestmark = pytest.mark.gpu
+
+UINF2 = np.array([1.1, 0.4, -0.3, 2.0 / 0.4 + 0.5 * (0.4 ** 2 + 0.3 ** 2) / 1.1])
+
+
+def _solver(mesh, phys, prec, M="3k", **kw):
+    from paper_2607_16044_b300.dgx import Solver
+    return Solver(mesh, phys, prec, scheme="dgip", quad_points=M, **kw)
+
+
+def _euler():
+    return I.Physics(gamma=1.4, viscous=False)
+
+
+def _ns(Re=200.0):
+    return I.Physics(gamma=1.4, Re=Re, Pr=0.72, Ma=0.3, viscous=True)
+
+
+def _dt(prec):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def _oracle(mesh, phys, M=None, **kw):
+    return OverIntegratedSIPG(mesh, gas_of(phys), M=M, **kw)
+
+
+def _rhs_check(mesh, phys, prec, name, M="3k", seed=700, U_inf=None):
+    U = I.random_state(mesh, seed)
+    s = _solver(mesh, phys, prec, M, U_inf=U_inf)
+    f = s.rhs(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    Uref = U if prec == "fp64" else quantize32(U)
+    ref = _oracle(mesh, phys, None if M == "3k" else M, U_inf=U_inf).residual(torch.as_tensor(Uref)).numpy()
+    err = rel_err(f.double().cpu().numpy(), ref)
+    record(name, rel=err, E=mesh.n_elem, M=s.quad_points)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_oi_2d_walls_stretched(p, viscous, prec):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 7), I.wall_stretched_edges(3, 1.5)], [True, False])
+    _rhs_check(mesh, _ns() if viscous else _euler(), prec, f"oi-2d-{viscous}-p{p}-{prec}", seed=700 + p)
+
+
+@pytest.mark.parametrize("p,M", [(1, 3), (1, 6), (2, 3), (2, 5), (2, 6), (4, 6)])
+def test_oi_2d_other_rules(p, M):
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])
+    _rhs_check(mesh, _ns(), "fp64", f"oi-2d-p{p}-M{M}", M=M, seed=710 + M)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_oi_3d_walls(p, prec):
+    cells = {1: 3, 2: 2, 3: 2}[p]
+    mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells), I.uniform_edges(0, 1.2, cells + 1),
+                                     I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    _rhs_check(mesh, _ns(), prec, f"oi-3d-p{p}-{prec}", seed=720 + p)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_oi_farfield(viscous):
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.uniform_edges(0, 1, 4)], [True, False], wall_tag=1)
+    _rhs_check(mesh, _ns() if viscous else _euler(), "fp64", f"oi-farfield-{viscous}", seed=730, U_inf=UINF2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_oi_with_p_plus_1_points_is_the_collocated_operator(dim, prec):
+    """M = p+1: the transfers are identities (exactly: l_j at the nodes is 0 or
+    1, omega_m / w_q = 1), so residual and VJP equal the collocated handle's
+    bit for bit."""
+    if dim == 2:
+        mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])
+    else:
+        mesh = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1, 3),
+                                         I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    U = torch.as_tensor(I.random_state(mesh, 740)).to("cuda", _dt(prec)).contiguous()
+    lam = torch.as_tensor(I.gaussian_cotangent(U.shape, 741)).to("cuda", _dt(prec)).contiguous()
+    s0 = _solver(mesh, _ns(), prec, None)
+    s1 = _solver(mesh, _ns(), prec, mesh.p + 1)
+    assert torch.equal(s0.rhs(U), s1.rhs(U))
+    assert torch.equal(s0.rhs_vjp(U, lam), s1.rhs_vjp(U, lam))
+    s0.check()
+    s1.check()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 3), (3, 2)])
+def test_oi_vjp(dim, p, prec):
+    if dim == 2:
+        mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])
+    else:
+        mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1.2, 3),
+                                         I.wall_stretched_edges(1, 1.0)], [True, True, False])
+    U = I.random_state(mesh, 750 + p)
+    lam = I.gaussian_cotangent(U.shape, 751 + p)
+    s = _solver(mesh, _ns(), prec)
+    g = s.rhs_vjp(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous(),
+                  torch.as_tensor(lam).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    if prec == "fp32":
+        U, lam = quantize32(U), quantize32(lam)
+    ref = vjp(_oracle(mesh, _ns()), torch.as_tensor(U), torch.as_tensor(lam)).numpy()
+    err = rel_err(g.double().cpu().numpy(), ref)
+    record(f"oi-vjp-{dim}d-p{p}-{prec}", rel=err)
+    assert err < TOL[prec], err
+
+
+def test_oi_geometry_split_interface():
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 6), I.wall_stretched_edges(2, 1.3)], [True, False])
+    col = np.arange(mesh.n_elem) % 6
+    explicit = (col != 2) & (col != 3)
+    Uex, Uim = I.random_state(mesh, 760), I.random_state(mesh, 761)
+    s = _solver(mesh, _ns(), "fp64")
+    s.set_explicit_mask(explicit)
+    f = s.rhs_split(torch.as_tensor(Uex).cuda(), torch.as_tensor(Uim).cuda()).cpu().numpy()
+    s.check()
+    ref = _oracle(mesh, _ns(), explicit=explicit).residual(torch.as_tensor(Uex), torch.as_tensor(Uim)).numpy()
+    assert np.all(f[~explicit] == 0)
+    err = rel_err(f[explicit], ref[explicit])
+    record("oi-split-2d", rel=err)
+    assert err < TOL["fp64"], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_oi_ark_step_and_adjoint(prec):
+    """One ARS(3,4,3) step with the over-integrated operator and its discrete
+    adjoint against the oracle's recurrences; the one-call step + adjoint
+    equals the separate calls bit for bit."""
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.3)], [True, False])
+    phys = _ns()
+    U0 = I.random_state(mesh, 770)
+    lam0 = I.gaussian_cotangent(U0.shape, 771)
+    dt = 2e-5
+    s = _solver(mesh, phys, prec)
+    s.set_tableau(*ars343_explicit())
+    U = torch.as_tensor(U0).cuda()
+    s.ark_step(U, dt)
+    Us = torch.as_tensor(U0).cuda()
+    stages = s.stage_buffer()
+    s.ark_step_stages(Us, dt, stages)
+    lam = torch.as_tensor(lam0).cuda()
+    s.ark_adjoint_step(stages, lam, dt)
+    U2, lam2 = torch.as_tensor(U0).cuda(), torch.as_tensor(lam0).cuda()
+    s.ark_step_adjoint(U2, lam2, dt, s.stage_buffer())
+    s.check()
+    assert torch.equal(Us, U2) and torch.equal(lam, lam2)
+    op = _oracle(mesh, phys)
+    A, b, c = ark.ars343()
+    Uref, ys, _ = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b, return_stages=True)
+    err = rel_err(U.cpu().numpy() - U0, Uref.numpy() - U0)
+    record(f"oi-ark-{prec}", rel=err)
+    assert err < TOL[prec], err
+    assert rel_err(Us.cpu().numpy() - U0, Uref.numpy() - U0) < TOL[prec]
+    if prec == "fp32":
+        ys = [torch.as_tensor(quantize32(y.numpy())) for y in ys]
+    ref = ark.erk_adjoint_step(lambda y, mu: vjp(op, y, mu), ys, torch.as_tensor(lam0), dt, A, b).numpy()
+    err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
+    record(f"oi-ark-adjoint-{prec}", rel=err)
+    assert err < TOL[prec], err
+
+
+def test_oi_differs_from_collocated_where_it_should():
+    """On a rough state the order-3k rule changes the residual (aliasing);
+    on a uniform flow both vanish."""
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.uniform_edges(0, 1, 4)], [True, True])
+    U = torch.as_tensor(I.random_state(mesh, 780)).cuda()
+    f0 = _solver(mesh, _ns(), "fp64", None).rhs(U)
+    f1 = _solver(mesh, _ns(), "fp64").rhs(U)
+    assert float((f1 - f0).abs().max() / f0.abs().max()) > 1e-4
+    Uc = torch.zeros_like(U)
+    Uc[:, 0], Uc[:, 1], Uc[:, 2], Uc[:, 3] = 1.2, 0.3, -0.2, 3.0
+    assert float(_solver(mesh, _ns(), "fp64").rhs(Uc).abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_oi_channel2d_p3_full_size_sampled(prec):
+    """The 256 x 128 wall-stretched 2D channel at p = 3 with the order-3k rule
+    (M = 5): sampled elements including both walls against the oracle on
+    their 2-ring sub-mesh; FP32 on the 10 %-perturbed state."""
+    mesh, phys, _ = I.channel2d_workload(p=3)
+    U = I.channel_state(mesh, phys, 2, amp=0.1 if prec == "fp32" else 1e-3)
+    s = _solver(mesh, phys, prec)
+    f = s.rhs(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous()).double().cpu().numpy()
+    s.check()
+    rng = np.random.default_rng(19)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, 16, replace=False), [0, mesh.n_elem - 1]]))
+    Uref = U if prec == "fp64" else quantize32(U)
+    sub, keep, loc = submesh_around(mesh, rows, 2)
+    ref = _oracle(sub, phys).residual(torch.as_tensor(Uref[keep])).numpy()[loc]
+    err = rel_err(f[rows], ref)
+    record(f"oi-channel2d-p3-{prec}", rel=err, sampled=len(rows))
+    assert err < TOL[prec], err

@@ -74,3 +74,40 @@ def test_binding_constants_match_header():
     assert len(dgx.KERNELS) == kinds["DGX_KERNEL_KINDS"]
     for i, name in enumerate(dgx.KERNELS):
         assert kinds["DGX_K_" + name.upper()] == i
+
+
+def test_problem_desc_layout_matches_header(tmp_path):
+    """The binding's dgx_problem_desc has the header's fields at the header's
+    offsets (compiled with the host C compiler)."""
+    import ctypes
+    from paper_2607_16044_b300 import dgx
+    names = [n for n, _ in dgx._Desc._fields_]
+    src = tmp_path / "desc.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dgx.h"\nint main(void) {\n'
+                   + "".join(f'  printf("%zu\\n", offsetof(dgx_problem_desc, {n}));\n' for n in names)
+                   + '  printf("%zu\\n", sizeof(dgx_problem_desc));\n  return 0;\n}\n')
+    exe = tmp_path / "desc"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [getattr(dgx._Desc, n).offset for n in names] + [ctypes.sizeof(dgx._Desc)]
+    assert got == want
+
+
+@pytest.mark.skipif(not os.path.exists(LIB), reason="library not built")
+def test_over_integration_descriptor_checks_without_gpu():
+    """quad_points below p + 1 is invalid; above the kernels' largest rule, or
+    with the LLF scheme, unsupported (answered before any device work)."""
+    import ctypes
+    from paper_2607_16044_b300 import dgx
+    lib = dgx.load_library()
+
+    def create(p, M, scheme="dgip"):
+        conv, visc = dgx.SCHEMES[scheme]
+        d = dgx._Desc(2, p, 4, 1, dgx.FP64, 1.4, 100.0, 0.72, 0.3, conv, visc, 1.0, M)
+        h = ctypes.c_void_p()
+        return lib.dgx_create(ctypes.byref(d), ctypes.byref(h))
+
+    status = _enum_values("DGX_E")
+    assert create(3, 3) == status["DGX_EINVAL"]
+    assert create(5, 8) == status["DGX_EUNSUPPORTED"]
+    assert create(2, 4, "llf-br1") == status["DGX_EUNSUPPORTED"]
