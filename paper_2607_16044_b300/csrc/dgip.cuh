@@ -614,27 +614,32 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
   }
 }
 
-// Cotangents of one face point's inputs by forward-mode differentiation of
-// dgip_face_fn: one dual pass per input component.
+// Cotangents of one face point's inputs: interior faces by the hand-written
+// reverse mode (dgip_face_interior_vjp); boundary faces by forward-mode
+// differentiation of dgip_face_fn, one dual pass per input component.
 template <int D, typename S, bool VISC, int KIND>
 __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
                                                  const Gas<S>& g, const Gas<S>& gw, S tau, bool ifL, bool ifR,
                                                  const S (&Fb)[D + 2], const S (&HLb)[D][D + 2],
                                                  const S (&HRb)[D][D + 2], S (&ULb)[D + 2], S (&URb)[D + 2]) {
   constexpr int nf = D + 2;
+  if constexpr (KIND == DGIP_INTERIOR) {
+#pragma unroll
+    for (int f = 0; f < nf; ++f) ULb[f] = URb[f] = S(0);
+    dgip_face_interior_vjp<D, S, VISC>(UL, UR, nv, g, tau, ifL, ifR, Fb, HLb, HRb, ULb, URb);
+    return;
+  }
   using T = Dual<S, 1>;
   const Gas<T> gd = gas_as<T, S>(g), gwd = gas_as<T, S>(gw);
-  constexpr int NIN = KIND == DGIP_INTERIOR ? 2 * nf : nf;
 #pragma unroll 1
-  for (int k = 0; k < NIN; ++k) {
+  for (int k = 0; k < nf; ++k) {
     T L[nf], R[nf], F[nf], HL[D][nf], HR[D][nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       L[f] = T(UL[f]);
       R[f] = T(UR[f]);
     }
-    if (k < nf) L[k].d[0] = S(1);
-    else R[k - nf].d[0] = S(1);
+    L[k].d[0] = S(1);
     dgip_face_fn<D, T, S, VISC, KIND>(L, R, nv, gd, gwd, tau, ifL, ifR, F, HL, HR);
     S s = 0;
 #pragma unroll
@@ -643,13 +648,9 @@ __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          s += HL[c][f].d[0] * HLb[c][f];
-          if (KIND == DGIP_INTERIOR) s += HR[c][f].d[0] * HRb[c][f];
-        }
+        for (int f = 0; f < nf; ++f) s += HL[c][f].d[0] * HLb[c][f];
     }
-    if (k < nf) ULb[k] = s;
-    else URb[k - nf] = s;
+    ULb[k] = s;
   }
 }
 
@@ -659,26 +660,8 @@ template <int D, typename S, bool VISC>
 inline void dgip_face_fn_vjp_host(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D], const Gas<S>& g,
                                   S tau, const S (&Fb)[D + 2], const S (&HLb)[D][D + 2], const S (&HRb)[D][D + 2],
                                   S (&ULb)[D + 2], S (&URb)[D + 2]) {
-  constexpr int nf = D + 2;
-  using T = Dual<S, 1>;
-  const Gas<T> gd = gas_as<T, S>(g);
-  for (int k = 0; k < 2 * nf; ++k) {
-    T L[nf], R[nf], F[nf], HL[D][nf], HR[D][nf];
-    for (int f = 0; f < nf; ++f) {
-      L[f] = T(UL[f]);
-      R[f] = T(UR[f]);
-    }
-    if (k < nf) L[k].d[0] = S(1);
-    else R[k - nf].d[0] = S(1);
-    dgip_face_fn<D, T, S, VISC, DGIP_INTERIOR>(L, R, nv, gd, gd, tau, false, false, F, HL, HR);
-    S s = S(0);
-    for (int f = 0; f < nf; ++f) s += F[f].d[0] * Fb[f];
-    if (VISC)
-      for (int c = 0; c < D; ++c)
-        for (int f = 0; f < nf; ++f) s += HL[c][f].d[0] * HLb[c][f] + HR[c][f].d[0] * HRb[c][f];
-    if (k < nf) ULb[k] = s;
-    else URb[k - nf] = s;
-  }
+  for (int f = 0; f < D + 2; ++f) ULb[f] = URb[f] = S(0);
+  dgip_face_interior_vjp<D, S, VISC>(UL, UR, nv, g, tau, false, false, Fb, HLb, HRb, ULb, URb);
 }
 
 // k_dgip_vjp_face: one thread per unique face point: cotangents of both sides'

@@ -354,4 +354,176 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
   }
 }
 
+
+// Reverse-mode adjoint of dgip_face_fn on an interior face: given the
+// cotangents Fb of F and HLb, HRb of the adjoint-consistency vectors,
+// ULb += (dF/dUL)^T Fb + (dHL/dUL)^T HLb + (dHR/dUL)^T HRb and likewise URb.
+// Written statement by statement against vij_flux (F_n(Ubar) through
+// conv_flux_all_vjp, then the wave sum |A| dU / 2 reversed through the
+// characteristic quantities of Waves) and the K-products (visc_flux_all_vjp at
+// the rank-one gradient nv (x) delta).  d|x|/dx = sign(x), sign(0) = 0, as the
+// dual numbers take it.
+template <int D, typename S, bool VISC>
+__host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2],
+                                                                const S (&nv)[D], const Gas<S>& g, S tau_over_s,
+                                                                bool ifL, bool ifR, const S (&Fb)[D + 2],
+                                                                const S (&HLb)[D][D + 2], const S (&HRb)[D][D + 2],
+                                                                S (&ULb)[D + 2], S (&URb)[D + 2]) {
+  constexpr int nf = D + 2;
+  using ::sqrt;
+  S n2 = S(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
+  const S sJ = sqrt(n2);
+  S nh[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  S Ub[nf], dU[nf];
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    Ub[f] = S(0.5) * (UL[f] + UR[f]);
+    dU[f] = UL[f] - UR[f];
+  }
+  // forward: characteristic quantities at Ubar
+  const S rho = Ub[0], ir = S(1) / rho;
+  S u[D], q2 = S(0), un = S(0), udm = S(0), ndm = S(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    u[i] = Ub[1 + i] * ir;
+    q2 += u[i] * u[i];
+    un += u[i] * nh[i];
+  }
+  const S p = g.gm1 * (Ub[D + 1] - S(0.5) * rho * q2);
+  const S c2 = g.gamma * p * ir;
+  const S c = sqrt(c2);
+  const S H = (Ub[D + 1] + p) * ir;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    udm += u[i] * dU[1 + i];
+    ndm += nh[i] * dU[1 + i];
+  }
+  const S dp = g.gm1 * (S(0.5) * q2 * dU[0] - udm + dU[D + 1]);
+  const S rdun = ndm - un * dU[0];
+  const S i2c2 = S(0.5) / c2;
+  const S am = (dp - c * rdun) * i2c2, ap = (dp + c * rdun) * i2c2;
+  const S l0 = fabs(un), lm = fabs(un - c), lp = fabs(un + c);
+  const S cm = (lm - l0) * am, cp = (lp - l0) * ap;
+  // reverse of F += hs (l0 dU + cm rm + cp rp)
+  const S hs = S(0.5) * sJ;
+  S dUb[nf], l0b = S(0), cmb = S(0), cpb = S(0), Hb = S(0), unb = S(0), cb = S(0), ub[D];
+  {
+    S G[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      G[f] = hs * Fb[f];
+      dUb[f] = l0 * G[f];
+      l0b += G[f] * dU[f];
+    }
+    // rm = (1, u - c nh, H - c un), rp = (1, u + c nh, H + c un)
+    cmb = G[0];
+    cpb = G[0];
+    S nr = S(0);  // sum_i nh_i (G_{1+i} cp - G_{1+i} cm) folded below
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      cmb += G[1 + i] * (u[i] - c * nh[i]);
+      cpb += G[1 + i] * (u[i] + c * nh[i]);
+      ub[i] = (cm + cp) * G[1 + i];
+      nr += nh[i] * G[1 + i];
+    }
+    cmb += G[D + 1] * (H - c * un);
+    cpb += G[D + 1] * (H + c * un);
+    Hb = (cm + cp) * G[D + 1];
+    cb = (cp - cm) * (nr + un * G[D + 1]);
+    unb = c * (cp - cm) * G[D + 1];
+  }
+  // cm = (lm - l0) am, cp = (lp - l0) ap
+  const S lmb = cmb * am, lpb = cpb * ap;
+  l0b -= cmb * am + cpb * ap;
+  const S amb = cmb * (lm - l0), apb = cpb * (lp - l0);
+  // l0 = |un|, lm = |un - c|, lp = |un + c|
+  const S sm = sgn(un - c), sp = sgn(un + c);
+  unb += sgn(un) * l0b + sm * lmb + sp * lpb;
+  cb += sp * lpb - sm * lmb;
+  // am = (dp - c rdun) i2c2, ap = (dp + c rdun) i2c2
+  const S dpb = (amb + apb) * i2c2;
+  const S rdunb = c * (apb - amb) * i2c2;
+  cb += rdun * (apb - amb) * i2c2;
+  const S i2c2b = amb * (dp - c * rdun) + apb * (dp + c * rdun);
+  S c2b = -i2c2b * i2c2 / c2;
+  // rdun = ndm - un dU0
+  const S ndmb = rdunb;
+  unb -= dU[0] * rdunb;
+  dUb[0] -= un * rdunb;
+  // dp = gm1 (q2 dU0 / 2 - udm + dU_E)
+  S q2b = g.gm1 * S(0.5) * dU[0] * dpb;
+  dUb[0] += g.gm1 * S(0.5) * q2 * dpb;
+  const S udmb = -g.gm1 * dpb;
+  dUb[D + 1] += g.gm1 * dpb;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ub[i] += udmb * dU[1 + i];
+    dUb[1 + i] += udmb * u[i] + ndmb * nh[i];
+  }
+  // c = sqrt(c2), c2 = gamma p ir, H = (E + p) ir
+  c2b += cb * S(0.5) / c;
+  const S pb0 = Hb * ir + c2b * g.gamma * ir;
+  S Eb = Hb * ir;
+  S irb = Hb * (Ub[D + 1] + p) + c2b * g.gamma * p;
+  // p = gm1 (E - rho q2 / 2)
+  Eb += g.gm1 * pb0;
+  S rhob = -g.gm1 * S(0.5) * q2 * pb0;
+  q2b -= g.gm1 * S(0.5) * rho * pb0;
+  // un = u . nh, q2 = u . u, u = m ir
+  S Ubb[nf];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ub[i] += nh[i] * unb + S(2) * u[i] * q2b;
+    Ubb[1 + i] = ub[i] * ir;
+    irb += ub[i] * Ub[1 + i];
+  }
+  rhob -= irb * ir * ir;
+  Ubb[0] = rhob;
+  Ubb[D + 1] = Eb;
+  {  // F_n(Ubar) = sum_c nv_c F_c(Ubar)
+    S Fcb[D][nf];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Fcb[a][f] = nv[a] * Fb[f];
+    conv_flux_all_vjp<D, S>(Ub, Fcb, g, Ubb);
+  }
+#pragma unroll
+  for (int f = 0; f < nf; ++f) {
+    ULb[f] += S(0.5) * Ubb[f] + dUb[f];
+    URb[f] += S(0.5) * Ubb[f] - dUb[f];
+  }
+  if (VISC) {
+    // F += (tau / 2) sum_c (KL + KR)[c] nv_c; HL = KL / 2 (+ KR / 2 at an
+    // interface), HR = KR / 2 (+ KL / 2); K(U) = F^nu(U, nv (x) delta)
+    const S h = S(0.5) * tau_over_s;
+    S KLb[D][nf], KRb[D][nf], Q[D][nf], QLb[D][nf], QRb[D][nf];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        const S fb = h * nv[a] * Fb[f];
+        KLb[a][f] = fb + S(0.5) * HLb[a][f] + (ifR ? S(0.5) * HRb[a][f] : S(0));
+        KRb[a][f] = fb + S(0.5) * HRb[a][f] + (ifL ? S(0.5) * HLb[a][f] : S(0));
+        Q[a][f] = nv[a] * dU[f];
+        QLb[a][f] = S(0);
+        QRb[a][f] = S(0);
+      }
+    visc_flux_all_vjp<D, S>(UL, Q, KLb, g, ULb, QLb);
+    visc_flux_all_vjp<D, S>(UR, Q, KRb, g, URb, QRb);
+#pragma unroll
+    for (int f = 0; f < nf; ++f) {
+      S db = S(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) db += nv[a] * (QLb[a][f] + QRb[a][f]);
+      ULb[f] += db;
+      URb[f] -= db;
+    }
+  }
+}
+
 }  // namespace dgx
