@@ -87,11 +87,21 @@ __device__ __forceinline__ void face_gradient(const S* us, const S* tu, const S*
       const int st = tan_stride<D, P>(c, a0);
       const int ic = (fp / st) % n;
       const int base = fp - ic * st;
+      // row ic of D by selects among compile-time constants (a runtime index
+      // into the constexpr table would copy it to local memory)
+      S row[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) {
+        S v = tb.D[0][m];
+#pragma unroll
+        for (int k = 1; k < n; ++k) v = (ic == k) ? tb.D[k][m] : v;
+        row[m] = v;
+      }
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         S s = 0;
 #pragma unroll
-        for (int m = 0; m < n; ++m) s += tb.D[ic][m] * tu[f * nfp + base + m * st];
+        for (int m = 0; m < n; ++m) s += row[m] * tu[f * nfp + base + m * st];
         Q[c][f] = r * s;
       }
     }
@@ -363,9 +373,15 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
       for (int a0 = 0; a0 < D; ++a0) {
         const S r0 = M.geo.rh[e * D + a0];
         const int fp = H::fpoint(q, a0), k0 = H::qa(q, a0);
+        S Lm0 = tb.Lm[0], Lp0 = tb.Lp[0];  // L(-+1) at node k0 by selects (no runtime table index)
+#pragma unroll
+        for (int k = 1; k < n; ++k) {
+          Lm0 = (k0 == k) ? tb.Lm[k] : Lm0;
+          Lp0 = (k0 == k) ? tb.Lp[k] : Lp0;
+        }
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-          const S L = r0 * (side ? tb.Lp[k0] : tb.Lm[k0]);
+          const S L = r0 * (side ? Lp0 : Lm0);
           const S* hf = has + (t * NF + 2 * a0 + side) * D * nf * nfp + fp;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -856,11 +872,19 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
         const int st = tan_stride<D, P>(c, a0);
         const int ic = (fp / st) % n;
         const int base = fp - ic * st;
+        S col[n];  // column ic of D by selects among compile-time constants
+#pragma unroll
+        for (int j = 0; j < n; ++j) {
+          S v = tb.D[j][0];
+#pragma unroll
+          for (int k = 1; k < n; ++k) v = (ic == k) ? tb.D[j][k] : v;
+          col[j] = v;
+        }
 #pragma unroll
         for (int f = 0; f < nf; ++f) {
           S s = 0;
 #pragma unroll
-          for (int j = 0; j < n; ++j) s += tb.D[j][ic] * qo[(c * nf + f) * nfp + base + j * st];
+          for (int j = 0; j < n; ++j) s += col[j] * qo[(c * nf + f) * nfp + base + j * st];
           acc[f] += r * s;
         }
       }
