@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_elem(Mesh<S> M, co
 
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool CURV>
-__global__ void __launch_bounds__(256, 6) k_vjp_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ FFb,
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 2 : 6) k_vjp_face(Mesh<S> M, const S* __restrict__ TU, const S* __restrict__ FFb,
                                                   S* __restrict__ TUb) {
   using H = Sh<D, P>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
