@@ -97,10 +97,10 @@ typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
  * viscous = 0); penalty_alpha is the SIPG alpha (0 means the paper's 1).
  *
  * quad_points (DG-IP scheme, box meshes): 0 = collocated (the volume and face
- * integrals by the (p+1)-point Gauss rule of the nodes); M in [p+1, 6] = the
+ * integrals by the (p+1)-point Gauss rule of the nodes); M in [p+1, 8] = the
  * nonlinear terms integrated by the M-point Gauss rule per direction (Sec. 5:
- * a rule of order 3k, M = ceil((3p+1)/2), which is 2, 4, 5 for p = 1, 2, 3;
- * p = 4, 5 need more points than the kernels have).  The handle then
+ * a rule of order 3k, M = ceil((3p+1)/2), which is 2, 4, 5, 7, 8 for
+ * p = 1 .. 5).  The handle then
  * evaluates f = Pi f'(I U): I interpolates U to the M points, f' is the
  * collocated DG-IP operator of degree M-1 there with the penalty of degree p,
  * tau = alpha (p+1)^2 / l, and Pi[q][m] = omega_m l_q(z_m) / w_q projects back

@@ -69,6 +69,18 @@ const Table* table_d{D}_{T}_p{P}() {{
 }}  // namespace dgx
 """
 
+# degrees above the LLF/BR1 range: the DG-IP launch table alone (the point
+# operator of over-integration with 7 or 8 points per direction)
+DGIP_DEGREES = (6, 7)
+
+DGIP_UNIT = """// generated by build.py: the DG-IP launch table alone for (D={D}, S={S}, P={P})
+#include "dispatch.h"
+#include "dgip.cuh"
+namespace dgx {{
+const void* dgip_only_d{D}_{T}_p{P}() {{ return dgip_table<{D}, {P}, {S}>(); }}
+}}  // namespace dgx
+"""
+
 TC_FN = """  static cudaError_t elem_tc(const void* M, int tc, bool v, bool c, const void* U, const Work& w, void* out,
                              const void* sa, cudaStream_t st) {{
     return TcOps<{D}, {P}>::elem(m(M), tc, v, c, (const float*)U, w, (float*)out, (const Stage<float>*)sa, st);
@@ -110,6 +122,16 @@ def _write_sources():
                 _write_if_changed(path, src)
                 units.append(path)
             funcs.append(f"const Table* table_d{D}_{T}(int P) {{\n  switch (P) {{\n" + "\n".join(cases)
+                         + "\n    default: return nullptr;\n  }\n}")
+            only = []
+            for P in DGIP_DEGREES:
+                name = f"dgip_only_d{D}_{T}_p{P}"
+                decls.append(f"const void* {name}();")
+                only.append(f"    case {P}: return {name}();")
+                path = os.path.join(BUILD, f"dgip_unit_d{D}_{T}_p{P}.cu")
+                _write_if_changed(path, DGIP_UNIT.format(D=D, S=S, P=P, T=T))
+                units.append(path)
+            funcs.append(f"const void* dgip_only_d{D}_{T}(int P) {{\n  switch (P) {{\n" + "\n".join(only)
                          + "\n    default: return nullptr;\n  }\n}")
     path = os.path.join(BUILD, "dispatch_gen.cu")
     _write_if_changed(path, DISPATCH.format(DECLS="\n".join(decls), FUNCS="\n".join(funcs)))

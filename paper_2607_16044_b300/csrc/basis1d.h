@@ -15,7 +15,7 @@
 
 namespace dgx {
 
-constexpr int MAXN = 6;  // p <= 5
+constexpr int MAXN = 8;  // p <= 7 (degrees 6 and 7 serve only as the point operator of over-integration)
 
 struct Basis1 {
   int n;

@@ -38,4 +38,11 @@ const Table* table_d3_f64(int P);
 const Table* table_d2_f32(int P);
 const Table* table_d3_f32(int P);
 
+// DG-IP launch table (a DgipTable) alone for degrees 6 and 7, the point
+// operator of over-integration with 7 or 8 points per direction; else nullptr.
+const void* dgip_only_d2_f64(int P);
+const void* dgip_only_d3_f64(int P);
+const void* dgip_only_d2_f32(int P);
+const void* dgip_only_d3_f32(int P);
+
 }  // namespace dgx

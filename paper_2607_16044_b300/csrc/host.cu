@@ -121,12 +121,13 @@ template <typename S>
 void fill_tab(int p, Tab<S>& t) {
   std::memset(&t, 0, sizeof(t));
   const dgx::Tab1<S> c = dgx::make_tab1<S>(p);
-  for (int i = 0; i < dgx::MAXN; ++i)
-    for (int j = 0; j < dgx::MAXN; ++j) {
-      t.D[i * 6 + j] = c.D[i][j];
-      t.Dh[i * 6 + j] = c.Dh[i][j];
+  constexpr int W = 6;  // Tab<S> holds degrees up to 5
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < W; ++j) {
+      t.D[i * W + j] = c.D[i][j];
+      t.Dh[i * W + j] = c.Dh[i][j];
     }
-  for (int j = 0; j < dgx::MAXN; ++j) {
+  for (int j = 0; j < W; ++j) {
     t.lm[j] = c.lm[j];
     t.lp[j] = c.lp[j];
     t.Lm[j] = c.Lm[j];
@@ -1266,12 +1267,14 @@ __attribute__((visibility("hidden"))) int dgx_internal_handle_device(const dgx_h
   return h ? h->dev : -1;
 }
 
-dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
+// point_op: the degree-(M-1) DG-IP handle of an over-integrated handle, whose
+// degree may reach 7 (DG-IP launch table alone above 5).
+static dgx_status create_impl(const dgx_problem_desc* desc, dgx_handle** out, bool point_op) {
   if (!out) return DGX_EINVAL;
   *out = nullptr;
   if (!desc) return DGX_EINVAL;
   if (desc->dim != 2 && desc->dim != 3) return DGX_EINVAL;
-  if (desc->p < 1 || desc->p > 5 || desc->n_elem < 1) return DGX_EINVAL;
+  if (desc->p < 1 || desc->p > (point_op ? 7 : 5) || desc->n_elem < 1) return DGX_EINVAL;
   if (desc->precision != DGX_FP64 && desc->precision != DGX_FP32) return DGX_EINVAL;
   if (!(desc->gamma > 1.0)) return DGX_EINVAL;
   if (desc->viscous && (!(desc->Re > 0.0) || !(desc->Pr > 0.0))) return DGX_EINVAL;
@@ -1302,13 +1305,18 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   h->s = h->fp64 ? 8 : 4;
   h->dgip = dgip;
   h->alpha = desc->penalty_alpha > 0.0 ? desc->penalty_alpha : 1.0;
-  if (h->d == 2) h->tab = h->fp64 ? dgx::table_d2_f64(h->p) : dgx::table_d2_f32(h->p);
-  else h->tab = h->fp64 ? dgx::table_d3_f64(h->p) : dgx::table_d3_f32(h->p);
-  if (!h->tab || (h->dgip && !h->tab->dgip)) {
+  if (h->p <= 5) {
+    if (h->d == 2) h->tab = h->fp64 ? dgx::table_d2_f64(h->p) : dgx::table_d2_f32(h->p);
+    else h->tab = h->fp64 ? dgx::table_d3_f64(h->p) : dgx::table_d3_f32(h->p);
+    h->dtab = h->tab ? (const dgx::DgipTable*)h->tab->dgip : nullptr;
+  } else if (h->dgip) {  // point operator of degree 6 or 7: DG-IP launches only
+    if (h->d == 2) h->dtab = (const dgx::DgipTable*)(h->fp64 ? dgx::dgip_only_d2_f64(h->p) : dgx::dgip_only_d2_f32(h->p));
+    else h->dtab = (const dgx::DgipTable*)(h->fp64 ? dgx::dgip_only_d3_f64(h->p) : dgx::dgip_only_d3_f32(h->p));
+  }
+  if ((!h->tab && h->p <= 5) || (h->dgip && !h->dtab)) {
     delete h;
     return DGX_EUNSUPPORTED;
   }
-  h->dtab = (const dgx::DgipTable*)h->tab->dgip;
   dgx_status st = DGX_OK;
   if (h->fp64) {
     std::vector<Tab<double>> t(6);
@@ -1321,7 +1329,7 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   }
   // default tile variant: about 256 threads, or the largest smaller one whose
   // shared memory fits (small 3D elements in FP64)
-  for (int k = 0; k < DGX_KERNEL_KINDS; ++k) {
+  for (int k = 0; k < DGX_KERNEL_KINDS && h->tab; ++k) {
     if (!is_tile_kind(k)) continue;
     int v = 1;
     while (v > 0 && tile_smem(h, k, v) > dgx::SMEM_LIMIT) --v;
@@ -1344,7 +1352,7 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
     dgx_problem_desc dq = *desc;
     dq.p = desc->quad_points - 1;
     dq.quad_points = 0;
-    st = dgx_create(&dq, &h->inner);
+    st = create_impl(&dq, &h->inner, /*point_op=*/true);
     if (st == DGX_OK) {
       h->inner->pen_k = h->p;
       h->Mq = desc->quad_points;
@@ -1358,6 +1366,8 @@ dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) {
   *out = h;
   return DGX_OK;
 }
+
+dgx_status dgx_create(const dgx_problem_desc* desc, dgx_handle** out) { return create_impl(desc, out, false); }
 
 dgx_status dgx_destroy(dgx_handle* h) {
   if (!h) return DGX_EINVAL;

@@ -126,6 +126,8 @@ cudaError_t run(const void* in, void* out, int E, const double* a, int nsm, cuda
   return cudaGetLastError();
 }
 
+// (ni, no) pairs: the nodes have at most 6 points per direction (p <= 5), the
+// quadrature points at most 8; one side of every transfer is the nodes.
 template <int D, typename S, int NI>
 cudaError_t by_no(int no, const void* in, void* out, int E, const double* a, int nsm, cudaStream_t st) {
   switch (no) {
@@ -134,6 +136,12 @@ cudaError_t by_no(int no, const void* in, void* out, int E, const double* a, int
     case 4: return run<D, S, NI, 4>(in, out, E, a, nsm, st);
     case 5: return run<D, S, NI, 5>(in, out, E, a, nsm, st);
     case 6: return run<D, S, NI, 6>(in, out, E, a, nsm, st);
+    case 7:
+      if constexpr (NI <= 6) return run<D, S, NI, 7>(in, out, E, a, nsm, st);
+      return cudaErrorInvalidValue;
+    case 8:
+      if constexpr (NI <= 6) return run<D, S, NI, 8>(in, out, E, a, nsm, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -146,6 +154,12 @@ cudaError_t by_ni(int ni, int no, const void* in, void* out, int E, const double
     case 4: return by_no<D, S, 4>(no, in, out, E, a, nsm, st);
     case 5: return by_no<D, S, 5>(no, in, out, E, a, nsm, st);
     case 6: return by_no<D, S, 6>(no, in, out, E, a, nsm, st);
+    case 7:
+      if (no <= 6) return by_no<D, S, 7>(no, in, out, E, a, nsm, st);
+      return cudaErrorInvalidValue;
+    case 8:
+      if (no <= 6) return by_no<D, S, 8>(no, in, out, E, a, nsm, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -6,7 +6,7 @@
 
 namespace dgx {
 
-constexpr int OI_MAXQ = 6;  // points per direction (the kernels' largest degree + 1)
+constexpr int OI_MAXQ = 8;  // points per direction (the DG-IP kernels' largest degree + 1)
 
 // out[e][f] = (A x A [x A]) in[e][f]: the [no][ni] matrix A applied along
 // every reference direction of each element's nodal field ([E][nf][ni^D] in,

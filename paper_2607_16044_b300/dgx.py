@@ -173,7 +173,7 @@ class Solver:
     :class:`inputs.Physics`.  ``precision`` is "fp64" or "fp32".
     ``quad_points`` (DG-IP scheme, box meshes): None for the collocated
     operator, "3k" for the over-integration rule of order 3k (M = (3p+2)//2
-    Gauss points per direction), or an explicit M in [p+1, 6].
+    Gauss points per direction), or an explicit M in [p+1, 8].
     """
 
     def __init__(self, mesh, phys, precision: str = "fp64", device: Optional[torch.device] = None,

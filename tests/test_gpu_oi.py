@@ -53,23 +53,23 @@ def _rhs_check(mesh, phys, prec, name, M="3k", seed=700, U_inf=None):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("viscous", [False, True])
 def test_oi_2d_walls_stretched(p, viscous, prec):
     mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 7), I.wall_stretched_edges(3, 1.5)], [True, False])
     _rhs_check(mesh, _ns() if viscous else _euler(), prec, f"oi-2d-{viscous}-p{p}-{prec}", seed=700 + p)
 
 
-@pytest.mark.parametrize("p,M", [(1, 3), (1, 6), (2, 3), (2, 5), (2, 6), (4, 6)])
+@pytest.mark.parametrize("p,M", [(1, 3), (1, 6), (2, 3), (2, 5), (2, 6), (4, 6), (3, 8), (5, 7)])
 def test_oi_2d_other_rules(p, M):
     mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])
     _rhs_check(mesh, _ns(), "fp64", f"oi-2d-p{p}-M{M}", M=M, seed=710 + M)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 def test_oi_3d_walls(p, prec):
-    cells = {1: 3, 2: 2, 3: 2}[p]
+    cells = {1: 3, 2: 2, 3: 2, 4: 1, 5: 1}[p]
     mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells), I.uniform_edges(0, 1.2, cells + 1),
                                      I.wall_stretched_edges(1, 1.0)], [True, True, False])
     _rhs_check(mesh, _ns(), prec, f"oi-3d-p{p}-{prec}", seed=720 + p)
@@ -103,7 +103,7 @@ def test_oi_with_p_plus_1_points_is_the_collocated_operator(dim, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("dim,p", [(2, 2), (2, 3), (3, 2)])
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 3), (2, 5), (3, 2), (3, 4)])
 def test_oi_vjp(dim, p, prec):
     if dim == 2:
         mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)], [True, False])

@@ -95,7 +95,7 @@ def test_problem_desc_layout_matches_header(tmp_path):
 
 @pytest.mark.skipif(not os.path.exists(LIB), reason="library not built")
 def test_over_integration_descriptor_checks_without_gpu():
-    """quad_points below p + 1 is invalid; above the kernels' largest rule, or
+    """quad_points below p + 1 is invalid; above 8 points (the largest rule), or
     with the LLF scheme, unsupported (answered before any device work)."""
     import ctypes
     from paper_2607_16044_b300 import dgx
@@ -109,5 +109,5 @@ def test_over_integration_descriptor_checks_without_gpu():
 
     status = _enum_values("DGX_E")
     assert create(3, 3) == status["DGX_EINVAL"]
-    assert create(5, 8) == status["DGX_EUNSUPPORTED"]
+    assert create(5, 9) == status["DGX_EUNSUPPORTED"]
     assert create(2, 4, "llf-br1") == status["DGX_EUNSUPPORTED"]
