@@ -184,15 +184,21 @@ def aggregate_rate(units_per_rank, ms_max, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 def make_solver(prec, workload="channel3d"):
+    """Solver, mesh, physics and state of a workload name: "channel3d" (48^3
+    p = 5), "channel2d" (256x128 p = 4), "channel3d-<cells in x, y>-<layers
+    per wall>"; a "dgip-" prefix selects the DG-IP scheme on the same mesh."""
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
     from paper_2607_16044_b300.tableaux import ars343_explicit
+    scheme = "llf-br1"
+    if workload.startswith("dgip-"):
+        scheme, workload = "dgip", workload[len("dgip-"):]
     if workload.startswith("channel3d-"):   # a smaller 3D channel, "channel3d-<cells in x, y>-<layers per wall>"
         nxy, nh = (int(v) for v in workload.split("-")[1:3])
         mesh, phys, U0 = I.channel3d_workload(nxy=nxy, n_half=nh)
     else:
         mesh, phys, U0 = I.channel3d_workload() if workload == "channel3d" else I.channel2d_workload()
-    s = Solver(mesh, phys, prec)
+    s = Solver(mesh, phys, prec, scheme=scheme)
     A, b, c = ars343_explicit()
     s.set_tableau(A, b, c)
     return s, mesh, phys, U0
@@ -203,6 +209,11 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
     + the discrete adjoint of that step (4 VJPs), L2 flushed between steps."""
     import torch
     s, mesh, phys, U0 = make_solver(prec, workload)
+    if workload.startswith("dgip-"):
+        # the DG-IP penalty on the 2e-5-thin wall cells makes |f| ~ 4e8: a step
+        # far below the explicit limit keeps repeated steps finite (the work of
+        # a step does not depend on dt)
+        dt = 1e-13
     dev = torch.device("cuda", torch.cuda.current_device())
     U = torch.as_tensor(U0, device=dev).contiguous()
     lam0 = np.random.default_rng(102).standard_normal(U0.shape)
@@ -621,8 +632,8 @@ def ensemble_perf(reps=10, steps_err=20):
 
 def dgip_perf(reps=5):
     """The paper's DG-IP operator (Vijayasundaram flux + symmetric interior
-    penalty) on the 2D channel (256x128, p = 4) in FP32 and FP64 and on the 3D
-    channel (48^3, p = 5) in FP64: residual, VJP and one ARS(3,4,3) step, L2
+    penalty) on the 2D channel (256x128, p = 4) and on the 3D channel (48^3,
+    p = 5), each in FP32 and FP64: residual, VJP and one ARS(3,4,3) step, L2
     flushed between repetitions; per-kernel work from the library's event
     profiler; and the geometry-split residual R^DG(U^ex, U^im) of the 2D
     channel with the 16 element rows next to each wall implicit."""
@@ -633,7 +644,7 @@ def dgip_perf(reps=5):
     pk = peaks()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {}
-    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp64")):
+    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp32"), ("channel3d", "fp64")):
         mesh, phys, U0 = I.channel2d_workload() if wl == "channel2d" else I.channel3d_workload()
         s = Solver(mesh, phys, prec, scheme="dgip")
         s.set_tableau(*ars343_explicit())
@@ -692,7 +703,7 @@ def dgip_perf(reps=5):
         out[f"{wl}-{prec}"] = r
         s.close()
     out["workload"] = ("DG-IP (Vijayasundaram + SIPG, alpha = 1): 2D NS channel 256x128 p=4 and 3D NS channel "
-                       "48^3 p=5, residual / VJP / ARS(3,4,3) step")
+                       "48^3 p=5 (FP32, FP64), residual / VJP / ARS(3,4,3) step / step + adjoint")
     return out
 
 
@@ -973,7 +984,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--legs", default="fp64,fp32",
                     help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' / "
-                         "'fp64:channel3d-<nxy>-<layers>' alone (profiling runs), 'tgv' for the TGV engine "
+                         "'fp64:channel3d-<nxy>-<layers>' / 'fp64:dgip-channel3d-<nxy>-<layers>' alone (profiling "
+                         "runs), 'tgv' for the TGV engine "
                          "comparison, 'dgip' for the DG-IP legs, or 'oi' for the over-integrated DG-IP comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")

@@ -210,3 +210,46 @@ def test_oi_channel2d_p3_full_size_sampled(prec):
     err = rel_err(f[rows], ref)
     record(f"oi-channel2d-p3-{prec}", rel=err, sampled=len(rows))
     assert err < TOL[prec], err
+
+
+def test_oi_handle_bookkeeping():
+    """An over-integrated handle: the event profiler reports the two transfers
+    and the point operator's three DG-IP kernels per residual; a non-finite
+    state is flagged through the point operator's kernels; the calls it does
+    not support answer DGX_EUNSUPPORTED; the allocation-free entry point gives
+    the workspace-based residual."""
+    import ctypes
+    from paper_2607_16044_b300.dgx import DGXError
+    mesh = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 4), I.wall_stretched_edges(2, 1.3)], [True, False])
+    s = _solver(mesh, _ns(), "fp64")
+    U = torch.as_tensor(I.random_state(mesh, 790)).cuda()
+    f = s.rhs(U)
+    s.profile(True)
+    s.profile_reset()
+    for _ in range(3):
+        s.rhs(U, out=f)
+    torch.cuda.synchronize()
+    prof = s.profile_read()
+    s.profile(False)
+    assert {k: v[0] for k, v in prof.items()} == {"oi_to_quad": 3, "oi_to_nodes": 3, "dgip_trace": 3,
+                                                   "dgip_face": 3, "dgip_elem": 3}
+    for k in prof:
+        fl, by = s.kernel_work(k)
+        assert fl > 0 and by > 0
+    out = torch.full_like(U, float("nan"))
+    assert s.lib.dgx_rhs_noalloc(s.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(out, f)
+    s.check()
+    Ubad = U.clone()
+    Ubad[3, 0, 2] = float("nan")
+    s.rhs(Ubad)
+    with pytest.raises(DGXError) as err:
+        s.check()
+    assert err.value.code == 4  # DGX_ENONFINITE
+    s.check()  # the flag was cleared
+    Uh = torch.zeros((mesh.n_elem, 4, 4, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(DGXError) as err:
+        s.hdg_blocks(U, Uh, 0.1)
+    assert err.value.code == 6  # DGX_EUNSUPPORTED
