@@ -146,6 +146,20 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
 dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz,
                               const int32_t* neighbor, const int8_t* nbr_face, const int8_t* orient);
 
+/* Geometry override (Sec. 3.1 element maps, given rather than derived): the
+ * Jacobian J[E][N] > 0 and the metric terms metric[E][N][d][d],
+ * metric[e][q][a][b] = J dxi_a/dx_b at the Gauss nodes (host, double,
+ * copied), replacing the metrics of the current mesh, whose connectivity
+ * stays.  Face normals follow from the metric as for dgx_set_mesh_nodes (each
+ * side's J dxi_a/dx traced to its face, averaged across interior faces); the
+ * handle then runs the curvilinear kernels.  The caller answers for the
+ * metric identities (sum_a d/dxi_a (J dxi_a/dx_b) = 0 discretely, which free
+ * stream preservation needs).  DGX_ESTATE without a mesh, DGX_EUNSUPPORTED on
+ * DG-IP handles (box kernels) and, afterwards, in dgx_batch_create (the batch
+ * rebuilds geometry from the mesh description); the next dgx_set_mesh_*
+ * call drops the override. */
+dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric);
+
 /* Explicit Butcher tableau of an (s)-stage ERK (Sec. 4.2, padded ERK half of
  * the ARK pair): A[s][s] row-major, strictly lower triangular, b[s], c[s]
  * (host, double, copied).  s <= 8.  Default: none (dgx_ark_step -> DGX_ESTATE). */

@@ -33,6 +33,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dgip_physics.cuh"
 #include "kernels.cuh"
 #include "ops.cuh"
@@ -62,9 +64,23 @@ __device__ __forceinline__ int tan_stride(int c, int a0) {
   return c < a0 ? HD<D, P>::pw(c) : HD<D, P>::pw(c - 1);
 }
 
+// f(std::integral_constant<int, v>) for a runtime v in [I, N): face and
+// direction numbers become compile-time constants, so the node and face-point
+// index arithmetic that depends on them is constant multiplies (a runtime
+// face number makes every such index an integer division).
+template <int I, int N, typename F>
+__device__ __forceinline__ void with_const(int v, F&& f) {
+  if constexpr (I < N) {
+    if (v == I) f(std::integral_constant<int, I>{});
+    else with_const<I + 1, N>(v, f);
+  }
+}
+
 // Physical (broken) gradient of an element's polynomial at one of its own face
 // points: the normal derivative from the line through the point, tangential
-// ones from the face's traced values (boxes: scaled by 2/h).
+// ones from the face's traced values (boxes: scaled by 2/h).  The face number
+// stays a runtime value here: one warp's face points span two faces, and a
+// compile-time face would run both faces' code in turn.
 template <int D, int P, typename S>
 __device__ __forceinline__ void face_gradient(const S* us, const S* tu, const S* rh, int face, int fp,
                                               S (&Q)[D][D + 2]) {
@@ -312,15 +328,28 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
   const bool active = t < nel;
   const int e = e0 + t;
   const bool expl = active && dgip_explicit(dp, e);
-  for (int i = tid; i < nel * FACE; i += blockDim.x) {
-    const bool x = dgip_explicit(dp, e0 + i / FACE);
-    ffs[i] = x ? FF[(size_t)e0 * FACE + i] : S(0);
-  }
-  if (VISC) {
-    for (int i = tid; i < nel * D * FACE; i += blockDim.x) {
-      const bool x = dgip_explicit(dp, e0 + i / (D * FACE));
-      has[i] = x ? HA[(size_t)e0 * D * FACE + i] : S(0);
+  // face inputs, one thread per face point: all of its loads before its stores
+  for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
+    const int fp = i % nfp, tf = i / nfp;  // tf = element-in-tile * NF + face
+    const bool x = dgip_explicit(dp, e0 + tf / NF);
+    S v[nf];
+    const S* ff = FF + ((size_t)e0 * NF + tf) * nf * nfp + fp;
+#pragma unroll
+    for (int f = 0; f < nf; ++f) v[f] = x ? ff[f * nfp] : S(0);
+    if (VISC) {
+      S hv[D][nf];
+      const S* ha = HA + ((size_t)e0 * NF + tf) * D * nf * nfp + fp;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) hv[c][f] = x ? ha[(c * nf + f) * nfp] : S(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) has[(tf * D + c) * nf * nfp + f * nfp + fp] = hv[c][f];
     }
+#pragma unroll
+    for (int f = 0; f < nf; ++f) ffs[(tf * nf + f) * nfp + fp] = v[f];
   }
   S Uq[nf];
   if (active) {
@@ -550,21 +579,29 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
   }
   __syncthreads();
   if (VISC) {  // tangential adjoint-term cotangents: HAb[a0,side][a] = r_a0 sum_k L(side)[k] Fb_a(line along a0)
-    constexpr int ITEMS = NF * (D - 1) * nf * nfp;
+    constexpr int ITEMS = D * (D - 1) * nf * nfp;  // (a0, a != a0, f, fp): both sides from one line
     for (int i = tid; i < nel * ITEMS; i += blockDim.x) {
       const int fp = i % nfp;
       const int f = (i / nfp) % nf;
-      const int ai = (i / (nfp * nf)) % (D - 1);
-      const int face = (i / (nfp * nf * (D - 1))) % NF;
+      const int pair = (i / (nfp * nf)) % (D * (D - 1));
       const int tt = i / ITEMS;
-      const int a0 = face >> 1, side = face & 1;
-      const int a = ai + (ai >= a0);
-      const S r0 = M.geo.rh[(e0 + tt) * D + a0];
-      const S* v = fb + (tt * D + a) * STATE + f * N;
-      S s = 0;
+      with_const<0, D * (D - 1)>(pair, [&](auto PC) {
+        constexpr Tab1<S> tbl = make_tab1<S>(P);
+        constexpr int a0 = decltype(PC)::value / (D - 1), ai = decltype(PC)::value % (D - 1);
+        constexpr int a = ai + (ai >= a0);
+        const S r0 = M.geo.rh[(e0 + tt) * D + a0];
+        const S* v = fb + (tt * D + a) * STATE + f * N;
+        S sm = 0, sp = 0;
 #pragma unroll
-      for (int k = 0; k < n; ++k) s += (side ? tb.Lp[k] : tb.Lm[k]) * v[H::node(k, fp, a0)];
-      HAb[((((size_t)(e0 + tt) * NF + face) * D + a) * nf + f) * nfp + fp] = r0 * s;
+        for (int k = 0; k < n; ++k) {
+          const S x = v[H::node(k, fp, a0)];
+          sm += tbl.Lm[k] * x;
+          sp += tbl.Lp[k] * x;
+        }
+        S* ho = HAb + ((((size_t)(e0 + tt) * NF + 2 * a0) * D + a) * nf + f) * nfp + fp;
+        ho[0] = r0 * sm;
+        ho[D * nf * nfp] = r0 * sp;
+      });
     }
   }
   // pointwise flux adjoint: F = F^c - F^nu(U, Q)
@@ -792,7 +829,14 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
       }
     }
   }
-  for (int i = tid; i < nel * FACE; i += blockDim.x) tub[i] = TUb[(size_t)e0 * FACE + i];
+  for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {  // one thread per face point, loads before stores
+    const int fp = i % nfp, tf = i / nfp;
+    S v[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) v[f] = TUb[((size_t)e0 * NF + tf) * nf * nfp + f * nfp + fp];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) tub[(tf * nf + f) * nfp + fp] = v[f];
+  }
   __syncthreads();
   if (VISC) {
 #pragma unroll

@@ -35,6 +35,7 @@ struct dgx_handle {
   unsigned* d_flags = nullptr;
   // mesh
   bool has_mesh = false, curv = false;
+  bool geo_override = false;  // metrics given by dgx_set_geometry (not derivable from the host mesh copies)
   int nFaces = 0;
   int* d_nb = nullptr;
   int8_t* d_nbf = nullptr;
@@ -185,6 +186,48 @@ void free_mesh(dgx_handle* h) {
   h->d_faces = nullptr;
   h->d_rh = h->d_Ja = h->d_iJ = h->d_SnE = h->d_SnF = nullptr;
   h->has_mesh = false;
+}
+
+// Element metrics Ja[E][a][c][N] = J dxi_a/dx_c and iJ[E][N] = 1/J (host, FP64)
+// to the device, with the face normals they imply: each element's own
+// outward area normals +-Ja_a traced to xi_a = +-1, and on every unique face
+// the average (Sn^- - Sn^+)/2 of both sides' (the owner's face-point order).
+dgx_status upload_metrics(dgx_handle* h, const std::vector<double>& Ja, const std::vector<double>& iJ,
+                          const std::vector<int4>& faces) {
+  const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
+  const dgx::Basis1 B = dgx::make_basis1(h->p);
+  std::vector<double> SnE((size_t)E * NF * d * nfp);
+  for (int e = 0; e < E; ++e) {
+    const double* JaE = &Ja[(size_t)e * d * d * N];
+    for (int face = 0; face < NF; ++face) {
+      const int a = face >> 1;
+      const double* l = (face & 1) ? B.lp : B.lm;
+      const double sgn = (face & 1) ? 1.0 : -1.0;
+      for (int c = 0; c < d; ++c)
+        for (int fp = 0; fp < nfp; ++fp) {
+          double s = 0.0;
+          for (int m = 0; m < n; ++m) s += l[m] * JaE[(a * d + c) * N + node_of(n, m, fp, a)];
+          SnE[(((size_t)e * NF + face) * d + c) * nfp + fp] = sgn * s;
+        }
+    }
+  }
+  std::vector<double> SnF(faces.size() * d * nfp);
+  for (size_t F = 0; F < faces.size(); ++F) {
+    const int4 r = faces[F];
+    const int em = r.x, ep = r.y, fm = r.z & 0xff, fo = (r.z >> 8) & 0xff, code = (r.z >> 16) & 0xff;
+    for (int c = 0; c < d; ++c)
+      for (int fp = 0; fp < nfp; ++fp) {
+        const double own = SnE[(((size_t)em * NF + fm) * d + c) * nfp + fp];
+        double v = own;
+        if (ep >= 0) v = 0.5 * (own - SnE[(((size_t)ep * NF + fo) * d + c) * nfp + omap(code, fp, n, d)]);
+        SnF[(F * d + c) * nfp + fp] = v;
+      }
+  }
+  dgx_status st;
+  if ((st = upload_real(h, Ja, &h->d_Ja)) != DGX_OK) return st;
+  if ((st = upload_real(h, iJ, &h->d_iJ)) != DGX_OK) return st;
+  if ((st = upload_real(h, SnE, &h->d_SnE)) != DGX_OK) return st;
+  return upload_real(h, SnF, &h->d_SnF);
 }
 
 // Connectivity checks shared by both mesh kinds; builds the unique-face list.
@@ -1422,6 +1465,7 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   h->h_size.assign(size, size + (size_t)E * d);
   h->h_xyz.clear();
   h->curv = false;
+  h->geo_override = false;
   h->mesh64 = mesh_view<double>(h);
   h->mesh32 = mesh_view<float>(h);
   if (h->inner && (st = dgx_set_mesh_boxes(h->inner, lo, size, neighbor, nbr_face, orient)) != DGX_OK) return st;
@@ -1433,7 +1477,7 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
                               const int8_t* orient) {
   if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
   if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels (and their over-integration) take box meshes
-  const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
+  const int E = h->E, d = h->d, n = h->n, N = h->N;
   for (size_t i = 0; i < (size_t)E * d * N; ++i)
     if (!std::isfinite(xyz[i])) return DGX_EINVAL;
   std::vector<int4> faces;
@@ -1449,7 +1493,7 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
       out[q] = s;
     }
   };
-  std::vector<double> Ja((size_t)E * d * d * N), iJ((size_t)E * N), SnE((size_t)E * NF * d * nfp);
+  std::vector<double> Ja((size_t)E * d * d * N), iJ((size_t)E * N);
   std::vector<double> dX(d * d * N), G(N), tmp(N), tmp2(N);
   for (int e = 0; e < E; ++e) {
     const double* X = xyz + (size_t)e * d * N;
@@ -1487,43 +1531,53 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
         }
       }
     }
-    // own outward area normals: +-Ja_a traced to xi_a = +-1
-    for (int face = 0; face < NF; ++face) {
-      const int a = face >> 1;
-      const std::vector<double>& l = (face & 1) ? B.lp : B.lm;
-      const double sgn = (face & 1) ? 1.0 : -1.0;
-      for (int c = 0; c < d; ++c)
-        for (int fp = 0; fp < nfp; ++fp) {
-          double s = 0.0;
-          for (int m = 0; m < n; ++m) s += l[m] * JaE[(a * d + c) * N + node_of(n, m, fp, a)];
-          SnE[(((size_t)e * NF + face) * d + c) * nfp + fp] = sgn * s;
-        }
-    }
-  }
-  // averaged normals of the unique faces, in the owner's face-point order
-  std::vector<double> SnF(faces.size() * d * nfp);
-  for (size_t F = 0; F < faces.size(); ++F) {
-    const int4 r = faces[F];
-    const int em = r.x, ep = r.y, fm = r.z & 0xff, fo = (r.z >> 8) & 0xff, code = (r.z >> 16) & 0xff;
-    for (int c = 0; c < d; ++c)
-      for (int fp = 0; fp < nfp; ++fp) {
-        const double own = SnE[(((size_t)em * NF + fm) * d + c) * nfp + fp];
-        double v = own;
-        if (ep >= 0) v = 0.5 * (own - SnE[(((size_t)ep * NF + fo) * d + c) * nfp + omap(code, fp, n, d)]);
-        SnF[(F * d + c) * nfp + fp] = v;
-      }
   }
   free_mesh(h);
   if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
-  if ((st = upload_real(h, Ja, &h->d_Ja)) != DGX_OK) return st;
-  if ((st = upload_real(h, iJ, &h->d_iJ)) != DGX_OK) return st;
-  if ((st = upload_real(h, SnE, &h->d_SnE)) != DGX_OK) return st;
-  if ((st = upload_real(h, SnF, &h->d_SnF)) != DGX_OK) return st;
+  if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK) return st;
   h->h_xyz.assign(xyz, xyz + (size_t)E * d * N);
   h->h_lo.clear();
   h->h_size.clear();
   h->curv = true;
+  h->geo_override = false;
   h->has_mesh = true;
+  h->mesh64 = mesh_view<double>(h);
+  h->mesh32 = mesh_view<float>(h);
+  return DGX_OK;
+}
+
+dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric) {
+  if (!h || !J || !metric) return DGX_EINVAL;
+  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels take box meshes
+  if (!h->has_mesh) return DGX_ESTATE;
+  const int E = h->E, d = h->d, N = h->N;
+  for (size_t i = 0; i < (size_t)E * N; ++i)
+    if (!(J[i] > 0.0) || !std::isfinite(J[i])) return DGX_EINVAL;
+  for (size_t i = 0; i < (size_t)E * N * d * d; ++i)
+    if (!std::isfinite(metric[i])) return DGX_EINVAL;
+  std::vector<double> Ja((size_t)E * d * d * N), iJ((size_t)E * N);
+  for (int e = 0; e < E; ++e)
+    for (int q = 0; q < N; ++q) {
+      iJ[(size_t)e * N + q] = 1.0 / J[(size_t)e * N + q];
+      for (int a = 0; a < d; ++a)
+        for (int c = 0; c < d; ++c)
+          Ja[(((size_t)e * d + a) * d + c) * N + q] = metric[(((size_t)e * N + q) * d + a) * d + c];
+    }
+  std::vector<int4> faces;
+  dgx_status st = check_connectivity(h, h->h_nb.data(), h->h_nbf.data(), h->h_ori.data(), faces);
+  if (st != DGX_OK) return st;
+  void** geo[] = {&h->d_Ja, &h->d_iJ, &h->d_SnE, &h->d_SnF};
+  for (void** g : geo)
+    if (*g) {
+      cudaFree(*g);
+      *g = nullptr;
+    }
+  if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK) {
+    free_mesh(h);
+    return st;
+  }
+  h->curv = true;
+  h->geo_override = true;
   h->mesh64 = mesh_view<double>(h);
   h->mesh32 = mesh_view<float>(h);
   return DGX_OK;
@@ -2158,6 +2212,7 @@ dgx_status dgx_batch_create(dgx_handle* const* inst, int32_t count, dgx_batch** 
     const dgx_handle* h = inst[i];
     if (!h) return DGX_EINVAL;
     if (h->dgip) return DGX_EUNSUPPORTED;  // batches run the LLF/BR1 scheme
+    if (h->geo_override) return DGX_EUNSUPPORTED;  // the batch rebuilds geometry from the mesh description
     if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
     if (h->stages != h0->stages) return DGX_EINVAL;
     for (int r = 0; r < dgx::MAXSTAGES * dgx::MAXSTAGES; ++r)

@@ -49,7 +49,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
            "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source",
            "dgx_set_wait_limit", "dgx_batch_set_persistent", "dgx_hdg_sizes", "dgx_hdg_blocks",
-           "dgx_hdg_condense"]
+           "dgx_hdg_condense", "dgx_set_geometry"]
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_destroy.argtypes = [vp]
     lib.dgx_set_mesh_boxes.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_set_mesh_nodes.argtypes = [vp, vp, vp, vp, vp]
+    lib.dgx_set_geometry.argtypes = [vp, vp, vp]
     lib.dgx_set_tableau.argtypes = [vp, i32, vp, vp, vp]
     lib.dgx_workspace_bytes.argtypes = [vp, i32]
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
@@ -219,6 +220,16 @@ class Solver:
         """Free-stream state (conservative) of the farfield boundaries (DG-IP scheme)."""
         u = np.ascontiguousarray(U_inf, dtype=np.float64)
         _check(self.lib.dgx_set_farfield(self.h, _ptr(u)), "dgx_set_farfield")
+
+    def set_geometry(self, J, metric):
+        """Replace the mesh's metrics by J[E][N] and metric[E][N][d][d] = J dxi_a/dx_b
+        (host arrays; the connectivity stays)."""
+        Jh = np.ascontiguousarray(J, dtype=np.float64)
+        Mh = np.ascontiguousarray(metric, dtype=np.float64)
+        E, N, d = self.mesh.n_elem, self.mesh.N, self.mesh.dim
+        if Jh.shape != (E, N) or Mh.shape != (E, N, d, d):
+            raise ValueError("J must be [E][N] and metric [E][N][d][d]")
+        _check(self.lib.dgx_set_geometry(self.h, _ptr(Jh), _ptr(Mh)), "dgx_set_geometry")
 
     def set_explicit_mask(self, mask):
         """Explicit-region element mask of the geometry split (None removes it)."""
