@@ -76,50 +76,110 @@ __device__ __forceinline__ void with_const(int v, F&& f) {
   }
 }
 
-// Physical (broken) gradient of an element's polynomial at one of its own face
-// points: the normal derivative from the line through the point, tangential
-// ones from the face's traced values (boxes: scaled by 2/h).  The face number
-// stays a runtime value here: one warp's face points span two faces, and a
-// compile-time face would run both faces' code in turn.
-template <int D, int P, typename S>
-__device__ __forceinline__ void face_gradient(const S* us, const S* tu, const S* rh, int face, int fp,
-                                              S (&Q)[D][D + 2]) {
+// Face quantities of a staged tile (us[t][f][q]), one thread per (element,
+// field, line) and direction: the traces tu[t][face][f][fp] at both ends of
+// every line and, for the viscous terms, the normal derivative of the
+// element's polynomial there, qf[t][face][a][f][fp] = (2/h_a) l'(+-1) . line
+// (face normal to a).  TUg (or nullptr) receives the traces in global memory.
+template <int D, int P, typename S, bool VISC>
+__device__ __forceinline__ void face_lines(const S* us, S* tu, S* qf, const S* rh, int e0, int nel, S* TUg) {
   using H = HD<D, P>;
-  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp;
+  constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, STATE = H::STATE, FACE = H::FACE;
   constexpr Tab1<S> tb = make_tab1<S>(P);
-  const int a0 = face >> 1, side = face & 1;
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const S r = rh[c];
-    if (c == a0) {
+  for (int a = 0; a < D; ++a) {
+    for (int i = threadIdx.x; i < nel * nf * nfp; i += blockDim.x) {
+      int t, f, line;
+      line_item<nf, nfp>(i, t, f, line);
+      const S* v = us + t * STATE + f * N;
+      S x[n];
 #pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        S s = 0;
-#pragma unroll
-        for (int j = 0; j < n; ++j) s += (side ? tb.dlp[j] : tb.dlm[j]) * us[f * N + H::node(j, fp, a0)];
-        Q[c][f] = r * s;
-      }
-    } else {
-      const int st = tan_stride<D, P>(c, a0);
-      const int ic = (fp / st) % n;
-      const int base = fp - ic * st;
-      // row ic of D by selects among compile-time constants (a runtime index
-      // into the constexpr table would copy it to local memory)
-      S row[n];
+      for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
+      S sm = 0, sp = 0, dm = 0, dq = 0;
 #pragma unroll
       for (int m = 0; m < n; ++m) {
-        S v = tb.D[0][m];
-#pragma unroll
-        for (int k = 1; k < n; ++k) v = (ic == k) ? tb.D[k][m] : v;
-        row[m] = v;
+        sm += tb.lm[m] * x[m];
+        sp += tb.lp[m] * x[m];
+        if (VISC) {
+          dm += tb.dlm[m] * x[m];
+          dq += tb.dlp[m] * x[m];
+        }
       }
-#pragma unroll
-      for (int f = 0; f < nf; ++f) {
-        S s = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) s += row[m] * tu[f * nfp + base + m * st];
-        Q[c][f] = r * s;
+      const int om = (t * NF + 2 * a) * nf * nfp + f * nfp + line, op = om + nf * nfp;
+      tu[om] = sm;
+      tu[op] = sp;
+      if (TUg) {
+        TUg[(size_t)e0 * FACE + om] = sm;
+        TUg[(size_t)e0 * FACE + op] = sp;
       }
+      if (VISC) {
+        const S r = rh[(e0 + t) * D + a];
+        qf[((t * NF + 2 * a) * D + a) * nf * nfp + f * nfp + line] = r * dm;
+        qf[((t * NF + 2 * a + 1) * D + a) * nf * nfp + f * nfp + line] = r * dq;
+      }
+    }
+  }
+}
+
+// The tangential derivatives on every face from its traced values, one thread
+// per (element, face, tangential direction, field, face line): the line's n
+// values in, the derivative at its n points out (rows of D as compile-time
+// constants), qf[t][face][c][f][fp] = (2/h_c) (D y)(fp).
+template <int D, int P, typename S>
+__device__ __forceinline__ void face_tangential(const S* tu, S* qf, const S* rh, int e0, int nel) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
+  constexpr int NL = nfp / n;  // lines of one tangential direction on a face
+  constexpr int ITEMS = NF * (D - 1) * nf * NL;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  for (int i = threadIdx.x; i < nel * ITEMS; i += blockDim.x) {
+    const int fl = i % NL, f = (i / NL) % nf, ci = (i / (NL * nf)) % (D - 1);
+    const int face = (i / (NL * nf * (D - 1))) % NF, t = i / ITEMS;
+    const int a0 = face >> 1, c = ci + (ci >= a0);
+    const int st = tan_stride<D, P>(c, a0);
+    const int base = (D == 2) ? 0 : (st == 1 ? fl * n : fl);
+    const S* y = tu + (t * NF + face) * nf * nfp + f * nfp + base;
+    S yv[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) yv[k] = y[k * st];
+    const S r = rh[(e0 + t) * D + c];
+    S* o = qf + ((t * NF + face) * D + c) * nf * nfp + f * nfp + base;
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+      S s = 0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) s += tb.D[j][k] * yv[k];
+      o[j * st] = r * s;
+    }
+  }
+}
+
+// Transposed face_tangential for one tangential direction index ci:
+// tub[t][face][f] += (2/h_c) D^T qfb[t][face][c][f] along every face line.
+template <int D, int P, typename S>
+__device__ __forceinline__ void face_tangential_t(const S* qfb, S* tub, const S* rh, int e0, int nel, int ci) {
+  using H = HD<D, P>;
+  constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
+  constexpr int NL = nfp / n;
+  constexpr int ITEMS = NF * nf * NL;
+  constexpr Tab1<S> tb = make_tab1<S>(P);
+  for (int i = threadIdx.x; i < nel * ITEMS; i += blockDim.x) {
+    const int fl = i % NL, f = (i / NL) % nf, face = (i / (NL * nf)) % NF, t = i / ITEMS;
+    const int a0 = face >> 1, c = ci + (ci >= a0);
+    const int st = tan_stride<D, P>(c, a0);
+    const int base = (D == 2) ? 0 : (st == 1 ? fl * n : fl);
+    const S* z = qfb + ((t * NF + face) * D + c) * nf * nfp + f * nfp + base;
+    S zv[n];
+#pragma unroll
+    for (int j = 0; j < n; ++j) zv[j] = z[j * st];
+    const S r = rh[(e0 + t) * D + c];
+    S* o = tub + (t * NF + face) * nf * nfp + f * nfp + base;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      S s = 0;
+#pragma unroll
+      for (int j = 0; j < n; ++j) s += tb.D[j][k] * zv[j];
+      o[k * st] += r * s;
     }
   }
 }
@@ -152,6 +212,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* us = reinterpret_cast<S*>(smem_raw);  // [T][nf][N]
   S* tu = us + T * STATE;                  // [T][NF][nf][nfp]
+  S* qf = tu + T * FACE;                   // [T][NF][D][nf][nfp] face gradients (viscous)
   const int e0 = blockIdx.x * T;
   const int nel = min(T, M.E - e0);
   const int tid = threadIdx.x;
@@ -168,37 +229,24 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
-      int t, f, line;
-      line_item<nf, nfp>(i, t, f, line);
-      const S* v = us + t * STATE + f * N;
-      S sm = 0, sp = 0;
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        const S x = v[H::node(m, line, a)];
-        sm += tb.lm[m] * x;
-        sp += tb.lp[m] * x;
-      }
-      const int om = (t * NF + 2 * a) * nf * nfp + f * nfp + line, op = om + nf * nfp;
-      tu[om] = sm;
-      tu[op] = sp;
-      TU[(size_t)e0 * FACE + om] = sm;
-      TU[(size_t)e0 * FACE + op] = sp;
-    }
-  }
+  face_lines<D, P, S, VISC>(us, tu, qf, M.geo.rh, e0, nel, TU);
   if (!VISC) return;
+  __syncthreads();
+  face_tangential<D, P, S>(tu, qf, M.geo.rh, e0, nel);
   __syncthreads();
   const Gas<S> gw = gas_no_heat(M.gas);
   for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
     const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
     const int e = e0 + t;
     const S* tf = tu + (t * NF + face) * nf * nfp;
+    const S* qg = qf + (t * NF + face) * D * nf * nfp + fp;
     S Uf[nf], Q[D][nf], nv[D], Gv[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) Uf[f] = tf[f * nfp + fp];
-    face_gradient<D, P, S>(us + t * STATE, tf, M.geo.rh + (size_t)e * D, face, fp, Q);
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) Q[c][f] = qg[(c * nf + f) * nfp];
     unit_normal<D, S>(face, nv);
     const int nbk = M.nb[e * NF + face];
     if (nbk >= 0) {
@@ -839,31 +887,19 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
   }
   __syncthreads();
   if (VISC) {
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      for (int i = tid; i < nel * nf * nfp; i += blockDim.x) {
-        int t, f, line;
-        line_item<nf, nfp>(i, t, f, line);
-        const S* v = us + t * STATE + f * N;
-        S sm = 0, sp = 0;
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          const S x = v[H::node(m, line, a)];
-          sm += tb.lm[m] * x;
-          sp += tb.lp[m] * x;
-        }
-        tu[(t * NF + 2 * a) * nf * nfp + f * nfp + line] = sm;
-        tu[(t * NF + 2 * a + 1) * nf * nfp + f * nfp + line] = sp;
-      }
-    }
+    face_lines<D, P, S, true>(us, tu, qfb, M.geo.rh, e0, nel, nullptr);
+    __syncthreads();
+    face_tangential<D, P, S>(tu, qfb, M.geo.rh, e0, nel);
     __syncthreads();
     const Gas<S> gw = gas_no_heat(M.gas);
     // adjoint of G at every own face point: its U_f part goes to the trace
-    // cotangent (own entry), its gradient part to qfb
+    // cotangent (own entry), its gradient part replaces the gradient in qfb
+    // (each thread reads and then overwrites only its own face point's entries)
     for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
       const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
       const int e = e0 + t;
       const S* tf = tu + (t * NF + face) * nf * nfp;
+      S* qg = qfb + (t * NF + face) * D * nf * nfp + fp;
       S Uf[nf], Q[D][nf], nv[D], Gbar[nf], Ufb[nf], Qb[D][nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
@@ -874,8 +910,10 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) Qb[c][f] = S(0);
-      face_gradient<D, P, S>(us + t * STATE, tf, M.geo.rh + (size_t)e * D, face, fp, Q);
+        for (int f = 0; f < nf; ++f) {
+          Q[c][f] = qg[(c * nf + f) * nfp];
+          Qb[c][f] = S(0);
+        }
       unit_normal<D, S>(face, nv);
       const int nbk = M.nb[e * NF + face];
       if (nbk >= 0) {
@@ -894,48 +932,17 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
       S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
 #pragma unroll
       for (int f = 0; f < nf; ++f) tb_[f * nfp] += Ufb[f];
-      S* qo = qfb + (t * NF + face) * D * nf * nfp + fp;
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) qo[(c * nf + f) * nfp] = Qb[c][f];
+        for (int f = 0; f < nf; ++f) qg[(c * nf + f) * nfp] = Qb[c][f];
     }
-    __syncthreads();
-    // tangential face derivatives, transposed (a gather along each tangential line)
-    for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
-      const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
-      const int a0 = face >> 1;
-      const S* qo = qfb + (t * NF + face) * D * nf * nfp;
-      S acc[nf];
+    // tangential face derivatives, transposed: one tangential direction per
+    // pass (lines of different directions share face points)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) acc[f] = S(0);
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        if (c == a0) continue;
-        const S r = M.geo.rh[(e0 + t) * D + c];
-        const int st = tan_stride<D, P>(c, a0);
-        const int ic = (fp / st) % n;
-        const int base = fp - ic * st;
-        S col[n];  // column ic of D by selects among compile-time constants
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-          S v = tb.D[j][0];
-#pragma unroll
-          for (int k = 1; k < n; ++k) v = (ic == k) ? tb.D[j][k] : v;
-          col[j] = v;
-        }
-#pragma unroll
-        for (int f = 0; f < nf; ++f) {
-          S s = 0;
-#pragma unroll
-          for (int j = 0; j < n; ++j) s += col[j] * qo[(c * nf + f) * nfp + base + j * st];
-          acc[f] += r * s;
-        }
-      }
-      // qfb is only read in this pass and each thread writes only its own tub entry
-      S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
-#pragma unroll
-      for (int f = 0; f < nf; ++f) tb_[f * nfp] += acc[f];
+    for (int ci = 0; ci < D - 1; ++ci) {
+      __syncthreads();
+      face_tangential_t<D, P, S>(qfb, tub, M.geo.rh, e0, nel, ci);
     }
   }
   __syncthreads();
@@ -994,14 +1001,17 @@ template <int D, int P, typename S>
 struct DgipOps {
   using H = HD<D, P>;
   static int blocks(int E) { return (E + H::T - 1) / H::T; }
-  static size_t smem_trace() { return r16(sizeof(S) * (H::T * H::STATE + H::T * H::FACE)); }
+  template <bool VISC>
+  static size_t smem_trace() {
+    return r16(sizeof(S) * (H::T * H::STATE + H::T * H::FACE + (VISC ? H::T * D * H::FACE : 0)));
+  }
 
   template <bool VISC>
   static cudaError_t trace_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, cudaStream_t st) {
     static SmemGate done;
     auto k = k_dgip_trace<D, P, S, VISC>;
-    if (const cudaError_t e = allow_smem_once(k, smem_trace(), done)) return e;
-    k<<<blocks(M.E), H::THREADS, smem_trace(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G);
+    if (const cudaError_t e = allow_smem_once(k, smem_trace<VISC>(), done)) return e;
+    k<<<blocks(M.E), H::THREADS, smem_trace<VISC>(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G);
     return cudaGetLastError();
   }
   static cudaError_t trace(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w,
