@@ -432,11 +432,11 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 # headline's dominant kernel (k_vjp_br1, FP64) from one ncu capture of the same
 # step on the 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2),
 # scaled to the 48^3 launch by the element count (the kernel's traffic is per
-# element tile): 1,833,356,032 B x 110,592 / 16,384.  Summary and command in
+# element tile): 1,832,997,888 B x 110,592 / 16,384.  Summary and command in
 # profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
 # sources hash to `sources`.
-NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375153216,
-               "sources": "745a6328d7a9e4c610c8c74d738bce96b4062ab4664f305144fd4ac356cf4bab"}
+NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12372735744,
+               "sources": "ffe072cf811df2310d9a41241bd54e335b661db6bab9cd61af357fd0084fb15a"}
 
 
 def sources_hash(root_header="vjp.cuh"):
