@@ -1004,7 +1004,8 @@ def main():
                     help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' / "
                          "'fp64:channel3d-<nxy>-<layers>' / 'fp64:dgip-channel3d-<nxy>-<layers>' alone (profiling "
                          "runs), 'tgv' for the TGV engine "
-                         "comparison, 'dgip' for the DG-IP legs, or 'oi' for the over-integrated DG-IP comparison")
+                         "comparison, 'dgip' for the DG-IP legs, 'hdg' for the HDG-IP blocks, or 'oi' for the over-integrated "
+                         "DG-IP comparison")
     ap.add_argument("--profile-range", action="store_true",
                     help="wrap the first timed step in cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -1033,6 +1034,9 @@ def main():
         return
     if legs == ["dgip"]:  # the DG-IP operator's legs alone
         print(json.dumps({"dgip": dgip_perf()}))
+        return
+    if legs == ["hdg"]:   # the HDG-IP element blocks alone
+        print(json.dumps({"hdg": hdg_perf()}))
         return
     if len(legs) == 1:    # one precision of one workload alone (profiling runs)
         prec, _, wl = legs[0].partition(":")

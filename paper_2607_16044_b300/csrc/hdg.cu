@@ -2,12 +2,13 @@
 // (Sec. 3.4 element and facet forms, Sec. 4.3 static condensation), FP64,
 // 2D box meshes.
 //
-// k_hdg_jacobian: one thread per (element, input column).  The element's
-// residual R_T (the HDG-IP element form tested with each nodal basis
-// function) and facet residual h_T (the transmission form tested with each
-// facet basis function) are evaluated serially by that thread with
-// forward-mode dual numbers seeded on its column (an element DOF or a facet
-// DOF), which yields column j of
+// k_hdg_jacobian: one thread per (element, group of KC input columns).  The
+// element's residual R_T (the HDG-IP element form tested with each nodal
+// basis function) and facet residual h_T (the transmission form tested with
+// each facet basis function) are evaluated serially by that thread with
+// forward-mode dual numbers carrying KC tangents, one seeded on each of its
+// columns (element or facet DOFs; the primal part is computed once for all
+// KC), which yields columns j of
 //   K = M + gamma dR/dU,  C = gamma dR/dUhat,  D = dh/dU,  A33_T = dh/dUhat.
 // With unit normals on boxes (r_a = 2/h_a, J = prod h_a/2, area factor
 // J r_a0 on a face normal to a0) the element form is written like the DG-IP
@@ -29,6 +30,10 @@
 
 namespace dgx {
 namespace {
+
+// columns of the Newton blocks one thread differentiates at once (tangents
+// of its dual numbers): the primal evaluation is shared by that many columns
+constexpr int HDG_COLUMNS_PER_THREAD = 8;
 
 template <typename T, typename S, int D>
 __device__ __forceinline__ void split_apply(const T (&Us)[D + 2], const T (&dU)[D + 2], const S (&nh)[D],
@@ -174,37 +179,46 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
     }
 }
 
-template <int P>
+template <int P, int KC>
 __global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* __restrict__ U,
                                                       const double* __restrict__ Uh, double gamma, double* K,
                                                       double* C, double* Dm, double* A33, double* Rv, double* hv) {
   constexpr int n = P + 1, N = n * n, nf = 4, NU = nf * N, NH = 4 * nf * n;
-  using T = Dual<double, 1>;
+  constexpr int NCOL = NU + NH, NG = (NCOL + KC - 1) / KC;  // column groups per element
+  using T = Dual<double, KC>;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)a.E * (NU + NH)) return;
-  const int e = (int)(gid / (NU + NH)), col = (int)(gid % (NU + NH));
+  if (gid >= (long long)a.E * NG) return;
+  const int e = (int)(gid / NG), c0 = (int)(gid % NG) * KC;
   T u[NU], uh[NH], R[NU], h[NH];
   for (int i = 0; i < NU; ++i) u[i] = T(U[(size_t)e * NU + i]);
   for (int i = 0; i < NH; ++i) uh[i] = T(Uh[(size_t)e * NH + i]);
-  if (col < NU) u[col].d[0] = 1.0;
-  else uh[col - NU].d[0] = 1.0;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    const int col = c0 + k;
+    if (col < NU) u[col].d[k] = 1.0;
+    else if (col < NCOL) uh[col - NU].d[k] = 1.0;
+  }
   hdg_forms<P, T>(a, e, u, uh, R, h);
-  if (col == 0 && Rv) {  // the forms' values (any column's value part)
+  if (c0 == 0 && Rv) {  // the forms' values (the value part of any group)
     for (int i = 0; i < NU; ++i) Rv[(size_t)e * NU + i] = R[i].v;
     for (int k = 0; k < NH; ++k) hv[(size_t)e * NH + k] = h[k].v;
   }
-  if (col < NU) {
-    const double J = 1.0 / (a.rh[e * 2] * a.rh[e * 2 + 1]);
-    for (int i = 0; i < NU; ++i) {
-      const int q = i % N;
-      const double m = (i == col) ? a.w[q % n] * a.w[q / n] * J : 0.0;
-      K[((size_t)e * NU + i) * NU + col] = m + gamma * R[i].d[0];
+  const double J = 1.0 / (a.rh[e * 2] * a.rh[e * 2 + 1]);
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    const int col = c0 + k;
+    if (col < NU) {
+      for (int i = 0; i < NU; ++i) {
+        const int q = i % N;
+        const double m = (i == col) ? a.w[q % n] * a.w[q / n] * J : 0.0;
+        K[((size_t)e * NU + i) * NU + col] = m + gamma * R[i].d[k];
+      }
+      for (int r = 0; r < NH; ++r) Dm[((size_t)e * NH + r) * NU + col] = h[r].d[k];
+    } else if (col < NCOL) {
+      const int j = col - NU;
+      for (int i = 0; i < NU; ++i) C[((size_t)e * NU + i) * NH + j] = gamma * R[i].d[k];
+      for (int r = 0; r < NH; ++r) A33[((size_t)e * NH + r) * NH + j] = h[r].d[k];
     }
-    for (int k = 0; k < NH; ++k) Dm[((size_t)e * NH + k) * NU + col] = h[k].d[0];
-  } else {
-    const int j = col - NU;
-    for (int i = 0; i < NU; ++i) C[((size_t)e * NU + i) * NH + j] = gamma * R[i].d[0];
-    for (int k = 0; k < NH; ++k) A33[((size_t)e * NH + k) * NH + j] = h[k].d[0];
   }
 }
 
@@ -303,9 +317,9 @@ __global__ void __launch_bounds__(256) k_hdg_condense(int E, int NU, int NH, con
 template <int P>
 cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, double gamma, double* K, double* C,
                        double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
-  constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n;
-  const long long total = (long long)a.E * (NU + NH);
-  k_hdg_jacobian<P><<<(int)((total + 127) / 128), 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+  constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n, KC = HDG_COLUMNS_PER_THREAD;
+  const long long total = (long long)a.E * ((NU + NH + KC - 1) / KC);
+  k_hdg_jacobian<P, KC><<<(int)((total + 127) / 128), 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
   return cudaGetLastError();
 }
 
