@@ -186,13 +186,16 @@ def adiabatic_wall_viscous_flux(U, Q, Sn, gas, d):
 # ---------------------------------------------------------------------------
 
 def posr(x):
-    """max(x, 0), branching on the real part (complex-step differentiable)."""
-    return torch.where(x.real > 0, x, torch.zeros_like(x))
+    """max(x, 0), branching on the real part (complex-step differentiable).
+    At x = 0 exactly, where max(x, 0) has no derivative, the value is 0 and
+    the derivative the mean of the one-sided ones, 1/2 (through x/2): the
+    same convention as d|x|/dx(0) = 0 in max(x, 0) = (x + |x|)/2."""
+    return torch.where(x.real > 0, x, torch.where(x.real < 0, torch.zeros_like(x), 0.5 * x))
 
 
 def negr(x):
-    """min(x, 0), branching on the real part."""
-    return torch.where(x.real < 0, x, torch.zeros_like(x))
+    """min(x, 0), branching on the real part; derivative 1/2 at x = 0 exactly."""
+    return torch.where(x.real < 0, x, torch.where(x.real > 0, torch.zeros_like(x), 0.5 * x))
 
 
 def acoustic_eigenvectors(U, Sn, gas, d):

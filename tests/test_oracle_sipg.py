@@ -405,3 +405,31 @@ def test_over_integration_changes_the_aliased_operator():
     d = [float((f[M] - f[10]).abs().max() / f[10].abs().max()) for M in (3, 4, 6, 8)]
     assert d[0] > 1e-4
     assert d[0] > d[1] > d[2] > d[3]
+
+
+def test_vijayasundaram_derivative_at_a_zero_eigenvalue_is_the_mean_of_the_one_sided_ones():
+    """A_n^+(Ubar) U+ + A_n^-(Ubar) U- is not differentiable where an
+    eigenvalue of A_n(Ubar) vanishes (here u.n = 0 exactly: no normal
+    velocity on either side).  The oracle's derivative there is the mean of
+    the derivatives from both sides, measured by one-sided differences."""
+    gas = ph.Gas(1.4)
+    d = 2
+    UL = torch.tensor([[1.1, 0.4, 0.0, 2.7]], dtype=torch.float64)
+    UR = torch.tensor([[0.9, -0.3, 0.0, 2.4]], dtype=torch.float64)
+    Sn = torch.tensor([[0.0, 1.3]], dtype=torch.float64)      # normal along y: u.n = v = 0
+    w = torch.tensor([[0.2, -0.4, 1.0, 0.3]], dtype=torch.float64)  # moves v through 0
+    lam = torch.tensor([[0.7, -0.2, 0.5, 1.1]], dtype=torch.float64)
+
+    def F(t):
+        return (ph.vijayasundaram_flux(UL + t * w, UR + t * w, Sn, gas, d) * lam).sum()
+
+    h = 1e-7
+    right = (F(h) - F(0.0)) / h
+    left = (F(0.0) - F(-h)) / h
+    assert abs(right - left) > 1e-3 * abs(right)               # a genuine kink
+    UL_ = UL.clone().requires_grad_(True)
+    UR_ = UR.clone().requires_grad_(True)
+    f = (ph.vijayasundaram_flux(UL_, UR_, Sn, gas, d) * lam).sum()
+    gL, gR = torch.autograd.grad(f, (UL_, UR_))
+    deriv = float(((gL + gR) * w).sum())
+    assert abs(deriv - 0.5 * float(left + right)) < 1e-6 * abs(float(right))
