@@ -44,10 +44,12 @@ __device__ __forceinline__ void split_apply(const T (&Us)[D + 2], const T (&dU)[
   T rm[nf], rp[nf];
   w.r(-1, nh, rm);
   w.r(1, nh, rp);
+  // positive / negative part; at x = 0 exactly the value 0 with the mean of
+  // the one-sided derivatives (x / 2)
   auto part = [&](const T& x) {
     if (sign == 0) return x;
-    if (sign > 0) return x > T(0) ? x : T(0);
-    return x < T(0) ? x : T(0);
+    if (sign > 0) return x > T(0) ? x : (x < T(0) ? T(0) : T(0.5) * x);
+    return x < T(0) ? x : (x > T(0) ? T(0) : T(0.5) * x);
   };
   const T l0 = part(w.un), lm = part(w.un - w.c), lp = part(w.un + w.c);
 #pragma unroll

@@ -278,3 +278,49 @@ def test_dgip_ark_adjoint_matches_oracle(prec):
     err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
     record(f"dgip-ark-adjoint-{prec}", rel=err)
     assert err < TOL[prec], err
+
+
+def _sampled_rows_and_vjp(op_factory, mesh, U, lam, rows):
+    """Oracle residual rows and VJP rows of the DG-IP operator for a few
+    elements of a large mesh: the residual of an element reads its face
+    neighbours (their traces and own gradients), so rows + 2 rings of
+    elements hold every residual that the rows' residuals and VJP rows need;
+    the VJP rows come from autograd of the sub-mesh residual with the
+    cotangent kept on the rows' 1-ring."""
+    sub, keep, loc = submesh_around(mesh, rows, 2)
+    op = op_factory(sub)
+    Ut = torch.as_tensor(U[keep]).clone().requires_grad_(True)
+    f = op.residual(Ut)
+    ring = set(int(x) for x in loc)
+    for r in loc:
+        ring.update(int(x) for x in sub.neighbor[r] if x >= 0)
+    lt = torch.zeros_like(Ut)
+    idx = torch.as_tensor(sorted(ring))
+    lt[idx] = torch.as_tensor(lam[keep])[idx]
+    (g,) = torch.autograd.grad(f, Ut, grad_outputs=lt)
+    return f.detach().numpy()[loc], g.numpy()[loc]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_dgip_channel3d_full_size_sampled(prec):
+    """The 48^3 p = 5 wall-stretched 3D channel (the bench's DG-IP leg):
+    residual and VJP rows of sampled elements, both walls included, against
+    the oracle on the rings around them; FP32 on the 10 %-perturbed state."""
+    mesh, phys, _ = I.channel3d_workload()
+    U = I.channel_state(mesh, phys, 5, amp=0.1 if prec == "fp32" else 1e-3)
+    lam = I.gaussian_cotangent(U.shape, 105)
+    s = _solver(mesh, phys, prec)
+    Ud = torch.as_tensor(U).to("cuda", _dt(prec)).contiguous()
+    f = s.rhs(Ud).double().cpu().numpy()
+    g = s.rhs_vjp(Ud, torch.as_tensor(lam).to("cuda", _dt(prec)).contiguous()).double().cpu().numpy()
+    s.check()
+    del s, Ud
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(11)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, 6, replace=False), [0, mesh.n_elem - 1]]))
+    Uref, lref = (U, lam) if prec == "fp64" else (quantize32(U), quantize32(lam))
+    fref, gref = _sampled_rows_and_vjp(lambda m: SIPGOperator(m, gas_of(phys)), mesh, Uref, lref, rows)
+    ferr, gerr = rel_err(f[rows], fref), rel_err(g[rows], gref)
+    record(f"dgip-channel3d-{prec}", rel=ferr, vjp_rel=gerr, sampled=len(rows))
+    assert ferr < TOL[prec], ferr
+    assert gerr < TOL[prec], gerr

@@ -253,3 +253,31 @@ def test_oi_handle_bookkeeping():
     with pytest.raises(DGXError) as err:
         s.hdg_blocks(U, Uh, 0.1)
     assert err.value.code == 6  # DGX_EUNSUPPORTED
+
+
+def test_oi_channel3d_p5_full_size_sampled():
+    """The 48^3 p = 5 channel with the order-3k rule (8 points per direction,
+    the bench's over-integration leg), FP64: residual and VJP rows of sampled
+    elements against the oracle on the rings around them, on the 10 %-perturbed
+    state (on the 1e-3-perturbed one the residual is a small difference of
+    large terms across the 2e-5-thin wall cells, and its rounding floor sits
+    at the 1e-12 bar)."""
+    from tests.test_gpu_dgip import _sampled_rows_and_vjp
+    mesh, phys, _ = I.channel3d_workload()
+    U = I.channel_state(mesh, phys, 5, amp=0.1)
+    lam = I.gaussian_cotangent(U.shape, 107)
+    s = _solver(mesh, phys, "fp64")
+    assert s.quad_points == 8
+    Ud = torch.as_tensor(U).cuda()
+    f = s.rhs(Ud).cpu().numpy()
+    g = s.rhs_vjp(Ud, torch.as_tensor(lam).cuda()).cpu().numpy()
+    s.check()
+    del s, Ud
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(13)
+    rows = np.unique(np.concatenate([rng.choice(mesh.n_elem, 4, replace=False), [0, mesh.n_elem - 1]]))
+    fref, gref = _sampled_rows_and_vjp(lambda m: OverIntegratedSIPG(m, gas_of(phys)), mesh, U, lam, rows)
+    ferr, gerr = rel_err(f[rows], fref), rel_err(g[rows], gref)
+    record("oi-channel3d-p5-fp64", rel=ferr, vjp_rel=gerr, sampled=len(rows))
+    assert ferr < TOL["fp64"], ferr
+    assert gerr < TOL["fp64"], gerr
