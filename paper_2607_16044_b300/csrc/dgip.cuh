@@ -44,6 +44,10 @@ namespace dgx {
 template <typename S>
 struct Dgip {
   const S* il;          // [E] 1/l = |dT| / |T| of every element (boxes: 2 sum_a 1/h_a)
+  // curvilinear meshes (nullptr on boxes): the metric terms and 1/J traced to
+  // every own face point, JaF[E][2D][a][c][nfp] = (J dxi_a/dx_c)(x_f), iJF[E][2D][nfp]
+  const S* JaF;
+  const S* iJF;
   S tk2;                // alpha (k+1)^2
   const int8_t* mask;   // [E] 1 = explicit element; nullptr: every element explicit
   const S* Uim;         // states of the implicit elements ([E][nf][N] layout) or nullptr
@@ -81,7 +85,7 @@ __device__ __forceinline__ void with_const(int v, F&& f) {
 // every line and, for the viscous terms, the normal derivative of the
 // element's polynomial there, qf[t][face][a][f][fp] = (2/h_a) l'(+-1) . line
 // (face normal to a).  TUg (or nullptr) receives the traces in global memory.
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV = false>
 __device__ __forceinline__ void face_lines(const S* us, S* tu, S* qf, const S* rh, int e0, int nel, S* TUg) {
   using H = HD<D, P>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, STATE = H::STATE, FACE = H::FACE;
@@ -112,8 +116,8 @@ __device__ __forceinline__ void face_lines(const S* us, S* tu, S* qf, const S* r
         TUg[(size_t)e0 * FACE + om] = sm;
         TUg[(size_t)e0 * FACE + op] = sp;
       }
-      if (VISC) {
-        const S r = rh[(e0 + t) * D + a];
+      if (VISC) {  // boxes: physical (2/h_a); curvilinear: reference derivatives
+        const S r = CURV ? S(1) : rh[(e0 + t) * D + a];
         qf[((t * NF + 2 * a) * D + a) * nf * nfp + f * nfp + line] = r * dm;
         qf[((t * NF + 2 * a + 1) * D + a) * nf * nfp + f * nfp + line] = r * dq;
       }
@@ -125,7 +129,7 @@ __device__ __forceinline__ void face_lines(const S* us, S* tu, S* qf, const S* r
 // per (element, face, tangential direction, field, face line): the line's n
 // values in, the derivative at its n points out (rows of D as compile-time
 // constants), qf[t][face][c][f][fp] = (2/h_c) (D y)(fp).
-template <int D, int P, typename S>
+template <int D, int P, typename S, bool CURV = false>
 __device__ __forceinline__ void face_tangential(const S* tu, S* qf, const S* rh, int e0, int nel) {
   using H = HD<D, P>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
@@ -142,7 +146,7 @@ __device__ __forceinline__ void face_tangential(const S* tu, S* qf, const S* rh,
     S yv[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) yv[k] = y[k * st];
-    const S r = rh[(e0 + t) * D + c];
+    const S r = CURV ? S(1) : rh[(e0 + t) * D + c];
     S* o = qf + ((t * NF + face) * D + c) * nf * nfp + f * nfp + base;
 #pragma unroll
     for (int j = 0; j < n; ++j) {
@@ -202,7 +206,7 @@ __device__ __forceinline__ Gas<S> gas_no_heat(const Gas<S>& g) {
 // (interior: F^nu(U_f, grad U_f).n; wall: the same with kappa = 0 (q.n = 0);
 // farfield: F^nu(U_inf, grad U_f).n).
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
                                                                   S* __restrict__ TU, S* __restrict__ G) {
   using H = HD<D, P>;
@@ -229,10 +233,10 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
     }
   }
   __syncthreads();
-  face_lines<D, P, S, VISC>(us, tu, qf, M.geo.rh, e0, nel, TU);
+  face_lines<D, P, S, VISC, CURV>(us, tu, qf, M.geo.rh, e0, nel, TU);
   if (!VISC) return;
   __syncthreads();
-  face_tangential<D, P, S>(tu, qf, M.geo.rh, e0, nel);
+  face_tangential<D, P, S, CURV>(tu, qf, M.geo.rh, e0, nel);
   __syncthreads();
   const Gas<S> gw = gas_no_heat(M.gas);
   for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
@@ -243,11 +247,32 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
     S Uf[nf], Q[D][nf], nv[D], Gv[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) Uf[f] = tf[f * nfp + fp];
+    if (CURV) {  // grad U = (1/J) sum_b (J dxi_b/dx) d/dxi_b U with the traced metric; own area normal
+      const size_t fo = (size_t)e * NF + face;
+      const S ij = dp.iJF[fo * nfp + fp];
+      S ja[D][D];
 #pragma unroll
-    for (int c = 0; c < D; ++c)
+      for (int b = 0; b < D; ++b)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) Q[c][f] = qg[(c * nf + f) * nfp];
-    unit_normal<D, S>(face, nv);
+        for (int c = 0; c < D; ++c) ja[b][c] = dp.JaF[((fo * D + b) * D + c) * nfp + fp];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        nv[c] = M.geo.SnE[(fo * D + c) * nfp + fp];
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          S v = 0;
+#pragma unroll
+          for (int b = 0; b < D; ++b) v += ja[b][c] * qg[(b * nf + f) * nfp];
+          Q[c][f] = ij * v;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) Q[c][f] = qg[(c * nf + f) * nfp];
+      unit_normal<D, S>(face, nv);
+    }
     const int nbk = M.nb[e * NF + face];
     if (nbk >= 0) {
       visc_flux_normal<D, S>(Uf, Q, nv, M.gas, Gv);
@@ -268,7 +293,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
 // ---------------------------------------------------------------------------
 // k_dgip_face: one thread per unique face point (unit normals on boxes).
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const S* __restrict__ TU,
                                                    const S* __restrict__ G, S* __restrict__ FF, S* __restrict__ HA) {
   using H = HD<D, P>;
@@ -283,7 +308,18 @@ __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const 
   const bool exp_ = ep >= 0 && dgip_explicit(dp, ep);
   if (!exm && !exp_) return;
   S nv[D];
-  unit_normal<D, S>(fm, nv);
+  S isJ = S(1);  // 1 / |area normal| (the penalty term is tau K(..).n / |n|)
+  if (CURV) {    // averaged area normal (own one on boundary faces)
+    S n2 = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      nv[c] = M.geo.SnF[((size_t)F * D + c) * nfp + fp];
+      n2 += nv[c] * nv[c];
+    }
+    isJ = S(1) / sqrt(n2);
+  } else {
+    unit_normal<D, S>(fm, nv);
+  }
   S UL[nf], UR[nf], Fv[nf], HL[D][nf], HR[D][nf];
   const S* tl = TU + ((size_t)em * NF + fm) * nf * nfp + fp;
 #pragma unroll
@@ -295,7 +331,7 @@ __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const 
     const S* tr = TU + ((size_t)ep * NF + fo) * nf * nfp + fpn;
 #pragma unroll
     for (int f = 0; f < nf; ++f) UR[f] = tr[f * nfp];
-    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]);
+    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]) * isJ;
     dgip_face_fn<D, S, S, VISC, DGIP_INTERIOR>(UL, UR, nv, M.gas, gw, tau, exm && !exp_, exp_ && !exm, Fv, HL, HR);
     if (VISC) {
       const S* gl = G + ((size_t)em * NF + fm) * nf * nfp + fp;
@@ -304,7 +340,7 @@ __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const 
       for (int f = 0; f < nf; ++f) Fv[f] -= S(0.5) * (gl[f * nfp] - gr[f * nfp]);
     }
   } else {
-    const S tau = dp.tk2 * dp.il[em];
+    const S tau = dp.tk2 * dp.il[em] * isJ;
     if (ep == -1) {
       dgip_face_fn<D, S, S, VISC, DGIP_WALL>(UL, UL, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
     } else {
@@ -355,7 +391,7 @@ constexpr size_t smem_dgip_elem() {
 // k_dgip_elem: residual of every explicit element (0 on implicit ones).
 // MODE 0 writes f; MODE 1 performs the ARK stage update (Sec. 4.2).
 // ---------------------------------------------------------------------------
-template <int D, int P, typename S, bool VISC, int MODE>
+template <int D, int P, typename S, bool VISC, int MODE, bool CURV>
 __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
                                                                  const S* __restrict__ FF, const S* __restrict__ HA,
                                                                  S* __restrict__ out, Stage<S> st) {
@@ -391,6 +427,28 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int f = 0; f < nf; ++f) hv[c][f] = x ? ha[(c * nf + f) * nfp] : S(0);
+      if (CURV) {  // contravariant components (1/J) sum_c (J dxi_a/dx_c) H_c at the face point
+        const size_t fo = (size_t)e0 * NF + tf;
+        const S ij = dp.iJF[fo * nfp + fp];
+        S ht[D][nf];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          S ja[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) ja[c] = dp.JaF[((fo * D + a) * D + c) * nfp + fp];
+#pragma unroll
+          for (int f = 0; f < nf; ++f) {
+            S v = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) v += ja[c] * hv[c][f];
+            ht[a][f] = ij * v;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) hv[a][f] = ht[a][f];
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
@@ -427,7 +485,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
         S x[n];
 #pragma unroll
         for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
-        const S r = M.geo.rh[(e0 + tt) * D + a];
+        const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];  // curvilinear: reference derivative
         S* o = gs + (tt * D + a) * STATE + f * N;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
@@ -442,9 +500,23 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
   }
   if (active) {
     S Fa[D][nf];
-    node_flux<D, S, VISC, false>(
-        M.gas, Uq, [&](int c, int f) { return gs[(t * D + c) * STATE + f * N + q]; },
-        [&](int, int) { return S(0); }, Fa);
+    if (CURV) {  // grad U = (1/J) sum_b Ja[b] d/dxi_b U; contravariant flux sum_c Ja[a][c] F_c
+      const S* ja = M.geo.Ja + (size_t)e * D * D * N + q;
+      const S ij = M.geo.iJ[(size_t)e * N + q];
+      node_flux<D, S, VISC, true>(
+          M.gas, Uq,
+          [&](int c, int f) {
+            S v = 0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) v += ja[(b * D + c) * N] * gs[(t * D + b) * STATE + f * N + q];
+            return ij * v;
+          },
+          [&](int a, int c) { return ja[(a * D + c) * N]; }, Fa);
+    } else {
+      node_flux<D, S, VISC, false>(
+          M.gas, Uq, [&](int c, int f) { return gs[(t * D + c) * STATE + f * N + q]; },
+          [&](int, int) { return S(0); }, Fa);
+    }
     if (VISC) {  // tangential part of the adjoint-consistency term
 #pragma unroll
       for (int a0 = 0; a0 < D; ++a0) {
@@ -458,7 +530,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
         }
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-          const S L = r0 * (side ? Lp0 : Lm0);
+          const S L = (CURV ? S(1) : r0) * (side ? Lp0 : Lm0);
           const S* hf = has + (t * NF + 2 * a0 + side) * D * nf * nfp + fp;
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -491,7 +563,9 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
         hm = has[(((tt * NF + 2 * a) * D + a) * nf + f) * nfp + line];
         hp = has[(((tt * NF + 2 * a + 1) * D + a) * nf + f) * nfp + line];
       }
-      const S r = M.geo.rh[(e0 + tt) * D + a];
+      // boxes: the 2/h_a factors here; curvilinear: the contravariant fluxes
+      // and face vectors carry the metric, and 1/J comes at the node
+      const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
 #pragma unroll
       for (int k = 0; k < n; ++k) {
         S s = 0;
@@ -506,12 +580,13 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_elem(Mesh<S> M, Dgip
   __syncthreads();
   if (!active) return;
   S res[nf];
+  const S ijq = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
     S s = 0;
 #pragma unroll
     for (int a = 0; a < D; ++a) s += fs[(t * D + a) * STATE + f * N + q];
-    res[f] = expl ? s : S(0);
+    res[f] = expl ? (CURV ? ijq * s : s) : S(0);
   }
   if (expl) flag_nonfinite<nf>(res, M.flags);
   if (MODE == 0) {
@@ -1006,19 +1081,22 @@ struct DgipOps {
     return r16(sizeof(S) * (H::T * H::STATE + H::T * H::FACE + (VISC ? H::T * D * H::FACE : 0)));
   }
 
-  template <bool VISC>
+  template <bool VISC, bool CURV>
   static cudaError_t trace_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, cudaStream_t st) {
     static SmemGate done;
-    auto k = k_dgip_trace<D, P, S, VISC>;
+    auto k = k_dgip_trace<D, P, S, VISC, CURV>;
     if (const cudaError_t e = allow_smem_once(k, smem_trace<VISC>(), done)) return e;
     k<<<blocks(M.E), H::THREADS, smem_trace<VISC>(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G);
     return cudaGetLastError();
   }
+  // curvilinear meshes are recognised by their face metric (dp.JaF)
   static cudaError_t trace(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w,
                            cudaStream_t st) {
     const Mesh<S>& m = *(const Mesh<S>*)M;
     const Dgip<S>& p = *(const Dgip<S>*)dp;
-    return visc ? trace_v<true>(m, p, (const S*)U, w, st) : trace_v<false>(m, p, (const S*)U, w, st);
+    if (p.JaF)
+      return visc ? trace_v<true, true>(m, p, (const S*)U, w, st) : trace_v<false, true>(m, p, (const S*)U, w, st);
+    return visc ? trace_v<true, false>(m, p, (const S*)U, w, st) : trace_v<false, false>(m, p, (const S*)U, w, st);
   }
   static cudaError_t face(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st) {
     const Mesh<S>& m = *(const Mesh<S>*)M;
@@ -1026,19 +1104,34 @@ struct DgipOps {
     const int total = m.nFaces * H::nfp;
     if (total == 0) return cudaSuccess;
     const int nb = (total + 127) / 128;
-    if (visc) k_dgip_face<D, P, S, true><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.G, (S*)w.FF, (S*)w.HA);
-    else k_dgip_face<D, P, S, false><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.G, (S*)w.FF, (S*)w.HA);
+    const S* TU = (const S*)w.TU;
+    const S* G = (const S*)w.G;
+    S* FF = (S*)w.FF;
+    S* HA = (S*)w.HA;
+    if (p.JaF) {
+      if (visc) k_dgip_face<D, P, S, true, true><<<nb, 128, 0, st>>>(m, p, TU, G, FF, HA);
+      else k_dgip_face<D, P, S, false, true><<<nb, 128, 0, st>>>(m, p, TU, G, FF, HA);
+    } else {
+      if (visc) k_dgip_face<D, P, S, true, false><<<nb, 128, 0, st>>>(m, p, TU, G, FF, HA);
+      else k_dgip_face<D, P, S, false, false><<<nb, 128, 0, st>>>(m, p, TU, G, FF, HA);
+    }
+    return cudaGetLastError();
+  }
+  template <bool VISC, int MODE, bool CURV>
+  static cudaError_t elem_vc(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, S* out,
+                             const Stage<S>& sa, cudaStream_t st) {
+    static SmemGate done;
+    auto k = k_dgip_elem<D, P, S, VISC, MODE, CURV>;
+    constexpr size_t sm = smem_dgip_elem<D, P, S, VISC>();
+    if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
+    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.FF, (const S*)w.HA, out, sa);
     return cudaGetLastError();
   }
   template <bool VISC, int MODE>
   static cudaError_t elem_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, S* out,
                             const Stage<S>& sa, cudaStream_t st) {
-    static SmemGate done;
-    auto k = k_dgip_elem<D, P, S, VISC, MODE>;
-    constexpr size_t sm = smem_dgip_elem<D, P, S, VISC>();
-    if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
-    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.FF, (const S*)w.HA, out, sa);
-    return cudaGetLastError();
+    return dp.JaF ? elem_vc<VISC, MODE, true>(M, dp, U, w, out, sa, st)
+                  : elem_vc<VISC, MODE, false>(M, dp, U, w, out, sa, st);
   }
   // stage == nullptr: write f to out; otherwise the ARK stage update
   static cudaError_t elem(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* out,

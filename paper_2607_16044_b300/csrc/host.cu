@@ -73,6 +73,8 @@ struct dgx_handle {
   bool dgip = false;
   double alpha = 1.0;          // SIPG penalty factor
   void* d_il = nullptr;        // [E] 1/l = |dT| / |T|, handle precision
+  void* d_JaF = nullptr;       // curvilinear DG-IP: [E][2d][d][d][nfp] metric at the own face points
+  void* d_iJF = nullptr;       // curvilinear DG-IP: [E][2d][nfp] 1/J there
   double* d_lo = nullptr;      // [E][d] box corners and sizes, FP64 (node coordinates)
   double* d_size = nullptr;
   bool has_farfield = false;   // the mesh has farfield faces (tag 1)
@@ -174,10 +176,11 @@ dgx_status upload_real(dgx_handle* h, const std::vector<double>& v, void** dst) 
 
 void free_mesh(dgx_handle* h) {
   void* ptrs[] = {h->d_nb, h->d_nbf, h->d_ori, h->d_faces, h->d_rh, h->d_Ja, h->d_iJ, h->d_SnE, h->d_SnF,
-                  h->d_il, h->d_lo, h->d_size};
+                  h->d_il, h->d_lo, h->d_size, h->d_JaF, h->d_iJF};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->d_il = nullptr;
+  h->d_JaF = h->d_iJF = nullptr;
   h->d_lo = h->d_size = nullptr;
   h->has_farfield = false;
   h->d_nb = nullptr;
@@ -228,6 +231,54 @@ dgx_status upload_metrics(dgx_handle* h, const std::vector<double>& Ja, const st
   if ((st = upload_real(h, iJ, &h->d_iJ)) != DGX_OK) return st;
   if ((st = upload_real(h, SnE, &h->d_SnE)) != DGX_OK) return st;
   return upload_real(h, SnF, &h->d_SnF);
+}
+
+// DG-IP on curvilinear meshes: the metric terms and J traced to every own face
+// point (JaF[E][2d][a][c][nfp], iJF = 1 / trace of J, as the face gradients
+// and the contravariant adjoint-consistency vectors need them) and the
+// characteristic length of the penalty, 1/l = |dT| / |T| with
+// |T| = sum_q w_q J_q and |dT| = sum over faces of w_f |J dxi_a0/dx| (Gauss rules).
+dgx_status upload_dgip_metrics(dgx_handle* h, const std::vector<double>& Ja, const std::vector<double>& iJ) {
+  const int E = h->E, d = h->d, n = h->n, N = h->N, NF = h->NF, nfp = h->nfp;
+  const dgx::Basis1 B = dgx::make_basis1(h->p);
+  std::vector<double> JaF((size_t)E * NF * d * d * nfp), iJF((size_t)E * NF * nfp), il(E);
+  for (int e = 0; e < E; ++e) {
+    double vol = 0.0, area = 0.0;
+    for (int q = 0; q < N; ++q) {
+      double wq = 1.0;
+      for (int a = 0; a < d; ++a) wq *= B.w[(q / pw(n, a)) % n];
+      vol += wq / iJ[(size_t)e * N + q];
+    }
+    for (int face = 0; face < NF; ++face) {
+      const int a0 = face >> 1;
+      const double* l = (face & 1) ? B.lp : B.lm;
+      const size_t fo = (size_t)e * NF + face;
+      for (int fp = 0; fp < nfp; ++fp) {
+        double Jf = 0.0;
+        for (int m = 0; m < n; ++m) Jf += l[m] / iJ[(size_t)e * N + node_of(n, m, fp, a0)];
+        iJF[fo * nfp + fp] = 1.0 / Jf;
+        for (int a = 0; a < d; ++a)
+          for (int c = 0; c < d; ++c) {
+            double s = 0.0;
+            for (int m = 0; m < n; ++m) s += l[m] * Ja[(((size_t)e * d + a) * d + c) * N + node_of(n, m, fp, a0)];
+            JaF[((fo * d + a) * d + c) * nfp + fp] = s;
+          }
+        double wf = 1.0, sn = 0.0;  // tangential weights, |area normal|
+        for (int a = 0, k = 0; a < d; ++a)
+          if (a != a0) wf *= B.w[(fp / pw(n, k++)) % n];
+        for (int c = 0; c < d; ++c) {
+          const double v = JaF[((fo * d + a0) * d + c) * nfp + fp];
+          sn += v * v;
+        }
+        area += wf * std::sqrt(sn);
+      }
+    }
+    il[e] = area / vol;
+  }
+  dgx_status st;
+  if ((st = upload_real(h, JaF, &h->d_JaF)) != DGX_OK) return st;
+  if ((st = upload_real(h, iJF, &h->d_iJF)) != DGX_OK) return st;
+  return upload_real(h, il, &h->d_il);
 }
 
 // Connectivity checks shared by both mesh kinds; builds the unique-face list.
@@ -400,6 +451,8 @@ template <typename S>
 dgx::Dgip<S> dgip_params(const dgx_handle* h, const int8_t* mask, const void* Uim) {
   dgx::Dgip<S> p{};
   p.il = (const S*)h->d_il;
+  p.JaF = (const S*)h->d_JaF;
+  p.iJF = (const S*)h->d_iJF;
   const int k = h->pen_k >= 0 ? h->pen_k : h->p;
   p.tk2 = (S)(h->alpha * (k + 1) * (k + 1));
   p.mask = mask;
@@ -1476,7 +1529,7 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
 dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
                               const int8_t* orient) {
   if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
-  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels (and their over-integration) take box meshes
+  if (h->inner) return DGX_EUNSUPPORTED;  // the over-integrated operator takes box meshes
   const int E = h->E, d = h->d, n = h->n, N = h->N;
   for (size_t i = 0; i < (size_t)E * d * N; ++i)
     if (!std::isfinite(xyz[i])) return DGX_EINVAL;
@@ -1535,6 +1588,7 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
   free_mesh(h);
   if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
   if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK) return st;
+  if (h->dgip && (st = upload_dgip_metrics(h, Ja, iJ)) != DGX_OK) return st;
   h->h_xyz.assign(xyz, xyz + (size_t)E * d * N);
   h->h_lo.clear();
   h->h_size.clear();
@@ -1548,7 +1602,7 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
 
 dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric) {
   if (!h || !J || !metric) return DGX_EINVAL;
-  if (h->dgip) return DGX_EUNSUPPORTED;  // the DG-IP kernels take box meshes
+  if (h->inner) return DGX_EUNSUPPORTED;  // the over-integrated operator takes box meshes
   if (!h->has_mesh) return DGX_ESTATE;
   const int E = h->E, d = h->d, N = h->N;
   for (size_t i = 0; i < (size_t)E * N; ++i)
@@ -1566,13 +1620,14 @@ dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric
   std::vector<int4> faces;
   dgx_status st = check_connectivity(h, h->h_nb.data(), h->h_nbf.data(), h->h_ori.data(), faces);
   if (st != DGX_OK) return st;
-  void** geo[] = {&h->d_Ja, &h->d_iJ, &h->d_SnE, &h->d_SnF};
+  void** geo[] = {&h->d_Ja, &h->d_iJ, &h->d_SnE, &h->d_SnF, &h->d_JaF, &h->d_iJF, &h->d_il};
   for (void** g : geo)
     if (*g) {
       cudaFree(*g);
       *g = nullptr;
     }
-  if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK) {
+  if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK ||
+      (h->dgip && (st = upload_dgip_metrics(h, Ja, iJ)) != DGX_OK)) {
     free_mesh(h);
     return st;
   }
@@ -1665,7 +1720,7 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
 dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace, void* stream) {
   if (!h || !U || !lambda || !gU || !workspace || gU == U || gU == lambda) return DGX_EINVAL;
   if (!h->has_mesh) return DGX_ESTATE;
-  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;  // DG-IP adjoint: box meshes
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
@@ -1730,7 +1785,7 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
                                 void* stream) {
   if (!h || !stages || !lam64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   if (h->inner)
@@ -1748,7 +1803,7 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
   if (!h || !U64 || !lam64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (((uintptr_t)stages & 255) != 0 || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   if (h->inner) {  // the step, then its adjoint, on the caller's stream

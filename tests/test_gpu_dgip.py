@@ -324,3 +324,83 @@ def test_dgip_channel3d_full_size_sampled(prec):
     record(f"dgip-channel3d-{prec}", rel=ferr, vjp_rel=gerr, sampled=len(rows))
     assert ferr < TOL[prec], ferr
     assert gerr < TOL[prec], gerr
+
+
+# ---------------------------------------------------------------- curvilinear
+def _curved(case):
+    if case == "warped2d-walls":
+        return I.warped_mesh(3, [5, 4], [1.0, 1.2], 0.04, periodic=[True, False])
+    if case == "rotated2d":
+        return I.rotate_elements(I.warped_mesh(3, [4, 4], [1.0, 1.3], 0.05), 3)
+    if case == "rotated2d-walls-p5":
+        return I.rotate_elements(I.warped_mesh(5, [3, 3], [1.0, 1.0], 0.04, periodic=[True, False]), 4)
+    return I.warped_mesh(2, [2, 3, 2], [1.0, 1.0, 1.0], 0.03, periodic=[True, True, False])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("case", ["warped2d-walls", "rotated2d", "rotated2d-walls-p5", "warped3d-walls"])
+def test_dgip_curvilinear(case, viscous, prec):
+    """The paper's operator on curved elements (metric terms traced to the
+    faces, area normals, contravariant adjoint-consistency vectors, 1/l from
+    the geometry): parity with the oracle on warped and rotated meshes."""
+    mesh = _curved(case)
+    _check(mesh, _ns() if viscous else _euler(), I.random_state(mesh, 690), prec,
+           f"dgip-curv-{case}-{viscous}-{prec}")
+
+
+def test_dgip_curvilinear_split_ark_and_no_adjoint():
+    """Curved elements: the geometry-split residual and one ARK step against
+    the oracle; the adjoint entry points answer DGX_EUNSUPPORTED there."""
+    from paper_2607_16044_b300.dgx import DGXError
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = _curved("warped2d-walls")
+    phys = _ns()
+    col = np.arange(mesh.n_elem) % 5
+    explicit = col != 2
+    Uex, Uim = I.random_state(mesh, 691), I.random_state(mesh, 692)
+    s = _solver(mesh, phys, "fp64")
+    s.set_explicit_mask(explicit)
+    f = s.rhs_split(torch.as_tensor(Uex).cuda(), torch.as_tensor(Uim).cuda()).cpu().numpy()
+    ref = _oracle(mesh, phys, Uex, explicit=explicit, U_im=Uim)
+    assert np.all(f[~explicit] == 0)
+    err = rel_err(f[explicit], ref[explicit])
+    record("dgip-curv-split", rel=err)
+    assert err < TOL["fp64"], err
+    s.set_explicit_mask(None)
+    s.set_tableau(*ars343_explicit())
+    U0 = I.random_state(mesh, 693)
+    U = torch.as_tensor(U0).cuda()
+    dt = 2e-5
+    s.ark_step(U, dt)
+    s.check()
+    op = SIPGOperator(mesh, gas_of(phys))
+    A, b, c = ark.ars343()
+    Uref = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b).numpy()
+    err = rel_err(U.cpu().numpy() - U0, Uref - U0)
+    record("dgip-curv-ark", rel=err)
+    assert err < TOL["fp64"], err
+    with pytest.raises(DGXError) as e:
+        s.rhs_vjp(torch.as_tensor(U0).cuda(), torch.as_tensor(U0).cuda())
+    assert e.value.code == 6
+
+
+def test_dgip_geometry_override_on_boxes():
+    """A DG-IP box handle given the boxes' exact metrics runs the curvilinear
+    kernels and still equals the oracle (and the box kernels)."""
+    mesh = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.3)], [True, False])
+    U = torch.as_tensor(I.random_state(mesh, 694)).cuda()
+    s0, s1 = _solver(mesh, _ns(), "fp64"), _solver(mesh, _ns(), "fp64")
+    E, N = mesh.n_elem, mesh.N
+    half = 0.5 * mesh.size
+    J = np.repeat(np.prod(half, 1)[:, None], N, 1)
+    M = np.zeros((E, N, 2, 2))
+    M[:, :, 0, 0] = half[:, 1:2]
+    M[:, :, 1, 1] = half[:, 0:1]
+    s1.set_geometry(J, M)
+    f0, f1 = s0.rhs(U).cpu().numpy(), s1.rhs(U).cpu().numpy()
+    s0.check()
+    s1.check()
+    ref = _oracle(mesh, _ns(), U.cpu().numpy())
+    assert rel_err(f1, ref) < TOL["fp64"]
+    assert rel_err(f1, f0) < 1e-13
