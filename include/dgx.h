@@ -82,11 +82,11 @@ typedef enum {
  *     tau = alpha (k+1)^2 / l, l = |T| / |dT|, the face taking the larger 1/l of its
  *     two elements) with the element's own (broken) gradient; adiabatic walls by
  *     App. B.1.2 (K_w: no normal heat flux; the convective flux against the mirror
- *     state), farfield boundaries (tag 1) by App. B.1.1.  Box meshes, and curved
+ *     state), farfield boundaries (tag 1) by App. B.1.1.  Box meshes and curved
  *     meshes (dgx_set_mesh_nodes / dgx_set_geometry: metric terms traced to the
- *     faces, area normals, 1/l from Gauss rules of J and of the face areas) for
- *     the residual, the ARK step and the split form; the DG-IP adjoint entry
- *     points take box meshes (DGX_EUNSUPPORTED on curved ones). */
+ *     faces, area normals, 1/l from Gauss rules of J and of the face areas),
+ *     for every residual, adjoint and ARK entry point (over-integration:
+ *     box meshes). */
 typedef enum { DGX_FLUX_LLF = 0, DGX_FLUX_VIJAYASUNDARAM = 1 } dgx_conv_flux;
 typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
 

@@ -160,7 +160,7 @@ __device__ __forceinline__ void face_tangential(const S* tu, S* qf, const S* rh,
 
 // Transposed face_tangential for one tangential direction index ci:
 // tub[t][face][f] += (2/h_c) D^T qfb[t][face][c][f] along every face line.
-template <int D, int P, typename S>
+template <int D, int P, typename S, bool CURV = false>
 __device__ __forceinline__ void face_tangential_t(const S* qfb, S* tub, const S* rh, int e0, int nel, int ci) {
   using H = HD<D, P>;
   constexpr int n = H::n, nf = H::nf, nfp = H::nfp, NF = H::NF;
@@ -176,7 +176,7 @@ __device__ __forceinline__ void face_tangential_t(const S* qfb, S* tub, const S*
     S zv[n];
 #pragma unroll
     for (int j = 0; j < n; ++j) zv[j] = z[j * st];
-    const S r = rh[(e0 + t) * D + c];
+    const S r = CURV ? S(1) : rh[(e0 + t) * D + c];
     S* o = tub + (t * NF + face) * nf * nfp + f * nfp + base;
 #pragma unroll
     for (int k = 0; k < n; ++k) {
@@ -611,7 +611,7 @@ constexpr size_t smem_dgip_vjp_elem() {
 
 // k_dgip_vjp_elem: from lambda, the cotangents of the face quantities (FFb, HAb)
 // and the element-local part of g (volume flux and gradient).
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, const S* __restrict__ U,
                                                                      const S* __restrict__ lam, S* __restrict__ gpart,
                                                                      S* __restrict__ FFb, S* __restrict__ HAb) {
@@ -633,11 +633,14 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
   const int e = e0 + t;
   S Uq[nf];
   if (active) {
+    // curvilinear: f = (1/J) (...) at the node, so the cotangent entering the
+    // transposed passes is lambda / J
+    const S ijq = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       Uq[f] = U[(size_t)e * STATE + f * N + q];
       us[t * STATE + f * N + q] = Uq[f];
-      ls[t * STATE + f * N + q] = lam[(size_t)e * STATE + f * N + q];
+      ls[t * STATE + f * N + q] = ijq * lam[(size_t)e * STATE + f * N + q];
     }
   }
   __syncthreads();
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
       S y[n];
 #pragma unroll
       for (int k = 0; k < n; ++k) y[k] = v[H::node(k, line, a)];
-      const S r = M.geo.rh[(e0 + tt) * D + a];
+      const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
       S* o = fb + (tt * D + a) * STATE + f * N;
       S sm = 0, sp = 0, dm = 0, dpp = 0;
 #pragma unroll
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
         S x[n];
 #pragma unroll
         for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
-        const S r = M.geo.rh[(e0 + tt) * D + a];
+        const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
         S* o = gs + (tt * D + a) * STATE + f * N;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
@@ -712,7 +715,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
         constexpr Tab1<S> tbl = make_tab1<S>(P);
         constexpr int a0 = decltype(PC)::value / (D - 1), ai = decltype(PC)::value % (D - 1);
         constexpr int a = ai + (ai >= a0);
-        const S r0 = M.geo.rh[(e0 + tt) * D + a0];
+        const S r0 = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a0];
         const S* v = fb + (tt * D + a) * STATE + f * N;
         S sm = 0, sp = 0;
 #pragma unroll
@@ -731,10 +734,24 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
   S Ub[nf];
   if (active) {
     S Fb[D][nf];
+    const S* jaq = CURV ? M.geo.Ja + (size_t)e * D * D * N + q : nullptr;
+    const S ijq = CURV ? M.geo.iJ[(size_t)e * N + q] : S(1);
+    if (CURV) {  // cotangent of F_c from those of the contravariant fluxes sum_c Ja[a][c] F_c
 #pragma unroll
-    for (int a = 0; a < D; ++a)
+      for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int f = 0; f < nf; ++f) Fb[a][f] = fb[(t * D + a) * STATE + f * N + q];
+        for (int f = 0; f < nf; ++f) {
+          S v = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) v += jaq[(a * D + c) * N] * fb[(t * D + a) * STATE + f * N + q];
+          Fb[c][f] = v;
+        }
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) Fb[a][f] = fb[(t * D + a) * STATE + f * N + q];
+    }
 #pragma unroll
     for (int f = 0; f < nf; ++f) Ub[f] = S(0);
     conv_flux_all_vjp<D, S>(Uq, Fb, M.gas, Ub);
@@ -744,15 +761,31 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int f = 0; f < nf; ++f) {
-          Q[c][f] = gs[(t * D + c) * STATE + f * N + q];
+          if (CURV) {  // physical gradient (1/J) sum_b Ja[b][c] d/dxi_b U
+            S v = 0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) v += jaq[(b * D + c) * N] * gs[(t * D + b) * STATE + f * N + q];
+            Q[c][f] = ijq * v;
+          } else {
+            Q[c][f] = gs[(t * D + c) * STATE + f * N + q];
+          }
           Fn[c][f] = -Fb[c][f];
           Qb[c][f] = S(0);
         }
       visc_flux_all_vjp<D, S>(Uq, Q, Fn, M.gas, Ub, Qb);
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+      for (int b = 0; b < D; ++b)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) qb[(t * D + c) * STATE + f * N + q] = Qb[c][f];
+        for (int f = 0; f < nf; ++f) {
+          S v = Qb[b][f];
+          if (CURV) {  // cotangent of the reference derivative d/dxi_b U
+            v = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) v += jaq[(b * D + c) * N] * Qb[c][f];
+            v *= ijq;
+          }
+          qb[(t * D + b) * STATE + f * N + q] = v;
+        }
     }
   }
   __syncthreads();  // everyone is done with ls (lambda) and the line reads
@@ -771,7 +804,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
         S x[n];
 #pragma unroll
         for (int m = 0; m < n; ++m) x[m] = v[H::node(m, line, a)];
-        const S r = M.geo.rh[(e0 + tt) * D + a];
+        const S r = CURV ? S(1) : M.geo.rh[(e0 + tt) * D + a];
         S* o = ls + tt * STATE + f * N;
 #pragma unroll
         for (int k = 0; k < n; ++k) {
@@ -842,7 +875,7 @@ inline void dgip_face_fn_vjp_host(const S (&UL)[D + 2], const S (&UR)[D + 2], co
 
 // k_dgip_vjp_face: one thread per unique face point: cotangents of both sides'
 // traces (TUb) and viscous normal fluxes (Gb) from those of FF and HA.
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, const S* __restrict__ TU,
                                                        const S* __restrict__ FFb, const S* __restrict__ HAb,
                                                        S* __restrict__ TUb, S* __restrict__ Gb) {
@@ -855,7 +888,38 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
   const int em = rec.x, ep = rec.y;
   const int fm = rec.z & 0xff, fo = (rec.z >> 8) & 0xff, code = (rec.z >> 16) & 0xff;
   S nv[D];
-  unit_normal<D, S>(fm, nv);
+  S isJ = S(1);
+  if (CURV) {
+    S n2 = 0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      nv[c] = M.geo.SnF[((size_t)F * D + c) * nfp + fp];
+      n2 += nv[c] * nv[c];
+    }
+    isJ = S(1) / sqrt(n2);
+  } else {
+    unit_normal<D, S>(fm, nv);
+  }
+  // curvilinear: HAb holds the cotangents of the contravariant vectors
+  // (1/J_f) sum_c Ja_f[a][c] H_c; back to those of H_c by the transpose
+  auto to_physical = [&](size_t fo_, int fp_, S (&hb)[D][D + 2]) {
+    if (!CURV) return;
+    const S ij = dp.iJF[fo_ * nfp + fp_];
+    S out[D][D + 2];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) {
+        S v = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v += dp.JaF[((fo_ * D + a) * D + c) * nfp + fp_] * hb[a][f];
+        out[c][f] = ij * v;
+      }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int f = 0; f < nf; ++f) hb[c][f] = out[c][f];
+  };
   const Gas<S> gw = gas_no_heat(M.gas);
   const size_t ol = ((size_t)em * NF + fm) * nf * nfp + fp;
   S UL[nf], UR[nf], Fbar[nf], HLb[D][nf], HRb[D][nf], ULb[nf], URb[nf];
@@ -871,6 +935,7 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
       HLb[c][f] = VISC ? HAb[((size_t)em * NF + fm) * D * nf * nfp + (c * nf + f) * nfp + fp] : S(0);
       HRb[c][f] = S(0);
     }
+  if (VISC) to_physical((size_t)em * NF + fm, fp, HLb);
   if (ep >= 0) {
     const int fpn = orient_map<D, n>(code, fp);
     const size_t orr = ((size_t)ep * NF + fo) * nf * nfp + fpn;
@@ -884,8 +949,9 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int f = 0; f < nf; ++f) HRb[c][f] = HAb[((size_t)ep * NF + fo) * D * nf * nfp + (c * nf + f) * nfp + fpn];
+      to_physical((size_t)ep * NF + fo, fpn, HRb);
     }
-    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]);
+    const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]) * isJ;
     dgip_face_fn_vjp<D, S, VISC, DGIP_INTERIOR>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
@@ -897,7 +963,7 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
       }
     }
   } else {
-    const S tau = dp.tk2 * dp.il[em];
+    const S tau = dp.tk2 * dp.il[em] * isJ;
     if (ep == -1) {
       dgip_face_fn_vjp<D, S, VISC, DGIP_WALL>(UL, UL, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
     } else {
@@ -922,7 +988,7 @@ constexpr size_t smem_dgip_gather() {
 
 // k_dgip_vjp_gather: g = gpart + the adjoint of the traces and of each own
 // face's viscous normal flux G = F^nu(U_f, grad U_f).n.
-template <int D, int P, typename S, bool VISC>
+template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
                                                                        const S* __restrict__ TUb,
                                                                        const S* __restrict__ Gb,
@@ -962,9 +1028,9 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
   }
   __syncthreads();
   if (VISC) {
-    face_lines<D, P, S, true>(us, tu, qfb, M.geo.rh, e0, nel, nullptr);
+    face_lines<D, P, S, true, CURV>(us, tu, qfb, M.geo.rh, e0, nel, nullptr);
     __syncthreads();
-    face_tangential<D, P, S>(tu, qfb, M.geo.rh, e0, nel);
+    face_tangential<D, P, S, CURV>(tu, qfb, M.geo.rh, e0, nel);
     __syncthreads();
     const Gas<S> gw = gas_no_heat(M.gas);
     // adjoint of G at every own face point: its U_f part goes to the trace
@@ -982,14 +1048,35 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
         Gbar[f] = Gb[((size_t)e * NF + face) * nf * nfp + f * nfp + fp];
         Ufb[f] = S(0);
       }
+      const size_t fo = (size_t)e * NF + face;
+      S ij = S(1), ja[D][D];
+      if (CURV) {
+        ij = dp.iJF[fo * nfp + fp];
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+          for (int c = 0; c < D; ++c) ja[b][c] = dp.JaF[((fo * D + b) * D + c) * nfp + fp];
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int f = 0; f < nf; ++f) {
-          Q[c][f] = qg[(c * nf + f) * nfp];
+          if (CURV) {  // physical gradient from the reference derivatives
+            S v = 0;
+#pragma unroll
+            for (int b = 0; b < D; ++b) v += ja[b][c] * qg[(b * nf + f) * nfp];
+            Q[c][f] = ij * v;
+          } else {
+            Q[c][f] = qg[(c * nf + f) * nfp];
+          }
           Qb[c][f] = S(0);
         }
-      unit_normal<D, S>(face, nv);
+      if (CURV) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) nv[c] = M.geo.SnE[(fo * D + c) * nfp + fp];
+      } else {
+        unit_normal<D, S>(face, nv);
+      }
       const int nbk = M.nb[e * NF + face];
       if (nbk >= 0) {
         visc_flux_normal_vjp<D, S>(Uf, Q, nv, Gbar, M.gas, Ufb, Qb);
@@ -1007,17 +1094,34 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
       S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
 #pragma unroll
       for (int f = 0; f < nf; ++f) tb_[f * nfp] += Ufb[f];
+      if (CURV) {  // cotangents of the reference derivatives: the transposed metric
+        S rb[D][nf];
 #pragma unroll
-      for (int c = 0; c < D; ++c)
+        for (int b = 0; b < D; ++b)
 #pragma unroll
-        for (int f = 0; f < nf; ++f) qg[(c * nf + f) * nfp] = Qb[c][f];
+          for (int f = 0; f < nf; ++f) {
+            S v = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) v += ja[b][c] * Qb[c][f];
+            rb[b][f] = ij * v;
+          }
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) qg[(b * nf + f) * nfp] = rb[b][f];
+      } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int f = 0; f < nf; ++f) qg[(c * nf + f) * nfp] = Qb[c][f];
+      }
     }
     // tangential face derivatives, transposed: one tangential direction per
     // pass (lines of different directions share face points)
 #pragma unroll
     for (int ci = 0; ci < D - 1; ++ci) {
       __syncthreads();
-      face_tangential_t<D, P, S>(qfb, tub, M.geo.rh, e0, nel, ci);
+      face_tangential_t<D, P, S, CURV>(qfb, tub, M.geo.rh, e0, nel, ci);
     }
   }
   __syncthreads();
@@ -1031,7 +1135,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
       const S bp = tub[(t * NF + 2 * a + 1) * nf * nfp + f * nfp + line];
       S qm = 0, qp = 0;
       if (VISC) {
-        const S r = M.geo.rh[(e0 + t) * D + a];
+        const S r = CURV ? S(1) : M.geo.rh[(e0 + t) * D + a];
         qm = r * qfb[((t * NF + 2 * a) * D + a) * nf * nfp + f * nfp + line];
         qp = r * qfb[((t * NF + 2 * a + 1) * D + a) * nf * nfp + f * nfp + line];
       }
@@ -1147,20 +1251,24 @@ struct DgipOps {
     return visc ? elem_v<true, 0>(m, p, (const S*)U, w, (S*)out, none, st)
                 : elem_v<false, 0>(m, p, (const S*)U, w, (S*)out, none, st);
   }
-  template <bool VISC>
+  template <bool VISC, bool CURV>
   static cudaError_t vjp_elem_v(const Mesh<S>& M, const S* U, const S* lam, const DgipWork& w, cudaStream_t st) {
     static SmemGate done;
-    auto k = k_dgip_vjp_elem<D, P, S, VISC>;
+    auto k = k_dgip_vjp_elem<D, P, S, VISC, CURV>;
     constexpr size_t sm = smem_dgip_vjp_elem<D, P, S, VISC>();
     if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
     k<<<blocks(M.E), H::THREADS, sm, st>>>(M, U, lam, (S*)w.gpart, (S*)w.FF, (S*)w.HA);
     return cudaGetLastError();
   }
+  // the element adjoint reads the metric from the mesh (geo.Ja set on curved meshes)
   static cudaError_t vjp_elem(const void* M, bool visc, const void* U, const void* lam, const DgipWork& w,
                               cudaStream_t st) {
     const Mesh<S>& m = *(const Mesh<S>*)M;
-    return visc ? vjp_elem_v<true>(m, (const S*)U, (const S*)lam, w, st)
-                : vjp_elem_v<false>(m, (const S*)U, (const S*)lam, w, st);
+    if (m.geo.Ja)
+      return visc ? vjp_elem_v<true, true>(m, (const S*)U, (const S*)lam, w, st)
+                  : vjp_elem_v<false, true>(m, (const S*)U, (const S*)lam, w, st);
+    return visc ? vjp_elem_v<true, false>(m, (const S*)U, (const S*)lam, w, st)
+                : vjp_elem_v<false, false>(m, (const S*)U, (const S*)lam, w, st);
   }
   static cudaError_t vjp_face(const void* M, const void* dp, bool visc, const DgipWork& w, cudaStream_t st) {
     const Mesh<S>& m = *(const Mesh<S>*)M;
@@ -1168,19 +1276,23 @@ struct DgipOps {
     const int total = m.nFaces * H::nfp;
     if (total == 0) return cudaSuccess;
     const int nb = (total + 127) / 128;
-    if (visc)
-      k_dgip_vjp_face<D, P, S, true><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.FF, (const S*)w.HA,
-                                                          (S*)w.TUb, (S*)w.Gb);
-    else
-      k_dgip_vjp_face<D, P, S, false><<<nb, 128, 0, st>>>(m, p, (const S*)w.TU, (const S*)w.FF, (const S*)w.HA,
-                                                           (S*)w.TUb, (S*)w.Gb);
+    const S* TU = (const S*)w.TU;
+    const S* FFb = (const S*)w.FF;
+    const S* HAb = (const S*)w.HA;
+    if (p.JaF) {
+      if (visc) k_dgip_vjp_face<D, P, S, true, true><<<nb, 128, 0, st>>>(m, p, TU, FFb, HAb, (S*)w.TUb, (S*)w.Gb);
+      else k_dgip_vjp_face<D, P, S, false, true><<<nb, 128, 0, st>>>(m, p, TU, FFb, HAb, (S*)w.TUb, (S*)w.Gb);
+    } else {
+      if (visc) k_dgip_vjp_face<D, P, S, true, false><<<nb, 128, 0, st>>>(m, p, TU, FFb, HAb, (S*)w.TUb, (S*)w.Gb);
+      else k_dgip_vjp_face<D, P, S, false, false><<<nb, 128, 0, st>>>(m, p, TU, FFb, HAb, (S*)w.TUb, (S*)w.Gb);
+    }
     return cudaGetLastError();
   }
-  template <bool VISC>
+  template <bool VISC, bool CURV>
   static cudaError_t gather_v(const Mesh<S>& M, const Dgip<S>& dp, const S* U, const DgipWork& w, S* g,
                               cudaStream_t st) {
     static SmemGate done;
-    auto k = k_dgip_vjp_gather<D, P, S, VISC>;
+    auto k = k_dgip_vjp_gather<D, P, S, VISC, CURV>;
     constexpr size_t sm = smem_dgip_gather<D, P, S, VISC>();
     if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
     k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.TUb, (const S*)w.Gb, (const S*)w.gpart, g);
@@ -1190,7 +1302,11 @@ struct DgipOps {
                                 cudaStream_t st) {
     const Mesh<S>& m = *(const Mesh<S>*)M;
     const Dgip<S>& p = *(const Dgip<S>*)dp;
-    return visc ? gather_v<true>(m, p, (const S*)U, w, (S*)g, st) : gather_v<false>(m, p, (const S*)U, w, (S*)g, st);
+    if (p.JaF)
+      return visc ? gather_v<true, true>(m, p, (const S*)U, w, (S*)g, st)
+                  : gather_v<false, true>(m, p, (const S*)U, w, (S*)g, st);
+    return visc ? gather_v<true, false>(m, p, (const S*)U, w, (S*)g, st)
+                : gather_v<false, false>(m, p, (const S*)U, w, (S*)g, st);
   }
 };
 

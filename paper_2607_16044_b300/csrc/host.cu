@@ -1720,7 +1720,7 @@ dgx_status dgx_rhs(dgx_handle* h, const void* U, void* dUdt, void* workspace, vo
 dgx_status dgx_rhs_vjp(dgx_handle* h, const void* U, const void* lambda, void* gU, void* workspace, void* stream) {
   if (!h || !U || !lambda || !gU || !workspace || gU == U || gU == lambda) return DGX_EINVAL;
   if (!h->has_mesh) return DGX_ESTATE;
-  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;  // DG-IP adjoint: box meshes
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip) {
     if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
@@ -1785,7 +1785,7 @@ dgx_status dgx_ark_adjoint_step(dgx_handle* h, const void* stages, double* lam64
                                 void* stream) {
   if (!h || !stages || !lam64 || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   if (((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   if (h->inner)
@@ -1803,7 +1803,7 @@ dgx_status dgx_ark_step_adjoint(dgx_handle* h, double* U64, double* lam64, doubl
   if (!h || !U64 || !lam64 || !stages || !workspace || !std::isfinite(dt)) return DGX_EINVAL;
   if (((uintptr_t)stages & 255) != 0 || ((uintptr_t)workspace & 255) != 0) return DGX_EINVAL;
   if (!h->has_mesh || h->stages == 0) return DGX_ESTATE;
-  if (!h->tab->vjp || (h->dgip && h->curv)) return DGX_EUNSUPPORTED;
+  if (!h->tab->vjp) return DGX_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   if (h->dgip && h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   if (h->inner) {  // the step, then its adjoint, on the caller's stream

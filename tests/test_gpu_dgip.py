@@ -349,10 +349,9 @@ def test_dgip_curvilinear(case, viscous, prec):
            f"dgip-curv-{case}-{viscous}-{prec}")
 
 
-def test_dgip_curvilinear_split_ark_and_no_adjoint():
-    """Curved elements: the geometry-split residual and one ARK step against
-    the oracle; the adjoint entry points answer DGX_EUNSUPPORTED there."""
-    from paper_2607_16044_b300.dgx import DGXError
+def test_dgip_curvilinear_split_and_ark():
+    """Curved elements: the geometry-split residual and one ARS(3,4,3) step
+    against the oracle."""
     from paper_2607_16044_b300.tableaux import ars343_explicit
     mesh = _curved("warped2d-walls")
     phys = _ns()
@@ -380,9 +379,39 @@ def test_dgip_curvilinear_split_ark_and_no_adjoint():
     err = rel_err(U.cpu().numpy() - U0, Uref - U0)
     record("dgip-curv-ark", rel=err)
     assert err < TOL["fp64"], err
-    with pytest.raises(DGXError) as e:
-        s.rhs_vjp(torch.as_tensor(U0).cuda(), torch.as_tensor(U0).cuda())
-    assert e.value.code == 6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("case", ["warped2d-walls", "rotated2d", "rotated2d-walls-p5", "warped3d-walls"])
+def test_dgip_vjp_curvilinear(case, viscous, prec):
+    """The DG-IP adjoint on curved elements against the oracle's autograd."""
+    _vjp_check(_curved(case), _ns() if viscous else _euler(), prec, f"dgip-vjp-curv-{case}-{viscous}-{prec}",
+               seed=695)
+
+
+def test_dgip_ark_adjoint_curvilinear():
+    """One DG-IP ARS(3,4,3) step and its discrete adjoint on a warped mesh
+    against the oracle's recurrences."""
+    from oracle.vjp import vjp
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = _curved("warped2d-walls")
+    phys = _ns()
+    U0 = I.random_state(mesh, 696)
+    lam0 = I.gaussian_cotangent(U0.shape, 697)
+    dt = 2e-5
+    s = _solver(mesh, phys, "fp64")
+    s.set_tableau(*ars343_explicit())
+    U, lam = torch.as_tensor(U0).cuda(), torch.as_tensor(lam0).cuda()
+    s.ark_step_adjoint(U, lam, dt, s.stage_buffer())
+    s.check()
+    op = SIPGOperator(mesh, gas_of(phys))
+    A, b, c = ark.ars343()
+    _, ys, _ = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b, return_stages=True)
+    ref = ark.erk_adjoint_step(lambda y, mu: vjp(op, y, mu), ys, torch.as_tensor(lam0), dt, A, b).numpy()
+    err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
+    record("dgip-ark-adjoint-curv", rel=err)
+    assert err < TOL["fp64"], err
 
 
 def test_dgip_geometry_override_on_boxes():
