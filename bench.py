@@ -656,8 +656,14 @@ def dgip_perf(reps=5):
     pk = peaks()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {}
-    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp32"), ("channel3d", "fp64")):
-        mesh, phys, U0 = I.channel2d_workload() if wl == "channel2d" else I.channel3d_workload()
+    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp32"), ("channel3d", "fp64"),
+                     ("warped3d", "fp32"), ("warped3d", "fp64")):
+        if wl == "warped3d":   # curved elements: a smoothly warped periodic 32^3 box, p = 3
+            mesh = I.warped_mesh(3, [32, 32, 32], [2 * np.pi] * 3, 0.03, periodic=[True, True, True])
+            phys = I.Physics(gamma=1.4, Re=1600.0, Pr=0.71, Ma=0.1, viscous=True)
+            U0 = I.random_state(mesh, 5)
+        else:
+            mesh, phys, U0 = I.channel2d_workload() if wl == "channel2d" else I.channel3d_workload()
         s = Solver(mesh, phys, prec, scheme="dgip")
         s.set_tableau(*ars343_explicit())
         dt = torch.float64 if prec == "fp64" else torch.float32
@@ -714,8 +720,9 @@ def dgip_perf(reps=5):
             r["split"] = {"explicit_elements": int(explicit.sum()), "ms_rhs_split": round(ms_split, 4)}
         out[f"{wl}-{prec}"] = r
         s.close()
-    out["workload"] = ("DG-IP (Vijayasundaram + SIPG, alpha = 1): 2D NS channel 256x128 p=4 and 3D NS channel "
-                       "48^3 p=5 (FP32, FP64), residual / VJP / ARS(3,4,3) step / step + adjoint")
+    out["workload"] = ("DG-IP (Vijayasundaram + SIPG, alpha = 1): 2D NS channel 256x128 p=4, 3D NS channel "
+                       "48^3 p=5 and a warped (curved) periodic 32^3 box p=3 (FP32, FP64), residual / VJP / "
+                       "ARS(3,4,3) step / step + adjoint")
     return out
 
 
