@@ -305,8 +305,9 @@ class OverIntegratedSIPG:
     """The DG-IP operator with its volume and face integrals taken by the
     M-point Gauss rule per direction (Sec. 5: the nonlinear terms are
     integrated by a rule of order 3k, M = ceil((3k+1)/2) by default) on the
-    degree-k solution space of box meshes; the mass matrix is the Gauss-node
-    one, exact on boxes.
+    degree-k solution space; the mass matrix is the Gauss-node one (exact on
+    boxes, the collocated w_q J_q on curved elements, as in the collocated
+    operator).
 
     Written through an identity.  Every degree-k test function l_q lies in
     the degree-(M-1) Lagrange space of the M Gauss points,
@@ -315,20 +316,28 @@ class OverIntegratedSIPG:
     sum_r l_q(z_r) B'_r, where B'_r is the collocated degree-(M-1) form of
     the same polynomial state tested with L_r: collocation at the M points
     is exactly the M-point rule, and the state's values, traces and
-    gradients there are those of the degree-k polynomial.  With
-    B'_r = -omega_r J f'_r this gives f = Pi f'(I U): I interpolates U to the
-    M points (I[m][j] = l_j(z_m)), f' is the collocated DG-IP operator there
-    with the penalty of the true degree, tau = alpha (k+1)^2 / l, and
-    Pi[q][m] = omega_m l_q(z_m) / w_q projects back.  Pinned by
-    ``brute.BruteSIPG.residual_sipg_oi``, which evaluates every integrand
-    pointwise at the M-point rule instead.
+    gradients there are those of the degree-k polynomial.  The element map
+    is the degree-k interpolant of the node coordinates; at the M points it
+    is represented exactly by the interpolated coordinates, from which the
+    degree-(M-1) operator takes J', its metric terms and normals.  With
+    B'_r = -omega_r J'_r f'_r and the collocated mass w_q J_q this gives
+
+        f = J^-1 Pi (J' f'(I U)),
+
+    I interpolating U to the M points (I[m][j] = l_j(z_m)), f' the
+    collocated DG-IP operator there with the penalty of the true degree,
+    tau = alpha (k+1)^2 / l, and Pi[q][m] = omega_m l_q(z_m) / w_q
+    projecting back; on boxes J' = J and f = Pi f'(I U).  Pinned by
+    ``brute.BruteSIPG.residual_sipg_oi`` (affine elements: every integrand
+    evaluated pointwise at the M-point rule instead), and on curved
+    elements by conservation (sum_q w_q J_q f_q = 0 on a periodic mesh),
+    free-stream preservation and the manufactured-solution rate.
     """
 
     def __init__(self, mesh, gas, alpha=1.0, U_inf=None, explicit=None, M=None):
         import dataclasses
-        from .basis import gauss_legendre, lagrange_eval
-        if mesh.kind != "boxes":
-            raise ValueError("the over-integrated operator takes box meshes")
+        from .basis import Basis1D, gauss_legendre, lagrange_eval
+        from .geometry import Geometry
         self.mesh, self.gas, self.p = mesh, gas, mesh.p
         self.d = d = mesh.dim
         self.n = n = mesh.p + 1
@@ -339,13 +348,21 @@ class OverIntegratedSIPG:
         z, om = (np.asarray(v) for v in gauss_legendre(M))
         self.I = torch.as_tensor(lagrange_eval(x, z))                           # [M][n]
         self.Pi = torch.as_tensor(om[None, :] * lagrange_eval(x, z).T / w[:, None])  # [n][M]
-        qi = [(np.arange(M ** d) // M ** a) % M for a in range(d)]             # direction a: stride M^a
-        xyz = np.empty((mesh.n_elem, d, M ** d))
-        for a in range(d):
-            xyz[:, a, :] = mesh.lo[:, a:a + 1] + 0.5 * (1.0 + z[qi[a]])[None, :] * mesh.size[:, a:a + 1]
+        if mesh.kind == "boxes":
+            qi = [(np.arange(M ** d) // M ** a) % M for a in range(d)]         # direction a: stride M^a
+            xyz = np.empty((mesh.n_elem, d, M ** d))
+            for a in range(d):
+                xyz[:, a, :] = mesh.lo[:, a:a + 1] + 0.5 * (1.0 + z[qi[a]])[None, :] * mesh.size[:, a:a + 1]
+        else:   # the degree-k element map at the M points
+            xyz = self._apply(torch.as_tensor(mesh.xyz, dtype=torch.float64), self.I, n, M).numpy()
         self.mesh_q = dataclasses.replace(mesh, p=M - 1, xyz=xyz)
         self.inner = SIPGOperator(self.mesh_q, gas, alpha=alpha, U_inf=U_inf, explicit=explicit,
                                   k_penalty=mesh.p)
+        E = mesh.n_elem
+        self.J = self.Jq = None                                                # boxes: J' = J cancels
+        if mesh.kind != "boxes":
+            self.J = Geometry(mesh, Basis1D(mesh.p)).J.reshape(E, 1, -1)       # at the nodes
+            self.Jq = self.inner.geo.J.reshape(E, 1, -1)                       # at the M points
 
     def _apply(self, V, Mat, m_in, m_out):
         """Mat ([m_out][m_in]) applied along every reference direction."""
@@ -365,4 +382,7 @@ class OverIntegratedSIPG:
     def residual(self, U, U_im=None):
         Uq = self.interpolate(U)
         Uimq = None if U_im is None else self.interpolate(U_im)
-        return self.project(self.inner.residual(Uq, Uimq))
+        Fq = self.inner.residual(Uq, Uimq)
+        if self.J is None:
+            return self.project(Fq)
+        return self.project(self.Jq * Fq) / self.J

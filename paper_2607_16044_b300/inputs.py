@@ -154,11 +154,13 @@ def _lagrange_matrix(nodes, at):
 
 
 def warped_mesh(p: int, counts: Sequence[int], length: Sequence[float], amp: float,
-                periodic: Optional[Sequence[bool]] = None) -> Mesh:
+                periodic: Optional[Sequence[bool]] = None, mixed: bool = False) -> Mesh:
     """Smoothly warped tensor mesh of [0, L_0] x ... with a periodic sine warp.
 
-    x_a' = x_a + amp * L_a * prod_b sin(2 pi x_b / L_b)  (vanishes on the box
-    boundary, so periodic wrap and walls stay planar).
+    x_a' = x_a + amp * L_a * prod_b sin(2 pi k_a x_b / L_b)  (vanishes on the
+    box boundary, so periodic wrap and walls stay planar), k_a = 1; with
+    ``mixed`` k_a = a + 1, so the displacement gradient is no longer rank one
+    and J is not a degree-p polynomial in each direction.
     """
     dim = len(counts)
     periodic = periodic if periodic is not None else [True] * dim
@@ -173,11 +175,12 @@ def warped_mesh(p: int, counts: Sequence[int], length: Sequence[float], amp: flo
     xl = np.empty((base.n_elem, dim, n ** dim))
     for a in range(dim):
         xl[:, a, :] = base.lo[:, a:a + 1] + 0.5 * (1.0 + gl[qi[a]])[None, :] * base.size[:, a:a + 1]
-    prod = np.ones((base.n_elem, n ** dim))
-    for b in range(dim):
-        prod = prod * np.sin(2.0 * np.pi * xl[:, b, :] / length[b])
     warped = np.empty_like(xl)
     for a in range(dim):
+        k = a + 1 if mixed else 1
+        prod = np.ones((base.n_elem, n ** dim))
+        for b in range(dim):
+            prod = prod * np.sin(2.0 * np.pi * k * xl[:, b, :] / length[b])
         warped[:, a, :] = xl[:, a, :] + amp * length[a] * prod
     # tensor-product interpolation Lobatto -> Gauss
     xyz = np.empty_like(warped)

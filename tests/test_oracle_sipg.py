@@ -433,3 +433,114 @@ def test_vijayasundaram_derivative_at_a_zero_eigenvalue_is_the_mean_of_the_one_s
     gL, gR = torch.autograd.grad(f, (UL_, UR_))
     deriv = float(((gL + gR) * w).sum())
     assert abs(deriv - 0.5 * float(left + right)) < 1e-6 * abs(float(right))
+
+
+# ------------------------------------------- over-integration on curved elements
+# f = J^-1 Pi (J' f'(I U)): the element map is the degree-k interpolant of the
+# node coordinates, evaluated at the M points for the point operator.  Affine
+# non-box elements go against the pointwise brute force; curved elements
+# against conservation, free stream and the manufactured-solution rate.
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("p,M", [(1, 3), (2, 4)])
+def test_over_integration_brute_force_2d_rotated(p, M, viscous):
+    m = I.rotate_elements(I.structured_box_mesh(p, [I.uniform_edges(0, 1, 3), I.wall_stretched_edges(1, 1.0)],
+                                                [True, False]), 31 + p)
+    U = I.random_state(m, 32)
+    f1 = OverIntegratedSIPG(m, _gas(viscous), M=M).residual(torch.as_tensor(U)).numpy()
+    f2 = BruteSIPG(m, _gas(viscous), period=[1.0, 100.0]).residual_sipg_oi(U, M)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+def test_over_integration_brute_force_2d_sheared_affine():
+    m = I.structured_box_mesh(2, [I.uniform_edges(0, 1, 3), I.uniform_edges(0, 1, 2)], [True, True])
+    xyz = m.xyz.copy()
+    xyz[:, 0, :] += 0.3 * xyz[:, 1, :]
+    m = I.Mesh(2, m.p, m.n_elem, "nodes", xyz, m.neighbor, m.nbr_face, m.orient)
+    U = I.random_state(m, 33)
+    f1 = OverIntegratedSIPG(m, _gas()).residual(torch.as_tensor(U)).numpy()
+    brute = BruteSIPG(m, _gas(), period=[1.0, 1.0])
+    brute.locate = _sheared_locate(brute, 0.3)
+    f2 = brute.residual_sipg_oi(U, 4)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+def test_over_integration_brute_force_3d_rotated():
+    m = I.rotate_elements(I.structured_box_mesh(1, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1.5, 2),
+                                                    I.wall_stretched_edges(1, 1.0)], [True, True, False]), 34)
+    U = I.random_state(m, 35)
+    f1 = OverIntegratedSIPG(m, _gas(True), M=3).residual(torch.as_tensor(U)).numpy()
+    f2 = BruteSIPG(m, _gas(True), period=[1.0, 1.5, 100.0]).residual_sipg_oi(U, 3)
+    assert np.abs(f1 - f2).max() / np.abs(f1).max() < 1e-12
+
+
+def _warped(d):
+    """Warps whose J is no degree-p polynomial (J' at the M points differs
+    from the interpolant of the nodal J)."""
+    if d == 2:
+        return I.rotate_elements(I.warped_mesh(3, [3, 4], [1.0, 1.3], 0.03, mixed=True), 36)
+    return I.warped_mesh(3, [3, 3, 2], [1.0, 1.0, 1.0], 0.02, mixed=True)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_over_integration_curved_conservation(d):
+    """sum_q w_q J_q f_q = sum_m omega_m J'_m f'_m: the point operator's
+    total, which the interior faces cancel on a periodic mesh.  Dropping the
+    J'/J weights (f = Pi f') breaks it by the O(h) variation of J."""
+    m = _warped(d)
+    op = OverIntegratedSIPG(m, _gas(True))
+    f = op.residual(torch.as_tensor(I.random_state(m, 37)))
+    w = np.polynomial.legendre.leggauss(m.p + 1)[1]
+    Wq = w
+    for _ in range(d - 1):
+        Wq = np.multiply.outer(w, Wq)
+    W = torch.as_tensor(Wq.reshape(-1))[None, None, :] * op.J
+    tot = (f * W).sum((0, 2))
+    scale = (f.abs() * W).sum((0, 2))
+    assert (tot.abs() / scale).max() < 1e-13
+    unweighted = (op.project(op.inner.residual(op.interpolate(torch.as_tensor(I.random_state(m, 37))))) * W).sum((0, 2))
+    assert (unweighted.abs() / scale).max() > 1e-6
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_over_integration_curved_free_stream(d):
+    """A uniform state stays at rest.  In 3D the mesh is the rank-one warp:
+    with Gauss nodes the curl-form metric terms traced to a face differ
+    between its two elements unless the warp is that simple, and the
+    averaged face normal then no longer matches either side (the collocated
+    operator behaves the same way)."""
+    m = _warped(2) if d == 2 else I.warped_mesh(3, [2, 2, 2], [1.0, 1.0, 1.0], 0.04)
+    U = np.zeros((m.n_elem, d + 2, m.N))
+    U[:, 0], U[:, 1], U[:, 2], U[:, d + 1] = 1.2, 0.3, -0.2, 3.0
+    if d == 3:
+        U[:, 3] = 0.1
+    f = OverIntegratedSIPG(m, _gas(True)).residual(torch.as_tensor(U))
+    assert f.abs().max() < 1e-13 * 4.0 / 1e-2
+
+
+def test_over_integration_curved_with_p_plus_1_points_is_the_collocated_operator():
+    m = _warped(2)
+    U = torch.as_tensor(I.random_state(m, 38))
+    f1 = OverIntegratedSIPG(m, _gas(True), M=m.p + 1).residual(U)
+    f0 = SIPGOperator(m, _gas(True)).residual(U)
+    assert (f1 - f0).abs().max() < 1e-13 * f0.abs().max()
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_over_integration_curved_manufactured_solution_order(viscous):
+    """The manufactured solution on warped elements: the truncation error
+    falls at the scheme's rate (as on boxes); a wrong metric or J weighting
+    at the M points leaves an O(1) error."""
+    p = 2
+    mu = 0.01
+    fns = mms_sympy.build(2, 1.4, mu if viscous else 0.0, 0.72)
+    gas = ph.Gas(1.4, Re=1 / mu if viscous else 0.0, Pr=0.72, viscous=viscous)
+    errs = []
+    for nc in (8, 16):
+        m = I.warped_mesh(p, [nc, nc], [1.0, 1.0], 0.02, mixed=True)
+        U = mms_sympy.evaluate(fns["U"], m.xyz, 0.0)
+        exact = -(mms_sympy.evaluate(fns["divFc"], m.xyz, 0.0) - mms_sympy.evaluate(fns["divFv"], m.xyz, 0.0))
+        f = OverIntegratedSIPG(m, gas).residual(torch.as_tensor(U)).numpy()
+        errs.append(np.sqrt(np.mean((f - exact) ** 2)) / np.sqrt(np.mean(exact ** 2)))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > (p - 1 if viscous else p) - 0.4, (errs, rate)
