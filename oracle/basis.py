@@ -46,6 +46,15 @@ def gauss_legendre(n):
     return x[order], w[order]
 
 
+def gauss_lobatto_points(n):
+    """The n Gauss-Lobatto points on [-1, 1] (ascending): the end points and
+    the roots of P_{n-1}', here from numpy's Legendre-series routines."""
+    if n == 2:
+        return np.array([-1.0, 1.0])
+    inner = np.sort(np.polynomial.legendre.Legendre.basis(n - 1).deriv().roots().real)
+    return np.concatenate([[-1.0], inner, [1.0]])
+
+
 def barycentric_weights(x):
     n = len(x)
     b = np.ones(n)

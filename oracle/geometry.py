@@ -9,7 +9,20 @@ tensor-product interpolant x(xi) of its node coordinates.  Quantities:
              scaled by J).  2D: Ja_0 = (y_eta, -x_eta), Ja_1 = (-y_xi, x_xi).
              3D: the conservative curl form of Kopriva (2006),
              J a^i_n = -e_i . curl_xi( X_l grad_xi X_m ), (n, m, l) cyclic,
-             which satisfies the discrete metric identities exactly.
+             with X_l grad_xi X_m replaced by its degree-p interpolant through
+             the (p+1)^3 Gauss-Lobatto points (the map evaluated there) and the
+             curl taken exactly; Ja is then a degree-p polynomial per
+             direction, carried to the Gauss nodes exactly.  So the Gauss
+             derivative matrices satisfy the metric identities
+             sum_i D_i Ja_i = 0, and the trace of Ja_a on a face depends on the
+             map's values at that face's Lobatto points only: both elements of
+             a conforming face see the same area normal, and a uniform flow
+             stays at rest on any curved mesh.  (Interpolating at the Gauss
+             nodes instead also satisfies the identities, but its face traces
+             extrapolate interior values and differ from side to side.)  X_l
+             enters relative to the element's mean: the curl of c grad X_m
+             vanishes identically (derivatives along different directions
+             commute), and the offset only adds rounding.
 * ``Sn``  -- area-weighted outward normal at every face point: +-Ja_a traced
              to the face xi_a = +-1 (s_J * n in the paper's notation).
 
@@ -24,7 +37,7 @@ q = i0 + n*i1 (+ n*n*i2).
 import numpy as np
 import torch
 
-from .basis import Basis1D
+from .basis import Basis1D, derivative_matrix, gauss_lobatto_points, lagrange_eval
 
 
 def along(V, a, dim, M):
@@ -89,14 +102,27 @@ class Geometry:
                 self.J = (m[:, 0, 0] * (m[:, 1, 1] * m[:, 2, 2] - m[:, 1, 2] * m[:, 2, 1])
                           - m[:, 0, 1] * (m[:, 1, 0] * m[:, 2, 2] - m[:, 1, 2] * m[:, 2, 0])
                           + m[:, 0, 2] * (m[:, 1, 0] * m[:, 2, 1] - m[:, 1, 1] * m[:, 2, 0]))
+                # the map at the Lobatto points, relative to the element mean
+                xl = gauss_lobatto_points(n)
+                G2L = torch.as_tensor(lagrange_eval(basis.x, xl))              # Gauss values -> Lobatto
+                L2G = torch.as_tensor(lagrange_eval(xl, basis.x))              # Lobatto values -> Gauss
+                DL = torch.as_tensor(derivative_matrix(xl))
+                XL = X
+                for a in range(3):
+                    XL = along(XL, a, 4, G2L)
+                XL = XL - XL.mean(dim=(2, 3, 4), keepdim=True)
+                dXL = torch.stack([torch.stack([along(XL[:, c], b, 3, DL) for b in range(3)], 1)
+                                   for c in range(3)], 1)                      # [E, c, b, ...]
                 Ja = torch.zeros((E, 3, 3) + (n,) * 3, dtype=torch.float64)
                 for nn in range(3):
                     mm, ll = (nn + 1) % 3, (nn + 2) % 3
-                    # G_b = X_l * d X_m / d xi_b  (nodal product = its interpolant)
-                    G = [X[:, ll] * dX[:, mm, b] for b in range(3)]
+                    # G_b = X_l * d X_m / d xi_b at the Lobatto points = its Lobatto interpolant
+                    G = [XL[:, ll] * dXL[:, mm, b] for b in range(3)]
                     for i in range(3):
                         j, k = (i + 1) % 3, (i + 2) % 3
-                        curl_i = along(G[k], j, 3, D) - along(G[j], k, 3, D)
+                        curl_i = along(G[k], j, 3, DL) - along(G[j], k, 3, DL)
+                        for a in range(3):
+                            curl_i = along(curl_i, a, 3, L2G)
                         Ja[:, i, nn] = -curl_i
                 self.Ja = Ja
         # face area-normals Sn[E][2d][d][nfp]

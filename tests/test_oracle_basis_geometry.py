@@ -98,3 +98,64 @@ def test_face_normals_opposite():
             mine = g.Sn[e, f]
             theirs = g.Sn[nb, nf][:, orient_index(o, 4, 2)]
             assert torch.allclose(mine, -theirs, atol=1e-13)
+
+
+def test_gauss_lobatto_closed_forms():
+    from oracle.basis import gauss_lobatto_points
+    r = math.sqrt
+    want = {2: [-1, 1], 3: [-1, 0, 1], 4: [-1, -1 / r(5), 1 / r(5), 1], 5: [-1, -r(3 / 7), 0, r(3 / 7), 1],
+            6: [-1, -r(1 / 3 + 2 * r(7) / 21), -r(1 / 3 - 2 * r(7) / 21), r(1 / 3 - 2 * r(7) / 21),
+                r(1 / 3 + 2 * r(7) / 21), 1]}
+    for n, x in want.items():
+        assert np.allclose(gauss_lobatto_points(n), x, atol=1e-15, rtol=0)
+
+
+def _mixed_warp_3d(p=3, rotate=None):
+    m = I.warped_mesh(p, [3, 3, 2], [1.0, 1.2, 1.0], 0.02, mixed=True)
+    return I.rotate_elements(m, rotate) if rotate is not None else m
+
+
+def test_face_normals_opposite_3d_curved():
+    """A warp whose displacement gradient is not rank one and rotated local
+    frames: each face's area normal, traced from either element, is the
+    same up to sign (the curl form through the Lobatto interpolant depends
+    on the face's own points only)."""
+    m = _mixed_warp_3d(3, rotate=4)
+    g = Geometry(m, Basis1D(3))
+    from oracle.residual import orient_index
+    scale = g.Sn.abs().max()
+    for e in range(m.n_elem):
+        for f in range(6):
+            nb, nf, o = m.neighbor[e, f], m.nbr_face[e, f], m.orient[e, f]
+            mine = g.Sn[e, f]
+            theirs = g.Sn[nb, nf][:, orient_index(o, 4, 3)]
+            assert (mine + theirs).abs().max() < 1e-13 * scale
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_geometry_curved_3d_identities_and_volume(p):
+    m = _mixed_warp_3d(p, rotate=5)
+    b = Basis1D(p)
+    g = Geometry(m, b)
+    assert torch.all(g.J > 0)
+    w3 = torch.as_tensor(np.einsum("i,j,k->ijk", b.w, b.w, b.w))
+    assert abs((g.J * w3).sum().item() - 1.2) < 1e-6       # quadrature of the exact volume
+    D = torch.as_tensor(b.D)
+    for c in range(3):
+        ident = sum(along(g.Ja[:, a, c], a, 3, D) for a in range(3))
+        assert ident.abs().max() < 1e-13 * g.Ja.abs().max() * (p + 1) ** 2
+
+
+@pytest.mark.parametrize("op", ["llf-br1", "dgip"])
+def test_free_stream_3d_curved(op):
+    """A uniform flow stays at rest on a curved 3D mesh with rotated frames."""
+    from oracle import physics as ph
+    from oracle.residual import DGOperator
+    from oracle.sipg import SIPGOperator
+    m = _mixed_warp_3d(3, rotate=6)
+    gas = ph.Gas(1.4, Re=80.0, Pr=0.72, viscous=True)
+    U = np.zeros((m.n_elem, 5, m.N))
+    U[:, 0], U[:, 1], U[:, 2], U[:, 3], U[:, 4] = 1.2, 0.3, -0.2, 0.1, 3.0
+    cls = DGOperator if op == "llf-br1" else SIPGOperator
+    f = cls(m, gas).residual(torch.as_tensor(U))
+    assert f.abs().max() < 1e-13 * 4.0 / 0.1
