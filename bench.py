@@ -729,10 +729,11 @@ def dgip_perf(reps=5):
 def oi_perf(reps=5):
     """The DG-IP operator over-integrated by the order-3k rule (Sec. 5) next
     to the collocated one on the same state: p = 3 (M = 5 Gauss points per
-    direction) on the 2D NS channel 256x128 (FP32, FP64) and the 3D NS channel
-    32^3 (FP64), p = 5 (M = 8) on the 3D NS channel 48^3 (FP64); residual, VJP
-    and ARS(3,4,3) step + adjoint, L2 flushed between repetitions; per-kernel
-    times from the library's event profiler."""
+    direction) on the 2D NS channel 256x128 (FP32, FP64), the 3D NS channel
+    32^3 (FP64) and a warped (curved) periodic 32^3 box (FP32, FP64), p = 5
+    (M = 8) on the 3D NS channel 48^3 (FP64); residual, VJP and ARS(3,4,3)
+    step + adjoint, L2 flushed between repetitions; per-kernel times from the
+    library's event profiler."""
     import torch
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
@@ -740,10 +741,15 @@ def oi_perf(reps=5):
     pk = peaks()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     out = {}
-    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp64"), ("channel3d-48-p5", "fp64")):
+    for wl, prec in (("channel2d", "fp32"), ("channel2d", "fp64"), ("channel3d", "fp64"), ("warped3d", "fp32"),
+                     ("warped3d", "fp64"), ("channel3d-48-p5", "fp64")):
         alu = alu_peak_tflops(prec)
         if wl == "channel2d":
             mesh, phys, U0 = I.channel2d_workload(p=3)
+        elif wl == "warped3d":   # the curved box of the DG-IP leg, p = 3
+            mesh = I.warped_mesh(3, [32, 32, 32], [2 * np.pi] * 3, 0.03, periodic=[True, True, True])
+            phys = I.Physics(gamma=1.4, Re=1600.0, Pr=0.71, Ma=0.1, viscous=True)
+            U0 = I.random_state(mesh, 5)
         elif wl == "channel3d":
             mesh, phys, U0 = I.channel3d_workload(p=3, nxy=32, n_half=16)
         else:  # the headline mesh: p = 5, 8 points per direction
@@ -789,8 +795,8 @@ def oi_perf(reps=5):
         r["rhs_cost_ratio"] = round(r["3k"]["ms_rhs"] / r["collocated"]["ms_rhs"], 3)
         out[f"{wl}-{prec}"] = r
     out["workload"] = ("DG-IP collocated vs over-integrated (order 3k): p=3 (4 vs 5 points per direction) on the "
-                       "2D NS channel 256x128 and the 3D NS channel 32^3; p=5 (6 vs 8 points) on the 3D NS channel "
-                       "48^3")
+                       "2D NS channel 256x128, the 3D NS channel 32^3 and a warped periodic 32^3 box (curved "
+                       "elements); p=5 (6 vs 8 points) on the 3D NS channel 48^3")
     return out
 
 

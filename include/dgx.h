@@ -86,7 +86,7 @@ typedef enum {
  *     meshes (dgx_set_mesh_nodes / dgx_set_geometry: metric terms traced to the
  *     faces, area normals, 1/l from Gauss rules of J and of the face areas),
  *     for every residual, adjoint and ARK entry point (over-integration:
- *     box meshes). */
+ *     box meshes and dgx_set_mesh_nodes meshes). */
 typedef enum { DGX_FLUX_LLF = 0, DGX_FLUX_VIJAYASUNDARAM = 1 } dgx_conv_flux;
 typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
 
@@ -100,7 +100,7 @@ typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
  * SIPG; other pairs give DGX_EUNSUPPORTED; visc_flux is ignored when
  * viscous = 0); penalty_alpha is the SIPG alpha (0 means the paper's 1).
  *
- * quad_points (DG-IP scheme, box meshes): 0 = collocated (the volume and face
+ * quad_points (DG-IP scheme): 0 = collocated (the volume and face
  * integrals by the (p+1)-point Gauss rule of the nodes); M in [p+1, 8] = the
  * nonlinear terms integrated by the M-point Gauss rule per direction (Sec. 5:
  * a rule of order 3k, M = ceil((3p+1)/2), which is 2, 4, 5, 7, 8 for
@@ -108,11 +108,14 @@ typedef enum { DGX_VISC_BR1 = 0, DGX_VISC_SIPG = 1 } dgx_visc_flux;
  * evaluates f = Pi f'(I U): I interpolates U to the M points, f' is the
  * collocated DG-IP operator of degree M-1 there with the penalty of degree p,
  * tau = alpha (p+1)^2 / l, and Pi[q][m] = omega_m l_q(z_m) / w_q projects back
- * (exact: the degree-p test functions lie in the degree-(M-1) space).  States
- * stay on the (p+1)^d nodes; every residual, VJP and ARK entry point applies
- * the rule; dgx_set_mesh_nodes, the HDG entry points and the batch runtime
- * return DGX_EUNSUPPORTED for such a handle; dgx_mms_source still samples the
- * source at the nodes.  quad_points is read only by dgx_create. */
+ * (exact: the degree-p test functions lie in the degree-(M-1) space).  On a
+ * curved mesh (dgx_set_mesh_nodes) f' runs on the element maps evaluated at
+ * the M points (J', metric terms and normals of the degree-p map there) and,
+ * with the nodal mass w_q J_q, f = J^-1 Pi (J' f'(I U)).  States stay on the
+ * (p+1)^d nodes; every residual, VJP and ARK entry point applies the rule;
+ * dgx_set_geometry, the HDG entry points and the batch runtime return
+ * DGX_EUNSUPPORTED for such a handle; dgx_mms_source still samples the source
+ * at the nodes.  quad_points is read only by dgx_create. */
 typedef struct {
   int32_t dim;        /* 2 or 3                                  */
   int32_t p;          /* 1 .. 5                                  */
@@ -150,6 +153,14 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
 dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz,
                               const int32_t* neighbor, const int8_t* nbr_face, const int8_t* orient);
 
+/* The metric terms dgx_set_mesh_nodes derives, on the host alone (no handle,
+ * no device): for n_elem elements of degree p (1 .. 7) in dim = 2 or 3 with
+ * node coordinates xyz[E][d][N] (host, double), J[E][N] = det dx/dxi and
+ * metric[E][N][d][d], metric[e][q][a][b] = J dxi_a/dx_b (caller-owned host
+ * arrays), in the layout dgx_set_geometry takes.  DGX_EINVAL for bad
+ * arguments, non-finite coordinates or an element with J <= 0 at a node. */
+dgx_status dgx_mesh_metrics(int32_t dim, int32_t p, int32_t n_elem, const double* xyz, double* J, double* metric);
+
 /* Geometry override (Sec. 3.1 element maps, given rather than derived): the
  * Jacobian J[E][N] > 0 and the metric terms metric[E][N][d][d],
  * metric[e][q][a][b] = J dxi_a/dx_b at the Gauss nodes (host, double,
@@ -159,9 +170,10 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz,
  * handle then runs the curvilinear kernels.  The caller answers for the
  * metric identities (sum_a d/dxi_a (J dxi_a/dx_b) = 0 discretely, which free
  * stream preservation needs).  DGX_ESTATE without a mesh, DGX_EUNSUPPORTED on
- * DG-IP handles (box kernels) and, afterwards, in dgx_batch_create (the batch
- * rebuilds geometry from the mesh description); the next dgx_set_mesh_*
- * call drops the override. */
+ * over-integrated handles (their point operator needs the geometry at the M
+ * points, which nodal values do not fix) and, afterwards, in dgx_batch_create
+ * (the batch rebuilds geometry from the mesh description); the next
+ * dgx_set_mesh_* call drops the override. */
 dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric);
 
 /* Explicit Butcher tableau of an (s)-stage ERK (Sec. 4.2, padded ERK half of

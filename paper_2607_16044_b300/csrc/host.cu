@@ -91,6 +91,7 @@ struct dgx_handle {
   double oiP[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};   // [n][M]  omega_m l_q(z_m) / w_q
   double oiPT[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};  // [M][n]  Pi^T
   double oiIT[dgx::OI_MAXQ * dgx::OI_MAXQ] = {};  // [n][M]  I^T
+  void* d_oiJq = nullptr;  // curved elements: [E][M^d] J at the M points (handle precision)
   // tableau
   int stages = 0;
   double A[dgx::MAXSTAGES * dgx::MAXSTAGES], b[dgx::MAXSTAGES], c[dgx::MAXSTAGES];
@@ -176,10 +177,11 @@ dgx_status upload_real(dgx_handle* h, const std::vector<double>& v, void** dst) 
 
 void free_mesh(dgx_handle* h) {
   void* ptrs[] = {h->d_nb, h->d_nbf, h->d_ori, h->d_faces, h->d_rh, h->d_Ja, h->d_iJ, h->d_SnE, h->d_SnF,
-                  h->d_il, h->d_lo, h->d_size, h->d_JaF, h->d_iJF};
+                  h->d_il, h->d_lo, h->d_size, h->d_JaF, h->d_iJF, h->d_oiJq};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   h->d_il = nullptr;
+  h->d_oiJq = nullptr;
   h->d_JaF = h->d_iJF = nullptr;
   h->d_lo = h->d_size = nullptr;
   h->has_farfield = false;
@@ -888,15 +890,20 @@ OiLayout layout_oi(const dgx_handle* h, int op) {
   return L;
 }
 
-// one transfer: the [no][ni] matrix a along every direction of each element
+// one transfer: the [no][ni] matrix a along every direction of each element,
+// on curved elements optionally scaled by Jacobians at its input and output
+// points (pre, post: [E][points], or nullptr)
 cudaError_t oi_transfer(dgx_handle* h, int kind, const void* in, void* out, bool to_quad, const double* a,
-                        cudaStream_t st) {
+                        cudaStream_t st, const void* pre = nullptr, const void* post = nullptr) {
   const int ni = to_quad ? h->n : h->Mq, no = to_quad ? h->Mq : h->n;
-  return launch(h, kind, st,
-                [&] { return dgx::oi_apply(h->d, h->fp64, in, out, h->E, h->nf, ni, no, a, h->nsm, st); });
+  return launch(h, kind, st, [&] {
+    return dgx::oi_apply(h->d, h->fp64, in, out, h->E, h->nf, ni, no, a, pre, post, h->nsm, st);
+  });
 }
 
-// f = Pi f'(I U) into out (U_im: the implicit state of the split form, or nullptr)
+// f = Pi f'(I U) into out (U_im: the implicit state of the split form, or
+// nullptr); on curved elements f = J^-1 Pi (J' f'(I U)), the mass w_q J_q at
+// the nodes and J' at the M points (d_oiJq set)
 template <typename S>
 cudaError_t oi_residual(dgx_handle* h, const void* U, const void* Uim, void* out, char* base, const OiLayout& L,
                         cudaStream_t st) {
@@ -910,11 +917,13 @@ cudaError_t oi_residual(dgx_handle* h, const void* U, const void* Uim, void* out
     const dgx::DgipWork w = dgip_work_at(q, base + L.inner, layout(q, DGX_OP_RHS));
     err = dgip_residual<S>(q, Uq, Uim ? h->d_mask : nullptr, Xq, Fq, w, nullptr, st);
   }
-  if (err == cudaSuccess) err = oi_transfer(h, DGX_K_OI_TO_NODES, Fq, out, false, h->oiP, st);
+  if (err == cudaSuccess)
+    err = h->d_oiJq ? oi_transfer(h, DGX_K_OI_TO_NODES, Fq, out, false, h->oiP, st, h->d_oiJq, h->d_iJ)
+                    : oi_transfer(h, DGX_K_OI_TO_NODES, Fq, out, false, h->oiP, st);
   return err;
 }
 
-// g = I^T (df'/dU')^T (Pi^T lam)
+// g = I^T (df'/dU')^T (Pi^T lam); curved: Pi^T lam becomes J' Pi^T (J^-1 lam)
 template <typename S>
 cudaError_t oi_vjp(dgx_handle* h, const void* U, const void* lam, void* g, char* base, const OiLayout& L,
                    cudaStream_t st) {
@@ -923,7 +932,9 @@ cudaError_t oi_vjp(dgx_handle* h, const void* U, const void* lam, void* g, char*
   void* Lq = base + L.Fq;
   void* Gq = base + L.Gq;
   cudaError_t err = oi_transfer(h, DGX_K_OI_TO_QUAD, U, Uq, true, h->oiI, st);
-  if (err == cudaSuccess) err = oi_transfer(h, DGX_K_OI_TO_QUAD, lam, Lq, true, h->oiPT, st);
+  if (err == cudaSuccess)
+    err = h->d_oiJq ? oi_transfer(h, DGX_K_OI_TO_QUAD, lam, Lq, true, h->oiPT, st, h->d_iJ, h->d_oiJq)
+                    : oi_transfer(h, DGX_K_OI_TO_QUAD, lam, Lq, true, h->oiPT, st);
   if (err == cudaSuccess) {
     const dgx::DgipWork w = dgip_work_at(q, base + L.inner, layout(q, DGX_OP_VJP));
     err = dgip_vjp<S>(q, Uq, Lq, Gq, w, st);
@@ -1526,17 +1537,83 @@ dgx_status dgx_set_mesh_boxes(dgx_handle* h, const double* lo, const double* siz
   return DGX_OK;
 }
 
-dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
-                              const int8_t* orient) {
-  if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
-  if (h->inner) return DGX_EUNSUPPORTED;  // the over-integrated operator takes box meshes
-  const int E = h->E, d = h->d, n = h->n, N = h->N;
-  for (size_t i = 0; i < (size_t)E * d * N; ++i)
-    if (!std::isfinite(xyz[i])) return DGX_EINVAL;
-  std::vector<int4> faces;
-  dgx_status st = check_connectivity(h, neighbor, nbr_face, orient, faces);
-  if (st != DGX_OK) return st;
-  const Basis B = make_basis(h->p);
+namespace {
+
+// Gauss-Lobatto points of n >= 2 per direction on [-1, 1], ascending: the
+// end points and the roots of P'_{n-1}, by Newton's method from the
+// Chebyshev-Lobatto points (P and P' by the three-term recurrence,
+// P'' = (2x P' - p(p+1) P) / (1 - x^2)).
+std::vector<double> lobatto_points(int n) {
+  const int p = n - 1;
+  std::vector<double> x(n);
+  x[0] = -1.0;
+  x[p] = 1.0;
+  for (int j = 1; j < p; ++j) {
+    double t = -std::cos(M_PI * j / p);
+    for (int it = 0; it < 100; ++it) {
+      double P0 = 1.0, P1 = t;
+      for (int k = 1; k < p; ++k) {
+        const double P2 = ((2 * k + 1) * t * P1 - k * P0) / (k + 1);
+        P0 = P1;
+        P1 = P2;
+      }
+      const double dP = p * (P0 - t * P1) / (1.0 - t * t);             // P_p'
+      const double d2P = (2.0 * t * dP - p * (p + 1.0) * P1) / (1.0 - t * t);  // P_p''
+      const double dt = dP / d2P;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[j] = t;
+  }
+  return x;
+}
+
+// L[m][j] = l_j(xe_m), the Lagrange basis through nodes x at the points xe
+std::vector<double> lagrange_matrix(const std::vector<double>& x, const std::vector<double>& xe) {
+  const int n = (int)x.size(), m = (int)xe.size();
+  std::vector<double> L((size_t)m * n, 1.0);
+  for (int r = 0; r < m; ++r)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k)
+        if (k != j) L[r * n + j] *= (xe[r] - x[k]) / (x[j] - x[k]);
+  return L;
+}
+
+// D[i][j] = l_j'(x_i) by barycentric weights, rows summing to zero
+std::vector<double> derivative_matrix(const std::vector<double>& x) {
+  const int n = (int)x.size();
+  std::vector<double> b(n, 1.0), D((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) b[j] /= (x[j] - x[k]);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j)
+      if (j != i) {
+        D[i * n + j] = (b[j] / b[i]) / (x[i] - x[j]);
+        s += D[i * n + j];
+      }
+    D[i * n + i] = -s;
+  }
+  return D;
+}
+
+// Metric terms of the degree-p element maps given by their node coordinates
+// (host, FP64): Ja[E][a][c][N] = J dxi_a/dx_c, iJ[E][N] = 1/J and, when
+// asked, J[E][N] (J = det dx/dxi at each node).  2D: the cofactors of dx/dxi.
+// 3D: the conservative curl form Ja[i][c] = -(D_j (X_l d_k X_m) - D_k (X_l
+// d_j X_m)), (c, m, l) and (i, j, k) cyclic, with X_l d X_m taken as its
+// degree-p interpolant through the Gauss-Lobatto points (the map evaluated
+// there, X_l relative to the element's mean) and carried back to the Gauss
+// nodes exactly: Ja is a degree-p polynomial per direction, so the Gauss
+// derivative matrices satisfy the metric identities, and its trace on a face
+// depends on that face's Lobatto points only, the same from both sides of a
+// conforming face (a uniform flow stays at rest).  The mean offset drops out
+// exactly (the curl of c grad X_m vanishes) and would only add rounding.
+dgx_status nodal_metrics(int d, int p, int E, const double* xyz, std::vector<double>& Ja, std::vector<double>& iJ,
+                         std::vector<double>* Jout) {
+  const int n = p + 1, N = ipow(n, d);
+  const Basis B = make_basis(p);
   // derivative of nodal data along direction a
   auto along = [&](const double* v, int a, double* out) {
     for (int q = 0; q < N; ++q) {
@@ -1546,7 +1623,27 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
       out[q] = s;
     }
   };
-  std::vector<double> Ja((size_t)E * d * d * N), iJ((size_t)E * N);
+  // an n x n matrix along direction a of nodal data
+  auto apply = [&](const double* Mat, const double* v, int a, double* out) {
+    for (int q = 0; q < N; ++q) {
+      const int fp = fpoint_of(n, q, a), qa = (q / pw(n, a)) % n;
+      double s = 0.0;
+      for (int m = 0; m < n; ++m) s += Mat[qa * n + m] * v[node_of(n, m, fp, a)];
+      out[q] = s;
+    }
+  };
+  std::vector<double> G2L, L2G, DL, XL, dXL;
+  if (d == 3) {
+    const std::vector<double> xl = lobatto_points(n), xg(B.x.begin(), B.x.end());
+    G2L = lagrange_matrix(xg, xl);  // Gauss-node values -> the map at the Lobatto points
+    L2G = lagrange_matrix(xl, xg);  // Lobatto values -> Gauss nodes
+    DL = derivative_matrix(xl);
+    XL.resize(3 * N);
+    dXL.resize(9 * N);
+  }
+  Ja.assign((size_t)E * d * d * N, 0.0);
+  iJ.assign((size_t)E * N, 0.0);
+  if (Jout) Jout->assign((size_t)E * N, 0.0);
   std::vector<double> dX(d * d * N), G(N), tmp(N), tmp2(N);
   for (int e = 0; e < E; ++e) {
     const double* X = xyz + (size_t)e * d * N;
@@ -1568,27 +1665,90 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
       }
       if (!(J > 0.0)) return DGX_EINVAL;  // inverted or degenerate element
       iJ[(size_t)e * N + q] = 1.0 / J;
+      if (Jout) (*Jout)[(size_t)e * N + q] = J;
     }
     if (d == 3) {
-      // conservative curl form: Ja[i][c] = -(D_j (X_l d_k X_m) - D_k (X_l d_j X_m)),
-      // (c, m, l) cyclic, (i, j, k) cyclic
+      // the map at the Lobatto points, relative to its mean
+      for (int c = 0; c < 3; ++c) {
+        apply(G2L.data(), X + c * N, 0, tmp.data());
+        apply(G2L.data(), tmp.data(), 1, tmp2.data());
+        apply(G2L.data(), tmp2.data(), 2, &XL[c * N]);
+        double mean = 0.0;
+        for (int q = 0; q < N; ++q) mean += XL[c * N + q];
+        mean /= N;
+        for (int q = 0; q < N; ++q) XL[c * N + q] -= mean;
+        for (int b = 0; b < 3; ++b) apply(DL.data(), &XL[c * N], b, &dXL[(c * 3 + b) * N]);
+      }
       for (int c = 0; c < 3; ++c) {
         const int mm = (c + 1) % 3, ll = (c + 2) % 3;
         for (int i = 0; i < 3; ++i) {
           const int j = (i + 1) % 3, k = (i + 2) % 3;
-          for (int q = 0; q < N; ++q) G[q] = X[ll * N + q] * dX[(mm * 3 + k) * N + q];
-          along(G.data(), j, tmp.data());
-          for (int q = 0; q < N; ++q) G[q] = X[ll * N + q] * dX[(mm * 3 + j) * N + q];
-          along(G.data(), k, tmp2.data());
-          for (int q = 0; q < N; ++q) JaE[(i * 3 + c) * N + q] = -(tmp[q] - tmp2[q]);
+          for (int q = 0; q < N; ++q) G[q] = XL[ll * N + q] * dXL[(mm * 3 + k) * N + q];
+          apply(DL.data(), G.data(), j, tmp.data());
+          for (int q = 0; q < N; ++q) G[q] = XL[ll * N + q] * dXL[(mm * 3 + j) * N + q];
+          apply(DL.data(), G.data(), k, tmp2.data());
+          for (int q = 0; q < N; ++q) G[q] = -(tmp[q] - tmp2[q]);  // at the Lobatto points
+          apply(L2G.data(), G.data(), 0, tmp.data());
+          apply(L2G.data(), tmp.data(), 1, tmp2.data());
+          apply(L2G.data(), tmp2.data(), 2, &JaE[(i * 3 + c) * N]);
         }
       }
     }
   }
+  return DGX_OK;
+}
+
+// The node coordinates [E][d][n^d] of the degree-p maps evaluated at the M
+// points per direction ([E][d][M^d]): the [M][n] matrix I along each direction.
+std::vector<double> interpolate_nodes(int d, int n, int M, int E, const double* xyz, const double* I) {
+  const int N = ipow(n, d), NQ = ipow(M, d);
+  std::vector<double> out((size_t)E * d * NQ), a(NQ), b(NQ);
+  for (size_t r = 0; r < (size_t)E * d; ++r) {
+    std::copy(xyz + r * N, xyz + (r + 1) * N, a.begin());
+    int lo = 1;  // extent of the directions already at M points
+    for (int dir = 0; dir < d; ++dir) {
+      const int hi = ipow(n, d - 1 - dir);  // directions still at the nodes
+      for (int t = 0; t < hi; ++t)
+        for (int m = 0; m < M; ++m)
+          for (int l = 0; l < lo; ++l) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += I[m * n + j] * a[l + lo * (j + n * t)];
+            b[l + lo * (m + M * t)] = s;
+          }
+      std::swap(a, b);
+      lo *= M;
+    }
+    std::copy(a.begin(), a.begin() + NQ, out.begin() + r * NQ);
+  }
+  return out;
+}
+
+// Curved mesh of handle h; J_out (optional) receives J at the nodes.  An
+// over-integrated handle also gives its point operator the element maps at
+// the M points and keeps J there for the projection's weights.
+dgx_status set_nodes_impl(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
+                          const int8_t* orient, std::vector<double>* J_out) {
+  const int E = h->E, d = h->d, N = h->N;
+  for (size_t i = 0; i < (size_t)E * d * N; ++i)
+    if (!std::isfinite(xyz[i])) return DGX_EINVAL;
+  std::vector<int4> faces;
+  dgx_status st = check_connectivity(h, neighbor, nbr_face, orient, faces);
+  if (st != DGX_OK) return st;
+  std::vector<double> Ja, iJ;
+  if ((st = nodal_metrics(d, h->p, E, xyz, Ja, iJ, J_out)) != DGX_OK) return st;
   free_mesh(h);
   if ((st = upload_connectivity(h, neighbor, nbr_face, orient, faces)) != DGX_OK) return st;
   if ((st = upload_metrics(h, Ja, iJ, faces)) != DGX_OK) return st;
   if (h->dgip && (st = upload_dgip_metrics(h, Ja, iJ)) != DGX_OK) return st;
+  if (h->inner) {
+    const std::vector<double> xq = interpolate_nodes(d, h->n, h->Mq, E, xyz, h->oiI);
+    std::vector<double> Jq;
+    if ((st = set_nodes_impl(h->inner, xq.data(), neighbor, nbr_face, orient, &Jq)) != DGX_OK ||
+        (st = upload_real(h, Jq, &h->d_oiJq)) != DGX_OK) {
+      free_mesh(h);
+      return st;
+    }
+  }
   h->h_xyz.assign(xyz, xyz + (size_t)E * d * N);
   h->h_lo.clear();
   h->h_size.clear();
@@ -1600,9 +1760,37 @@ dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* n
   return DGX_OK;
 }
 
+}  // namespace
+
+dgx_status dgx_set_mesh_nodes(dgx_handle* h, const double* xyz, const int32_t* neighbor, const int8_t* nbr_face,
+                              const int8_t* orient) {
+  if (!h || !xyz || !neighbor || !nbr_face || !orient) return DGX_EINVAL;
+  return set_nodes_impl(h, xyz, neighbor, nbr_face, orient, nullptr);
+}
+
+dgx_status dgx_mesh_metrics(int32_t dim, int32_t p, int32_t n_elem, const double* xyz, double* J, double* metric) {
+  if (!xyz || !J || !metric || (dim != 2 && dim != 3) || p < 1 || p > dgx::MAXN - 1 || n_elem < 1)
+    return DGX_EINVAL;
+  const int N = ipow(p + 1, dim);
+  for (size_t i = 0; i < (size_t)n_elem * dim * N; ++i)
+    if (!std::isfinite(xyz[i])) return DGX_EINVAL;
+  std::vector<double> Ja, iJ, Jv;
+  const dgx_status st = nodal_metrics(dim, p, n_elem, xyz, Ja, iJ, &Jv);
+  if (st != DGX_OK) return st;
+  std::copy(Jv.begin(), Jv.end(), J);
+  for (int e = 0; e < n_elem; ++e)
+    for (int q = 0; q < N; ++q)
+      for (int a = 0; a < dim; ++a)
+        for (int c = 0; c < dim; ++c)
+          metric[(((size_t)e * N + q) * dim + a) * dim + c] = Ja[(((size_t)e * dim + a) * dim + c) * N + q];
+  return DGX_OK;
+}
+
 dgx_status dgx_set_geometry(dgx_handle* h, const double* J, const double* metric) {
   if (!h || !J || !metric) return DGX_EINVAL;
-  if (h->inner) return DGX_EUNSUPPORTED;  // the over-integrated operator takes box meshes
+  // the point operator of over-integration needs the geometry at the M
+  // points, which nodal values of J and the metric do not determine
+  if (h->inner) return DGX_EUNSUPPORTED;
   if (!h->has_mesh) return DGX_ESTATE;
   const int E = h->E, d = h->d, N = h->N;
   for (size_t i = 0; i < (size_t)E * N; ++i)

@@ -49,7 +49,7 @@ EXPORTS = ["dgx_create", "dgx_destroy", "dgx_set_mesh_boxes", "dgx_set_mesh_node
            "dgx_set_contraction", "dgx_get_contraction", "dgx_ark_step_adjoint", "dgx_probe_fma",
            "dgx_set_farfield", "dgx_set_explicit_mask", "dgx_rhs_split", "dgx_mms_source",
            "dgx_set_wait_limit", "dgx_batch_set_persistent", "dgx_hdg_sizes", "dgx_hdg_blocks",
-           "dgx_hdg_condense", "dgx_set_geometry"]
+           "dgx_hdg_condense", "dgx_set_geometry", "dgx_mesh_metrics"]
 SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgx_set_mesh_boxes.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.dgx_set_mesh_nodes.argtypes = [vp, vp, vp, vp, vp]
     lib.dgx_set_geometry.argtypes = [vp, vp, vp]
+    lib.dgx_mesh_metrics.argtypes = [i32, i32, i32, vp, vp, vp]
     lib.dgx_set_tableau.argtypes = [vp, i32, vp, vp, vp]
     lib.dgx_workspace_bytes.argtypes = [vp, i32]
     lib.dgx_workspace_bytes.restype = ctypes.c_size_t
@@ -127,6 +128,18 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
+def mesh_metrics(mesh):
+    """J[E][N] and metric[E][N][d][d] = J dxi_a/dx_b that the library derives
+    from a node-coordinate mesh (dgx_mesh_metrics: host only, no GPU)."""
+    lib = load_library()
+    E, N, d = mesh.n_elem, mesh.N, mesh.dim
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    J = np.empty((E, N))
+    metric = np.empty((E, N, d, d))
+    _check(lib.dgx_mesh_metrics(d, mesh.p, E, _ptr(xyz), _ptr(J), _ptr(metric)), "dgx_mesh_metrics")
+    return J, metric
+
+
 def measure_fma_peak(precision: str, reps: int = 5, iters: Optional[int] = None) -> float:
     """Measured FMA throughput (TFLOP/s, best of ``reps``) of the current CUDA
     device in "fp64" or "fp32": dgx_probe_fma launches, each timed with CUDA
@@ -172,7 +185,7 @@ class Solver:
 
     ``mesh`` is a :class:`paper_2607_16044_b300.inputs.Mesh`; ``phys`` an
     :class:`inputs.Physics`.  ``precision`` is "fp64" or "fp32".
-    ``quad_points`` (DG-IP scheme, box meshes): None for the collocated
+    ``quad_points`` (DG-IP scheme, box or curved meshes): None for the collocated
     operator, "3k" for the over-integration rule of order 3k (M = (3p+2)//2
     Gauss points per direction), or an explicit M in [p+1, 8].
     """
@@ -200,21 +213,30 @@ class Solver:
             _check(self.lib.dgx_create(ctypes.byref(desc), ctypes.byref(h)), "dgx_create")
         self.h = h
         self.shape = (mesh.n_elem, mesh.dim + 2, mesh.N)
+        self.set_mesh(mesh)
+        self._ws = {}
+        self.stages = 0
+        if U_inf is not None:
+            self.set_farfield(U_inf)
+
+    def set_mesh(self, mesh):
+        """Upload a mesh (boxes or node coordinates) of the handle's dimension,
+        degree and element count, replacing the current one."""
+        if (mesh.dim, mesh.p, mesh.n_elem) != (self.mesh.dim, self.mesh.p, self.mesh.n_elem):
+            raise ValueError("the mesh must keep the handle's dimension, degree and element count")
         nb = np.ascontiguousarray(mesh.neighbor, dtype=np.int32)
         nbf = np.ascontiguousarray(mesh.nbr_face, dtype=np.int8)
         ori = np.ascontiguousarray(mesh.orient, dtype=np.int8)
         if mesh.kind == "boxes":
             lo = np.ascontiguousarray(mesh.lo, dtype=np.float64)
             sz = np.ascontiguousarray(mesh.size, dtype=np.float64)
-            _check(self.lib.dgx_set_mesh_boxes(h, _ptr(lo), _ptr(sz), _ptr(nb), _ptr(nbf), _ptr(ori)),
+            _check(self.lib.dgx_set_mesh_boxes(self.h, _ptr(lo), _ptr(sz), _ptr(nb), _ptr(nbf), _ptr(ori)),
                    "dgx_set_mesh_boxes")
         else:
             xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
-            _check(self.lib.dgx_set_mesh_nodes(h, _ptr(xyz), _ptr(nb), _ptr(nbf), _ptr(ori)), "dgx_set_mesh_nodes")
-        self._ws = {}
-        self.stages = 0
-        if U_inf is not None:
-            self.set_farfield(U_inf)
+            _check(self.lib.dgx_set_mesh_nodes(self.h, _ptr(xyz), _ptr(nb), _ptr(nbf), _ptr(ori)),
+                   "dgx_set_mesh_nodes")
+        self.mesh = mesh
 
     def set_farfield(self, U_inf):
         """Free-stream state (conservative) of the farfield boundaries (DG-IP scheme)."""

@@ -281,3 +281,124 @@ def test_oi_channel3d_p5_full_size_sampled():
     record("oi-channel3d-p5-fp64", rel=ferr, vjp_rel=gerr, sampled=len(rows))
     assert ferr < TOL["fp64"], ferr
     assert gerr < TOL["fp64"], gerr
+
+
+# ---------------------------------------------------------------- curved elements
+# f = J^-1 Pi (J' f'(I U)): the point operator runs on the element maps
+# evaluated at the M points; the projection carries the Jacobians.
+
+def _curved(dim, p, kind="warped"):
+    if dim == 2 and kind == "warped":   # J is no degree-p polynomial (mixed warp)
+        return I.rotate_elements(I.warped_mesh(p, [5, 4], [1.0, 1.3], 0.03, mixed=True), 40 + p)
+    if dim == 2:                        # rotated local frames, wall-stretched layers, adiabatic walls
+        return I.rotate_elements(I.structured_box_mesh(p, [I.uniform_edges(0, 1, 5), I.wall_stretched_edges(2, 1.4)],
+                                                       [True, False]), 41 + p)
+    if kind == "warped":
+        return I.warped_mesh(p, [3, 3, 2], [1.0, 1.0, 1.0], 0.02, mixed=True)
+    return I.rotate_elements(I.structured_box_mesh(p, [I.uniform_edges(0, 1, 2), I.uniform_edges(0, 1.2, 2),
+                                                       I.wall_stretched_edges(1, 1.0)], [True, True, False]), 42 + p)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_oi_curved_rhs(dim, p, prec):
+    _rhs_check(_curved(dim, p), _ns(), prec, f"oi-curved-{dim}d-p{p}-{prec}", seed=800 + p)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 4), (3, 2), (3, 3)])
+def test_oi_curved_walls_rotated(dim, p, viscous):
+    _rhs_check(_curved(dim, p, "rotated"), _ns() if viscous else _euler(), "fp64",
+               f"oi-rotated-{dim}d-p{p}-{viscous}", seed=810 + p)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,p", [(2, 2), (2, 3), (2, 5), (3, 2), (3, 4)])
+def test_oi_curved_vjp(dim, p, prec):
+    mesh = _curved(dim, p)
+    U = I.random_state(mesh, 820 + p)
+    lam = I.gaussian_cotangent(U.shape, 821 + p)
+    s = _solver(mesh, _ns(), prec)
+    g = s.rhs_vjp(torch.as_tensor(U).to("cuda", _dt(prec)).contiguous(),
+                  torch.as_tensor(lam).to("cuda", _dt(prec)).contiguous())
+    s.check()
+    if prec == "fp32":
+        U, lam = quantize32(U), quantize32(lam)
+    ref = vjp(_oracle(mesh, _ns()), torch.as_tensor(U), torch.as_tensor(lam)).numpy()
+    err = rel_err(g.double().cpu().numpy(), ref)
+    record(f"oi-curved-vjp-{dim}d-p{p}-{prec}", rel=err)
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_oi_curved_ark_step_and_adjoint(prec):
+    from paper_2607_16044_b300.tableaux import ars343_explicit
+    mesh = _curved(2, 3)
+    phys = _ns()
+    U0 = I.random_state(mesh, 830)
+    lam0 = I.gaussian_cotangent(U0.shape, 831)
+    dt = 2e-5
+    s = _solver(mesh, phys, prec)
+    s.set_tableau(*ars343_explicit())
+    U = torch.as_tensor(U0).cuda()
+    stages = s.stage_buffer()
+    s.ark_step_stages(U, dt, stages)
+    lam = torch.as_tensor(lam0).cuda()
+    s.ark_adjoint_step(stages, lam, dt)
+    s.check()
+    op = _oracle(mesh, phys)
+    A, b, c = ark.ars343()
+    Uref, ys, _ = ark.erk_step(op.residual, torch.as_tensor(U0), dt, A, b, return_stages=True)
+    err = rel_err(U.cpu().numpy() - U0, Uref.numpy() - U0)
+    record(f"oi-curved-ark-{prec}", rel=err)
+    assert err < TOL[prec], err
+    if prec == "fp32":
+        ys = [torch.as_tensor(quantize32(y.numpy())) for y in ys]
+    ref = ark.erk_adjoint_step(lambda y, mu: vjp(op, y, mu), ys, torch.as_tensor(lam0), dt, A, b).numpy()
+    err = rel_err(lam.cpu().numpy() - lam0, ref - lam0)
+    record(f"oi-curved-ark-adjoint-{prec}", rel=err)
+    assert err < TOL[prec], err
+
+
+def test_oi_curved_geometry_split_interface():
+    mesh = _curved(2, 3)
+    col = np.arange(mesh.n_elem) % 5
+    explicit = col != 2
+    Uex, Uim = I.random_state(mesh, 840), I.random_state(mesh, 841)
+    s = _solver(mesh, _ns(), "fp64")
+    s.set_explicit_mask(explicit)
+    f = s.rhs_split(torch.as_tensor(Uex).cuda(), torch.as_tensor(Uim).cuda()).cpu().numpy()
+    s.check()
+    ref = _oracle(mesh, _ns(), explicit=explicit).residual(torch.as_tensor(Uex), torch.as_tensor(Uim)).numpy()
+    assert np.all(f[~explicit] == 0)
+    err = rel_err(f[explicit], ref[explicit])
+    record("oi-curved-split-2d", rel=err)
+    assert err < TOL["fp64"], err
+
+
+def test_oi_curved_mesh_changes_and_geometry_override():
+    """Replacing a curved mesh by boxes drops the Jacobian weights (the box
+    result equals a fresh box handle's bit for bit) and a new curved mesh
+    brings them back; M = p+1 on a curved mesh is the collocated operator up
+    to the rounding of the weights; the nodal geometry override is refused."""
+    from paper_2607_16044_b300.dgx import DGXError
+    curved = _curved(2, 3)
+    boxes = I.structured_box_mesh(3, [I.uniform_edges(0, 1, 5), I.uniform_edges(0, 1.3, 4)], [True, True])
+    U = torch.as_tensor(I.random_state(curved, 850)).cuda()
+    s = _solver(curved, _ns(), "fp64")
+    f_curved = s.rhs(U).clone()
+    s.set_mesh(boxes)
+    assert torch.equal(s.rhs(U), _solver(boxes, _ns(), "fp64").rhs(U))
+    s.set_mesh(curved)
+    assert torch.equal(s.rhs(U), f_curved)
+    f0 = _solver(curved, _ns(), "fp64", None).rhs(U)
+    f1 = _solver(curved, _ns(), "fp64", curved.p + 1).rhs(U)
+    assert float((f1 - f0).abs().max() / f0.abs().max()) < 1e-14
+    J = np.ones((curved.n_elem, curved.N))
+    metric = np.zeros((curved.n_elem, curved.N, 2, 2))
+    metric[..., 0, 0] = metric[..., 1, 1] = 1.0
+    with pytest.raises(DGXError) as err:
+        s.set_geometry(J, metric)
+    assert err.value.code == 6  # DGX_EUNSUPPORTED
+    s.check()
