@@ -504,12 +504,10 @@ def test_over_integration_curved_conservation(d):
 
 @pytest.mark.parametrize("d", [2, 3])
 def test_over_integration_curved_free_stream(d):
-    """A uniform state stays at rest.  In 3D the mesh is the rank-one warp:
-    with Gauss nodes the curl-form metric terms traced to a face differ
-    between its two elements unless the warp is that simple, and the
-    averaged face normal then no longer matches either side (the collocated
-    operator behaves the same way)."""
-    m = _warped(2) if d == 2 else I.warped_mesh(3, [2, 2, 2], [1.0, 1.0, 1.0], 0.04)
+    """A uniform state stays at rest: the point operator's element maps at
+    the M points keep their face normals equal across faces (the 3D curl
+    form through the Lobatto interpolant) and the metric identities."""
+    m = _warped(d)
     U = np.zeros((m.n_elem, d + 2, m.N))
     U[:, 0], U[:, 1], U[:, 2], U[:, d + 1] = 1.2, 0.3, -0.2, 3.0
     if d == 3:
