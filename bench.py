@@ -186,19 +186,29 @@ def aggregate_rate(units_per_rank, ms_max, world):
 def make_solver(prec, workload="channel3d"):
     """Solver, mesh, physics and state of a workload name: "channel3d" (48^3
     p = 5), "channel2d" (256x128 p = 4), "channel3d-<cells in x, y>-<layers
-    per wall>"; a "dgip-" prefix selects the DG-IP scheme on the same mesh."""
+    per wall>", "warped3d-<cells>-p<degree>" (a warped periodic box, curved
+    elements, random state); a "dgip-" prefix selects the DG-IP scheme on the
+    same mesh, an "oi-" prefix the DG-IP scheme over-integrated by the
+    order-3k rule."""
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
     from paper_2607_16044_b300.tableaux import ars343_explicit
-    scheme = "llf-br1"
+    scheme, quad = "llf-br1", None
     if workload.startswith("dgip-"):
         scheme, workload = "dgip", workload[len("dgip-"):]
+    elif workload.startswith("oi-"):
+        scheme, quad, workload = "dgip", "3k", workload[len("oi-"):]
     if workload.startswith("channel3d-"):   # a smaller 3D channel, "channel3d-<cells in x, y>-<layers per wall>"
         nxy, nh = (int(v) for v in workload.split("-")[1:3])
         mesh, phys, U0 = I.channel3d_workload(nxy=nxy, n_half=nh)
+    elif workload.startswith("warped3d-"):
+        _, cells, deg = workload.split("-")
+        mesh = I.warped_mesh(int(deg[1:]), [int(cells)] * 3, [2 * np.pi] * 3, 0.03, periodic=[True, True, True])
+        phys = I.Physics(gamma=1.4, Re=1600.0, Pr=0.71, Ma=0.1, viscous=True)
+        U0 = I.random_state(mesh, 5)
     else:
         mesh, phys, U0 = I.channel3d_workload() if workload == "channel3d" else I.channel2d_workload()
-    s = Solver(mesh, phys, prec, scheme=scheme)
+    s = Solver(mesh, phys, prec, scheme=scheme, quad_points=quad)
     A, b, c = ars343_explicit()
     s.set_tableau(A, b, c)
     return s, mesh, phys, U0
@@ -209,7 +219,7 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
     + the discrete adjoint of that step (4 VJPs), L2 flushed between steps."""
     import torch
     s, mesh, phys, U0 = make_solver(prec, workload)
-    if workload.startswith("dgip-"):
+    if workload.startswith(("dgip-", "oi-")):
         # the DG-IP penalty on the 2e-5-thin wall cells makes |f| ~ 4e8: a step
         # far below the explicit limit keeps repeated steps finite (the work of
         # a step does not depend on dt)
@@ -1015,7 +1025,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--legs", default="fp64,fp32",
                     help="the full run (default), one leg 'fp64' / 'fp32' / 'fp32:channel2d' / "
-                         "'fp64:channel3d-<nxy>-<layers>' / 'fp64:dgip-channel3d-<nxy>-<layers>' alone (profiling "
+                         "'fp64:channel3d-<nxy>-<layers>' / 'fp64:dgip-channel3d-<nxy>-<layers>' / "
+                         "'fp64:oi-warped3d-<cells>-p<p>' alone (profiling "
                          "runs), 'tgv' for the TGV engine "
                          "comparison, 'dgip' for the DG-IP legs, 'hdg' for the HDG-IP blocks, or 'oi' for the over-integrated "
                          "DG-IP comparison")
