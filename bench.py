@@ -822,12 +822,18 @@ def hdg_perf(cells=64, reps=3):
     import torch
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
-    out = {"workload": f"HDG-IP element blocks, {cells}x{cells} periodic 2D NS quads, Re 100, FP64"}
+    out = {"workload": f"HDG-IP element blocks, {cells}x{cells} periodic 2D NS quads, Re 100, FP64; "
+                       "curved: the same on a warped mesh (metric terms per node and face point)"}
     alu = alu_peak_tflops("fp64")
-    for p in (1, 2, 3, 4, 5):
-        mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells)] * 2, [True, True])
+    for p in (1, 2, 3, 4, 5, "5-curved"):
+        curved = p == "5-curved"
+        p = 5 if curved else p
+        if curved:
+            mesh = I.warped_mesh(p, [cells, cells], [1.0, 1.0], 0.02, mixed=True)
+        else:
+            mesh = I.structured_box_mesh(p, [I.uniform_edges(0, 1, cells)] * 2, [True, True])
         phys = I.Physics(gamma=1.4, Re=100.0, Pr=0.72, Ma=0.3, viscous=True)
-        s = Solver(mesh, phys, "fp64")
+        s = Solver(mesh, phys, "fp64", scheme="dgip" if curved else "llf-br1")
         U0 = I.random_state(mesh, 3)
         U = torch.as_tensor(U0).cuda()
         # facet state: each element's own traces, perturbed
@@ -842,7 +848,8 @@ def hdg_perf(cells=64, reps=3):
         s.check()
         nu, nh = 4 * n * n, 16 * n
         fl = 2.0 * mesh.n_elem * (nu * nu * (nu + nh) + nh * nh * nu)
-        out[f"p{p}"] = {"elements": mesh.n_elem, "nu": nu, "nh": nh, "ms_blocks": round(ms_b, 3),
+        out[f"p{p}" + ("-curved" if curved else "")] = {"elements": mesh.n_elem, "nu": nu, "nh": nh,
+                                                       "ms_blocks": round(ms_b, 3),
                         "ms_condense": round(ms_c, 3),
                         "elements_per_s": round(mesh.n_elem / ((ms_b + ms_c) / 1e3), 1),
                         "condense_TFLOP_s": round(fl / (ms_c / 1e3) / 1e12, 3),

@@ -285,7 +285,10 @@ dgx_status dgx_set_wait_limit(dgx_handle* h, int64_t polls);
 
 /* Element-local blocks of the implicit region's Newton system (Sec. 4.3) for
  * the HDG-IP discretisation of Sec. 3.4 (no mixed variables: the element
- * unknowns are U), FP64 handles on 2D box meshes (else DGX_EUNSUPPORTED):
+ * unknowns are U), FP64 handles on 2D meshes (else DGX_EUNSUPPORTED): box
+ * meshes, and curved meshes of DG-IP handles (dgx_set_mesh_nodes or
+ * dgx_set_geometry: the metric terms at the nodes and traced to the faces,
+ * each element's own area normal; other curved handles DGX_EUNSUPPORTED):
  * for every element T, with its nodal state U (device [E][nf][N]) and the
  * facet state Uhat on its faces (device [E][2d][nf][n], the element's own
  * face-point order), the element form R_T (Eq.

@@ -1,6 +1,6 @@
 // Element-local blocks of the implicit region's HDG-IP Newton system
 // (Sec. 3.4 element and facet forms, Sec. 4.3 static condensation), FP64,
-// 2D box meshes.
+// 2D box and curved meshes.
 //
 // k_hdg_jacobian: one thread per (element, group of KC input columns).  The
 // element's residual R_T (the HDG-IP element form tested with each nodal
@@ -56,13 +56,23 @@ __device__ __forceinline__ void split_apply(const T (&Us)[D + 2], const T (&dU)[
   for (int f = 0; f < nf; ++f) out[f] = l0 * dU[f] + (lm - l0) * w.am * rm[f] + (lp - l0) * w.ap * rp[f];
 }
 
-template <int P, typename T>
+// CURV: the element's metric terms come from the arrays of HdgArgs (curved
+// or general affine elements); FF is then the area-weighted flux through the
+// own area normal Sn (|Sn| = s_J), HA the contravariant adjoint-consistency
+// vector (1/J_f) sum_c (J dxi_a/dx_c)_f H_c of H = F^nu(Uhat; (U_f - Uhat) (x) Sn),
+// and R = -w_q (sum_a Dh_a(Ja_a . (F - F^nu) + tangential H parts) - lift(FF)
+// + normal H parts).  On boxes both reduce to the unit-normal forms above.
+template <int P, bool CURV, typename T>
 __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R, T* hres) {
   constexpr int D = 2, n = P + 1, N = n * n, nf = 4, nfp = n, NF = 4;
   using H = Sh<D, P, 1>;
   constexpr Tab1<double> tb = make_tab1<double>(P);
-  const double rh[2] = {a.rh[e * 2], a.rh[e * 2 + 1]};
-  const double J = 1.0 / (rh[0] * rh[1]);  // prod(h_a / 2) = 1 / prod(r_a)
+  double rh[2] = {0.0, 0.0}, J = 0.0;
+  if constexpr (!CURV) {
+    rh[0] = a.rh[e * 2];
+    rh[1] = a.rh[e * 2 + 1];
+    J = 1.0 / (rh[0] * rh[1]);  // prod(h_a / 2) = 1 / prod(r_a)
+  }
   const double tau = a.tk2 * a.il[e];
   const Gas<T> g = gas_as<T, double>(a.gas);
   Gas<double> gw0 = a.gas;
@@ -82,10 +92,18 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
   for (int face = 0; face < NF; ++face) {
     const int a0 = face >> 1, side = face & 1, c = 1 - a0;
     const int kind = a.nb[e * NF + face];
-    const double sJ = J * rh[a0];
-    double nv[D] = {0.0, 0.0};
-    nv[a0] = side ? 1.0 : -1.0;
     for (int fp = 0; fp < nfp; ++fp) {
+      double nv[D] = {0.0, 0.0}, sJ, iJf = 0.0, JF[D][D] = {};
+      if constexpr (CURV) {
+        for (int cc = 0; cc < D; ++cc) nv[cc] = a.SnE[(((size_t)e * NF + face) * D + cc) * nfp + fp];
+        sJ = sqrt(nv[0] * nv[0] + nv[1] * nv[1]);
+        iJf = a.iJF[((size_t)e * NF + face) * nfp + fp];
+        for (int aa = 0; aa < D; ++aa)
+          for (int cc = 0; cc < D; ++cc) JF[aa][cc] = a.JaF[((((size_t)e * NF + face) * D + aa) * D + cc) * nfp + fp];
+      } else {
+        nv[a0] = side ? 1.0 : -1.0;
+        sJ = J * rh[a0];
+      }
       T Uf[nf], Uhf[nf], Q[D][nf], dl[nf];
       for (int f = 0; f < nf; ++f) {
         Uf[f] = TU[face][f][fp];
@@ -94,17 +112,27 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
         T sn = T(0), st = T(0);
         for (int j = 0; j < n; ++j) sn += T(side ? tb.dlp[j] : tb.dlm[j]) * u[f * N + H::node(j, fp, a0)];
         for (int m = 0; m < n; ++m) st += T(tb.D[fp][m]) * TU[face][f][m];
-        Q[a0][f] = T(rh[a0]) * sn;
-        Q[c][f] = T(rh[c]) * st;
+        if constexpr (CURV) {  // grad U = (1/J_f) sum_b (J dxi_b/dx)_f d_b U
+          for (int cc = 0; cc < D; ++cc) Q[cc][f] = T(iJf) * (T(JF[a0][cc]) * sn + T(JF[c][cc]) * st);
+        } else {
+          Q[a0][f] = T(rh[a0]) * sn;
+          Q[c][f] = T(rh[c]) * st;
+        }
       }
+      // the characteristic split takes the unit normal: A^+-(Sn) = s_J A^+-(n)
+      double nu[D];
+      for (int cc = 0; cc < D; ++cc) nu[cc] = CURV ? nv[cc] / sJ : nv[cc];
+      const T sa = T(CURV ? sJ : 1.0);
       const Gas<T>& gk = (kind == -1) ? gw : g;
       T Fn[nf], Ad[nf], Vg[D][nf], Kd[D][nf], Qd[D][nf];
       conv_flux_normal<D, T, double>(Uhf, nv, g, Fn);
-      split_apply<T, double, D>(Uhf, dl, nv, g, 1, Ad);
+      split_apply<T, double, D>(Uhf, dl, nu, g, 1, Ad);
+      for (int f = 0; f < nf; ++f) Ad[f] *= sa;
       visc_flux_all<D, T>(Uhf, Q, gk, Vg);
       for (int cc = 0; cc < D; ++cc)
         for (int f = 0; f < nf; ++f) Qd[cc][f] = T(nv[cc]) * dl[f];
       visc_flux_all<D, T>(Uhf, Qd, gk, Kd);
+      const double tpen = CURV ? tau / sJ : tau;
       T ff[nf];
       for (int f = 0; f < nf; ++f) {
         T vn = T(0), kn = T(0);
@@ -112,28 +140,36 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
           vn += Vg[cc][f] * T(nv[cc]);
           kn += Kd[cc][f] * T(nv[cc]);
         }
-        ff[f] = Fn[f] + Ad[f] - vn + T(tau) * kn;
+        ff[f] = Fn[f] + Ad[f] - vn + T(tpen) * kn;
         FF[face][f][fp] = ff[f];
-        for (int cc = 0; cc < D; ++cc) HA[face][cc][f][fp] = Kd[cc][f];
+        for (int aa = 0; aa < D; ++aa) {
+          if constexpr (CURV) {
+            T ht = T(0);
+            for (int cc = 0; cc < D; ++cc) ht += T(JF[aa][cc]) * Kd[cc][f];
+            HA[face][aa][f][fp] = T(iJf) * ht;
+          } else {
+            HA[face][aa][f][fp] = Kd[aa][f];
+          }
+        }
       }
       // facet residual
-      const double wf = a.w[fp] * sJ;
+      const double wf = CURV ? a.w[fp] : a.w[fp] * sJ;
       T hv[nf];
       if (kind >= 0) {
         for (int f = 0; f < nf; ++f) hv[f] = -ff[f];
       } else if (kind == -1) {
         T Uw[nf];
         wall_state<D, T>(Uf, Uw);
-        for (int f = 0; f < nf; ++f) hv[f] = Uhf[f] - Uw[f];
+        for (int f = 0; f < nf; ++f) hv[f] = (CURV ? T(sJ) : T(1)) * (Uhf[f] - Uw[f]);
       } else {
         T d1[nf], d2[nf], p1[nf], m2[nf];
         for (int f = 0; f < nf; ++f) {
           d1[f] = Uhf[f] - Uf[f];
           d2[f] = Uhf[f] - T(a.Uinf[f]);
         }
-        split_apply<T, double, D>(Uhf, d1, nv, g, 1, p1);
-        split_apply<T, double, D>(Uhf, d2, nv, g, -1, m2);
-        for (int f = 0; f < nf; ++f) hv[f] = p1[f] - m2[f];
+        split_apply<T, double, D>(Uhf, d1, nu, g, 1, p1);
+        split_apply<T, double, D>(Uhf, d2, nu, g, -1, m2);
+        for (int f = 0; f < nf; ++f) hv[f] = sa * (p1[f] - m2[f]);
       }
       for (int f = 0; f < nf; ++f) hres[(face * nf + f) * nfp + fp] = T(wf) * hv[f];
     }
@@ -146,22 +182,39 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
         const int line = H::fpoint(q, cc), k = H::qa(q, cc);
         T s = T(0);
         for (int m = 0; m < n; ++m) s += T(tb.D[k][m]) * u[f * N + H::node(m, line, cc)];
-        Q[cc][f][q] = T(rh[cc]) * s;
+        Q[cc][f][q] = CURV ? s : T(rh[cc]) * s;  // curved: reference derivatives, mapped below
       }
   for (int q = 0; q < N; ++q) {
+    double Ja[D][D] = {}, iJ = 0.0;
+    if constexpr (CURV) {
+      iJ = a.iJ[(size_t)e * N + q];
+      for (int aa = 0; aa < D; ++aa)
+        for (int cc = 0; cc < D; ++cc) Ja[aa][cc] = a.Ja[(((size_t)e * D + aa) * D + cc) * N + q];
+    }
     T Uq[nf], Qq[D][nf], F[D][nf], V[D][nf];
     for (int f = 0; f < nf; ++f) {
       Uq[f] = u[f * N + q];
-      for (int cc = 0; cc < D; ++cc) Qq[cc][f] = Q[cc][f][q];
+      if constexpr (CURV) {
+        for (int cc = 0; cc < D; ++cc) Qq[cc][f] = T(iJ) * (T(Ja[0][cc]) * Q[0][f][q] + T(Ja[1][cc]) * Q[1][f][q]);
+      } else {
+        for (int cc = 0; cc < D; ++cc) Qq[cc][f] = Q[cc][f][q];
+      }
     }
     conv_flux_all<D, T>(Uq, g, F);
     visc_flux_all<D, T>(Uq, Qq, g, V);
     for (int aa = 0; aa < D; ++aa)
       for (int f = 0; f < nf; ++f) {
-        T x = F[aa][f] - V[aa][f];
+        T x;
+        if constexpr (CURV) {
+          x = T(0);
+          for (int cc = 0; cc < D; ++cc) x += T(Ja[aa][cc]) * (F[cc][f] - V[cc][f]);
+        } else {
+          x = F[aa][f] - V[aa][f];
+        }
         const int a0 = 1 - aa;  // the other direction's faces carry the tangential part
         const int fp = H::fpoint(q, a0), k0 = H::qa(q, a0);
-        x += T(rh[a0] * tb.Lm[k0]) * HA[2 * a0][aa][f][fp] + T(rh[a0] * tb.Lp[k0]) * HA[2 * a0 + 1][aa][f][fp];
+        const double r0 = CURV ? 1.0 : rh[a0];
+        x += T(r0 * tb.Lm[k0]) * HA[2 * a0][aa][f][fp] + T(r0 * tb.Lp[k0]) * HA[2 * a0 + 1][aa][f][fp];
         Fa[aa][f][q] = x;
       }
   }
@@ -170,18 +223,19 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
       T s = T(0);
       for (int aa = 0; aa < D; ++aa) {
         const int line = H::fpoint(q, aa), k = H::qa(q, aa);
+        const double ra = CURV ? 1.0 : rh[aa];
         T v = T(0);
         for (int m = 0; m < n; ++m) v += T(tb.Dh[k][m]) * Fa[aa][f][H::node(m, line, aa)];
         v -= T(tb.Lm[k]) * FF[2 * aa][f][line] + T(tb.Lp[k]) * FF[2 * aa + 1][f][line];
-        v += T(rh[aa]) * (T(tb.dLm[k]) * HA[2 * aa][aa][f][line] + T(tb.dLp[k]) * HA[2 * aa + 1][aa][f][line]);
-        s += T(rh[aa]) * v;
+        v += T(ra) * (T(tb.dLm[k]) * HA[2 * aa][aa][f][line] + T(tb.dLp[k]) * HA[2 * aa + 1][aa][f][line]);
+        s += T(ra) * v;
       }
       const double wq = a.w[q % n] * a.w[q / n];
-      R[f * N + q] = -T(wq * J) * s;
+      R[f * N + q] = -T(CURV ? wq : wq * J) * s;
     }
 }
 
-template <int P, int KC>
+template <int P, int KC, bool CURV>
 __global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* __restrict__ U,
                                                       const double* __restrict__ Uh, double gamma, double* K,
                                                       double* C, double* Dm, double* A33, double* Rv, double* hv) {
@@ -200,19 +254,20 @@ __global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* _
     if (col < NU) u[col].d[k] = 1.0;
     else if (col < NCOL) uh[col - NU].d[k] = 1.0;
   }
-  hdg_forms<P, T>(a, e, u, uh, R, h);
+  hdg_forms<P, CURV, T>(a, e, u, uh, R, h);
   if (c0 == 0 && Rv) {  // the forms' values (the value part of any group)
     for (int i = 0; i < NU; ++i) Rv[(size_t)e * NU + i] = R[i].v;
     for (int k = 0; k < NH; ++k) hv[(size_t)e * NH + k] = h[k].v;
   }
-  const double J = 1.0 / (a.rh[e * 2] * a.rh[e * 2 + 1]);
+  const double J = CURV ? 0.0 : 1.0 / (a.rh[e * 2] * a.rh[e * 2 + 1]);
 #pragma unroll
   for (int k = 0; k < KC; ++k) {
     const int col = c0 + k;
     if (col < NU) {
       for (int i = 0; i < NU; ++i) {
         const int q = i % N;
-        const double m = (i == col) ? a.w[q % n] * a.w[q / n] * J : 0.0;
+        const double Jq = CURV ? 1.0 / a.iJ[(size_t)e * N + q] : J;
+        const double m = (i == col) ? a.w[q % n] * a.w[q / n] * Jq : 0.0;
         K[((size_t)e * NU + i) * NU + col] = m + gamma * R[i].d[k];
       }
       for (int r = 0; r < NH; ++r) Dm[((size_t)e * NH + r) * NU + col] = h[r].d[k];
@@ -321,7 +376,11 @@ cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, doub
                        double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
   constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n, KC = HDG_COLUMNS_PER_THREAD;
   const long long total = (long long)a.E * ((NU + NH + KC - 1) / KC);
-  k_hdg_jacobian<P, KC><<<(int)((total + 127) / 128), 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+  const int grid = (int)((total + 127) / 128);
+  if (a.Ja)
+    k_hdg_jacobian<P, KC, true><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+  else
+    k_hdg_jacobian<P, KC, false><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
   return cudaGetLastError();
 }
 

@@ -2045,11 +2045,20 @@ dgx_status dgx_hdg_blocks(dgx_handle* h, const double* U, const double* Uhat, do
                           double* D, double* A33, double* R, double* hres, void* stream) {
   if (!h || !U || !Uhat || !K || !C || !D || !A33 || !std::isfinite(gamma) || (!R) != (!hres)) return DGX_EINVAL;
   if (!h->fp64 || h->d != 2 || h->inner) return DGX_EUNSUPPORTED;
-  if (!h->has_mesh || h->curv) return h->curv ? DGX_EUNSUPPORTED : DGX_ESTATE;
+  if (!h->has_mesh) return DGX_ESTATE;
+  if (h->curv && !h->d_JaF) return DGX_EUNSUPPORTED;  // curved: the DG-IP face metric (DG-IP handles)
   if (h->has_farfield && !h->has_uinf) return DGX_ESTATE;
   dgx::HdgArgs a{};
   a.E = h->E;
-  a.rh = (const double*)h->d_rh;
+  if (h->curv) {
+    a.Ja = (const double*)h->d_Ja;
+    a.iJ = (const double*)h->d_iJ;
+    a.SnE = (const double*)h->d_SnE;
+    a.JaF = (const double*)h->d_JaF;
+    a.iJF = (const double*)h->d_iJF;
+  } else {
+    a.rh = (const double*)h->d_rh;
+  }
   a.il = (const double*)h->d_il;
   a.nb = h->d_nb;
   a.tk2 = 10.0 * (h->p + 1) * (h->p + 1);
