@@ -336,7 +336,8 @@ class Solver:
 
     def hdg_blocks(self, U: torch.Tensor, Uhat: torch.Tensor, gamma: float, forms: bool = False, stream=None):
         """Element-local HDG-IP Newton blocks (K, C, D, A33[, R, h]) of an SDIRK
-        stage with gamma = dt a_ii (FP64, 2D boxes); Uhat is [E][2d][nf][n]."""
+        stage with gamma = dt a_ii (FP64, 2D; box meshes, or curved meshes of a DG-IP
+        handle); Uhat is [E][2d][nf][n]."""
         nu, nh = ctypes.c_int32(), ctypes.c_int32()
         _check(self.lib.dgx_hdg_sizes(self.h, ctypes.byref(nu), ctypes.byref(nh)), "dgx_hdg_sizes")
         E = self.shape[0]
