@@ -815,10 +815,14 @@ def hdg_perf(cells=64, reps=3):
     HDG-IP, FP64) on a cells x cells periodic 2D NS mesh, degrees 1..5: the
     blocks K, C, D, A33 by forward-mode differentiation of the element and
     facet forms, and their static condensation (K^-1 C and the element Schur
-    contribution, Gauss-Jordan with partial pivoting), per element; counted
-    flops of the condensation (nu^2 (nu + nh) multiply-adds of the
-    elimination and nh^2 nu of D K^-1 C, two flops each) against the
-    measured FP64 peak."""
+    contribution: from p = 3 LU with partial pivoting in shared memory and
+    the columns of C solved in panels, below Gauss-Jordan elimination in
+    global memory), per element; counted flops of the condensation as
+    implemented (LU: the factorisation's sum over m < nu of m + 2 m^2 and
+    2 nu (nu - 1) + nu per column of C for the two triangular solves;
+    Gauss-Jordan: 2 (nu - 1)(nu (nu - 1) / 2 + nu nh) for the elimination and
+    nu (nu + 1) / 2 + nu nh for the pivot rows' scaling; both 2 nh^2 nu for
+    D K^-1 C) against the measured FP64 peak."""
     import torch
     from paper_2607_16044_b300 import inputs as I
     from paper_2607_16044_b300.dgx import Solver
@@ -847,7 +851,11 @@ def hdg_perf(cells=64, reps=3):
         ms_c = _time_events(lambda: s.hdg_condense(K, C, D, A), reps)
         s.check()
         nu, nh = 4 * n * n, 16 * n
-        fl = 2.0 * mesh.n_elem * (nu * nu * (nu + nh) + nh * nh * nu)
+        if nu >= 64:   # LU in shared memory
+            fl_el = nu * (nu - 1) / 2 + (nu - 1) * nu * (2 * nu - 1) / 3 + nh * (2.0 * nu * (nu - 1) + nu)
+        else:          # Gauss-Jordan
+            fl_el = 2.0 * (nu - 1) * (nu * (nu - 1) / 2 + nu * nh) + nu * (nu + 1) / 2 + nu * nh
+        fl = mesh.n_elem * (fl_el + 2.0 * nh * nh * nu)
         out[f"p{p}" + ("-curved" if curved else "")] = {"elements": mesh.n_elem, "nu": nu, "nh": nh,
                                                        "ms_blocks": round(ms_b, 3),
                         "ms_condense": round(ms_c, 3),

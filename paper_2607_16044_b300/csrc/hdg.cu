@@ -20,8 +20,11 @@
 // area factor s_J) -w_f s_J FF inside, w_f s_J (Uhat - U_w(U_f)) on walls,
 // w_f s_J (A^+(Uhat)(Uhat - U_f) - A^-(Uhat)(Uhat - U_inf)) on farfield faces.
 //
-// k_hdg_condense: one CTA per element: Gauss-Jordan elimination with partial
-// pivoting of [K | C] (K^{-1} C in place of C), then S_T = A33_T - D K^{-1} C.
+// k_hdg_condense_lu: one CTA per element: LU factorisation of K with partial
+// pivoting in shared memory, the columns of C solved in shared-memory panels
+// (K^{-1} C), then S_T = A33_T - D K^{-1} C.  k_hdg_condense (Gauss-Jordan
+// elimination of [K | C] in global memory) serves where K does not fit in
+// shared memory.
 #include <cuda_runtime.h>
 
 #include "dgip_physics.cuh"
@@ -371,6 +374,164 @@ __global__ void __launch_bounds__(256) k_hdg_condense(int E, int NU, int NH, con
   }
 }
 
+// The same blocks by LU factorisation in shared memory: K (nu x nu) is
+// copied into shared memory and factorised in place with partial pivoting
+// (full-row swaps, unit lower triangle below the diagonal); the columns of C
+// are then solved in panels of pc columns held in shared memory (the row
+// swaps, forward substitution with L, back substitution with U) and stored as
+// K^{-1} C; S = A33 - D K^{-1} C follows from global memory (the CTA's own,
+// L2-resident writes).  One CTA per element; the FP64 arithmetic works on
+// shared memory only, where the global Gauss-Jordan form streams its
+// nu x (nu + nh) working set through L2 at every elimination step.
+template <int NT>
+__device__ __forceinline__ void argmax_abs(double v, int i, double* rv, int* ri, double& best, int& bi) {
+  // block-wide max of |v| (ties: the smaller index); every thread gets the result
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, v, o);
+    const int oi = __shfl_down_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    rv[warp] = v;
+    ri[warp] = i;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int NW = NT / 32;
+    v = lane < NW ? rv[lane] : -1.0;
+    i = lane < NW ? ri[lane] : 0x7fffffff;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, v, o);
+      const int oi = __shfl_down_sync(0xffffffffu, i, o);
+      if (ov > v || (ov == v && oi < i)) {
+        v = ov;
+        i = oi;
+      }
+    }
+    if (lane == 0) {
+      rv[0] = v;
+      ri[0] = i;
+    }
+  }
+  __syncthreads();
+  best = rv[0];
+  bi = ri[0];
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_hdg_condense_lu(int E, int NU, int NH, int PC,
+                                                                    const double* __restrict__ K,
+                                                                    const double* __restrict__ C,
+                                                                    const double* __restrict__ Dm,
+                                                                    const double* __restrict__ A33,
+                                                                    double* __restrict__ X, double* __restrict__ S) {
+  extern __shared__ __align__(16) double sm_lu[];
+  double* W = sm_lu;                      // [NU][NU]
+  double* Pn = W + (size_t)NU * NU;       // [NU][PC] panel of C, then of K^{-1} C
+  int* piv = (int*)(Pn + (size_t)NU * PC);
+  __shared__ double rv[NT / 32];
+  __shared__ int ri[NT / 32];
+  constexpr int NWARP = NT / 32;
+  const int e = blockIdx.x;
+  if (e >= E) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* Ke = K + (size_t)e * NU * NU;
+  const double* Ce = C + (size_t)e * NU * NH;
+  double* Xe = X + (size_t)e * NU * NH;
+  for (int i = tid; i < NU * NU; i += NT) W[i] = Ke[i];
+  __syncthreads();
+  for (int k = 0; k < NU; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < NU; i += NT) {
+      const double v = fabs(W[(size_t)i * NU + k]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    argmax_abs<NT>(best, bi, rv, ri, best, bi);
+    const int p = bi;
+    if (tid == 0) piv[k] = p;
+    if (p != k)
+      for (int j = tid; j < NU; j += NT) {
+        const double t = W[(size_t)k * NU + j];
+        W[(size_t)k * NU + j] = W[(size_t)p * NU + j];
+        W[(size_t)p * NU + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / W[(size_t)k * NU + k];
+    for (int i = k + 1 + tid; i < NU; i += NT) W[(size_t)i * NU + k] *= inv;
+    __syncthreads();
+    // trailing update: rows over warps, columns over lanes (no index division)
+    for (int i = k + 1 + warp; i < NU; i += NWARP) {
+      const double l = W[(size_t)i * NU + k];
+      for (int j = k + 1 + lane; j < NU; j += 32) W[(size_t)i * NU + j] -= l * W[(size_t)k * NU + j];
+    }
+    __syncthreads();
+  }
+  for (int c0 = 0; c0 < NH; c0 += PC) {
+    const int pc = min(PC, NH - c0);
+    for (int t = tid; t < NU * pc; t += NT) {
+      const int i = t / pc, j = t % pc;
+      Pn[(size_t)i * PC + j] = Ce[(size_t)i * NH + c0 + j];
+    }
+    __syncthreads();
+    for (int j = tid; j < pc; j += NT)  // the row swaps, in order, one thread per column
+      for (int k = 0; k < NU; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+          const double t = Pn[(size_t)k * PC + j];
+          Pn[(size_t)k * PC + j] = Pn[(size_t)p * PC + j];
+          Pn[(size_t)p * PC + j] = t;
+        }
+      }
+    __syncthreads();
+    for (int k = 0; k + 1 < NU; ++k) {  // L y = P c
+      for (int i = k + 1 + warp; i < NU; i += NWARP) {
+        const double l = W[(size_t)i * NU + k];
+        for (int j = lane; j < pc; j += 32) Pn[(size_t)i * PC + j] -= l * Pn[(size_t)k * PC + j];
+      }
+      __syncthreads();
+    }
+    for (int k = NU - 1; k >= 0; --k) {  // U x = y
+      const double d = 1.0 / W[(size_t)k * NU + k];
+      for (int j = tid; j < pc; j += NT) Pn[(size_t)k * PC + j] *= d;
+      __syncthreads();
+      for (int i = warp; i < k; i += NWARP) {
+        const double u = W[(size_t)i * NU + k];
+        for (int j = lane; j < pc; j += 32) Pn[(size_t)i * PC + j] -= u * Pn[(size_t)k * PC + j];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < NU * pc; t += NT) {
+      const int i = t / pc, j = t % pc;
+      Xe[(size_t)i * NH + c0 + j] = Pn[(size_t)i * PC + j];
+    }
+    __syncthreads();
+  }
+  // S = A33 - D X, with X staged in the shared memory the factors held
+  // (nu nh <= nu nu doubles: nh <= nu for every degree here; else from global)
+  const double* De = Dm + (size_t)e * NH * NU;
+  const double* Ae = A33 + (size_t)e * NH * NH;
+  double* Se = S + (size_t)e * NH * NH;
+  const bool staged = NH <= NU;
+  if (staged)
+    for (int i = tid; i < NU * NH; i += NT) W[i] = Xe[i];
+  __syncthreads();
+  const double* Xs = staged ? W : Xe;
+  for (int t = tid; t < NH * NH; t += NT) {
+    const int r = t / NH, c = t % NH;
+    double s = Ae[t];
+    for (int m = 0; m < NU; ++m) s -= De[(size_t)r * NU + m] * Xs[(size_t)m * NH + c];
+    Se[t] = s;
+  }
+}
+
 template <int P>
 cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, double gamma, double* K, double* C,
                        double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
@@ -381,6 +542,36 @@ cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, doub
     k_hdg_jacobian<P, KC, true><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
   else
     k_hdg_jacobian<P, KC, false><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+  return cudaGetLastError();
+}
+
+// One launch of the shared-memory LU kernel, or cudaErrorNotSupported when
+// its shared memory cannot be had here (the caller then takes Gauss-Jordan).
+template <int NT>
+cudaError_t condense_lu(int E, int NU, int NH, const double* K, const double* C, const double* Dm,
+                        const double* A33, double* X, double* S, cudaStream_t st) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k_hdg_condense_lu<NT>) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  const size_t budget = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  const size_t fixed = (size_t)NU * NU * 8 + (size_t)NU * 4 + 16;
+  if (budget <= fixed) return cudaErrorNotSupported;
+  int PC = fixed + (size_t)NU * NH * 8 <= budget / 2 ? NH : (int)((budget - fixed) / ((size_t)NU * 8));
+  PC = PC > NH ? NH : PC;
+  if (PC < 8) return cudaErrorNotSupported;
+  const size_t smem = fixed + (size_t)NU * PC * 8;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_hdg_condense_lu<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return cudaErrorNotSupported;
+  }
+  k_hdg_condense_lu<NT><<<E, NT, smem, st>>>(E, NU, NH, PC, K, C, Dm, A33, X, S);
   return cudaGetLastError();
 }
 
@@ -400,6 +591,16 @@ cudaError_t hdg_jacobian(int P, const HdgArgs& a, const double* U, const double*
 cudaError_t hdg_condense(int E, int NU, int NH, const double* K, const double* C, const double* Dm, const double* A33,
                          double* X, double* S, double* W, cudaStream_t st) {
   if (E == 0) return cudaSuccess;
+  // shared-memory LU (nu >= 64, p >= 3 in 2D; smaller K are faster with the
+  // global Gauss-Jordan kernel) when K and a panel of at least 8 columns of C
+  // fit next to the kernel's static shared memory; the panel takes all of C
+  // when the whole [K | C] fits in half the limit (two CTAs per SM), else as
+  // many columns as fit.  512 threads from nu = 100 (one CTA per SM), 256 below.
+  if (NU >= 64) {
+    const cudaError_t e = NU >= 100 ? condense_lu<512>(E, NU, NH, K, C, Dm, A33, X, S, st)
+                                    : condense_lu<256>(E, NU, NH, K, C, Dm, A33, X, S, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   k_hdg_condense<<<E, 256, 0, st>>>(E, NU, NH, K, C, Dm, A33, X, S, W);
   return cudaGetLastError();
 }
