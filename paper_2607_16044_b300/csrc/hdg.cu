@@ -65,8 +65,15 @@ __device__ __forceinline__ void split_apply(const T (&Us)[D + 2], const T (&dU)[
 // vector (1/J_f) sum_c (J dxi_a/dx_c)_f H_c of H = F^nu(Uhat; (U_f - Uhat) (x) Sn),
 // and R = -w_q (sum_a Dh_a(Ja_a . (F - F^nu) + tangential H parts) - lift(FF)
 // + normal H parts).  On boxes both reduce to the unit-normal forms above.
-template <int P, bool CURV, typename T>
-__device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R, T* hres) {
+// FACET: the tangents of a column group seeded on facet DOFs alone (the bits
+// of fmask: the faces holding them).  The forms depend on Uhat only through
+// the face quantities of the face the DOF sits on, so only those faces are
+// evaluated (the others' FF, HA and h have zero tangents) and the element
+// residual takes no volume flux (its tangent is zero): what remains is the
+// lift of FF and the adjoint-consistency terms of HA.  The values are then
+// not the forms' values (they come from the full evaluation).
+template <int P, bool CURV, bool FACET, typename T>
+__device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R, T* hres, int fmask = 0xf) {
   constexpr int D = 2, n = P + 1, N = n * n, nf = 4, nfp = n, NF = 4;
   using H = Sh<D, P, 1>;
   constexpr Tab1<double> tb = make_tab1<double>(P);
@@ -95,6 +102,15 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
   for (int face = 0; face < NF; ++face) {
     const int a0 = face >> 1, side = face & 1, c = 1 - a0;
     const int kind = a.nb[e * NF + face];
+    if (FACET && !((fmask >> face) & 1)) {  // no seeded DOF on this face: zero tangents
+      for (int f = 0; f < nf; ++f)
+        for (int fp = 0; fp < nfp; ++fp) {
+          FF[face][f][fp] = T(0);
+          for (int aa = 0; aa < D; ++aa) HA[face][aa][f][fp] = T(0);
+          hres[(face * nf + f) * nfp + fp] = T(0);
+        }
+      continue;
+    }
     for (int fp = 0; fp < nfp; ++fp) {
       double nv[D] = {0.0, 0.0}, sJ, iJf = 0.0, JF[D][D] = {};
       if constexpr (CURV) {
@@ -178,7 +194,18 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
     }
   }
   // element residual: the DG-IP strong form with these face quantities, R = -M f
-  T Q[D][nf][N], Fa[D][nf][N];
+  T Fa[D][nf][N];
+  if constexpr (FACET) {  // the volume flux has zero tangent: only the tangential H parts
+    for (int q = 0; q < N; ++q)
+      for (int aa = 0; aa < D; ++aa)
+        for (int f = 0; f < nf; ++f) {
+          const int a0 = 1 - aa;
+          const int fp = H::fpoint(q, a0), k0 = H::qa(q, a0);
+          const double r0 = CURV ? 1.0 : rh[a0];
+          Fa[aa][f][q] = T(r0 * tb.Lm[k0]) * HA[2 * a0][aa][f][fp] + T(r0 * tb.Lp[k0]) * HA[2 * a0 + 1][aa][f][fp];
+        }
+  } else {
+  T Q[D][nf][N];
   for (int cc = 0; cc < D; ++cc)
     for (int f = 0; f < nf; ++f)
       for (int q = 0; q < N; ++q) {
@@ -221,6 +248,7 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
         Fa[aa][f][q] = x;
       }
   }
+  }
   for (int q = 0; q < N; ++q)
     for (int f = 0; f < nf; ++f) {
       T s = T(0);
@@ -238,16 +266,32 @@ __device__ void hdg_forms(const HdgArgs& a, int e, const T* u, const T* uh, T* R
     }
 }
 
+// Column groups of KC columns: the first NGE cover the element DOFs (the
+// last of them may reach into the facet DOFs), the remaining NGF hold facet
+// DOFs only.  One launch takes both sets, the element groups in its first
+// EB blocks and the facet groups after them, so that a warp never mixes the
+// full evaluation with the facet-only one.
+template <int P, int KC>
+struct HdgGroups {
+  static constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n, NCOL = NU + NH;
+  static constexpr int NGE = (NU + KC - 1) / KC;
+  static constexpr int NGF = (NCOL - NGE * KC + KC - 1) / KC;
+};
+
 template <int P, int KC, bool CURV>
 __global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* __restrict__ U,
                                                       const double* __restrict__ Uh, double gamma, double* K,
-                                                      double* C, double* Dm, double* A33, double* Rv, double* hv) {
+                                                      double* C, double* Dm, double* A33, double* Rv, double* hv,
+                                                      int EB) {
+  using G = HdgGroups<P, KC>;
   constexpr int n = P + 1, N = n * n, nf = 4, NU = nf * N, NH = 4 * nf * n;
-  constexpr int NCOL = NU + NH, NG = (NCOL + KC - 1) / KC;  // column groups per element
+  constexpr int NCOL = NU + NH;
   using T = Dual<double, KC>;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool facet = (int)blockIdx.x >= EB;  // uniform over the block
+  const int NG = facet ? G::NGF : G::NGE;    // column groups per element in this part
+  const long long gid = (long long)(facet ? blockIdx.x - EB : blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= (long long)a.E * NG) return;
-  const int e = (int)(gid / NG), c0 = (int)(gid % NG) * KC;
+  const int e = (int)(gid / NG), c0 = (facet ? G::NGE * KC : 0) + (int)(gid % NG) * KC;
   T u[NU], uh[NH], R[NU], h[NH];
   for (int i = 0; i < NU; ++i) u[i] = T(U[(size_t)e * NU + i]);
   for (int i = 0; i < NH; ++i) uh[i] = T(Uh[(size_t)e * NH + i]);
@@ -257,7 +301,14 @@ __global__ void __launch_bounds__(128) k_hdg_jacobian(HdgArgs a, const double* _
     if (col < NU) u[col].d[k] = 1.0;
     else if (col < NCOL) uh[col - NU].d[k] = 1.0;
   }
-  hdg_forms<P, CURV, T>(a, e, u, uh, R, h);
+  if (facet) {  // facet columns only: the faces that hold them
+    int fmask = 0;
+    for (int k = 0; k < KC; ++k)
+      if (c0 + k < NCOL) fmask |= 1 << ((c0 + k - NU) / (nf * n));
+    hdg_forms<P, CURV, true, T>(a, e, u, uh, R, h, fmask);
+  } else {
+    hdg_forms<P, CURV, false, T>(a, e, u, uh, R, h);
+  }
   if (c0 == 0 && Rv) {  // the forms' values (the value part of any group)
     for (int i = 0; i < NU; ++i) Rv[(size_t)e * NU + i] = R[i].v;
     for (int k = 0; k < NH; ++k) hv[(size_t)e * NH + k] = h[k].v;
@@ -535,13 +586,13 @@ __global__ void __launch_bounds__(NT) k_hdg_condense_lu(int E, int NU, int NH, i
 template <int P>
 cudaError_t launch_jac(const HdgArgs& a, const double* U, const double* Uh, double gamma, double* K, double* C,
                        double* Dm, double* A33, double* Rv, double* hv, cudaStream_t st) {
-  constexpr int n = P + 1, NU = 4 * n * n, NH = 16 * n, KC = HDG_COLUMNS_PER_THREAD;
-  const long long total = (long long)a.E * ((NU + NH + KC - 1) / KC);
-  const int grid = (int)((total + 127) / 128);
+  constexpr int KC = HDG_COLUMNS_PER_THREAD;
+  using G = HdgGroups<P, KC>;
+  const int ge = (int)(((long long)a.E * G::NGE + 127) / 128), gf = (int)(((long long)a.E * G::NGF + 127) / 128);
   if (a.Ja)
-    k_hdg_jacobian<P, KC, true><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+    k_hdg_jacobian<P, KC, true><<<ge + gf, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, ge);
   else
-    k_hdg_jacobian<P, KC, false><<<grid, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv);
+    k_hdg_jacobian<P, KC, false><<<ge + gf, 128, 0, st>>>(a, U, Uh, gamma, K, C, Dm, A33, Rv, hv, ge);
   return cudaGetLastError();
 }
 
