@@ -386,8 +386,16 @@ void profile_collect(dgx_handle* h) {
 }
 
 struct Layout {
-  size_t TU, FF, G, Q, Y, K, SH, TUb, JB, Qb, NU, LAM, HA, GB, GP, total;
+  size_t TU, FF, G, Q, Y, K, SH, TUb, JB, Qb, NU, LAM, HA, GB, GP, TQ, total;
 };
+
+// FP64 viscous LLF/BR1 handles keep the face traces of Q from the forward BR1
+// kernel for the adjoint (in the VJP workspace and in each stage checkpoint):
+// the adjoint then reads them instead of tracing Q again, which saves FP64
+// arithmetic on an FP64-bound path for 3 state vectors of writes (at p = 5 in
+// 3D the traces are as large as Q).  FP32 handles trace Q again: there the
+// extra writes would cost more than the arithmetic.
+bool keep_tq(const dgx_handle* h) { return h->fp64 && h->viscous && !h->dgip; }
 
 // DG-IP scheme: TU, FF (+ G, HA viscous); the VJP adds TUb (+ Gb) and the
 // element-local part of g; the ARK step adds Y, k_0..k_{s-2} and the FP32 shadow.
@@ -488,6 +496,10 @@ Layout layout(const dgx_handle* h, int op) {
       L.Qb = off;
       off += align256(state * h->d);
     }
+    if (op == DGX_OP_VJP && keep_tq(h)) {  // the recomputed forward's traces of Q
+      L.TQ = off;
+      off += align256(face * h->d);
+    }
   }
   if (op == DGX_OP_ARK_ADJOINT) {
     L.NU = off;
@@ -511,9 +523,9 @@ Layout layout(const dgx_handle* h, int op) {
   return L;
 }
 
-// Stage-checkpoint slot: y_i | TU_i | Q_i (viscous).
+// Stage-checkpoint slot: y_i | TU_i | Q_i (viscous) | traces of Q_i (FP64 viscous).
 struct Slot {
-  size_t y, TU, Q, bytes;
+  size_t y, TU, Q, TQ, bytes;
 };
 
 Slot slot_layout(const dgx_handle* h) {
@@ -528,7 +540,8 @@ Slot slot_layout(const dgx_handle* h) {
   }
   S.TU = align256(state);
   S.Q = S.TU + align256(face);
-  S.bytes = S.Q + (h->viscous ? align256(state * h->d) : 0);
+  S.TQ = S.Q + (h->viscous ? align256(state * h->d) : 0);
+  S.bytes = S.TQ + (keep_tq(h) ? align256(face * h->d) : 0);
   return S;
 }
 
@@ -552,6 +565,7 @@ dgx::VjpWork vjp_work_at(const dgx_handle* h, void* ws, const Layout& L) {
   w.TUb = b + L.TUb;
   w.JB = h->viscous ? b + L.JB : nullptr;
   w.Qb = h->viscous ? b + L.Qb : nullptr;
+  w.TQ = keep_tq(h) && L.TQ ? b + L.TQ : nullptr;
   return w;
 }
 
@@ -568,7 +582,7 @@ cudaError_t vjp_chain(dgx_handle* h, const void* U, const dgx::Cot<S>& cot, cons
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Table* t = h->tab;
   const dgx::VjpTable* v = (const dgx::VjpTable*)t->vjp;
-  dgx::Work w{vw.TU, vw.FFb, vw.G, vw.Q};
+  dgx::Work w{vw.TU, vw.FFb, vw.G, vw.Q, vw.TQ};
   cudaError_t err = cudaSuccess;
   if (!have_forward) {  // recompute the forward traces and BR1 gradient
     err = launch(h, DGX_K_TRACE, st, [&] { return t->trace(M, h->var[DGX_K_TRACE], U, w.TU, st); });
@@ -603,6 +617,7 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
   auto slot_y = [&](int i) { return (S*)(ck + SL.bytes * i + SL.y); };
   auto slot_tu = [&](int i) { return (void*)(ck + SL.bytes * i + SL.TU); };
   auto slot_q = [&](int i) { return (void*)(ck + SL.bytes * i + SL.Q); };
+  auto slot_tq = [&](int i) { return keep_tq(h) ? (void*)(ck + SL.bytes * i + SL.TQ) : nullptr; };
   S* first = ck ? slot_y(0) : shadow;  // where the rounded (or copied) U_n goes
   dgx::Work w0 = w;
   if (ck) w0.TU = slot_tu(0);
@@ -636,6 +651,7 @@ dgx_status ark_impl(dgx_handle* h, double* U64, double dt, void* stages, void* w
     if (ck) {
       wi.TU = slot_tu(i);
       wi.Q = h->viscous ? slot_q(i) : nullptr;
+      wi.TQ = slot_tq(i);
     }
     sa.TU = (S*)((ck && !sa.last) ? slot_tu(i + 1) : w.TU);
     const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
@@ -684,6 +700,7 @@ dgx_status ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam64, do
     const void* y = slot + SL.y;
     vw.TU = (void*)(slot + SL.TU);
     vw.Q = h->viscous ? (void*)(slot + SL.Q) : nullptr;
+    vw.TQ = keep_tq(h) ? (void*)(slot + SL.TQ) : nullptr;
     dgx::Cot<S> cot{}, fin{};
     if (h->fp64) {
       cot.lam64 = lam64;
@@ -1163,6 +1180,8 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       flops = E * (NF * nfp * nf * 2 + N * D * nf * 2 * n + N * D * nf * (c ? (8 * D + 1) : 5) +
                    NF * nfp * D * nf * 2 * n + NF * nfp * pc.visc_n);
       bytes = E * ((STATE + 2 * FACE + D * STATE + FACE) * s + geo_node + geo_face);
+      // FP64 stage checkpoints and VJPs: the traces of Q are also written
+      if (keep_tq(h)) bytes += E * D * FACE * s;
       break;
     case DGX_K_FACE:
       flops = F * nfp * ((c ? pc.llf_area : pc.llf_unit) + (v ? 3 * nf : 0));
@@ -1224,6 +1243,10 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
                    N * nf * D * 2 * n + NF * nfp * nf * (c ? D * (2 * n + 2) : 2 * n + 1) + NF * nfp * nf * 4);
       // face arrays: TU, both sides' Fhat_bar, TU_bar read and written, JB written
       bytes = E * ((6 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);
+      if (keep_tq(h)) {  // the stored traces of Q replace Q and its tracing
+        flops -= E * NF * nfp * D * nf * 2 * n;
+        bytes += E * (D * FACE - D * STATE) * s;
+      }
       break;
     case DGX_K_DGIP_TRACE:  // traces; face gradients and own-face viscous fluxes
       flops = E * FACE * 2 * n + (v ? E * NF * nfp * (D * nf * 2 * n + pc.visc_n) : 0.0);

@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_trace(int E, const Sin
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool CURV, int V>
 __device__ __forceinline__ void br1_tile(int tile, unsigned char* smem_raw, const Mesh<S>& M, const S* __restrict__ U,
-                                         const S* __restrict__ TU, S* __restrict__ Q, S* __restrict__ G) {
+                                         const S* __restrict__ TU, S* __restrict__ Q, S* __restrict__ G,
+                                         S* __restrict__ TQg = nullptr) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
@@ -493,6 +494,11 @@ __device__ __forceinline__ void br1_tile(int tile, unsigned char* smem_raw, cons
     }
   }
   g_sync<V>();
+  if (TQg) {  // keep the traces of Q for the adjoint (the tile's block is contiguous)
+    constexpr int TQS = NF * D * nf * nfp;
+    S* dst = TQg + (size_t)e0 * TQS;
+    for (int i = g_tid<V>(); i < nel * TQS; i += g_size<V>()) dst[i] = tq[i];
+  }
   // own-face viscous fluxes
   auto flux_at = [&](int i, const S (&UL)[nf], int nbe) {
     const int fp = i % nfp;
@@ -536,9 +542,9 @@ __device__ __forceinline__ void br1_tile(int tile, unsigned char* smem_raw, cons
 template <int D, int P, typename S, bool CURV, int V>
 __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_br1(Mesh<S> M, const S* __restrict__ U,
                                                               const S* __restrict__ TU, S* __restrict__ Q,
-                                                              S* __restrict__ G) {
+                                                              S* __restrict__ G, S* __restrict__ TQ) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  br1_tile<D, P, S, CURV, V>(g_index<V>(), smem_raw, M, U, TU, Q, G);
+  br1_tile<D, P, S, CURV, V>(g_index<V>(), smem_raw, M, U, TU, Q, G, TQ);
 }
 
 // ---------------------------------------------------------------------------

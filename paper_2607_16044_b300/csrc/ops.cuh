@@ -19,6 +19,7 @@ struct Work {            // caller-owned scratch, in the handle's precision
   void* FF;              // [E][2D][nf][nfp]
   void* G;               // [E][2D][nf][nfp]   (viscous)
   void* Q;               // [E][D][nf][N]      (viscous)
+  void* TQ = nullptr;    // [E][2D][D][nf][nfp] traces of Q, stored by k_br1 when set (FP64 stage checkpoints)
 };
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;  // opt-in shared memory per CTA on sm_103a
@@ -106,7 +107,7 @@ struct Ops {
     static SmemGate done;
     auto k = k_br1<D, P, S, CURV, V>;
     if (const cudaError_t e = allow_smem_once(k, smem_br1<V>(), done)) return e;
-    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, U, (const S*)w.TU, (S*)w.Q, (S*)w.G);
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, U, (const S*)w.TU, (S*)w.Q, (S*)w.G, (S*)w.TQ);
     return cudaGetLastError();
   }
   static cudaError_t br1(const Mesh<S>& M, int V, bool curv, const S* U, const Work& w, cudaStream_t st) {

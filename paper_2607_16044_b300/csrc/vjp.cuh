@@ -34,6 +34,8 @@ struct VjpWork {
               // [E][2D][nf][nfp] at (e, face, fp) holds the cotangent of the jump seen by the
               // neighbour across that face (zero on walls)
   void* Qb;   // gradient cotangents              [E][D][nf][N]
+  void* TQ;   // forward traces of Q [E][2D][D][nf][nfp] when the forward stored them (else nullptr:
+              // k_vjp_br1 traces Q itself)
 };
 
 // Element strides (in scalars) of k_vjp_elem's [T][nf][N] cotangent tile and
@@ -369,7 +371,8 @@ template <int D, int P, typename S, bool CURV, int V>
 __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, const S* __restrict__ TU,
                                                                   const S* __restrict__ Q, const S* __restrict__ FFb,
                                                                   S* __restrict__ Qb, S* __restrict__ TUb,
-                                                                  S* __restrict__ JB, S* __restrict__ Ub) {
+                                                                  S* __restrict__ JB, S* __restrict__ Ub,
+                                                                  const S* __restrict__ TQg) {
   using H = Sh<D, P, V>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T;
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
@@ -425,18 +428,23 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   // Q_bar: curvilinear meshes combine its components node by node (staged
   // tile); on boxes each line of Q_bar_b is read once, from global memory
   if (CURV) stage_nodes<D, P, S, V, D * nf>(qbs, Qb + (size_t)e0 * D * H::STATE, nel);
-  // 0. traces of Q (the forward Q is needed only here).  2D: each line read
-  //    straight from global memory (every value is read twice); 3D: every
-  //    value is read three times, so Q is staged once into qs (scratch for
-  //    the later phases) and the lines are read from there.
+  // 0. traces of Q (the forward Q is needed only here): copied when the
+  //    forward stored them (TQg), else traced.  2D: each line read straight
+  //    from global memory (every value is read twice); 3D: every value is
+  //    read three times, so Q is staged once into qs (scratch for the later
+  //    phases) and the lines are read from there.
   const S* qsrc = Q + (size_t)e0 * D * H::STATE;
-  if (D == 3) {
+  if (TQg) {
+    const S* src = TQg + (size_t)e0 * TQS;
+    for (int i = g_tid<V>(); i < nel * TQS; i += g_size<V>()) tq[i] = src[i];
+  } else if (D == 3) {
     stage_nodes<D, P, S, V, D * nf>(qs, qsrc, nel);
     g_sync<V>();
     qsrc = qs;
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
+    if (TQg) break;
     for (int i = g_tid<V>(); i < nel * D * nf * nfp; i += g_size<V>()) {
       const int line = i % nfp;
       const int f = (i / nfp) % nf;
@@ -867,7 +875,7 @@ struct VjpOps {
     auto k = k_vjp_br1<D, P, S, CURV, V>;
     if (const cudaError_t e = allow_smem_once(k, smem_br1<V>(), done)) return e;
     k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.FFb,
-                                                             (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub);
+                                                             (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub, (const S*)w.TQ);
     return cudaGetLastError();
   }
   static cudaError_t br1(const Mesh<S>& M, int V, bool curv, const VjpWork& w, S* Ub, cudaStream_t st) {
