@@ -445,8 +445,8 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 # element tile): 1,832,997,888 B x 110,592 / 16,384.  Summary and command in
 # profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
 # sources hash to `sources`.
-NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12385279296,
-               "sources": "eda6630d686e4c94ad57ec0a247c6a511bf50edb17867f51fb4d125222265e16"}
+NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12392243136,
+               "sources": "0a14cd6cc484d08ffcd9b451ad9c43240e8540f757d3c390a4d2b545c09f2884"}
 
 
 def sources_hash(root_header="vjp.cuh"):

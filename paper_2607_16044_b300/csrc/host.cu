@@ -1075,7 +1075,7 @@ void oi_matrices(dgx_handle* h) {
 // ------------------------------------------------------------ work model
 struct Pointwise {
   double conv, visc, visc_n, wall_visc, llf_unit, llf_area, conv_vjp, visc_vjp, visc_n_vjp, llf_unit_vjp,
-      llf_area_vjp, dgip_face, dgip_face_euler, dgip_face_vjp, dgip_face_euler_vjp;
+      llf_area_vjp, dgip_face, dgip_face_euler, dgip_face_vjp, dgip_face_euler_vjp, visc_n_axis, visc_n_axis_vjp;
 };
 
 template <int D>
@@ -1111,12 +1111,14 @@ Pointwise count_pointwise() {
   pc.conv = cnt([&] { dgx::conv_flux_all<D, C>(U, g, Fo); });
   pc.visc = cnt([&] { dgx::visc_flux_all<D, C>(U, Q, g, Fo); });
   pc.visc_n = cnt([&] { dgx::visc_flux_normal<D, C>(U, Q, nv, g, Go); });
+  pc.visc_n_axis = cnt([&] { dgx::visc_flux_axis<D, 0, C>(U, Q, C(1.0), g, Go); });
   pc.wall_visc = cnt([&] { dgx::wall_visc_flux<D, C>(U, Q, nv, g, Go); });
   pc.llf_unit = cnt([&] { dgx::llf_flux<D, C, true>(U, V, nv, g, Go); });
   pc.llf_area = cnt([&] { dgx::llf_flux<D, C, false>(U, V, nv, g, Go); });
   pc.conv_vjp = cnt([&] { dgx::conv_flux_all_vjp<D, C>(U, F, g, Ub); });
   pc.visc_vjp = cnt([&] { dgx::visc_flux_all_vjp<D, C>(U, Q, F, g, Ub, Qb); });
   pc.visc_n_vjp = cnt([&] { dgx::visc_flux_normal_vjp<D, C>(U, Q, nv, G, g, Ub, Qb); });
+  pc.visc_n_axis_vjp = cnt([&] { dgx::visc_flux_axis_vjp<D, 0, C>(U, Q, C(1.0), G, g, Ub, Qb); });
   pc.llf_unit_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, true>(U, V, nv, G, g, Ub, Vb); });
   pc.llf_area_vjp = cnt([&] { dgx::llf_flux_vjp<D, C, false>(U, V, nv, G, g, Ub, Vb); });
   {  // DG-IP face function (interior face point), forward and its dual-number adjoint
@@ -1178,7 +1180,7 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       break;
     case DGX_K_BR1:
       flops = E * (NF * nfp * nf * 2 + N * D * nf * 2 * n + N * D * nf * (c ? (8 * D + 1) : 5) +
-                   NF * nfp * D * nf * 2 * n + NF * nfp * pc.visc_n);
+                   NF * nfp * D * nf * 2 * n + NF * nfp * (c ? pc.visc_n : pc.visc_n_axis));
       bytes = E * ((STATE + 2 * FACE + D * STATE + FACE) * s + geo_node + geo_face);
       // FP64 stage checkpoints and VJPs: the traces of Q are also written
       if (keep_tq(h)) bytes += E * D * FACE * s;
@@ -1239,7 +1241,8 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       bytes = E * FACE * s * 3 + (c ? F * D * nfp * s : 0.0);
       break;
     case DGX_K_VJP_BR1:
-      flops = E * (NF * nfp * (D * nf * 2 * n + pc.visc_n_vjp) + N * D * nf * 4 * D + N * D * nf * (c ? 2 * D : 1) +
+      flops = E * (NF * nfp * (D * nf * 2 * n + (c ? pc.visc_n_vjp : pc.visc_n_axis_vjp)) + N * D * nf * 4 * D +
+                   N * D * nf * (c ? 2 * D : 1) +
                    N * nf * D * 2 * n + NF * nfp * nf * (c ? D * (2 * n + 2) : 2 * n + 1) + NF * nfp * nf * 4);
       // face arrays: TU, both sides' Fhat_bar, TU_bar read and written, JB written
       bytes = E * ((6 * FACE + 2 * D * STATE + 2 * STATE) * s + geo_node + geo_face);

@@ -519,10 +519,12 @@ __device__ __forceinline__ void br1_tile(int tile, unsigned char* smem_raw, cons
       for (int c = 0; c < D; ++c) nv[c] = (c == a) ? ((face & 1) ? S(1) : S(-1)) : S(0);
     }
     S Gv[nf];
-    if (nbe >= 0)
-      visc_flux_normal<D, S>(UL, TQ, nv, M.gas, Gv);
-    else
+    if (nbe < 0)
       wall_visc_flux<D, S>(UL, TQ, nv, M.gas, Gv);
+    else if (CURV)
+      visc_flux_normal<D, S>(UL, TQ, nv, M.gas, Gv);
+    else  // axis normal: the one row of the flux
+      visc_flux_axis_rt<D, S>(UL, TQ, a, (face & 1) ? S(1) : S(-1), M.gas, Gv);
     S* gd = G + ((size_t)e * NF + face) * nf * nfp + fp;
 #pragma unroll
     for (int f = 0; f < nf; ++f) gd[f * nfp] = Gv[f];

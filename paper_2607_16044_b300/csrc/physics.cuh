@@ -100,6 +100,55 @@ __host__ __device__ __forceinline__ void visc_flux_normal(const S (&U)[D + 2], c
   }
 }
 
+// The same through an axis normal, nv = sgn e_A (box faces normal to A):
+// G = sgn F^nu_A, the one row of the flux.  It needs the velocity gradients
+// of row A, of column A and of the diagonal (for div u) and the energy
+// gradient along A only, about half the arithmetic of the full flux.
+template <int D, int A, typename S>
+__host__ __device__ __forceinline__ void visc_flux_axis(const S (&U)[D + 2], const S (&Q)[D][D + 2], S sgn,
+                                                        const Gas<S>& g, S (&G)[D + 2]) {
+  const S ir = S(1) / U[0];
+  S u[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = U[1 + i] * ir;
+  const S Et = U[D + 1] * ir;
+  S row[D], col[D], s = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    row[j] = (Q[A][1 + j] - u[j] * Q[A][0]) * ir;  // d_A u_j
+    s += u[j] * row[j];
+  }
+  S div = row[A];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == A) {
+      col[j] = row[A];
+    } else {
+      col[j] = (Q[j][1 + A] - u[A] * Q[j][0]) * ir;  // d_j u_A
+      div += (Q[j][1 + j] - u[j] * Q[j][0]) * ir;    // d_j u_j
+    }
+  }
+  const S geA = (Q[A][D + 1] - Et * Q[A][0]) * ir - s;
+  G[0] = S(0);
+  S w = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const S tau = g.mu * (row[j] + col[j]) + (j == A ? g.lam * div : S(0));
+    G[1 + j] = sgn * tau;
+    w += tau * u[j];
+  }
+  G[D + 1] = sgn * (w + g.kcv * geA);
+}
+
+// visc_flux_axis with the axis A given at run time (0 .. D-1)
+template <int D, typename S>
+__host__ __device__ __forceinline__ void visc_flux_axis_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A, S sgn,
+                                                           const Gas<S>& g, S (&G)[D + 2]) {
+  if (A == 0) visc_flux_axis<D, 0, S>(U, Q, sgn, g, G);
+  else if (D == 2 || A == 1) visc_flux_axis<D, 1, S>(U, Q, sgn, g, G);
+  else visc_flux_axis<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, g, G);
+}
+
 // Adiabatic no-slip wall: F^nu(U_w, Q).nv with U_w = (rho, 0, rho e_i) and q.n = 0,
 // i.e. (0, tau(U_w, Q) nv, 0) where d_a u_i = Q[a][1+i] / rho.
 template <int D, typename S>
@@ -350,6 +399,117 @@ __host__ __device__ __forceinline__ void visc_flux_normal_vjp(const S (&U)[D + 2
 #pragma unroll
     for (int f = 0; f < D + 2; ++f) Fb[i][f] = Gb[f] * nv[i];
   visc_flux_all_vjp<D, S>(U, Q, Fb, g, Ub, Qb);
+}
+
+// Cotangent of visc_flux_axis: Gb -> (Ub, Qb), accumulated; the reverse of
+// its steps in the opposite order.
+template <int D, int A, typename S>
+__host__ __device__ __forceinline__ void visc_flux_axis_vjp(const S (&U)[D + 2], const S (&Q)[D][D + 2], S sgn,
+                                                            const S (&Gb)[D + 2], const Gas<S>& g, S (&Ub)[D + 2],
+                                                            S (&Qb)[D][D + 2]) {
+  const S ir = S(1) / U[0];
+  S u[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = U[1 + i] * ir;
+  const S Et = U[D + 1] * ir;
+  // forward values needed by the reverse
+  S nrow[D], ncol[D], ndia[D], row[D], col[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    nrow[j] = Q[A][1 + j] - u[j] * Q[A][0];
+    row[j] = nrow[j] * ir;
+  }
+  S div = row[A];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == A) {
+      ncol[j] = ndia[j] = S(0);
+      col[j] = row[A];
+    } else {
+      ncol[j] = Q[j][1 + A] - u[A] * Q[j][0];
+      col[j] = ncol[j] * ir;
+      ndia[j] = Q[j][1 + j] - u[j] * Q[j][0];
+      div += ndia[j] * ir;
+    }
+  }
+  const S ngeA = Q[A][D + 1] - Et * Q[A][0];
+  // G[D+1] = sgn (sum_j tau_j u_j + kcv geA),  G[1+j] = sgn tau_j
+  const S gE = sgn * Gb[D + 1];
+  S ub[D], rowb[D], colb[D], diab[D], divb = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    ub[j] = S(0);
+    rowb[j] = colb[j] = diab[j] = S(0);
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const S tau = g.mu * (row[j] + col[j]) + (j == A ? g.lam * div : S(0));
+    const S taub = sgn * Gb[1 + j] + gE * u[j];
+    ub[j] += gE * tau;
+    rowb[j] += g.mu * taub;
+    if (j == A) {
+      rowb[A] += g.mu * taub;  // col[A] is row[A]
+      divb += g.lam * taub;
+    } else {
+      colb[j] += g.mu * taub;
+    }
+  }
+  const S geAb = gE * g.kcv;
+  // div = row[A] + sum_{j != A} ndia[j] ir
+  rowb[A] += divb;
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    if (j != A) diab[j] += divb;
+  // geA = ngeA ir - sum_j u_j row_j
+  S irb = geAb * ngeA;
+  const S cge = geAb * ir;
+  Qb[A][D + 1] += cge;
+  Qb[A][0] -= Et * cge;
+  const S Etb = -Q[A][0] * cge;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    ub[j] -= geAb * row[j];
+    rowb[j] -= geAb * u[j];
+  }
+  // row_j = (Q[A][1+j] - u_j Q[A][0]) ir
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const S r = rowb[j] * ir;
+    Qb[A][1 + j] += r;
+    Qb[A][0] -= u[j] * r;
+    ub[j] -= Q[A][0] * r;
+    irb += rowb[j] * nrow[j];
+  }
+  // col_j = (Q[j][1+A] - u_A Q[j][0]) ir and dia_j = (Q[j][1+j] - u_j Q[j][0]) ir, j != A
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == A) continue;
+    const S rc = colb[j] * ir, rd = diab[j] * ir;
+    Qb[j][1 + A] += rc;
+    Qb[j][0] -= u[A] * rc + u[j] * rd;
+    ub[A] -= Q[j][0] * rc;
+    Qb[j][1 + j] += rd;
+    ub[j] -= Q[j][0] * rd;
+    irb += colb[j] * ncol[j] + diab[j] * ndia[j];
+  }
+  // u_i = U[1+i] ir, Et = U[D+1] ir, ir = 1 / U[0]
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Ub[1 + i] += ub[i] * ir;
+    irb += ub[i] * U[1 + i];
+  }
+  Ub[D + 1] += Etb * ir;
+  irb += Etb * U[D + 1];
+  Ub[0] -= irb * ir * ir;
+}
+
+template <int D, typename S>
+__host__ __device__ __forceinline__ void visc_flux_axis_vjp_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
+                                                               S sgn, const S (&Gb)[D + 2], const Gas<S>& g,
+                                                               S (&Ub)[D + 2], S (&Qb)[D][D + 2]) {
+  if (A == 0) visc_flux_axis_vjp<D, 0, S>(U, Q, sgn, Gb, g, Ub, Qb);
+  else if (D == 2 || A == 1) visc_flux_axis_vjp<D, 1, S>(U, Q, sgn, Gb, g, Ub, Qb);
+  else visc_flux_axis_vjp<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, Gb, g, Ub, Qb);
 }
 
 // Adiabatic wall flux (0, tau(U_w, Q) nv, 0), d_a u_i = Q[a][1+i] / rho.

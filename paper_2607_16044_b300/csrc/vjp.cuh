@@ -485,10 +485,12 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
 #pragma unroll
       for (int c = 0; c < D; ++c) nv[c] = (c == a) ? ((face & 1) ? S(1) : S(-1)) : S(0);
     }
-    if (nbe >= 0)
-      visc_flux_normal_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
-    else
+    if (nbe < 0)
       wall_visc_flux_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
+    else if (CURV)
+      visc_flux_normal_vjp<D, S>(UL, TQ, nv, gb, M.gas, ubf, tqbv);
+    else  // axis normal: the one row of the flux
+      visc_flux_axis_vjp_rt<D, S>(UL, TQ, a, (face & 1) ? S(1) : S(-1), gb, M.gas, ubf, tqbv);
 #pragma unroll
     for (int f = 0; f < nf; ++f) tub[((t * NF + face) * nf + f) * nfp + fp] = ubf[f];
 #pragma unroll
