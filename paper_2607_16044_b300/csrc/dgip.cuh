@@ -274,15 +274,20 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
       unit_normal<D, S>(face, nv);
     }
     const int nbk = M.nb[e * NF + face];
+    // boxes: the axis normal selects one row of the flux
+    auto vflux = [&](const S (&Us)[nf], const Gas<S>& gg) {
+      if (CURV) visc_flux_normal<D, S>(Us, Q, nv, gg, Gv);
+      else visc_flux_axis_rt<D, S>(Us, Q, face >> 1, (face & 1) ? S(1) : S(-1), gg, Gv);
+    };
     if (nbk >= 0) {
-      visc_flux_normal<D, S>(Uf, Q, nv, M.gas, Gv);
+      vflux(Uf, M.gas);
     } else if (nbk == -1) {
-      visc_flux_normal<D, S>(Uf, Q, nv, gw, Gv);
+      vflux(Uf, gw);
     } else {
       S Ui[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) Ui[f] = dp.Uinf[f];
-      visc_flux_normal<D, S>(Ui, Q, nv, M.gas, Gv);
+      vflux(Ui, M.gas);
     }
     S* gd = G + ((size_t)e * NF + face) * nf * nfp + fp;
 #pragma unroll
@@ -1078,10 +1083,15 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
         unit_normal<D, S>(face, nv);
       }
       const int nbk = M.nb[e * NF + face];
+      // boxes: the axis normal selects one row of the flux
+      auto vflux_vjp = [&](const S (&Us)[nf], const Gas<S>& gg, S (&Usb)[nf]) {
+        if (CURV) visc_flux_normal_vjp<D, S>(Us, Q, nv, Gbar, gg, Usb, Qb);
+        else visc_flux_axis_vjp_rt<D, S>(Us, Q, face >> 1, (face & 1) ? S(1) : S(-1), Gbar, gg, Usb, Qb);
+      };
       if (nbk >= 0) {
-        visc_flux_normal_vjp<D, S>(Uf, Q, nv, Gbar, M.gas, Ufb, Qb);
+        vflux_vjp(Uf, M.gas, Ufb);
       } else if (nbk == -1) {
-        visc_flux_normal_vjp<D, S>(Uf, Q, nv, Gbar, gw, Ufb, Qb);
+        vflux_vjp(Uf, gw, Ufb);
       } else {
         S Ui[nf], Uib[nf];
 #pragma unroll
@@ -1089,7 +1099,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
           Ui[f] = dp.Uinf[f];
           Uib[f] = S(0);
         }
-        visc_flux_normal_vjp<D, S>(Ui, Q, nv, Gbar, M.gas, Uib, Qb);
+        vflux_vjp(Ui, M.gas, Uib);
       }
       S* tb_ = tub + (t * NF + face) * nf * nfp + fp;
 #pragma unroll

@@ -1252,7 +1252,7 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       }
       break;
     case DGX_K_DGIP_TRACE:  // traces; face gradients and own-face viscous fluxes
-      flops = E * FACE * 2 * n + (v ? E * NF * nfp * (D * nf * 2 * n + pc.visc_n) : 0.0);
+      flops = E * FACE * 2 * n + (v ? E * NF * nfp * (D * nf * 2 * n + (c ? pc.visc_n : pc.visc_n_axis)) : 0.0);
       bytes = E * ((STATE + FACE + (v ? FACE : 0)) * s + D * s);
       break;
     case DGX_K_DGIP_FACE:  // both sides' traces and G read; FF and HA of both sides written
@@ -1275,7 +1275,9 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       break;
     case DGX_K_DGIP_VJP_GATHER:  // U, gpart, TUb (+ Gb) in, g out
       flops = E * (FACE * 2 * n + STATE * 2 * D +
-                   (v ? NF * nfp * (D * nf * 2 * n + pc.visc_n_vjp + (D - 1) * nf * 2 * n + 2 * n * nf) : 0));
+                   (v ? NF * nfp * (D * nf * 2 * n + (c ? pc.visc_n_vjp : pc.visc_n_axis_vjp) + (D - 1) * nf * 2 * n +
+                                    2 * n * nf)
+                      : 0));
       bytes = E * ((3 * STATE + FACE + (v ? FACE : 0)) * s + D * s);
       break;
     case DGX_K_VJP_GATHER:

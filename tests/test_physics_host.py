@@ -2,7 +2,6 @@
 with nvcc, no GPU): the axis-normal viscous flux that box faces use, and its
 hand-derived adjoint, against the full-tensor flux through the same normal."""
 import os
-import shutil
 import subprocess
 import tempfile
 
