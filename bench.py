@@ -445,8 +445,8 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 # element tile): 1,832,997,888 B x 110,592 / 16,384.  Summary and command in
 # profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
 # sources hash to `sources`.
-NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12392243136,
-               "sources": "0a14cd6cc484d08ffcd9b451ad9c43240e8540f757d3c390a4d2b545c09f2884"}
+NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12381368832,
+               "sources": "e7f29e81c6f4e20b8ade4bb9c41da0ab2f6bf7e0aa07e6d979d8e792fa6f1f6c"}
 
 
 def sources_hash(root_header="vjp.cuh"):

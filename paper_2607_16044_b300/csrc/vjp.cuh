@@ -60,11 +60,13 @@ constexpr size_t smem_velem_g() {
   using h = Sh<D, P, V>;
   return r16(sizeof(S) * (h::T * (vjp_mu_stride<D, P, V>() + vjp_fb_stride<D, P, V>()) + 2 * h::n));
 }
-template <int D, int P, typename S, int V>
+// k_vjp_br1's shared memory per element group: the Q_bar staging tile only on
+// curvilinear meshes (boxes read each Q_bar line straight from global memory)
+template <int D, int P, typename S, int V, bool CURV = true>
 constexpr size_t smem_vbr1_g() {
   using h = Sh<D, P, V>;
-  return r16(sizeof(S) * (2 * h::T * D * h::STATE + 2 * h::T * h::NF * D * h::nf * h::nfp + h::T * h::FACE +
-                          2 * h::n));
+  return r16(sizeof(S) * ((CURV ? 2 : 1) * h::T * D * h::STATE + 2 * h::T * h::NF * D * h::nf * h::nfp +
+                          h::T * h::FACE + 2 * h::n));
 }
 template <int D, int P, typename S, int V>
 constexpr size_t smem_vgather_g() {
@@ -378,9 +380,9 @@ __global__ void __launch_bounds__(Sh<D, P, V>::THREADS) k_vjp_br1(Mesh<S> M, con
   constexpr Tab1<S> tb = make_tab1<S>(P);  // compile-time 1D tables
   constexpr int TQS = NF * D * nf * nfp;      // traces of Q per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V>()));   // [T][D][nf][N]  dU_bar and D^T dU_bar
-  S* qbs = qs + T * D * H::STATE;            // [T][D][nf][N]  Q_bar (total), later P
-  S* tq = qbs + T * D * H::STATE;            // [T][NF][D][nf][nfp] traces of Q, later J_bar [T][NF][nf][nfp]
+  S* qs = reinterpret_cast<S*>(g_smem<V>(smem_raw, smem_vbr1_g<D, P, S, V, CURV>()));  // [T][D][nf][N]  dU_bar and D^T dU_bar
+  S* qbs = qs + T * D * H::STATE;            // [T][D][nf][N]  Q_bar (total), later P (curvilinear only)
+  S* tq = CURV ? qbs + T * D * H::STATE : qbs;  // [T][NF][D][nf][nfp] traces of Q, later J_bar [T][NF][nf][nfp]
   S* tqb = tq + T * TQS;                     // [T][NF][D][nf][nfp] TQ_bar
   S* tub = tqb + T * TQS;                    // [T][NF][nf][nfp] own TU_bar
   S* lm = tub + T * H::FACE;                 // node-indexed trace weights
@@ -800,9 +802,9 @@ struct VjpOps {
   static size_t smem_elem() {
     return H<V>::GROUPS * smem_velem_g<D, P, S, V>();
   }
-  template <int V>
+  template <int V, bool CURV = true>  // the curvilinear size bounds both
   static size_t smem_br1() {
-    return H<V>::GROUPS * smem_vbr1_g<D, P, S, V>();
+    return H<V>::GROUPS * smem_vbr1_g<D, P, S, V, CURV>();
   }
   template <int V>
   static size_t smem_gather() {
@@ -875,8 +877,8 @@ struct VjpOps {
   static cudaError_t br1_v(const Mesh<S>& M, const VjpWork& w, S* Ub, cudaStream_t st) {
     static SmemGate done;
     auto k = k_vjp_br1<D, P, S, CURV, V>;
-    if (const cudaError_t e = allow_smem_once(k, smem_br1<V>(), done)) return e;
-    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.FFb,
+    if (const cudaError_t e = allow_smem_once(k, smem_br1<V, CURV>(), done)) return e;
+    k<<<blocks<V>(M.E), H<V>::THREADS, smem_br1<V, CURV>(), st>>>(M, (const S*)w.TU, (const S*)w.Q, (const S*)w.FFb,
                                                              (S*)w.Qb, (S*)w.TUb, (S*)w.JB, Ub, (const S*)w.TQ);
     return cudaGetLastError();
   }
