@@ -74,8 +74,8 @@ def _rusanov_by_hand(UL, UR, Sn, gamma, d):
 
 @pytest.mark.parametrize("d", [2, 3])
 def test_llf_wave_speed_closed_form(d):
-    """The dissipation of the LLF flux (the convective face flux of the task's
-    reading of Sec. 3.3) is -lam/2 (UR - UL) with lam the larger of the two
+    """The dissipation of the LLF flux (the convective face flux of the LLF/BR1
+    scheme's reading of Sec. 3.3) is -lam/2 (UR - UL) with lam the larger of the two
     sides' |u.Sn| + c|Sn|, written out here from rho, u, p and gamma.  Fails
     for any other wave speed (e.g. lam scaled by a constant or taken from
     one side only)."""
