@@ -372,7 +372,8 @@ typedef enum {
   DGX_K_DGIP_VJP_GATHER = 14, /* DG-IP adjoint: traces and face gradients        */
   DGX_K_OI_TO_QUAD = 15,      /* over-integration: nodes -> M points (I, Pi^T)   */
   DGX_K_OI_TO_NODES = 16,     /* over-integration: M points -> nodes (Pi, I^T)   */
-  DGX_KERNEL_KINDS = 17
+  DGX_K_DGIP_VJP_TRACE = 17,  /* DG-IP adjoint: the traces of U alone            */
+  DGX_KERNEL_KINDS = 18
 } dgx_kernel_kind;
 
 /* Per-kernel device timing (tracing).  While enabled, every kernel the

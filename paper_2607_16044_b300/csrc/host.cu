@@ -57,7 +57,7 @@ struct dgx_handle {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // tile variant per kernel kind (autotuned; 1 = about 256 threads per CTA)
-  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
+  int var[DGX_KERNEL_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};  // 0..2: CTA tiles, 3: warp per element
   // per-kernel event profiler (tracing)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -756,7 +756,10 @@ cudaError_t dgip_vjp(dgx_handle* h, const void* U, const void* lam, void* g, con
   const void* M = h->fp64 ? (const void*)&h->mesh64 : (const void*)&h->mesh32;
   const dgx::Dgip<S> dp = dgip_params<S>(h, nullptr, nullptr);
   const dgx::DgipTable* t = h->dtab;
-  cudaError_t err = launch(h, DGX_K_DGIP_TRACE, st, [&] { return t->trace(M, &dp, h->viscous, U, w, st); });
+  // the adjoint needs the traces of U alone (its face kernel reads them; the
+  // gather recomputes the face gradients it needs): the trace kernel without
+  // its viscous part
+  cudaError_t err = launch(h, DGX_K_DGIP_VJP_TRACE, st, [&] { return t->trace(M, &dp, false, U, w, st); });
   if (err == cudaSuccess)
     err = launch(h, DGX_K_DGIP_VJP_ELEM, st, [&] { return t->vjp_elem(M, h->viscous, U, lam, w, st); });
   if (err == cudaSuccess)
@@ -1143,7 +1146,8 @@ Pointwise count_pointwise() {
 
 // Algorithmic flops and bytes of one launch of a kernel kind on this handle.
 void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
-  if (h->inner && kind >= DGX_K_DGIP_TRACE && kind <= DGX_K_DGIP_VJP_GATHER) {  // run at the M points
+  if (h->inner && ((kind >= DGX_K_DGIP_TRACE && kind <= DGX_K_DGIP_VJP_GATHER) || kind == DGX_K_DGIP_VJP_TRACE)) {
+    // run at the M points
     kernel_work(h->inner, kind, flops, bytes);
     return;
   }
@@ -1251,6 +1255,10 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
         bytes += E * (D * FACE - D * STATE) * s;
       }
       break;
+    case DGX_K_DGIP_VJP_TRACE:  // the traces alone
+      flops = E * FACE * 2 * n;
+      bytes = E * (STATE + FACE) * s;
+      break;
     case DGX_K_DGIP_TRACE:  // traces; face gradients and own-face viscous fluxes
       flops = E * FACE * 2 * n + (v ? E * NF * nfp * (D * nf * 2 * n + (c ? pc.visc_n : pc.visc_n_axis)) : 0.0);
       bytes = E * ((STATE + FACE + (v ? FACE : 0)) * s + D * s);
@@ -1331,7 +1339,7 @@ const char* dgx_kernel_name(int32_t kind) {
                                                 "elem_stage", "vjp_elem",      "vjp_face",      "vjp_br1",
                                                 "vjp_gather", "dgip_trace",    "dgip_face",     "dgip_elem",
                                                 "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather",
-                                                "oi_to_quad",    "oi_to_nodes"};
+                                                "oi_to_quad",    "oi_to_nodes",   "dgip_vjp_trace"};
   return (kind >= 0 && kind < DGX_KERNEL_KINDS) ? names[kind] : "unknown";
 }
 

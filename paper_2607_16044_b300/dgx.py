@@ -54,7 +54,7 @@ SCHEMES = {"llf-br1": (0, 0), "dgip": (1, 1)}   # (conv_flux, visc_flux)
 CONTRACTIONS = {"cuda_core": 0, "tf32": 1, "bf16": 2, "3xtf32": 3}
 KERNELS = ["trace", "br1", "face", "elem", "elem_stage", "vjp_elem", "vjp_face", "vjp_br1", "vjp_gather",
            "dgip_trace", "dgip_face", "dgip_elem", "dgip_vjp_elem", "dgip_vjp_face", "dgip_vjp_gather",
-           "oi_to_quad", "oi_to_nodes"]
+           "oi_to_quad", "oi_to_nodes", "dgip_vjp_trace"]
 
 
 def load_library(path: str = LIB_PATH):
