@@ -210,8 +210,9 @@ dgx_status dgx_ark_step(dgx_handle* h, double* U64, double dt, void* workspace, 
  * buffer holds s equal slots of dgx_stage_bytes / s bytes; slot i (0-based)
  * begins with the stage state y_{i+1} [E][nf][N] in the handle's precision,
  * followed (LLF/BR1 scheme) by that stage's face traces and (viscous) BR1
- * gradient, which the adjoint reuses instead of recomputing them; DG-IP slots
- * hold the stage state only. */
+ * gradient (FP64: also the gradient's face traces), which the adjoint reuses
+ * instead of recomputing them; DG-IP slots hold the stage state (FP64 viscous:
+ * also its face traces and face gradients, read by the adjoint). */
 size_t dgx_stage_bytes(const dgx_handle* h);
 
 /* The same step, also storing the stage states y_1..y_s it evaluates and their

@@ -208,7 +208,8 @@ __device__ __forceinline__ Gas<S> gas_no_heat(const Gas<S>& g) {
 // ---------------------------------------------------------------------------
 template <int D, int P, typename S, bool VISC, bool CURV>
 __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgip<S> dp, const S* __restrict__ U,
-                                                                  S* __restrict__ TU, S* __restrict__ G) {
+                                                                  S* __restrict__ TU, S* __restrict__ G,
+                                                                  S* __restrict__ QF) {
   using H = HD<D, P>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
                 FACE = H::FACE;
@@ -238,6 +239,11 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_trace(Mesh<S> M, Dgi
   __syncthreads();
   face_tangential<D, P, S, CURV>(tu, qf, M.geo.rh, e0, nel);
   __syncthreads();
+  if (QF) {  // keep the face gradients for the adjoint (the tile's block is contiguous)
+    constexpr int QS = NF * D * nf * nfp;
+    S* dst = QF + (size_t)e0 * QS;
+    for (int i = tid; i < nel * QS; i += blockDim.x) dst[i] = qf[i];
+  }
   const Gas<S> gw = gas_no_heat(M.gas);
   for (int i = tid; i < nel * NF * nfp; i += blockDim.x) {
     const int fp = i % nfp, face = (i / nfp) % NF, t = i / (nfp * NF);
@@ -998,7 +1004,9 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
                                                                        const S* __restrict__ TUb,
                                                                        const S* __restrict__ Gb,
                                                                        const S* __restrict__ gpart,
-                                                                       S* __restrict__ g) {
+                                                                       S* __restrict__ g,
+                                                                       const S* __restrict__ TUg,
+                                                                       const S* __restrict__ QFg) {
   using H = HD<D, P>;
   constexpr int n = H::n, N = H::N, nf = H::nf, nfp = H::nfp, NF = H::NF, T = H::T, STATE = H::STATE,
                 FACE = H::FACE;
@@ -1018,7 +1026,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
       const size_t off = (size_t)(e0 + t) * STATE + q;
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
-        us[t * STATE + f * N + q] = U[off + f * N];
+        if (!QFg) us[t * STATE + f * N + q] = U[off + f * N];
         ub[t * STATE + f * N + q] = gpart[off + f * N];
       }
     }
@@ -1033,10 +1041,19 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_gather(Mesh<S> M
   }
   __syncthreads();
   if (VISC) {
-    face_lines<D, P, S, true, CURV>(us, tu, qfb, M.geo.rh, e0, nel, nullptr);
-    __syncthreads();
-    face_tangential<D, P, S, CURV>(tu, qfb, M.geo.rh, e0, nel);
-    __syncthreads();
+    if (QFg) {  // the forward's traces and face gradients (stage checkpoints)
+      constexpr int QS = NF * D * nf * nfp;
+      const S* tsrc = TUg + (size_t)e0 * FACE;
+      const S* qsrc = QFg + (size_t)e0 * QS;
+      for (int i = tid; i < nel * FACE; i += blockDim.x) tu[i] = tsrc[i];
+      for (int i = tid; i < nel * QS; i += blockDim.x) qfb[i] = qsrc[i];
+      __syncthreads();
+    } else {
+      face_lines<D, P, S, true, CURV>(us, tu, qfb, M.geo.rh, e0, nel, nullptr);
+      __syncthreads();
+      face_tangential<D, P, S, CURV>(tu, qfb, M.geo.rh, e0, nel);
+      __syncthreads();
+    }
     const Gas<S> gw = gas_no_heat(M.gas);
     // adjoint of G at every own face point: its U_f part goes to the trace
     // cotangent (own entry), its gradient part replaces the gradient in qfb
@@ -1184,6 +1201,8 @@ struct DgipWork {       // caller-owned scratch, in the handle's precision
   void* TUb;            // VJP: trace cotangents
   void* Gb;             // VJP: cotangents of G
   void* gpart;          // VJP: element-local part of g [E][nf][N]
+  void* QF = nullptr;   // [E][2D][D][nf][nfp] face gradients: stored by the viscous trace kernel
+                        // when set, read by the gather instead of recomputing them (with TU)
 };
 
 template <int D, int P, typename S>
@@ -1200,7 +1219,7 @@ struct DgipOps {
     static SmemGate done;
     auto k = k_dgip_trace<D, P, S, VISC, CURV>;
     if (const cudaError_t e = allow_smem_once(k, smem_trace<VISC>(), done)) return e;
-    k<<<blocks(M.E), H::THREADS, smem_trace<VISC>(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G);
+    k<<<blocks(M.E), H::THREADS, smem_trace<VISC>(), st>>>(M, dp, U, (S*)w.TU, (S*)w.G, (S*)w.QF);
     return cudaGetLastError();
   }
   // curvilinear meshes are recognised by their face metric (dp.JaF)
@@ -1305,7 +1324,8 @@ struct DgipOps {
     auto k = k_dgip_vjp_gather<D, P, S, VISC, CURV>;
     constexpr size_t sm = smem_dgip_gather<D, P, S, VISC>();
     if (const cudaError_t e = allow_smem_once(k, sm, done)) return e;
-    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.TUb, (const S*)w.Gb, (const S*)w.gpart, g);
+    k<<<blocks(M.E), H::THREADS, sm, st>>>(M, dp, U, (const S*)w.TUb, (const S*)w.Gb, (const S*)w.gpart, g,
+                                           (const S*)w.TU, (const S*)w.QF);
     return cudaGetLastError();
   }
   static cudaError_t vjp_gather(const void* M, const void* dp, bool visc, const void* U, const DgipWork& w, void* g,

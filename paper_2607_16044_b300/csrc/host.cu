@@ -396,6 +396,7 @@ struct Layout {
 // 3D the traces are as large as Q).  FP32 handles trace Q again: there the
 // extra writes would cost more than the arithmetic.
 bool keep_tq(const dgx_handle* h) { return h->fp64 && h->viscous && !h->dgip; }
+bool keep_dgip_faces(const dgx_handle* h) { return h->fp64 && h->viscous && h->dgip && !h->inner; }
 
 // DG-IP scheme: TU, FF (+ G, HA viscous); the VJP adds TUb (+ Gb) and the
 // element-local part of g; the ARK step adds Y, k_0..k_{s-2} and the FP32 shadow.
@@ -523,9 +524,10 @@ Layout layout(const dgx_handle* h, int op) {
   return L;
 }
 
-// Stage-checkpoint slot: y_i | TU_i | Q_i (viscous) | traces of Q_i (FP64 viscous).
+// Stage-checkpoint slot: y_i | TU_i | Q_i (viscous) | traces of Q_i (FP64 viscous);
+// DG-IP: y_i (| TU_i | face gradients of y_i, viscous).
 struct Slot {
-  size_t y, TU, Q, TQ, bytes;
+  size_t y, TU, Q, TQ, QF, bytes;
 };
 
 Slot slot_layout(const dgx_handle* h) {
@@ -533,9 +535,19 @@ Slot slot_layout(const dgx_handle* h) {
   const size_t state = (size_t)h->E * h->nf * h->N * h->s;
   Slot S{};
   S.y = 0;
-  if (h->dgip) {  // the DG-IP adjoint recomputes traces from y_i: slots hold the stage states only
-    S.TU = S.Q = 0;
+  if (h->dgip) {
+    // FP64 viscous: the forward stage's traces and face gradients, which the
+    // adjoint's face and gather kernels read instead of recomputing them
+    // (FP64-bound arithmetic saved for bandwidth to spare; in FP32 the extra
+    // traffic cost more than it saved, and Euler and over-integrated handles
+    // keep the stage states only: their adjoint traces them again)
+    S.TU = S.Q = S.TQ = S.QF = 0;
     S.bytes = align256(state);
+    if (keep_dgip_faces(h)) {
+      S.TU = S.bytes;
+      S.QF = S.TU + align256(face);
+      S.bytes = S.QF + align256(face * h->d);
+    }
     return S;
   }
   S.TU = align256(state);
@@ -758,8 +770,10 @@ cudaError_t dgip_vjp(dgx_handle* h, const void* U, const void* lam, void* g, con
   const dgx::DgipTable* t = h->dtab;
   // the adjoint needs the traces of U alone (its face kernel reads them; the
   // gather recomputes the face gradients it needs): the trace kernel without
-  // its viscous part
-  cudaError_t err = launch(h, DGX_K_DGIP_VJP_TRACE, st, [&] { return t->trace(M, &dp, false, U, w, st); });
+  // its viscous part -- unless the stage checkpoint holds them (w.QF set:
+  // traces and face gradients of the forward stage, read in place)
+  cudaError_t err = cudaSuccess;
+  if (!w.QF) err = launch(h, DGX_K_DGIP_VJP_TRACE, st, [&] { return t->trace(M, &dp, false, U, w, st); });
   if (err == cudaSuccess)
     err = launch(h, DGX_K_DGIP_VJP_ELEM, st, [&] { return t->vjp_elem(M, h->viscous, U, lam, w, st); });
   if (err == cudaSuccess)
@@ -810,7 +824,12 @@ dgx_status dgip_ark_impl(dgx_handle* h, double* U64, double dt, void* stages, vo
     sa.Kout = sa.last ? nullptr : (S*)(base + L.K + state * i);
     sa.shadow = shadow;
     const S* Uin = (i == 0) ? y0 : (ck ? slot_y(i) : Y);
-    err = dgip_residual<S>(h, Uin, nullptr, nullptr, nullptr, w, &sa, st);
+    dgx::DgipWork wi = w;
+    if (ck && keep_dgip_faces(h)) {  // the stage's traces and face gradients go to its checkpoint
+      wi.TU = ck + SL.bytes * i + SL.TU;
+      wi.QF = ck + SL.bytes * i + SL.QF;
+    }
+    err = dgip_residual<S>(h, Uin, nullptr, nullptr, nullptr, wi, &sa, st);
   }
   return cuda_status(err);
 }
@@ -847,7 +866,12 @@ dgx_status dgip_ark_adjoint_impl(dgx_handle* h, const void* stages, double* lam6
     lc.out = mu;
     cudaError_t err = dgx::lincomb<S>(lc, st);
     const void* y = (const char*)stages + SL.bytes * i + SL.y;
-    if (err == cudaSuccess) err = dgip_vjp<S>(h, y, mu, NU(i), w, st);
+    dgx::DgipWork wi = w;
+    if (keep_dgip_faces(h)) {  // the forward stage's traces and face gradients, from its checkpoint
+      wi.TU = (char*)stages + SL.bytes * i + SL.TU;
+      wi.QF = (char*)stages + SL.bytes * i + SL.QF;
+    }
+    if (err == cudaSuccess) err = dgip_vjp<S>(h, y, mu, NU(i), wi, st);
     if (err != cudaSuccess) return DGX_ECUDA;
   }
   dgx::LinComb<S> fin{};
