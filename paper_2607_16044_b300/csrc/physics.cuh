@@ -140,13 +140,49 @@ __host__ __device__ __forceinline__ void visc_flux_axis(const S (&U)[D + 2], con
   G[D + 1] = sgn * (w + g.kcv * geA);
 }
 
-// visc_flux_axis with the axis A given at run time (0 .. D-1)
+// get(s) for the run-time shift s = A (0 .. D-1), each candidate formed with
+// s fixed at compile time and the result chosen by selects, not branches.
+template <int D, typename Get>
+__host__ __device__ __forceinline__ auto by_shift(int A, Get get) -> decltype(get(0)) {
+  if (D == 2) return A == 0 ? get(0) : get(1);
+  return A == 0 ? get(0) : (A == 1 ? get(1) : get(D > 2 ? 2 : 1));
+}
+
+// Axes relabelled i -> (i + A) mod D, so that axis A becomes axis 0.  The
+// viscous flux is isotropic (it commutes with every orthogonal change of
+// axes, permutations included), so the row along A of the original equals
+// the row along 0 of the relabelled state and gradient, its momentum
+// components relabelled back.
+template <int D, typename S>
+__host__ __device__ __forceinline__ void axis_relabel(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
+                                                      S (&Ur)[D + 2], S (&Qr)[D][D + 2]) {
+  Ur[0] = U[0];
+  Ur[D + 1] = U[D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) Ur[1 + i] = by_shift<D>(A, [&](int s) { return U[1 + (i + s) % D]; });
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    Qr[c][0] = by_shift<D>(A, [&](int s) { return Q[(c + s) % D][0]; });
+    Qr[c][D + 1] = by_shift<D>(A, [&](int s) { return Q[(c + s) % D][D + 1]; });
+#pragma unroll
+    for (int i = 0; i < D; ++i) Qr[c][1 + i] = by_shift<D>(A, [&](int s) { return Q[(c + s) % D][1 + (i + s) % D]; });
+  }
+}
+
+// visc_flux_axis with the axis A given at run time (0 .. D-1).  Lanes of one
+// warp often hold faces of different axes (a face's points do not fill whole
+// warps), so rather than branch to the instance for A, the state and gradient
+// are relabelled to put A first and the instance for axis 0 runs on every lane.
 template <int D, typename S>
 __host__ __device__ __forceinline__ void visc_flux_axis_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A, S sgn,
                                                            const Gas<S>& g, S (&G)[D + 2]) {
-  if (A == 0) visc_flux_axis<D, 0, S>(U, Q, sgn, g, G);
-  else if (D == 2 || A == 1) visc_flux_axis<D, 1, S>(U, Q, sgn, g, G);
-  else visc_flux_axis<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, g, G);
+  S Ur[D + 2], Qr[D][D + 2], Gr[D + 2];
+  axis_relabel<D, S>(U, Q, A, Ur, Qr);
+  visc_flux_axis<D, 0, S>(Ur, Qr, sgn, g, Gr);
+  G[0] = Gr[0];
+  G[D + 1] = Gr[D + 1];
+#pragma unroll
+  for (int j = 0; j < D; ++j) G[1 + j] = by_shift<D>(A, [&](int s) { return Gr[1 + (j + D - s) % D]; });
 }
 
 // Adiabatic no-slip wall: F^nu(U_w, Q).nv with U_w = (rho, 0, rho e_i) and q.n = 0,
@@ -507,9 +543,19 @@ template <int D, typename S>
 __host__ __device__ __forceinline__ void visc_flux_axis_vjp_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
                                                                S sgn, const S (&Gb)[D + 2], const Gas<S>& g,
                                                                S (&Ub)[D + 2], S (&Qb)[D][D + 2]) {
-  if (A == 0) visc_flux_axis_vjp<D, 0, S>(U, Q, sgn, Gb, g, Ub, Qb);
-  else if (D == 2 || A == 1) visc_flux_axis_vjp<D, 1, S>(U, Q, sgn, Gb, g, Ub, Qb);
-  else visc_flux_axis_vjp<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, Gb, g, Ub, Qb);
+  // the same relabelling as visc_flux_axis_rt; the accumulators are relabelled
+  // in and back out, so nothing is added beyond what the axis-0 adjoint adds
+  S Ur[D + 2], Qr[D][D + 2], Gbr[D + 2], Ubr[D + 2], Qbr[D][D + 2];
+  axis_relabel<D, S>(U, Q, A, Ur, Qr);
+  axis_relabel<D, S>(Ub, Qb, A, Ubr, Qbr);
+  Gbr[0] = Gb[0];
+  Gbr[D + 1] = Gb[D + 1];
+#pragma unroll
+  for (int i = 0; i < D; ++i) Gbr[1 + i] = by_shift<D>(A, [&](int s) { return Gb[1 + (i + s) % D]; });
+  visc_flux_axis_vjp<D, 0, S>(Ur, Qr, sgn, Gbr, g, Ubr, Qbr);
+  // inverse relabelling: shift by (D - A) mod D
+  const int Ai = (D - A) % D;
+  axis_relabel<D, S>(Ubr, Qbr, Ai, Ub, Qb);
 }
 
 // Adiabatic wall flux (0, tau(U_w, Q) nv, 0), d_a u_i = Q[a][1+i] / rho.
