@@ -442,11 +442,11 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 # headline's dominant kernel (k_vjp_br1, FP64) from one ncu capture of the same
 # step on the 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2),
 # scaled to the 48^3 launch by the element count (the kernel's traffic is per
-# element tile): 1,832,997,888 B x 110,592 / 16,384.  Summary and command in
+# element tile): 1,833,463,296 B x 110,592 / 16,384.  Summary and command in
 # profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
 # sources hash to `sources`.
-NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12381368832,
-               "sources": "e7f29e81c6f4e20b8ade4bb9c41da0ab2f6bf7e0aa07e6d979d8e792fa6f1f6c"}
+NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375877248,
+               "sources": "af369664ec0c4651e5cdb0a1b0c7b84fab0f2c0b8d340104fee33d13047585af"}
 
 
 def sources_hash(root_header="vjp.cuh"):
