@@ -189,10 +189,10 @@ __host__ __device__ __forceinline__ void vij_flux(const T (&UL)[D + 2], const T 
 #pragma unroll
   for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
   using ::sqrt;
-  const N sJ = sqrt(n2);
+  const N sJ = sqrt(n2), isJ = N(1) / sJ;
   N nh[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
   T Ub[nf], dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
@@ -220,10 +220,10 @@ __host__ __device__ __forceinline__ void farfield_state(const T (&U)[D + 2], con
 #pragma unroll
   for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
   using ::sqrt;
-  const N sJ = sqrt(n2);
+  const N sJ = sqrt(n2), isJ = N(1) / sJ;
   N nh[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
   T dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) dU[f] = U[f] - Ui[f];
@@ -374,10 +374,10 @@ __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D 
   S n2 = S(0);
 #pragma unroll
   for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
-  const S sJ = sqrt(n2);
+  const S sJ = sqrt(n2), isJ = S(1) / sJ;
   S nh[D];
 #pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] / sJ;
+  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
   S Ub[nf], dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
@@ -449,7 +449,7 @@ __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D 
   const S rdunb = c * (apb - amb) * i2c2;
   cb += rdun * (apb - amb) * i2c2;
   const S i2c2b = amb * (dp - c * rdun) + apb * (dp + c * rdun);
-  S c2b = -i2c2b * i2c2 / c2;
+  S c2b = -S(2) * i2c2b * i2c2 * i2c2;  // d(1/(2 c2)) = -2 (1/(2 c2))^2 dc2
   // rdun = ndm - un dU0
   const S ndmb = rdunb;
   unb -= dU[0] * rdunb;

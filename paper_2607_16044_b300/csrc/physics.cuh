@@ -674,9 +674,10 @@ __host__ __device__ __forceinline__ void llf_flux_vjp(const S (&UL)[D + 2], cons
     const S cb = sideLam * sJ;
     // c = sqrt(gamma p ir)
     S pb = 0, irb = 0;
-    if (c > S(0)) {
-      pb += cb * g.gamma * ir / (S(2) * c);
-      irb += cb * g.gamma * p / (S(2) * c);
+    if (c > S(0)) {  // dc = gamma (ir dp + p dir) / (2 c), one division for both
+      const S h2c = cb * g.gamma / (S(2) * c);
+      pb += h2c * ir;
+      irb += h2c * p;
     }
     // Fn = (m.n, m_j un + p n_j, (E + p) un) with cotangent Fb/2
     S mb[D];
