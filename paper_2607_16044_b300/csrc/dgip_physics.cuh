@@ -137,6 +137,26 @@ __host__ __device__ __forceinline__ void conv_flux_normal(const T (&U)[D + 2], c
   F[D + 1] = (U[D + 1] + p) * un;
 }
 
+// |nv| and the unit normal nv / |nv| (one reciprocal); UNIT: nv is a unit
+// vector already (box faces) and is taken as it is.
+template <int D, typename N, bool UNIT>
+__host__ __device__ __forceinline__ void unit_of(const N (&nv)[D], N& sJ, N (&nh)[D]) {
+  if (UNIT) {
+    sJ = N(1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nv[i];
+  } else {
+    using ::sqrt;
+    N n2 = N(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
+    sJ = sqrt(n2);
+    const N isJ = N(1) / sJ;
+#pragma unroll
+    for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
+  }
+}
+
 // Characteristic quantities of a state along the unit normal nh and the two
 // acoustic wave strengths of a jump dU (see the header comment).
 template <int D, typename T, typename N>
@@ -181,18 +201,13 @@ struct Waves {
 };
 
 // Vijayasundaram flux through the area normal nv (own side UL outward).
-template <int D, typename T, typename N>
+// UNIT: nv is known to be a unit vector (box faces), so |nv| is not formed.
+template <int D, typename T, typename N, bool UNIT = false>
 __host__ __device__ __forceinline__ void vij_flux(const T (&UL)[D + 2], const T (&UR)[D + 2], const N (&nv)[D],
                                                   const Gas<T>& g, T (&F)[D + 2]) {
   constexpr int nf = D + 2;
-  N n2 = N(0);
-#pragma unroll
-  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
-  using ::sqrt;
-  const N sJ = sqrt(n2), isJ = N(1) / sJ;
-  N nh[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
+  N sJ = N(1), nh[D];
+  unit_of<D, N, UNIT>(nv, sJ, nh);
   T Ub[nf], dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
@@ -212,18 +227,12 @@ __host__ __device__ __forceinline__ void vij_flux(const T (&UL)[D + 2], const T 
 }
 
 // Farfield boundary state U_Gamma (App. B.1.1) for the area normal nv.
-template <int D, typename T, typename N>
+template <int D, typename T, typename N, bool UNIT = false>
 __host__ __device__ __forceinline__ void farfield_state(const T (&U)[D + 2], const T (&Ui)[D + 2], const N (&nv)[D],
                                                         const Gas<T>& g, T (&UG)[D + 2]) {
   constexpr int nf = D + 2;
-  N n2 = N(0);
-#pragma unroll
-  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
-  using ::sqrt;
-  const N sJ = sqrt(n2), isJ = N(1) / sJ;
-  N nh[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
+  N sJ = N(1), nh[D];
+  unit_of<D, N, UNIT>(nv, sJ, nh);
   T dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) dU[f] = U[f] - Ui[f];
@@ -255,6 +264,162 @@ __host__ __device__ __forceinline__ void k_product(const T (&U)[D + 2], const T 
   visc_flux_all<D, T>(U, Q, g, K);
 }
 
+// The axis A and sign s of a box normal nv = s e_A (its other components are
+// exactly zero), chosen by selects.
+template <int D, typename N>
+__host__ __device__ __forceinline__ int axis_of(const N (&nv)[D]) {
+  int A = 0;
+#pragma unroll
+  for (int i = 1; i < D; ++i) A = nv[i] != N(0) ? i : A;
+  return A;
+}
+
+// K(U)(delta (x) nv) for the axis normal nv = s e_0: the gradient n (x) delta
+// has one non-zero row, d_0 u_i = s (delta_{1+i} - u_i delta_0) / rho =: d_i,
+// so div u = d_0, tau = mu (d e_0^T + e_0 d^T) + lambda d_0 I, and the energy
+// gradient is non-zero along 0 only.  About a quarter of the arithmetic of
+// the full flux at a general gradient.
+template <int D, typename T>
+__host__ __device__ __forceinline__ void k_product_axis0(const T (&U)[D + 2], const T (&delta)[D + 2], T s,
+                                                         const Gas<T>& g, T (&K)[D][D + 2]) {
+  const T ir = T(1) / U[0];
+  T u[D], d[D], ud = T(0);
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = U[1 + i] * ir;
+  const T Et = U[D + 1] * ir;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    d[i] = s * (delta[1 + i] - u[i] * delta[0]) * ir;
+    ud += u[i] * d[i];
+  }
+  const T ge = s * (delta[D + 1] - Et * delta[0]) * ir - ud;
+  const T t00 = g.mu * (d[0] + d[0]) + g.lam * d[0];
+  K[0][0] = T(0);
+  K[0][1] = t00;
+  T w = t00 * u[0];
+#pragma unroll
+  for (int j = 1; j < D; ++j) {
+    const T t = g.mu * d[j];
+    K[0][1 + j] = t;
+    w += t * u[j];
+  }
+  K[0][D + 1] = w + g.kcv * ge;
+  const T ld = g.lam * d[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    const T t = g.mu * d[i];
+    K[i][0] = T(0);
+    K[i][1] = t;
+#pragma unroll
+    for (int j = 1; j < D; ++j) K[i][1 + j] = j == i ? ld : T(0);
+    K[i][D + 1] = t * u[0] + ld * u[i];
+  }
+}
+
+// k_product for a box normal nv = s e_A given at run time: the axes are
+// relabelled so that A becomes 0 (selects, no branches), k_product_axis0 is
+// applied and the result is relabelled back.
+template <int D, typename T, typename N>
+__host__ __device__ __forceinline__ void k_product_axis(const T (&U)[D + 2], const T (&delta)[D + 2], const N (&nv)[D],
+                                                        const Gas<T>& g, T (&K)[D][D + 2]) {
+  const int A = axis_of<D, N>(nv);
+  const T s = T(by_shift<D>(A, [&](int k) { return nv[k]; }));
+  T Ur[D + 2], dr[D + 2], Kr[D][D + 2];
+  relabel_state<D, T>(U, A, Ur);
+  relabel_state<D, T>(delta, A, dr);
+  k_product_axis0<D, T>(Ur, dr, s, g, Kr);
+  relabel_grad<D, T>(Kr, (D - A) % D, K);
+}
+
+// Cotangent of k_product_axis0: Kb -> Ub, deltab (accumulated), the reverse
+// of its steps.
+template <int D, typename S>
+__host__ __device__ __forceinline__ void k_product_axis0_vjp(const S (&U)[D + 2], const S (&delta)[D + 2], S s,
+                                                             const S (&Kb)[D][D + 2], const Gas<S>& g,
+                                                             S (&Ub)[D + 2], S (&deltab)[D + 2]) {
+  const S ir = S(1) / U[0];
+  S u[D], nd[D], d[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = U[1 + i] * ir;
+  const S Et = U[D + 1] * ir;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    nd[i] = s * (delta[1 + i] - u[i] * delta[0]);
+    d[i] = nd[i] * ir;
+  }
+  const S nge = s * (delta[D + 1] - Et * delta[0]);
+  const S t00 = g.mu * (d[0] + d[0]) + g.lam * d[0];
+  // K[0][1] = t00, K[0][1+j] = mu d_j, K[0][D+1] = t00 u_0 + sum_j mu d_j u_j + kcv ge,
+  // K[i][1] = mu d_i, K[i][1+i] = lam d_0, K[i][D+1] = mu d_i u_0 + lam d_0 u_i
+  const S e0 = Kb[0][D + 1];
+  const S geb = g.kcv * e0;
+  const S t00b = Kb[0][1] + e0 * u[0];
+  S db[D], ub[D];
+  ub[0] = e0 * t00;
+  db[0] = g.mu * (t00b + t00b) + g.lam * t00b;
+#pragma unroll
+  for (int j = 1; j < D; ++j) {
+    const S ej = Kb[j][D + 1];
+    db[j] = g.mu * (Kb[0][1 + j] + e0 * u[j] + Kb[j][1] + ej * u[0]);
+    ub[j] = g.mu * e0 * d[j] + g.lam * ej * d[0];
+    ub[0] += g.mu * ej * d[j];
+    db[0] += g.lam * (Kb[j][1 + j] + ej * u[j]);
+  }
+  // ge = nge ir - sum_i u_i d_i, nge = s (delta_E - Et delta_0)
+  S irb = geb * nge;
+  const S cg = geb * s * ir;
+  deltab[D + 1] += cg;
+  deltab[0] -= Et * cg;
+  const S Etb = -delta[0] * cg;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    ub[i] -= geb * d[i];
+    db[i] -= geb * u[i];
+  }
+  // d_i = nd_i ir, nd_i = s (delta_{1+i} - u_i delta_0)
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    irb += db[i] * nd[i];
+    const S rs = s * db[i] * ir;
+    deltab[1 + i] += rs;
+    deltab[0] -= u[i] * rs;
+    ub[i] -= delta[0] * rs;
+  }
+  // u_i = m_i ir, Et = E ir, ir = 1 / rho
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    Ub[1 + i] += ub[i] * ir;
+    irb += ub[i] * U[1 + i];
+  }
+  Ub[D + 1] += Etb * ir;
+  irb += Etb * U[D + 1];
+  Ub[0] -= irb * ir * ir;
+}
+
+// Cotangent of k_product_axis: Ub += (dK/dU)^T Kb, deltab += (dK/ddelta)^T Kb.
+template <int D, typename S>
+__host__ __device__ __forceinline__ void k_product_axis_vjp(const S (&U)[D + 2], const S (&delta)[D + 2],
+                                                            const S (&nv)[D], const S (&Kb)[D][D + 2],
+                                                            const Gas<S>& g, S (&Ub)[D + 2], S (&deltab)[D + 2]) {
+  constexpr int nf = D + 2;
+  const int A = axis_of<D, S>(nv);
+  const S s = by_shift<D>(A, [&](int k) { return nv[k]; });
+  S Ur[nf], dr[nf], Kbr[D][nf], Ubr[nf], dbr[nf], t[nf];
+  relabel_state<D, S>(U, A, Ur);
+  relabel_state<D, S>(delta, A, dr);
+  relabel_grad<D, S>(Kb, A, Kbr);
+#pragma unroll
+  for (int f = 0; f < nf; ++f) Ubr[f] = dbr[f] = S(0);
+  k_product_axis0_vjp<D, S>(Ur, dr, s, Kbr, g, Ubr, dbr);
+  const int Ai = (D - A) % D;
+  relabel_state<D, S>(Ubr, Ai, t);
+#pragma unroll
+  for (int f = 0; f < nf; ++f) Ub[f] += t[f];
+  relabel_state<D, S>(dbr, Ai, t);
+#pragma unroll
+  for (int f = 0; f < nf; ++f) deltab[f] += t[f];
+}
+
 // Mirror state (rho, m - 2 (m.n) n, rho E) for a normal of another scalar type.
 template <int D, typename T, typename N>
 __host__ __device__ __forceinline__ void mirror_state_n(const T (&U)[D + 2], const N (&nv)[D], T (&R)[D + 2]) {
@@ -284,21 +449,28 @@ enum { DGIP_INTERIOR = 0, DGIP_WALL = 1, DGIP_FARFIELD = 2 };
 //   wall:     F = Vij(UL, mirror(UL)) + tau K_w(UL)(dw (x) n).n / |n|, HL = K_w(UL)(dw (x) n),
 //   farfield: F = F^c(U_Gamma).n + tau K(U_inf)(di (x) n).n / |n|, HL = K(U_inf)(di (x) n),
 // delta = UL - UR, dw = UL - U_w(UL), di = UL - U_inf.  gw: the gas with kappa = 0.
-template <int D, typename T, typename N, bool VISC, int KIND>
+// AXIS: nv = +-e_A (box faces): unit normal, and the K-products take the
+// rank-one axis form.
+template <int D, typename T, typename N, bool VISC, int KIND, bool AXIS = false>
 __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], const T (&UR)[D + 2], const N (&nv)[D],
                                                       const Gas<T>& g, const Gas<T>& gw, N tau_over_s, bool ifL,
                                                       bool ifR, T (&F)[D + 2], T (&HL)[D][D + 2],
                                                       T (&HR)[D][D + 2]) {
   constexpr int nf = D + 2;
   if (KIND == DGIP_INTERIOR) {
-    vij_flux<D, T, N>(UL, UR, nv, g, F);
+    vij_flux<D, T, N, AXIS>(UL, UR, nv, g, F);
     if (VISC) {
       T dl[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) dl[f] = UL[f] - UR[f];
       T KL[D][nf], KR[D][nf];
-      k_product<D, T, N>(UL, dl, nv, g, KL);
-      k_product<D, T, N>(UR, dl, nv, g, KR);
+      if (AXIS) {
+        k_product_axis<D, T, N>(UL, dl, nv, g, KL);
+        k_product_axis<D, T, N>(UR, dl, nv, g, KR);
+      } else {
+        k_product<D, T, N>(UL, dl, nv, g, KL);
+        k_product<D, T, N>(UR, dl, nv, g, KR);
+      }
       const T h = T(0.5) * T(tau_over_s);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
@@ -319,13 +491,14 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
   } else if (KIND == DGIP_WALL) {
     T Um[nf];
     mirror_state_n<D, T, N>(UL, nv, Um);
-    vij_flux<D, T, N>(UL, Um, nv, g, F);
+    vij_flux<D, T, N, AXIS>(UL, Um, nv, g, F);
     if (VISC) {
       T Uw[nf], dw[nf];
       wall_state<D, T>(UL, Uw);
 #pragma unroll
       for (int f = 0; f < nf; ++f) dw[f] = UL[f] - Uw[f];
-      k_product<D, T, N>(UL, dw, nv, gw, HL);
+      if (AXIS) k_product_axis<D, T, N>(UL, dw, nv, gw, HL);
+      else k_product<D, T, N>(UL, dw, nv, gw, HL);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         T s = T(0);
@@ -336,13 +509,14 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
     }
   } else {  // farfield: UR holds U_inf
     T UG[nf];
-    farfield_state<D, T, N>(UL, UR, nv, g, UG);
+    farfield_state<D, T, N, AXIS>(UL, UR, nv, g, UG);
     conv_flux_normal<D, T, N>(UG, nv, g, F);
     if (VISC) {
       T di[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) di[f] = UL[f] - UR[f];
-      k_product<D, T, N>(UR, di, nv, g, HL);
+      if (AXIS) k_product_axis<D, T, N>(UR, di, nv, g, HL);
+      else k_product<D, T, N>(UR, di, nv, g, HL);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
         T s = T(0);
@@ -361,23 +535,17 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
 // Written statement by statement against vij_flux (F_n(Ubar) through
 // conv_flux_all_vjp, then the wave sum |A| dU / 2 reversed through the
 // characteristic quantities of Waves) and the K-products (visc_flux_all_vjp at
-// the rank-one gradient nv (x) delta).  d|x|/dx = sign(x), sign(0) = 0, as the
+// the rank-one gradient nv (x) delta; AXIS: k_product_axis_vjp).  d|x|/dx = sign(x), sign(0) = 0, as the
 // dual numbers take it.
-template <int D, typename S, bool VISC>
+template <int D, typename S, bool VISC, bool AXIS = false>
 __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2],
                                                                 const S (&nv)[D], const Gas<S>& g, S tau_over_s,
                                                                 bool ifL, bool ifR, const S (&Fb)[D + 2],
                                                                 const S (&HLb)[D][D + 2], const S (&HRb)[D][D + 2],
                                                                 S (&ULb)[D + 2], S (&URb)[D + 2]) {
   constexpr int nf = D + 2;
-  using ::sqrt;
-  S n2 = S(0);
-#pragma unroll
-  for (int i = 0; i < D; ++i) n2 += nv[i] * nv[i];
-  const S sJ = sqrt(n2), isJ = S(1) / sJ;
-  S nh[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) nh[i] = nv[i] * isJ;
+  S sJ = S(1), nh[D];
+  unit_of<D, S, AXIS>(nv, sJ, nh);
   S Ub[nf], dU[nf];
 #pragma unroll
   for (int f = 0; f < nf; ++f) {
@@ -501,7 +669,7 @@ __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D 
     // F += (tau / 2) sum_c (KL + KR)[c] nv_c; HL = KL / 2 (+ KR / 2 at an
     // interface), HR = KR / 2 (+ KL / 2); K(U) = F^nu(U, nv (x) delta)
     const S h = S(0.5) * tau_over_s;
-    S KLb[D][nf], KRb[D][nf], Q[D][nf], QLb[D][nf], QRb[D][nf];
+    S KLb[D][nf], KRb[D][nf];
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -509,19 +677,34 @@ __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D 
         const S fb = h * nv[a] * Fb[f];
         KLb[a][f] = fb + S(0.5) * HLb[a][f] + (ifR ? S(0.5) * HRb[a][f] : S(0));
         KRb[a][f] = fb + S(0.5) * HRb[a][f] + (ifL ? S(0.5) * HLb[a][f] : S(0));
-        Q[a][f] = nv[a] * dU[f];
-        QLb[a][f] = S(0);
-        QRb[a][f] = S(0);
       }
-    visc_flux_all_vjp<D, S>(UL, Q, KLb, g, ULb, QLb);
-    visc_flux_all_vjp<D, S>(UR, Q, KRb, g, URb, QRb);
+    S db[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) db[f] = S(0);
+    if constexpr (AXIS) {
+      k_product_axis_vjp<D, S>(UL, dU, nv, KLb, g, ULb, db);
+      k_product_axis_vjp<D, S>(UR, dU, nv, KRb, g, URb, db);
+    } else {
+      S Q[D][nf], QLb[D][nf], QRb[D][nf];
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int f = 0; f < nf; ++f) {
+          Q[a][f] = nv[a] * dU[f];
+          QLb[a][f] = S(0);
+          QRb[a][f] = S(0);
+        }
+      visc_flux_all_vjp<D, S>(UL, Q, KLb, g, ULb, QLb);
+      visc_flux_all_vjp<D, S>(UR, Q, KRb, g, URb, QRb);
+#pragma unroll
+      for (int f = 0; f < nf; ++f)
+#pragma unroll
+        for (int a = 0; a < D; ++a) db[f] += nv[a] * (QLb[a][f] + QRb[a][f]);
+    }
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
-      S db = S(0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) db += nv[a] * (QLb[a][f] + QRb[a][f]);
-      ULb[f] += db;
-      URb[f] -= db;
+      ULb[f] += db[f];
+      URb[f] -= db[f];
     }
   }
 }

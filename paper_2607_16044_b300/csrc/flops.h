@@ -33,6 +33,7 @@ inline Count& operator*=(Count& a, Count b) { a = a * b; return a; }
 inline bool operator>=(Count a, Count b) { return a.v >= b.v; }
 inline bool operator>(Count a, Count b) { return a.v > b.v; }
 inline bool operator<(Count a, Count b) { return a.v < b.v; }
+inline bool operator!=(Count a, Count b) { return a.v != b.v; }
 inline Count sqrt(Count a) { ++Count::ops; return Count(std::sqrt(a.v)); }
 inline Count fabs(Count a) { ++Count::ops; return Count(std::fabs(a.v)); }
 

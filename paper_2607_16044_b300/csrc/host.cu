@@ -1155,9 +1155,9 @@ Pointwise count_pointwise() {
       for (int a = 0; a < D; ++a) Hb[a][f] = 0.2;
     }
     const C tau = 10.0;
-    pc.dgip_face = cnt([&] { dgx::dgip_face_fn<D, C, C, true, dgx::DGIP_INTERIOR>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
+    pc.dgip_face = cnt([&] { dgx::dgip_face_fn<D, C, C, true, dgx::DGIP_INTERIOR, true>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
     pc.dgip_face_euler =
-        cnt([&] { dgx::dgip_face_fn<D, C, C, false, dgx::DGIP_INTERIOR>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
+        cnt([&] { dgx::dgip_face_fn<D, C, C, false, dgx::DGIP_INTERIOR, true>(U, V, nv, g, g, tau, false, false, Go, HL, HR); });
     pc.dgip_face_vjp = cnt([&] {
       dgx::dgip_face_fn_vjp_host<D, C, true>(U, V, nv, g, tau, Fb, Hb, Hb, Ub, Vb);
     });

@@ -154,12 +154,15 @@ __host__ __device__ __forceinline__ auto by_shift(int A, Get get) -> decltype(ge
 // the row along 0 of the relabelled state and gradient, its momentum
 // components relabelled back.
 template <int D, typename S>
-__host__ __device__ __forceinline__ void axis_relabel(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
-                                                      S (&Ur)[D + 2], S (&Qr)[D][D + 2]) {
+__host__ __device__ __forceinline__ void relabel_state(const S (&U)[D + 2], int A, S (&Ur)[D + 2]) {
   Ur[0] = U[0];
   Ur[D + 1] = U[D + 1];
 #pragma unroll
   for (int i = 0; i < D; ++i) Ur[1 + i] = by_shift<D>(A, [&](int s) { return U[1 + (i + s) % D]; });
+}
+// the same for a gradient-shaped array Q[c][f] (direction c, field f)
+template <int D, typename S>
+__host__ __device__ __forceinline__ void relabel_grad(const S (&Q)[D][D + 2], int A, S (&Qr)[D][D + 2]) {
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     Qr[c][0] = by_shift<D>(A, [&](int s) { return Q[(c + s) % D][0]; });
@@ -167,6 +170,12 @@ __host__ __device__ __forceinline__ void axis_relabel(const S (&U)[D + 2], const
 #pragma unroll
     for (int i = 0; i < D; ++i) Qr[c][1 + i] = by_shift<D>(A, [&](int s) { return Q[(c + s) % D][1 + (i + s) % D]; });
   }
+}
+template <int D, typename S>
+__host__ __device__ __forceinline__ void axis_relabel(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
+                                                      S (&Ur)[D + 2], S (&Qr)[D][D + 2]) {
+  relabel_state<D, S>(U, A, Ur);
+  relabel_grad<D, S>(Q, A, Qr);
 }
 
 // visc_flux_axis with the axis A given at run time (0 .. D-1).  Lanes of one
