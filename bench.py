@@ -439,14 +439,23 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# headline's dominant kernel (k_vjp_br1, FP64) from one ncu capture of the same
-# step on the 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2),
-# scaled to the 48^3 launch by the element count (the kernel's traffic is per
-# element tile): 1,833,463,296 B x 110,592 / 16,384.  Summary and command in
-# profiles/k_vjp_br1_channel3d_p5_fp64.md; valid only while the kernel's
-# sources hash to `sources`.
-NCU_TRAFFIC = {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375877248,
-               "sources": "af369664ec0c4651e5cdb0a1b0c7b84fab0f2c0b8d340104fee33d13047585af"}
+# headline's dominant kernels (FP64) from ncu captures of the same step on the
+# 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2), scaled to the
+# 48^3 launch by the element count (the kernels' traffic is per element tile).
+# k_vjp_elem: the mean of eight consecutive launches (two adjoints: each one
+# launch without and three with the fused gather), 1,870,204,896 B x 110,592 /
+# 16,384; k_vjp_br1: 1,833,463,296 B x 110,592 / 16,384.  Summaries and
+# commands in profiles/k_vjp_elem_channel3d_p5_fp64.md and
+# profiles/k_vjp_br1_channel3d_p5_fp64.md; an entry is used only while the
+# kernels' sources hash to its `sources`.
+NCU_TRAFFIC = [
+    {"prec": "fp64", "kernel": "vjp_elem", "bytes": 12623883048,
+     "sources": "1dab9773fc96544e506804f8e44b59d6aba5f8fdb7feb37bf75d78a8b2987a8d",
+     "profile": "profiles/k_vjp_elem_channel3d_p5_fp64.md"},
+    {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375877248,
+     "sources": "af369664ec0c4651e5cdb0a1b0c7b84fab0f2c0b8d340104fee33d13047585af",
+     "profile": "profiles/k_vjp_br1_channel3d_p5_fp64.md"},
+]
 
 
 def sources_hash(root_header="vjp.cuh"):
@@ -522,11 +531,12 @@ def roofline(res, prec, pk):
                 "frac_alu_step": round(step_flops / step_s / 1e12 / alu, 4),
                 "alu_peak_tflops": round(alu, 3), "alu_peak_source": alu_src,
                 "hbm_peak_gbs": pk["hbm_gbs"]})
-    if (prec == NCU_TRAFFIC["prec"] and name == NCU_TRAFFIC["kernel"] and res["mesh"].n_elem == 110592
-            and sources_hash() == NCU_TRAFFIC["sources"]):
-        out["traffic"] = NCU_TRAFFIC["bytes"]
-        out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 32x32x16 "
-                                 "channel scaled by the element count (profiles/k_vjp_br1_channel3d_p5_fp64.md)")
+    for nt in NCU_TRAFFIC:
+        if (prec == nt["prec"] and name == nt["kernel"] and res["mesh"].n_elem == 110592
+                and sources_hash() == nt["sources"]):
+            out["traffic"] = nt["bytes"]
+            out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch on the 32x32x16 "
+                                     "channel scaled by the element count (" + nt["profile"] + ")")
     return out
 
 
