@@ -180,11 +180,21 @@ __host__ __device__ __forceinline__ void axis_relabel(const S (&U)[D + 2], const
 
 // visc_flux_axis with the axis A given at run time (0 .. D-1).  Lanes of one
 // warp often hold faces of different axes (a face's points do not fill whole
-// warps), so rather than branch to the instance for A, the state and gradient
-// are relabelled to put A first and the instance for axis 0 runs on every lane.
+// warps).  In FP64, where the kernels are bound by the FP64 pipe, branching to
+// the instance for A would run two instances in those warps, so the state and
+// gradient are relabelled to put A first (selects on the integer pipe) and
+// the instance for axis 0 runs on every lane.  FP32 kernels are bound by
+// memory and issue instead; there the relabelling's extra instructions and
+// registers cost more than the divergence, and the branch is kept.
 template <int D, typename S>
 __host__ __device__ __forceinline__ void visc_flux_axis_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A, S sgn,
                                                            const Gas<S>& g, S (&G)[D + 2]) {
+  if constexpr (sizeof(S) == 4) {
+    if (A == 0) visc_flux_axis<D, 0, S>(U, Q, sgn, g, G);
+    else if (D == 2 || A == 1) visc_flux_axis<D, 1, S>(U, Q, sgn, g, G);
+    else visc_flux_axis<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, g, G);
+    return;
+  }
   S Ur[D + 2], Qr[D][D + 2], Gr[D + 2];
   axis_relabel<D, S>(U, Q, A, Ur, Qr);
   visc_flux_axis<D, 0, S>(Ur, Qr, sgn, g, Gr);
@@ -552,8 +562,15 @@ template <int D, typename S>
 __host__ __device__ __forceinline__ void visc_flux_axis_vjp_rt(const S (&U)[D + 2], const S (&Q)[D][D + 2], int A,
                                                                S sgn, const S (&Gb)[D + 2], const Gas<S>& g,
                                                                S (&Ub)[D + 2], S (&Qb)[D][D + 2]) {
-  // the same relabelling as visc_flux_axis_rt; the accumulators are relabelled
-  // in and back out, so nothing is added beyond what the axis-0 adjoint adds
+  // the same choice as visc_flux_axis_rt (branch in FP32, relabel in FP64);
+  // the accumulators are relabelled in and back out, so nothing is added
+  // beyond what the axis-0 adjoint adds
+  if constexpr (sizeof(S) == 4) {
+    if (A == 0) visc_flux_axis_vjp<D, 0, S>(U, Q, sgn, Gb, g, Ub, Qb);
+    else if (D == 2 || A == 1) visc_flux_axis_vjp<D, 1, S>(U, Q, sgn, Gb, g, Ub, Qb);
+    else visc_flux_axis_vjp<D, (D > 2 ? 2 : 1), S>(U, Q, sgn, Gb, g, Ub, Qb);
+    return;
+  }
   S Ur[D + 2], Qr[D][D + 2], Gbr[D + 2], Ubr[D + 2], Qbr[D][D + 2];
   axis_relabel<D, S>(U, Q, A, Ur, Qr);
   axis_relabel<D, S>(Ub, Qb, A, Ubr, Qbr);
