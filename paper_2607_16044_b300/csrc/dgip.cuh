@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const 
 #pragma unroll
     for (int f = 0; f < nf; ++f) UR[f] = tr[f * nfp];
     const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]) * isJ;
-    dgip_face_fn<D, S, S, VISC, DGIP_INTERIOR, !CURV>(UL, UR, nv, M.gas, gw, tau, exm && !exp_, exp_ && !exm, Fv, HL, HR);
+    dgip_face_fn<D, S, S, VISC, DGIP_INTERIOR, !CURV, !CURV && sizeof(S) == 8>(UL, UR, nv, M.gas, gw, tau, exm && !exp_, exp_ && !exm, Fv, HL, HR);
     if (VISC) {
       const S* gl = G + ((size_t)em * NF + fm) * nf * nfp + fp;
       const S* gr = G + ((size_t)ep * NF + fo) * nf * nfp + fpn;
@@ -353,11 +353,11 @@ __global__ void __launch_bounds__(128) k_dgip_face(Mesh<S> M, Dgip<S> dp, const 
   } else {
     const S tau = dp.tk2 * dp.il[em] * isJ;
     if (ep == -1) {
-      dgip_face_fn<D, S, S, VISC, DGIP_WALL, !CURV>(UL, UL, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
+      dgip_face_fn<D, S, S, VISC, DGIP_WALL, !CURV, !CURV && sizeof(S) == 8>(UL, UL, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
     } else {
 #pragma unroll
       for (int f = 0; f < nf; ++f) UR[f] = dp.Uinf[f];
-      dgip_face_fn<D, S, S, VISC, DGIP_FARFIELD, !CURV>(UL, UR, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
+      dgip_face_fn<D, S, S, VISC, DGIP_FARFIELD, !CURV, !CURV && sizeof(S) == 8>(UL, UR, nv, M.gas, gw, tau, false, false, Fv, HL, HR);
     }
     if (VISC) {
       const S* gl = G + ((size_t)em * NF + fm) * nf * nfp + fp;
@@ -837,7 +837,7 @@ __global__ void __launch_bounds__(HD<D, P>::THREADS) k_dgip_vjp_elem(Mesh<S> M, 
 // Cotangents of one face point's inputs: interior faces by the hand-written
 // reverse mode (dgip_face_interior_vjp); boundary faces by forward-mode
 // differentiation of dgip_face_fn, one dual pass per input component.
-template <int D, typename S, bool VISC, int KIND, bool AXIS = false>
+template <int D, typename S, bool VISC, int KIND, bool AXIS = false, bool KAXIS = AXIS>
 __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D],
                                                  const Gas<S>& g, const Gas<S>& gw, S tau, bool ifL, bool ifR,
                                                  const S (&Fb)[D + 2], const S (&HLb)[D][D + 2],
@@ -846,7 +846,7 @@ __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (
   if constexpr (KIND == DGIP_INTERIOR) {
 #pragma unroll
     for (int f = 0; f < nf; ++f) ULb[f] = URb[f] = S(0);
-    dgip_face_interior_vjp<D, S, VISC, AXIS>(UL, UR, nv, g, tau, ifL, ifR, Fb, HLb, HRb, ULb, URb);
+    dgip_face_interior_vjp<D, S, VISC, AXIS, KAXIS>(UL, UR, nv, g, tau, ifL, ifR, Fb, HLb, HRb, ULb, URb);
     return;
   }
   using T = Dual<S, 1>;
@@ -860,7 +860,7 @@ __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (
       R[f] = T(UR[f]);
     }
     L[k].d[0] = S(1);
-    dgip_face_fn<D, T, S, VISC, KIND, AXIS>(L, R, nv, gd, gwd, tau, ifL, ifR, F, HL, HR);
+    dgip_face_fn<D, T, S, VISC, KIND, AXIS, KAXIS>(L, R, nv, gd, gwd, tau, ifL, ifR, F, HL, HR);
     S s = 0;
 #pragma unroll
     for (int f = 0; f < nf; ++f) s += F[f].d[0] * Fb[f];
@@ -875,13 +875,14 @@ __device__ __forceinline__ void dgip_face_fn_vjp(const S (&UL)[D + 2], const S (
 }
 
 // Host twin of dgip_face_fn_vjp (interior box face: unit normal, no
-// interface) for the operation-counting work model.
-template <int D, typename S, bool VISC>
+// interface; KAX: the axis K-products of the FP64 kernels) for the
+// operation-counting work model.
+template <int D, typename S, bool VISC, bool KAX = true>
 inline void dgip_face_fn_vjp_host(const S (&UL)[D + 2], const S (&UR)[D + 2], const S (&nv)[D], const Gas<S>& g,
                                   S tau, const S (&Fb)[D + 2], const S (&HLb)[D][D + 2], const S (&HRb)[D][D + 2],
                                   S (&ULb)[D + 2], S (&URb)[D + 2]) {
   for (int f = 0; f < D + 2; ++f) ULb[f] = URb[f] = S(0);
-  dgip_face_interior_vjp<D, S, VISC, true>(UL, UR, nv, g, tau, false, false, Fb, HLb, HRb, ULb, URb);
+  dgip_face_interior_vjp<D, S, VISC, true, KAX>(UL, UR, nv, g, tau, false, false, Fb, HLb, HRb, ULb, URb);
 }
 
 // k_dgip_vjp_face: one thread per unique face point: cotangents of both sides'
@@ -963,7 +964,7 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
       to_physical((size_t)ep * NF + fo, fpn, HRb);
     }
     const S tau = dp.tk2 * fmax(dp.il[em], dp.il[ep]) * isJ;
-    dgip_face_fn_vjp<D, S, VISC, DGIP_INTERIOR, !CURV>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
+    dgip_face_fn_vjp<D, S, VISC, DGIP_INTERIOR, !CURV, !CURV && sizeof(S) == 8>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
 #pragma unroll
     for (int f = 0; f < nf; ++f) {
       TUb[ol + f * nfp] = ULb[f];
@@ -976,11 +977,11 @@ __global__ void __launch_bounds__(128) k_dgip_vjp_face(Mesh<S> M, Dgip<S> dp, co
   } else {
     const S tau = dp.tk2 * dp.il[em] * isJ;
     if (ep == -1) {
-      dgip_face_fn_vjp<D, S, VISC, DGIP_WALL, !CURV>(UL, UL, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
+      dgip_face_fn_vjp<D, S, VISC, DGIP_WALL, !CURV, !CURV && sizeof(S) == 8>(UL, UL, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb, URb);
     } else {
 #pragma unroll
       for (int f = 0; f < nf; ++f) UR[f] = dp.Uinf[f];
-      dgip_face_fn_vjp<D, S, VISC, DGIP_FARFIELD, !CURV>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb,
+      dgip_face_fn_vjp<D, S, VISC, DGIP_FARFIELD, !CURV, !CURV && sizeof(S) == 8>(UL, UR, nv, M.gas, gw, tau, false, false, Fbar, HLb, HRb, ULb,
                                                  URb);
     }
 #pragma unroll

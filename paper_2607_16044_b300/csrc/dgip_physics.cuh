@@ -449,9 +449,11 @@ enum { DGIP_INTERIOR = 0, DGIP_WALL = 1, DGIP_FARFIELD = 2 };
 //   wall:     F = Vij(UL, mirror(UL)) + tau K_w(UL)(dw (x) n).n / |n|, HL = K_w(UL)(dw (x) n),
 //   farfield: F = F^c(U_Gamma).n + tau K(U_inf)(di (x) n).n / |n|, HL = K(U_inf)(di (x) n),
 // delta = UL - UR, dw = UL - U_w(UL), di = UL - U_inf.  gw: the gas with kappa = 0.
-// AXIS: nv = +-e_A (box faces): unit normal, and the K-products take the
-// rank-one axis form.
-template <int D, typename T, typename N, bool VISC, int KIND, bool AXIS = false>
+// AXIS: nv = +-e_A (box faces), so |nv| is not formed; KAXIS (with AXIS):
+// the K-products also take the rank-one axis form (FP64 kernels, bound by
+// the FP64 pipe; in FP32 its selects and registers cost more than the
+// arithmetic it saves).
+template <int D, typename T, typename N, bool VISC, int KIND, bool AXIS = false, bool KAXIS = AXIS>
 __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], const T (&UR)[D + 2], const N (&nv)[D],
                                                       const Gas<T>& g, const Gas<T>& gw, N tau_over_s, bool ifL,
                                                       bool ifR, T (&F)[D + 2], T (&HL)[D][D + 2],
@@ -464,7 +466,7 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
 #pragma unroll
       for (int f = 0; f < nf; ++f) dl[f] = UL[f] - UR[f];
       T KL[D][nf], KR[D][nf];
-      if (AXIS) {
+      if (KAXIS) {
         k_product_axis<D, T, N>(UL, dl, nv, g, KL);
         k_product_axis<D, T, N>(UR, dl, nv, g, KR);
       } else {
@@ -497,7 +499,7 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
       wall_state<D, T>(UL, Uw);
 #pragma unroll
       for (int f = 0; f < nf; ++f) dw[f] = UL[f] - Uw[f];
-      if (AXIS) k_product_axis<D, T, N>(UL, dw, nv, gw, HL);
+      if (KAXIS) k_product_axis<D, T, N>(UL, dw, nv, gw, HL);
       else k_product<D, T, N>(UL, dw, nv, gw, HL);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
@@ -515,7 +517,7 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
       T di[nf];
 #pragma unroll
       for (int f = 0; f < nf; ++f) di[f] = UL[f] - UR[f];
-      if (AXIS) k_product_axis<D, T, N>(UR, di, nv, g, HL);
+      if (KAXIS) k_product_axis<D, T, N>(UR, di, nv, g, HL);
       else k_product<D, T, N>(UR, di, nv, g, HL);
 #pragma unroll
       for (int f = 0; f < nf; ++f) {
@@ -535,9 +537,9 @@ __host__ __device__ __forceinline__ void dgip_face_fn(const T (&UL)[D + 2], cons
 // Written statement by statement against vij_flux (F_n(Ubar) through
 // conv_flux_all_vjp, then the wave sum |A| dU / 2 reversed through the
 // characteristic quantities of Waves) and the K-products (visc_flux_all_vjp at
-// the rank-one gradient nv (x) delta; AXIS: k_product_axis_vjp).  d|x|/dx = sign(x), sign(0) = 0, as the
+// the rank-one gradient nv (x) delta; KAXIS: k_product_axis_vjp).  d|x|/dx = sign(x), sign(0) = 0, as the
 // dual numbers take it.
-template <int D, typename S, bool VISC, bool AXIS = false>
+template <int D, typename S, bool VISC, bool AXIS = false, bool KAXIS = AXIS>
 __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D + 2], const S (&UR)[D + 2],
                                                                 const S (&nv)[D], const Gas<S>& g, S tau_over_s,
                                                                 bool ifL, bool ifR, const S (&Fb)[D + 2],
@@ -681,7 +683,7 @@ __host__ __device__ __forceinline__ void dgip_face_interior_vjp(const S (&UL)[D 
     S db[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) db[f] = S(0);
-    if constexpr (AXIS) {
+    if constexpr (KAXIS) {
       k_product_axis_vjp<D, S>(UL, dU, nv, KLb, g, ULb, db);
       k_product_axis_vjp<D, S>(UR, dU, nv, KRb, g, URb, db);
     } else {

@@ -1102,7 +1102,8 @@ void oi_matrices(dgx_handle* h) {
 // ------------------------------------------------------------ work model
 struct Pointwise {
   double conv, visc, visc_n, wall_visc, llf_unit, llf_area, conv_vjp, visc_vjp, visc_n_vjp, llf_unit_vjp,
-      llf_area_vjp, dgip_face, dgip_face_euler, dgip_face_vjp, dgip_face_euler_vjp, visc_n_axis, visc_n_axis_vjp;
+      llf_area_vjp, dgip_face, dgip_face_euler, dgip_face_vjp, dgip_face_euler_vjp, visc_n_axis, visc_n_axis_vjp,
+      dgip_face_gen, dgip_face_vjp_gen;  // *_gen: general K-products (FP32 and curved kernels)
 };
 
 template <int D>
@@ -1163,6 +1164,12 @@ Pointwise count_pointwise() {
     });
     pc.dgip_face_euler_vjp = cnt([&] {
       dgx::dgip_face_fn_vjp_host<D, C, false>(U, V, nv, g, tau, Fb, Hb, Hb, Ub, Vb);
+    });
+    pc.dgip_face_gen = cnt([&] {
+      dgx::dgip_face_fn<D, C, C, true, dgx::DGIP_INTERIOR, true, false>(U, V, nv, g, g, tau, false, false, Go, HL, HR);
+    });
+    pc.dgip_face_vjp_gen = cnt([&] {
+      dgx::dgip_face_fn_vjp_host<D, C, true, false>(U, V, nv, g, tau, Fb, Hb, Hb, Ub, Vb);
     });
   }
   return pc;
@@ -1288,7 +1295,7 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       bytes = E * ((STATE + FACE + (v ? FACE : 0)) * s + D * s);
       break;
     case DGX_K_DGIP_FACE:  // both sides' traces and G read; FF and HA of both sides written
-      flops = F * nfp * ((v ? pc.dgip_face : pc.dgip_face_euler) + (v ? 3 * nf : 0));
+      flops = F * nfp * ((v ? (!c && s == 8 ? pc.dgip_face : pc.dgip_face_gen) : pc.dgip_face_euler) + (v ? 3 * nf : 0));
       bytes = E * FACE * s * (2 + (v ? 1 + D : 0));
       break;
     case DGX_K_DGIP_ELEM:  // U, FF (+ HA) in, f out; gradient lines, flux, tangential terms, divergence + lift
@@ -1302,7 +1309,7 @@ void kernel_work(const dgx_handle* h, int kind, double& flops, double& bytes) {
       bytes = E * ((3 * STATE + FACE + (v ? D * FACE : 0)) * s + D * s);
       break;
     case DGX_K_DGIP_VJP_FACE:  // traces, FFb (+ HAb) of both sides read; TUb (+ Gb) written
-      flops = F * nfp * (v ? pc.dgip_face_vjp : pc.dgip_face_euler_vjp);
+      flops = F * nfp * (v ? (!c && s == 8 ? pc.dgip_face_vjp : pc.dgip_face_vjp_gen) : pc.dgip_face_euler_vjp);
       bytes = E * FACE * s * (3 + (v ? D + 1 : 0));
       break;
     case DGX_K_DGIP_VJP_GATHER:  // U, gpart, TUb (+ Gb) in, g out
