@@ -442,18 +442,19 @@ def time_gpu(prec, steps, warmup, dt=1e-9, profile_range=False, workload="channe
 # headline's dominant kernels (FP64) from ncu captures of the same step on the
 # 32x32x(2x8) p = 5 channel (16,384 elements, state 142 MB > L2), scaled to the
 # 48^3 launch by the element count (the kernels' traffic is per element tile).
-# k_vjp_elem: the mean of eight consecutive launches (two adjoints: each one
-# launch without and three with the fused gather), 1,870,204,896 B x 110,592 /
-# 16,384; k_vjp_br1: 1,833,463,296 B x 110,592 / 16,384.  Summaries and
+# Both from one capture of sixteen consecutive launches (two adjoints, eight
+# of each kernel).  k_vjp_elem: the mean of its eight (each adjoint: one launch
+# without and three with the fused gather), 1,870,225,152 B x 110,592 /
+# 16,384; k_vjp_br1: the mean of its eight, 1,830,859,232 B x 110,592 / 16,384.  Summaries and
 # commands in profiles/k_vjp_elem_channel3d_p5_fp64.md and
 # profiles/k_vjp_br1_channel3d_p5_fp64.md; an entry is used only while the
 # kernels' sources hash to its `sources`.
 NCU_TRAFFIC = [
-    {"prec": "fp64", "kernel": "vjp_elem", "bytes": 12623883048,
-     "sources": "1dab9773fc96544e506804f8e44b59d6aba5f8fdb7feb37bf75d78a8b2987a8d",
+    {"prec": "fp64", "kernel": "vjp_elem", "bytes": 12624019776,
+     "sources": "894eae402c2919bb0367a8e81abf69412660976934b8ca8610186d47aee37806",
      "profile": "profiles/k_vjp_elem_channel3d_p5_fp64.md"},
-    {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12375877248,
-     "sources": "af369664ec0c4651e5cdb0a1b0c7b84fab0f2c0b8d340104fee33d13047585af",
+    {"prec": "fp64", "kernel": "vjp_br1", "bytes": 12358299816,
+     "sources": "894eae402c2919bb0367a8e81abf69412660976934b8ca8610186d47aee37806",
      "profile": "profiles/k_vjp_br1_channel3d_p5_fp64.md"},
 ]
 
